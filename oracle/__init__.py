@@ -1,0 +1,270 @@
+"""FP64 CPU oracle of the in-hand tracking hot path (test infrastructure).
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path never does: it shares
+no code with the oracle, and the oracle shares none with it. The arithmetic
+lives in ``inhand_oracle.c`` (plain C, FP64); this module compiles it with gcc
+when needed and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "inhand_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DIAG = 6  # per-env diagnostics of orc_step
+NONFINITE, ESCAPED, OVERFLOW = 1, 2, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so with gcc (FP64, no contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
+                               "-fno-fast-math", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Scene(C.Structure):
+    _fields_ = [("n_shapes", C.c_int32), ("shape_first", C.c_void_p), ("shape_count", C.c_void_p),
+                ("spheres", C.c_void_p), ("palm_half", C.c_double * 3), ("n_fingers", C.c_int32),
+                ("finger_root", C.c_void_p), ("link_len", C.c_double), ("link_rad", C.c_double),
+                ("n_pads", C.c_int32), ("pad_link", C.c_void_p), ("pad_s0", C.c_void_p),
+                ("pad_s1", C.c_void_p)]
+
+
+class Config(C.Structure):
+    _fields_ = [("frame_dt", C.c_double), ("substeps", C.c_int32), ("iters", C.c_int32),
+                ("margin", C.c_double), ("beta", C.c_double), ("slop", C.c_double),
+                ("vmax", C.c_double), ("gravity", C.c_double * 3), ("tau", C.c_double),
+                ("w_force", C.c_double), ("w_contact", C.c_double), ("c_max", C.c_int32),
+                ("escape_radius", C.c_double)]
+
+
+class Opt(C.Structure):
+    _fields_ = [("elite_frac", C.c_double), ("floor_std", C.c_double * 8), ("m_lo", C.c_double),
+                ("m_hi", C.c_double), ("mu_lo", C.c_double), ("mu_hi", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            L.orc_fk.argtypes = [P, P, P]
+            L.orc_contacts.argtypes = [P, P, C.c_int, P, P, C.c_int, P]
+            L.orc_unit_inertia.argtypes = [P, C.c_int, P]
+            L.orc_step.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P]
+            L.orc_cost.argtypes = [P, C.c_int, C.c_int, P, P, P, P, C.c_int, P, P]
+            L.orc_philox4x32_10.argtypes = [P, P, P]
+            L.orc_philox4x32_10.restype = None
+            L.orc_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, P]
+            L.orc_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, P]
+            L.orc_sample_initial.argtypes = [C.c_int, P, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, C.c_double, C.c_double, C.c_uint64, P, P]
+            L.orc_cholesky8.argtypes = [P, P]
+            L.orc_optimizer.argtypes = [P, C.c_int, P, P, P, P, P, C.c_uint64, C.c_uint32, P, P]
+            L.orc_add.argtypes = [P, C.c_int, P, P]
+            L.orc_add.restype = C.c_double
+            L.orc_quat_exp.argtypes = [P, P]
+            L.orc_quat_log.argtypes = [P, P]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class OracleScene:
+    """Holds the ctypes scene record and keeps its numpy buffers alive."""
+
+    def __init__(self, scene):
+        first, count, rows = scene.flat_spheres()
+        self._keep = [np.ascontiguousarray(first, np.int32), np.ascontiguousarray(count, np.int32),
+                      np.ascontiguousarray(rows, np.float64),
+                      np.ascontiguousarray(scene.finger_root, np.float64).reshape(-1, 4),
+                      np.ascontiguousarray(scene.pad_link, np.int32),
+                      np.ascontiguousarray(scene.pad_s0, np.float64),
+                      np.ascontiguousarray(scene.pad_s1, np.float64)]
+        k = self._keep
+        self.rec = Scene(len(scene.shapes), k[0].ctypes.data, k[1].ctypes.data, k[2].ctypes.data,
+                         (C.c_double * 3)(*scene.palm_half), scene.n_fingers,
+                         k[3].ctypes.data if k[3].size else None, scene.link_len, scene.link_rad,
+                         scene.n_pads, k[4].ctypes.data, k[5].ctypes.data, k[6].ctypes.data)
+        self.n_links = 1 + 4 * scene.n_fingers
+        self.n_pads = scene.n_pads
+        self.n_joints = 4 * scene.n_fingers
+        self.scene = scene
+
+
+def make_config(sim) -> Config:
+    return Config(sim.frame_dt, sim.substeps, sim.iters, sim.margin, sim.beta, sim.slop, sim.vmax,
+                  (C.c_double * 3)(*sim.gravity), sim.tau, sim.w_force, sim.w_contact, sim.c_max,
+                  sim.escape_radius)
+
+
+def make_opt(opt) -> Opt:
+    return Opt(opt.elite_frac, (C.c_double * 8)(*opt.floor_std), opt.m_range[0], opt.m_range[1],
+               opt.mu_range[0], opt.mu_range[1])
+
+
+def pose8_to7(p8: np.ndarray) -> np.ndarray:
+    """(…, 8) float pose (xyz, pad, wxyz) -> (…, 7) float64 (xyz, wxyz), exact."""
+    p8 = np.asarray(p8)
+    return np.concatenate([p8[..., :3], p8[..., 4:8]], axis=-1).astype(np.float64)
+
+
+def vel8_to6(v8: np.ndarray) -> np.ndarray:
+    v8 = np.asarray(v8)
+    return np.concatenate([v8[..., :3], v8[..., 4:7]], axis=-1).astype(np.float64)
+
+
+def fk(osc: OracleScene, q) -> np.ndarray:
+    q = np.ascontiguousarray(q, np.float64)
+    out = np.zeros((osc.n_links, 7))
+    lib().orc_fk(C.byref(osc.rec), _p(q), _p(out))
+    return out
+
+
+def contacts(osc: OracleScene, sim, shape: int, pose7, link_pose, max_out: int = 4096) -> np.ndarray:
+    cfg = make_config(sim)
+    pose7 = np.ascontiguousarray(pose7, np.float64)
+    lp = np.ascontiguousarray(link_pose, np.float64)
+    out = np.zeros((max_out, 12))
+    n = lib().orc_contacts(C.byref(osc.rec), C.byref(cfg), shape, _p(pose7), _p(lp), max_out, _p(out))
+    return out[:min(n, max_out)]
+
+
+def unit_inertia(osc: OracleScene, shape: int) -> np.ndarray:
+    out = np.zeros(9)
+    lib().orc_unit_inertia(C.byref(osc.rec), shape, _p(out))
+    return out.reshape(3, 3)
+
+
+class State:
+    """FP64 state of N environments: pose (N,7), vel (N,6), theta (N,2), status (N,)."""
+
+    def __init__(self, pose7, vel6, theta, shape=None, iters=None, status=None):
+        self.pose = np.ascontiguousarray(pose7, np.float64).copy()
+        self.vel = np.ascontiguousarray(vel6, np.float64).copy()
+        self.theta = np.ascontiguousarray(theta, np.float64).copy()
+        n = self.pose.shape[0]
+        self.shape = np.zeros(n, np.int32) if shape is None else np.ascontiguousarray(shape, np.int32).copy()
+        self.iters = None if iters is None else np.ascontiguousarray(iters, np.int32).copy()
+        self.status = np.zeros(n, np.int32) if status is None else np.ascontiguousarray(status, np.int32).copy()
+
+    @property
+    def n(self) -> int:
+        return self.pose.shape[0]
+
+    def subset(self, idx):
+        return State(self.pose[idx], self.vel[idx], self.theta[idx], self.shape[idx],
+                     None if self.iters is None else self.iters[idx], self.status[idx])
+
+
+def step(osc: OracleScene, sim, st: State, q_traj, frame0: int, n_frames: int = 1):
+    """Advance `st` in place; returns (forces (N,P,3) of the last frame, diag (N,6))."""
+    cfg = make_config(sim)
+    q = np.ascontiguousarray(q_traj, np.float64)
+    forces = np.zeros((st.n, osc.n_pads, 3))
+    diag = np.zeros((st.n, DIAG))
+    lib().orc_step(C.byref(osc.rec), C.byref(cfg), st.n, _p(q), frame0, n_frames, _p(st.pose),
+                   _p(st.vel), _p(st.theta), _p(st.shape),
+                   None if st.iters is None else _p(st.iters), _p(st.status), _p(forces), _p(diag))
+    return forces, diag
+
+
+def cost(sim, forces, obs, status, c_sum, n_window: int):
+    """Accumulates one frame's cost into c_sum (in place); returns (i*, c_mean, frame cost)."""
+    cfg = make_config(sim)
+    forces = np.ascontiguousarray(forces, np.float64)
+    obs = np.ascontiguousarray(obs, np.float64)
+    status = np.ascontiguousarray(status, np.int32)
+    n, p = forces.shape[0], forces.shape[1]
+    c_mean = np.zeros(n)
+    c_frame = np.zeros(n)
+    i = lib().orc_cost(C.byref(cfg), n, p, _p(forces), _p(obs), _p(status), _p(c_sum), n_window,
+                       _p(c_mean), _p(c_frame))
+    return i, c_mean, c_frame
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def normals(seed: int, stream: int, index: int, env: int, n: int) -> np.ndarray:
+    out = np.zeros(n)
+    lib().orc_normals(seed, stream, index, env, n, _p(out))
+    return out
+
+
+def uniforms(seed: int, stream: int, index: int, env: int, blk: int) -> np.ndarray:
+    out = np.zeros(2)
+    lib().orc_uniforms(seed, stream, index, env, blk, _p(out))
+    return out
+
+
+def sample_initial(n: int, nominal7, init, seed: int):
+    nominal7 = np.ascontiguousarray(nominal7, np.float64)
+    pose = np.zeros((n, 7))
+    theta = np.zeros((n, 2))
+    lib().orc_sample_initial(n, _p(nominal7), init.sigma_p, init.sigma_r, init.m_range[0],
+                             init.m_range[1], init.mu_range[0], init.mu_range[1], seed,
+                             _p(pose), _p(theta))
+    return pose, theta
+
+
+def cholesky8(A) -> tuple[int, np.ndarray]:
+    A = np.ascontiguousarray(A, np.float64)
+    L = np.zeros((8, 8))
+    rc = lib().orc_cholesky8(_p(A), _p(L))
+    return rc, L
+
+
+def optimizer(opt, st: State, C_mean, seed: int, update_index: int):
+    """In-place update of st; returns (i*, parent (N,), stats dict)."""
+    o = make_opt(opt)
+    Cm = np.ascontiguousarray(C_mean, np.float64)
+    parent = np.zeros(st.n, np.int32)
+    stats = np.zeros(139)
+    i = lib().orc_optimizer(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
+                            _p(st.status), seed, update_index, _p(parent), _p(stats))
+    return i, parent, {"mean": stats[:8].copy(), "cov": stats[8:72].reshape(8, 8).copy(),
+                       "L": stats[72:136].reshape(8, 8).copy(), "k": int(stats[136]),
+                       "istar": int(stats[137]), "sd": float(stats[138])}
+
+
+def add(osc: OracleScene, shape: int, pose_a7, pose_b7) -> float:
+    a = np.ascontiguousarray(pose_a7, np.float64)
+    b = np.ascontiguousarray(pose_b7, np.float64)
+    return float(lib().orc_add(C.byref(osc.rec), shape, _p(a), _p(b)))
+
+
+def quat_exp(w3) -> np.ndarray:
+    w = np.ascontiguousarray(w3, np.float64)
+    out = np.zeros(4)
+    lib().orc_quat_exp(_p(w), _p(out))
+    return out
+
+
+def quat_log(q4) -> np.ndarray:
+    q = np.ascontiguousarray(q4, np.float64)
+    out = np.zeros(3)
+    lib().orc_quat_log(_p(q), _p(out))
+    return out
