@@ -1,0 +1,308 @@
+"""Benchmark of the in-hand tracking hot path on one GB300 (or N replicas).
+
+A step is one tracking window of Algorithm 1 over N environments: T = 10
+frames, each a batched simulation step (kinematic hand, narrowphase, Jacobi
+contact solve, integration, sensor pads) followed by the FP64 cost and the
+argmin estimate, then one optimizer update (elite-weighted resample and
+perturbation). The default workload is the N = 1024 tracking loop (cylinder
+of 64 spheres, 4 fingers x 4 capsule links + palm, 8 pads, 20 Jacobi
+iterations, 2 substeps at 30 Hz). Inputs are seeded and synthetic.
+
+Output: one JSON line (metric env-steps/s: environment-frames advanced per
+second including cost, argmin and the amortised optimizer update).
+  --impl ours        the CUDA path through libinhand.so (default)
+  --impl reference   the FP64 CPU oracle on the same workload (bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP32 operations of the step, counted from the kernel's source
+# per unit of work (an FMA counts as 2, a compare/min/max/select as 1, sqrt /
+# rsqrt / division / sin / cos as 1 each). The counts are attached to the
+# work counters the step kernel reports (pairs tested after culling, contacts,
+# contact-iterations, env-substeps).
+FLOP_PER_ENV_SUBSTEP = 150     # gravity, rotation matrix, world inverse inertia,
+                               # link cull (21 links x 20), integration
+FLOP_PER_PAIR = 40             # sphere to world (15), capsule/box distance (25)
+FLOP_PER_CONTACT = 95          # effective masses, bias, link velocity, pad sum
+FLOP_PER_CONTACT_ITER = 62     # relative velocity, normal/tangent update,
+                               # cone clamp, relaxation, impulse/moment sums
+FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
+                               # the body velocity update
+# bytes of HBM traffic per env-frame the step must move: state in/out
+# (pose, vel 64 B each way), params (8 B), shape/iters/status (12 B), forces
+STATE_BYTES_PER_ENV = 64 + 64 + 8 + 12 + 4
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="tracking_cyl64")
+    p.add_argument("--n-envs", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 oracle as it stands on the host cores: whole tracking windows on
+    a bounded sample of environments of the same workload."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2002_12160_gb300 import workloads as W
+    T = 10
+    n_sample = 16
+    wl = W.make_workload(args.workload, n_envs=n_sample, frames=(args.warmup + args.steps) * T + 1)
+    osc = O.OracleScene(wl.scene)
+    pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed)
+    st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
+    gt = O.State(O.pose8_to7(wl.nominal_pose)[None], np.zeros((1, 6)), np.array([wl.theta_gt]))
+    times = []
+    frame = 0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        c_sum = np.zeros(n_sample)
+        for k in range(T):
+            obs, _ = O.step(osc, wl.sim, gt, wl.q_traj, frame, 1)
+            forces, _ = O.step(osc, wl.sim, st, wl.q_traj, frame, 1)
+            i, c_mean, _ = O.cost(wl.sim, forces, obs[0], st.status, c_sum, k + 1)
+            frame += 1
+        O.optimizer(wl.opt, st, c_mean, wl.seed, s)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n_sample * T / (ms / 1e3)
+    line = {"impl": "reference", "metric": "env-steps/s", "value": value, "unit": "env-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n_envs_sampled": n_sample,
+                                            "window_frames": T},
+            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sample} envs x {T}-frame windows incl. the ground-truth env"},
+            "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(workload, budget_s=12.0):
+    """Oracle env-steps/s on the host, single thread, on a bounded sample."""
+    import oracle as O
+    from paper_2002_12160_gb300 import workloads as W
+    T, n_sample = 10, 32
+    wl = W.make_workload(workload, n_envs=n_sample, frames=400)
+    osc = O.OracleScene(wl.scene)
+    pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed)
+    st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
+    frames = 0
+    t0 = time.perf_counter()
+    f = 0
+    upd = 0
+    while time.perf_counter() - t0 < budget_s and f + T < 400:
+        c_sum = np.zeros(n_sample)
+        for k in range(T):
+            forces, _ = O.step(osc, wl.sim, st, wl.q_traj, f, 1)
+            _, c_mean, _ = O.cost(wl.sim, forces, forces[0], st.status, c_sum, k + 1)
+            f += 1
+            frames += 1
+        O.optimizer(wl.opt, st, c_mean, wl.seed, upd)
+        upd += 1
+    el = time.perf_counter() - t0
+    return {"value": n_sample * frames / el, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_sample} envs x {frames} frames of {workload} (windows of {T} + optimizer), {el:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2002_12160_gb300 import inhand, tracking, workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T = 10
+    n_windows = args.warmup + args.steps
+    frames = n_windows * T
+    wl = W.make_workload(args.workload, n_envs=args.n_envs, frames=frames)
+    seed = wl.seed + 7919 * rank   # independent replicas per rank
+    tr = tracking.Tracker(wl, seed=seed)
+    tr.prepare()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
+               for _ in range(args.steps)]
+    for w in range(args.warmup):
+        tr.window(w)
+    torch.cuda.synchronize()
+    tr.sim.sim_work_counters(reset=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            tr.window(args.warmup + s, step_events=step_ev[s])
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms_steps = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
+    ms_step_kernel = [a.elapsed_time(b) for s in range(args.steps) for (a, b) in step_ev[s]]
+    work = tr.sim.sim_work_counters(reset=True)
+    ms = sum(ms_steps) / len(ms_steps)
+    ms = max_over_ranks(ms, world)
+    n = tr.n
+    value = world * n * T / (ms / 1e3)
+    # roofline of the dominant kernel (the batched step), FP32 issue bound
+    launches = args.steps * T
+    flops = (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP) + work["pairs"] * FLOP_PER_PAIR +
+             work["contacts"] * FLOP_PER_CONTACT + work["contact_iters"] * FLOP_PER_CONTACT_ITER)
+    flops += work.get("env_iters", 0) * FLOP_PER_ENV_ITER
+    per_launch_flops = flops / launches
+    step_ms = sum(ms_step_kernel) / len(ms_step_kernel)
+    achieved = per_launch_flops / (step_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    # e2e through the public API with host buffers
+    e2e = tr.e2e_windows(args.warmup + args.steps - 2, 2)
+    add_mm = tr.add_mm()
+    line = {"metric": "env-steps/s", "value": value, "unit": "env-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n_envs": n, "window_frames": T,
+                       "spheres": int(len(wl.scene.shapes[0])), "links": wl.scene.n_links,
+                       "pads": wl.scene.n_pads, "iters": int(wl.sim.iters), "substeps": wl.sim.substeps,
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}"},
+            "tracking_frames_per_s": world * T / (ms / 1e3) if world == 1 else T / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "step_kernel", "step_kernel_ms": step_ms,
+                         "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"},
+            "hbm": {"step_bytes_per_launch": n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12,
+                    "achieved_gbs": (n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12) / (step_ms / 1e3) / 1e9,
+                    "peak_gbs": 6777.0},
+            "work_per_launch": {k: v / launches for k, v in work.items()},
+            "clocks": clocks,
+            "gpu_launches": args.steps * (2 * T + 2),
+            "e2e": e2e,
+            "add_mm_argmin_env": add_mm}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tr.close()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

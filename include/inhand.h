@@ -1,0 +1,228 @@
+/*
+ * inhand.h -- C ABI of libinhand.so, the GB300 (sm_103a) hot path of
+ * sim-in-the-loop in-hand object pose tracking (arXiv 2002.12160).
+ *
+ * The library steps N independent hand-plus-object simulations (the forward
+ * model s_{t+1} = f(s_t, u_t, theta) of Sec. III-A), reads the contact-sensor
+ * forces c_t^(l) (Sec. III-A), scores every environment against the observed
+ * forces and tracks i* = argmin_i C_i (Eqs. 1-2, Sec. III-C), and runs the
+ * periodic resample-and-perturb update of pose, mass and friction
+ * (Sec. III-D, Algorithm 1). Every computation runs in CUDA kernels.
+ *
+ * Conventions, shared by every entry point:
+ *  - Units are SI (m, kg, s, N, rad). The palm is at the origin, its top face
+ *    at z = +palm_half[2], gravity is `gravity` (normally (0, 0, -9.81)).
+ *  - Array arguments documented "device" are device pointers owned by the
+ *    caller; "host" arguments are read during the call and may be freed after
+ *    it returns. Nothing here takes ownership of a caller's buffer.
+ *  - Per-environment layouts (row-major, N rows):
+ *      pose   float[N][8]: position x y z, 0, quaternion w x y z (world frame)
+ *      vel    float[N][8]: linear x y z, 0, angular x y z (world frame), 0
+ *      params float[N][2]: mass (kg), friction coefficient mu
+ *      forces float[N][P][3]: force on each sensor pad by the object (N)
+ *  - Every call is asynchronous on the handle's CUDA stream (sim_create,
+ *    sim_set_stream). Host-detectable errors (bad arguments) return at once
+ *    and change nothing; device-side conditions are reported per environment
+ *    through the env_status bits below and never stop the batch.
+ *  - A handle is not thread safe; different handles are independent.
+ *  - No call throws; every call returns an ih_status. sim_last_error() gives
+ *    a message for the last non-IH_OK status of that handle.
+ */
+#ifndef INHAND_H
+#define INHAND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ih_sim ih_sim;
+
+typedef enum {
+    IH_OK = 0,
+    IH_ERR_ARG = 1,      /* invalid argument (nothing was launched) */
+    IH_ERR_CUDA = 2,     /* a CUDA runtime call or launch failed */
+    IH_ERR_OOM = 3,      /* device allocation failed */
+    IH_ERR_TIMEOUT = 4,  /* reserved: no kernel here waits on another */
+    IH_ERR_STATE = 5,    /* call not valid in the handle's current state */
+    IH_ERR_OVERFLOW = 6  /* a size exceeds a fixed capacity */
+} ih_status;
+
+/* per-environment status bits (sticky until the optimizer replaces the env) */
+#define IH_ENV_NONFINITE 1   /* a pose or velocity component is not finite */
+#define IH_ENV_ESCAPED   2   /* object farther than escape_radius from the palm */
+#define IH_ENV_OVERFLOW  4   /* more contacts than c_max in one substep */
+#define IH_ENV_INVALID   8   /* sim_set_state received an invalid value */
+
+/* Fixed geometry shared by all environments (host arrays, copied at create).
+ * Link 0 is the palm box; finger f has links 1+4f+j, j = 0..3, each a capsule
+ * of length link_len and radius link_rad along its frame's +x axis:
+ *   T_0 = Trans(root_f) Rz(yaw_f + q_{4f}) Ry(-pi/2),
+ *   T_j = T_{j-1} Trans(link_len, 0, 0) Ry(-q_{4f+j}), j = 1..3.
+ * Object shapes are clusters of spheres in the body frame; the library takes
+ * the centroid of the sphere centres as the body origin. A contact on link l
+ * at axial fraction t belongs to the first pad k with pad_link[k] == l and
+ * pad_s0[k] <= t < pad_s1[k] (t <= 1 when pad_s1[k] >= 1); palm contacts
+ * belong to the first pad whose link is 0. */
+typedef struct {
+    int32_t n_shapes;             /* >= 1 */
+    const int32_t *shape_first;   /* host [n_shapes] first row in `spheres` */
+    const int32_t *shape_count;   /* host [n_shapes] spheres, 1..IH_MAX_SPHERES */
+    const float *spheres;         /* host [total][4] centre x y z, radius */
+    float palm_half[3];           /* palm box half extents */
+    int32_t n_fingers;            /* 0..IH_MAX_FINGERS */
+    const float *finger_root;     /* host [F][4] root x y z, yaw */
+    float link_len, link_rad;
+    int32_t n_pads;               /* 1..IH_MAX_PADS */
+    const int32_t *pad_link;      /* host [P] */
+    const float *pad_s0, *pad_s1; /* host [P] */
+} ih_scene;
+
+#define IH_MAX_SPHERES 1024
+#define IH_MAX_FINGERS 7
+#define IH_MAX_PADS 32
+#define IH_MAX_CONTACTS 256
+
+/* Step, sensor and cost constants. */
+typedef struct {
+    int32_t n_envs;        /* N >= 1 */
+    int32_t max_frames;    /* capacity of the commanded-trajectory table */
+    float frame_dt;        /* 1/30 s */
+    int32_t substeps;      /* ns >= 1, h = frame_dt / ns */
+    int32_t iters;         /* Jacobi iterations when no per-env count is set */
+    float margin;          /* pair is a contact when its gap d < margin */
+    float beta, slop, vmax;/* bias: d/h if d > 0 else max(beta min(d+slop,0)/h, -vmax) */
+    float gravity[3];
+    float tau;             /* sensor on/off threshold on |c| (N) */
+    float w_force;         /* weight of sum_l |c_sim - c_obs|^2 */
+    float w_contact;       /* weight of each on/off mismatch */
+    int32_t c_max;         /* contacts per env per substep, <= IH_MAX_CONTACTS */
+    float escape_radius;   /* |x| beyond this marks the env escaped */
+} ih_config;
+
+/* Optimizer constants (elite-weighted Gaussian resample). */
+typedef struct {
+    float elite_frac;      /* k = max(1, floor(elite_frac N)) elites */
+    float floor_std[8];    /* exploration floor: x y z (m), rotation (rad) x3, m (kg), mu */
+    float m_lo, m_hi;      /* clamp of the perturbed mass */
+    float mu_lo, mu_hi;    /* clamp of the perturbed friction */
+} ih_opt_config;
+
+/* Create a simulator for cfg->n_envs environments on the current device.
+ * Copies the scene, allocates the handle's device state (poses, velocities,
+ * parameters, forces, cost sums, link-pose table, optimizer scratch) and
+ * derives each shape's centroid frame, unit inertia and bounding radius on
+ * the GPU. `seed` keys every random stream (Philox4x32-10). `stream` is a
+ * cudaStream_t (NULL = legacy default stream). Errors: IH_ERR_ARG for a bad
+ * scene or config, IH_ERR_OOM, IH_ERR_CUDA. Passage: Sec. III-B (K
+ * concurrent simulations initialised from s_0). */
+ih_status sim_create(const ih_scene *scene, const ih_config *cfg, uint64_t seed,
+                     void *stream, ih_sim **out);
+
+/* Free the handle and everything it allocated (synchronises its stream). */
+ih_status sim_destroy(ih_sim *sim);
+
+/* Use another cudaStream_t for subsequent calls. */
+ih_status sim_set_stream(ih_sim *sim, void *stream);
+
+/* Upload commanded joint angles u_t (desired joint positions, Sec. III-A) for
+ * frames [frame0, frame0 + n_frames) and compute the kinematic hand's link
+ * poses at every substep boundary of those frames. q is device
+ * float[n_frames + 1][4F]: row k holds the command at the start of frame
+ * frame0 + k (the last row closes the last frame); it may be NULL when the
+ * hand has no fingers. Within a frame the hand moves linearly in joint
+ * space. Errors: IH_ERR_ARG if the range exceeds max_frames. The same
+ * command goes to every environment (Sec. III-B). */
+ih_status sim_set_commands(ih_sim *sim, int32_t frame0, int32_t n_frames, const float *q);
+
+/* Initial sampling (Sec. III-D, Algorithm 1 initialisation): for every env i,
+ *   x = x0 + sigma_p n_{0..2},  R = exp([sigma_r n_{3..5}]x) R0,
+ *   m ~ U[m_lo, m_hi], mu ~ U[mu_lo, mu_hi], velocities 0, status 0,
+ * with n standard normals (Box-Muller, FP64) of Philox4x32-10 counter
+ * (0, 0, i, block 0..2) and the uniforms from block 3, key = seed.
+ * nominal_pose is host float[8] (layout of `pose`). Also clears the cost
+ * window. Errors: IH_ERR_ARG for negative sigmas or empty ranges. */
+ih_status sim_sample_initial(ih_sim *sim, const float *nominal_pose, float sigma_p, float sigma_r,
+                             float m_lo, float m_hi, float mu_lo, float mu_hi);
+
+/* Overwrite the state of all N environments from device arrays (pose, vel,
+ * params as above; shape_id int32[N] and iters int32[N] may be NULL to keep
+ * the current values). Values are checked on the GPU: a non-finite number,
+ * mass <= 0, mu < 0, a shape id outside [0, n_shapes) or an iteration count
+ * outside [0, 4096] sets IH_ENV_INVALID for that env (which then costs +inf
+ * and is not stepped). Other status bits are cleared. */
+ih_status sim_set_state(ih_sim *sim, const float *pose, const float *vel, const float *params,
+                        const int32_t *shape_id, const int32_t *iters);
+
+/* Copy the state out to device arrays; any pointer may be NULL. */
+ih_status sim_get_state(ih_sim *sim, float *pose, float *vel, float *params, int32_t *env_status);
+
+/* Advance every environment over frames [frame0, frame0 + n_frames) with the
+ * commands set by sim_set_commands (Algorithm 1, "step simulation"). Per
+ * substep: gravity prediction, object spheres to world, bounding-sphere cull,
+ * sphere-capsule / sphere-box narrowphase (a pair is a contact when its gap
+ * d < margin), per-contact effective masses and bias, `iters` Jacobi
+ * projected-impulse iterations with Coulomb friction and 1/n_c relaxation,
+ * symplectic Euler with the exact rotation update, and sensor-pad sums.
+ * Environments with IH_ENV_NONFINITE/ESCAPED/OVERFLOW/INVALID are skipped.
+ * The pad forces of the last frame stepped stay in the handle for
+ * sim_read_sensors and cost_eval. Errors: IH_ERR_ARG for a frame range
+ * without commands. */
+ih_status sim_step(ih_sim *sim, int32_t frame0, int32_t n_frames);
+
+/* Copy the last frame's pad forces (device float[N][P][3], world frame,
+ * averaged over the frame's substeps: the observation c_t^(l) of Sec. III-A)
+ * and the status bits (device int32[N]); either may be NULL. */
+ih_status sim_read_sensors(ih_sim *sim, float *forces, int32_t *env_status);
+
+/* Score the last stepped frame against the observation (Sec. III-C, force and
+ * contact-state terms; Eqs. 1-2 with the running mean of Algorithm 1):
+ *   cost_i = sum_l [ w_force |c_il - o_l|^2 + w_contact ((|c_il| > tau) != (|o_l| > tau)) ]
+ * in FP64 (+inf for a skipped env), C_i = (sum of costs since the window
+ * start) / (frames in the window), i* = argmin C_i (NaN = +inf, ties to the
+ * lowest index). obs is device float[P][3]. Outputs (device, any may be
+ * NULL): cost_mean double[N], argmin int32[1], est_pose float[8] (pose of
+ * i*). */
+ih_status cost_eval(ih_sim *sim, const float *obs, double *cost_mean, int32_t *argmin,
+                    float *est_pose);
+
+/* Optimizer update (Sec. III-D, population-based variant with elite-weighted
+ * Gaussian exploration; Algorithm 1, "update simulations"), on the current
+ * window means C_i:
+ *  1. rank by (C_i, i); the first k = max(1, floor(elite_frac N)) are elites;
+ *  2. w_j = exp(-(C_j - C_min) / s) over the elites, s = standard deviation of
+ *     their finite costs (uniform when s < 1e-12), normalised (FP64);
+ *  3. z = [x, log(R R_{i*}^T), m, mu]; weighted mean and covariance Sigma_w
+ *     over the elites; L = chol(Sigma_w + diag(floor_std^2)) (FP64);
+ *  4. non-elites, in index order r = 0..N-k-1, draw parents by systematic
+ *     resampling over the elites in index order at (u + r)/(N - k), u from
+ *     Philox counter (2, update_index, 0, 0);
+ *  5. each non-elite copies its parent's pose, velocity, parameters and
+ *     status and adds L eps (eps from counter (1, update_index, i, 0..3)):
+ *     x += d_0..2, R <- exp([d_3..5]x) R, m += d_6, mu += d_7, then clamps.
+ * Elites are unchanged. The cost window is reset. Outputs (device, may be
+ * NULL): argmin int32[1] = i*, parent int32[N] (self for elites).
+ * Errors: IH_ERR_ARG for elite_frac outside (0, 1] or bad clamps;
+ * IH_ERR_STATE when no frame has been scored since the last reset. */
+ih_status optimizer_update(ih_sim *sim, const ih_opt_config *opt, uint32_t update_index,
+                           int32_t *argmin, int32_t *parent);
+
+/* Work done by sim_step since the last call with reset != 0: out[0] = pair
+ * tests after culling, out[1] = contacts, out[2] = contact-iterations,
+ * out[3] = env-substeps stepped, out[4] = solver iterations summed over
+ * env-substeps with contacts (host uint64[5]; synchronises the stream). */
+ih_status sim_work_counters(ih_sim *sim, uint64_t *out, int32_t reset);
+
+/* Wait for the handle's stream; IH_ERR_CUDA if a kernel failed. */
+ih_status sim_sync(ih_sim *sim);
+
+/* Message for the handle's last error (never NULL, valid until the next
+ * call on that handle). */
+const char *sim_last_error(const ih_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INHAND_H */

@@ -1,0 +1,394 @@
+// api.cu -- host side of the C ABI declared in include/inhand.h: argument
+// checks, device allocations owned by the handle, and kernel launches on the
+// handle's stream. No arithmetic of the method runs here.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace ih;
+
+struct ih_sim {
+    // scene
+    int n_shapes = 0, n_fingers = 0, n_links = 0, n_pads = 0, n_joints = 0, total_spheres = 0;
+    float palm_half[3] = {0, 0, 0};
+    float link_len = 0, link_rad = 0;
+    // config
+    ih_config cfg{};
+    DevConfig dcfg{};
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    StepVariant variant{32, 4, 128};
+    int step_grid = 0;
+    // device buffers
+    float4 *spheres_raw = nullptr, *spheres = nullptr, *finger_root = nullptr;
+    int *shape_first = nullptr, *shape_count = nullptr, *pad_link = nullptr;
+    float *shape_jinv = nullptr, *shape_bound = nullptr, *pad_s0 = nullptr, *pad_s1 = nullptr;
+    float4 *link_tab = nullptr;
+    float4 *pose = nullptr, *vel = nullptr;
+    float2 *params = nullptr;
+    int *shape = nullptr, *iters = nullptr, *status = nullptr;
+    float *forces = nullptr;
+    double *c_sum = nullptr;
+    int *n_window = nullptr, *argmin = nullptr;
+    double *part_c = nullptr;
+    int *part_i = nullptr;
+    unsigned int *done = nullptr;
+    unsigned long long *work = nullptr;
+    unsigned char *is_elite = nullptr;
+    int *rank = nullptr, *elite_env = nullptr;
+    double *elite_cdf = nullptr, *chol = nullptr;
+    std::vector<void *> owned;
+    // host bookkeeping
+    std::vector<char> frame_ready;   // commands uploaded for frame f
+    int window_frames = 0;           // frames scored since the last reset
+    bool stepped = false;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+ih_status fail(ih_sim *s, ih_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf; else g_create_err = buf;
+    return code;
+}
+
+ih_status cuda_fail(ih_sim *s, cudaError_t e, const char *what) {
+    return fail(s, e == cudaErrorMemoryAllocation ? IH_ERR_OOM : IH_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t dalloc(ih_sim *s, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) return e;
+    s->owned.push_back(q);
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+DevScene dev_scene(const ih_sim *s) {
+    DevScene d;
+    d.n_shapes = s->n_shapes; d.n_fingers = s->n_fingers; d.n_links = s->n_links;
+    d.n_pads = s->n_pads; d.n_joints = s->n_joints;
+    d.palm_hx = s->palm_half[0]; d.palm_hy = s->palm_half[1]; d.palm_hz = s->palm_half[2];
+    d.link_len = s->link_len; d.link_rad = s->link_rad;
+    d.spheres = s->spheres; d.shape_first = s->shape_first; d.shape_count = s->shape_count;
+    d.shape_jinv = s->shape_jinv; d.shape_bound = s->shape_bound; d.finger_root = s->finger_root;
+    d.pad_link = s->pad_link; d.pad_s0 = s->pad_s0; d.pad_s1 = s->pad_s1;
+    return d;
+}
+
+// Step-kernel shape: the smallest group width whose contact capacity covers
+// c_max, with register-resident contacts per lane kept at 4 or 8.
+StepVariant pick_variant(int c_max) {
+    const StepVariant order[] = {{32, 2, 128}, {32, 4, 128}, {32, 8, 128}};
+    for (const auto &v : order)
+        if (step_variant_max_contacts(v) >= c_max) return v;
+    return {32, 8, 128};
+}
+
+int grid_for(const StepVariant &v, int N) {
+    const int groups_per_block = v.block / v.group;
+    const int need = (N + groups_per_block - 1) / groups_per_block;
+    return need > 0 ? need : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, void *stream,
+                     ih_sim **out) {
+    if (!sc || !cfg || !out) return fail(nullptr, IH_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (sc->n_shapes < 1 || !sc->shape_first || !sc->shape_count || !sc->spheres)
+        return fail(nullptr, IH_ERR_ARG, "scene needs at least one shape");
+    if (sc->n_fingers < 0 || sc->n_fingers > IH_MAX_FINGERS)
+        return fail(nullptr, IH_ERR_ARG, "n_fingers must be in [0, %d]", IH_MAX_FINGERS);
+    if (sc->n_fingers > 0 && !sc->finger_root) return fail(nullptr, IH_ERR_ARG, "finger_root is null");
+    if (sc->n_pads < 1 || sc->n_pads > IH_MAX_PADS || !sc->pad_link || !sc->pad_s0 || !sc->pad_s1)
+        return fail(nullptr, IH_ERR_ARG, "n_pads must be in [1, %d] with pad arrays", IH_MAX_PADS);
+    if (!finite_pos(sc->palm_half[0]) || !finite_pos(sc->palm_half[1]) || !finite_pos(sc->palm_half[2]) ||
+        !finite_pos(sc->link_len) || !(sc->link_rad >= 0.0f))
+        return fail(nullptr, IH_ERR_ARG, "palm and link dimensions must be positive");
+    const int n_links = 1 + 4 * sc->n_fingers;
+    int total = 0;
+    for (int k = 0; k < sc->n_shapes; ++k) {
+        const int f = sc->shape_first[k], c = sc->shape_count[k];
+        if (c < 1 || c > IH_MAX_SPHERES || f < 0)
+            return fail(nullptr, IH_ERR_ARG, "shape %d: count must be in [1, %d]", k, IH_MAX_SPHERES);
+        total = std::max(total, f + c);
+    }
+    for (int j = 0; j < total; ++j)
+        if (!(sc->spheres[4 * j + 3] > 0.0f) || !std::isfinite(sc->spheres[4 * j]) ||
+            !std::isfinite(sc->spheres[4 * j + 1]) || !std::isfinite(sc->spheres[4 * j + 2]))
+            return fail(nullptr, IH_ERR_ARG, "sphere %d is invalid", j);
+    for (int p = 0; p < sc->n_pads; ++p)
+        if (sc->pad_link[p] < 0 || sc->pad_link[p] >= n_links || !(sc->pad_s0[p] <= sc->pad_s1[p]))
+            return fail(nullptr, IH_ERR_ARG, "pad %d is invalid", p);
+    if (cfg->n_envs < 1 || cfg->max_frames < 1 || cfg->substeps < 1 || cfg->iters < 0 ||
+        !finite_pos(cfg->frame_dt) || !(cfg->margin >= 0.0f) || !(cfg->beta >= 0.0f) ||
+        !(cfg->slop >= 0.0f) || !(cfg->vmax >= 0.0f) || !(cfg->tau >= 0.0f) ||
+        cfg->c_max < 1 || cfg->c_max > IH_MAX_CONTACTS || !finite_pos(cfg->escape_radius))
+        return fail(nullptr, IH_ERR_ARG, "invalid config");
+
+    ih_sim *s = new ih_sim();
+    s->n_shapes = sc->n_shapes; s->n_fingers = sc->n_fingers; s->n_links = n_links;
+    s->n_pads = sc->n_pads; s->n_joints = 4 * sc->n_fingers; s->total_spheres = total;
+    for (int k = 0; k < 3; ++k) s->palm_half[k] = sc->palm_half[k];
+    s->link_len = sc->link_len; s->link_rad = sc->link_rad;
+    s->cfg = *cfg;
+    s->seed = seed;
+    s->stream = static_cast<cudaStream_t>(stream);
+    DevConfig &d = s->dcfg;
+    d.h = cfg->frame_dt / (float)cfg->substeps;
+    d.substeps = cfg->substeps; d.iters = cfg->iters;
+    d.margin = cfg->margin; d.beta = cfg->beta; d.slop = cfg->slop; d.vmax = cfg->vmax;
+    d.gx = cfg->gravity[0]; d.gy = cfg->gravity[1]; d.gz = cfg->gravity[2];
+    d.tau = cfg->tau; d.w_force = cfg->w_force; d.w_contact = cfg->w_contact;
+    d.c_max = cfg->c_max; d.escape_radius = cfg->escape_radius;
+    s->variant = pick_variant(cfg->c_max);
+    const int N = cfg->n_envs, P = sc->n_pads, F = sc->n_fingers;
+
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(s, &s->spheres_raw, total)); A(dalloc(s, &s->spheres, total));
+    A(dalloc(s, &s->shape_first, sc->n_shapes)); A(dalloc(s, &s->shape_count, sc->n_shapes));
+    A(dalloc(s, &s->shape_jinv, 6 * sc->n_shapes)); A(dalloc(s, &s->shape_bound, sc->n_shapes));
+    A(dalloc(s, &s->finger_root, F > 0 ? F : 1));
+    A(dalloc(s, &s->pad_link, P)); A(dalloc(s, &s->pad_s0, P)); A(dalloc(s, &s->pad_s1, P));
+    A(dalloc(s, &s->link_tab, (size_t)cfg->max_frames * (cfg->substeps + 1) * n_links * kLinkStride));
+    A(dalloc(s, &s->pose, 2 * (size_t)N)); A(dalloc(s, &s->vel, 2 * (size_t)N));
+    A(dalloc(s, &s->params, N)); A(dalloc(s, &s->shape, N)); A(dalloc(s, &s->iters, N));
+    A(dalloc(s, &s->status, N)); A(dalloc(s, &s->forces, (size_t)N * P * 3));
+    A(dalloc(s, &s->c_sum, N)); A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
+    A(dalloc(s, &s->part_c, cost_blocks(N))); A(dalloc(s, &s->part_i, cost_blocks(N)));
+    A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 5));
+    A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
+    A(dalloc(s, &s->elite_cdf, N)); A(dalloc(s, &s->chol, 68));
+    if (e != cudaSuccess) {
+        ih_status st = cuda_fail(nullptr, e, "sim_create allocation");
+        sim_destroy(s);
+        return st;
+    }
+    std::vector<float4> sph(total);
+    for (int j = 0; j < total; ++j)
+        sph[j] = make_float4(sc->spheres[4 * j], sc->spheres[4 * j + 1], sc->spheres[4 * j + 2], sc->spheres[4 * j + 3]);
+    std::vector<float4> roots(F > 0 ? F : 1, make_float4(0, 0, 0, 0));
+    for (int f = 0; f < F; ++f)
+        roots[f] = make_float4(sc->finger_root[4 * f], sc->finger_root[4 * f + 1], sc->finger_root[4 * f + 2],
+                               sc->finger_root[4 * f + 3]);
+    std::vector<int> shp0(N, 0), it0(N, cfg->iters);
+    cudaStream_t st = s->stream;
+    A(cudaMemcpyAsync(s->spheres_raw, sph.data(), total * sizeof(float4), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->shape_first, sc->shape_first, sc->n_shapes * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->shape_count, sc->shape_count, sc->n_shapes * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->finger_root, roots.data(), roots.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->pad_link, sc->pad_link, P * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->pad_s0, sc->pad_s0, P * sizeof(float), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->pad_s1, sc->pad_s1, P * sizeof(float), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->shape, shp0.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->iters, it0.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemsetAsync(s->pose, 0, 2 * (size_t)N * sizeof(float4), st));
+    A(cudaMemsetAsync(s->vel, 0, 2 * (size_t)N * sizeof(float4), st));
+    A(cudaMemsetAsync(s->params, 0, (size_t)N * sizeof(float2), st));
+    A(cudaMemsetAsync(s->status, 0, (size_t)N * sizeof(int), st));
+    A(cudaMemsetAsync(s->forces, 0, (size_t)N * P * 3 * sizeof(float), st));
+    A(cudaMemsetAsync(s->c_sum, 0, (size_t)N * sizeof(double), st));
+    A(cudaMemsetAsync(s->n_window, 0, sizeof(int), st));
+    A(cudaMemsetAsync(s->argmin, 0, sizeof(int), st));
+    A(cudaMemsetAsync(s->done, 0, sizeof(unsigned int), st));
+    A(cudaMemsetAsync(s->work, 0, 5 * sizeof(unsigned long long), st));
+    A(launch_shape_setup(s->spheres_raw, s->spheres, s->shape_first, s->shape_count, sc->n_shapes,
+                         s->shape_jinv, s->shape_bound, st));
+    A(cudaStreamSynchronize(st));   // host vectors above go out of scope
+    if (e != cudaSuccess) {
+        ih_status r = cuda_fail(nullptr, e, "sim_create upload");
+        sim_destroy(s);
+        return r;
+    }
+    s->frame_ready.assign(cfg->max_frames, 0);
+    s->step_grid = grid_for(s->variant, N);
+    *out = s;
+    return IH_OK;
+}
+
+ih_status sim_destroy(ih_sim *s) {
+    if (!s) return IH_OK;
+    cudaStreamSynchronize(s->stream);
+    for (void *p : s->owned) cudaFree(p);
+    delete s;
+    return IH_OK;
+}
+
+ih_status sim_set_stream(ih_sim *s, void *stream) {
+    if (!s) return IH_ERR_ARG;
+    s->stream = static_cast<cudaStream_t>(stream);
+    return IH_OK;
+}
+
+ih_status sim_set_commands(ih_sim *s, int32_t frame0, int32_t n_frames, const float *q) {
+    if (!s) return IH_ERR_ARG;
+    if ((!q && s->n_joints > 0) || n_frames < 1 || frame0 < 0 || frame0 + n_frames > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table of %d", frame0, frame0 + n_frames,
+                    s->cfg.max_frames);
+    float4 *tab = s->link_tab + (size_t)frame0 * (s->cfg.substeps + 1) * s->n_links * kLinkStride;
+    cudaError_t e = launch_fk(dev_scene(s), q, n_frames, s->cfg.substeps, tab, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fk launch");
+    for (int f = frame0; f < frame0 + n_frames; ++f) s->frame_ready[f] = 1;
+    return IH_OK;
+}
+
+ih_status sim_sample_initial(ih_sim *s, const float *nominal, float sigma_p, float sigma_r, float m_lo,
+                             float m_hi, float mu_lo, float mu_hi) {
+    if (!s) return IH_ERR_ARG;
+    if (!nominal || !(sigma_p >= 0.0f) || !(sigma_r >= 0.0f) || !(m_lo > 0.0f) || !(m_hi >= m_lo) ||
+        !(mu_lo >= 0.0f) || !(mu_hi >= mu_lo))
+        return fail(s, IH_ERR_ARG, "invalid sampling parameters");
+    const float4 x0 = make_float4(nominal[0], nominal[1], nominal[2], 0.0f);
+    const float4 q0 = make_float4(nominal[4], nominal[5], nominal[6], nominal[7]);
+    cudaError_t e = launch_sample_initial(s->cfg.n_envs, x0, q0, sigma_p, sigma_r, m_lo, m_hi, mu_lo, mu_hi,
+                                          s->seed, s->pose, s->vel, s->params, s->status, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->c_sum, 0, s->cfg.n_envs * sizeof(double), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->n_window, 0, sizeof(int), s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "sample_initial");
+    s->window_frames = 0;
+    return IH_OK;
+}
+
+ih_status sim_set_state(ih_sim *s, const float *pose, const float *vel, const float *params,
+                        const int32_t *shape_id, const int32_t *iters) {
+    if (!s) return IH_ERR_ARG;
+    if (!pose || !vel || !params) return fail(s, IH_ERR_ARG, "pose, vel and params are required");
+    if (!aligned16(pose) || !aligned16(vel) || (reinterpret_cast<uintptr_t>(params) & 7u))
+        return fail(s, IH_ERR_ARG, "pose/vel must be 16-byte aligned, params 8-byte aligned");
+    cudaError_t e = launch_set_state(s->cfg.n_envs, s->n_shapes, pose, vel, params, shape_id, iters,
+                                     s->pose, s->vel, s->params, s->shape, s->iters, s->status, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
+    return IH_OK;
+}
+
+ih_status sim_get_state(ih_sim *s, float *pose, float *vel, float *params, int32_t *env_status) {
+    if (!s) return IH_ERR_ARG;
+    const size_t N = s->cfg.n_envs;
+    cudaError_t e = cudaSuccess;
+    if (pose) e = cudaMemcpyAsync(pose, s->pose, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && vel)
+        e = cudaMemcpyAsync(vel, s->vel, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && params)
+        e = cudaMemcpyAsync(params, s->params, N * sizeof(float2), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && env_status)
+        e = cudaMemcpyAsync(env_status, s->status, N * sizeof(int), cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "get_state");
+    return IH_OK;
+}
+
+ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
+    if (!s) return IH_ERR_ARG;
+    if (n_frames < 1 || frame0 < 0 || frame0 + n_frames > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + n_frames);
+    for (int f = frame0; f < frame0 + n_frames; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    StepArgs a;
+    a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
+    a.frame0 = frame0; a.n_frames = n_frames; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
+    a.shape = s->shape; a.iters = s->iters; a.status = s->status; a.forces = s->forces; a.work = s->work;
+    cudaError_t e = launch_step(a, s->variant, s->step_grid, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    s->stepped = true;
+    return IH_OK;
+}
+
+ih_status sim_read_sensors(ih_sim *s, float *forces, int32_t *env_status) {
+    if (!s) return IH_ERR_ARG;
+    const size_t N = s->cfg.n_envs;
+    cudaError_t e = cudaSuccess;
+    if (forces)
+        e = cudaMemcpyAsync(forces, s->forces, N * s->n_pads * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && env_status)
+        e = cudaMemcpyAsync(env_status, s->status, N * sizeof(int), cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read_sensors");
+    return IH_OK;
+}
+
+ih_status cost_eval(ih_sim *s, const float *obs, double *cost_mean, int32_t *argmin, float *est_pose) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
+    CostArgs a;
+    a.N = s->cfg.n_envs; a.P = s->n_pads; a.cfg = s->dcfg; a.forces = s->forces; a.obs = obs;
+    a.status = s->status; a.c_sum = s->c_sum; a.n_window = s->n_window; a.cost_mean = cost_mean;
+    a.pose = s->pose; a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est_pose;
+    a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
+    cudaError_t e = launch_cost(a, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cost launch");
+    s->window_frames += 1;
+    return IH_OK;
+}
+
+ih_status optimizer_update(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int32_t *argmin,
+                           int32_t *parent) {
+    if (!s) return IH_ERR_ARG;
+    if (!opt || !(opt->elite_frac > 0.0f) || !(opt->elite_frac <= 1.0f) || !(opt->m_lo > 0.0f) ||
+        !(opt->m_hi >= opt->m_lo) || !(opt->mu_lo >= 0.0f) || !(opt->mu_hi >= opt->mu_lo))
+        return fail(s, IH_ERR_ARG, "invalid optimizer config");
+    for (int k = 0; k < 8; ++k)
+        if (!(opt->floor_std[k] >= 0.0f) || !std::isfinite(opt->floor_std[k]))
+            return fail(s, IH_ERR_ARG, "floor_std[%d] is invalid", k);
+    if (s->window_frames < 1) return fail(s, IH_ERR_STATE, "no frame scored since the last update");
+    OptArgs a;
+    a.N = s->cfg.n_envs; a.elite_frac = opt->elite_frac;
+    for (int k = 0; k < 8; ++k) a.floor_var[k] = (double)opt->floor_std[k] * (double)opt->floor_std[k];
+    a.m_lo = opt->m_lo; a.m_hi = opt->m_hi; a.mu_lo = opt->mu_lo; a.mu_hi = opt->mu_hi;
+    a.seed = s->seed; a.update_index = update_index; a.c_sum = s->c_sum; a.n_window = s->n_window;
+    a.pose = s->pose; a.vel = s->vel; a.params = s->params; a.status = s->status;
+    a.is_elite = s->is_elite; a.rank = s->rank; a.elite_env = s->elite_env; a.elite_cdf = s->elite_cdf;
+    a.chol = s->chol; a.argmin_state = s->argmin; a.argmin_out = argmin; a.parent_out = parent;
+    a.c_sum_reset = s->c_sum; a.n_window_reset = s->n_window;
+    cudaError_t e = launch_optimizer(a, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "optimizer launch");
+    s->window_frames = 0;
+    return IH_OK;
+}
+
+ih_status sim_work_counters(ih_sim *s, uint64_t *out, int32_t reset) {
+    if (!s || !out) return IH_ERR_ARG;
+    unsigned long long w[5];
+    cudaError_t e = cudaMemcpyAsync(w, s->work, sizeof w, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(s->work, 0, sizeof w, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "work counters");
+    for (int k = 0; k < 5; ++k) out[k] = w[k];
+    return IH_OK;
+}
+
+ih_status sim_sync(ih_sim *s) {
+    if (!s) return IH_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "sync");
+    return IH_OK;
+}
+
+const char *sim_last_error(const ih_sim *s) {
+    if (!s) return g_create_err.c_str();
+    return s->err.c_str();
+}
+
+}  // extern "C"

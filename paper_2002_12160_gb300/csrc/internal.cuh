@@ -1,0 +1,249 @@
+// internal.cuh -- device-side records and FP32 helpers shared by the kernels
+// of libinhand.so. Nothing here is part of the public ABI (include/inhand.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/inhand.h"
+
+namespace ih {
+
+constexpr int kDiverged = IH_ENV_NONFINITE | IH_ENV_ESCAPED | IH_ENV_OVERFLOW | IH_ENV_INVALID;
+constexpr int kLinkStride = 3;  // float4 per link pose: (a, 0), (axis, 0), (quat wxyz)
+
+// Scene as seen by the kernels (device pointers, fixed at create).
+struct DevScene {
+    int n_shapes, n_fingers, n_links, n_pads, n_joints;
+    float palm_hx, palm_hy, palm_hz;
+    float link_len, link_rad;
+    const float4 *spheres;      // [total] centroid-frame centre xyz, radius
+    const int *shape_first;     // [n_shapes]
+    const int *shape_count;     // [n_shapes]
+    const float *shape_jinv;    // [n_shapes][6] inverse unit inertia xx yy zz xy xz yz
+    const float *shape_bound;   // [n_shapes] bounding radius about the centroid
+    const float4 *finger_root;  // [F] x y z yaw
+    const int *pad_link;        // [P]
+    const float *pad_s0, *pad_s1;
+};
+
+struct DevConfig {
+    float h;            // substep length
+    int substeps;
+    int iters;
+    float margin, beta, slop, vmax;
+    float gx, gy, gz;
+    float tau, w_force, w_contact;
+    int c_max;
+    float escape_radius;
+};
+
+// ---------------------------------------------------------------- FP32 math
+struct V3 { float x, y, z; };
+struct Q4 { float w, x, y, z; };
+
+__host__ __device__ __forceinline__ V3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 xyz(float4 v) { return {v.x, v.y, v.z}; }
+
+__device__ __forceinline__ Q4 qmul(Q4 a, Q4 b) {
+    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+            a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+            a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ Q4 qnorm(Q4 q) {
+    float s = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+    return {q.w * s, q.x * s, q.y * s, q.z * s};
+}
+// rotate v by unit quaternion q: v + 2 w (u x v) + 2 u x (u x v)
+__device__ __forceinline__ V3 qrot(Q4 q, V3 v) {
+    V3 u = {q.x, q.y, q.z};
+    V3 t = cross(u, v) * 2.0f;
+    return v + t * q.w + cross(u, t);
+}
+__device__ __forceinline__ V3 qrot_inv(Q4 q, V3 v) { return qrot({q.w, -q.x, -q.y, -q.z}, v); }
+
+// symmetric 3x3 stored as xx yy zz xy xz yz
+struct S6 { float xx, yy, zz, xy, xz, yz; };
+__device__ __forceinline__ V3 smul(const S6 &A, V3 v) {
+    return {A.xx * v.x + A.xy * v.y + A.xz * v.z,
+            A.xy * v.x + A.yy * v.y + A.yz * v.z,
+            A.xz * v.x + A.yz * v.y + A.zz * v.z};
+}
+// columns of the rotation matrix of q
+struct M3 { V3 c0, c1, c2; };
+__device__ __forceinline__ M3 qmat(Q4 q) {
+    M3 R;
+    R.c0 = {1 - 2 * (q.y * q.y + q.z * q.z), 2 * (q.x * q.y + q.w * q.z), 2 * (q.x * q.z - q.w * q.y)};
+    R.c1 = {2 * (q.x * q.y - q.w * q.z), 1 - 2 * (q.x * q.x + q.z * q.z), 2 * (q.y * q.z + q.w * q.x)};
+    R.c2 = {2 * (q.x * q.z + q.w * q.y), 2 * (q.y * q.z - q.w * q.x), 1 - 2 * (q.x * q.x + q.y * q.y)};
+    return R;
+}
+__device__ __forceinline__ V3 mmul(const M3 &R, V3 v) { return R.c0 * v.x + R.c1 * v.y + R.c2 * v.z; }
+__device__ __forceinline__ V3 mtmul(const M3 &R, V3 v) { return {dot(R.c0, v), dot(R.c1, v), dot(R.c2, v)}; }
+
+// W = R J^-1 R^T / m for symmetric J^-1 (body frame)
+__device__ __forceinline__ S6 world_inv_inertia(const M3 &R, const S6 &Jb, float inv_m) {
+    // columns of J R^T: rows of R are (c0.x, c1.x, c2.x) etc.
+    V3 r0 = {R.c0.x, R.c1.x, R.c2.x}, r1 = {R.c0.y, R.c1.y, R.c2.y}, r2 = {R.c0.z, R.c1.z, R.c2.z};
+    V3 a0 = smul(Jb, r0), a1 = smul(Jb, r1), a2 = smul(Jb, r2);
+    S6 W;
+    W.xx = dot(r0, a0) * inv_m; W.yy = dot(r1, a1) * inv_m; W.zz = dot(r2, a2) * inv_m;
+    W.xy = dot(r0, a1) * inv_m; W.xz = dot(r0, a2) * inv_m; W.yz = dot(r1, a2) * inv_m;
+    return W;
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon et al., "Parallel random numbers: as easy
+// as 1, 2, 3" (SC'11): 10 rounds of a multiply-xor bijection on four 32-bit
+// words, keyed by two 32-bit words bumped by the golden-ratio Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ uint4 rng_words(uint64_t seed, uint32_t stream, uint32_t index,
+                                           uint32_t env, uint32_t block) {
+    return philox4x32_10(make_uint4(stream, index, env, block),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+// uniform in (0, 1) from the top 53 bits of (hi, lo)
+__device__ __forceinline__ double unit53(uint32_t hi, uint32_t lo) {
+    const uint64_t b = ((uint64_t)hi << 21) | (lo >> 11);
+    return ((double)b + 0.5) * 0x1.0p-53;
+}
+// two standard normals (Box-Muller, FP64) from one block
+__device__ __forceinline__ void gauss2(uint4 w, double &z0, double &z1) {
+    const double a = unit53(w.x, w.y), b = unit53(w.z, w.w);
+    const double rad = sqrt(-2.0 * log(a));
+    double s, c;
+    sincospi(2.0 * b, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// FP64 so(3) maps on (w, x, y, z) quaternions
+struct Q4d { double w, x, y, z; };
+__device__ __forceinline__ Q4d qexp_d(double x, double y, double z) {
+    const double th = sqrt(x * x + y * y + z * z);
+    if (th < 1e-300) return {1.0, 0.0, 0.0, 0.0};
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    const double k = s / th;
+    return {c, x * k, y * k, z * k};
+}
+__device__ __forceinline__ Q4d qmul_d(Q4d a, Q4d b) {
+    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+            a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+            a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ Q4d qnorm_d(Q4d q) {
+    const double n = sqrt(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+    return {q.w / n, q.x / n, q.y / n, q.z / n};
+}
+__device__ __forceinline__ void qlog_d(Q4d q, double out[3]) {
+    if (q.w < 0) { q.w = -q.w; q.x = -q.x; q.y = -q.y; q.z = -q.z; }
+    const double s = sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
+    if (s < 1e-300) { out[0] = out[1] = out[2] = 0.0; return; }
+    const double th = 2.0 * atan2(s, q.w);
+    out[0] = q.x * th / s; out[1] = q.y * th / s; out[2] = q.z * th / s;
+}
+
+// ---------------------------------------------------------------- launches
+// Declared here, defined in the kernel translation units.
+cudaError_t launch_shape_setup(const float4 *spheres_in, float4 *spheres_out, const int *first,
+                               const int *count, int n_shapes, float *jinv, float *bound,
+                               cudaStream_t s);
+cudaError_t launch_fk(const DevScene &sc, const float *q, int n_frames, int substeps,
+                      float4 *link_tab_out, cudaStream_t s);
+cudaError_t launch_sample_initial(int N, float4 pose0, float4 quat0, float sigma_p, float sigma_r,
+                                  float m_lo, float m_hi, float mu_lo, float mu_hi, uint64_t seed,
+                                  float4 *pose, float4 *vel, float2 *params, int *status,
+                                  cudaStream_t s);
+cudaError_t launch_set_state(int N, int n_shapes, const float *pose, const float *vel,
+                             const float *params, const int *shape_in, const int *iters_in,
+                             float4 *pose_out, float4 *vel_out, float2 *params_out, int *shape,
+                             int *iters, int *status, cudaStream_t s);
+
+struct StepArgs {
+    DevScene sc;
+    DevConfig cfg;
+    int N;
+    const float4 *link_tab;   // [frames][ns+1][Lk][3]
+    int frame0, n_frames;
+    float4 *pose, *vel;       // [N][2]
+    const float2 *params;
+    const int *shape, *iters;
+    int *status;
+    float *forces;            // [N][P][3]
+    unsigned long long *work; // [5]
+};
+struct StepVariant {
+    int group;        // lanes per environment
+    int cpl;          // register-resident contacts per lane
+    int block;        // threads per CTA
+};
+cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, cudaStream_t s);
+int step_variant_max_contacts(const StepVariant &v);
+bool step_variant_supported(const StepVariant &v);
+
+struct CostArgs {
+    int N, P;
+    DevConfig cfg;
+    const float *forces;     // [N][P][3]
+    const float *obs;        // [P][3]
+    const int *status;
+    double *c_sum;           // [N]
+    int *n_window;           // device counter
+    double *cost_mean;       // [N] or null
+    const float4 *pose;      // for est_pose
+    int *argmin_state;       // handle's i*
+    int *argmin_out;         // user or null
+    float *est_pose_out;     // user float[8] or null
+    double *part_c;          // [blocks] scratch
+    int *part_i;             // [blocks] scratch
+    unsigned int *done;      // scratch counter (zero between launches)
+};
+cudaError_t launch_cost(const CostArgs &a, cudaStream_t s);
+int cost_blocks(int N);
+
+struct OptArgs {
+    int N;
+    float elite_frac;
+    double floor_var[8];
+    float m_lo, m_hi, mu_lo, mu_hi;
+    uint64_t seed;
+    uint32_t update_index;
+    const double *c_sum;
+    const int *n_window;
+    float4 *pose, *vel;
+    float2 *params;
+    int *status;
+    // scratch written by the select kernel, read by the apply kernel
+    unsigned char *is_elite;  // [N]
+    int *rank;                // [N] elite rank or non-elite rank
+    int *elite_env;           // [N] elites in index order (first k used)
+    double *elite_cdf;        // [N]
+    double *chol;             // [64 + 4]: L, then k, u, i*, ok
+    int *argmin_state;
+    int *argmin_out;
+    int *parent_out;
+    double *c_sum_reset;      // same as c_sum (reset by apply)
+    int *n_window_reset;
+};
+cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
+
+}  // namespace ih

@@ -1,0 +1,205 @@
+// setup.cu -- kernels that prepare the step: each shape's centroid frame,
+// unit inertia and bounding radius; the kinematic hand's link poses for a
+// block of commanded frames (the robot state driven by u_t, Sec. III-A); the
+// initial sampling of pose, mass and friction (Sec. III-D, Algorithm 1
+// initialisation); and the validated upload of a caller's state.
+#include "internal.cuh"
+
+namespace ih {
+namespace {
+
+// One block per shape. Centroid of the sphere centres, recentred spheres,
+// unit inertia J = (1/S) sum_s [(2/5) r_s^2 I + |c_s|^2 I - c_s c_s^T] of
+// equal solid balls about the centroid, its inverse, and the bounding radius
+// max_s |c_s| + r_s.
+__global__ void shape_setup_kernel(const float4 *in, float4 *out, const int *first, const int *count,
+                                   float *jinv, float *bound) {
+    __shared__ double red[7][256];
+    const int sh = blockIdx.x, t = threadIdx.x;
+    const int f = first[sh], S = count[sh];
+    double cx = 0, cy = 0, cz = 0;
+    for (int j = t; j < S; j += blockDim.x) {
+        const float4 s = in[f + j];
+        cx += s.x; cy += s.y; cz += s.z;
+    }
+    red[0][t] = cx; red[1][t] = cy; red[2][t] = cz;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) for (int k = 0; k < 3; ++k) red[k][t] += red[k][t + o];
+        __syncthreads();
+    }
+    const double mx = red[0][0] / S, my = red[1][0] / S, mz = red[2][0] / S;
+    __syncthreads();
+    double a[7] = {0, 0, 0, 0, 0, 0, 0};   // xx yy zz xy xz yz, bound
+    for (int j = t; j < S; j += blockDim.x) {
+        const float4 s = in[f + j];
+        const double x = s.x - mx, y = s.y - my, z = s.z - mz, r = s.w;
+        out[f + j] = make_float4((float)x, (float)y, (float)z, s.w);
+        const double ball = 0.4 * r * r;
+        a[0] += ball + y * y + z * z;
+        a[1] += ball + x * x + z * z;
+        a[2] += ball + x * x + y * y;
+        a[3] -= x * y;
+        a[4] -= x * z;
+        a[5] -= y * z;
+        a[6] = fmax(a[6], sqrt(x * x + y * y + z * z) + r);
+    }
+    for (int k = 0; k < 7; ++k) red[k][t] = a[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            for (int k = 0; k < 6; ++k) red[k][t] += red[k][t + o];
+            red[6][t] = fmax(red[6][t], red[6][t + o]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double xx = red[0][0] / S, yy = red[1][0] / S, zz = red[2][0] / S;
+        const double xy = red[3][0] / S, xz = red[4][0] / S, yz = red[5][0] / S;
+        // adjugate of the symmetric matrix
+        const double c00 = yy * zz - yz * yz, c11 = xx * zz - xz * xz, c22 = xx * yy - xy * xy;
+        const double c01 = xz * yz - xy * zz, c02 = xy * yz - xz * yy, c12 = xy * xz - xx * yz;
+        const double det = xx * c00 + xy * c01 + xz * c02;
+        float *o = jinv + 6 * sh;
+        o[0] = (float)(c00 / det); o[1] = (float)(c11 / det); o[2] = (float)(c22 / det);
+        o[3] = (float)(c01 / det); o[4] = (float)(c02 / det); o[5] = (float)(c12 / det);
+        bound[sh] = (float)red[6][0];
+    }
+}
+
+// One thread per (substep boundary, finger): quaternion chain of the finger
+//   Q_0 = qz(yaw + q_0) qy(-pi/2),  a_0 = root,
+//   a_j = a_{j-1} + L Q_{j-1} e_x,  Q_j = Q_{j-1} qy(-q_j).
+// Boundary k of frame f uses q = q_f + (k / ns)(q_{f+1} - q_f).
+// Output per link: (a, 0), (Q e_x, 0), (Q as w x y z).
+__global__ void fk_kernel(const DevScene sc, const float *q, int n_frames, int ns, float4 *tab) {
+    const int F = sc.n_fingers, D = sc.n_joints, Lk = sc.n_links;
+    const int per = (F > 0) ? F : 1;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_frames * (ns + 1) * per) return;
+    const int b = id / per, f = id % per;
+    const int fr = b / (ns + 1), k = b % (ns + 1);
+    float4 *o = tab + (size_t)b * Lk * kLinkStride;
+    if (f == 0) {   // palm: identity pose at the origin
+        o[0] = make_float4(0, 0, 0, 0);
+        o[1] = make_float4(1, 0, 0, 0);
+        o[2] = make_float4(1, 0, 0, 0);
+    }
+    if (F == 0) return;
+    const float frac = (float)k / (float)ns;
+    float qf[4];
+    for (int j = 0; j < 4; ++j) {
+        const float q0 = q[(size_t)fr * D + 4 * f + j], q1 = q[(size_t)(fr + 1) * D + 4 * f + j];
+        qf[j] = q0 + frac * (q1 - q0);
+    }
+    const float4 root = sc.finger_root[f];
+    float sz, cz, sy, cy;
+    sincosf(0.5f * (root.w + qf[0]), &sz, &cz);
+    const float hs = 0.70710678118654752f;   // sin(pi/4) = cos(pi/4)
+    // qz(yaw + q0) * qy(-pi/2)
+    Q4 Q = qmul({cz, 0.0f, 0.0f, sz}, {hs, 0.0f, -hs, 0.0f});
+    V3 a = mk(root.x, root.y, root.z);
+    for (int j = 0; j < 4; ++j) {
+        if (j > 0) {
+            a = a + qrot(Q, mk(sc.link_len, 0, 0));
+            sincosf(-0.5f * qf[j], &sy, &cy);
+            Q = qnorm(qmul(Q, {cy, 0.0f, sy, 0.0f}));
+        }
+        const V3 ax = qrot(Q, mk(1, 0, 0));
+        float4 *lo = o + (1 + 4 * f + j) * kLinkStride;
+        lo[0] = make_float4(a.x, a.y, a.z, 0.0f);
+        lo[1] = make_float4(ax.x, ax.y, ax.z, 0.0f);
+        lo[2] = make_float4(Q.w, Q.x, Q.y, Q.z);
+    }
+}
+
+// One thread per environment: x = x0 + sigma_p n_{0..2}, R = exp(sigma_r n_{3..5}) R0,
+// m, mu uniform; normals from Philox counter (0, 0, i, 0..2), uniforms from block 3.
+__global__ void sample_initial_kernel(int N, float4 x0, float4 q0, float sigma_p, float sigma_r,
+                                      float m_lo, float m_hi, float mu_lo, float mu_hi,
+                                      uint64_t seed, float4 *pose, float4 *vel, float2 *params,
+                                      int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double n[6];
+    for (int b = 0; b < 3; ++b) gauss2(rng_words(seed, 0, 0, (uint32_t)i, (uint32_t)b), n[2 * b], n[2 * b + 1]);
+    const uint4 u = rng_words(seed, 0, 0, (uint32_t)i, 3);
+    const double um = unit53(u.x, u.y), umu = unit53(u.z, u.w);
+    const Q4d dq = qexp_d(sigma_r * n[3], sigma_r * n[4], sigma_r * n[5]);
+    const Q4d qn = qnorm_d(qmul_d(dq, {q0.x, q0.y, q0.z, q0.w}));
+    pose[2 * i] = make_float4((float)(x0.x + sigma_p * n[0]), (float)(x0.y + sigma_p * n[1]),
+                              (float)(x0.z + sigma_p * n[2]), 0.0f);
+    pose[2 * i + 1] = make_float4((float)qn.w, (float)qn.x, (float)qn.y, (float)qn.z);
+    vel[2 * i] = make_float4(0, 0, 0, 0);
+    vel[2 * i + 1] = make_float4(0, 0, 0, 0);
+    params[i] = make_float2((float)(m_lo + (m_hi - m_lo) * um), (float)(mu_lo + (mu_hi - mu_lo) * umu));
+    status[i] = 0;
+}
+
+__device__ __forceinline__ bool fin4(float4 v) {
+    return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+}
+
+__global__ void set_state_kernel(int N, int n_shapes, const float4 *pose_in, const float4 *vel_in,
+                                 const float2 *params_in, const int *shape_in, const int *iters_in,
+                                 float4 *pose, float4 *vel, float2 *params, int *shape, int *iters,
+                                 int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 p0 = pose_in[2 * i], p1 = pose_in[2 * i + 1];
+    const float4 v0 = vel_in[2 * i], v1 = vel_in[2 * i + 1];
+    const float2 th = params_in[i];
+    const int sh = shape_in ? shape_in[i] : shape[i];
+    const int it = iters_in ? iters_in[i] : iters[i];
+    bool ok = fin4(p0) && fin4(p1) && fin4(v0) && fin4(v1) && isfinite(th.x) && isfinite(th.y);
+    ok = ok && th.x > 0.0f && th.y >= 0.0f && sh >= 0 && sh < n_shapes && it >= 0 && it <= 4096;
+    const float qn = p1.x * p1.x + p1.y * p1.y + p1.z * p1.z + p1.w * p1.w;
+    ok = ok && qn > 0.5f && qn < 2.0f;
+    pose[2 * i] = make_float4(p0.x, p0.y, p0.z, 0.0f);
+    pose[2 * i + 1] = p1;
+    vel[2 * i] = make_float4(v0.x, v0.y, v0.z, 0.0f);
+    vel[2 * i + 1] = make_float4(v1.x, v1.y, v1.z, 0.0f);
+    params[i] = th;
+    shape[i] = (sh >= 0 && sh < n_shapes) ? sh : 0;
+    iters[i] = (it >= 0 && it <= 4096) ? it : 0;
+    status[i] = ok ? 0 : IH_ENV_INVALID;
+}
+
+}  // namespace
+
+cudaError_t launch_shape_setup(const float4 *spheres_in, float4 *spheres_out, const int *first,
+                               const int *count, int n_shapes, float *jinv, float *bound,
+                               cudaStream_t s) {
+    shape_setup_kernel<<<n_shapes, 256, 0, s>>>(spheres_in, spheres_out, first, count, jinv, bound);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fk(const DevScene &sc, const float *q, int n_frames, int substeps,
+                      float4 *link_tab_out, cudaStream_t s) {
+    const int per = sc.n_fingers > 0 ? sc.n_fingers : 1;
+    const int n = n_frames * (substeps + 1) * per;
+    fk_kernel<<<(n + 127) / 128, 128, 0, s>>>(sc, q, n_frames, substeps, link_tab_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_initial(int N, float4 pose0, float4 quat0, float sigma_p, float sigma_r,
+                                  float m_lo, float m_hi, float mu_lo, float mu_hi, uint64_t seed,
+                                  float4 *pose, float4 *vel, float2 *params, int *status,
+                                  cudaStream_t s) {
+    sample_initial_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, pose0, quat0, sigma_p, sigma_r, m_lo, m_hi,
+                                                          mu_lo, mu_hi, seed, pose, vel, params, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(int N, int n_shapes, const float *pose, const float *vel,
+                             const float *params, const int *shape_in, const int *iters_in,
+                             float4 *pose_out, float4 *vel_out, float2 *params_out, int *shape,
+                             int *iters, int *status, cudaStream_t s) {
+    set_state_kernel<<<(N + 127) / 128, 128, 0, s>>>(
+        N, n_shapes, reinterpret_cast<const float4 *>(pose), reinterpret_cast<const float4 *>(vel),
+        reinterpret_cast<const float2 *>(params), shape_in, iters_in, pose_out, vel_out, params_out,
+        shape, iters, status);
+    return cudaGetLastError();
+}
+
+}  // namespace ih

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libinhand.so (include/inhand.h).
+
+Argument marshalling only: every function forwards torch CUDA tensors' data
+pointers and the current CUDA stream to the C ABI of the same name. All
+computation runs in the library's kernels; there is no CPU fallback, and
+loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libinhand.so")
+
+IH_OK, IH_ERR_ARG, IH_ERR_CUDA, IH_ERR_OOM, IH_ERR_TIMEOUT, IH_ERR_STATE, IH_ERR_OVERFLOW = range(7)
+ENV_NONFINITE, ENV_ESCAPED, ENV_OVERFLOW, ENV_INVALID = 1, 2, 4, 8
+MAX_CONTACTS = 256
+
+
+class InhandError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed with status {code}: {msg}")
+        self.code = code
+
+
+class IHScene(C.Structure):
+    _fields_ = [("n_shapes", C.c_int32), ("shape_first", C.c_void_p), ("shape_count", C.c_void_p),
+                ("spheres", C.c_void_p), ("palm_half", C.c_float * 3), ("n_fingers", C.c_int32),
+                ("finger_root", C.c_void_p), ("link_len", C.c_float), ("link_rad", C.c_float),
+                ("n_pads", C.c_int32), ("pad_link", C.c_void_p), ("pad_s0", C.c_void_p),
+                ("pad_s1", C.c_void_p)]
+
+
+class IHConfig(C.Structure):
+    _fields_ = [("n_envs", C.c_int32), ("max_frames", C.c_int32), ("frame_dt", C.c_float),
+                ("substeps", C.c_int32), ("iters", C.c_int32), ("margin", C.c_float),
+                ("beta", C.c_float), ("slop", C.c_float), ("vmax", C.c_float),
+                ("gravity", C.c_float * 3), ("tau", C.c_float), ("w_force", C.c_float),
+                ("w_contact", C.c_float), ("c_max", C.c_int32), ("escape_radius", C.c_float)]
+
+
+class IHOptConfig(C.Structure):
+    _fields_ = [("elite_frac", C.c_float), ("floor_std", C.c_float * 8), ("m_lo", C.c_float),
+                ("m_hi", C.c_float), ("mu_lo", C.c_float), ("mu_hi", C.c_float)]
+
+
+_lib = None
+EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "sim_sample_initial",
+           "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
+           "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error"]
+
+
+def lib() -> C.CDLL:
+    """Load libinhand.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        P, I, U32 = C.c_void_p, C.c_int32, C.c_uint32
+        sig = {
+            "sim_create": [P, P, C.c_uint64, P, C.POINTER(P)],
+            "sim_destroy": [P],
+            "sim_set_stream": [P, P],
+            "sim_set_commands": [P, I, I, P],
+            "sim_sample_initial": [P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
+            "sim_set_state": [P, P, P, P, P, P],
+            "sim_get_state": [P, P, P, P, P],
+            "sim_step": [P, I, I],
+            "sim_read_sensors": [P, P, P],
+            "cost_eval": [P, P, P, P, P],
+            "optimizer_update": [P, P, U32, P, P],
+            "sim_work_counters": [P, P, I],
+            "sim_sync": [P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.sim_last_error.argtypes = [P]
+        L.sim_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(t, dtype, shape, name):
+    if t is None:
+        return
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Sim:
+    """One handle of the C ABI: N environments of one scene on the current device."""
+
+    def __init__(self, scene, sim_cfg, n_envs: int, max_frames: int, seed: int):
+        L = lib()
+        first, count, rows = scene.flat_spheres()
+        self._keep = [np.ascontiguousarray(first, np.int32), np.ascontiguousarray(count, np.int32),
+                      np.ascontiguousarray(rows, np.float32),
+                      np.ascontiguousarray(scene.finger_root, np.float32).reshape(-1, 4),
+                      np.ascontiguousarray(scene.pad_link, np.int32),
+                      np.ascontiguousarray(scene.pad_s0, np.float32),
+                      np.ascontiguousarray(scene.pad_s1, np.float32)]
+        k = self._keep
+        self._scene = IHScene(len(scene.shapes), k[0].ctypes.data, k[1].ctypes.data, k[2].ctypes.data,
+                              (C.c_float * 3)(*scene.palm_half), scene.n_fingers,
+                              k[3].ctypes.data if k[3].size else None, scene.link_len, scene.link_rad,
+                              scene.n_pads, k[4].ctypes.data, k[5].ctypes.data, k[6].ctypes.data)
+        self._cfg = IHConfig(n_envs, max_frames, sim_cfg.frame_dt, sim_cfg.substeps, sim_cfg.iters,
+                             sim_cfg.margin, sim_cfg.beta, sim_cfg.slop, sim_cfg.vmax,
+                             (C.c_float * 3)(*sim_cfg.gravity), sim_cfg.tau, sim_cfg.w_force,
+                             sim_cfg.w_contact, sim_cfg.c_max, sim_cfg.escape_radius)
+        self.n = n_envs
+        self.n_pads = scene.n_pads
+        self.n_joints = scene.n_joints
+        self.max_frames = max_frames
+        h = C.c_void_p()
+        rc = L.sim_create(C.byref(self._scene), C.byref(self._cfg), seed, _stream(), C.byref(h))
+        if rc != IH_OK:
+            raise InhandError("sim_create", rc, L.sim_last_error(None).decode())
+        self._h = h
+
+    # -- helpers
+    def _call(self, name, *args):
+        L = lib()
+        L.sim_set_stream(self._h, _stream())
+        rc = getattr(L, name)(self._h, *args)
+        if rc != IH_OK:
+            raise InhandError(name, rc, L.sim_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the C ABI, one method per entry point
+    def sim_set_commands(self, frame0: int, q: torch.Tensor):
+        _check(q, torch.float32, (q.shape[0], self.n_joints), "q")
+        self._call("sim_set_commands", frame0, q.shape[0] - 1, _ptr(q) if q.numel() else None)
+
+    def sim_sample_initial(self, nominal_pose, sigma_p, sigma_r, m_range, mu_range):
+        nom = (C.c_float * 8)(*[float(v) for v in nominal_pose])
+        self._call("sim_sample_initial", nom, sigma_p, sigma_r, m_range[0], m_range[1],
+                   mu_range[0], mu_range[1])
+
+    def sim_set_state(self, pose, vel, params, shape_id=None, iters=None):
+        _check(pose, torch.float32, (self.n, 8), "pose")
+        _check(vel, torch.float32, (self.n, 8), "vel")
+        _check(params, torch.float32, (self.n, 2), "params")
+        _check(shape_id, torch.int32, (self.n,), "shape_id")
+        _check(iters, torch.int32, (self.n,), "iters")
+        self._call("sim_set_state", _ptr(pose), _ptr(vel), _ptr(params), _ptr(shape_id), _ptr(iters))
+
+    def sim_get_state(self):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        pose = torch.empty((self.n, 8), dtype=torch.float32, device=dev)
+        vel = torch.empty((self.n, 8), dtype=torch.float32, device=dev)
+        params = torch.empty((self.n, 2), dtype=torch.float32, device=dev)
+        status = torch.empty((self.n,), dtype=torch.int32, device=dev)
+        self._call("sim_get_state", _ptr(pose), _ptr(vel), _ptr(params), _ptr(status))
+        return pose, vel, params, status
+
+    def sim_step(self, frame0: int, n_frames: int = 1):
+        self._call("sim_step", frame0, n_frames)
+
+    def sim_read_sensors(self, forces=None, status=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if forces is None:
+            forces = torch.empty((self.n, self.n_pads, 3), dtype=torch.float32, device=dev)
+        if status is None:
+            status = torch.empty((self.n,), dtype=torch.int32, device=dev)
+        self._call("sim_read_sensors", _ptr(forces), _ptr(status))
+        return forces, status
+
+    def cost_eval(self, obs, cost_mean=None, argmin=None, est_pose=None):
+        _check(obs, torch.float32, (self.n_pads, 3), "obs")
+        _check(cost_mean, torch.float64, (self.n,), "cost_mean")
+        _check(argmin, torch.int32, (1,), "argmin")
+        _check(est_pose, torch.float32, (8,), "est_pose")
+        self._call("cost_eval", _ptr(obs), _ptr(cost_mean), _ptr(argmin), _ptr(est_pose))
+
+    def optimizer_update(self, opt, update_index: int, argmin=None, parent=None):
+        oc = IHOptConfig(opt.elite_frac, (C.c_float * 8)(*opt.floor_std), opt.m_range[0],
+                         opt.m_range[1], opt.mu_range[0], opt.mu_range[1])
+        _check(argmin, torch.int32, (1,), "argmin")
+        _check(parent, torch.int32, (self.n,), "parent")
+        self._call("optimizer_update", C.byref(oc), C.c_uint32(update_index), _ptr(argmin), _ptr(parent))
+
+    def sim_work_counters(self, reset: bool = False):
+        out = (C.c_uint64 * 5)()
+        self._call("sim_work_counters", out, 1 if reset else 0)
+        return {"pairs": out[0], "contacts": out[1], "contact_iters": out[2], "env_substeps": out[3],
+                "env_iters": out[4]}
+
+    def sim_sync(self):
+        self._call("sim_sync")
+
+
+def make_sim(workload, n_envs: int | None = None, max_frames: int | None = None, seed: int | None = None) -> Sim:
+    """A handle for a workload from paper_2002_12160_gb300.workloads."""
+    n = workload.n_envs if n_envs is None else n_envs
+    mf = (workload.frames if max_frames is None else max_frames)
+    return Sim(workload.scene, workload.sim, n, mf, workload.seed if seed is None else seed)

@@ -1,0 +1,122 @@
+"""Algorithm 1 (sample-based optimization for in-hand pose tracking) on the GPU.
+
+The tracker holds two handles of the C ABI: the N tracking environments and
+one ground-truth environment (nominal pose, hidden mass and friction) whose
+pad forces stand in for the real robot's observations o_t^(gt) (Sec. IV-A
+uses a simulated ground truth the same way). A window is T frames of
+"step all environments, score them, take i* = argmin C_i", followed by the
+optimizer update. All of it runs in libinhand.so's kernels; this module only
+orders the calls and moves buffers.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import inhand, workloads as W
+
+
+class Tracker:
+    def __init__(self, wl: W.Workload, seed: int | None = None, n_envs: int | None = None):
+        self.wl = wl
+        self.T = wl.opt.window
+        self.seed = wl.seed if seed is None else seed
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.sim = inhand.make_sim(wl, n_envs=n_envs, max_frames=wl.frames, seed=self.seed)
+        self.gt = inhand.make_sim(wl, n_envs=1, max_frames=wl.frames, seed=self.seed + 1)
+        self.n = self.sim.n
+        P = wl.scene.n_pads
+        self.obs = torch.zeros((wl.frames, P, 3), dtype=torch.float32, device=self.dev)
+        self.gt_pose = torch.zeros((wl.frames, 8), dtype=torch.float32, device=self.dev)
+        self.argmin = torch.zeros((wl.frames, 1), dtype=torch.int32, device=self.dev)
+        self.est = torch.zeros((wl.frames, 8), dtype=torch.float32, device=self.dev)
+
+    def prepare(self):
+        """Commands for every frame, the ground-truth run, and the initial samples."""
+        wl = self.wl
+        q = torch.from_numpy(wl.q_traj).contiguous().to(self.dev)
+        self.sim.sim_set_commands(0, q)
+        self.gt.sim_set_commands(0, q)
+        pose = torch.from_numpy(wl.nominal_pose[None].copy()).to(self.dev)
+        vel = torch.zeros((1, 8), dtype=torch.float32, device=self.dev)
+        par = torch.tensor([wl.theta_gt], dtype=torch.float32, device=self.dev)
+        self.gt.sim_set_state(pose, vel, par)
+        f_buf = torch.empty((1, wl.scene.n_pads, 3), dtype=torch.float32, device=self.dev)
+        st_buf = torch.empty((1,), dtype=torch.int32, device=self.dev)
+        for f in range(wl.frames):
+            self.gt.sim_step(f, 1)
+            self.gt.sim_read_sensors(f_buf, st_buf)
+            self.obs[f].copy_(f_buf[0])
+            self.gt_pose[f].copy_(self.gt.sim_get_state()[0][0])
+        self.sim.sim_sample_initial(wl.nominal_pose, wl.init.sigma_p, wl.init.sigma_r,
+                                    wl.init.m_range, wl.init.mu_range)
+        torch.cuda.synchronize()
+
+    def window(self, w: int, step_events=None):
+        """Frames [wT, (w+1)T): step, score, argmin each frame; then the optimizer update."""
+        T = self.T
+        for k in range(T):
+            f = w * T + k
+            if step_events is not None:
+                step_events[k][0].record()
+            self.sim.sim_step(f, 1)
+            if step_events is not None:
+                step_events[k][1].record()
+            self.sim.cost_eval(self.obs[f], None, self.argmin[f], self.est[f])
+        self.sim.optimizer_update(self.wl.opt, w)
+
+    def e2e_windows(self, w0: int, count: int):
+        """Windows driven through the public API from pinned host buffers: per window
+        the commands and observations go host -> device, the estimates come back."""
+        T, D, P = self.T, self.wl.scene.n_joints, self.wl.scene.n_pads
+        q_host = torch.from_numpy(self.wl.q_traj).pin_memory()
+        obs_host = self.obs.cpu().pin_memory()
+        est_host = torch.empty((T, 8), dtype=torch.float32).pin_memory()
+        am_host = torch.empty((T, 1), dtype=torch.int32).pin_memory()
+        q_dev = torch.empty((T + 1, D), dtype=torch.float32, device=self.dev)
+        obs_dev = torch.empty((T, P, 3), dtype=torch.float32, device=self.dev)
+        times = []
+        for w in range(w0, w0 + count):
+            f0 = w * T
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q_dev.copy_(q_host[f0:f0 + T + 1], non_blocking=True)
+            obs_dev.copy_(obs_host[f0:f0 + T], non_blocking=True)
+            self.sim.sim_set_commands(f0, q_dev)
+            for k in range(T):
+                self.sim.sim_step(f0 + k, 1)
+                self.sim.cost_eval(obs_dev[k], None, self.argmin[f0 + k], self.est[f0 + k])
+            self.sim.optimizer_update(self.wl.opt, w)
+            est_host.copy_(self.est[f0:f0 + T], non_blocking=True)
+            am_host.copy_(self.argmin[f0:f0 + T], non_blocking=True)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        ms = 1e3 * sum(times) / len(times)
+        return {"value": self.n * T / (ms / 1e3), "unit": "env-steps/s", "ms_per_step": ms,
+                "h2d_bytes_per_step": (T + 1) * D * 4 + T * P * 3 * 4,
+                "d2h_bytes_per_step": T * 8 * 4 + T * 4, "windows": count}
+
+    def add_mm(self, frames: int | None = None) -> float:
+        """Mean ADD (mm) of the argmin estimate against the ground truth over the
+        scored frames, on the object's sphere centres (evaluation, Sec. IV)."""
+        est = self.est.cpu().numpy().astype(np.float64)
+        gt = self.gt_pose.cpu().numpy().astype(np.float64)
+        used = frames if frames is not None else int((np.abs(est).sum(1) > 0).sum())
+        pts = self.wl.scene.shapes[0][:, :3]
+
+        def world(p):
+            w, x, y, z = p[4:]
+            R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                          [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                          [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+            return p[:3] + pts @ R.T
+
+        errs = [np.linalg.norm(world(est[f]) - world(gt[f]), axis=1).mean() for f in range(used)
+                if np.abs(est[f]).sum() > 0]
+        return 1e3 * float(np.mean(errs)) if errs else float("nan")
+
+    def close(self):
+        self.sim.close()
+        self.gt.close()

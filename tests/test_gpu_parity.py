@@ -1,0 +1,206 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every comparison starts both sides from the same state -- the GPU's FP32
+state widened exactly to FP64 -- and advances one frame. Tolerances: pose
+1e-5 m and 1e-5 rad, pad force 1e-3 relative with a 1e-4 N floor; status bits,
+contact counts, elite sets and parents are compared exactly. Environments
+whose contact set or pad membership sits within 1e-6 m of a threshold are
+excluded and counted (a branch that FP32 and FP64 may take differently).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_12160_gb300 import workloads as W
+
+from gpu_common import (assert_report, compare_frame, dev, oracle_state, scene32, sim32, start,
+                        torch)
+
+pytestmark = pytest.mark.gpu
+
+
+def test_initial_sampling_matches_oracle():
+    wl = W.make_workload("tracking_cyl64", n_envs=257, frames=4)
+    sim = start(wl, n=257, frames=4)
+    pose, vel, params, status = (t.cpu().numpy() for t in sim.sim_get_state())
+    p_or, th_or = O.sample_initial(257, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed)
+    np.testing.assert_allclose(pose[:, :3], p_or[:, :3], atol=1e-7)
+    q = pose[:, 4:]
+    assert np.max(np.abs(np.abs(np.sum(q * p_or[:, 3:], 1)) - 1)) < 1e-6
+    np.testing.assert_allclose(params, th_or, rtol=1e-6)
+    assert np.all(vel == 0) and np.all(status == 0)
+
+
+@pytest.mark.parametrize("name,n,frames,check", [
+    ("tracking_box27", 16, 40, [0, 5, 17, 30, 39]),
+    ("tracking_cyl64", 61, 30, [3, 12, 29]),
+    ("uneven_mixed", 67, 20, [2, 9, 19]),
+    ("sweep_mug128", 29, 12, [4, 11]),
+])
+def test_one_frame_parity(name, n, frames, check):
+    wl = W.make_workload(name, n_envs=n, frames=frames)
+    sim = start(wl, n=n, frames=frames)
+    total_ok = 0
+    contacts = 0
+    for f in range(frames):
+        if f in check:
+            rep = compare_frame(wl, sim, f)
+            assert_report(rep)
+            total_ok += rep["ok"].sum()
+            contacts += rep["contacts_or"]
+            if rep["ok"].all():
+                # culled GPU enumeration finds exactly the oracle's brute-force contact set
+                assert rep["work"]["contacts"] == rep["contacts_or"]
+        else:
+            sim.sim_step(f, 1)
+    assert contacts > 0 and total_ok > 0
+
+
+@pytest.mark.parametrize("name,n,frames,warm", [
+    ("tracking_cyl64", 1024, 8, 6),
+    ("uneven_mixed", 8192, 6, 4),
+    ("sweep_mug128", 32768, 4, 2),
+])
+def test_full_size_sampled_parity(name, n, frames, warm):
+    """At the benchmark sizes and launch shape, a sample of envs is checked one by one."""
+    wl = W.make_workload(name, n_envs=n, frames=frames)
+    sim = start(wl, n=n, frames=frames)
+    sim.sim_step(0, warm)
+    rng = np.random.default_rng(0)
+    envs = np.sort(rng.choice(n, 24, replace=False))
+    envs[-1] = n - 1          # the ragged tail of the last block
+    rep = compare_frame(wl, sim, warm, envs)
+    assert_report(rep)
+
+
+def test_cost_and_argmin_match_oracle_bit_for_bit():
+    wl = W.make_workload("tracking_box27", n_envs=16, frames=8)
+    sim = start(wl, n=16, frames=8)
+    d = dev()
+    c_sum = np.zeros(16)
+    cm = torch.empty(16, dtype=torch.float64, device=d)
+    am = torch.empty(1, dtype=torch.int32, device=d)
+    est = torch.empty(8, dtype=torch.float32, device=d)
+    for f in range(8):
+        sim.sim_step(f, 1)
+        forces, status = sim.sim_read_sensors()
+        obs = forces[3].clone()           # score everybody against env 3
+        sim.cost_eval(obs, cm, am, est)
+        i_or, c_or, _ = O.cost(sim32(wl.sim), forces.cpu().numpy().astype(np.float64),
+                               obs.cpu().numpy().astype(np.float64), status.cpu().numpy(), c_sum, f + 1)
+        np.testing.assert_array_equal(cm.cpu().numpy(), c_or)
+        # env 3 scores zero against itself; a lower index with zero cost wins the tie
+        assert int(am.item()) == i_or <= 3 and c_or[i_or] == 0.0 == c_or.min()
+        pose = sim.sim_get_state()[0]
+        np.testing.assert_array_equal(est.cpu().numpy(), pose[i_or].cpu().numpy())
+
+
+def test_optimizer_update_matches_oracle():
+    wl = W.make_workload("tracking_cyl64", n_envs=300, frames=6)
+    sim = start(wl, n=300, frames=6)
+    d = dev()
+    cm = torch.empty(300, dtype=torch.float64, device=d)
+    for f in range(6):
+        sim.sim_step(f, 1)
+        forces, _ = sim.sim_read_sensors()
+        sim.cost_eval(forces[7].clone(), cm)
+    before = oracle_state(sim.sim_get_state())
+    C = cm.cpu().numpy()
+    am = torch.empty(1, dtype=torch.int32, device=d)
+    par = torch.empty(300, dtype=torch.int32, device=d)
+    sim.optimizer_update(wl.opt, 5, am, par)
+    after = oracle_state(sim.sim_get_state())
+    istar, parent, stats = O.optimizer(wl.opt, before, C, wl.seed, 5)
+    assert int(am.item()) == istar
+    np.testing.assert_array_equal(par.cpu().numpy(), parent)
+    np.testing.assert_allclose(after.pose[:, :3], before.pose[:, :3], atol=2e-7)
+    assert rot_close(after.pose, before.pose, 2e-6)
+    np.testing.assert_allclose(after.theta, before.theta, rtol=2e-6)
+    np.testing.assert_array_equal(after.vel, before.vel)
+    np.testing.assert_array_equal(after.status, before.status)
+    # the window restarts: the next frame's mean is that frame's cost alone
+    sim.sim_step(0, 1)
+    forces, status = sim.sim_read_sensors()
+    sim.cost_eval(forces[7].clone(), cm)
+    _, c_one, _ = O.cost(sim32(wl.sim), forces.cpu().numpy().astype(np.float64),
+                         forces[7].cpu().numpy().astype(np.float64), status.cpu().numpy(), np.zeros(300), 1)
+    np.testing.assert_array_equal(cm.cpu().numpy(), c_one)
+
+
+def rot_close(a, b, tol):
+    from gpu_common import rot_angle
+    return rot_angle(a, b).max() < tol
+
+
+def test_invalid_state_is_flagged_and_skipped():
+    wl = W.make_workload("tracking_box27", n_envs=8, frames=3)
+    sim = start(wl, n=8, frames=3)
+    pose, vel, params, _ = sim.sim_get_state()
+    params[2, 0] = float("nan")
+    params[3, 0] = -1.0
+    shape = torch.zeros(8, dtype=torch.int32, device=pose.device)
+    shape[4] = 5
+    sim.sim_set_state(pose, vel, params, shape, None)
+    _, _, _, status = sim.sim_get_state()
+    st = status.cpu().numpy()
+    assert list(np.nonzero(st)[0]) == [2, 3, 4] and np.all(st[[2, 3, 4]] == 8)
+    p_before = sim.sim_get_state()[0].cpu().numpy()
+    sim.sim_step(0, 2)
+    forces, _ = sim.sim_read_sensors()
+    p_after = sim.sim_get_state()[0].cpu().numpy()
+    np.testing.assert_array_equal(p_after[[2, 3, 4]], p_before[[2, 3, 4]])
+    cm = torch.empty(8, dtype=torch.float64, device=pose.device)
+    sim.cost_eval(forces[0].clone(), cm)
+    assert np.all(np.isinf(cm.cpu().numpy()[[2, 3, 4]]))
+
+
+def test_free_fall_and_resting_closed_forms_on_gpu():
+    """The GPU step reproduces the discrete free fall and carries exactly the weight at rest."""
+    from paper_2002_12160_gb300 import inhand
+    d = dev()
+    rows = W.box27()
+    sc = W.ground_scene(rows)
+    cfg = W.SimConfig()
+    sim = inhand.Sim(sc, cfg, 2, 400, seed=1)
+    sim.sim_set_commands(0, torch.zeros((401, 0), dtype=torch.float32, device=d))
+    z0 = 0.01 + W.bottom_depth(rows)
+    pose = torch.tensor([[0, 0, 0.2, 0, 1, 0, 0, 0], [0, 0, z0 - 0.001, 0, 1, 0, 0, 0]], dtype=torch.float32, device=d)
+    vel = torch.tensor([[0.1, 0, 0.3, 0, 0, 0, 0, 0], [0] * 8], dtype=torch.float32, device=d)
+    params = torch.tensor([[0.1, 0.5], [0.17, 0.6]], dtype=torch.float32, device=d)
+    sim.sim_set_state(pose, vel, params)
+    sim.sim_step(0, 3)
+    p = sim.sim_get_state()[0].cpu().numpy()
+    h = cfg.frame_dt / cfg.substeps
+    n = 3 * cfg.substeps
+    z_ref = 0.2 + n * h * 0.3 - 9.81 * h * h * n * (n + 1) / 2
+    assert abs(p[0, 2] - z_ref) < 2e-6 and abs(p[0, 0] - 0.1 * n * h) < 1e-6
+    sim.sim_step(3, 297)
+    forces, status = sim.sim_read_sensors()
+    f = forces.cpu().numpy()
+    np.testing.assert_allclose(f[1, 0], [0, 0, -0.17 * 9.81], rtol=2e-4, atol=1e-5)
+    v = sim.sim_get_state()[1].cpu().numpy()
+    assert np.abs(v[1]).max() < 1e-5
+
+
+def test_contact_overflow_and_escape_flags_match_oracle():
+    wl = W.make_workload("tracking_cyl64", n_envs=4, frames=3)
+    wl.sim.c_max = 8
+    sim = start(wl, n=4, frames=3)
+    d = dev()
+    pose, vel, params, _ = sim.sim_get_state()
+    pose[3, 2] = 0.29
+    vel[3, 2] = 3.0
+    sim.sim_set_state(pose, vel, params)
+    rep = compare_frame(wl, sim, 0)
+    np.testing.assert_array_equal(rep["status_gpu"], rep["status_or"])
+    assert rep["status_gpu"][3] & 2
+    assert (rep["status_gpu"][:3] & 4).all()
+
+
+def test_single_environment_and_ragged_batches():
+    for n in (1, 5, 33):
+        wl = W.make_workload("tracking_box27", n_envs=n, frames=6)
+        sim = start(wl, n=n, frames=6)
+        sim.sim_step(0, 3)
+        rep = compare_frame(wl, sim, 3)
+        assert_report(rep, min_ok_frac=0.0)
