@@ -684,9 +684,12 @@ static double frame_cost(const orc_config *cfg, int P, const double *c_sim, cons
         const double *a = c_sim + 3 * l, *b = c_obs + 3 * l;
         double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
         cost += cfg->w_force * (dx * dx + dy * dy + dz * dz);
-        double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-        double nb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-        int in_a = na > cfg->tau, in_b = nb > cfg->tau;
+        /* a sensor is in contact when its force magnitude exceeds tau,
+           i.e. when the squared magnitude exceeds tau^2 (Sec. III-C) */
+        double na2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+        double nb2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        double tau2 = cfg->tau * cfg->tau;
+        int in_a = na2 > tau2, in_b = nb2 > tau2;
         if (in_a != in_b) cost += cfg->w_contact;   /* w (1 - alpha) */
     }
     return cost;
