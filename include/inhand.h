@@ -79,7 +79,7 @@ typedef struct {
     const float *pad_s0, *pad_s1; /* host [P] */
 } ih_scene;
 
-#define IH_MAX_SPHERES 1024
+#define IH_MAX_SPHERES 256
 #define IH_MAX_FINGERS 7
 #define IH_MAX_PADS 32
 #define IH_MAX_CONTACTS 256
@@ -213,6 +213,27 @@ ih_status optimizer_update(ih_sim *sim, const ih_opt_config *opt, uint32_t updat
  * out[3] = env-substeps stepped, out[4] = solver iterations summed over
  * env-substeps with contacts (host uint64[5]; synchronises the stream). */
 ih_status sim_work_counters(ih_sim *sim, uint64_t *out, int32_t reset);
+
+/* Choose the step kernel's shape -- threads per environment (16, 32, 64 or
+ * 128) and register-resident contacts per thread -- by timing every
+ * supported shape whose capacity covers c_max on frames [frame0, frame0 +
+ * n_frames) of the current state. The state, forces and work counters are
+ * restored after every trial, so the call leaves the simulation unchanged.
+ * Results of different shapes agree up to FP32 summation order. chosen
+ * (host int32[2], may be NULL) receives the shape; ms (host float[16], may be
+ * NULL) the time of each tried shape in the order of sim_step_variants.
+ * Synchronises the stream. Not a passage of the paper: the batching of
+ * environments onto the GPU is this library's. */
+ih_status sim_autotune(ih_sim *sim, int32_t frame0, int32_t n_frames, int32_t *chosen, float *ms);
+
+/* Force the step kernel's shape (threads per env, contacts per thread);
+ * IH_ERR_ARG if unsupported or below c_max. */
+ih_status sim_set_variant(ih_sim *sim, int32_t threads_per_env, int32_t contacts_per_thread);
+
+/* The supported shapes as pairs (threads per env, contacts per thread):
+ * writes up to `cap` pairs into out (host int32[2 * cap]) and returns how
+ * many exist. */
+int32_t sim_step_variants(int32_t *out, int32_t cap);
 
 /* Wait for the handle's stream; IH_ERR_CUDA if a kernel failed. */
 ih_status sim_sync(ih_sim *sim);

@@ -25,6 +25,7 @@ struct ih_sim {
     cudaStream_t stream = nullptr;
     StepVariant variant{32, 4, 128};
     int step_grid = 0;
+    int s_max = 1;   // most spheres in one shape
     // device buffers
     float4 *spheres_raw = nullptr, *spheres = nullptr, *finger_root = nullptr;
     int *shape_first = nullptr, *shape_count = nullptr, *pad_link = nullptr;
@@ -34,7 +35,7 @@ struct ih_sim {
     float2 *params = nullptr;
     int *shape = nullptr, *iters = nullptr, *status = nullptr;
     float *forces = nullptr;
-    double *c_sum = nullptr;
+    double *c_sum = nullptr, *c_mean = nullptr;
     int *n_window = nullptr, *argmin = nullptr;
     double *part_c = nullptr;
     int *part_i = nullptr;
@@ -42,7 +43,7 @@ struct ih_sim {
     unsigned long long *work = nullptr;
     unsigned char *is_elite = nullptr;
     int *rank = nullptr, *elite_env = nullptr;
-    double *elite_cdf = nullptr, *chol = nullptr;
+    double *elite_w = nullptr, *block_w = nullptr, *moments = nullptr, *misc = nullptr;
     std::vector<void *> owned;
     // host bookkeeping
     std::vector<char> frame_ready;   // commands uploaded for frame f
@@ -95,13 +96,16 @@ DevScene dev_scene(const ih_sim *s) {
     return d;
 }
 
-// Step-kernel shape: the smallest group width whose contact capacity covers
-// c_max, with register-resident contacts per lane kept at 4 or 8.
-StepVariant pick_variant(int c_max) {
-    const StepVariant order[] = {{32, 2, 128}, {32, 4, 128}, {32, 8, 128}};
-    for (const auto &v : order)
+// Default step-kernel shape before any autotuning: few environments get a
+// whole CTA each (latency bound), many get one warp each (issue bound); the
+// register-resident contacts per thread must cover c_max.
+StepVariant default_variant(int N, int c_max) {
+    const StepVariant wide[] = {{128, 1, 128}, {128, 2, 128}};
+    const StepVariant narrow[] = {{32, 4, 128}, {32, 8, 128}};
+    const bool few = N <= 4096;
+    for (const auto &v : (few ? wide : narrow))
         if (step_variant_max_contacts(v) >= c_max) return v;
-    return {32, 8, 128};
+    return few ? wide[1] : narrow[1];
 }
 
 int grid_for(const StepVariant &v, int N) {
@@ -129,20 +133,25 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
         !finite_pos(sc->link_len) || !(sc->link_rad >= 0.0f))
         return fail(nullptr, IH_ERR_ARG, "palm and link dimensions must be positive");
     const int n_links = 1 + 4 * sc->n_fingers;
-    int total = 0;
+    int total = 0, s_max_scene = 1;
     for (int k = 0; k < sc->n_shapes; ++k) {
         const int f = sc->shape_first[k], c = sc->shape_count[k];
         if (c < 1 || c > IH_MAX_SPHERES || f < 0)
             return fail(nullptr, IH_ERR_ARG, "shape %d: count must be in [1, %d]", k, IH_MAX_SPHERES);
         total = std::max(total, f + c);
+        s_max_scene = std::max(s_max_scene, c);
     }
     for (int j = 0; j < total; ++j)
         if (!(sc->spheres[4 * j + 3] > 0.0f) || !std::isfinite(sc->spheres[4 * j]) ||
             !std::isfinite(sc->spheres[4 * j + 1]) || !std::isfinite(sc->spheres[4 * j + 2]))
             return fail(nullptr, IH_ERR_ARG, "sphere %d is invalid", j);
-    for (int p = 0; p < sc->n_pads; ++p)
+    for (int p = 0; p < sc->n_pads; ++p) {
         if (sc->pad_link[p] < 0 || sc->pad_link[p] >= n_links || !(sc->pad_s0[p] <= sc->pad_s1[p]))
             return fail(nullptr, IH_ERR_ARG, "pad %d is invalid", p);
+        int same = 0;
+        for (int k = 0; k < sc->n_pads; ++k) same += sc->pad_link[k] == sc->pad_link[p];
+        if (same > 4) return fail(nullptr, IH_ERR_ARG, "more than 4 pads on link %d", sc->pad_link[p]);
+    }
     if (cfg->n_envs < 1 || cfg->max_frames < 1 || cfg->substeps < 1 || cfg->iters < 0 ||
         !finite_pos(cfg->frame_dt) || !(cfg->margin >= 0.0f) || !(cfg->beta >= 0.0f) ||
         !(cfg->slop >= 0.0f) || !(cfg->vmax >= 0.0f) || !(cfg->tau >= 0.0f) ||
@@ -152,6 +161,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     ih_sim *s = new ih_sim();
     s->n_shapes = sc->n_shapes; s->n_fingers = sc->n_fingers; s->n_links = n_links;
     s->n_pads = sc->n_pads; s->n_joints = 4 * sc->n_fingers; s->total_spheres = total;
+    s->s_max = s_max_scene;
     for (int k = 0; k < 3; ++k) s->palm_half[k] = sc->palm_half[k];
     s->link_len = sc->link_len; s->link_rad = sc->link_rad;
     s->cfg = *cfg;
@@ -164,7 +174,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     d.gx = cfg->gravity[0]; d.gy = cfg->gravity[1]; d.gz = cfg->gravity[2];
     d.tau = cfg->tau; d.w_force = cfg->w_force; d.w_contact = cfg->w_contact;
     d.c_max = cfg->c_max; d.escape_radius = cfg->escape_radius;
-    s->variant = pick_variant(cfg->c_max);
+    s->variant = default_variant(cfg->n_envs, cfg->c_max);
     const int N = cfg->n_envs, P = sc->n_pads, F = sc->n_fingers;
 
     cudaError_t e = cudaSuccess;
@@ -178,11 +188,13 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->pose, 2 * (size_t)N)); A(dalloc(s, &s->vel, 2 * (size_t)N));
     A(dalloc(s, &s->params, N)); A(dalloc(s, &s->shape, N)); A(dalloc(s, &s->iters, N));
     A(dalloc(s, &s->status, N)); A(dalloc(s, &s->forces, (size_t)N * P * 3));
-    A(dalloc(s, &s->c_sum, N)); A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
+    A(dalloc(s, &s->c_sum, N)); A(dalloc(s, &s->c_mean, N));
+    A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
     A(dalloc(s, &s->part_c, cost_blocks(N))); A(dalloc(s, &s->part_i, cost_blocks(N)));
     A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 5));
     A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
-    A(dalloc(s, &s->elite_cdf, N)); A(dalloc(s, &s->chol, 68));
+    A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
+    A(dalloc(s, &s->moments, (size_t)opt_blocks(N) * kMoments)); A(dalloc(s, &s->misc, 80));
     if (e != cudaSuccess) {
         ih_status st = cuda_fail(nullptr, e, "sim_create allocation");
         sim_destroy(s);
@@ -212,6 +224,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemsetAsync(s->status, 0, (size_t)N * sizeof(int), st));
     A(cudaMemsetAsync(s->forces, 0, (size_t)N * P * 3 * sizeof(float), st));
     A(cudaMemsetAsync(s->c_sum, 0, (size_t)N * sizeof(double), st));
+    A(cudaMemsetAsync(s->c_mean, 0, (size_t)N * sizeof(double), st));
     A(cudaMemsetAsync(s->n_window, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->argmin, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->done, 0, sizeof(unsigned int), st));
@@ -310,7 +323,7 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
     a.frame0 = frame0; a.n_frames = n_frames; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
     a.shape = s->shape; a.iters = s->iters; a.status = s->status; a.forces = s->forces; a.work = s->work;
-    cudaError_t e = launch_step(a, s->variant, s->step_grid, s->stream);
+    cudaError_t e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->stepped = true;
     return IH_OK;
@@ -333,7 +346,8 @@ ih_status cost_eval(ih_sim *s, const float *obs, double *cost_mean, int32_t *arg
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     CostArgs a;
     a.N = s->cfg.n_envs; a.P = s->n_pads; a.cfg = s->dcfg; a.forces = s->forces; a.obs = obs;
-    a.status = s->status; a.c_sum = s->c_sum; a.n_window = s->n_window; a.cost_mean = cost_mean;
+    a.status = s->status; a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window;
+    a.cost_mean = cost_mean;
     a.pose = s->pose; a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est_pose;
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
     cudaError_t e = launch_cost(a, s->stream);
@@ -356,11 +370,11 @@ ih_status optimizer_update(ih_sim *s, const ih_opt_config *opt, uint32_t update_
     a.N = s->cfg.n_envs; a.elite_frac = opt->elite_frac;
     for (int k = 0; k < 8; ++k) a.floor_var[k] = (double)opt->floor_std[k] * (double)opt->floor_std[k];
     a.m_lo = opt->m_lo; a.m_hi = opt->m_hi; a.mu_lo = opt->mu_lo; a.mu_hi = opt->mu_hi;
-    a.seed = s->seed; a.update_index = update_index; a.c_sum = s->c_sum; a.n_window = s->n_window;
-    a.pose = s->pose; a.vel = s->vel; a.params = s->params; a.status = s->status;
-    a.is_elite = s->is_elite; a.rank = s->rank; a.elite_env = s->elite_env; a.elite_cdf = s->elite_cdf;
-    a.chol = s->chol; a.argmin_state = s->argmin; a.argmin_out = argmin; a.parent_out = parent;
-    a.c_sum_reset = s->c_sum; a.n_window_reset = s->n_window;
+    a.seed = s->seed; a.update_index = update_index; a.c_mean = s->c_mean; a.c_sum = s->c_sum;
+    a.n_window = s->n_window; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
+    a.status = s->status; a.is_elite = s->is_elite; a.rank = s->rank; a.elite_env = s->elite_env;
+    a.elite_w = s->elite_w; a.block_w = s->block_w; a.moments = s->moments; a.misc = s->misc;
+    a.argmin_state = s->argmin; a.argmin_out = argmin; a.parent_out = parent;
     cudaError_t e = launch_optimizer(a, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "optimizer launch");
     s->window_frames = 0;
@@ -375,6 +389,96 @@ ih_status sim_work_counters(ih_sim *s, uint64_t *out, int32_t reset) {
     if (e == cudaSuccess && reset) e = cudaMemsetAsync(s->work, 0, sizeof w, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "work counters");
     for (int k = 0; k < 5; ++k) out[k] = w[k];
+    return IH_OK;
+}
+
+ih_status sim_set_variant(ih_sim *s, int32_t tpe, int32_t cpl) {
+    if (!s) return IH_ERR_ARG;
+    StepVariant v{tpe, cpl, 128};
+    if (!step_variant_supported(v)) return fail(s, IH_ERR_ARG, "unsupported step shape %d x %d", tpe, cpl);
+    if (step_variant_max_contacts(v) < s->cfg.c_max)
+        return fail(s, IH_ERR_ARG, "shape %d x %d holds fewer than c_max = %d contacts", tpe, cpl, s->cfg.c_max);
+    s->variant = v;
+    s->step_grid = grid_for(v, s->cfg.n_envs);
+    return IH_OK;
+}
+
+int32_t sim_step_variants(int32_t *out, int32_t cap) {
+    StepVariant v[32];
+    const int n = step_variant_list(v, 32);
+    for (int k = 0; k < n && k < cap && out; ++k) { out[2 * k] = v[k].group; out[2 * k + 1] = v[k].cpl; }
+    return n;
+}
+
+ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *chosen, float *ms_out) {
+    if (!s) return IH_ERR_ARG;
+    if (n_frames < 1 || frame0 < 0 || frame0 + n_frames > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + n_frames);
+    for (int f = frame0; f < frame0 + n_frames; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    const size_t N = s->cfg.n_envs, P = s->n_pads;
+    // scratch copy of everything a step writes
+    void *bp = nullptr, *bv = nullptr, *bs = nullptr, *bf = nullptr;
+    unsigned long long wsave[5];
+    cudaError_t e = cudaMalloc(&bp, N * 2 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&bv, N * 2 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&bs, N * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&bf, N * P * 3 * sizeof(float));
+    cudaStream_t st = s->stream;
+    auto save = [&]() {
+        cudaMemcpyAsync(bp, s->pose, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(bv, s->vel, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(bs, s->status, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(bf, s->forces, N * P * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(wsave, s->work, sizeof wsave, cudaMemcpyDeviceToHost, st);
+    };
+    auto restore = [&]() {
+        cudaMemcpyAsync(s->pose, bp, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s->vel, bv, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s->status, bs, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s->forces, bf, N * P * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s->work, wsave, sizeof wsave, cudaMemcpyHostToDevice, st);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    StepVariant cand[32];
+    const int nv = step_variant_list(cand, 32);
+    const StepVariant keep = s->variant;
+    StepVariant best = keep;
+    float best_ms = INFINITY;
+    if (e == cudaSuccess) { save(); e = cudaStreamSynchronize(st); }
+    for (int k = 0; k < nv && e == cudaSuccess; ++k) {
+        float ms = NAN;
+        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max) {
+            s->variant = cand[k];
+            s->step_grid = grid_for(cand[k], (int)N);
+            ih_status r = sim_step(s, frame0, n_frames);   // warm-up (and first-use setup)
+            restore();
+            if (r == IH_OK) {
+                cudaEventRecord(e0, st);
+                r = sim_step(s, frame0, n_frames);
+                cudaEventRecord(e1, st);
+                restore();
+                e = cudaStreamSynchronize(st);
+                if (e == cudaSuccess && r == IH_OK) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (r != IH_OK && e == cudaSuccess) e = cudaErrorLaunchFailure;
+            if (ms < best_ms) { best_ms = ms; best = cand[k]; }
+        }
+        if (ms_out && k < 16) ms_out[k] = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(bp); cudaFree(bv); cudaFree(bs); cudaFree(bf);
+    if (e != cudaSuccess) {
+        s->variant = keep;
+        s->step_grid = grid_for(keep, (int)N);
+        return cuda_fail(s, e, "autotune");
+    }
+    s->variant = best;
+    s->step_grid = grid_for(best, (int)N);
+    if (chosen) { chosen[0] = best.group; chosen[1] = best.cpl; }
     return IH_OK;
 }
 

@@ -196,9 +196,11 @@ struct StepVariant {
     int cpl;          // register-resident contacts per lane
     int block;        // threads per CTA
 };
-cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, cudaStream_t s);
+cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s);
 int step_variant_max_contacts(const StepVariant &v);
 bool step_variant_supported(const StepVariant &v);
+size_t step_smem_bytes(const StepVariant &v, int s_max);
+int step_variant_list(StepVariant *out, int cap);
 
 struct CostArgs {
     int N, P;
@@ -206,19 +208,23 @@ struct CostArgs {
     const float *forces;     // [N][P][3]
     const float *obs;        // [P][3]
     const int *status;
-    double *c_sum;           // [N]
+    double *c_sum;           // [N] window sums
+    double *c_mean;          // [N] window means (handle-owned, read by the optimizer)
     int *n_window;           // device counter
-    double *cost_mean;       // [N] or null
+    double *cost_mean;       // [N] caller copy or null
     const float4 *pose;      // for est_pose
     int *argmin_state;       // handle's i*
     int *argmin_out;         // user or null
     float *est_pose_out;     // user float[8] or null
     double *part_c;          // [blocks] scratch
     int *part_i;             // [blocks] scratch
-    unsigned int *done;      // scratch counter (zero between launches)
+    unsigned int *done;      // scratch ticket (zero between launches)
 };
 cudaError_t launch_cost(const CostArgs &a, cudaStream_t s);
 int cost_blocks(int N);
+
+constexpr int kOptBlock = 32;   // elites / environments per block in the grid kernels
+constexpr int kMoments = 45;    // sum w, sum w d (8), sum w d d^T (36, lower triangle)
 
 struct OptArgs {
     int N;
@@ -227,23 +233,25 @@ struct OptArgs {
     float m_lo, m_hi, mu_lo, mu_hi;
     uint64_t seed;
     uint32_t update_index;
-    const double *c_sum;
-    const int *n_window;
+    const double *c_mean;     // [N] window means
+    double *c_sum;            // [N] reset by apply
+    int *n_window;            // reset by apply
     float4 *pose, *vel;
     float2 *params;
     int *status;
-    // scratch written by the select kernel, read by the apply kernel
+    // scratch
     unsigned char *is_elite;  // [N]
-    int *rank;                // [N] elite rank or non-elite rank
+    int *rank;                // [N] rank among elites or among non-elites
     int *elite_env;           // [N] elites in index order (first k used)
-    double *elite_cdf;        // [N]
-    double *chol;             // [64 + 4]: L, then k, u, i*, ok
+    double *elite_w;          // [N] unnormalised weights, then inclusive prefix within its block
+    double *block_w;          // [blocks] weight sum per block, then exclusive offsets
+    double *moments;          // [blocks][kMoments]
+    double *misc;             // [80]: L (64), k, u, i*, ok, wsum, cmin, sd, nfin, nblocks
     int *argmin_state;
     int *argmin_out;
     int *parent_out;
-    double *c_sum_reset;      // same as c_sum (reset by apply)
-    int *n_window_reset;
 };
+int opt_blocks(int N);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
 
 }  // namespace ih

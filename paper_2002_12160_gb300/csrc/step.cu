@@ -2,44 +2,111 @@
 // independent hand-plus-object simulations (Sec. III-A; Algorithm 1, "step
 // simulation"), with the contact-sensor readout c_t^(l) of every pad.
 //
-// One group of G lanes (G = 8, 16 or 32) owns one environment at a time and
-// walks the environments grid-stride. Per substep the group
-//   1. predicts the velocity under gravity;
+// A group of TPE threads (16, 32, 64 or 128) owns one environment at a time
+// and walks the environments grid-stride; groups wider than a warp
+// synchronise with named barriers. Per substep the group
+//   1. predicts the velocity under gravity and caches the object's spheres,
+//      rotated into the world frame, in shared memory;
 //   2. culls hand links against the object's bounding sphere (one ballot);
-//   3. tests every (sphere, surviving link) pair, spread over the G lanes,
-//      and compacts contacts (gap d < margin) into shared memory by ballot;
-//   4. moves each contact into the registers of one lane (CPL per lane) with
-//      its lever arm, normal, scalar normal/tangential effective masses and
-//      bias folded into a target velocity;
+//   3. tests every (surviving link, sphere) pair, TPE pairs per round, and
+//      compacts contacts (gap d < margin) into shared memory in pair order by
+//      ballot (and, across warps, by per-warp counts);
+//   4. moves each contact into the registers of one thread (CPL per thread)
+//      with its lever arm, normal, scalar normal/tangential effective masses
+//      and the bias folded into a target velocity;
 //   5. runs `iters` Jacobi projected-impulse iterations: every contact updates
-//      against the same body velocity, then the group sums the impulses and
-//      their moments with xor shuffles and recomputes the velocity;
+//      against the same body velocity, then the group sums impulses and
+//      moments (xor shuffles, then a double-buffered shared-memory exchange
+//      between warps) and recomputes the body velocity;
 //   6. integrates (symplectic Euler, exact rotation exponential) and adds the
-//      contacts' impulses into their sensor pads in a fixed order.
+//      contacts' impulses into their sensor pads in a fixed order, each pad
+//      scanning only the contacts of its own link.
 // Nothing here is a dense contraction: the kernel is bound by FP32 issue and
-// by the shuffles of step 5.
+// by the latency of the solver's reductions.
 #include "internal.cuh"
 
 namespace ih {
 namespace {
 
 constexpr int kBlock = 128;
+constexpr int kMaxLinks = 32;
+constexpr int kPadsPerLink = 4;
 
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-    if constexpr (G == 32) {
-        return 0xffffffffu;
-    } else {
-        const int lane = threadIdx.x & 31;
-        return ((1u << G) - 1u) << ((lane / G) * G);
+template <int TPE>
+struct Group {
+    static constexpr int GPB = kBlock / TPE;               // groups per block
+    static constexpr int W = TPE >= 32 ? TPE / 32 : 1;     // warps per group
+    static constexpr int WIDTH = TPE < 32 ? TPE : 32;      // lanes of the group in one warp
+    int grp, tid, wid, lane;
+    unsigned mask;    // this group's lanes in the warp
+    int shift;        // first lane of this group in the warp
+    __device__ Group() {
+        grp = threadIdx.x / TPE;
+        tid = threadIdx.x % TPE;
+        lane = threadIdx.x & 31;
+        wid = tid / 32;
+        if constexpr (TPE < 32) {
+            shift = (lane / TPE) * TPE;
+            mask = ((1u << TPE) - 1u) << shift;
+        } else {
+            shift = 0;
+            mask = 0xffffffffu;
+        }
     }
+    __device__ __forceinline__ void sync() const {
+        if constexpr (TPE <= 32) {
+            __syncwarp(mask);
+        } else if constexpr (TPE == kBlock) {
+            __syncthreads();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(TPE) : "memory");
+        }
+    }
+    // ballot of `p` over the group's lanes in this warp, bit 0 = first lane
+    __device__ __forceinline__ unsigned ballot(bool p) const {
+        const unsigned b = __ballot_sync(mask, p);
+        if constexpr (TPE < 32) return (b >> shift) & ((1u << TPE) - 1u);
+        return b;
+    }
+    __device__ __forceinline__ int lane_in_warp() const { return TPE < 32 ? tid : lane; }
+};
+
+// Shared memory of one group (dynamic, sized by the host for the scene).
+struct GroupSmem {
+    float4 *sph;          // [S_max]   sphere centre relative to x (world frame), radius
+    float4 *stage;        // [CAP][2]  (r, gap), (n, link | pad << 8)
+    float *padacc;        // [IH_MAX_PADS*3]
+    float *red;           // [2][W][8] cross-warp partial sums
+    int *cnt;             // [2][W]    cross-warp hit counts
+    unsigned char *links; // [32]      surviving links in order
+    unsigned short *lbeg, *lend;  // [32] contact range of each link
+    unsigned *surv;       // [1]
+};
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t group_smem_bytes(int s_max, int cap, int w) {
+    return align16(sizeof(float4) * s_max) + align16(sizeof(float4) * 2 * cap) +
+           align16(sizeof(float) * IH_MAX_PADS * 3) + align16(sizeof(float) * 2 * w * 8) +
+           align16(sizeof(int) * 2 * w) + align16(kMaxLinks) + 2 * align16(2 * kMaxLinks) + 16;
+}
+__host__ __device__ inline size_t block_smem_bytes() {
+    return align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink) + 2 * align16(4 * IH_MAX_PADS);
 }
 
-template <int G>
-__device__ __forceinline__ float group_sum(float v, unsigned mask) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
-    return v;
+__device__ GroupSmem carve_group(unsigned char *base, int s_max, int cap, int w) {
+    GroupSmem g;
+    size_t o = 0;
+    g.sph = reinterpret_cast<float4 *>(base + o); o += align16(sizeof(float4) * s_max);
+    g.stage = reinterpret_cast<float4 *>(base + o); o += align16(sizeof(float4) * 2 * cap);
+    g.padacc = reinterpret_cast<float *>(base + o); o += align16(sizeof(float) * IH_MAX_PADS * 3);
+    g.red = reinterpret_cast<float *>(base + o); o += align16(sizeof(float) * 2 * w * 8);
+    g.cnt = reinterpret_cast<int *>(base + o); o += align16(sizeof(int) * 2 * w);
+    g.links = base + o; o += align16(kMaxLinks);
+    g.lbeg = reinterpret_cast<unsigned short *>(base + o); o += align16(2 * kMaxLinks);
+    g.lend = reinterpret_cast<unsigned short *>(base + o); o += align16(2 * kMaxLinks);
+    g.surv = reinterpret_cast<unsigned *>(base + o);
+    return g;
 }
 
 struct Hit {
@@ -75,10 +142,9 @@ __device__ __forceinline__ Hit hit_box(V3 c, float rs, V3 a, Q4 q, float hx, flo
     return h;
 }
 
-// sphere against a capsule of axis a + s d, s in [0, L], radius rc
-__device__ __forceinline__ Hit hit_capsule(V3 c, float rs, V3 a, V3 d, float L, float rc, Q4 q) {
-    const V3 ca = c - a;
-    const float t = fminf(fmaxf(dot(ca, d) / L, 0.0f), 1.0f);
+// sphere at ca (relative to the capsule start) against the axis s d, s in [0, L]
+__device__ __forceinline__ Hit hit_capsule(V3 ca, float rs, V3 d, float L, float inv_L, float rc, Q4 q) {
+    const float t = fminf(fmaxf(dot(ca, d) * inv_L, 0.0f), 1.0f);
     const V3 diff = ca - d * (t * L);
     const float dist = sqrtf(dot(diff, diff));
     Hit h;
@@ -88,14 +154,24 @@ __device__ __forceinline__ Hit hit_capsule(V3 c, float rs, V3 a, V3 d, float L, 
     return h;
 }
 
-__device__ __forceinline__ int pad_of(const DevScene &sc, int l, float t) {
-    for (int k = 0; k < sc.n_pads; ++k) {
-        if (__ldg(sc.pad_link + k) != l) continue;
-        if (l == 0) return k;
-        const float s0 = __ldg(sc.pad_s0 + k), s1 = __ldg(sc.pad_s1 + k);
-        if (t >= s0 && (t < s1 || s1 >= 1.0f)) return k;
+__device__ __forceinline__ bool link_reaches(const DevScene &sc, const DevConfig &cfg, const float4 *L0,
+                                             int l, V3 x, float bound) {
+    const V3 la = xyz(__ldg(L0 + l * kLinkStride));
+    const V3 xa = x - la;
+    if (l == 0) {
+        const float4 qq = __ldg(L0 + 2);
+        const V3 cl = qrot_inv({qq.x, qq.y, qq.z, qq.w}, xa);
+        const V3 k3 = mk(fminf(fmaxf(cl.x, -sc.palm_hx), sc.palm_hx), fminf(fmaxf(cl.y, -sc.palm_hy), sc.palm_hy),
+                         fminf(fmaxf(cl.z, -sc.palm_hz), sc.palm_hz));
+        const V3 dd = cl - k3;
+        const float reach = bound + cfg.margin;
+        return dot(dd, dd) < reach * reach;
     }
-    return -1;
+    const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
+    const float t = fminf(fmaxf(dot(xa, ld), 0.0f), sc.link_len);
+    const V3 dd = xa - ld * t;
+    const float reach = bound + sc.link_rad + cfg.margin;
+    return dot(dd, dd) < reach * reach;
 }
 
 __device__ __forceinline__ float contact_bias(const DevConfig &cfg, float gap) {
@@ -109,28 +185,65 @@ __device__ __forceinline__ bool all_finite(V3 x, Q4 q, V3 v, V3 w) {
            isfinite(w.x) && isfinite(w.y) && isfinite(w.z);
 }
 
-template <int G, int CPL>
-__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
-    constexpr int GPB = kBlock / G;   // groups per block
-    constexpr int CAP = G * CPL;      // staged contacts per group
-    // staging: [0] = lever arm r, gap ; [1] = normal n, (link | pad << 8)
-    __shared__ float4 stage[GPB][CAP][2];
-    __shared__ float padacc[GPB][IH_MAX_PADS * 3];
-    __shared__ unsigned char links[GPB][32];
+template <int TPE>
+__device__ __forceinline__ void group_sum6(float (&v)[6], const Group<TPE> &G, float *red, int parity) {
+    constexpr int WIDTH = Group<TPE>::WIDTH;
+#pragma unroll
+    for (int o = WIDTH / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(G.mask, v[k], o);
+    if constexpr (TPE > 32) {
+        constexpr int W = Group<TPE>::W;
+        float *r = red + parity * W * 8;
+        if (G.lane == 0)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r[G.wid * 8 + k] = v[k];
+        G.sync();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float s = r[k];
+#pragma unroll
+            for (int w = 1; w < W; ++w) s += r[w * 8 + k];
+            v[k] = s;
+        }
+    }
+}
 
+template <int TPE, int CPL>
+__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_max) {
+    using Grp = Group<TPE>;
+    constexpr int GPB = Grp::GPB, W = Grp::W, CAP = TPE * CPL;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Grp G;
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
-    const int grp = threadIdx.x / G;
-    const int g = threadIdx.x % G;
-    const unsigned gmask = group_mask<G>();
-    const int gshift = (threadIdx.x & 31) / G * G;
-    const unsigned gbits = (G == 32) ? 0xffffffffu : ((1u << (G & 31)) - 1u);
     const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads;
-    const float h = cfg.h;
+    const float h = cfg.h, inv_h = 1.0f / h, inv_L = 1.0f / sc.link_len;
     const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
-    unsigned long long w_pairs = 0, w_contacts = 0, w_citers = 0, w_substeps = 0, w_iters = 0;
 
-    for (int env = blockIdx.x * GPB + grp; env < a.N; env += gridDim.x * GPB) {
+    // block-wide tables: the pads of each link (in pad order) and their intervals
+    unsigned char *pl_cnt = smem;
+    unsigned char *pl_id = smem + align16(kMaxLinks);
+    float *p_s0 = reinterpret_cast<float *>(smem + align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink));
+    float *p_s1 = p_s0 + IH_MAX_PADS;
+    const size_t gbytes = group_smem_bytes(s_max, CAP, W);
+    const GroupSmem S = carve_group(smem + block_smem_bytes() + G.grp * gbytes, s_max, CAP, W);
+    if (threadIdx.x < kMaxLinks) {
+        int c = 0;
+        for (int p = 0; p < P && c < kPadsPerLink; ++p)
+            if (__ldg(sc.pad_link + p) == (int)threadIdx.x) pl_id[threadIdx.x * kPadsPerLink + c++] = (unsigned char)p;
+        pl_cnt[threadIdx.x] = (unsigned char)c;
+    }
+    for (int p = threadIdx.x; p < P; p += kBlock) {
+        p_s0[p] = __ldg(sc.pad_s0 + p);
+        p_s1[p] = __ldg(sc.pad_s1 + p);
+    }
+    __syncthreads();
+
+    unsigned long long w_pairs = 0, w_contacts = 0, w_citers = 0, w_substeps = 0, w_iters = 0;
+    int parity = 0;
+
+    for (int env = blockIdx.x * GPB + G.grp; env < a.N; env += gridDim.x * GPB) {
         int st = a.status[env];
         const float4 P0 = a.pose[2 * env], P1 = a.pose[2 * env + 1];
         const float4 V0 = a.vel[2 * env], V1 = a.vel[2 * env + 1];
@@ -141,15 +254,16 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
         Q4 q = {P1.x, P1.y, P1.z, P1.w};
         V3 v = xyz(V0), w = xyz(V1);
         const float m = th.x, mu = th.y, inv_m = 1.0f / m;
-        const int sfirst = __ldg(sc.shape_first + shp), S = __ldg(sc.shape_count + shp);
+        const int sfirst = __ldg(sc.shape_first + shp), NS = __ldg(sc.shape_count + shp);
         const float bound = __ldg(sc.shape_bound + shp);
+        const float inv_nsph = 1.0f / (float)NS;
         S6 Jb;
         Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
         Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
         Jb.xz = __ldg(sc.shape_jinv + 6 * shp + 4); Jb.yz = __ldg(sc.shape_jinv + 6 * shp + 5);
 
         for (int fr = 0; fr < a.n_frames; ++fr) {
-            for (int k = g; k < 3 * P; k += G) padacc[grp][k] = 0.0f;
+            for (int k = G.tid; k < 3 * P; k += TPE) S.padacc[k] = 0.0f;
             if (st & kDiverged) continue;
             const float4 *tab = a.link_tab + (size_t)(a.frame0 + fr) * (ns + 1) * Lk * kLinkStride;
             for (int s = 0; s < ns; ++s) {
@@ -158,83 +272,104 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
                 const V3 v_pred = v + grav;
                 const V3 w_pred = w;
                 const M3 R = qmat(q);
-                const S6 W = world_inv_inertia(R, Jb, inv_m);
+                const S6 Wi = world_inv_inertia(R, Jb, inv_m);
 
-                // -- 2. cull links whose bounding volume the object cannot reach
-                unsigned surv = 0;
-                for (int base = 0; base < Lk; base += G) {
-                    const int l = base + g;
-                    bool keep = false;
-                    if (l < Lk) {
-                        const V3 la = xyz(__ldg(L0 + l * kLinkStride));
-                        if (l == 0) {
-                            const float4 qq = __ldg(L0 + 2);
-                            const V3 cl = qrot_inv({qq.x, qq.y, qq.z, qq.w}, x - la);
-                            const V3 k3 = mk(fminf(fmaxf(cl.x, -sc.palm_hx), sc.palm_hx),
-                                             fminf(fmaxf(cl.y, -sc.palm_hy), sc.palm_hy),
-                                             fminf(fmaxf(cl.z, -sc.palm_hz), sc.palm_hz));
-                            const V3 dd = cl - k3;
-                            const float reach = bound + cfg.margin;
-                            keep = dot(dd, dd) < reach * reach;
-                        } else {
-                            const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-                            const V3 xa = x - la;
-                            const float t = fminf(fmaxf(dot(xa, ld), 0.0f), sc.link_len);
-                            const V3 dd = xa - ld * t;
-                            const float reach = bound + sc.link_rad + cfg.margin;
-                            keep = dot(dd, dd) < reach * reach;
-                        }
-                    }
-                    const unsigned bal = (__ballot_sync(gmask, keep) >> gshift) & gbits;
-                    surv |= bal << base;
+                // -- 1. spheres to world (relative to x), cached for the substep
+                for (int j = G.tid; j < NS; j += TPE) {
+                    const float4 sp = __ldg(sc.spheres + sfirst + j);
+                    const V3 cr = mmul(R, xyz(sp));
+                    S.sph[j] = make_float4(cr.x, cr.y, cr.z, sp.w);
                 }
+                // -- 2. cull links whose bounding volume the object cannot reach
+                if constexpr (TPE >= 32) {
+                    if (G.wid == 0) {
+                        const bool keep = G.lane < Lk && link_reaches(sc, cfg, L0, G.lane, x, bound);
+                        const unsigned ml = __ballot_sync(0xffffffffu, keep);
+                        if (G.lane == 0) *S.surv = ml;
+                    }
+                } else {
+                    unsigned ml = 0;
+                    for (int base = 0; base < Lk; base += TPE) {
+                        const int l = base + G.tid;
+                        const bool keep = l < Lk && link_reaches(sc, cfg, L0, l, x, bound);
+                        ml |= G.ballot(keep) << base;
+                    }
+                    if (G.tid == 0) *S.surv = ml;
+                }
+                G.sync();
+                const unsigned surv = *S.surv;
                 const int nsurv = __popc(surv);
-                for (int l = g; l < Lk; l += G)
-                    if ((surv >> l) & 1u) links[grp][__popc(surv & ((1u << l) - 1u))] = (unsigned char)l;
-                __syncwarp(gmask);
+                for (int l = G.tid; l < kMaxLinks; l += TPE) {
+                    if (l < Lk && ((surv >> l) & 1u)) S.links[__popc(surv & ((1u << l) - 1u))] = (unsigned char)l;
+                    S.lbeg[l] = 0;
+                    S.lend[l] = 0;
+                }
+                G.sync();
 
-                // -- 3. narrowphase over (surviving link, sphere) pairs, compacted by ballot
+                // -- 3. narrowphase over (surviving link, sphere) pairs in pair order
                 int nc = 0;
-                const int npairs = nsurv * S;
-                int li = 0, j = g;
-                while (j >= S && li < nsurv) { j -= S; ++li; }
-                for (int p0 = 0; p0 < npairs; p0 += G) {
+                const int npairs = nsurv * NS;
+                for (int p0 = 0; p0 < npairs; p0 += TPE) {
+                    const int p = p0 + G.tid;
                     bool hit = false;
                     Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
                     V3 r = mk(0, 0, 0);
                     int l = 0;
-                    if (p0 + g < npairs) {
-                        l = links[grp][li];
-                        const float4 sp = __ldg(sc.spheres + sfirst + j);
-                        const V3 cr = mmul(R, xyz(sp));     // centre relative to x
-                        const V3 c = x + cr;
+                    if (p < npairs) {
+                        int li = (int)(((float)p + 0.5f) * inv_nsph);
+                        li = min(max(li, 0), nsurv - 1);
+                        const int j = p - li * NS;
+                        l = S.links[li];
+                        const float4 sp = S.sph[j];
+                        const V3 cr = xyz(sp);
                         const float4 A0 = __ldg(L0 + l * kLinkStride);
                         const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
                         const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
                         if (l == 0) {
-                            hh = hit_box(c, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                            hh = hit_box(x + cr, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
                         } else {
                             const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-                            hh = hit_capsule(c, sp.w, xyz(A0), ld, sc.link_len, sc.link_rad, lq);
+                            hh = hit_capsule((x - xyz(A0)) + cr, sp.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
                         }
                         hit = hh.gap < cfg.margin;
                         r = cr - hh.n * sp.w;
                     }
-                    const unsigned bal = (__ballot_sync(gmask, hit) >> gshift) & gbits;
+                    const unsigned bal = G.ballot(hit);
+                    int off = nc, tot;
+                    if constexpr (TPE > 32) {
+                        int *cb = S.cnt + parity * W;
+                        if (G.lane == 0) cb[G.wid] = __popc(bal);
+                        G.sync();
+                        tot = 0;
+#pragma unroll
+                        for (int k = 0; k < W; ++k) {
+                            const int c = cb[k];
+                            if (k < G.wid) off += c;
+                            tot += c;
+                        }
+                        parity ^= 1;
+                    } else {
+                        tot = __popc(bal);
+                    }
                     if (hit) {
-                        const int idx = nc + __popc(bal & ((1u << g) - 1u));
+                        const int idx = off + __popc(bal & ((1u << G.lane_in_warp()) - 1u));
                         if (idx < CAP) {
-                            const int pad = pad_of(sc, l, hh.t);
-                            stage[grp][idx][0] = make_float4(r.x, r.y, r.z, hh.gap);
-                            stage[grp][idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z,
-                                                             __int_as_float(l | ((pad & 0xff) << 8)));
+                            int pad = -1;
+                            const int npl = pl_cnt[l];
+                            for (int k = 0; k < npl; ++k) {
+                                const int pp = pl_id[l * kPadsPerLink + k];
+                                if (l == 0) { pad = pp; break; }
+                                const float s0 = p_s0[pp], s1 = p_s1[pp];
+                                if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
+                            }
+                            S.stage[2 * idx] = make_float4(r.x, r.y, r.z, hh.gap);
+                            S.stage[2 * idx + 1] = make_float4(hh.n.x, hh.n.y, hh.n.z,
+                                                               __int_as_float(l | ((pad & 0xff) << 8)));
                         }
                     }
-                    nc += __popc(bal);
-                    j += G;
-                    while (j >= S && li < nsurv) { j -= S; ++li; }
+                    nc += tot;
                 }
-                __syncwarp(gmask);
+                G.sync();
                 w_pairs += npairs;
                 w_substeps += 1;
                 if (nc > cfg.c_max) {   // more contacts than the per-env capacity
@@ -243,24 +378,27 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
                 }
                 w_contacts += nc;
 
-                // -- 4. contact setup in registers
+                // -- 4. contact setup in registers; contact range of each link
                 V3 cr_[CPL], cn_[CPL], cc_[CPL], lam_[CPL];
                 float ikn_[CPL], ikt_[CPL];
-                const float trW = W.xx + W.yy + W.zz;
+                const float trW = Wi.xx + Wi.yy + Wi.zz;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
-                    const int ci = g + k * G;
+                    const int ci = G.tid + k * TPE;
                     lam_[k] = mk(0, 0, 0);
                     cr_[k] = mk(0, 0, 0); cn_[k] = mk(0, 0, 1); cc_[k] = mk(0, 0, 0);
                     ikn_[k] = 0.0f; ikt_[k] = 0.0f;
                     if (ci < nc) {
-                        const float4 s0 = stage[grp][ci][0], s1 = stage[grp][ci][1];
+                        const float4 s0 = S.stage[2 * ci], s1 = S.stage[2 * ci + 1];
                         const V3 r = xyz(s0), n = xyz(s1);
                         const int l = __float_as_int(s1.w) & 0xff;
+                        if (ci == 0 || (__float_as_int(S.stage[2 * ci - 1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
+                        if (ci == nc - 1 || (__float_as_int(S.stage[2 * ci + 3].w) & 0xff) != l)
+                            S.lend[l] = (unsigned short)(ci + 1);
                         // k_n = 1/m + (r x n)^T W (r x n); tr K = 3/m + |r|^2 tr W - r^T W r
                         const V3 rn = cross(r, n);
-                        const float kn = inv_m + dot(rn, smul(W, rn));
-                        const float trK = 3.0f * inv_m + dot(r, r) * trW - dot(r, smul(W, r));
+                        const float kn = inv_m + dot(rn, smul(Wi, rn));
+                        const float trK = 3.0f * inv_m + dot(r, r) * trW - dot(r, smul(Wi, r));
                         ikn_[k] = 1.0f / kn;
                         ikt_[k] = 2.0f / (trK - kn);
                         const float b = contact_bias(cfg, s0.w);
@@ -270,7 +408,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
                             const float4 Aq = __ldg(L0 + l * kLinkStride + 2), Bq = __ldg(L1 + l * kLinkStride + 2);
                             const Q4 qa = {Aq.x, Aq.y, Aq.z, Aq.w}, qb = {Bq.x, Bq.y, Bq.z, Bq.w};
                             const V3 pl = qrot_inv(qa, (x - xyz(A0)) + r);   // contact in link coords
-                            vl = ((xyz(B0) - xyz(A0)) + (qrot(qb, pl) - qrot(qa, pl))) * (1.0f / h);
+                            vl = ((xyz(B0) - xyz(A0)) + (qrot(qb, pl) - qrot(qa, pl))) * inv_h;
                         }
                         cr_[k] = r; cn_[k] = n; cc_[k] = vl - n * b;
                     }
@@ -281,10 +419,10 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
                 if (nc > 0) {
                     const float inv_nc = 1.0f / (float)nc;
                     for (int it = 0; it < iters; ++it) {
-                        V3 F = mk(0, 0, 0), T = mk(0, 0, 0);
+                        float acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
                         for (int k = 0; k < CPL; ++k) {
-                            if (g + k * G < nc) {
+                            if (G.tid + k * TPE < nc) {
                                 const V3 n = cn_[k];
                                 const V3 u = vv + cross(ww, cr_[k]) - cc_[k];
                                 const float un = dot(u, n);
@@ -296,15 +434,15 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
                                 if (tn2 > lim * lim) lt = lt * (lim * rsqrtf(tn2));
                                 const V3 lp = n * ln + lt;
                                 lam_[k] = lam_[k] + (lp - lam_[k]) * inv_nc;
-                                F = F + lam_[k];
-                                T = T + cross(cr_[k], lam_[k]);
+                                const V3 tq = cross(cr_[k], lam_[k]);
+                                acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
+                                acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                             }
                         }
-                        F.x = group_sum<G>(F.x, gmask); F.y = group_sum<G>(F.y, gmask);
-                        F.z = group_sum<G>(F.z, gmask); T.x = group_sum<G>(T.x, gmask);
-                        T.y = group_sum<G>(T.y, gmask); T.z = group_sum<G>(T.z, gmask);
-                        vv = v_pred + F * inv_m;
-                        ww = w_pred + smul(W, T);
+                        group_sum6<TPE>(acc, G, S.red, parity);
+                        parity ^= 1;
+                        vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
+                        ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
                     }
                     w_citers += (unsigned long long)nc * iters;
                     w_iters += iters;
@@ -322,31 +460,32 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
                     q = qnorm(qmul({cs, w.x * kq, w.y * kq, w.z * kq}, q));
                 }
                 // sensor pads: force on the pad by the object is -lambda / h,
-                // summed per pad in contact order by the lane that owns the pad
+                // summed over the contacts of the pad's link in contact order
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
-                    const int ci = g + k * G;
+                    const int ci = G.tid + k * TPE;
                     if (ci < nc) {
-                        float4 s0 = stage[grp][ci][0];
+                        float4 s0 = S.stage[2 * ci];
                         s0.x = lam_[k].x; s0.y = lam_[k].y; s0.z = lam_[k].z;
-                        stage[grp][ci][0] = s0;
+                        S.stage[2 * ci] = s0;
                     }
                 }
-                __syncwarp(gmask);
-                const float inv_h = 1.0f / h;
-                for (int p = g; p < P; p += G) {
+                G.sync();
+                for (int p = G.tid; p < P; p += TPE) {
+                    const int l = __ldg(sc.pad_link + p);
                     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-                    for (int ci = 0; ci < nc; ++ci) {
-                        const float4 s1 = stage[grp][ci][1];
+                    const int e = S.lend[l];
+                    for (int ci = S.lbeg[l]; ci < e; ++ci) {
+                        const float4 s1 = S.stage[2 * ci + 1];
                         if (((__float_as_int(s1.w) >> 8) & 0xff) != p) continue;
-                        const float4 s0 = stage[grp][ci][0];
+                        const float4 s0 = S.stage[2 * ci];
                         fx -= s0.x * inv_h; fy -= s0.y * inv_h; fz -= s0.z * inv_h;
                     }
-                    padacc[grp][3 * p + 0] += fx;
-                    padacc[grp][3 * p + 1] += fy;
-                    padacc[grp][3 * p + 2] += fz;
+                    S.padacc[3 * p + 0] += fx;
+                    S.padacc[3 * p + 1] += fy;
+                    S.padacc[3 * p + 2] += fz;
                 }
-                __syncwarp(gmask);
+                G.sync();
             }
             if (!all_finite(x, q, v, w)) st |= IH_ENV_NONFINITE;
             else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
@@ -354,18 +493,18 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
         // forces of the last frame, averaged over its substeps
         const float inv_ns = 1.0f / (float)ns;
         float *fo = a.forces + (size_t)env * P * 3;
-        __syncwarp(gmask);
-        for (int k = g; k < 3 * P; k += G) fo[k] = padacc[grp][k] * inv_ns;
-        if (g == 0) {
+        G.sync();
+        for (int k = G.tid; k < 3 * P; k += TPE) fo[k] = S.padacc[k] * inv_ns;
+        if (G.tid == 0) {
             a.pose[2 * env] = make_float4(x.x, x.y, x.z, 0.0f);
             a.pose[2 * env + 1] = make_float4(q.w, q.x, q.y, q.z);
             a.vel[2 * env] = make_float4(v.x, v.y, v.z, 0.0f);
             a.vel[2 * env + 1] = make_float4(w.x, w.y, w.z, 0.0f);
             a.status[env] = st;
         }
-        __syncwarp(gmask);
+        G.sync();
     }
-    if (g == 0 && a.work) {
+    if (G.tid == 0 && a.work) {
         atomicAdd(a.work + 0, w_pairs);
         atomicAdd(a.work + 1, w_contacts);
         atomicAdd(a.work + 2, w_citers);
@@ -374,11 +513,20 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a) {
     }
 }
 
-template <int G, int CPL>
-cudaError_t launch_t(const StepArgs &a, int grid, cudaStream_t s) {
-    step_kernel<G, CPL><<<grid, kBlock, 0, s>>>(a);
+template <int TPE, int CPL>
+cudaError_t launch_t(const StepArgs &a, int grid, int s_max, cudaStream_t s) {
+    const size_t bytes = block_smem_bytes() + (size_t)Group<TPE>::GPB *
+                                                  group_smem_bytes(s_max, TPE * CPL, Group<TPE>::W);
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<TPE, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+    }
+    step_kernel<TPE, CPL><<<grid, kBlock, bytes, s>>>(a, s_max);
     return cudaGetLastError();
 }
+
+#define IH_STEP_VARIANTS(X) X(16, 8) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 1) X(128, 2)
 
 }  // namespace
 
@@ -386,22 +534,30 @@ int step_variant_max_contacts(const StepVariant &v) { return v.group * v.cpl; }
 
 bool step_variant_supported(const StepVariant &v) {
     if (v.block != kBlock) return false;
-    switch (v.group * 100 + v.cpl) {
-        case 3202: case 3204: case 3208: case 1604: case 1608: case 808: return true;
-        default: return false;
-    }
+#define IH_SUP(T, C) if (v.group == T && v.cpl == C) return true;
+    IH_STEP_VARIANTS(IH_SUP)
+#undef IH_SUP
+    return false;
 }
 
-cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, cudaStream_t s) {
-    switch (v.group * 100 + v.cpl) {
-        case 3202: return launch_t<32, 2>(a, grid, s);
-        case 3204: return launch_t<32, 4>(a, grid, s);
-        case 3208: return launch_t<32, 8>(a, grid, s);
-        case 1604: return launch_t<16, 4>(a, grid, s);
-        case 1608: return launch_t<16, 8>(a, grid, s);
-        case 808: return launch_t<8, 8>(a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
+int step_variant_list(StepVariant *out, int cap) {
+    int n = 0;
+#define IH_LIST(T, C) if (n < cap) out[n] = StepVariant{T, C, kBlock}; ++n;
+    IH_STEP_VARIANTS(IH_LIST)
+#undef IH_LIST
+    return n;
+}
+
+size_t step_smem_bytes(const StepVariant &v, int s_max) {
+    const int gpb = kBlock / v.group, w = v.group >= 32 ? v.group / 32 : 1;
+    return block_smem_bytes() + (size_t)gpb * group_smem_bytes(s_max, v.group * v.cpl, w);
+}
+
+cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s) {
+#define IH_LAUNCH(T, C) if (v.group == T && v.cpl == C) return launch_t<T, C>(a, grid, s_max, s);
+    IH_STEP_VARIANTS(IH_LAUNCH)
+#undef IH_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace ih

@@ -51,7 +51,8 @@ class IHOptConfig(C.Structure):
 _lib = None
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "sim_sample_initial",
            "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
-           "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error"]
+           "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
+           "sim_set_variant", "sim_step_variants"]
 
 
 def lib() -> C.CDLL:
@@ -77,6 +78,9 @@ def lib() -> C.CDLL:
             "optimizer_update": [P, P, U32, P, P],
             "sim_work_counters": [P, P, I],
             "sim_sync": [P],
+            "sim_autotune": [P, I, I, P, P],
+            "sim_set_variant": [P, I, I],
+            "sim_step_variants": [P, I],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -220,6 +224,23 @@ class Sim:
 
     def sim_sync(self):
         self._call("sim_sync")
+
+    def sim_autotune(self, frame0: int, n_frames: int):
+        chosen = (C.c_int32 * 2)()
+        ms = (C.c_float * 16)(*([float("nan")] * 16))
+        self._call("sim_autotune", frame0, n_frames, chosen, ms)
+        variants = step_variants()
+        return (chosen[0], chosen[1]), {v: ms[k] for k, v in enumerate(variants) if k < 16}
+
+    def sim_set_variant(self, threads_per_env: int, contacts_per_thread: int):
+        self._call("sim_set_variant", threads_per_env, contacts_per_thread)
+
+
+def step_variants():
+    """Supported step-kernel shapes (threads per env, contacts per thread)."""
+    out = (C.c_int32 * 64)()
+    n = lib().sim_step_variants(out, 32)
+    return [(out[2 * k], out[2 * k + 1]) for k in range(n)]
 
 
 def make_sim(workload, n_envs: int | None = None, max_frames: int | None = None, seed: int | None = None) -> Sim:

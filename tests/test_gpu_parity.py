@@ -204,3 +204,38 @@ def test_single_environment_and_ragged_batches():
         sim.sim_step(0, 3)
         rep = compare_frame(wl, sim, 3)
         assert_report(rep, min_ok_frac=0.0)
+
+
+@pytest.mark.parametrize("variant", [(16, 8), (32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2)])
+def test_every_step_shape_matches_oracle(variant):
+    """Each threads-per-environment shape of the step kernel gives the oracle's frame."""
+    from paper_2002_12160_gb300 import inhand
+    assert variant in inhand.step_variants()
+    wl = W.make_workload("tracking_cyl64", n_envs=37, frames=8)
+    sim = start(wl, n=37, frames=8)
+    sim.sim_set_variant(*variant)
+    sim.sim_step(0, 5)
+    rep = compare_frame(wl, sim, 5)
+    assert_report(rep)
+    if rep["ok"].all():
+        assert rep["work"]["contacts"] == rep["contacts_or"]
+
+
+def test_autotune_restores_the_state_and_picks_a_shape():
+    from paper_2002_12160_gb300 import inhand
+    wl = W.make_workload("tracking_cyl64", n_envs=300, frames=8)
+    sim = start(wl, n=300, frames=8)
+    sim.sim_step(0, 2)
+    before = [t.clone() for t in sim.sim_get_state()]
+    f_before, _ = sim.sim_read_sensors()
+    w_before = sim.sim_work_counters()
+    chosen, ms = sim.sim_autotune(2, 2)
+    after = sim.sim_get_state()
+    for a, b in zip(before, after):
+        assert torch.equal(a, b)
+    assert torch.equal(f_before, sim.sim_read_sensors()[0])
+    assert sim.sim_work_counters() == w_before
+    assert chosen in inhand.step_variants()
+    assert all(np.isfinite(v) for v in ms.values())
+    rep = compare_frame(wl, sim, 2)
+    assert_report(rep)

@@ -19,7 +19,7 @@ def libpath():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "inhand.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:ih_status|const char \*)\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:ih_status|int32_t|const char \*)\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declares_the_boundary():
