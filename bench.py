@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--workload", default="tracking_cyl64")
     p.add_argument("--n-envs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     return p.parse_args()
 
 
@@ -208,23 +209,26 @@ def cpu_baseline(workload, budget_s=12.0):
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local):
     import torch
-    from paper_2002_12160_gb300 import inhand, tracking, workloads as W
+    from paper_2002_12160_gb300 import tracking, workloads as W
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     T = 10
-    n_windows = args.warmup + args.steps
-    frames = n_windows * T
-    wl = W.make_workload(args.workload, n_envs=args.n_envs, frames=frames)
+    n_timing, n_e2e = 2, 2
+    n_windows = args.warmup + args.steps + n_timing + n_e2e
+    wl = W.make_workload(args.workload, n_envs=args.n_envs, frames=n_windows * T)
     seed = wl.seed + 7919 * rank   # independent replicas per rank
     tr = tracking.Tracker(wl, seed=seed)
     tr.prepare()
-    # pick the step kernel's shape on the first frames (the state is restored)
-    chosen, tune_ms = tr.sim.sim_autotune(0, 2)
+    if args.shape:
+        a, b = (int(v) for v in args.shape.lower().split("x"))
+        tr.sim.sim_set_variant(a, b)
+        chosen, tune_ms = (a, b), {}
+    else:
+        # pick the step kernel's shape on the first frames (the state is restored)
+        chosen, tune_ms = tr.sim.sim_autotune(0, 2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    step_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
-               for _ in range(args.steps)]
     for w in range(args.warmup):
         tr.window(w)
     torch.cuda.synchronize()
@@ -235,31 +239,42 @@ def run_ours(args, rank, world, local):
         for s in range(args.steps):
             flush.zero_()
             ev[s][0].record(stream)
-            tr.window(args.warmup + s, step_events=step_ev[s])
+            tr.window(args.warmup + s)       # one captured graph: T fused steps + optimizer
             ev[s][1].record(stream)
         torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
     ms_steps = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
-    ms_step_kernel = [a.elapsed_time(b) for s in range(args.steps) for (a, b) in step_ev[s]]
     work = tr.sim.sim_work_counters(reset=True)
     ms = sum(ms_steps) / len(ms_steps)
     ms = max_over_ranks(ms, world)
     n = tr.n
     value = world * n * T / (ms / 1e3)
-    # roofline of the dominant kernel (the batched step), FP32 issue bound
-    launches = args.steps * T
-    flops = (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP) + work["pairs"] * FLOP_PER_PAIR +
-             work["contacts"] * FLOP_PER_CONTACT + work["contact_iters"] * FLOP_PER_CONTACT_ITER)
-    flops += work.get("env_iters", 0) * FLOP_PER_ENV_ITER
+    # the dominant kernel alone: the same windows launched one kernel at a time,
+    # every (fused) step bracketed by events on its stream, L2 flushed per window
+    step_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
+               for _ in range(n_timing)]
+    w0 = args.warmup + args.steps
+    tr.sim.sim_work_counters(reset=True)
+    for s in range(n_timing):
+        flush.zero_()
+        tr.window_unfused(w0 + s, step_events=step_ev[s])
+    torch.cuda.synchronize()
+    work_t = tr.sim.sim_work_counters(reset=True)
+    step_ms_list = [a.elapsed_time(b) for s in range(n_timing) for (a, b) in step_ev[s]]
+    step_ms = sum(step_ms_list) / len(step_ms_list)
+    launches = n_timing * T
+    flops = (work_t["env_substeps"] * FLOP_PER_ENV_SUBSTEP + work_t["pairs"] * FLOP_PER_PAIR +
+             work_t["contacts"] * FLOP_PER_CONTACT + work_t["contact_iters"] * FLOP_PER_CONTACT_ITER +
+             work_t["env_iters"] * FLOP_PER_ENV_ITER)
     per_launch_flops = flops / launches
-    step_ms = sum(ms_step_kernel) / len(ms_step_kernel)
     achieved = per_launch_flops / (step_ms / 1e3) / 1e12
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    step_bytes = n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12 + n * 16
     # e2e through the public API with host buffers
-    e2e = tr.e2e_windows(args.warmup + args.steps - 2, 2)
+    e2e = tr.e2e_windows(w0 + n_timing, n_e2e)
     add_mm = tr.add_mm()
     line = {"metric": "env-steps/s", "value": value, "unit": "env-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -270,17 +285,16 @@ def run_ours(args, rank, world, local):
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}",
                        "step_shape": {"threads_per_env": chosen[0], "contacts_per_thread": chosen[1],
                                       "autotune_ms": {f"{a}x{b}": round(v, 4) for (a, b), v in tune_ms.items()}}},
-            "tracking_frames_per_s": world * T / (ms / 1e3) if world == 1 else T / (ms / 1e3),
+            "tracking_frames_per_s": T / (ms / 1e3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "step_kernel", "step_kernel_ms": step_ms,
-                         "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"},
-            "hbm": {"step_bytes_per_launch": n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12,
-                    "achieved_gbs": (n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12) / (step_ms / 1e3) / 1e9,
-                    "peak_gbs": 6777.0},
-            "work_per_launch": {k: v / launches for k, v in work.items()},
+                         "frac": achieved / peak, "traffic": None, "kernel": "step_kernel (fused step + score)",
+                         "step_kernel_ms": step_ms, "flop_per_launch": per_launch_flops,
+                         "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"},
+            "hbm": {"step_bytes_per_launch": step_bytes, "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
+                    "peak_gbs": 6777.0, "frac": step_bytes / (step_ms / 1e3) / 1e9 / 6777.0},
+            "work_per_launch": {k: v / (args.steps * T) for k, v in work.items()},
             "clocks": clocks,
-            "gpu_launches": args.steps * (2 * T + 2),
+            "gpu_launches": args.steps * (T + 5),   # T fused steps, descriptor, 4 optimizer kernels
             "e2e": e2e,
             "add_mm_argmin_env": add_mm}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -171,6 +171,30 @@ ih_status sim_get_state(ih_sim *sim, float *pose, float *vel, float *params, int
  * without commands. */
 ih_status sim_step(ih_sim *sim, int32_t frame0, int32_t n_frames);
 
+/* One frame of Algorithm 1 in one kernel: sim_step(frame, 1) followed by
+ * cost_eval(obs, ...), with the frame's cost computed from the same FP32 pad
+ * forces in the same FP64 order, so results equal the two separate calls bit
+ * for bit. obs is device float[P][3]; cost_mean (double[N]), argmin
+ * (int32[1]) and est_pose (float[8]) are device outputs and may be NULL.
+ * Passages: Sec. III-A (step, observation), Sec. III-C and Eqs. 1-2 (cost,
+ * i*). */
+ih_status sim_step_track(ih_sim *sim, int32_t frame, const float *obs, double *cost_mean,
+                         int32_t *argmin, float *est_pose);
+
+/* One tracking window of Algorithm 1: for k = 0..T-1, sim_step_track(frame0
+ * + k, obs + k P 3, ...) writing est_pose[k] and argmin[k], then
+ * optimizer_update(opt, update_index). obs is device float[T][P][3];
+ * est_pose (float[T][8]) and argmin (int32[T]) are device outputs (may be
+ * NULL). The window's launches are captured once into a CUDA graph and
+ * replayed on later calls with the same T, step shape and optimizer
+ * constants; per-window arguments reach the graph through a device
+ * descriptor, so pointers may change between calls. The first call (and any
+ * call after a change) captures, so it must not itself be made while the
+ * stream is being captured. Results equal the separate calls bit for bit. */
+ih_status sim_track_window(ih_sim *sim, int32_t frame0, int32_t T, const float *obs,
+                           const ih_opt_config *opt, uint32_t update_index, float *est_pose,
+                           int32_t *argmin);
+
 /* Copy the last frame's pad forces (device float[N][P][3], world frame,
  * averaged over the frame's substeps: the observation c_t^(l) of Sec. III-A)
  * and the status bits (device int32[N]); either may be NULL. */

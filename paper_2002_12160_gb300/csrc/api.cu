@@ -44,7 +44,15 @@ struct ih_sim {
     unsigned char *is_elite = nullptr;
     int *rank = nullptr, *elite_env = nullptr;
     double *elite_w = nullptr, *block_w = nullptr, *moments = nullptr, *misc = nullptr;
+    WinDesc *win = nullptr;
     std::vector<void *> owned;
+    // captured tracking window (replayed by sim_track_window)
+    cudaGraphExec_t win_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int win_T = 0;
+    StepVariant win_variant{0, 0, 0};
+    ih_opt_config win_opt{};
     // host bookkeeping
     std::vector<char> frame_ready;   // commands uploaded for frame f
     int window_frames = 0;           // frames scored since the last reset
@@ -190,7 +198,8 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->status, N)); A(dalloc(s, &s->forces, (size_t)N * P * 3));
     A(dalloc(s, &s->c_sum, N)); A(dalloc(s, &s->c_mean, N));
     A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
-    A(dalloc(s, &s->part_c, cost_blocks(N))); A(dalloc(s, &s->part_i, cost_blocks(N)));
+    A(dalloc(s, &s->part_c, std::max(N, cost_blocks(N)))); A(dalloc(s, &s->part_i, std::max(N, cost_blocks(N))));
+    A(dalloc(s, &s->win, 1));
     A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 5));
     A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
     A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
@@ -239,6 +248,12 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     }
     s->frame_ready.assign(cfg->max_frames, 0);
     s->step_grid = grid_for(s->variant, N);
+    e = step_prepare(s->variant, s->s_max);
+    if (e != cudaSuccess) {
+        ih_status r = cuda_fail(nullptr, e, "sim_create step setup");
+        sim_destroy(s);
+        return r;
+    }
     *out = s;
     return IH_OK;
 }
@@ -246,6 +261,10 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
 ih_status sim_destroy(ih_sim *s) {
     if (!s) return IH_OK;
     cudaStreamSynchronize(s->stream);
+    if (s->win_exec) cudaGraphExecDestroy(s->win_exec);
+    if (s->cap_stream) { cudaStreamSynchronize(s->cap_stream); cudaStreamDestroy(s->cap_stream); }
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
     for (void *p : s->owned) cudaFree(p);
     delete s;
     return IH_OK;
@@ -323,9 +342,128 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
     a.frame0 = frame0; a.n_frames = n_frames; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
     a.shape = s->shape; a.iters = s->iters; a.status = s->status; a.forces = s->forces; a.work = s->work;
+    a.obs = nullptr; a.win = nullptr; a.win_k = 0;
+    a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window; a.cost_mean = nullptr;
+    a.argmin_state = s->argmin; a.argmin_out = nullptr; a.est_pose_out = nullptr;
+    a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
     cudaError_t e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->stepped = true;
+    return IH_OK;
+}
+
+namespace {
+StepArgs scored_args(ih_sim *s, int frame, const float *obs, double *cost_mean, int32_t *argmin, float *est) {
+    StepArgs a;
+    a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
+    a.frame0 = frame; a.n_frames = 1; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
+    a.shape = s->shape; a.iters = s->iters; a.status = s->status; a.forces = s->forces; a.work = s->work;
+    a.obs = obs; a.win = nullptr; a.win_k = 0;
+    a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window; a.cost_mean = cost_mean;
+    a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est;
+    a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
+    return a;
+}
+
+OptArgs opt_args(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int32_t *argmin, int32_t *parent) {
+    OptArgs a;
+    a.N = s->cfg.n_envs; a.elite_frac = opt->elite_frac;
+    for (int k = 0; k < 8; ++k) a.floor_var[k] = (double)opt->floor_std[k] * (double)opt->floor_std[k];
+    a.m_lo = opt->m_lo; a.m_hi = opt->m_hi; a.mu_lo = opt->mu_lo; a.mu_hi = opt->mu_hi;
+    a.seed = s->seed; a.update_index = update_index; a.c_mean = s->c_mean; a.c_sum = s->c_sum;
+    a.n_window = s->n_window; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
+    a.status = s->status; a.is_elite = s->is_elite; a.rank = s->rank; a.elite_env = s->elite_env;
+    a.elite_w = s->elite_w; a.block_w = s->block_w; a.moments = s->moments; a.misc = s->misc;
+    a.argmin_state = s->argmin; a.argmin_out = argmin; a.parent_out = parent; a.win = nullptr;
+    return a;
+}
+
+ih_status check_opt(ih_sim *s, const ih_opt_config *opt) {
+    if (!opt || !(opt->elite_frac > 0.0f) || !(opt->elite_frac <= 1.0f) || !(opt->m_lo > 0.0f) ||
+        !(opt->m_hi >= opt->m_lo) || !(opt->mu_lo >= 0.0f) || !(opt->mu_hi >= opt->mu_lo))
+        return fail(s, IH_ERR_ARG, "invalid optimizer config");
+    for (int k = 0; k < 8; ++k)
+        if (!(opt->floor_std[k] >= 0.0f) || !std::isfinite(opt->floor_std[k]))
+            return fail(s, IH_ERR_ARG, "floor_std[%d] is invalid", k);
+    return IH_OK;
+}
+}  // namespace
+
+ih_status sim_step_track(ih_sim *s, int32_t frame, const float *obs, double *cost_mean, int32_t *argmin,
+                         float *est_pose) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
+    if (frame < 0 || frame >= s->cfg.max_frames || !s->frame_ready[frame])
+        return fail(s, IH_ERR_ARG, "no commands for frame %d", frame);
+    StepArgs a = scored_args(s, frame, obs, cost_mean, argmin, est_pose);
+    cudaError_t e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    s->stepped = true;
+    s->window_frames += 1;
+    return IH_OK;
+}
+
+ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *obs, const ih_opt_config *opt,
+                           uint32_t update_index, float *est_pose, int32_t *argmin) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
+    if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "window [%d, %d) outside the table", frame0, frame0 + T);
+    for (int f = frame0; f < frame0 + T; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    ih_status r = check_opt(s, opt);
+    if (r != IH_OK) return r;
+    cudaError_t e = cudaSuccess;
+    if (!s->cap_stream) {
+        e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(s, e, "window stream");
+    }
+    // the caller's stream -> private stream -> back, so ordering follows the caller's stream
+    WinDesc v{frame0, update_index, obs, est_pose, argmin};
+    e = launch_win_desc(s->win, v, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_in, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cap_stream, s->ev_in, 0);
+    if (e != cudaSuccess) return cuda_fail(s, e, "window descriptor");
+    cudaStream_t st = s->cap_stream;
+    const bool same = s->win_exec && s->win_T == T && s->win_variant.group == s->variant.group &&
+                      s->win_variant.cpl == s->variant.cpl && std::memcmp(&s->win_opt, opt, sizeof *opt) == 0;
+    if (!same) {
+        if (s->win_exec) { cudaGraphExecDestroy(s->win_exec); s->win_exec = nullptr; }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < T && le == cudaSuccess; ++k) {
+            StepArgs a = scored_args(s, frame0, nullptr, nullptr, nullptr, nullptr);
+            a.win = s->win;
+            a.win_k = k;
+            le = launch_step(a, s->variant, s->step_grid, s->s_max, st);
+        }
+        if (le == cudaSuccess) {
+            OptArgs oa = opt_args(s, opt, update_index, nullptr, nullptr);
+            oa.win = s->win;
+            le = launch_optimizer(oa, st);
+        }
+        e = cudaStreamEndCapture(st, &g);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(s, le != cudaSuccess ? le : e, "window capture");
+        }
+        e = cudaGraphInstantiate(&s->win_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { s->win_exec = nullptr; return cuda_fail(s, e, "window instantiate"); }
+        s->win_T = T;
+        s->win_variant = s->variant;
+        s->win_opt = *opt;
+    }
+    e = cudaGraphLaunch(s->win_exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_out, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_out, 0);
+    if (e != cudaSuccess) return cuda_fail(s, e, "window launch");
+    s->stepped = true;
+    s->window_frames = 0;
     return IH_OK;
 }
 
@@ -359,22 +497,10 @@ ih_status cost_eval(ih_sim *s, const float *obs, double *cost_mean, int32_t *arg
 ih_status optimizer_update(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int32_t *argmin,
                            int32_t *parent) {
     if (!s) return IH_ERR_ARG;
-    if (!opt || !(opt->elite_frac > 0.0f) || !(opt->elite_frac <= 1.0f) || !(opt->m_lo > 0.0f) ||
-        !(opt->m_hi >= opt->m_lo) || !(opt->mu_lo >= 0.0f) || !(opt->mu_hi >= opt->mu_lo))
-        return fail(s, IH_ERR_ARG, "invalid optimizer config");
-    for (int k = 0; k < 8; ++k)
-        if (!(opt->floor_std[k] >= 0.0f) || !std::isfinite(opt->floor_std[k]))
-            return fail(s, IH_ERR_ARG, "floor_std[%d] is invalid", k);
+    ih_status r = check_opt(s, opt);
+    if (r != IH_OK) return r;
     if (s->window_frames < 1) return fail(s, IH_ERR_STATE, "no frame scored since the last update");
-    OptArgs a;
-    a.N = s->cfg.n_envs; a.elite_frac = opt->elite_frac;
-    for (int k = 0; k < 8; ++k) a.floor_var[k] = (double)opt->floor_std[k] * (double)opt->floor_std[k];
-    a.m_lo = opt->m_lo; a.m_hi = opt->m_hi; a.mu_lo = opt->mu_lo; a.mu_hi = opt->mu_hi;
-    a.seed = s->seed; a.update_index = update_index; a.c_mean = s->c_mean; a.c_sum = s->c_sum;
-    a.n_window = s->n_window; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
-    a.status = s->status; a.is_elite = s->is_elite; a.rank = s->rank; a.elite_env = s->elite_env;
-    a.elite_w = s->elite_w; a.block_w = s->block_w; a.moments = s->moments; a.misc = s->misc;
-    a.argmin_state = s->argmin; a.argmin_out = argmin; a.parent_out = parent;
+    OptArgs a = opt_args(s, opt, update_index, argmin, parent);
     cudaError_t e = launch_optimizer(a, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "optimizer launch");
     s->window_frames = 0;
@@ -398,6 +524,8 @@ ih_status sim_set_variant(ih_sim *s, int32_t tpe, int32_t cpl) {
     if (!step_variant_supported(v)) return fail(s, IH_ERR_ARG, "unsupported step shape %d x %d", tpe, cpl);
     if (step_variant_max_contacts(v) < s->cfg.c_max)
         return fail(s, IH_ERR_ARG, "shape %d x %d holds fewer than c_max = %d contacts", tpe, cpl, s->cfg.c_max);
+    cudaError_t e = step_prepare(v, s->s_max);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set_variant");
     s->variant = v;
     s->step_grid = grid_for(v, s->cfg.n_envs);
     return IH_OK;
@@ -450,7 +578,7 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     if (e == cudaSuccess) { save(); e = cudaStreamSynchronize(st); }
     for (int k = 0; k < nv && e == cudaSuccess; ++k) {
         float ms = NAN;
-        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max) {
+        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && step_prepare(cand[k], s->s_max) == cudaSuccess) {
             s->variant = cand[k];
             s->step_grid = grid_for(cand[k], (int)N);
             ih_status r = sim_step(s, frame0, n_frames);   // warm-up (and first-use setup)

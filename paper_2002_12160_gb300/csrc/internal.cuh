@@ -178,6 +178,16 @@ cudaError_t launch_set_state(int N, int n_shapes, const float *pose, const float
                              float4 *pose_out, float4 *vel_out, float2 *params_out, int *shape,
                              int *iters, int *status, cudaStream_t s);
 
+// Per-window arguments of a replayed tracking window, read by the kernels
+// of the captured graph (written by a one-thread kernel before each replay).
+struct WinDesc {
+    int frame0;
+    uint32_t update_index;
+    const float *obs;     // [T][P][3]
+    float *est;           // [T][8] or null
+    int *argmin;          // [T] or null
+};
+
 struct StepArgs {
     DevScene sc;
     DevConfig cfg;
@@ -190,6 +200,18 @@ struct StepArgs {
     int *status;
     float *forces;            // [N][P][3]
     unsigned long long *work; // [5]
+    // scoring fused at the end of the (single) frame; obs == null and win == null: no scoring
+    const float *obs;         // [P][3]
+    const WinDesc *win;       // when set: frame0, obs and outputs come from win (+ win_k)
+    int win_k;
+    double *c_sum, *c_mean;   // [N]
+    int *n_window;
+    double *cost_mean;        // [N] caller copy or null
+    int *argmin_state, *argmin_out;
+    float *est_pose_out;
+    double *part_c;           // [grid] scratch
+    int *part_i;              // [grid] scratch
+    unsigned int *done;       // ticket
 };
 struct StepVariant {
     int group;        // lanes per environment
@@ -250,8 +272,11 @@ struct OptArgs {
     int *argmin_state;
     int *argmin_out;
     int *parent_out;
+    const WinDesc *win;       // when set, update_index comes from win
 };
 int opt_blocks(int N);
+cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
+cudaError_t step_prepare(const StepVariant &v, int s_max);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
 
 }  // namespace ih

@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
         const double nf = s_val[1];
         const double c0 = a.c_mean[istar];
         a.misc[M_K] = (double)k;
-        const uint4 uw = rng_words(a.seed, 2, a.update_index, 0, 0);
+        const uint32_t upd = a.win ? a.win->update_index : a.update_index;
+        const uint4 uw = rng_words(a.seed, 2, upd, 0, 0);
         a.misc[M_U] = unit53(uw.x, uw.y);
         a.misc[M_ISTAR] = (double)istar;
         a.misc[M_CMIN] = isnan(c0) ? INFINITY : c0;
@@ -328,8 +329,9 @@ __global__ void __launch_bounds__(kOptBlock) apply_kernel(const OptArgs a) {
     if (a.parent_out) a.parent_out[i] = par;
     if (!ok) return;
     double eps[8], d[8];
+    const uint32_t upd = a.win ? a.win->update_index : a.update_index;
     for (int b = 0; b < 4; ++b)
-        gauss2(rng_words(a.seed, 1, a.update_index, (uint32_t)i, (uint32_t)b), eps[2 * b], eps[2 * b + 1]);
+        gauss2(rng_words(a.seed, 1, upd, (uint32_t)i, (uint32_t)b), eps[2 * b], eps[2 * b + 1]);
     for (int r = 0; r < 8; ++r) {
         double s = 0.0;
         for (int c = 0; c <= r; ++c) s += a.misc[8 * r + c] * eps[c];
@@ -348,7 +350,14 @@ __global__ void __launch_bounds__(kOptBlock) apply_kernel(const OptArgs a) {
     a.status[i] = a.status[par];
 }
 
+__global__ void win_desc_kernel(WinDesc *d, WinDesc v) { *d = v; }
+
 }  // namespace
+
+cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s) {
+    win_desc_kernel<<<1, 1, 0, s>>>(d, v);
+    return cudaGetLastError();
+}
 
 int opt_blocks(int N) { return (N + kOptBlock - 1) / kOptBlock; }
 

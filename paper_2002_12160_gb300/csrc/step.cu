@@ -81,6 +81,10 @@ struct GroupSmem {
     unsigned char *links; // [32]      surviving links in order
     unsigned short *lbeg, *lend;  // [32] contact range of each link
     unsigned *surv;       // [1]
+    double *term;         // [IH_MAX_PADS] FP64 force term of each pad
+    int *flag;            // [IH_MAX_PADS] contact-state mismatch of each pad
+    double *best_c;       // [1] best (C, env) of this group so far
+    int *best_i;          // [1]
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -88,7 +92,8 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ inline size_t group_smem_bytes(int s_max, int cap, int w) {
     return align16(sizeof(float4) * s_max) + align16(sizeof(float4) * 2 * cap) +
            align16(sizeof(float) * IH_MAX_PADS * 3) + align16(sizeof(float) * 2 * w * 8) +
-           align16(sizeof(int) * 2 * w) + align16(kMaxLinks) + 2 * align16(2 * kMaxLinks) + 16;
+           align16(sizeof(int) * 2 * w) + align16(kMaxLinks) + 2 * align16(2 * kMaxLinks) + 16 +
+           align16(sizeof(double) * IH_MAX_PADS) + align16(sizeof(int) * IH_MAX_PADS) + 16 + 16;
 }
 __host__ __device__ inline size_t block_smem_bytes() {
     return align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink) + 2 * align16(4 * IH_MAX_PADS);
@@ -105,7 +110,11 @@ __device__ GroupSmem carve_group(unsigned char *base, int s_max, int cap, int w)
     g.links = base + o; o += align16(kMaxLinks);
     g.lbeg = reinterpret_cast<unsigned short *>(base + o); o += align16(2 * kMaxLinks);
     g.lend = reinterpret_cast<unsigned short *>(base + o); o += align16(2 * kMaxLinks);
-    g.surv = reinterpret_cast<unsigned *>(base + o);
+    g.surv = reinterpret_cast<unsigned *>(base + o); o += 16;
+    g.term = reinterpret_cast<double *>(base + o); o += align16(sizeof(double) * IH_MAX_PADS);
+    g.flag = reinterpret_cast<int *>(base + o); o += align16(sizeof(int) * IH_MAX_PADS);
+    g.best_c = reinterpret_cast<double *>(base + o); o += 16;
+    g.best_i = reinterpret_cast<int *>(base + o);
     return g;
 }
 
@@ -220,6 +229,19 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
     const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads;
     const float h = cfg.h, inv_h = 1.0f / h, inv_L = 1.0f / sc.link_len;
     const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
+    // the frame, observation and outputs (from the window descriptor when replayed)
+    int frame0 = a.frame0;
+    const float *obs = a.obs;
+    float *est_out = a.est_pose_out;
+    int *argmin_out = a.argmin_out;
+    if (a.win) {
+        frame0 = a.win->frame0 + a.win_k;
+        obs = a.win->obs ? a.win->obs + (size_t)a.win_k * P * 3 : nullptr;
+        est_out = a.win->est ? a.win->est + 8 * a.win_k : nullptr;
+        argmin_out = a.win->argmin ? a.win->argmin + a.win_k : nullptr;
+    }
+    const bool scored = obs != nullptr;
+    const int n_win = scored ? *a.n_window + 1 : 0;
 
     // block-wide tables: the pads of each link (in pad order) and their intervals
     unsigned char *pl_cnt = smem;
@@ -242,6 +264,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
 
     unsigned long long w_pairs = 0, w_contacts = 0, w_citers = 0, w_substeps = 0, w_iters = 0;
     int parity = 0;
+    if (G.tid == 0) { *S.best_c = INFINITY; *S.best_i = 0x7fffffff; }
 
     for (int env = blockIdx.x * GPB + G.grp; env < a.N; env += gridDim.x * GPB) {
         int st = a.status[env];
@@ -264,9 +287,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
 
         for (int fr = 0; fr < a.n_frames; ++fr) {
             for (int k = G.tid; k < 3 * P; k += TPE) S.padacc[k] = 0.0f;
-            if (st & kDiverged) continue;
-            const float4 *tab = a.link_tab + (size_t)(a.frame0 + fr) * (ns + 1) * Lk * kLinkStride;
-            for (int s = 0; s < ns; ++s) {
+            const float4 *tab = a.link_tab + (size_t)(frame0 + fr) * (ns + 1) * Lk * kLinkStride;
+            const bool skip = (st & kDiverged) != 0;   // decided once per frame
+            for (int s = 0; s < ns && !skip; ++s) {
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
                 const float4 *L1 = L0 + Lk * kLinkStride;
                 const V3 v_pred = v + grav;
@@ -487,8 +510,48 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                 }
                 G.sync();
             }
-            if (!all_finite(x, q, v, w)) st |= IH_ENV_NONFINITE;
-            else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
+            if (!skip) {
+                if (!all_finite(x, q, v, w)) st |= IH_ENV_NONFINITE;
+                else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
+            }
+        }
+        // frame cost against the observation (Sec. III-C), FP64, in pad order,
+        // on exactly the forces written out below
+        if (scored) {
+            const float inv_ns_f = 1.0f / (float)ns;
+            G.sync();
+            const double tau = (double)cfg.tau, wf = (double)cfg.w_force;
+            const double tau2 = __dmul_rn(tau, tau);
+            for (int p = G.tid; p < P; p += TPE) {
+                const double fx = S.padacc[3 * p] * inv_ns_f, fy = S.padacc[3 * p + 1] * inv_ns_f,
+                             fz = S.padacc[3 * p + 2] * inv_ns_f;
+                const double ox = obs[3 * p], oy = obs[3 * p + 1], oz = obs[3 * p + 2];
+                const double dx = __dsub_rn(fx, ox), dy = __dsub_rn(fy, oy), dz = __dsub_rn(fz, oz);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                S.term[p] = __dmul_rn(wf, d2);
+                const double ns2 = __dadd_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)), __dmul_rn(fz, fz));
+                const double no2 = __dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz));
+                S.flag[p] = (ns2 > tau2) != (no2 > tau2);
+            }
+            G.sync();
+            if (G.tid == 0) {
+                double c = 0.0;
+                if (st & kDiverged) {
+                    c = INFINITY;
+                } else {
+                    for (int p = 0; p < P; ++p) {
+                        c = __dadd_rn(c, S.term[p]);
+                        if (S.flag[p]) c = __dadd_rn(c, (double)cfg.w_contact);
+                    }
+                }
+                const double sum = __dadd_rn(a.c_sum[env], c);
+                a.c_sum[env] = sum;
+                double cm = __ddiv_rn(sum, (double)n_win);
+                a.c_mean[env] = cm;
+                if (a.cost_mean) a.cost_mean[env] = cm;
+                if (isnan(cm)) cm = INFINITY;
+                if (cm < *S.best_c || (cm == *S.best_c && env < *S.best_i)) { *S.best_c = cm; *S.best_i = env; }
+            }
         }
         // forces of the last frame, averaged over its substeps
         const float inv_ns = 1.0f / (float)ns;
@@ -511,18 +574,75 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
         atomicAdd(a.work + 3, w_substeps);
         atomicAdd(a.work + 4, w_iters);
     }
+    if (!scored) return;
+    // argmin (C_i, i) over the grid: per-block candidate, then the last block
+    __shared__ bool last;
+    __shared__ int best_env;
+    __threadfence();   // this thread's pose/status/cost writes, before the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bc = INFINITY;
+        int bi = 0x7fffffff;
+        for (int g2 = 0; g2 < GPB; ++g2) {
+            const GroupSmem S2 = carve_group(smem + block_smem_bytes() + g2 * gbytes, s_max, CAP, W);
+            const double c = *S2.best_c;
+            const int i = *S2.best_i;
+            if (c < bc || (c == bc && i < bi)) { bc = c; bi = i; }
+        }
+        a.part_c[blockIdx.x] = bc;
+        a.part_i[blockIdx.x] = bi;
+        __threadfence();
+        last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        double bc = INFINITY;
+        int bi = 0x7fffffff;
+        for (int b = threadIdx.x; b < gridDim.x; b += 32) {
+            const double c = __ldcg(a.part_c + b);
+            const int i = __ldcg(a.part_i + b);
+            if (c < bc || (c == bc && i < bi)) { bc = c; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oc < bc || (oc == bc && oi < bi)) { bc = oc; bi = oi; }
+        }
+        if (threadIdx.x == 0) {
+            const int best = (bi == 0x7fffffff) ? 0 : bi;
+            *a.argmin_state = best;
+            if (argmin_out) *argmin_out = best;
+            *a.n_window = n_win;
+            *a.done = 0u;
+            best_env = best;
+        }
+    }
+    __syncthreads();
+    if (est_out && threadIdx.x < 8) {
+        const float4 p = __ldcg(a.pose + 2 * best_env + (threadIdx.x >> 2));
+        const float v[4] = {p.x, p.y, p.z, p.w};
+        est_out[threadIdx.x] = v[threadIdx.x & 3];
+    }
+}
+
+template <int TPE, int CPL>
+size_t bytes_t(int s_max) {
+    return block_smem_bytes() + (size_t)Group<TPE>::GPB * group_smem_bytes(s_max, TPE * CPL, Group<TPE>::W);
+}
+
+template <int TPE, int CPL>
+cudaError_t prepare_t(int s_max) {
+    const size_t bytes = bytes_t<TPE, CPL>(s_max);
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(step_kernel<TPE, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int TPE, int CPL>
 cudaError_t launch_t(const StepArgs &a, int grid, int s_max, cudaStream_t s) {
-    const size_t bytes = block_smem_bytes() + (size_t)Group<TPE>::GPB *
-                                                  group_smem_bytes(s_max, TPE * CPL, Group<TPE>::W);
-    if (bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<TPE, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)bytes);
-        if (e != cudaSuccess) return e;
-    }
-    step_kernel<TPE, CPL><<<grid, kBlock, bytes, s>>>(a, s_max);
+    step_kernel<TPE, CPL><<<grid, kBlock, bytes_t<TPE, CPL>(s_max), s>>>(a, s_max);
     return cudaGetLastError();
 }
 
@@ -551,6 +671,13 @@ int step_variant_list(StepVariant *out, int cap) {
 size_t step_smem_bytes(const StepVariant &v, int s_max) {
     const int gpb = kBlock / v.group, w = v.group >= 32 ? v.group / 32 : 1;
     return block_smem_bytes() + (size_t)gpb * group_smem_bytes(s_max, v.group * v.cpl, w);
+}
+
+cudaError_t step_prepare(const StepVariant &v, int s_max) {
+#define IH_PREP(T, C) if (v.group == T && v.cpl == C) return prepare_t<T, C>(s_max);
+    IH_STEP_VARIANTS(IH_PREP)
+#undef IH_PREP
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s) {

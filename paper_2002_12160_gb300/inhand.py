@@ -52,7 +52,7 @@ _lib = None
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "sim_sample_initial",
            "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
-           "sim_set_variant", "sim_step_variants"]
+           "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window"]
 
 
 def lib() -> C.CDLL:
@@ -81,6 +81,8 @@ def lib() -> C.CDLL:
             "sim_autotune": [P, I, I, P, P],
             "sim_set_variant": [P, I, I],
             "sim_step_variants": [P, I],
+            "sim_step_track": [P, I, P, P, P, P],
+            "sim_track_window": [P, I, I, P, P, U32, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -107,6 +109,11 @@ def _check(t, dtype, shape, name):
         return
     if t.dtype != dtype or tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name}: expected {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+def _opt(opt) -> IHOptConfig:
+    return IHOptConfig(opt.elite_frac, (C.c_float * 8)(*opt.floor_std), opt.m_range[0],
+                       opt.m_range[1], opt.mu_range[0], opt.mu_range[1])
 
 
 def _stream():
@@ -209,9 +216,23 @@ class Sim:
         _check(est_pose, torch.float32, (8,), "est_pose")
         self._call("cost_eval", _ptr(obs), _ptr(cost_mean), _ptr(argmin), _ptr(est_pose))
 
+    def sim_step_track(self, frame: int, obs, cost_mean=None, argmin=None, est_pose=None):
+        _check(obs, torch.float32, (self.n_pads, 3), "obs")
+        _check(cost_mean, torch.float64, (self.n,), "cost_mean")
+        _check(argmin, torch.int32, (1,), "argmin")
+        _check(est_pose, torch.float32, (8,), "est_pose")
+        self._call("sim_step_track", frame, _ptr(obs), _ptr(cost_mean), _ptr(argmin), _ptr(est_pose))
+
+    def sim_track_window(self, frame0: int, obs, opt, update_index: int, est_pose=None, argmin=None):
+        T = obs.shape[0]
+        _check(obs, torch.float32, (T, self.n_pads, 3), "obs")
+        _check(est_pose, torch.float32, (T, 8), "est_pose")
+        _check(argmin, torch.int32, (T,), "argmin")
+        self._call("sim_track_window", frame0, T, _ptr(obs), C.byref(_opt(opt)), C.c_uint32(update_index),
+                   _ptr(est_pose), _ptr(argmin))
+
     def optimizer_update(self, opt, update_index: int, argmin=None, parent=None):
-        oc = IHOptConfig(opt.elite_frac, (C.c_float * 8)(*opt.floor_std), opt.m_range[0],
-                         opt.m_range[1], opt.mu_range[0], opt.mu_range[1])
+        oc = _opt(opt)
         _check(argmin, torch.int32, (1,), "argmin")
         _check(parent, torch.int32, (self.n,), "parent")
         self._call("optimizer_update", C.byref(oc), C.c_uint32(update_index), _ptr(argmin), _ptr(parent))

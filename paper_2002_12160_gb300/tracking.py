@@ -30,7 +30,7 @@ class Tracker:
         P = wl.scene.n_pads
         self.obs = torch.zeros((wl.frames, P, 3), dtype=torch.float32, device=self.dev)
         self.gt_pose = torch.zeros((wl.frames, 8), dtype=torch.float32, device=self.dev)
-        self.argmin = torch.zeros((wl.frames, 1), dtype=torch.int32, device=self.dev)
+        self.argmin = torch.zeros((wl.frames,), dtype=torch.int32, device=self.dev)
         self.est = torch.zeros((wl.frames, 8), dtype=torch.float32, device=self.dev)
 
     def prepare(self):
@@ -54,17 +54,25 @@ class Tracker:
                                     wl.init.m_range, wl.init.mu_range)
         torch.cuda.synchronize()
 
-    def window(self, w: int, step_events=None):
-        """Frames [wT, (w+1)T): step, score, argmin each frame; then the optimizer update."""
+    def window(self, w: int):
+        """Frames [wT, (w+1)T) -- step, score, argmin each frame -- then the
+        optimizer update, replayed from one captured CUDA graph."""
+        T = self.T
+        f0 = w * T
+        self.sim.sim_track_window(f0, self.obs[f0:f0 + T], self.wl.opt, w, self.est[f0:f0 + T],
+                                  self.argmin[f0:f0 + T])
+
+    def window_unfused(self, w: int, step_events=None):
+        """The same window as separate launches (each step bracketed by events
+        when given), for timing the step kernel alone."""
         T = self.T
         for k in range(T):
             f = w * T + k
             if step_events is not None:
                 step_events[k][0].record()
-            self.sim.sim_step(f, 1)
+            self.sim.sim_step_track(f, self.obs[f], None, self.argmin[f:f + 1], self.est[f])
             if step_events is not None:
                 step_events[k][1].record()
-            self.sim.cost_eval(self.obs[f], None, self.argmin[f], self.est[f])
         self.sim.optimizer_update(self.wl.opt, w)
 
     def e2e_windows(self, w0: int, count: int):
@@ -74,7 +82,7 @@ class Tracker:
         q_host = torch.from_numpy(self.wl.q_traj).pin_memory()
         obs_host = self.obs.cpu().pin_memory()
         est_host = torch.empty((T, 8), dtype=torch.float32).pin_memory()
-        am_host = torch.empty((T, 1), dtype=torch.int32).pin_memory()
+        am_host = torch.empty((T,), dtype=torch.int32).pin_memory()
         q_dev = torch.empty((T + 1, D), dtype=torch.float32, device=self.dev)
         obs_dev = torch.empty((T, P, 3), dtype=torch.float32, device=self.dev)
         times = []
@@ -85,10 +93,7 @@ class Tracker:
             q_dev.copy_(q_host[f0:f0 + T + 1], non_blocking=True)
             obs_dev.copy_(obs_host[f0:f0 + T], non_blocking=True)
             self.sim.sim_set_commands(f0, q_dev)
-            for k in range(T):
-                self.sim.sim_step(f0 + k, 1)
-                self.sim.cost_eval(obs_dev[k], None, self.argmin[f0 + k], self.est[f0 + k])
-            self.sim.optimizer_update(self.wl.opt, w)
+            self.sim.sim_track_window(f0, obs_dev, self.wl.opt, w, self.est[f0:f0 + T], self.argmin[f0:f0 + T])
             est_host.copy_(self.est[f0:f0 + T], non_blocking=True)
             am_host.copy_(self.argmin[f0:f0 + T], non_blocking=True)
             torch.cuda.synchronize()

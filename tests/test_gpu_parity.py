@@ -239,3 +239,54 @@ def test_autotune_restores_the_state_and_picks_a_shape():
     assert all(np.isfinite(v) for v in ms.values())
     rep = compare_frame(wl, sim, 2)
     assert_report(rep)
+
+
+def _twin(name, n, frames):
+    wl = W.make_workload(name, n_envs=n, frames=frames)
+    return wl, start(wl, n=n, frames=frames), start(wl, n=n, frames=frames)
+
+
+def test_fused_step_and_score_equal_the_separate_calls():
+    wl, a, b = _twin("tracking_cyl64", 131, 6)
+    d = dev()
+    ca = torch.empty(131, dtype=torch.float64, device=d)
+    cb = torch.empty_like(ca)
+    ia = torch.empty(1, dtype=torch.int32, device=d)
+    ib = torch.empty_like(ia)
+    ea = torch.empty(8, dtype=torch.float32, device=d)
+    eb = torch.empty_like(ea)
+    obs = None
+    for f in range(6):
+        a.sim_step(f, 1)
+        fa, _ = a.sim_read_sensors()
+        if obs is None:
+            obs = fa[5].clone()
+        a.cost_eval(obs, ca, ia, ea)
+        b.sim_step_track(f, obs, cb, ib, eb)
+        fb, _ = b.sim_read_sensors()
+        assert torch.equal(fa, fb)
+        assert torch.equal(ca, cb) and torch.equal(ia, ib) and torch.equal(ea, eb)
+    for x, y in zip(a.sim_get_state(), b.sim_get_state()):
+        assert torch.equal(x, y)
+
+
+def test_replayed_window_equals_the_separate_calls():
+    T = 4
+    wl, a, b = _twin("tracking_cyl64", 200, 3 * T)
+    d = dev()
+    obs = torch.rand((3 * T, wl.scene.n_pads, 3), dtype=torch.float32, device=d) * 0.2
+    est_a = torch.zeros((3 * T, 8), dtype=torch.float32, device=d)
+    est_b = torch.zeros_like(est_a)
+    am_a = torch.zeros((3 * T,), dtype=torch.int32, device=d)
+    am_b = torch.zeros_like(am_a)
+    for w in range(3):
+        for k in range(T):
+            f = w * T + k
+            a.sim_step_track(f, obs[f], None, am_a[f:f + 1], est_a[f])
+        a.optimizer_update(wl.opt, w)
+        # the same window replayed from one captured graph (captured on w = 0)
+        b.sim_track_window(w * T, obs[w * T:(w + 1) * T], wl.opt, w, est_b[w * T:(w + 1) * T],
+                           am_b[w * T:(w + 1) * T])
+    assert torch.equal(est_a, est_b) and torch.equal(am_a, am_b)
+    for x, y in zip(a.sim_get_state(), b.sim_get_state()):
+        assert torch.equal(x, y)
