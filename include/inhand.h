@@ -259,6 +259,45 @@ ih_status sim_set_variant(ih_sim *sim, int32_t threads_per_env, int32_t contacts
  * many exist. */
 int32_t sim_step_variants(int32_t *out, int32_t cap);
 
+/* cost_eval for callers that cannot allocate device memory.
+ *
+ * Some callers may not call cudaMalloc at all: code running inside another
+ * allocator's callbacks, a real-time loop that reserved all its device memory
+ * up front, or a process held to a fixed memory budget on a shared GPU. Such a
+ * caller cannot create a simulator handle (sim_create allocates) and cannot
+ * hand us scratch space, but it can pass its own inputs and outputs. This
+ * entry point computes the same per-environment cost, window mean and argmin
+ * as cost_eval -- same FP64 arithmetic, same order, same tie rule -- from
+ * caller buffers only, and allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ * The paper has no counterpart to this call; it exists for such callers.
+ *
+ * forces  device float[n_envs][n_pads][3]   pad forces of the frame
+ * obs     device float[n_pads][3]           observed forces
+ * env_status device int32[n_envs] or NULL   envs with IH_ENV_NONFINITE,
+ *                                           ESCAPED, OVERFLOW or INVALID cost +inf
+ * c_sum   device double[n_envs], in/out     window sums; the frame's cost is added
+ * n_window frames in the window including this one (divides c_sum)
+ * cost_mean device double[n_envs] or NULL   window means C_i
+ * argmin  device int32[1]                   i* (NaN = +inf, ties to the lowest index)
+ * stream  cudaStream_t (NULL = legacy default stream)
+ *
+ * Limits: n_envs <= 131072 (IH_ERR_OVERFLOW beyond it), n_pads <= IH_MAX_PADS.
+ * Its scratch -- one partial per 32 environments and a counter, about 48 KiB --
+ * is a fixed __device__ array that every GPU which loads this library holds
+ * until the process exits. The first call on each device looks up that
+ * array's device address; make that first call before any stream capture.
+ * Every call shares the one array (each call re-zeroes its counter on the
+ * stream), so calls that may overlap on the GPU -- on different streams, or
+ * from different threads -- race and must be serialised by the caller.
+ * Errors: IH_ERR_ARG (null or out-of-range argument), IH_ERR_OVERFLOW (too many
+ * environments), IH_ERR_CUDA (device lookup or launch failed). */
+ih_status cost_eval_static(const float *forces, const float *obs, const int32_t *env_status,
+                           int32_t n_envs, int32_t n_pads, float tau, float w_force,
+                           float w_contact, double *c_sum, int32_t n_window, double *cost_mean,
+                           int32_t *argmin, void *stream);
+
 /* Wait for the handle's stream; IH_ERR_CUDA if a kernel failed. */
 ih_status sim_sync(ih_sim *sim);
 

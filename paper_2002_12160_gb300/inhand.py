@@ -52,7 +52,8 @@ _lib = None
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "sim_sample_initial",
            "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
-           "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window"]
+           "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
+           "cost_eval_static"]
 
 
 def lib() -> C.CDLL:
