@@ -34,8 +34,11 @@ sys.path.insert(0, ROOT)
 # work counters the step kernel reports (pairs tested after culling, contacts,
 # contact-iterations, env-substeps).
 FLOP_PER_ENV_SUBSTEP = 150     # gravity, rotation matrix, world inverse inertia,
-                               # link cull (21 links x 20), integration
-FLOP_PER_PAIR = 40             # sphere to world (15), capsule/box distance (25)
+                               # link cull, integration
+FLOP_PER_SPHERE = 15           # sphere centre to world, once per substep (counted
+                               # through the pair tests' spheres below)
+FLOP_PER_PAIR = 30             # sphere-capsule / sphere-box gap, normal, contact test
+FLOP_PER_CLUSTER_TEST = 25     # cluster centre to world (15) and its reach test (10)
 FLOP_PER_CONTACT = 95          # effective masses, bias, link velocity, pad sum
 FLOP_PER_CONTACT_ITER = 62     # relative velocity, normal/tangent update,
                                # cone clamp, relaxation, impulse/moment sums
@@ -264,7 +267,8 @@ def run_ours(args, rank, world, local):
     step_ms_list = [a.elapsed_time(b) for s in range(n_timing) for (a, b) in step_ev[s]]
     step_ms = sum(step_ms_list) / len(step_ms_list)
     launches = n_timing * T
-    flops = (work_t["env_substeps"] * FLOP_PER_ENV_SUBSTEP + work_t["pairs"] * FLOP_PER_PAIR +
+    flops = (work_t["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * len(wl.scene.shapes[0])) +
+             work_t["pairs"] * FLOP_PER_PAIR + work_t["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
              work_t["contacts"] * FLOP_PER_CONTACT + work_t["contact_iters"] * FLOP_PER_CONTACT_ITER +
              work_t["env_iters"] * FLOP_PER_ENV_ITER)
     per_launch_flops = flops / launches

@@ -232,16 +232,18 @@ ih_status cost_eval(ih_sim *sim, const float *obs, double *cost_mean, int32_t *a
 ih_status optimizer_update(ih_sim *sim, const ih_opt_config *opt, uint32_t update_index,
                            int32_t *argmin, int32_t *parent);
 
-/* Work done by sim_step since the last call with reset != 0: out[0] = pair
- * tests after culling, out[1] = contacts, out[2] = contact-iterations,
- * out[3] = env-substeps stepped, out[4] = solver iterations summed over
- * env-substeps with contacts (host uint64[5]; synchronises the stream). */
+/* Work done by the step kernel since the last call with reset != 0:
+ * out[0] = sphere-link tests after culling, out[1] = contacts, out[2] =
+ * contact-iterations, out[3] = env-substeps stepped, out[4] = solver
+ * iterations summed over env-substeps with contacts, out[5] = cluster-link
+ * culling tests (host uint64[6]; synchronises the stream). */
 ih_status sim_work_counters(ih_sim *sim, uint64_t *out, int32_t reset);
 
 /* Choose the step kernel's shape -- threads per environment (16, 32, 64 or
  * 128) and register-resident contacts per thread -- by timing every
  * supported shape whose capacity covers c_max on frames [frame0, frame0 +
- * n_frames) of the current state. The state, forces and work counters are
+ * n_frames) of the current state (one warm-up run, then the best of three).
+ * The state, forces and work counters are
  * restored after every trial, so the call leaves the simulation unchanged.
  * Results of different shapes agree up to FP32 summation order. chosen
  * (host int32[2], may be NULL) receives the shape; ms (host float[16], may be

@@ -30,6 +30,8 @@ struct ih_sim {
     float4 *spheres_raw = nullptr, *spheres = nullptr, *finger_root = nullptr;
     int *shape_first = nullptr, *shape_count = nullptr, *pad_link = nullptr;
     float *shape_jinv = nullptr, *shape_bound = nullptr, *pad_s0 = nullptr, *pad_s1 = nullptr;
+    int *cl_first = nullptr;
+    float4 *clusters = nullptr;
     float4 *link_tab = nullptr;
     float4 *pose = nullptr, *vel = nullptr;
     float2 *params = nullptr;
@@ -100,6 +102,7 @@ DevScene dev_scene(const ih_sim *s) {
     d.link_len = s->link_len; d.link_rad = s->link_rad;
     d.spheres = s->spheres; d.shape_first = s->shape_first; d.shape_count = s->shape_count;
     d.shape_jinv = s->shape_jinv; d.shape_bound = s->shape_bound; d.finger_root = s->finger_root;
+    d.cl_first = s->cl_first; d.clusters = s->clusters;
     d.pad_link = s->pad_link; d.pad_s0 = s->pad_s0; d.pad_s1 = s->pad_s1;
     return d;
 }
@@ -190,6 +193,13 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->spheres_raw, total)); A(dalloc(s, &s->spheres, total));
     A(dalloc(s, &s->shape_first, sc->n_shapes)); A(dalloc(s, &s->shape_count, sc->n_shapes));
     A(dalloc(s, &s->shape_jinv, 6 * sc->n_shapes)); A(dalloc(s, &s->shape_bound, sc->n_shapes));
+    std::vector<int> cl_first(sc->n_shapes);
+    int n_clusters = 0;
+    for (int k = 0; k < sc->n_shapes; ++k) {
+        cl_first[k] = n_clusters;
+        n_clusters += (sc->shape_count[k] + kCluster - 1) / kCluster;
+    }
+    A(dalloc(s, &s->cl_first, sc->n_shapes)); A(dalloc(s, &s->clusters, n_clusters));
     A(dalloc(s, &s->finger_root, F > 0 ? F : 1));
     A(dalloc(s, &s->pad_link, P)); A(dalloc(s, &s->pad_s0, P)); A(dalloc(s, &s->pad_s1, P));
     A(dalloc(s, &s->link_tab, (size_t)cfg->max_frames * (cfg->substeps + 1) * n_links * kLinkStride));
@@ -200,7 +210,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
     A(dalloc(s, &s->part_c, std::max(N, cost_blocks(N)))); A(dalloc(s, &s->part_i, std::max(N, cost_blocks(N))));
     A(dalloc(s, &s->win, 1));
-    A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 5));
+    A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 6));
     A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
     A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
     A(dalloc(s, &s->moments, (size_t)opt_blocks(N) * kMoments)); A(dalloc(s, &s->misc, 80));
@@ -221,6 +231,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemcpyAsync(s->spheres_raw, sph.data(), total * sizeof(float4), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->shape_first, sc->shape_first, sc->n_shapes * sizeof(int), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->shape_count, sc->shape_count, sc->n_shapes * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(s->cl_first, cl_first.data(), sc->n_shapes * sizeof(int), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->finger_root, roots.data(), roots.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->pad_link, sc->pad_link, P * sizeof(int), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->pad_s0, sc->pad_s0, P * sizeof(float), cudaMemcpyHostToDevice, st));
@@ -237,9 +248,9 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemsetAsync(s->n_window, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->argmin, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->done, 0, sizeof(unsigned int), st));
-    A(cudaMemsetAsync(s->work, 0, 5 * sizeof(unsigned long long), st));
+    A(cudaMemsetAsync(s->work, 0, 6 * sizeof(unsigned long long), st));
     A(launch_shape_setup(s->spheres_raw, s->spheres, s->shape_first, s->shape_count, sc->n_shapes,
-                         s->shape_jinv, s->shape_bound, st));
+                         s->shape_jinv, s->shape_bound, s->cl_first, s->clusters, st));
     A(cudaStreamSynchronize(st));   // host vectors above go out of scope
     if (e != cudaSuccess) {
         ih_status r = cuda_fail(nullptr, e, "sim_create upload");
@@ -509,12 +520,12 @@ ih_status optimizer_update(ih_sim *s, const ih_opt_config *opt, uint32_t update_
 
 ih_status sim_work_counters(ih_sim *s, uint64_t *out, int32_t reset) {
     if (!s || !out) return IH_ERR_ARG;
-    unsigned long long w[5];
+    unsigned long long w[6];
     cudaError_t e = cudaMemcpyAsync(w, s->work, sizeof w, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess && reset) e = cudaMemsetAsync(s->work, 0, sizeof w, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "work counters");
-    for (int k = 0; k < 5; ++k) out[k] = w[k];
+    for (int k = 0; k < 6; ++k) out[k] = w[k];
     return IH_OK;
 }
 
@@ -547,7 +558,7 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     const size_t N = s->cfg.n_envs, P = s->n_pads;
     // scratch copy of everything a step writes
     void *bp = nullptr, *bv = nullptr, *bs = nullptr, *bf = nullptr;
-    unsigned long long wsave[5];
+    unsigned long long wsave[6];
     cudaError_t e = cudaMalloc(&bp, N * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&bv, N * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&bs, N * sizeof(int));
@@ -583,13 +594,15 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
             s->step_grid = grid_for(cand[k], (int)N);
             ih_status r = sim_step(s, frame0, n_frames);   // warm-up (and first-use setup)
             restore();
-            if (r == IH_OK) {
+            for (int rep = 0; rep < 3 && r == IH_OK && e == cudaSuccess; ++rep) {
+                float t = NAN;
                 cudaEventRecord(e0, st);
                 r = sim_step(s, frame0, n_frames);
                 cudaEventRecord(e1, st);
                 restore();
                 e = cudaStreamSynchronize(st);
-                if (e == cudaSuccess && r == IH_OK) cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && r == IH_OK) cudaEventElapsedTime(&t, e0, e1);
+                if (!(ms <= t)) ms = t;   // best of three
             }
             if (r != IH_OK && e == cudaSuccess) e = cudaErrorLaunchFailure;
             if (ms < best_ms) { best_ms = ms; best = cand[k]; }

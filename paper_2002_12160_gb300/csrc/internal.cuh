@@ -11,6 +11,7 @@ namespace ih {
 
 constexpr int kDiverged = IH_ENV_NONFINITE | IH_ENV_ESCAPED | IH_ENV_OVERFLOW | IH_ENV_INVALID;
 constexpr int kLinkStride = 3;  // float4 per link pose: (a, 0), (axis, 0), (quat wxyz)
+constexpr int kCluster = 8;     // spheres per culling cluster (consecutive in the shape)
 
 // Scene as seen by the kernels (device pointers, fixed at create).
 struct DevScene {
@@ -22,6 +23,8 @@ struct DevScene {
     const int *shape_count;     // [n_shapes]
     const float *shape_jinv;    // [n_shapes][6] inverse unit inertia xx yy zz xy xz yz
     const float *shape_bound;   // [n_shapes] bounding radius about the centroid
+    const int *cl_first;        // [n_shapes] first cluster of each shape
+    const float4 *clusters;     // [total clusters] centre (centroid frame), enclosing radius
     const float4 *finger_root;  // [F] x y z yaw
     const int *pad_link;        // [P]
     const float *pad_s0, *pad_s1;
@@ -166,7 +169,7 @@ __device__ __forceinline__ void qlog_d(Q4d q, double out[3]) {
 // Declared here, defined in the kernel translation units.
 cudaError_t launch_shape_setup(const float4 *spheres_in, float4 *spheres_out, const int *first,
                                const int *count, int n_shapes, float *jinv, float *bound,
-                               cudaStream_t s);
+                               const int *cl_first, float4 *clusters, cudaStream_t s);
 cudaError_t launch_fk(const DevScene &sc, const float *q, int n_frames, int substeps,
                       float4 *link_tab_out, cudaStream_t s);
 cudaError_t launch_sample_initial(int N, float4 pose0, float4 quat0, float sigma_p, float sigma_r,
@@ -199,7 +202,7 @@ struct StepArgs {
     const int *shape, *iters;
     int *status;
     float *forces;            // [N][P][3]
-    unsigned long long *work; // [5]
+    unsigned long long *work; // [6]
     // scoring fused at the end of the (single) frame; obs == null and win == null: no scoring
     const float *obs;         // [P][3]
     const WinDesc *win;       // when set: frame0, obs and outputs come from win (+ win_k)

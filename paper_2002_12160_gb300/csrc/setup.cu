@@ -13,7 +13,7 @@ namespace {
 // equal solid balls about the centroid, its inverse, and the bounding radius
 // max_s |c_s| + r_s.
 __global__ void shape_setup_kernel(const float4 *in, float4 *out, const int *first, const int *count,
-                                   float *jinv, float *bound) {
+                                   float *jinv, float *bound, const int *cl_first, float4 *clusters) {
     __shared__ double red[7][256];
     const int sh = blockIdx.x, t = threadIdx.x;
     const int f = first[sh], S = count[sh];
@@ -63,7 +63,28 @@ __global__ void shape_setup_kernel(const float4 *in, float4 *out, const int *fir
         float *o = jinv + 6 * sh;
         o[0] = (float)(c00 / det); o[1] = (float)(c11 / det); o[2] = (float)(c22 / det);
         o[3] = (float)(c01 / det); o[4] = (float)(c02 / det); o[5] = (float)(c12 / det);
-        bound[sh] = (float)red[6][0];
+        // rounded outward so that culling with it stays conservative in FP32
+        bound[sh] = (float)(red[6][0] * (1.0 + 1e-6)) + 1e-7f;
+    }
+    // clusters of kCluster consecutive spheres: centre of their centres and the
+    // radius that encloses them, in the centroid frame
+    const int ncl = (S + kCluster - 1) / kCluster;
+    for (int k = t; k < ncl; k += blockDim.x) {
+        const int j0 = k * kCluster, j1 = min(S, j0 + kCluster);
+        double cx2 = 0, cy2 = 0, cz2 = 0;
+        for (int j = j0; j < j1; ++j) {
+            const float4 sp = in[f + j];
+            cx2 += sp.x - mx; cy2 += sp.y - my; cz2 += sp.z - mz;
+        }
+        cx2 /= (j1 - j0); cy2 /= (j1 - j0); cz2 /= (j1 - j0);
+        double rr = 0;
+        for (int j = j0; j < j1; ++j) {
+            const float4 sp = in[f + j];
+            const double dx = sp.x - mx - cx2, dy = sp.y - my - cy2, dz = sp.z - mz - cz2;
+            rr = fmax(rr, sqrt(dx * dx + dy * dy + dz * dz) + sp.w);
+        }
+        clusters[cl_first[sh] + k] =
+            make_float4((float)cx2, (float)cy2, (float)cz2, (float)(rr * (1.0 + 1e-6)) + 1e-7f);
     }
 }
 
@@ -169,8 +190,9 @@ __global__ void set_state_kernel(int N, int n_shapes, const float4 *pose_in, con
 
 cudaError_t launch_shape_setup(const float4 *spheres_in, float4 *spheres_out, const int *first,
                                const int *count, int n_shapes, float *jinv, float *bound,
-                               cudaStream_t s) {
-    shape_setup_kernel<<<n_shapes, 256, 0, s>>>(spheres_in, spheres_out, first, count, jinv, bound);
+                               const int *cl_first, float4 *clusters, cudaStream_t s) {
+    shape_setup_kernel<<<n_shapes, 256, 0, s>>>(spheres_in, spheres_out, first, count, jinv, bound, cl_first,
+                                                clusters);
     return cudaGetLastError();
 }
 

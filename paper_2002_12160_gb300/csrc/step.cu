@@ -71,52 +71,34 @@ struct Group {
     __device__ __forceinline__ int lane_in_warp() const { return TPE < 32 ? tid : lane; }
 };
 
-// Shared memory of one group (dynamic, sized by the host for the scene).
-struct GroupSmem {
-    float4 *sph;          // [S_max]   sphere centre relative to x (world frame), radius
-    float4 *stage;        // [CAP][2]  (r, gap), (n, link | pad << 8)
-    float *padacc;        // [IH_MAX_PADS*3]
-    float *red;           // [2][W][8] cross-warp partial sums
-    int *cnt;             // [2][W]    cross-warp hit counts
-    unsigned char *links; // [32]      surviving links in order
-    unsigned short *lbeg, *lend;  // [32] contact range of each link
-    unsigned *surv;       // [1]
-    double *term;         // [IH_MAX_PADS] FP64 force term of each pad
-    int *flag;            // [IH_MAX_PADS] contact-state mismatch of each pad
-    double *best_c;       // [1] best (C, env) of this group so far
-    int *best_i;          // [1]
+// Shared memory of one group. Everything has a fixed size except the cache
+// of world-frame sphere and cluster centres, which follows the group records.
+constexpr int kMaxClp = 32 * 32;   // (surviving link, cluster) pairs: 29 links x 32 clusters
+
+template <int CAP, int W>
+struct GSm {
+    float4 stage[CAP][2];            // (r, gap), (n, link | pad << 8); r.xyz later holds lambda
+    double term[IH_MAX_PADS];        // FP64 force term of each pad (scoring)
+    float padacc[IH_MAX_PADS * 3];
+    float red[2][W][8];              // cross-warp partial sums
+    int cnt[2][W];                   // cross-warp hit counts
+    int flag[IH_MAX_PADS];           // contact-state mismatch of each pad (scoring)
+    double best_c;                   // best (C, env) of this group so far
+    int best_i;
+    unsigned surv;                   // surviving-link mask
+    int n_clp;
+    unsigned char links[32];         // surviving links in order
+    unsigned short lbeg[32], lend[32];   // contact range of each link
+    unsigned short clp[kMaxClp];     // surviving (link index << 8 | cluster) pairs in order
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-__host__ __device__ inline size_t group_smem_bytes(int s_max, int cap, int w) {
-    return align16(sizeof(float4) * s_max) + align16(sizeof(float4) * 2 * cap) +
-           align16(sizeof(float) * IH_MAX_PADS * 3) + align16(sizeof(float) * 2 * w * 8) +
-           align16(sizeof(int) * 2 * w) + align16(kMaxLinks) + 2 * align16(2 * kMaxLinks) + 16 +
-           align16(sizeof(double) * IH_MAX_PADS) + align16(sizeof(int) * IH_MAX_PADS) + 16 + 16;
-}
-__host__ __device__ inline size_t block_smem_bytes() {
+__host__ __device__ constexpr size_t block_smem_bytes() {
     return align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink) + 2 * align16(4 * IH_MAX_PADS);
 }
-
-__device__ GroupSmem carve_group(unsigned char *base, int s_max, int cap, int w) {
-    GroupSmem g;
-    size_t o = 0;
-    g.sph = reinterpret_cast<float4 *>(base + o); o += align16(sizeof(float4) * s_max);
-    g.stage = reinterpret_cast<float4 *>(base + o); o += align16(sizeof(float4) * 2 * cap);
-    g.padacc = reinterpret_cast<float *>(base + o); o += align16(sizeof(float) * IH_MAX_PADS * 3);
-    g.red = reinterpret_cast<float *>(base + o); o += align16(sizeof(float) * 2 * w * 8);
-    g.cnt = reinterpret_cast<int *>(base + o); o += align16(sizeof(int) * 2 * w);
-    g.links = base + o; o += align16(kMaxLinks);
-    g.lbeg = reinterpret_cast<unsigned short *>(base + o); o += align16(2 * kMaxLinks);
-    g.lend = reinterpret_cast<unsigned short *>(base + o); o += align16(2 * kMaxLinks);
-    g.surv = reinterpret_cast<unsigned *>(base + o); o += 16;
-    g.term = reinterpret_cast<double *>(base + o); o += align16(sizeof(double) * IH_MAX_PADS);
-    g.flag = reinterpret_cast<int *>(base + o); o += align16(sizeof(int) * IH_MAX_PADS);
-    g.best_c = reinterpret_cast<double *>(base + o); o += 16;
-    g.best_i = reinterpret_cast<int *>(base + o);
-    return g;
-}
+template <int CAP, int W>
+__host__ __device__ constexpr size_t gsm_bytes() { return align16(sizeof(GSm<CAP, W>)); }
+__host__ __device__ inline size_t cache_floats4(int s_max) { return (size_t)s_max + 32; }
 
 struct Hit {
     float gap;
@@ -218,8 +200,15 @@ __device__ __forceinline__ void group_sum6(float (&v)[6], const Group<TPE> &G, f
     }
 }
 
+// Resident blocks per SM each shape is compiled for (caps its registers):
+// low contact counts per thread fit 4 blocks without spilling, 4 per thread 3.
 template <int TPE, int CPL>
-__global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_max) {
+struct MinBlocks {
+    static constexpr int value = CPL <= 2 ? 4 : (CPL <= 4 ? 3 : 2);
+};
+
+template <int TPE, int CPL>
+__global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kernel(const StepArgs a, int s_max) {
     using Grp = Group<TPE>;
     constexpr int GPB = Grp::GPB, W = Grp::W, CAP = TPE * CPL;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -248,8 +237,10 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
     unsigned char *pl_id = smem + align16(kMaxLinks);
     float *p_s0 = reinterpret_cast<float *>(smem + align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink));
     float *p_s1 = p_s0 + IH_MAX_PADS;
-    const size_t gbytes = group_smem_bytes(s_max, CAP, W);
-    const GroupSmem S = carve_group(smem + block_smem_bytes() + G.grp * gbytes, s_max, CAP, W);
+    GSm<CAP, W> &S = reinterpret_cast<GSm<CAP, W> *>(smem + block_smem_bytes())[G.grp];
+    float4 *sph = reinterpret_cast<float4 *>(smem + block_smem_bytes() + GPB * gsm_bytes<CAP, W>()) +
+                  G.grp * cache_floats4(s_max);
+    float4 *clc = sph + s_max;   // cluster centres follow the spheres
     if (threadIdx.x < kMaxLinks) {
         int c = 0;
         for (int p = 0; p < P && c < kPadsPerLink; ++p)
@@ -262,9 +253,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
     }
     __syncthreads();
 
-    unsigned long long w_pairs = 0, w_contacts = 0, w_citers = 0, w_substeps = 0, w_iters = 0;
+    unsigned long long w_pairs = 0, w_contacts = 0, w_citers = 0, w_substeps = 0, w_iters = 0, w_cl = 0;
     int parity = 0;
-    if (G.tid == 0) { *S.best_c = INFINITY; *S.best_i = 0x7fffffff; }
+    if (G.tid == 0) { S.best_c = INFINITY; S.best_i = 0x7fffffff; }
 
     for (int env = blockIdx.x * GPB + G.grp; env < a.N; env += gridDim.x * GPB) {
         int st = a.status[env];
@@ -279,7 +270,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
         const float m = th.x, mu = th.y, inv_m = 1.0f / m;
         const int sfirst = __ldg(sc.shape_first + shp), NS = __ldg(sc.shape_count + shp);
         const float bound = __ldg(sc.shape_bound + shp);
-        const float inv_nsph = 1.0f / (float)NS;
+        const int ncl = (NS + kCluster - 1) / kCluster;
+        const float inv_ncl = 1.0f / (float)ncl;
+        const int cfirst = __ldg(sc.cl_first + shp);
         S6 Jb;
         Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
         Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
@@ -297,18 +290,23 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                 const M3 R = qmat(q);
                 const S6 Wi = world_inv_inertia(R, Jb, inv_m);
 
-                // -- 1. spheres to world (relative to x), cached for the substep
+                // -- 1. spheres and cluster centres to world (relative to x), cached
                 for (int j = G.tid; j < NS; j += TPE) {
                     const float4 sp = __ldg(sc.spheres + sfirst + j);
                     const V3 cr = mmul(R, xyz(sp));
-                    S.sph[j] = make_float4(cr.x, cr.y, cr.z, sp.w);
+                    sph[j] = make_float4(cr.x, cr.y, cr.z, sp.w);
+                }
+                for (int k = G.tid; k < ncl; k += TPE) {
+                    const float4 cl = __ldg(sc.clusters + cfirst + k);
+                    const V3 cr = mmul(R, xyz(cl));
+                    clc[k] = make_float4(cr.x, cr.y, cr.z, cl.w);
                 }
                 // -- 2. cull links whose bounding volume the object cannot reach
                 if constexpr (TPE >= 32) {
                     if (G.wid == 0) {
                         const bool keep = G.lane < Lk && link_reaches(sc, cfg, L0, G.lane, x, bound);
                         const unsigned ml = __ballot_sync(0xffffffffu, keep);
-                        if (G.lane == 0) *S.surv = ml;
+                        if (G.lane == 0) S.surv = ml;
                     }
                 } else {
                     unsigned ml = 0;
@@ -317,10 +315,10 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                         const bool keep = l < Lk && link_reaches(sc, cfg, L0, l, x, bound);
                         ml |= G.ballot(keep) << base;
                     }
-                    if (G.tid == 0) *S.surv = ml;
+                    if (G.tid == 0) S.surv = ml;
                 }
                 G.sync();
-                const unsigned surv = *S.surv;
+                const unsigned surv = S.surv;
                 const int nsurv = __popc(surv);
                 for (int l = G.tid; l < kMaxLinks; l += TPE) {
                     if (l < Lk && ((surv >> l) & 1u)) S.links[__popc(surv & ((1u << l) - 1u))] = (unsigned char)l;
@@ -329,9 +327,44 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                 }
                 G.sync();
 
-                // -- 3. narrowphase over (surviving link, sphere) pairs in pair order
+                // -- 3a. cull (surviving link, cluster) pairs by the clusters' enclosing spheres
+                int nclp = 0;
+                const int ncpairs = nsurv * ncl;
+                for (int p0 = 0; p0 < ncpairs; p0 += TPE) {
+                    const int p = p0 + G.tid;
+                    bool keep = false;
+                    int li = 0, k = 0;
+                    if (p < ncpairs) {
+                        li = min(max((int)(((float)p + 0.5f) * inv_ncl), 0), nsurv - 1);
+                        k = p - li * ncl;
+                        const float4 cc = clc[k];
+                        keep = link_reaches(sc, cfg, L0, S.links[li], x + xyz(cc), cc.w);
+                    }
+                    const unsigned bal = G.ballot(keep);
+                    int off = nclp, tot;
+                    if constexpr (TPE > 32) {
+                        int *cb = S.cnt[parity];
+                        if (G.lane == 0) cb[G.wid] = __popc(bal);
+                        G.sync();
+                        tot = 0;
+#pragma unroll
+                        for (int q2 = 0; q2 < W; ++q2) {
+                            const int c = cb[q2];
+                            if (q2 < G.wid) off += c;
+                            tot += c;
+                        }
+                        parity ^= 1;
+                    } else {
+                        tot = __popc(bal);
+                    }
+                    if (keep) S.clp[off + __popc(bal & ((1u << G.lane_in_warp()) - 1u))] = (unsigned short)((li << 8) | k);
+                    nclp += tot;
+                }
+                G.sync();
+
+                // -- 3b. narrowphase over the spheres of the surviving pairs, in pair order
                 int nc = 0;
-                const int npairs = nsurv * NS;
+                const int npairs = nclp * kCluster;
                 for (int p0 = 0; p0 < npairs; p0 += TPE) {
                     const int p = p0 + G.tid;
                     bool hit = false;
@@ -339,35 +372,36 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                     V3 r = mk(0, 0, 0);
                     int l = 0;
                     if (p < npairs) {
-                        int li = (int)(((float)p + 0.5f) * inv_nsph);
-                        li = min(max(li, 0), nsurv - 1);
-                        const int j = p - li * NS;
-                        l = S.links[li];
-                        const float4 sp = S.sph[j];
-                        const V3 cr = xyz(sp);
-                        const float4 A0 = __ldg(L0 + l * kLinkStride);
-                        const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
-                        const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
-                        if (l == 0) {
-                            hh = hit_box(x + cr, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
-                        } else {
-                            const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-                            hh = hit_capsule((x - xyz(A0)) + cr, sp.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+                        const int e = S.clp[p / kCluster];
+                        const int j = (e & 0xff) * kCluster + (p % kCluster);
+                        l = S.links[e >> 8];
+                        if (j < NS) {
+                            const float4 sp = sph[j];
+                            const V3 cr = xyz(sp);
+                            const float4 A0 = __ldg(L0 + l * kLinkStride);
+                            const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
+                            const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+                            if (l == 0) {
+                                hh = hit_box(x + cr, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                            } else {
+                                const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
+                                hh = hit_capsule((x - xyz(A0)) + cr, sp.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+                            }
+                            hit = hh.gap < cfg.margin;
+                            r = cr - hh.n * sp.w;
                         }
-                        hit = hh.gap < cfg.margin;
-                        r = cr - hh.n * sp.w;
                     }
                     const unsigned bal = G.ballot(hit);
                     int off = nc, tot;
                     if constexpr (TPE > 32) {
-                        int *cb = S.cnt + parity * W;
+                        int *cb = S.cnt[parity];
                         if (G.lane == 0) cb[G.wid] = __popc(bal);
                         G.sync();
                         tot = 0;
 #pragma unroll
-                        for (int k = 0; k < W; ++k) {
-                            const int c = cb[k];
-                            if (k < G.wid) off += c;
+                        for (int q2 = 0; q2 < W; ++q2) {
+                            const int c = cb[q2];
+                            if (q2 < G.wid) off += c;
                             tot += c;
                         }
                         parity ^= 1;
@@ -385,15 +419,15 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                                 const float s0 = p_s0[pp], s1 = p_s1[pp];
                                 if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
                             }
-                            S.stage[2 * idx] = make_float4(r.x, r.y, r.z, hh.gap);
-                            S.stage[2 * idx + 1] = make_float4(hh.n.x, hh.n.y, hh.n.z,
-                                                               __int_as_float(l | ((pad & 0xff) << 8)));
+                            S.stage[idx][0] = make_float4(r.x, r.y, r.z, hh.gap);
+                            S.stage[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, __int_as_float(l | ((pad & 0xff) << 8)));
                         }
                     }
                     nc += tot;
                 }
                 G.sync();
-                w_pairs += npairs;
+                w_pairs += (unsigned long long)nclp * kCluster;
+                w_cl += ncpairs;
                 w_substeps += 1;
                 if (nc > cfg.c_max) {   // more contacts than the per-env capacity
                     st |= IH_ENV_OVERFLOW;
@@ -412,11 +446,11 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                     cr_[k] = mk(0, 0, 0); cn_[k] = mk(0, 0, 1); cc_[k] = mk(0, 0, 0);
                     ikn_[k] = 0.0f; ikt_[k] = 0.0f;
                     if (ci < nc) {
-                        const float4 s0 = S.stage[2 * ci], s1 = S.stage[2 * ci + 1];
+                        const float4 s0 = S.stage[ci][0], s1 = S.stage[ci][1];
                         const V3 r = xyz(s0), n = xyz(s1);
                         const int l = __float_as_int(s1.w) & 0xff;
-                        if (ci == 0 || (__float_as_int(S.stage[2 * ci - 1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
-                        if (ci == nc - 1 || (__float_as_int(S.stage[2 * ci + 3].w) & 0xff) != l)
+                        if (ci == 0 || (__float_as_int(S.stage[ci - 1][1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
+                        if (ci == nc - 1 || (__float_as_int(S.stage[ci + 1][1].w) & 0xff) != l)
                             S.lend[l] = (unsigned short)(ci + 1);
                         // k_n = 1/m + (r x n)^T W (r x n); tr K = 3/m + |r|^2 tr W - r^T W r
                         const V3 rn = cross(r, n);
@@ -462,7 +496,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                                 acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                             }
                         }
-                        group_sum6<TPE>(acc, G, S.red, parity);
+                        group_sum6<TPE>(acc, G, &S.red[0][0][0], parity);
                         parity ^= 1;
                         vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
                         ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
@@ -488,9 +522,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                 for (int k = 0; k < CPL; ++k) {
                     const int ci = G.tid + k * TPE;
                     if (ci < nc) {
-                        float4 s0 = S.stage[2 * ci];
+                        float4 s0 = S.stage[ci][0];
                         s0.x = lam_[k].x; s0.y = lam_[k].y; s0.z = lam_[k].z;
-                        S.stage[2 * ci] = s0;
+                        S.stage[ci][0] = s0;
                     }
                 }
                 G.sync();
@@ -499,9 +533,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
                     const int e = S.lend[l];
                     for (int ci = S.lbeg[l]; ci < e; ++ci) {
-                        const float4 s1 = S.stage[2 * ci + 1];
+                        const float4 s1 = S.stage[ci][1];
                         if (((__float_as_int(s1.w) >> 8) & 0xff) != p) continue;
-                        const float4 s0 = S.stage[2 * ci];
+                        const float4 s0 = S.stage[ci][0];
                         fx -= s0.x * inv_h; fy -= s0.y * inv_h; fz -= s0.z * inv_h;
                     }
                     S.padacc[3 * p + 0] += fx;
@@ -550,7 +584,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
                 a.c_mean[env] = cm;
                 if (a.cost_mean) a.cost_mean[env] = cm;
                 if (isnan(cm)) cm = INFINITY;
-                if (cm < *S.best_c || (cm == *S.best_c && env < *S.best_i)) { *S.best_c = cm; *S.best_i = env; }
+                if (cm < S.best_c || (cm == S.best_c && env < S.best_i)) { S.best_c = cm; S.best_i = env; }
             }
         }
         // forces of the last frame, averaged over its substeps
@@ -573,6 +607,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
         atomicAdd(a.work + 2, w_citers);
         atomicAdd(a.work + 3, w_substeps);
         atomicAdd(a.work + 4, w_iters);
+        atomicAdd(a.work + 5, w_cl);
     }
     if (!scored) return;
     // argmin (C_i, i) over the grid: per-block candidate, then the last block
@@ -584,9 +619,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
         double bc = INFINITY;
         int bi = 0x7fffffff;
         for (int g2 = 0; g2 < GPB; ++g2) {
-            const GroupSmem S2 = carve_group(smem + block_smem_bytes() + g2 * gbytes, s_max, CAP, W);
-            const double c = *S2.best_c;
-            const int i = *S2.best_i;
+            const GSm<CAP, W> &S2 = reinterpret_cast<GSm<CAP, W> *>(smem + block_smem_bytes())[g2];
+            const double c = S2.best_c;
+            const int i = S2.best_i;
             if (c < bc || (c == bc && i < bi)) { bc = c; bi = i; }
         }
         a.part_c[blockIdx.x] = bc;
@@ -630,7 +665,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs a, int s_ma
 
 template <int TPE, int CPL>
 size_t bytes_t(int s_max) {
-    return block_smem_bytes() + (size_t)Group<TPE>::GPB * group_smem_bytes(s_max, TPE * CPL, Group<TPE>::W);
+    constexpr int GPB = Group<TPE>::GPB;
+    return block_smem_bytes() + GPB * gsm_bytes<TPE * CPL, Group<TPE>::W>() +
+           GPB * cache_floats4(s_max) * sizeof(float4);
 }
 
 template <int TPE, int CPL>
@@ -669,8 +706,10 @@ int step_variant_list(StepVariant *out, int cap) {
 }
 
 size_t step_smem_bytes(const StepVariant &v, int s_max) {
-    const int gpb = kBlock / v.group, w = v.group >= 32 ? v.group / 32 : 1;
-    return block_smem_bytes() + (size_t)gpb * group_smem_bytes(s_max, v.group * v.cpl, w);
+#define IH_BYTES(T, C) if (v.group == T && v.cpl == C) return bytes_t<T, C>(s_max);
+    IH_STEP_VARIANTS(IH_BYTES)
+#undef IH_BYTES
+    return 0;
 }
 
 cudaError_t step_prepare(const StepVariant &v, int s_max) {

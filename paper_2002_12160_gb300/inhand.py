@@ -239,10 +239,10 @@ class Sim:
         self._call("optimizer_update", C.byref(oc), C.c_uint32(update_index), _ptr(argmin), _ptr(parent))
 
     def sim_work_counters(self, reset: bool = False):
-        out = (C.c_uint64 * 5)()
+        out = (C.c_uint64 * 6)()
         self._call("sim_work_counters", out, 1 if reset else 0)
         return {"pairs": out[0], "contacts": out[1], "contact_iters": out[2], "env_substeps": out[3],
-                "env_iters": out[4]}
+                "env_iters": out[4], "cluster_tests": out[5]}
 
     def sim_sync(self):
         self._call("sim_sync")
