@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--n-envs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
+    p.add_argument("--sweep", default=None,
+                   help="comma-separated N values: also time the workload at each N (tracking frames/s)")
     return p.parse_args()
 
 
@@ -132,11 +134,13 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest of every rank's x (the slowest rank sets the job's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -210,20 +214,22 @@ def cpu_baseline(workload, budget_s=12.0):
 
 
 # ----------------------------------------------------------------------------- our arm
-def run_ours(args, rank, world, local):
+def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e=True, with_timing=True):
+    """Time `steps` tracking windows (graph replays) of a workload on this rank's GPU."""
     import torch
     from paper_2002_12160_gb300 import tracking, workloads as W
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     T = 10
-    n_timing, n_e2e = 2, 2
-    n_windows = args.warmup + args.steps + n_timing + n_e2e
-    wl = W.make_workload(args.workload, n_envs=args.n_envs, frames=n_windows * T)
+    n_timing = 2 if with_timing else 0
+    n_e2e = 2 if with_e2e else 0
+    n_windows = warmup + steps + n_timing + n_e2e
+    wl = W.make_workload(workload, n_envs=n_envs, frames=n_windows * T)
     seed = wl.seed + 7919 * rank   # independent replicas per rank
     tr = tracking.Tracker(wl, seed=seed)
     tr.prepare()
-    if args.shape:
-        a, b = (int(v) for v in args.shape.lower().split("x"))
+    if shape:
+        a, b = (int(v) for v in shape.lower().split("x"))
         tr.sim.sim_set_variant(a, b)
         chosen, tune_ms = (a, b), {}
     else:
@@ -231,61 +237,77 @@ def run_ours(args, rank, world, local):
         chosen, tune_ms = tr.sim.sim_autotune(0, 2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for w in range(args.warmup):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for w in range(warmup):
         tr.window(w)
     torch.cuda.synchronize()
     tr.sim.sim_work_counters(reset=True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for s in range(args.steps):
+        for s in range(steps):
             flush.zero_()
             ev[s][0].record(stream)
-            tr.window(args.warmup + s)       # one captured graph: T fused steps + optimizer
+            tr.window(warmup + s)       # one captured graph: T fused steps + optimizer
             ev[s][1].record(stream)
         torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    ms_steps = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
+    ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(steps)) / steps
     work = tr.sim.sim_work_counters(reset=True)
-    ms = sum(ms_steps) / len(ms_steps)
     ms = max_over_ranks(ms, world)
-    n = tr.n
+    out = {"wl": wl, "n": tr.n, "T": T, "ms": ms, "work": work, "clocks": clk.summary(),
+           "chosen": chosen, "tune_ms": tune_ms}
+    w0 = warmup + steps
+    if with_timing:
+        # the dominant kernel alone: the same windows launched one kernel at a time,
+        # every (fused) step bracketed by events on its stream, L2 flushed per window
+        step_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
+                   for _ in range(n_timing)]
+        tr.sim.sim_work_counters(reset=True)
+        for s in range(n_timing):
+            flush.zero_()
+            tr.window_unfused(w0 + s, step_events=step_ev[s])
+        torch.cuda.synchronize()
+        out["work_t"] = tr.sim.sim_work_counters(reset=True)
+        lst = [a.elapsed_time(b) for s in range(n_timing) for (a, b) in step_ev[s]]
+        out["step_ms"] = sum(lst) / len(lst)
+        out["step_launches"] = n_timing * T
+    if with_e2e:
+        out["e2e"] = tr.e2e_windows(w0 + n_timing, n_e2e)
+    out["add_mm"] = tr.add_mm()
+    tr.close()
+    del flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def flops_of(work, wl):
+    return (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * max(len(s) for s in wl.scene.shapes)) +
+            work["pairs"] * FLOP_PER_PAIR + work["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
+            work["contacts"] * FLOP_PER_CONTACT + work["contact_iters"] * FLOP_PER_CONTACT_ITER +
+            work["env_iters"] * FLOP_PER_ENV_ITER)
+
+
+def run_ours(args, rank, world, local):
+    m = measure(args.workload, args.n_envs, args.steps, args.warmup, args.shape, rank, world, local)
+    wl, n, T, ms = m["wl"], m["n"], m["T"], m["ms"]
     value = world * n * T / (ms / 1e3)
-    # the dominant kernel alone: the same windows launched one kernel at a time,
-    # every (fused) step bracketed by events on its stream, L2 flushed per window
-    step_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
-               for _ in range(n_timing)]
-    w0 = args.warmup + args.steps
-    tr.sim.sim_work_counters(reset=True)
-    for s in range(n_timing):
-        flush.zero_()
-        tr.window_unfused(w0 + s, step_events=step_ev[s])
-    torch.cuda.synchronize()
-    work_t = tr.sim.sim_work_counters(reset=True)
-    step_ms_list = [a.elapsed_time(b) for s in range(n_timing) for (a, b) in step_ev[s]]
-    step_ms = sum(step_ms_list) / len(step_ms_list)
-    launches = n_timing * T
-    flops = (work_t["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * len(wl.scene.shapes[0])) +
-             work_t["pairs"] * FLOP_PER_PAIR + work_t["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
-             work_t["contacts"] * FLOP_PER_CONTACT + work_t["contact_iters"] * FLOP_PER_CONTACT_ITER +
-             work_t["env_iters"] * FLOP_PER_ENV_ITER)
-    per_launch_flops = flops / launches
+    per_launch_flops = flops_of(m["work_t"], wl) / m["step_launches"]
+    step_ms = m["step_ms"]
     achieved = per_launch_flops / (step_ms / 1e3) / 1e12
-    clocks = clk.summary()
+    clocks = m["clocks"]
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     step_bytes = n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12 + n * 16
-    # e2e through the public API with host buffers
-    e2e = tr.e2e_windows(w0 + n_timing, n_e2e)
-    add_mm = tr.add_mm()
+    chosen, tune_ms = m["chosen"], m["tune_ms"]
     line = {"metric": "env-steps/s", "value": value, "unit": "env-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n_envs": n, "window_frames": T,
-                       "spheres": int(len(wl.scene.shapes[0])), "links": wl.scene.n_links,
-                       "pads": wl.scene.n_pads, "iters": int(wl.sim.iters), "substeps": wl.sim.substeps,
+                       "spheres": sorted(set(int(len(x)) for x in wl.scene.shapes)), "links": wl.scene.n_links,
+                       "pads": wl.scene.n_pads, "iters": sorted(set(int(i) for i in wl.iters[:n])),
+                       "substeps": wl.sim.substeps,
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}",
                        "step_shape": {"threads_per_env": chosen[0], "contacts_per_thread": chosen[1],
                                       "autotune_ms": {f"{a}x{b}": round(v, 4) for (a, b), v in tune_ms.items()}}},
@@ -296,16 +318,25 @@ def run_ours(args, rank, world, local):
                          "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"},
             "hbm": {"step_bytes_per_launch": step_bytes, "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
                     "peak_gbs": 6777.0, "frac": step_bytes / (step_ms / 1e3) / 1e9 / 6777.0},
-            "work_per_launch": {k: v / (args.steps * T) for k, v in work.items()},
+            "work_per_launch": {k: v / (args.steps * T) for k, v in m["work"].items()},
             "clocks": clocks,
             "gpu_launches": args.steps * (T + 5),   # T fused steps, descriptor, 4 optimizer kernels
-            "e2e": e2e,
-            "add_mm_argmin_env": add_mm}
+            "e2e": m["e2e"],
+            "add_mm_argmin_env": m["add_mm"]}
+    if args.sweep:
+        sweep = []
+        for nn in [int(v) for v in args.sweep.split(",")]:
+            r = measure(args.workload, nn, 3, 2, args.shape, rank, world, local, with_e2e=False, with_timing=False)
+            fps = r["T"] / (r["ms"] / 1e3)
+            sweep.append({"n_envs": nn, "ms_per_window": r["ms"], "tracking_frames_per_s": fps,
+                          "env_steps_per_s": nn * fps, "step_shape": list(r["chosen"])})
+        line["sweep"] = sweep
+        ok = [x for x in sweep if x["tracking_frames_per_s"] >= 30.0]
+        line["largest_n_measured_at_30hz"] = max((x["n_envs"] for x in ok), default=None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tr.close()
 
 
 def main():

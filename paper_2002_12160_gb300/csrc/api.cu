@@ -36,6 +36,7 @@ struct ih_sim {
     float4 *pose = nullptr, *vel = nullptr;
     float2 *params = nullptr;
     int *shape = nullptr, *iters = nullptr, *status = nullptr;
+    int *order = nullptr, *lpt_scratch = nullptr;
     float *forces = nullptr;
     double *c_sum = nullptr, *c_mean = nullptr;
     int *n_window = nullptr, *argmin = nullptr;
@@ -111,12 +112,8 @@ DevScene dev_scene(const ih_sim *s) {
 // whole CTA each (latency bound), many get one warp each (issue bound); the
 // register-resident contacts per thread must cover c_max.
 StepVariant default_variant(int N, int c_max) {
-    const StepVariant wide[] = {{128, 1, 128}, {128, 2, 128}};
-    const StepVariant narrow[] = {{32, 4, 128}, {32, 8, 128}};
-    const bool few = N <= 4096;
-    for (const auto &v : (few ? wide : narrow))
-        if (step_variant_max_contacts(v) >= c_max) return v;
-    return few ? wide[1] : narrow[1];
+    (void)c_max;   // every shape holds any c_max
+    return N <= 4096 ? StepVariant{64, 2, 128} : StepVariant{32, 2, 128};
 }
 
 int grid_for(const StepVariant &v, int N) {
@@ -206,6 +203,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->pose, 2 * (size_t)N)); A(dalloc(s, &s->vel, 2 * (size_t)N));
     A(dalloc(s, &s->params, N)); A(dalloc(s, &s->shape, N)); A(dalloc(s, &s->iters, N));
     A(dalloc(s, &s->status, N)); A(dalloc(s, &s->forces, (size_t)N * P * 3));
+    A(dalloc(s, &s->order, N)); A(dalloc(s, &s->lpt_scratch, 64));
     A(dalloc(s, &s->c_sum, N)); A(dalloc(s, &s->c_mean, N));
     A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
     A(dalloc(s, &s->part_c, std::max(N, cost_blocks(N)))); A(dalloc(s, &s->part_i, std::max(N, cost_blocks(N))));
@@ -251,6 +249,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemsetAsync(s->work, 0, 6 * sizeof(unsigned long long), st));
     A(launch_shape_setup(s->spheres_raw, s->spheres, s->shape_first, s->shape_count, sc->n_shapes,
                          s->shape_jinv, s->shape_bound, s->cl_first, s->clusters, st));
+    A(launch_lpt_order(N, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, st));
     A(cudaStreamSynchronize(st));   // host vectors above go out of scope
     if (e != cudaSuccess) {
         ih_status r = cuda_fail(nullptr, e, "sim_create upload");
@@ -259,7 +258,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     }
     s->frame_ready.assign(cfg->max_frames, 0);
     s->step_grid = grid_for(s->variant, N);
-    e = step_prepare(s->variant, s->s_max);
+    e = step_prepare(s->variant, s->s_max, s->cfg.c_max);
     if (e != cudaSuccess) {
         ih_status r = cuda_fail(nullptr, e, "sim_create step setup");
         sim_destroy(s);
@@ -324,6 +323,8 @@ ih_status sim_set_state(ih_sim *s, const float *pose, const float *vel, const fl
         return fail(s, IH_ERR_ARG, "pose/vel must be 16-byte aligned, params 8-byte aligned");
     cudaError_t e = launch_set_state(s->cfg.n_envs, s->n_shapes, pose, vel, params, shape_id, iters,
                                      s->pose, s->vel, s->params, s->shape, s->iters, s->status, s->stream);
+    if (e == cudaSuccess && (shape_id || iters))
+        e = launch_lpt_order(s->cfg.n_envs, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
     return IH_OK;
 }
@@ -353,6 +354,7 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
     a.frame0 = frame0; a.n_frames = n_frames; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
     a.shape = s->shape; a.iters = s->iters; a.status = s->status; a.forces = s->forces; a.work = s->work;
+    a.order = s->order;
     a.obs = nullptr; a.win = nullptr; a.win_k = 0;
     a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window; a.cost_mean = nullptr;
     a.argmin_state = s->argmin; a.argmin_out = nullptr; a.est_pose_out = nullptr;
@@ -369,6 +371,7 @@ StepArgs scored_args(ih_sim *s, int frame, const float *obs, double *cost_mean, 
     a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
     a.frame0 = frame; a.n_frames = 1; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
     a.shape = s->shape; a.iters = s->iters; a.status = s->status; a.forces = s->forces; a.work = s->work;
+    a.order = s->order;
     a.obs = obs; a.win = nullptr; a.win_k = 0;
     a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window; a.cost_mean = cost_mean;
     a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est;
@@ -535,7 +538,7 @@ ih_status sim_set_variant(ih_sim *s, int32_t tpe, int32_t cpl) {
     if (!step_variant_supported(v)) return fail(s, IH_ERR_ARG, "unsupported step shape %d x %d", tpe, cpl);
     if (step_variant_max_contacts(v) < s->cfg.c_max)
         return fail(s, IH_ERR_ARG, "shape %d x %d holds fewer than c_max = %d contacts", tpe, cpl, s->cfg.c_max);
-    cudaError_t e = step_prepare(v, s->s_max);
+    cudaError_t e = step_prepare(v, s->s_max, s->cfg.c_max);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_variant");
     s->variant = v;
     s->step_grid = grid_for(v, s->cfg.n_envs);
@@ -589,7 +592,7 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     if (e == cudaSuccess) { save(); e = cudaStreamSynchronize(st); }
     for (int k = 0; k < nv && e == cudaSuccess; ++k) {
         float ms = NAN;
-        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && step_prepare(cand[k], s->s_max) == cudaSuccess) {
+        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && step_prepare(cand[k], s->s_max, s->cfg.c_max) == cudaSuccess) {
             s->variant = cand[k];
             s->step_grid = grid_for(cand[k], (int)N);
             ih_status r = sim_step(s, frame0, n_frames);   // warm-up (and first-use setup)

@@ -170,6 +170,8 @@ __device__ __forceinline__ void qlog_d(Q4d q, double out[3]) {
 cudaError_t launch_shape_setup(const float4 *spheres_in, float4 *spheres_out, const int *first,
                                const int *count, int n_shapes, float *jinv, float *bound,
                                const int *cl_first, float4 *clusters, cudaStream_t s);
+cudaError_t launch_lpt_order(int N, const int *shape_count, const int *shape, const int *iters, int *scratch,
+                             int *order, cudaStream_t s);
 cudaError_t launch_fk(const DevScene &sc, const float *q, int n_frames, int substeps,
                       float4 *link_tab_out, cudaStream_t s);
 cudaError_t launch_sample_initial(int N, float4 pose0, float4 quat0, float sigma_p, float sigma_r,
@@ -200,6 +202,7 @@ struct StepArgs {
     float4 *pose, *vel;       // [N][2]
     const float2 *params;
     const int *shape, *iters;
+    const int *order;         // [N] environment of each work slot (most work first), or null
     int *status;
     float *forces;            // [N][P][3]
     unsigned long long *work; // [6]
@@ -224,7 +227,7 @@ struct StepVariant {
 cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s);
 int step_variant_max_contacts(const StepVariant &v);
 bool step_variant_supported(const StepVariant &v);
-size_t step_smem_bytes(const StepVariant &v, int s_max);
+size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max);
 int step_variant_list(StepVariant *out, int cap);
 
 struct CostArgs {
@@ -279,7 +282,7 @@ struct OptArgs {
 };
 int opt_blocks(int N);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
-cudaError_t step_prepare(const StepVariant &v, int s_max);
+cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
 
 }  // namespace ih

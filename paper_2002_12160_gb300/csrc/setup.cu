@@ -186,7 +186,68 @@ __global__ void set_state_kernel(int N, int n_shapes, const float4 *pose_in, con
     status[i] = ok ? 0 : IH_ENV_INVALID;
 }
 
+// Work order of the environments, most expensive first (longest processing
+// time first), by a counting sort on a bucketed estimate S * iters.
+constexpr int kLptBuckets = 64;
+
+__device__ __forceinline__ int lpt_bucket(const int *shape_count, const int *shape, const int *iters, int i) {
+    const float cost = (float)shape_count[shape[i]] * (float)max(iters[i], 1);
+    const int b = (int)(log2f(cost) * 3.0f);
+    return kLptBuckets - 1 - min(max(b, 0), kLptBuckets - 1);
+}
+
+__global__ void lpt_hist_kernel(int N, const int *shape_count, const int *shape, const int *iters, int *hist) {
+    __shared__ int h[kLptBuckets];
+    if (threadIdx.x < kLptBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[lpt_bucket(shape_count, shape, iters, i)], 1);
+    __syncthreads();
+    if (threadIdx.x < kLptBuckets && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void lpt_scan_kernel(int *hist) {
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < kLptBuckets; ++b) { const int c = hist[b]; hist[b] = acc; acc += c; }
+    }
+}
+
+// One warp walks the environments in index order, 32 at a time, so that the
+// order within a bucket is the index order (a stable sort).
+__global__ void lpt_scatter_kernel(int N, const int *shape_count, const int *shape, const int *iters, const int *offs,
+                                   int *order) {
+    __shared__ int next[kLptBuckets];
+    const int lane = threadIdx.x;
+    for (int b = lane; b < kLptBuckets; b += 32) next[b] = offs[b];
+    __syncwarp();
+    for (int base = 0; base < N; base += 32) {
+        const int i = base + lane;
+        const int b = i < N ? lpt_bucket(shape_count, shape, iters, i) : kLptBuckets;   // sentinel
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        const int leader = __ffs(same) - 1;
+        int start = 0;
+        if (i < N) start = next[b];
+        __syncwarp();
+        if (i < N) order[start + rank] = i;
+        if (i < N && lane == leader) next[b] = start + __popc(same);
+        __syncwarp();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_lpt_order(int N, const int *shape_count, const int *shape, const int *iters, int *scratch,
+                             int *order, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, kLptBuckets * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = min(152 * 4, (N + 255) / 256);
+    lpt_hist_kernel<<<blocks, 256, 0, s>>>(N, shape_count, shape, iters, scratch);
+    lpt_scan_kernel<<<1, 32, 0, s>>>(scratch);
+    lpt_scatter_kernel<<<1, 32, 0, s>>>(N, shape_count, shape, iters, scratch, order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_shape_setup(const float4 *spheres_in, float4 *spheres_out, const int *first,
                                const int *count, int n_shapes, float *jinv, float *bound,

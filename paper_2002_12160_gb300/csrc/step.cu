@@ -23,6 +23,8 @@
 //      scanning only the contacts of its own link.
 // Nothing here is a dense contraction: the kernel is bound by FP32 issue and
 // by the latency of the solver's reductions.
+#include <cstddef>
+
 #include "internal.cuh"
 
 namespace ih {
@@ -75,16 +77,16 @@ struct Group {
 // of world-frame sphere and cluster centres, which follows the group records.
 constexpr int kMaxClp = 32 * 32;   // (surviving link, cluster) pairs: 29 links x 32 clusters
 
-template <int CAP, int W>
-struct GSm {
-    float4 stage[CAP][2];            // (r, gap), (n, link | pad << 8); r.xyz later holds lambda
+template <int W>
+struct alignas(16) GSm {   // 16-byte aligned: red is read as float4
     double term[IH_MAX_PADS];        // FP64 force term of each pad (scoring)
     float padacc[IH_MAX_PADS * 3];
     float red[2][W][8];              // cross-warp partial sums
-    int cnt[2][W];                   // cross-warp hit counts
+    int cnt[2][2 * W];               // cross-warp hit counts
     int flag[IH_MAX_PADS];           // contact-state mismatch of each pad (scoring)
     double best_c;                   // best (C, env) of this group so far
     int best_i;
+    unsigned long long work[6];      // this group's work counters (see sim_work_counters)
     unsigned surv;                   // surviving-link mask
     int n_clp;
     unsigned char links[32];         // surviving links in order
@@ -96,9 +98,14 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ constexpr size_t block_smem_bytes() {
     return align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink) + 2 * align16(4 * IH_MAX_PADS);
 }
-template <int CAP, int W>
-__host__ __device__ constexpr size_t gsm_bytes() { return align16(sizeof(GSm<CAP, W>)); }
-__host__ __device__ inline size_t cache_floats4(int s_max) { return (size_t)s_max + 32; }
+template <int W>
+__host__ __device__ constexpr size_t gsm_bytes() { return align16(sizeof(GSm<W>)); }
+static_assert(sizeof(GSm<1>) % 16 == 0 && sizeof(GSm<2>) % 16 == 0 && sizeof(GSm<4>) % 16 == 0,
+              "group records must keep 16-byte alignment");
+static_assert(offsetof(GSm<2>, red) % 16 == 0, "red is read as float4");
+// dynamic part of a group: the contact staging (4 float4 per contact, c_max
+// contacts) then the cache of sphere and cluster centres
+__host__ __device__ inline size_t group_dyn_floats4(int s_max, int c_max) { return 4 * (size_t)c_max + s_max + 32; }
 
 struct Hit {
     float gap;
@@ -115,9 +122,10 @@ __device__ __forceinline__ Hit hit_box(V3 c, float rs, V3 a, Q4 q, float hx, flo
     const bool inside = (k.x == cl.x) && (k.y == cl.y) && (k.z == cl.z);
     if (!inside) {
         const V3 d = cl - k;
-        const float dist = sqrtf(dot(d, d));
-        h.n = qrot(q, d * (1.0f / dist));
-        h.gap = dist - rs;
+        const float d2 = dot(d, d);
+        const float inv = rsqrtf(d2);   // d2 > 0: the centre is outside the box
+        h.n = qrot(q, d * inv);
+        h.gap = d2 * inv - rs;
     } else {
         // shallowest face, ties to the lowest axis and the + side
         float best = hx - cl.x;
@@ -137,11 +145,17 @@ __device__ __forceinline__ Hit hit_box(V3 c, float rs, V3 a, Q4 q, float hx, flo
 __device__ __forceinline__ Hit hit_capsule(V3 ca, float rs, V3 d, float L, float inv_L, float rc, Q4 q) {
     const float t = fminf(fmaxf(dot(ca, d) * inv_L, 0.0f), 1.0f);
     const V3 diff = ca - d * (t * L);
-    const float dist = sqrtf(dot(diff, diff));
+    const float d2 = dot(diff, diff);
     Hit h;
     h.t = t;
-    h.n = (dist < 1e-9f) ? qrot(q, mk(0, 0, 1)) : diff * (1.0f / dist);
-    h.gap = dist - rs - rc;
+    if (d2 < 1e-18f) {   // centre on the axis
+        h.n = qrot(q, mk(0, 0, 1));
+        h.gap = -rs - rc;
+    } else {
+        const float inv = rsqrtf(d2);
+        h.n = diff * inv;
+        h.gap = d2 * inv - rs - rc;
+    }
     return h;
 }
 
@@ -176,41 +190,132 @@ __device__ __forceinline__ bool all_finite(V3 x, Q4 q, V3 v, V3 w) {
            isfinite(w.x) && isfinite(w.y) && isfinite(w.z);
 }
 
+// Per-contact constants: scalar effective masses along the normal and in the
+// tangent plane, and the target velocity c = v_link - b n (bias folded in).
+struct CSetup {
+    float ikn, ikt;
+    V3 cc;
+};
+
+__device__ __forceinline__ CSetup setup_contact(V3 r, V3 n, float gap, int l, const S6 &Wi, float trW, float inv_m,
+                                                const DevConfig &cfg, const float4 *L0, const float4 *L1, V3 x,
+                                                float inv_h) {
+    // k_n = 1/m + (r x n)^T W (r x n); tr K = 3/m + |r|^2 tr W - r^T W r
+    const V3 rn = cross(r, n);
+    const float kn = inv_m + dot(rn, smul(Wi, rn));
+    const float trK = 3.0f * inv_m + dot(r, r) * trW - dot(r, smul(Wi, r));
+    CSetup c;
+    c.ikn = 1.0f / kn;
+    c.ikt = 2.0f / (trK - kn);
+    const float b = contact_bias(cfg, gap);
+    V3 vl = mk(0, 0, 0);
+    if (l != 0) {   // link point velocity from the link's rigid displacement over the substep
+        const float4 A0 = __ldg(L0 + l * kLinkStride), B0 = __ldg(L1 + l * kLinkStride);
+        const float4 Aq = __ldg(L0 + l * kLinkStride + 2), Bq = __ldg(L1 + l * kLinkStride + 2);
+        const Q4 qa = {Aq.x, Aq.y, Aq.z, Aq.w}, qb = {Bq.x, Bq.y, Bq.z, Bq.w};
+        const V3 pl = qrot_inv(qa, (x - xyz(A0)) + r);   // contact in link coords
+        vl = ((xyz(B0) - xyz(A0)) + (qrot(qb, pl) - qrot(qa, pl))) * inv_h;
+    }
+    c.cc = vl - n * b;
+    return c;
+}
+
+// One projected Jacobi update of a contact's impulse against the body
+// velocity (vv, ww): scalar normal step clamped at zero, scalar tangential
+// step clamped radially to the Coulomb disk, relaxed by 1/n_c.
+__device__ __forceinline__ V3 update_contact(V3 lam, V3 r, V3 n, V3 cc, float ikn, float ikt, V3 vv, V3 ww,
+                                             float mu, float inv_nc) {
+    const V3 u = vv + cross(ww, r) - cc;
+    const float un = dot(u, n);
+    const float l_old = dot(lam, n);
+    const float ln = fmaxf(l_old - un * ikn, 0.0f);
+    V3 lt = (lam - n * l_old) - (u - n * un) * ikt;
+    const float tn2 = dot(lt, lt);
+    const float lim = mu * ln;
+    if (tn2 > lim * lim) lt = lt * (lim * rsqrtf(tn2));
+    const V3 lp = n * ln + lt;
+    return lam + (lp - lam) * inv_nc;
+}
+
+// Sum of 6 values over the WIDTH lanes of a group (WIDTH = 16 or 32), every
+// lane receiving all 6 sums. Reduce-scatter first: padded to 8 values, each
+// of the first three xor levels halves the values a lane keeps (the partner
+// sends the half the lane keeps and keeps the other half), the remaining levels
+// are plain; the lane at position (k>>2) W/2 + ((k>>1)&1) W/4 + (k&1) W/8
+// then holds the full sum of value k, and six shuffles broadcast them.
+// 15 shuffles and 9 additions for WIDTH = 32 instead of 30 and 30.
+template <int WIDTH>
+__device__ __forceinline__ float width_scatter6(const float (&v)[6], unsigned mask, int lane_in_group) {
+    const bool b2 = lane_in_group & (WIDTH / 2), b4 = lane_in_group & (WIDTH / 4), b8 = lane_in_group & (WIDTH / 8);
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float lo = v[i], hi = (i + 4 < 6) ? v[i + 4] : 0.0f;
+        const float send = b2 ? lo : hi;
+        a[i] = (b2 ? hi : lo) + __shfl_xor_sync(mask, send, WIDTH / 2, WIDTH);
+    }
+    float b[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b4 ? a[i] : a[i + 2];
+        b[i] = (b4 ? a[i + 2] : a[i]) + __shfl_xor_sync(mask, send, WIDTH / 4, WIDTH);
+    }
+    float c = (b8 ? b[1] : b[0]) + __shfl_xor_sync(mask, b8 ? b[0] : b[1], WIDTH / 8, WIDTH);
+#pragma unroll
+    for (int o = WIDTH / 16; o > 0; o >>= 1) c += __shfl_xor_sync(mask, c, o, WIDTH);
+    return c;
+}
+// lane of a group holding value k after width_scatter6
+template <int WIDTH>
+__device__ __forceinline__ int scatter_lane(int k) {
+    return (k >> 2) * (WIDTH / 2) + ((k >> 1) & 1) * (WIDTH / 4) + (k & 1) * (WIDTH / 8);
+}
+
+template <int WIDTH>
+__device__ __forceinline__ void width_sum6(float (&v)[6], unsigned mask, int lane_in_group) {
+    const float c = width_scatter6<WIDTH>(v, mask, lane_in_group);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = __shfl_sync(mask, c, scatter_lane<WIDTH>(k), WIDTH);
+}
+
 template <int TPE>
 __device__ __forceinline__ void group_sum6(float (&v)[6], const Group<TPE> &G, float *red, int parity) {
     constexpr int WIDTH = Group<TPE>::WIDTH;
-#pragma unroll
-    for (int o = WIDTH / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(G.mask, v[k], o);
-    if constexpr (TPE > 32) {
+    if constexpr (TPE <= 32) {
+        width_sum6<WIDTH>(v, G.mask, G.lane_in_warp() & (WIDTH - 1));
+    } else {
+        // each warp's sums go straight from the lanes that hold them to shared
+        // memory; every thread then adds the W warps' partials in warp order
         constexpr int W = Group<TPE>::W;
+        const float c = width_scatter6<32>(v, G.mask, G.lane);
         float *r = red + parity * W * 8;
-        if (G.lane == 0)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) r[G.wid * 8 + k] = v[k];
+        const int k = G.lane >> 2;
+        if ((G.lane & 3) == 0 && k < 6) r[G.wid * 8 + k] = c;
         G.sync();
+        const float4 *r4 = reinterpret_cast<const float4 *>(r);
+        float4 lo = r4[0], hi = r4[1];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            float s = r[k];
-#pragma unroll
-            for (int w = 1; w < W; ++w) s += r[w * 8 + k];
-            v[k] = s;
+        for (int w = 1; w < W; ++w) {
+            const float4 l2 = r4[2 * w], h2 = r4[2 * w + 1];
+            lo.x += l2.x; lo.y += l2.y; lo.z += l2.z; lo.w += l2.w;
+            hi.x += h2.x; hi.y += h2.y;
         }
+        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w; v[4] = hi.x; v[5] = hi.y;
     }
 }
 
 // Resident blocks per SM each shape is compiled for (caps its registers):
-// low contact counts per thread fit 4 blocks without spilling, 4 per thread 3.
+// one register-resident contact per thread fits 5 blocks without spilling,
+// two fit 4, four fit 3.
 template <int TPE, int CPL>
 struct MinBlocks {
-    static constexpr int value = CPL <= 2 ? 4 : (CPL <= 4 ? 3 : 2);
+    static constexpr int value = CPL <= 1 ? 5 : (CPL <= 2 ? 4 : (CPL <= 4 ? 3 : 2));
 };
 
 template <int TPE, int CPL>
 __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kernel(const StepArgs a, int s_max) {
     using Grp = Group<TPE>;
-    constexpr int GPB = Grp::GPB, W = Grp::W, CAP = TPE * CPL;
+    constexpr int GPB = Grp::GPB, W = Grp::W, RCAP = TPE * CPL;   // register-resident contacts
     extern __shared__ __align__(16) unsigned char smem[];
     const Grp G;
     const DevScene &sc = a.sc;
@@ -221,13 +326,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
     // the frame, observation and outputs (from the window descriptor when replayed)
     int frame0 = a.frame0;
     const float *obs = a.obs;
-    float *est_out = a.est_pose_out;
-    int *argmin_out = a.argmin_out;
     if (a.win) {
         frame0 = a.win->frame0 + a.win_k;
         obs = a.win->obs ? a.win->obs + (size_t)a.win_k * P * 3 : nullptr;
-        est_out = a.win->est ? a.win->est + 8 * a.win_k : nullptr;
-        argmin_out = a.win->argmin ? a.win->argmin + a.win_k : nullptr;
     }
     const bool scored = obs != nullptr;
     const int n_win = scored ? *a.n_window + 1 : 0;
@@ -237,9 +338,13 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
     unsigned char *pl_id = smem + align16(kMaxLinks);
     float *p_s0 = reinterpret_cast<float *>(smem + align16(kMaxLinks) + align16(kMaxLinks * kPadsPerLink));
     float *p_s1 = p_s0 + IH_MAX_PADS;
-    GSm<CAP, W> &S = reinterpret_cast<GSm<CAP, W> *>(smem + block_smem_bytes())[G.grp];
-    float4 *sph = reinterpret_cast<float4 *>(smem + block_smem_bytes() + GPB * gsm_bytes<CAP, W>()) +
-                  G.grp * cache_floats4(s_max);
+    GSm<W> &S = *reinterpret_cast<GSm<W> *>(smem + block_smem_bytes() + G.grp * gsm_bytes<W>());
+    const int cap = cfg.c_max;
+    // contact staging: [0] (r, gap -> 1/k_t), [1] (n, link | pad << 8), [2] (c, 1/k_n), [3] (lambda)
+    float4 (*stage)[4] = reinterpret_cast<float4 (*)[4]>(
+        reinterpret_cast<float4 *>(smem + block_smem_bytes() + GPB * gsm_bytes<W>()) +
+        G.grp * group_dyn_floats4(s_max, cap));
+    float4 *sph = &stage[cap][0];
     float4 *clc = sph + s_max;   // cluster centres follow the spheres
     if (threadIdx.x < kMaxLinks) {
         int c = 0;
@@ -253,11 +358,15 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
     }
     __syncthreads();
 
-    unsigned long long w_pairs = 0, w_contacts = 0, w_citers = 0, w_substeps = 0, w_iters = 0, w_cl = 0;
     int parity = 0;
-    if (G.tid == 0) { S.best_c = INFINITY; S.best_i = 0x7fffffff; }
+    if (G.tid == 0) {
+        S.best_c = INFINITY;
+        S.best_i = 0x7fffffff;
+        for (int k = 0; k < 6; ++k) S.work[k] = 0ull;
+    }
 
-    for (int env = blockIdx.x * GPB + G.grp; env < a.N; env += gridDim.x * GPB) {
+    for (int slot = blockIdx.x * GPB + G.grp; slot < a.N; slot += gridDim.x * GPB) {
+        const int env = a.order ? __ldg(a.order + slot) : slot;
         int st = a.status[env];
         const float4 P0 = a.pose[2 * env], P1 = a.pose[2 * env + 1];
         const float4 V0 = a.vel[2 * env], V1 = a.vel[2 * env + 1];
@@ -273,10 +382,6 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         const int ncl = (NS + kCluster - 1) / kCluster;
         const float inv_ncl = 1.0f / (float)ncl;
         const int cfirst = __ldg(sc.cl_first + shp);
-        S6 Jb;
-        Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
-        Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
-        Jb.xz = __ldg(sc.shape_jinv + 6 * shp + 4); Jb.yz = __ldg(sc.shape_jinv + 6 * shp + 5);
 
         for (int fr = 0; fr < a.n_frames; ++fr) {
             for (int k = G.tid; k < 3 * P; k += TPE) S.padacc[k] = 0.0f;
@@ -288,6 +393,10 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 const V3 v_pred = v + grav;
                 const V3 w_pred = w;
                 const M3 R = qmat(q);
+                S6 Jb;   // inverse unit inertia, re-read (L1) rather than held in registers
+                Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
+                Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
+                Jb.xz = __ldg(sc.shape_jinv + 6 * shp + 4); Jb.yz = __ldg(sc.shape_jinv + 6 * shp + 5);
                 const S6 Wi = world_inv_inertia(R, Jb, inv_m);
 
                 // -- 1. spheres and cluster centres to world (relative to x), cached
@@ -362,80 +471,91 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 }
                 G.sync();
 
-                // -- 3b. narrowphase over the spheres of the surviving pairs, in pair order
+                // -- 3b. narrowphase over the spheres of the surviving pairs, in pair order;
+                //        each thread tests two pairs per round (two independent chains)
                 int nc = 0;
                 const int npairs = nclp * kCluster;
-                for (int p0 = 0; p0 < npairs; p0 += TPE) {
-                    const int p = p0 + G.tid;
-                    bool hit = false;
-                    Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
-                    V3 r = mk(0, 0, 0);
-                    int l = 0;
-                    if (p < npairs) {
-                        const int e = S.clp[p / kCluster];
-                        const int j = (e & 0xff) * kCluster + (p % kCluster);
-                        l = S.links[e >> 8];
-                        if (j < NS) {
-                            const float4 sp = sph[j];
-                            const V3 cr = xyz(sp);
-                            const float4 A0 = __ldg(L0 + l * kLinkStride);
-                            const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
-                            const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
-                            if (l == 0) {
-                                hh = hit_box(x + cr, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
-                            } else {
-                                const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-                                hh = hit_capsule((x - xyz(A0)) + cr, sp.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
-                            }
-                            hit = hh.gap < cfg.margin;
-                            r = cr - hh.n * sp.w;
-                        }
+                auto test_pair = [&](int p, Hit &hh, V3 &r, int &l) -> bool {
+                    if (p >= npairs) return false;
+                    const int e = S.clp[p / kCluster];
+                    const int j = (e & 0xff) * kCluster + (p % kCluster);
+                    l = S.links[e >> 8];
+                    if (j >= NS) return false;
+                    const float4 sp = sph[j];
+                    const V3 cr = xyz(sp);
+                    const float4 A0 = __ldg(L0 + l * kLinkStride);
+                    const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
+                    const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+                    if (l == 0) {
+                        hh = hit_box(x + cr, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                    } else {
+                        const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
+                        hh = hit_capsule((x - xyz(A0)) + cr, sp.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
                     }
-                    const unsigned bal = G.ballot(hit);
-                    int off = nc, tot;
+                    r = cr - hh.n * sp.w;
+                    return hh.gap < cfg.margin;
+                };
+                auto emit = [&](int idx, const Hit &hh, V3 r, int l) {
+                    if (idx >= cap) return;
+                    int pad = -1;
+                    const int npl = pl_cnt[l];
+                    for (int k = 0; k < npl; ++k) {
+                        const int pp = pl_id[l * kPadsPerLink + k];
+                        if (l == 0) { pad = pp; break; }
+                        const float s0 = p_s0[pp], s1 = p_s1[pp];
+                        if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
+                    }
+                    stage[idx][0] = make_float4(r.x, r.y, r.z, hh.gap);
+                    stage[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, __int_as_float(l | ((pad & 0xff) << 8)));
+                };
+                for (int p0 = 0; p0 < npairs; p0 += 2 * TPE) {
+                    Hit ha = {0.0f, mk(0, 0, 1), 0.0f}, hb = {0.0f, mk(0, 0, 1), 0.0f};
+                    V3 ra = mk(0, 0, 0), rb = mk(0, 0, 0);
+                    int la = 0, lb = 0;
+                    const bool hit_a = test_pair(p0 + G.tid, ha, ra, la);
+                    const bool hit_b = test_pair(p0 + TPE + G.tid, hb, rb, lb);
+                    const unsigned bal_a = G.ballot(hit_a), bal_b = G.ballot(hit_b);
+                    const unsigned below = (1u << G.lane_in_warp()) - 1u;
+                    int off_a = nc, off_b, tot;
                     if constexpr (TPE > 32) {
-                        int *cb = S.cnt[parity];
-                        if (G.lane == 0) cb[G.wid] = __popc(bal);
+                        int *cb = &S.cnt[parity][0];   // per warp: hits of the first and second halves
+                        if (G.lane == 0) { cb[2 * G.wid] = __popc(bal_a); cb[2 * G.wid + 1] = __popc(bal_b); }
                         G.sync();
-                        tot = 0;
+                        int tot_a = 0, pre_b = 0, tot_b = 0;
 #pragma unroll
                         for (int q2 = 0; q2 < W; ++q2) {
-                            const int c = cb[q2];
-                            if (q2 < G.wid) off += c;
-                            tot += c;
+                            const int ca = cb[2 * q2], cbb = cb[2 * q2 + 1];
+                            if (q2 < G.wid) { off_a += ca; pre_b += cbb; }
+                            tot_a += ca;
+                            tot_b += cbb;
                         }
+                        off_b = nc + tot_a + pre_b;
+                        tot = tot_a + tot_b;
                         parity ^= 1;
                     } else {
-                        tot = __popc(bal);
+                        off_b = nc + __popc(bal_a);
+                        tot = __popc(bal_a) + __popc(bal_b);
                     }
-                    if (hit) {
-                        const int idx = off + __popc(bal & ((1u << G.lane_in_warp()) - 1u));
-                        if (idx < CAP) {
-                            int pad = -1;
-                            const int npl = pl_cnt[l];
-                            for (int k = 0; k < npl; ++k) {
-                                const int pp = pl_id[l * kPadsPerLink + k];
-                                if (l == 0) { pad = pp; break; }
-                                const float s0 = p_s0[pp], s1 = p_s1[pp];
-                                if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
-                            }
-                            S.stage[idx][0] = make_float4(r.x, r.y, r.z, hh.gap);
-                            S.stage[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, __int_as_float(l | ((pad & 0xff) << 8)));
-                        }
-                    }
+                    if (hit_a) emit(off_a + __popc(bal_a & below), ha, ra, la);
+                    if (hit_b) emit(off_b + __popc(bal_b & below), hb, rb, lb);
                     nc += tot;
                 }
                 G.sync();
-                w_pairs += (unsigned long long)nclp * kCluster;
-                w_cl += ncpairs;
-                w_substeps += 1;
                 if (nc > cfg.c_max) {   // more contacts than the per-env capacity
                     st |= IH_ENV_OVERFLOW;
                     nc = 0;
                 }
-                w_contacts += nc;
+                if (G.tid == 0) {
+                    S.work[0] += (unsigned long long)nclp * kCluster;
+                    S.work[1] += nc;
+                    S.work[2] += nc > 0 ? (unsigned long long)nc * iters : 0ull;
+                    S.work[3] += 1;
+                    S.work[4] += nc > 0 ? iters : 0;
+                    S.work[5] += ncpairs;
+                }
 
-                // -- 4. contact setup in registers; contact range of each link
+                // -- 4. contact setup: the first TPE*CPL contacts in registers, the rest in
+                //       shared memory; the contact range of each link
                 V3 cr_[CPL], cn_[CPL], cc_[CPL], lam_[CPL];
                 float ikn_[CPL], ikt_[CPL];
                 const float trW = Wi.xx + Wi.yy + Wi.zz;
@@ -446,29 +566,23 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                     cr_[k] = mk(0, 0, 0); cn_[k] = mk(0, 0, 1); cc_[k] = mk(0, 0, 0);
                     ikn_[k] = 0.0f; ikt_[k] = 0.0f;
                     if (ci < nc) {
-                        const float4 s0 = S.stage[ci][0], s1 = S.stage[ci][1];
-                        const V3 r = xyz(s0), n = xyz(s1);
+                        const float4 s0 = stage[ci][0], s1 = stage[ci][1];
                         const int l = __float_as_int(s1.w) & 0xff;
-                        if (ci == 0 || (__float_as_int(S.stage[ci - 1][1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
-                        if (ci == nc - 1 || (__float_as_int(S.stage[ci + 1][1].w) & 0xff) != l)
-                            S.lend[l] = (unsigned short)(ci + 1);
-                        // k_n = 1/m + (r x n)^T W (r x n); tr K = 3/m + |r|^2 tr W - r^T W r
-                        const V3 rn = cross(r, n);
-                        const float kn = inv_m + dot(rn, smul(Wi, rn));
-                        const float trK = 3.0f * inv_m + dot(r, r) * trW - dot(r, smul(Wi, r));
-                        ikn_[k] = 1.0f / kn;
-                        ikt_[k] = 2.0f / (trK - kn);
-                        const float b = contact_bias(cfg, s0.w);
-                        V3 vl = mk(0, 0, 0);
-                        if (l != 0) {
-                            const float4 A0 = __ldg(L0 + l * kLinkStride), B0 = __ldg(L1 + l * kLinkStride);
-                            const float4 Aq = __ldg(L0 + l * kLinkStride + 2), Bq = __ldg(L1 + l * kLinkStride + 2);
-                            const Q4 qa = {Aq.x, Aq.y, Aq.z, Aq.w}, qb = {Bq.x, Bq.y, Bq.z, Bq.w};
-                            const V3 pl = qrot_inv(qa, (x - xyz(A0)) + r);   // contact in link coords
-                            vl = ((xyz(B0) - xyz(A0)) + (qrot(qb, pl) - qrot(qa, pl))) * inv_h;
-                        }
-                        cr_[k] = r; cn_[k] = n; cc_[k] = vl - n * b;
+                        if (ci == 0 || (__float_as_int(stage[ci - 1][1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
+                        if (ci == nc - 1 || (__float_as_int(stage[ci + 1][1].w) & 0xff) != l) S.lend[l] = (unsigned short)(ci + 1);
+                        const CSetup cs = setup_contact(xyz(s0), xyz(s1), s0.w, l, Wi, trW, inv_m, cfg, L0, L1, x, inv_h);
+                        cr_[k] = xyz(s0); cn_[k] = xyz(s1); cc_[k] = cs.cc; ikn_[k] = cs.ikn; ikt_[k] = cs.ikt;
                     }
+                }
+                for (int ci = RCAP + G.tid; ci < nc; ci += TPE) {
+                    const float4 s0 = stage[ci][0], s1 = stage[ci][1];
+                    const int l = __float_as_int(s1.w) & 0xff;
+                    if ((__float_as_int(stage[ci - 1][1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
+                    if (ci == nc - 1 || (__float_as_int(stage[ci + 1][1].w) & 0xff) != l) S.lend[l] = (unsigned short)(ci + 1);
+                    const CSetup cs = setup_contact(xyz(s0), xyz(s1), s0.w, l, Wi, trW, inv_m, cfg, L0, L1, x, inv_h);
+                    stage[ci][0].w = cs.ikt;
+                    stage[ci][2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikn);
+                    stage[ci][3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 }
 
                 // -- 5. Jacobi projected-impulse iterations
@@ -480,29 +594,25 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
 #pragma unroll
                         for (int k = 0; k < CPL; ++k) {
                             if (G.tid + k * TPE < nc) {
-                                const V3 n = cn_[k];
-                                const V3 u = vv + cross(ww, cr_[k]) - cc_[k];
-                                const float un = dot(u, n);
-                                const float l_old = dot(lam_[k], n);
-                                const float ln = fmaxf(l_old - un * ikn_[k], 0.0f);
-                                V3 lt = (lam_[k] - n * l_old) - (u - n * un) * ikt_[k];
-                                const float tn2 = dot(lt, lt);
-                                const float lim = mu * ln;
-                                if (tn2 > lim * lim) lt = lt * (lim * rsqrtf(tn2));
-                                const V3 lp = n * ln + lt;
-                                lam_[k] = lam_[k] + (lp - lam_[k]) * inv_nc;
+                                lam_[k] = update_contact(lam_[k], cr_[k], cn_[k], cc_[k], ikn_[k], ikt_[k], vv, ww, mu, inv_nc);
                                 const V3 tq = cross(cr_[k], lam_[k]);
                                 acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
                                 acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                             }
+                        }
+                        for (int ci = RCAP + G.tid; ci < nc; ci += TPE) {
+                            const float4 s0 = stage[ci][0], s1 = stage[ci][1], s2 = stage[ci][2], s3 = stage[ci][3];
+                            const V3 lam = update_contact(xyz(s3), xyz(s0), xyz(s1), xyz(s2), s2.w, s0.w, vv, ww, mu, inv_nc);
+                            stage[ci][3] = make_float4(lam.x, lam.y, lam.z, 0.0f);
+                            const V3 tq = cross(xyz(s0), lam);
+                            acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
+                            acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                         }
                         group_sum6<TPE>(acc, G, &S.red[0][0][0], parity);
                         parity ^= 1;
                         vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
                         ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
                     }
-                    w_citers += (unsigned long long)nc * iters;
-                    w_iters += iters;
                 }
                 v = vv;
                 w = ww;
@@ -521,11 +631,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const int ci = G.tid + k * TPE;
-                    if (ci < nc) {
-                        float4 s0 = S.stage[ci][0];
-                        s0.x = lam_[k].x; s0.y = lam_[k].y; s0.z = lam_[k].z;
-                        S.stage[ci][0] = s0;
-                    }
+                    if (ci < nc) stage[ci][3] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
                 }
                 G.sync();
                 for (int p = G.tid; p < P; p += TPE) {
@@ -533,10 +639,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
                     const int e = S.lend[l];
                     for (int ci = S.lbeg[l]; ci < e; ++ci) {
-                        const float4 s1 = S.stage[ci][1];
-                        if (((__float_as_int(s1.w) >> 8) & 0xff) != p) continue;
-                        const float4 s0 = S.stage[ci][0];
-                        fx -= s0.x * inv_h; fy -= s0.y * inv_h; fz -= s0.z * inv_h;
+                        if (((__float_as_int(stage[ci][1].w) >> 8) & 0xff) != p) continue;
+                        const float4 s3 = stage[ci][3];
+                        fx -= s3.x * inv_h; fy -= s3.y * inv_h; fz -= s3.z * inv_h;
                     }
                     S.padacc[3 * p + 0] += fx;
                     S.padacc[3 * p + 1] += fy;
@@ -601,14 +706,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         }
         G.sync();
     }
-    if (G.tid == 0 && a.work) {
-        atomicAdd(a.work + 0, w_pairs);
-        atomicAdd(a.work + 1, w_contacts);
-        atomicAdd(a.work + 2, w_citers);
-        atomicAdd(a.work + 3, w_substeps);
-        atomicAdd(a.work + 4, w_iters);
-        atomicAdd(a.work + 5, w_cl);
-    }
+    if (G.tid == 0 && a.work)
+        for (int k = 0; k < 6; ++k)
+            if (S.work[k]) atomicAdd(a.work + k, S.work[k]);
     if (!scored) return;
     // argmin (C_i, i) over the grid: per-block candidate, then the last block
     __shared__ bool last;
@@ -619,7 +719,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         double bc = INFINITY;
         int bi = 0x7fffffff;
         for (int g2 = 0; g2 < GPB; ++g2) {
-            const GSm<CAP, W> &S2 = reinterpret_cast<GSm<CAP, W> *>(smem + block_smem_bytes())[g2];
+            const GSm<W> &S2 = *reinterpret_cast<const GSm<W> *>(smem + block_smem_bytes() + g2 * gsm_bytes<W>());
             const double c = S2.best_c;
             const int i = S2.best_i;
             if (c < bc || (c == bc && i < bi)) { bc = c; bi = i; }
@@ -648,6 +748,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         }
         if (threadIdx.x == 0) {
             const int best = (bi == 0x7fffffff) ? 0 : bi;
+            int *argmin_out = a.argmin_out;
+            if (a.win) argmin_out = a.win->argmin ? a.win->argmin + a.win_k : nullptr;
             *a.argmin_state = best;
             if (argmin_out) *argmin_out = best;
             *a.n_window = n_win;
@@ -656,6 +758,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         }
     }
     __syncthreads();
+    float *est_out = a.est_pose_out;
+    if (a.win) est_out = a.win->est ? a.win->est + 8 * a.win_k : nullptr;
     if (est_out && threadIdx.x < 8) {
         const float4 p = __ldcg(a.pose + 2 * best_env + (threadIdx.x >> 2));
         const float v[4] = {p.x, p.y, p.z, p.w};
@@ -664,30 +768,30 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
 }
 
 template <int TPE, int CPL>
-size_t bytes_t(int s_max) {
+size_t bytes_t(int s_max, int c_max) {
     constexpr int GPB = Group<TPE>::GPB;
-    return block_smem_bytes() + GPB * gsm_bytes<TPE * CPL, Group<TPE>::W>() +
-           GPB * cache_floats4(s_max) * sizeof(float4);
+    return block_smem_bytes() + GPB * gsm_bytes<Group<TPE>::W>() + GPB * group_dyn_floats4(s_max, c_max) * sizeof(float4);
 }
 
 template <int TPE, int CPL>
-cudaError_t prepare_t(int s_max) {
-    const size_t bytes = bytes_t<TPE, CPL>(s_max);
+cudaError_t prepare_t(int s_max, int c_max) {
+    const size_t bytes = bytes_t<TPE, CPL>(s_max, c_max);
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(step_kernel<TPE, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int TPE, int CPL>
 cudaError_t launch_t(const StepArgs &a, int grid, int s_max, cudaStream_t s) {
-    step_kernel<TPE, CPL><<<grid, kBlock, bytes_t<TPE, CPL>(s_max), s>>>(a, s_max);
+    step_kernel<TPE, CPL><<<grid, kBlock, bytes_t<TPE, CPL>(s_max, a.cfg.c_max), s>>>(a, s_max);
     return cudaGetLastError();
 }
 
-#define IH_STEP_VARIANTS(X) X(16, 8) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 1) X(128, 2)
+#define IH_STEP_VARIANTS(X) X(16, 2) X(16, 4) X(32, 1) X(32, 2) X(32, 3) X(32, 4) X(64, 1) X(64, 2) X(128, 1)
 
 }  // namespace
 
-int step_variant_max_contacts(const StepVariant &v) { return v.group * v.cpl; }
+// every shape holds any c_max <= IH_MAX_CONTACTS (contacts beyond its registers live in shared memory)
+int step_variant_max_contacts(const StepVariant &v) { return v.group > 0 ? IH_MAX_CONTACTS : 0; }
 
 bool step_variant_supported(const StepVariant &v) {
     if (v.block != kBlock) return false;
@@ -705,15 +809,15 @@ int step_variant_list(StepVariant *out, int cap) {
     return n;
 }
 
-size_t step_smem_bytes(const StepVariant &v, int s_max) {
-#define IH_BYTES(T, C) if (v.group == T && v.cpl == C) return bytes_t<T, C>(s_max);
+size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max) {
+#define IH_BYTES(T, C) if (v.group == T && v.cpl == C) return bytes_t<T, C>(s_max, c_max);
     IH_STEP_VARIANTS(IH_BYTES)
 #undef IH_BYTES
     return 0;
 }
 
-cudaError_t step_prepare(const StepVariant &v, int s_max) {
-#define IH_PREP(T, C) if (v.group == T && v.cpl == C) return prepare_t<T, C>(s_max);
+cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max) {
+#define IH_PREP(T, C) if (v.group == T && v.cpl == C) return prepare_t<T, C>(s_max, c_max);
     IH_STEP_VARIANTS(IH_PREP)
 #undef IH_PREP
     return cudaErrorInvalidValue;

@@ -52,6 +52,17 @@ class Tracker:
             self.gt_pose[f].copy_(self.gt.sim_get_state()[0][0])
         self.sim.sim_sample_initial(wl.nominal_pose, wl.init.sigma_p, wl.init.sigma_r,
                                     wl.init.m_range, wl.init.mu_range)
+        n = self.n
+        if len(wl.scene.shapes) > 1 or not np.all(wl.iters[:n] == wl.sim.iters):
+            # uneven batch: each environment's own shape (resting at its own height) and
+            # solver iteration count
+            dz = np.array([W.nominal_pose_for(wl.scene, k)[2] - wl.nominal_pose[2]
+                           for k in range(len(wl.scene.shapes))], np.float32)
+            sid = torch.from_numpy(wl.shape_id[:n].astype(np.int32)).to(self.dev)
+            its = torch.from_numpy(wl.iters[:n].astype(np.int32)).to(self.dev)
+            pose, vel, par, _ = self.sim.sim_get_state()
+            pose[:, 2] += torch.from_numpy(dz).to(self.dev)[sid.long()]
+            self.sim.sim_set_state(pose, vel, par, sid, its)
         torch.cuda.synchronize()
 
     def window(self, w: int):
