@@ -300,6 +300,54 @@ ih_status cost_eval_static(const float *forces, const float *obs, const int32_t 
                            float w_contact, double *c_sum, int32_t n_window, double *cost_mean,
                            int32_t *argmin, void *stream);
 
+/* Gradient of the tracking cost over a horizon, by reverse mode (the
+ * derivative that the gradient-based refinement of the estimate needs; the
+ * paper optimises without it, Sec. III-D, and this call adds it).
+ *
+ * For each selected environment i, from its current state (the state at the
+ * start of frame0; left unchanged), the horizon's cost
+ *   L_i = sum_{f = frame0}^{frame0 + horizon - 1} sum_l [ w_force |c_il,f - o_l,f|^2
+ *                                                         + w_contact (contact-state mismatch) ]
+ * (Sec. III-C on the frame step of Sec. III-A) and its derivatives with respect
+ * to the initial position, the initial rotation (as a world-frame rotation
+ * vector d applied on the left, q -> exp(d) q, at d = 0), the mass and the
+ * friction coefficient. The contact-state terms are piecewise constant and
+ * contribute no derivative. Derivatives of the two projections of the Jacobi
+ * update are smoothed (the forward values stay exact): max(0, z) takes
+ * sigmoid(beta z), and the radial clamp of a tangential impulse z onto the
+ * Coulomb disk of radius L takes the derivative of z smin(|z|, L)/|z| with
+ * smin(a, b) = (a + b - sqrt((a - b)^2 + (width b)^2)) / 2. Contact
+ * membership, capsule end clamps, palm face choice and bias regimes are held
+ * fixed. The state after every checkpoint_every-th frame is kept; the
+ * reverse sweep recomputes the forward between checkpoints and, per substep,
+ * once more with a record of the Jacobi iterations.
+ *
+ * obs        device float[horizon][P][3]  observed pad forces of each frame
+ * envs       device int32[n] or NULL      environments to differentiate
+ *                                         (NULL: environments 0..n-1)
+ * n          1..N
+ * beta       > 0, slope of the smoothed normal clamp (1 / (N s))
+ * width      > 0, relative width of the smoothed disk clamp
+ * cost       device double[n] or NULL     L_i (FP64, as the scored step; +inf
+ *                                         for an environment that diverges or
+ *                                         is invalid, NaN for an index outside
+ *                                         [0, N))
+ * grad       device float[n][8]           dL/d(x, y, z, rx, ry, rz, m, mu)
+ *                                         (zero where the cost is not finite)
+ * grad_quat  device float[n][4] or NULL   dL/d(q_w, q_x, q_y, q_z) of the
+ *                                         initial quaternion's components
+ *
+ * Scratch: the handle grows a buffer of about (16 c_max (iters + 6) + 16
+ * (horizon / checkpoint_every + 2 checkpoint_every substeps)) floats per
+ * selected environment and keeps it until sim_destroy. Synchronises the stream
+ * once to size it (the largest iteration count among the selected
+ * environments is read back), so the call cannot be captured in a graph.
+ * Errors: IH_ERR_ARG (frames without commands, n or a constant out of range,
+ * null obs or grad), IH_ERR_OOM. */
+ih_status sim_adjoint(ih_sim *sim, int32_t frame0, int32_t horizon, int32_t checkpoint_every,
+                      const float *obs, const int32_t *envs, int32_t n, float beta, float width,
+                      double *cost, float *grad, float *grad_quat);
+
 /* Wait for the handle's stream; IH_ERR_CUDA if a kernel failed. */
 ih_status sim_sync(ih_sim *sim);
 

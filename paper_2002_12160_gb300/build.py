@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libinhand.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["step.cu", "setup.cu", "cost.cu", "optim.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["step.cu", "adjoint.cu", "setup.cu", "cost.cu", "optim.cu", "api.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:
@@ -45,7 +45,8 @@ def _stale(out: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, out_dir: str | None = None) -> str:
     obj_dir = out_dir or os.path.join(HERE, "_build")
     os.makedirs(obj_dir, exist_ok=True)
-    headers = [os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "inhand.h")]
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cuh")]
+    headers.append(os.path.join(INCLUDE, "inhand.h"))
     cc = nvcc()
 
     def one(src):

@@ -1,0 +1,807 @@
+// adjoint.cu -- reverse-mode derivative of the tracking cost with respect to
+// each environment's initial pose, mass and friction coefficient.
+//
+// The cost of one environment over the frames [frame0, frame0 + H) is
+//     L = sum_f sum_l w_force |c_f^(l) - o_f^(l)|^2  (+ contact-state terms)
+// -- the tracking cost of Sec. III-C on the simulated pad forces c_f of the
+// frame step s_{t+1} = f(s_t, u_t, theta) of Sec. III-A. The contact-state
+// terms are piecewise constant and carry no derivative. The gradient is taken
+// by hand-written reverse mode through every operation of the step: sphere
+// positions, narrowphase gaps, normals and lever arms, effective masses, bias
+// and link velocities, the fixed number of projected Jacobi iterations, and
+// the integrator (the same arithmetic as step.cu, through contact.cuh).
+//
+// The projections of the Jacobi update are not differentiable on the cone's
+// boundary. The reverse sweep therefore uses smooth stand-ins for their
+// derivatives only; the forward values stay exact:
+//   * normal clamp max(0, z): the derivative sigmoid(beta z) of a softplus;
+//   * radial clamp of the tangential impulse z onto the disk of radius L:
+//     the derivative of z smin(|z|, L) / |z| with
+//     smin(a, b) = (a + b - sqrt((a - b)^2 + (w b)^2)) / 2.
+// Contact membership (gap < margin), the capsule's end clamps, the palm's face
+// or clamp pattern and the bias regimes are held fixed.
+//
+// Work layout: one warp per environment, contacts strided over the lanes in
+// contact order (lane k % 32 owns contact k). The state at every K-th frame is
+// kept (checkpoints). The reverse sweep walks the segments between checkpoints
+// backwards: it recomputes the segment's substep start states and pad forces
+// from its checkpoint, then for each substep in reverse order recomputes the
+// substep once more while recording the impulses after every Jacobi iteration
+// and the per-iteration impulse sums (the tape), and runs that substep's
+// reverse sweep. Checkpoints, segment states and the tape live in a slice of
+// a scratch buffer owned by the handle, one slice per environment.
+#include "contact.cuh"
+#include "internal.cuh"
+
+namespace ih {
+namespace {
+
+constexpr int kAW = 4;   // environments (warps) per CTA
+constexpr int kABlock = 32 * kAW;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Body {
+    V3 x;
+    Q4 q;
+    V3 v, w;
+};
+struct Adj {   // derivatives of the cost w.r.t. a Body's components
+    V3 x;
+    Q4 q;
+    V3 v, w;
+};
+
+__device__ __forceinline__ void store_body(float4 *p, const Body &b) {
+    p[0] = make_float4(b.x.x, b.x.y, b.x.z, 0.0f);
+    p[1] = make_float4(b.q.w, b.q.x, b.q.y, b.q.z);
+    p[2] = make_float4(b.v.x, b.v.y, b.v.z, 0.0f);
+    p[3] = make_float4(b.w.x, b.w.y, b.w.z, 0.0f);
+}
+__device__ __forceinline__ Body load_body(const float4 *p) {
+    const float4 a = p[0], b = p[1], c = p[2], d = p[3];
+    return Body{xyz(a), Q4{b.x, b.y, b.z, b.w}, xyz(c), xyz(d)};
+}
+__device__ __forceinline__ Q4 qconj(Q4 q) { return {q.w, -q.x, -q.y, -q.z}; }
+
+struct WarpSm {
+    float padacc[IH_MAX_PADS * 3];
+    float fbar[IH_MAX_PADS * 3];   // dL/dF_p / (h ns): minus the derivative w.r.t. a final impulse
+    unsigned short lbeg[32], lend[32];
+};
+
+// Per-slot scratch layout in floats (every part starts on a float4 boundary).
+struct SlotLayout {
+    size_t ck, sg, sf, rec, lamh, lamf, sh, total;
+};
+__host__ __device__ inline size_t round4(size_t x) { return (x + 3) & ~size_t(3); }
+__host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, int cap, int iters_max) {
+    SlotLayout L;
+    size_t o = 0;
+    const size_t nck = (size_t)((H + K - 1) / K);
+    L.ck = o;   o += round4(nck * 16);                        // checkpoint states
+    L.sg = o;   o += round4((size_t)K * ns * 16);             // substep start states of a segment
+    L.sf = o;   o += round4((size_t)K * P * 3);               // pad forces of a segment's frames
+    L.rec = o;  o += round4((size_t)cap * 16);                // contact records
+    L.lamh = o; o += round4((size_t)iters_max * cap * 4);     // impulse after each iteration
+    L.lamf = o; o += round4((size_t)cap * 4);                 // final impulses (untaped passes)
+    L.sh = o;   o += round4((size_t)(iters_max > 0 ? iters_max : 1) * 8);   // sums after each iteration
+    L.total = o;
+    return L;
+}
+
+struct SlotPtr {
+    float4 *ck, *sg, *rec, *lamh, *lamf;
+    float *sf, *sh;
+};
+
+// Per-environment constants.
+struct Env {
+    int sfirst, NS, iters;
+    float mu, inv_m, bound;
+    S6 Jb;
+};
+
+// contact record: [0] (r, gap) [1] (n, 1/k_n) [2] (c, 1/k_t) [3] (t, link | pad << 8, sphere, -)
+__device__ __forceinline__ int rec_link(float4 r3) { return __float_as_int(r3.y) & 0xff; }
+__device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y) >> 8) & 0xff; }
+
+// One substep of one environment (the arithmetic of step.cu, contacts in the
+// same order: link, then sphere). With TAPE the impulses after every
+// iteration and the iteration sums are recorded; without, the pad forces of
+// the substep are added to S.padacc. Returns the contact count (0 on overflow).
+template <int PL, bool TAPE>
+__device__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4 *L0, const float4 *L1,
+                           const SlotPtr &sp, WarpSm &S, int lane, int &st) {
+    const DevScene &sc = a.sc;
+    const DevConfig &cfg = a.cfg;
+    const int Lk = sc.n_links, P = sc.n_pads, cap = cfg.c_max;
+    const float h = cfg.h, inv_h = 1.0f / h, inv_L = 1.0f / sc.link_len;
+    const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
+    const V3 v_pred = b.v + grav;
+    const V3 w_pred = b.w;
+    const M3 R = qmat(b.q);
+    const S6 Wi = world_inv_inertia(R, E.Jb, E.inv_m);
+
+    const bool keep = lane < Lk && link_reaches(sc, cfg, L0, lane, b.x, E.bound);
+    const unsigned surv = __ballot_sync(kFull, keep);
+    S.lbeg[lane] = 0;
+    S.lend[lane] = 0;
+    __syncwarp();
+    int nc = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (unsigned ms = surv; ms; ms &= ms - 1u) {
+        const int l = __ffs(ms) - 1;
+        const int first = nc;
+        const float4 A0 = __ldg(L0 + l * kLinkStride);
+        const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
+        const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+        const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
+        for (int j0 = 0; j0 < E.NS; j0 += 32) {
+            const int j = j0 + lane;
+            bool hit = false;
+            Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
+            V3 r = mk(0, 0, 0);
+            if (j < E.NS) {
+                const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
+                const V3 cr = mmul(R, xyz(s4));
+                if (l == 0) hh = hit_box(b.x + cr, s4.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                else hh = hit_capsule((b.x - xyz(A0)) + cr, s4.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+                r = cr - hh.n * s4.w;
+                hit = hh.gap < cfg.margin;
+            }
+            const unsigned bal = __ballot_sync(kFull, hit);
+            const int idx = nc + __popc(bal & below);
+            if (hit && idx < cap) {
+                int pad = -1;
+                for (int p = 0; p < P; ++p) {   // first pad of the link whose interval holds t
+                    if (__ldg(sc.pad_link + p) != l) continue;
+                    if (l == 0) { pad = p; break; }
+                    const float s0 = __ldg(sc.pad_s0 + p), s1 = __ldg(sc.pad_s1 + p);
+                    if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = p; break; }
+                }
+                float4 *rc = sp.rec + 4 * idx;
+                rc[0] = make_float4(r.x, r.y, r.z, hh.gap);
+                rc[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, 0.0f);
+                rc[3] = make_float4(hh.t, __int_as_float(l | ((pad & 0xff) << 8)), __int_as_float(j), 0.0f);
+            }
+            nc += __popc(bal);
+        }
+        if (lane == 0) {
+            S.lbeg[l] = (unsigned short)first;
+            S.lend[l] = (unsigned short)nc;
+        }
+    }
+    __syncwarp();
+    if (nc > cap) {   // more contacts than the per-env capacity: as the step, no contacts
+        st |= IH_ENV_OVERFLOW;
+        nc = 0;
+    }
+
+    // contact setup, by the lane that owns the contact from here on
+    const float trW = Wi.xx + Wi.yy + Wi.zz;
+    V3 lam_[PL];
+#pragma unroll
+    for (int k = 0; k < PL; ++k) {
+        lam_[k] = mk(0, 0, 0);
+        const int ci = lane + 32 * k;
+        if (ci < nc) {
+            float4 *rc = sp.rec + 4 * ci;
+            const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
+            const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, rec_link(r3), Wi, trW, E.inv_m, cfg, L0, L1, b.x,
+                                            inv_h);
+            rc[1] = make_float4(r1.x, r1.y, r1.z, cs.ikn);
+            rc[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikt);
+        }
+    }
+
+    // Jacobi projected-impulse iterations
+    V3 vv = v_pred, ww = w_pred;
+    if (nc > 0) {
+        const float inv_nc = 1.0f / (float)nc;
+        for (int it = 0; it < E.iters; ++it) {
+            float acc[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < PL; ++k) {
+                const int ci = lane + 32 * k;
+                if (ci < nc) {
+                    const float4 *rc = sp.rec + 4 * ci;
+                    const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
+                    lam_[k] = update_contact(lam_[k], xyz(r0), xyz(r1), xyz(r2), r1.w, r2.w, vv, ww, E.mu, inv_nc);
+                    const V3 tq = cross(xyz(r0), lam_[k]);
+                    acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
+                    acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                    if (TAPE) sp.lamh[(size_t)it * cap + ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
+                }
+            }
+            width_sum6<32>(acc, kFull, lane);
+            if (TAPE && lane == 0)
+                for (int q = 0; q < 6; ++q) sp.sh[8 * it + q] = acc[q];
+            vv = v_pred + mk(acc[0], acc[1], acc[2]) * E.inv_m;
+            ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
+        }
+    }
+    b.v = vv;
+    b.w = ww;
+    b.x = b.x + b.v * h;
+    {
+        const float wn = sqrtf(dot(b.w, b.w));
+        float sn, cs;
+        sincosf(0.5f * wn * h, &sn, &cs);
+        const float kq = (wn > 0.0f) ? sn / wn : 0.5f * h;
+        b.q = qnorm(qmul({cs, b.w.x * kq, b.w.y * kq, b.w.z * kq}, b.q));
+    }
+    if (!TAPE) {
+        // pad forces -lambda / h, each pad summing the contacts of its link in order
+#pragma unroll
+        for (int k = 0; k < PL; ++k) {
+            const int ci = lane + 32 * k;
+            if (ci < nc) sp.lamf[ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
+        }
+        __syncwarp();
+        if (lane < P && nc > 0) {
+            const int l = __ldg(sc.pad_link + lane);
+            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+            const int e = S.lend[l];
+            for (int ci = S.lbeg[l]; ci < e; ++ci) {
+                if (rec_pad(sp.rec[4 * ci + 3]) != lane) continue;
+                const float4 lf = sp.lamf[ci];
+                fx -= lf.x * inv_h; fy -= lf.y * inv_h; fz -= lf.z * inv_h;
+            }
+            S.padacc[3 * lane + 0] += fx;
+            S.padacc[3 * lane + 1] += fy;
+            S.padacc[3 * lane + 2] += fz;
+        }
+    }
+    __syncwarp();
+    return nc;
+}
+
+// d bias / d gap (contact_bias: gap / h when separated, else the clamped
+// Baumgarte term)
+__device__ __forceinline__ float bias_slope(const DevConfig &cfg, float gap) {
+    if (gap > 0.0f) return 1.0f / cfg.h;
+    const float z = gap + cfg.slop;
+    if (!(z < 0.0f)) return 0.0f;
+    return (cfg.beta * z / cfg.h > -cfg.vmax) ? cfg.beta / cfg.h : 0.0f;
+}
+
+__device__ __forceinline__ float sigmoid(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Reverse of the smoothed radial clamp out = z smin(|z|, L) / |z| for the
+// incoming derivative g: returns dL/dz and dL/dL. At z = 0 exactly the
+// derivative of the exact clamp inside the disk (identity) is used.
+__device__ __forceinline__ void disk_bwd(V3 z, float L, V3 g, float w, V3 &zb, float &Lb) {
+    const float a2 = dot(z, z);
+    if (!(a2 > 0.0f)) {
+        zb = (L > 0.0f) ? g : mk(0, 0, 0);
+        Lb = 0.0f;
+        return;
+    }
+    const float a = sqrtf(a2);
+    const float dl = a - L;
+    const float Q = sqrtf(dl * dl + (w * L) * (w * L));
+    const float phi = 0.5f * (a + L - Q);
+    const float pa = 0.5f * (1.0f - dl / Q);
+    const float pb = 0.5f * (1.0f + (dl - w * w * L) / Q);
+    const V3 zh = z * (1.0f / a);
+    const float s = dot(zh, g);
+    const float ra = phi / a;
+    zb = g * ra + zh * (s * (pa - ra));
+    Lb = s * pb;
+}
+
+// Reverse of the narrowphase (hit_box / hit_capsule) for the sphere centred
+// at x + cr: the derivative w.r.t. the centre given those w.r.t. gap and n.
+__device__ __forceinline__ V3 hit_bwd(const DevScene &sc, int l, V3 x, V3 cr, const float4 *L0, float gb, V3 nb) {
+    const float4 A0 = __ldg(L0 + l * kLinkStride);
+    const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
+    const Q4 q = {Aq.x, Aq.y, Aq.z, Aq.w};
+    if (l == 0) {
+        const float hx = sc.palm_hx, hy = sc.palm_hy, hz = sc.palm_hz;
+        const V3 cl = qrot_inv(q, (x + cr) - xyz(A0));
+        const V3 k = mk(fminf(fmaxf(cl.x, -hx), hx), fminf(fmaxf(cl.y, -hy), hy), fminf(fmaxf(cl.z, -hz), hz));
+        V3 clb = mk(0, 0, 0);
+        if (!((k.x == cl.x) && (k.y == cl.y) && (k.z == cl.z))) {
+            const V3 d = cl - k;
+            const float inv = rsqrtf(dot(d, d));
+            const V3 nl = d * inv;
+            const V3 nlb = qrot_inv(q, nb);
+            const V3 db = (nlb - nl * dot(nl, nlb)) * inv + nl * gb;
+            clb = mk(k.x != cl.x ? db.x : 0.0f, k.y != cl.y ? db.y : 0.0f, k.z != cl.z ? db.z : 0.0f);
+        } else {   // the face hit_box chose; the normal is constant, gap = +-cl_axis - half - r
+            float best = hx - cl.x;
+            int face = 0;
+            if (hx + cl.x < best) { best = hx + cl.x; face = 1; }
+            if (hy - cl.y < best) { best = hy - cl.y; face = 2; }
+            if (hy + cl.y < best) { best = hy + cl.y; face = 3; }
+            if (hz - cl.z < best) { best = hz - cl.z; face = 4; }
+            if (hz + cl.z < best) { best = hz + cl.z; face = 5; }
+            const float g = (face & 1) ? -gb : gb;
+            clb = mk(face >> 1 == 0 ? g : 0.0f, face >> 1 == 1 ? g : 0.0f, face >> 1 == 2 ? g : 0.0f);
+        }
+        return qrot(q, clb);
+    }
+    const V3 ca = (x - xyz(A0)) + cr;
+    const V3 d = xyz(__ldg(L0 + l * kLinkStride + 1));
+    const float tr = dot(ca, d) * (1.0f / sc.link_len);
+    const float t = fminf(fmaxf(tr, 0.0f), 1.0f);
+    const V3 diff = ca - d * (t * sc.link_len);
+    const float d2 = dot(diff, diff);
+    if (d2 < 1e-18f) return mk(0, 0, 0);   // centre on the axis: constant normal and gap
+    const float inv = rsqrtf(d2);
+    const V3 n = diff * inv;
+    V3 db = (nb - n * dot(n, nb)) * inv + n * gb;
+    if (tr > 0.0f && tr < 1.0f) db = db - d * dot(d, db);   // t follows the centre inside the segment
+    return db;
+}
+
+__device__ __forceinline__ void outer_add(float (&M)[9], V3 a, V3 b, float s) {
+    const float av[3] = {a.x * s, a.y * s, a.z * s}, bv[3] = {b.x, b.y, b.z};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] += av[i] * bv[j];
+}
+
+// Reverse sweep of one substep from start state b (whose forward has just
+// been recomputed with a tape; nc contacts). On entry `ad` holds the
+// derivatives w.r.t. the substep's end state, on return those w.r.t. b.
+// invm_b (lane-uniform) and mu_b (per lane) accumulate d/d(1/m) and d/dmu.
+template <int PL>
+__device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const float4 *L0, const float4 *L1,
+                            int nc, const SlotPtr &sp, const WarpSm &S, int lane, Adj &ad, float &invm_b,
+                            float &mu_b) {
+    const DevScene &sc = a.sc;
+    const DevConfig &cfg = a.cfg;
+    const int cap = cfg.c_max, I = E.iters;
+    const float h = cfg.h, inv_h = 1.0f / h;
+    const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
+    const V3 v_pred = b.v + grav;
+    const V3 w_pred = b.w;
+    const M3 R = qmat(b.q);
+    const S6 Wi = world_inv_inertia(R, E.Jb, E.inv_m);
+    const float trW = Wi.xx + Wi.yy + Wi.zz;
+    const bool solved = nc > 0 && I > 0;
+    V3 Vf = v_pred, Wf = w_pred;   // body velocity after the solve
+    if (solved) {
+        const float *s = sp.sh + 8 * (I - 1);
+        Vf = v_pred + mk(s[0], s[1], s[2]) * E.inv_m;
+        Wf = w_pred + smul(Wi, mk(s[3], s[4], s[5]));
+    }
+
+    // -- integration: x' = x + h V, q' = normalize(exp(h W) q)
+    V3 Vb = ad.v + ad.x * h;
+    V3 Wb = ad.w;
+    Q4 qb;
+    {
+        const float wn = sqrtf(dot(Wf, Wf));
+        float sn, cs;
+        sincosf(0.5f * wn * h, &sn, &cs);
+        const float kq = (wn > 0.0f) ? sn / wn : 0.5f * h;
+        const Q4 e = {cs, Wf.x * kq, Wf.y * kq, Wf.z * kq};
+        const Q4 p = qmul(e, b.q);
+        const float s = rsqrtf(p.w * p.w + p.x * p.x + p.y * p.y + p.z * p.z);
+        const Q4 qn = {p.w * s, p.x * s, p.y * s, p.z * s};
+        const float dq = ad.q.w * qn.w + ad.q.x * qn.x + ad.q.y * qn.y + ad.q.z * qn.z;
+        const Q4 pb = {(ad.q.w - qn.w * dq) * s, (ad.q.x - qn.x * dq) * s, (ad.q.y - qn.y * dq) * s,
+                       (ad.q.z - qn.z * dq) * s};
+        qb = qmul(qconj(e), pb);                // p = e q: dq = L(e)^T dp
+        const Q4 eb = qmul(pb, qconj(b.q));     // de = R(q)^T dp
+        // e = (cos(th/2), s(th) A), A = h W, th = |A|, s(th) = sin(th/2) / th
+        const float th = wn * h;
+        const float sf = kq / h;
+        float ds;   // s'(th) / th
+        if (th < 0.25f) {
+            const float t2 = th * th;
+            ds = -1.0f / 24.0f + t2 * (1.0f / 960.0f - t2 * (1.0f / 107520.0f));
+        } else {
+            ds = (0.5f * th * cs - sn) / (th * th * th);
+        }
+        const V3 av = Wf * h;
+        const V3 ev = mk(eb.x, eb.y, eb.z);
+        const V3 ab = av * (-0.5f * sf * eb.w) + ev * sf + av * (ds * dot(av, ev));
+        Wb = Wb + ab * h;
+    }
+    V3 vpb = mk(0, 0, 0), wpb = mk(0, 0, 0);
+    float Wbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // d/dW, this lane's part
+    float Rbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // d/dR, this lane's part
+    V3 xb_l = mk(0, 0, 0);
+    float invm_l = 0.0f;
+    if (solved) {
+        const float inv_nc = 1.0f / (float)nc;
+        V3 lb[PL], nb[PL], rb[PL], cb[PL];
+        float iknb[PL], iktb[PL];
+#pragma unroll
+        for (int k = 0; k < PL; ++k) {
+            lb[k] = nb[k] = rb[k] = cb[k] = mk(0, 0, 0);
+            iknb[k] = iktb[k] = 0.0f;
+            const int ci = lane + 32 * k;
+            if (ci < nc) {
+                const int pad = rec_pad(sp.rec[4 * ci + 3]);
+                if (pad < sc.n_pads) lb[k] = mk(-S.fbar[3 * pad], -S.fbar[3 * pad + 1], -S.fbar[3 * pad + 2]);
+            }
+        }
+        for (int it = I - 1; it >= 0; --it) {
+            // (a) V^{it+1} = v_pred + S1 / m, W^{it+1} = w_pred + W S2, sums of the impulses after it
+            const float *s = sp.sh + 8 * it;
+            const V3 S1 = mk(s[0], s[1], s[2]), S2 = mk(s[3], s[4], s[5]);
+            vpb = vpb + Vb;
+            wpb = wpb + Wb;
+            if (lane == 0) {
+                invm_l += dot(Vb, S1);
+                outer_add(Wbar, Wb, S2, 1.0f);
+            }
+            const V3 g = smul(Wi, Wb);
+            const V3 vm = Vb * E.inv_m;
+#pragma unroll
+            for (int k = 0; k < PL; ++k) {
+                const int ci = lane + 32 * k;
+                if (ci < nc) {
+                    const V3 r = xyz(sp.rec[4 * ci]);
+                    const V3 l1 = xyz(sp.lamh[(size_t)it * cap + ci]);
+                    lb[k] = lb[k] + vm + cross(g, r);
+                    rb[k] = rb[k] + cross(l1, g);
+                }
+            }
+            // (b) the contact updates of iteration it, against V^it, W^it
+            V3 Vi = v_pred, Wv = w_pred;
+            if (it > 0) {
+                const float *s0 = sp.sh + 8 * (it - 1);
+                Vi = v_pred + mk(s0[0], s0[1], s0[2]) * E.inv_m;
+                Wv = w_pred + smul(Wi, mk(s0[3], s0[4], s0[5]));
+            }
+            float acc[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < PL; ++k) {
+                const int ci = lane + 32 * k;
+                if (ci < nc) {
+                    const float4 *rc = sp.rec + 4 * ci;
+                    const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
+                    const V3 r = xyz(r0), n = xyz(r1), cc = xyz(r2);
+                    const float ikn = r1.w, ikt = r2.w;
+                    const V3 l0 = it > 0 ? xyz(sp.lamh[(size_t)(it - 1) * cap + ci]) : mk(0, 0, 0);
+                    const V3 u = Vi + cross(Wv, r) - cc;
+                    const float un = dot(u, n), lo = dot(l0, n);
+                    const float zn = lo - un * ikn;
+                    const float ln = fmaxf(zn, 0.0f);
+                    const V3 ut = u - n * un;
+                    const V3 zt = (l0 - n * lo) - ut * ikt;
+                    const float L = E.mu * ln;
+                    // lambda' = lambda + (n ln + lt - lambda) / n_c
+                    const V3 lpb = lb[k] * inv_nc;
+                    lb[k] = lb[k] * (1.0f - inv_nc);
+                    float lnb = dot(n, lpb);
+                    nb[k] = nb[k] + lpb * ln;
+                    V3 ztb;
+                    float Lb;
+                    disk_bwd(zt, L, lpb, a.width, ztb, Lb);
+                    lnb += E.mu * Lb;
+                    mu_b += ln * Lb;
+                    const float znb = lnb * sigmoid(a.beta_s * zn);
+                    float lob = znb;
+                    float unb = -znb * ikn;
+                    iknb[k] -= znb * un;
+                    // zt = (l0 - n lo) - (u - n un) ikt
+                    const float nzt = dot(n, ztb);
+                    lb[k] = lb[k] + ztb;
+                    nb[k] = nb[k] - ztb * lo;
+                    lob -= nzt;
+                    V3 ub = ztb * (-ikt);
+                    nb[k] = nb[k] + ztb * (ikt * un);
+                    unb += ikt * nzt;
+                    iktb[k] -= dot(ut, ztb);
+                    // lo = l0 . n, un = u . n
+                    lb[k] = lb[k] + n * lob;
+                    nb[k] = nb[k] + l0 * lob;
+                    ub = ub + n * unb;
+                    nb[k] = nb[k] + u * unb;
+                    // u = V + W x r - c
+                    const V3 rxu = cross(r, ub);
+                    acc[0] += ub.x; acc[1] += ub.y; acc[2] += ub.z;
+                    acc[3] += rxu.x; acc[4] += rxu.y; acc[5] += rxu.z;
+                    rb[k] = rb[k] + cross(ub, Wv);
+                    cb[k] = cb[k] - ub;
+                }
+            }
+            width_sum6<32>(acc, kFull, lane);
+            Vb = mk(acc[0], acc[1], acc[2]);
+            Wb = mk(acc[3], acc[4], acc[5]);
+        }
+        vpb = vpb + Vb;   // V^0 = v_pred, W^0 = w_pred
+        wpb = wpb + Wb;
+
+        // contact setup and narrowphase, in reverse
+#pragma unroll
+        for (int k = 0; k < PL; ++k) {
+            const int ci = lane + 32 * k;
+            if (ci < nc) {
+                const float4 *rc = sp.rec + 4 * ci;
+                const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2], r3 = rc[3];
+                const V3 r = xyz(r0), n = xyz(r1);
+                const float gap = r0.w, ikn = r1.w, ikt = r2.w;
+                const int l = rec_link(r3), j = __float_as_int(r3.z);
+                // 1/k_n and 1/k_t = 2 / (tr K - k_n)
+                float knb = -iknb[k] * ikn * ikn;
+                const float Db = -iktb[k] * ikt * ikt * 0.5f;
+                const float trKb = Db;
+                knb -= Db;
+                // k_n = 1/m + (r x n) . W (r x n)
+                const V3 rn = cross(r, n);
+                const V3 rnb = smul(Wi, rn) * (2.0f * knb);
+                invm_l += knb + 3.0f * trKb;
+                outer_add(Wbar, rn, rn, knb);
+                rb[k] = rb[k] + cross(n, rnb);
+                nb[k] = nb[k] + cross(rnb, r);
+                // tr K = 3/m + |r|^2 tr W - r . W r
+                rb[k] = rb[k] + (r * (2.0f * trW) - smul(Wi, r) * 2.0f) * trKb;
+                const float rr = dot(r, r) * trKb;
+                Wbar[0] += rr; Wbar[4] += rr; Wbar[8] += rr;
+                outer_add(Wbar, r, r, -trKb);
+                // c = v_link - n b(gap)
+                const float bias = contact_bias(cfg, gap);
+                const float gb = -dot(n, cb[k]) * bias_slope(cfg, gap);
+                nb[k] = nb[k] - cb[k] * bias;
+                if (l != 0) {   // v_link = (T_end T_start^-1 p - p) / h, p = x + r
+                    const float4 Aq = __ldg(L0 + l * kLinkStride + 2), Bq = __ldg(L1 + l * kLinkStride + 2);
+                    const Q4 qa = {Aq.x, Aq.y, Aq.z, Aq.w}, qe = {Bq.x, Bq.y, Bq.z, Bq.w};
+                    const V3 yb = (qrot(qa, qrot_inv(qe, cb[k])) - cb[k]) * inv_h;
+                    xb_l = xb_l + yb;
+                    rb[k] = rb[k] + yb;
+                }
+                // r = R s_j - n r_j, gap and n from the sphere centre x + R s_j
+                const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
+                nb[k] = nb[k] - rb[k] * s4.w;
+                const V3 cr = mmul(R, xyz(s4));
+                const V3 hb = hit_bwd(sc, l, b.x, cr, L0, gb, nb[k]);
+                xb_l = xb_l + hb;
+                outer_add(Rbar, rb[k] + hb, xyz(s4), 1.0f);
+            }
+        }
+    } else {
+        vpb = vpb + Vb;
+        wpb = wpb + Wb;
+    }
+
+    // sum the lanes' parts: x (3), 1/m (1), W (9), R (9)
+    float r1[6] = {xb_l.x, xb_l.y, xb_l.z, invm_l, Wbar[0], Wbar[1]};
+    float r2[6] = {Wbar[2], Wbar[3], Wbar[4], Wbar[5], Wbar[6], Wbar[7]};
+    float r3[6] = {Wbar[8], Rbar[0], Rbar[1], Rbar[2], Rbar[3], Rbar[4]};
+    float r4[6] = {Rbar[5], Rbar[6], Rbar[7], Rbar[8], 0.0f, 0.0f};
+    width_sum6<32>(r1, kFull, lane);
+    width_sum6<32>(r2, kFull, lane);
+    width_sum6<32>(r3, kFull, lane);
+    width_sum6<32>(r4, kFull, lane);
+    const float Wt[9] = {r1[4], r1[5], r2[0], r2[1], r2[2], r2[3], r2[4], r2[5], r3[0]};
+    float Rt[9] = {r3[1], r3[2], r3[3], r3[4], r3[5], r4[0], r4[1], r4[2], r4[3]};
+    // W = R J R^T / m:  d/d(1/m) += <Wbar, R J R^T>,  Rbar += (Wbar + Wbar^T) R J / m
+    {
+        const float Rm[9] = {R.c0.x, R.c1.x, R.c2.x, R.c0.y, R.c1.y, R.c2.y, R.c0.z, R.c1.z, R.c2.z};
+        const float J[9] = {E.Jb.xx, E.Jb.xy, E.Jb.xz, E.Jb.xy, E.Jb.yy, E.Jb.yz, E.Jb.xz, E.Jb.yz, E.Jb.zz};
+        float RJ[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) RJ[3 * i + j] = Rm[3 * i] * J[j] + Rm[3 * i + 1] * J[3 + j] + Rm[3 * i + 2] * J[6 + j];
+        float inner = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float Mij = RJ[3 * i] * Rm[3 * j] + RJ[3 * i + 1] * Rm[3 * j + 1] + RJ[3 * i + 2] * Rm[3 * j + 2];
+                inner += Wt[3 * i + j] * Mij;
+            }
+        invm_b += r1[3] + inner;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float sacc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) sacc += (Wt[3 * i + k] + Wt[3 * k + i]) * RJ[3 * k + j];
+                Rt[3 * i + j] += sacc * E.inv_m;
+            }
+    }
+    // R(q) -> q (the polynomial map of qmat)
+    {
+        const Q4 q = b.q;
+        const float R00 = Rt[0], R01 = Rt[1], R02 = Rt[2], R10 = Rt[3], R11 = Rt[4], R12 = Rt[5], R20 = Rt[6],
+                    R21 = Rt[7], R22 = Rt[8];
+        qb.w += 2.0f * (q.z * (R10 - R01) + q.y * (R02 - R20) + q.x * (R21 - R12));
+        qb.x += 2.0f * (-2.0f * q.x * (R11 + R22) + q.y * (R10 + R01) + q.z * (R20 + R02) + q.w * (R21 - R12));
+        qb.y += 2.0f * (-2.0f * q.y * (R00 + R22) + q.x * (R10 + R01) + q.z * (R21 + R12) + q.w * (R02 - R20));
+        qb.z += 2.0f * (-2.0f * q.z * (R00 + R11) + q.x * (R20 + R02) + q.y * (R21 + R12) + q.w * (R10 - R01));
+    }
+    ad.x = ad.x + mk(r1[0], r1[1], r1[2]);
+    ad.q = qb;
+    ad.v = vpb;
+    ad.w = wpb;
+}
+
+template <int PL>
+__global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
+    __shared__ WarpSm sm[kAW];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * kAW + wid;
+    if (slot >= a.n) return;   // whole warps only
+    WarpSm &S = sm[wid];
+    const DevScene &sc = a.sc;
+    const DevConfig &cfg = a.cfg;
+    const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads, cap = cfg.c_max;
+    const int env = a.envs ? a.envs[slot] : slot;
+    if (env < 0 || env >= a.N) {   // not an environment of the handle
+        if (lane < 8) a.grad[8 * slot + lane] = 0.0f;
+        if (a.grad_quat && lane < 4) a.grad_quat[4 * slot + lane] = 0.0f;
+        if (lane == 0 && a.cost) a.cost[slot] = NAN;
+        return;
+    }
+    const SlotLayout Ly = slot_layout(a.H, a.K, ns, P, cap, a.iters_max);
+    float *base = a.scratch + (size_t)slot * a.stride;
+    SlotPtr sp;
+    sp.ck = reinterpret_cast<float4 *>(base + Ly.ck);
+    sp.sg = reinterpret_cast<float4 *>(base + Ly.sg);
+    sp.sf = base + Ly.sf;
+    sp.rec = reinterpret_cast<float4 *>(base + Ly.rec);
+    sp.lamh = reinterpret_cast<float4 *>(base + Ly.lamh);
+    sp.lamf = reinterpret_cast<float4 *>(base + Ly.lamf);
+    sp.sh = base + Ly.sh;
+
+    const float4 P0 = a.pose[2 * env], P1 = a.pose[2 * env + 1];
+    const float4 V0 = a.vel[2 * env], V1 = a.vel[2 * env + 1];
+    const float2 th = a.params[env];
+    const int shp = a.shape[env];
+    Env E;
+    E.sfirst = __ldg(sc.shape_first + shp);
+    E.NS = __ldg(sc.shape_count + shp);
+    E.iters = a.iters[env];
+    E.mu = th.y;
+    E.inv_m = 1.0f / th.x;
+    E.bound = __ldg(sc.shape_bound + shp);
+    E.Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); E.Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
+    E.Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); E.Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
+    E.Jb.xz = __ldg(sc.shape_jinv + 6 * shp + 4); E.Jb.yz = __ldg(sc.shape_jinv + 6 * shp + 5);
+    const Body b0 = {xyz(P0), Q4{P1.x, P1.y, P1.z, P1.w}, xyz(V0), xyz(V1)};
+    int st = a.status[env];
+    if (E.iters > a.iters_max) st |= IH_ENV_INVALID;   // the tape cannot hold its iterations
+
+    const float h = cfg.h, inv_h = 1.0f / h, inv_ns = 1.0f / (float)ns;
+    const size_t tab_frame = (size_t)(ns + 1) * Lk * kLinkStride;
+    const float4 *tab0 = a.link_tab + (size_t)a.frame0 * tab_frame;
+
+    // -- pass 1: the cost, and the state at every K-th frame
+    double cost = 0.0;
+    Body b = b0;
+    for (int f = 0; f < a.H && !(st & kDiverged); ++f) {
+        if (f % a.K == 0 && lane == 0) store_body(sp.ck + 4 * (f / a.K), b);
+        for (int k = lane; k < 3 * P; k += 32) S.padacc[k] = 0.0f;
+        __syncwarp();
+        const float4 *tab = tab0 + (size_t)f * tab_frame;
+        for (int s = 0; s < ns; ++s) {
+            const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
+            fwd_substep<PL, false>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st);
+        }
+        if (!all_finite(b.x, b.q, b.v, b.w)) st |= IH_ENV_NONFINITE;
+        else if (dot(b.x, b.x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
+        if (lane == 0) {   // frame cost in FP64, in pad order, as the scored step
+            const float *o = a.obs + (size_t)f * P * 3;
+            const double tau = (double)cfg.tau, tau2 = __dmul_rn(tau, tau), wf = (double)cfg.w_force;
+            double cf = 0.0;
+            for (int p = 0; p < P; ++p) {
+                const double fx = S.padacc[3 * p] * inv_ns, fy = S.padacc[3 * p + 1] * inv_ns,
+                             fz = S.padacc[3 * p + 2] * inv_ns;
+                const double ox = o[3 * p], oy = o[3 * p + 1], oz = o[3 * p + 2];
+                const double dx = __dsub_rn(fx, ox), dy = __dsub_rn(fy, oy), dz = __dsub_rn(fz, oz);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                cf = __dadd_rn(cf, __dmul_rn(wf, d2));
+                const double n2 = __dadd_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)), __dmul_rn(fz, fz));
+                const double no = __dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz));
+                if ((n2 > tau2) != (no > tau2)) cf = __dadd_rn(cf, (double)cfg.w_contact);
+            }
+            cost = __dadd_rn(cost, cf);
+        }
+        __syncwarp();
+    }
+    if (st & kDiverged) {   // no derivative of a diverged or invalid environment
+        if (lane < 8) a.grad[8 * slot + lane] = 0.0f;
+        if (a.grad_quat && lane < 4) a.grad_quat[4 * slot + lane] = 0.0f;
+        if (lane == 0 && a.cost) a.cost[slot] = INFINITY;
+        return;
+    }
+
+    // -- pass 2: segments in reverse
+    Adj ad = {mk(0, 0, 0), Q4{0, 0, 0, 0}, mk(0, 0, 0), mk(0, 0, 0)};
+    float invm_b = 0.0f, mu_b = 0.0f;
+    const int nck = (a.H + a.K - 1) / a.K;
+    const float wf2 = 2.0f * cfg.w_force * inv_h * inv_ns;
+    for (int seg = nck - 1; seg >= 0; --seg) {
+        const int fb = seg * a.K, fe = min(a.H, fb + a.K);
+        b = load_body(sp.ck + 4 * seg);
+        for (int f = fb; f < fe; ++f) {   // substep start states and frame forces of the segment
+            for (int k = lane; k < 3 * P; k += 32) S.padacc[k] = 0.0f;
+            __syncwarp();
+            const float4 *tab = tab0 + (size_t)f * tab_frame;
+            for (int s = 0; s < ns; ++s) {
+                if (lane == 0) store_body(sp.sg + 4 * ((f - fb) * ns + s), b);
+                const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
+                fwd_substep<PL, false>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st);
+            }
+            for (int k = lane; k < 3 * P; k += 32) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
+            __syncwarp();
+        }
+        for (int f = fe - 1; f >= fb; --f) {
+            const float *o = a.obs + (size_t)f * P * 3;
+            for (int k = lane; k < 3 * P; k += 32)
+                S.fbar[k] = wf2 * (sp.sf[(size_t)(f - fb) * 3 * P + k] - o[k]);
+            __syncwarp();
+            const float4 *tab = tab0 + (size_t)f * tab_frame;
+            for (int s = ns - 1; s >= 0; --s) {
+                const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
+                const float4 *L1 = L0 + Lk * kLinkStride;
+                const Body bs = load_body(sp.sg + 4 * ((f - fb) * ns + s));
+                Body bt = bs;
+                int st2 = 0;
+                const int nc = fwd_substep<PL, true>(a, E, bt, L0, L1, sp, S, lane, st2);
+                rev_substep<PL>(a, E, bs, L0, L1, nc, sp, S, lane, ad, invm_b, mu_b);
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mu_b += __shfl_xor_sync(kFull, mu_b, o);
+    if (lane == 0) {
+        // rotation tangent: q = exp(delta) q0, d/d delta at 0 = vec(qbar (x) conj(q0)) / 2
+        const Q4 g = qmul(ad.q, qconj(b0.q));
+        float *gr = a.grad + 8 * slot;
+        gr[0] = ad.x.x; gr[1] = ad.x.y; gr[2] = ad.x.z;
+        gr[3] = 0.5f * g.x; gr[4] = 0.5f * g.y; gr[5] = 0.5f * g.z;
+        gr[6] = -invm_b * E.inv_m * E.inv_m;
+        gr[7] = mu_b;
+        if (a.grad_quat) {
+            a.grad_quat[4 * slot + 0] = ad.q.w; a.grad_quat[4 * slot + 1] = ad.q.x;
+            a.grad_quat[4 * slot + 2] = ad.q.y; a.grad_quat[4 * slot + 3] = ad.q.z;
+        }
+        if (a.cost) a.cost[slot] = cost;
+    }
+}
+
+template <int PL>
+cudaError_t launch_pl(const AdjArgs &a, cudaStream_t s) {
+    adjoint_kernel<PL><<<(a.n + kAW - 1) / kAW, kABlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void iters_max_kernel(int n, int N, const int *envs, const int *iters, int *out) {
+    int m = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int e = envs ? envs[i] : i;
+        if (e >= 0 && e < N) m = max(m, iters[e]);
+    }
+    m = __reduce_max_sync(kFull, m);
+    __shared__ int part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, part[w]);
+        *out = m;
+    }
+}
+
+}  // namespace
+
+size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max) {
+    return slot_layout(H, K, substeps, n_pads, c_max, iters_max).total;
+}
+
+cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s) {
+    iters_max_kernel<<<1, 256, 0, s>>>(n, N, envs, iters, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s) {
+    const int pl = (a.cfg.c_max + 31) / 32;
+    if (pl <= 1) return launch_pl<1>(a, s);
+    if (pl <= 2) return launch_pl<2>(a, s);
+    if (pl <= 4) return launch_pl<4>(a, s);
+    return launch_pl<8>(a, s);
+}
+
+}  // namespace ih

@@ -49,6 +49,10 @@ struct ih_sim {
     double *elite_w = nullptr, *block_w = nullptr, *moments = nullptr, *misc = nullptr;
     WinDesc *win = nullptr;
     std::vector<void *> owned;
+    // adjoint scratch (grown on demand, freed in sim_destroy)
+    float *adj_scratch = nullptr;
+    size_t adj_floats = 0;
+    int *adj_word = nullptr;
     // captured tracking window (replayed by sim_track_window)
     cudaGraphExec_t win_exec = nullptr;
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
@@ -208,7 +212,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->n_window, 1)); A(dalloc(s, &s->argmin, 1));
     A(dalloc(s, &s->part_c, std::max(N, cost_blocks(N)))); A(dalloc(s, &s->part_i, std::max(N, cost_blocks(N))));
     A(dalloc(s, &s->win, 1));
-    A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 6));
+    A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 6)); A(dalloc(s, &s->adj_word, 1));
     A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
     A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
     A(dalloc(s, &s->moments, (size_t)opt_blocks(N) * kMoments)); A(dalloc(s, &s->misc, 80));
@@ -276,6 +280,7 @@ ih_status sim_destroy(ih_sim *s) {
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_out) cudaEventDestroy(s->ev_out);
     for (void *p : s->owned) cudaFree(p);
+    if (s->adj_scratch) cudaFree(s->adj_scratch);
     delete s;
     return IH_OK;
 }
@@ -623,6 +628,51 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     s->variant = best;
     s->step_grid = grid_for(best, (int)N);
     if (chosen) { chosen[0] = best.group; chosen[1] = best.cpl; }
+    return IH_OK;
+}
+
+ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkpoint_every, const float *obs,
+                      const int32_t *envs, int32_t n, float beta, float width, double *cost, float *grad,
+                      float *grad_quat) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs || !grad) return fail(s, IH_ERR_ARG, "obs and grad are required");
+    if (horizon < 1 || frame0 < 0 || frame0 + horizon > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "horizon [%d, %d) outside the table", frame0, frame0 + horizon);
+    for (int f = frame0; f < frame0 + horizon; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    if (checkpoint_every < 1) return fail(s, IH_ERR_ARG, "checkpoint_every must be >= 1");
+    if (n < 1 || n > s->cfg.n_envs) return fail(s, IH_ERR_ARG, "n must be in [1, %d]", s->cfg.n_envs);
+    if (!(beta > 0.0f) || !std::isfinite(beta) || !(width > 0.0f) || !std::isfinite(width))
+        return fail(s, IH_ERR_ARG, "beta and width must be positive");
+    const int K = std::min(checkpoint_every, horizon);
+    cudaStream_t st = s->stream;
+    // the tape holds every Jacobi iteration of the most expensive selected environment
+    int imax = 0;
+    cudaError_t e = launch_adjoint_iters_max(n, s->cfg.n_envs, envs, s->iters, s->adj_word, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&imax, s->adj_word, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "adjoint sizing");
+    const size_t stride = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, imax);
+    const size_t need = stride * (size_t)n;
+    if (need > s->adj_floats) {
+        if (s->adj_scratch) cudaFree(s->adj_scratch);   // the stream is idle (synchronised above)
+        s->adj_scratch = nullptr;
+        s->adj_floats = 0;
+        void *p = nullptr;
+        e = cudaMalloc(&p, need * sizeof(float));
+        if (e != cudaSuccess) return cuda_fail(s, e, "adjoint scratch");
+        s->adj_scratch = static_cast<float *>(p);
+        s->adj_floats = need;
+    }
+    AdjArgs a;
+    a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.n = n; a.envs = envs;
+    a.link_tab = s->link_tab; a.frame0 = frame0; a.H = horizon; a.K = K;
+    a.pose = s->pose; a.vel = s->vel; a.params = s->params; a.shape = s->shape; a.iters = s->iters;
+    a.status = s->status; a.obs = obs; a.beta_s = beta; a.width = width;
+    a.cost = cost; a.grad = grad; a.grad_quat = grad_quat;
+    a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
+    e = launch_adjoint(a, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "adjoint launch");
     return IH_OK;
 }
 

@@ -281,6 +281,32 @@ struct OptArgs {
     const WinDesc *win;       // when set, update_index comes from win
 };
 int opt_blocks(int N);
+
+// Reverse-mode derivative of the tracking cost over a horizon (adjoint.cu).
+struct AdjArgs {
+    DevScene sc;
+    DevConfig cfg;
+    int N;                    // environments in the handle
+    int n;                    // environments differentiated (slots)
+    const int *envs;          // [n] environment of each slot, or null: slot = environment
+    const float4 *link_tab;   // [frames][ns+1][Lk][3]
+    int frame0, H, K;         // first frame, horizon, checkpoint interval (frames)
+    const float4 *pose, *vel; // [N][2] state at the start of frame0 (read only)
+    const float2 *params;
+    const int *shape, *iters, *status;
+    const float *obs;         // [H][P][3]
+    float beta_s;             // slope of the smoothed normal clamp (1 / (N s))
+    float width;              // relative width of the smoothed friction-disk clamp
+    double *cost;             // [n] or null
+    float *grad;              // [n][8]: position, rotation vector (world frame, left), m, mu
+    float *grad_quat;         // [n][4] derivative w.r.t. the quaternion's components, or null
+    float *scratch;           // [n][stride] floats
+    size_t stride;
+    int iters_max;
+};
+size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max);
+cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
+cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
 cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);

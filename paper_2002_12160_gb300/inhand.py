@@ -53,7 +53,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
-           "cost_eval_static"]
+           "cost_eval_static", "sim_adjoint"]
 
 
 def lib() -> C.CDLL:
@@ -84,6 +84,7 @@ def lib() -> C.CDLL:
             "sim_step_variants": [P, I],
             "sim_step_track": [P, I, P, P, P, P],
             "sim_track_window": [P, I, I, P, P, U32, P, P],
+            "sim_adjoint": [P, I, I, I, P, P, I, C.c_float, C.c_float, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -256,6 +257,30 @@ class Sim:
 
     def sim_set_variant(self, threads_per_env: int, contacts_per_thread: int):
         self._call("sim_set_variant", threads_per_env, contacts_per_thread)
+
+    def sim_adjoint(self, frame0: int, obs, envs=None, checkpoint_every: int = 10, beta: float = 1e3,
+                    width: float = 1e-3, cost=None, grad=None, grad_quat=None, want_quat: bool = False):
+        """Horizon cost and its gradient for each selected environment
+        (horizon = obs.shape[0] frames from frame0). Returns (cost float64[n],
+        grad float32[n][8] = d/d(x, y, z, rx, ry, rz, m, mu), grad_quat
+        float32[n][4] or None)."""
+        H = obs.shape[0]
+        _check(obs, torch.float32, (H, self.n_pads, 3), "obs")
+        n = self.n if envs is None else envs.shape[0]
+        _check(envs, torch.int32, (n,), "envs")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if cost is None:
+            cost = torch.empty((n,), dtype=torch.float64, device=dev)
+        if grad is None:
+            grad = torch.empty((n, 8), dtype=torch.float32, device=dev)
+        if grad_quat is None and want_quat:
+            grad_quat = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        _check(cost, torch.float64, (n,), "cost")
+        _check(grad, torch.float32, (n, 8), "grad")
+        _check(grad_quat, torch.float32, (n, 4), "grad_quat")
+        self._call("sim_adjoint", frame0, H, checkpoint_every, _ptr(obs), _ptr(envs), n, C.c_float(beta),
+                   C.c_float(width), _ptr(cost), _ptr(grad), _ptr(grad_quat))
+        return cost, grad, grad_quat
 
 
 def step_variants():

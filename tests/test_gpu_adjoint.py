@@ -1,0 +1,130 @@
+"""GPU adjoint (sim_adjoint through the C ABI) against the FP64 adjoint oracle.
+
+Both sides start from the same state -- the GPU's FP32 state after a warm-up,
+widened exactly to FP64 -- and differentiate the force term of the tracking
+cost over a 5-frame horizon with respect to the initial position, rotation
+tangent, mass and friction, with the same backward-only smoothing. Tolerance:
+1e-3 relative per block (position, rotation, m, mu), with an absolute floor of
+1e-3 of the environment's largest block norm. Environments whose horizon
+passes within 1e-6 m of a contact or pad threshold are excluded and counted.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import adjoint as A
+from paper_2002_12160_gb300 import workloads as W
+
+from gpu_common import FRAGILE, dev, oracle_state, scene32, sim32, start, torch
+
+pytestmark = pytest.mark.gpu
+
+WARM, H = 18, 5
+BLOCKS = [slice(0, 3), slice(3, 6), slice(6, 7), slice(7, 8)]
+
+
+def _setup(n=4, name="tracking_cyl64"):
+    wl = W.make_workload(name, n_envs=n, frames=WARM + H + 2)
+    sim = start(wl, n=n, frames=WARM + H + 2)
+    sim.sim_step(0, WARM)
+    st = oracle_state(sim.sim_get_state())
+    sc, sm = scene32(wl.scene), sim32(wl.sim)
+    osc = O.OracleScene(sc)
+    # observations: the ground-truth parameters from environment 0's state (oracle)
+    gt = O.State(st.pose[:1], st.vel[:1], np.array([wl.theta_gt], np.float64))
+    obs, fragile = [], np.zeros(n, bool)
+    probe = O.State(st.pose, st.vel, st.theta)
+    for k in range(H):
+        f, _ = O.step(osc, sm, gt, wl.q_traj, WARM + k, 1)
+        obs.append(f[0])
+        _, diag = O.step(osc, sm, probe, wl.q_traj, WARM + k, 1)
+        fragile |= (diag[:, 2] < FRAGILE) | (diag[:, 3] < FRAGILE) | (diag[:, 4] < FRAGILE)
+    obs = np.asarray(obs, np.float32)
+    return wl, sim, st, sc, sm, obs, fragile
+
+
+def test_adjoint_matches_oracle():
+    wl, sim, st, sc, sm, obs, fragile = _setup()
+    d = dev()
+    cost, grad, _ = sim.sim_adjoint(WARM, torch.from_numpy(obs).to(d), checkpoint_every=2)
+    cost, grad = cost.cpu().numpy(), grad.cpu().numpy().astype(np.float64)
+    checked = 0
+    for i in range(st.n):
+        if fragile[i]:
+            continue
+        c_or, g_or, _, _, _ = A.horizon(sc, sm, st.pose[i], st.vel[i], st.theta[i], wl.q_traj, WARM, H,
+                                        obs.astype(np.float64))
+        assert np.isfinite(cost[i]) and abs(cost[i] - c_or) <= 1e-3 * abs(c_or) + 1e-6, (i, cost[i], c_or)
+        floor = 1e-3 * max(np.linalg.norm(g_or[b]) for b in BLOCKS)
+        for b in BLOCKS:
+            err = np.linalg.norm(grad[i, b] - g_or[b])
+            assert err <= 1e-3 * np.linalg.norm(g_or[b]) + floor, (i, b, grad[i, b], g_or[b])
+        checked += 1
+    assert checked >= 3
+
+
+def test_checkpoint_interval_and_subset_do_not_change_results():
+    wl, sim, st, sc, sm, obs, fragile = _setup()
+    d = dev()
+    o = torch.from_numpy(obs).to(d)
+    ref_c, ref_g, ref_q = sim.sim_adjoint(WARM, o, checkpoint_every=10, want_quat=True)
+    for K in (1, 2, 3):
+        c, g, q = sim.sim_adjoint(WARM, o, checkpoint_every=K, want_quat=True)
+        assert torch.equal(c, ref_c) and torch.equal(g, ref_g) and torch.equal(q, ref_q), K
+    envs = torch.tensor([3, 1], dtype=torch.int32, device=d)
+    c, g, _ = sim.sim_adjoint(WARM, o, envs=envs, checkpoint_every=2)
+    assert torch.equal(c, ref_c[[3, 1]]) and torch.equal(g, ref_g[[3, 1]])
+    # the state is left unchanged
+    before = sim.sim_get_state()
+    sim.sim_adjoint(WARM, o)
+    after = sim.sim_get_state()
+    assert all(torch.equal(a, b) for a, b in zip(before, after))
+
+
+def test_adjoint_cost_is_the_scored_cost():
+    """The adjoint's forward is the step's arithmetic: with one warp per
+    environment the pad forces, hence the FP64 costs, are the scored step's."""
+    wl, sim, st, sc, sm, obs, fragile = _setup()
+    d = dev()
+    o = torch.from_numpy(obs).to(d)
+    sim.sim_set_variant(32, 4)
+    c_adj, _, _ = sim.sim_adjoint(WARM, o)
+    pose, vel, params, _ = sim.sim_get_state()
+    sim.sim_set_state(pose, vel, params)   # also resets nothing but status; start a fresh window
+    cm = torch.empty(sim.n, dtype=torch.float64, device=d)
+    opt = W.OptConfig()
+    sim.sim_step_track(WARM, o[0], cm)
+    sim.optimizer_update(opt, 0)   # resets the window (the state changes but only after scoring)
+    sim.sim_set_state(pose, vel, params)
+    for k in range(H):
+        sim.sim_step_track(WARM + k, o[k], cm)
+    np.testing.assert_allclose(cm.cpu().numpy() * H, c_adj.cpu().numpy(), rtol=1e-12)
+
+
+def test_autograd_function_and_invalid_env():
+    wl, sim, st, sc, sm, obs, fragile = _setup()
+    d = dev()
+    from paper_2002_12160_gb300.autograd import tracking_cost
+    o = torch.from_numpy(obs).to(d)
+    pose, vel, params, _ = sim.sim_get_state()
+    _, g_ref, q_ref = sim.sim_adjoint(WARM, o, want_quat=True)
+    pose = pose.clone().requires_grad_(True)
+    params = params.clone().requires_grad_(True)
+    c = tracking_cost(sim, pose, params, vel, WARM, o)
+    (2.0 * c).sum().backward()
+    assert torch.equal(pose.grad[:, :3], 2.0 * g_ref[:, :3])
+    assert torch.equal(pose.grad[:, 4:], 2.0 * q_ref)
+    assert torch.equal(params.grad, 2.0 * g_ref[:, 6:])
+    # the rotation tangent is the quaternion derivative projected: vec(qbar (x) conj(q)) / 2
+    q = pose.detach()[:, 4:].cpu().numpy().astype(np.float64)
+    qb = q_ref.cpu().numpy().astype(np.float64)
+    w1, v1, w2, v2 = qb[:, 0], qb[:, 1:], q[:, 0], -q[:, 1:]
+    vec = w1[:, None] * v2 + w2[:, None] * v1 + np.cross(v1, v2)
+    np.testing.assert_allclose(0.5 * vec, g_ref[:, 3:6].cpu().numpy(), rtol=1e-4, atol=1e-6 * np.abs(qb).max())
+    # an invalid environment (mass <= 0) has cost +inf and zero gradient
+    p2 = params.detach().clone()
+    p2[1, 0] = -1.0
+    sim.sim_set_state(pose.detach().contiguous(), vel, p2)
+    c2, g2, _ = sim.sim_adjoint(WARM, o)
+    assert torch.isinf(c2[1]) and torch.all(g2[1] == 0)
+    assert torch.isfinite(c2[[0, 2, 3]]).all()
