@@ -348,6 +348,39 @@ ih_status sim_adjoint(ih_sim *sim, int32_t frame0, int32_t horizon, int32_t chec
                       const float *obs, const int32_t *envs, int32_t n, float beta, float width,
                       double *cost, float *grad, float *grad_quat);
 
+/* Snapshot every environment's state (pose, velocity, parameters) into the
+ * handle: the start of a tracking window, for sim_refine_elites. */
+ih_status sim_mark_window(ih_sim *sim);
+
+/* Gradient refinement of the elite samples (an addition to the paper's
+ * derivative-free update of Sec. III-D, run between the window's last scored
+ * frame and optimizer_update).
+ *
+ * The window is frames [frame0, frame0 + T), all scored since the last
+ * sim_mark_window; obs is device float[T][P][3], those frames' observations.
+ * The elites are the optimizer's (the k = max(1, floor(elite_frac N)) lowest
+ * window means, ties to the lowest index). Each elite's window-start state
+ * z = (position, rotation, m, mu) is refined by `steps` steps
+ *   s = eta g, z <- z - scale eta s / |s|,  eta = step_scale floor_std,
+ * with g the gradient of the window's cost (sim_adjoint's, horizon T, same
+ * smoothing beta and width; the rotation step is exp([dz]x) on the left, m and
+ * mu are clamped to the optimizer's ranges). A step is kept when it lowers the
+ * cost, otherwise the elite's scale halves and the next step starts from its
+ * best state. An elite whose cost went down is then simulated from its best
+ * window-start state to the window's end, and that end state, its parameters
+ * and its window cost (sum and mean) replace the scored ones; the others keep
+ * theirs. optimizer_update then resamples around the refined elites.
+ * Outputs (device, k entries each, any may be NULL): elite_out int32 (the
+ * elites, index order), cost_before double (window cost of the unrefined
+ * state, as the adjoint's forward computes it), cost_after double (the best
+ * cost found; <= cost_before).
+ * Synchronises the stream once (adjoint scratch sizing).
+ * Errors: IH_ERR_ARG (bad range or constant), IH_ERR_STATE (no mark, or not
+ * exactly T frames scored since it), IH_ERR_OOM. */
+ih_status sim_refine_elites(ih_sim *sim, int32_t frame0, int32_t T, const float *obs,
+                            const ih_opt_config *opt, int32_t steps, float step_scale, float beta,
+                            float width, int32_t *elite_out, double *cost_before, double *cost_after);
+
 /* Wait for the handle's stream; IH_ERR_CUDA if a kernel failed. */
 ih_status sim_sync(ih_sim *sim);
 

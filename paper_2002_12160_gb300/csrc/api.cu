@@ -53,6 +53,14 @@ struct ih_sim {
     float *adj_scratch = nullptr;
     size_t adj_floats = 0;
     int *adj_word = nullptr;
+    // gradient refinement: window-start snapshot, trial, best and end states (allocated on first use)
+    bool rf_alloc = false, ws_valid = false;
+    int ws_frames = 0;
+    float4 *ws_pose = nullptr, *ws_vel = nullptr, *tr_pose = nullptr, *end_pose = nullptr, *end_vel = nullptr,
+           *best_pose = nullptr;
+    float2 *ws_params = nullptr, *tr_params = nullptr, *best_params = nullptr;
+    float *best_grad = nullptr, *scale = nullptr, *r_grad = nullptr;
+    double *best_c = nullptr, *c0 = nullptr, *r_cost = nullptr;
     // captured tracking window (replayed by sim_track_window)
     cudaGraphExec_t win_exec = nullptr;
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
@@ -317,6 +325,7 @@ ih_status sim_sample_initial(ih_sim *s, const float *nominal, float sigma_p, flo
     if (e == cudaSuccess) e = cudaMemsetAsync(s->n_window, 0, sizeof(int), s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "sample_initial");
     s->window_frames = 0;
+    s->ws_valid = false;
     return IH_OK;
 }
 
@@ -331,6 +340,7 @@ ih_status sim_set_state(ih_sim *s, const float *pose, const float *vel, const fl
     if (e == cudaSuccess && (shape_id || iters))
         e = launch_lpt_order(s->cfg.n_envs, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
+    s->ws_valid = false;
     return IH_OK;
 }
 
@@ -483,6 +493,7 @@ ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *ob
     if (e != cudaSuccess) return cuda_fail(s, e, "window launch");
     s->stepped = true;
     s->window_frames = 0;
+    s->ws_valid = false;
     return IH_OK;
 }
 
@@ -523,6 +534,7 @@ ih_status optimizer_update(ih_sim *s, const ih_opt_config *opt, uint32_t update_
     cudaError_t e = launch_optimizer(a, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "optimizer launch");
     s->window_frames = 0;
+    s->ws_valid = false;
     return IH_OK;
 }
 
@@ -631,29 +643,18 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     return IH_OK;
 }
 
-ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkpoint_every, const float *obs,
-                      const int32_t *envs, int32_t n, float beta, float width, double *cost, float *grad,
-                      float *grad_quat) {
-    if (!s) return IH_ERR_ARG;
-    if (!obs || !grad) return fail(s, IH_ERR_ARG, "obs and grad are required");
-    if (horizon < 1 || frame0 < 0 || frame0 + horizon > s->cfg.max_frames)
-        return fail(s, IH_ERR_ARG, "horizon [%d, %d) outside the table", frame0, frame0 + horizon);
-    for (int f = frame0; f < frame0 + horizon; ++f)
-        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
-    if (checkpoint_every < 1) return fail(s, IH_ERR_ARG, "checkpoint_every must be >= 1");
-    if (n < 1 || n > s->cfg.n_envs) return fail(s, IH_ERR_ARG, "n must be in [1, %d]", s->cfg.n_envs);
-    if (!(beta > 0.0f) || !std::isfinite(beta) || !(width > 0.0f) || !std::isfinite(width))
-        return fail(s, IH_ERR_ARG, "beta and width must be positive");
-    const int K = std::min(checkpoint_every, horizon);
+namespace {
+// Size (and grow) the adjoint scratch for n slots: reads back the largest
+// iteration count among the selected environments (synchronises the stream).
+ih_status adjoint_prepare(ih_sim *s, int n, const int32_t *envs, int horizon, int K, size_t *stride, int *imax) {
     cudaStream_t st = s->stream;
-    // the tape holds every Jacobi iteration of the most expensive selected environment
-    int imax = 0;
+    int m = 0;
     cudaError_t e = launch_adjoint_iters_max(n, s->cfg.n_envs, envs, s->iters, s->adj_word, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&imax, s->adj_word, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, s->adj_word, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(s, e, "adjoint sizing");
-    const size_t stride = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, imax);
-    const size_t need = stride * (size_t)n;
+    const size_t str = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, m);
+    const size_t need = str * (size_t)n;
     if (need > s->adj_floats) {
         if (s->adj_scratch) cudaFree(s->adj_scratch);   // the stream is idle (synchronised above)
         s->adj_scratch = nullptr;
@@ -664,15 +665,147 @@ ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkp
         s->adj_scratch = static_cast<float *>(p);
         s->adj_floats = need;
     }
+    *stride = str;
+    *imax = m;
+    return IH_OK;
+}
+
+ih_status check_horizon(ih_sim *s, int32_t frame0, int32_t horizon) {
+    if (horizon < 1 || frame0 < 0 || frame0 + horizon > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "horizon [%d, %d) outside the table", frame0, frame0 + horizon);
+    for (int f = frame0; f < frame0 + horizon; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    return IH_OK;
+}
+
+AdjArgs adjoint_args(ih_sim *s, int32_t frame0, int32_t horizon, int K, const float *obs, float beta, float width) {
     AdjArgs a;
-    a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.n = n; a.envs = envs;
+    a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.n = 0; a.envs = nullptr;
     a.link_tab = s->link_tab; a.frame0 = frame0; a.H = horizon; a.K = K;
     a.pose = s->pose; a.vel = s->vel; a.params = s->params; a.shape = s->shape; a.iters = s->iters;
     a.status = s->status; a.obs = obs; a.beta_s = beta; a.width = width;
-    a.cost = cost; a.grad = grad; a.grad_quat = grad_quat;
+    a.cost = nullptr; a.grad = nullptr; a.grad_quat = nullptr;
+    a.scratch = s->adj_scratch; a.stride = 0; a.iters_max = 0;
+    a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr;
+    return a;
+}
+}  // namespace
+
+ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkpoint_every, const float *obs,
+                      const int32_t *envs, int32_t n, float beta, float width, double *cost, float *grad,
+                      float *grad_quat) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs || !grad) return fail(s, IH_ERR_ARG, "obs and grad are required");
+    ih_status r = check_horizon(s, frame0, horizon);
+    if (r != IH_OK) return r;
+    if (checkpoint_every < 1) return fail(s, IH_ERR_ARG, "checkpoint_every must be >= 1");
+    if (n < 1 || n > s->cfg.n_envs) return fail(s, IH_ERR_ARG, "n must be in [1, %d]", s->cfg.n_envs);
+    if (!(beta > 0.0f) || !std::isfinite(beta) || !(width > 0.0f) || !std::isfinite(width))
+        return fail(s, IH_ERR_ARG, "beta and width must be positive");
+    const int K = std::min(checkpoint_every, horizon);
+    size_t stride = 0;
+    int imax = 0;
+    r = adjoint_prepare(s, n, envs, horizon, K, &stride, &imax);
+    if (r != IH_OK) return r;
+    AdjArgs a = adjoint_args(s, frame0, horizon, K, obs, beta, width);
+    a.n = n; a.envs = envs; a.cost = cost; a.grad = grad; a.grad_quat = grad_quat;
     a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
-    e = launch_adjoint(a, st);
+    cudaError_t e = launch_adjoint(a, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "adjoint launch");
+    return IH_OK;
+}
+
+namespace {
+cudaError_t refine_alloc(ih_sim *s) {
+    if (s->rf_alloc) return cudaSuccess;
+    const size_t N = s->cfg.n_envs;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(s, &s->ws_pose, 2 * N)); A(dalloc(s, &s->ws_vel, 2 * N)); A(dalloc(s, &s->ws_params, N));
+    A(dalloc(s, &s->tr_pose, 2 * N)); A(dalloc(s, &s->tr_params, N));
+    A(dalloc(s, &s->end_pose, 2 * N)); A(dalloc(s, &s->end_vel, 2 * N));
+    A(dalloc(s, &s->best_pose, 2 * N)); A(dalloc(s, &s->best_params, N)); A(dalloc(s, &s->best_grad, 8 * N));
+    A(dalloc(s, &s->scale, N)); A(dalloc(s, &s->r_grad, 8 * N));
+    A(dalloc(s, &s->best_c, N)); A(dalloc(s, &s->c0, N)); A(dalloc(s, &s->r_cost, N));
+    if (e == cudaSuccess) s->rf_alloc = true;
+    return e;
+}
+}  // namespace
+
+ih_status sim_mark_window(ih_sim *s) {
+    if (!s) return IH_ERR_ARG;
+    cudaError_t e = refine_alloc(s);
+    const size_t N = s->cfg.n_envs;
+    cudaStream_t st = s->stream;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ws_pose, s->pose, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ws_vel, s->vel, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ws_params, s->params, N * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "mark_window");
+    s->ws_valid = true;
+    s->ws_frames = s->window_frames;
+    return IH_OK;
+}
+
+ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *obs, const ih_opt_config *opt,
+                            int32_t steps, float step_scale, float beta, float width, int32_t *elite_out,
+                            double *cost_before, double *cost_after) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
+    ih_status r = check_opt(s, opt);
+    if (r != IH_OK) return r;
+    r = check_horizon(s, frame0, T);
+    if (r != IH_OK) return r;
+    if (steps < 0 || steps > 64 || !(step_scale > 0.0f) || !std::isfinite(step_scale))
+        return fail(s, IH_ERR_ARG, "steps must be in [0, 64] and step_scale positive");
+    if (!(beta > 0.0f) || !std::isfinite(beta) || !(width > 0.0f) || !std::isfinite(width))
+        return fail(s, IH_ERR_ARG, "beta and width must be positive");
+    if (!s->ws_valid) return fail(s, IH_ERR_STATE, "no window start marked (sim_mark_window)");
+    if (s->window_frames - s->ws_frames != T)
+        return fail(s, IH_ERR_STATE, "%d frames scored since the window start, expected %d",
+                    s->window_frames - s->ws_frames, T);
+    const int N = s->cfg.n_envs;
+    int k = (int)std::floor((double)opt->elite_frac * (double)N);
+    k = std::max(1, std::min(k, N));
+    cudaStream_t st = s->stream;
+    // elites of the window (the optimizer's own selection), trial states = window start
+    OptArgs oa = opt_args(s, opt, 0, nullptr, nullptr);
+    cudaError_t e = launch_select(oa, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->tr_pose, s->ws_pose, 2 * (size_t)N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->tr_params, s->ws_params, (size_t)N * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "refine select");
+    size_t stride = 0;
+    int imax = 0;
+    r = adjoint_prepare(s, k, s->elite_env, T, T, &stride, &imax);
+    if (r != IH_OK) return r;
+    AdjArgs a = adjoint_args(s, frame0, T, T, obs, beta, width);
+    a.n = k; a.envs = s->elite_env; a.pose = s->tr_pose; a.vel = s->ws_vel; a.params = s->tr_params;
+    a.cost = s->r_cost; a.grad = s->r_grad; a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
+    RefineArgs ra;
+    ra.k = k; ra.elite = s->elite_env; ra.tr_pose = s->tr_pose; ra.tr_params = s->tr_params;
+    ra.best_pose = s->best_pose; ra.best_params = s->best_params; ra.best_grad = s->best_grad;
+    ra.best_c = s->best_c; ra.c0 = s->c0; ra.scale = s->scale; ra.cost = s->r_cost; ra.grad = s->r_grad;
+    for (int d = 0; d < 8; ++d) ra.eta[d] = step_scale * opt->floor_std[d];
+    ra.m_lo = opt->m_lo; ra.m_hi = opt->m_hi; ra.mu_lo = opt->mu_lo; ra.mu_hi = opt->mu_hi;
+    for (int it = 0; it <= steps && e == cudaSuccess; ++it) {
+        a.forward_only = it == steps ? 1 : 0;   // the last trial needs its cost only
+        e = launch_adjoint(a, st);
+        ra.step = it;
+        ra.last = it == steps ? 1 : 0;
+        if (e == cudaSuccess) e = launch_refine(ra, st);
+    }
+    // the best state of each elite, simulated to the window's end, replaces the scored one
+    a.forward_only = 1; a.out_pose = s->end_pose; a.out_vel = s->end_vel;
+    if (e == cudaSuccess) e = launch_adjoint(a, st);
+    if (e == cudaSuccess)
+        e = launch_refine_commit(k, s->elite_env, s->best_c, s->c0, s->best_params, s->end_pose, s->end_vel, s->pose,
+                                 s->vel, s->params, s->c_sum, s->c_mean, s->n_window, st);
+    if (e == cudaSuccess && elite_out)
+        e = cudaMemcpyAsync(elite_out, s->elite_env, k * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && cost_before)
+        e = cudaMemcpyAsync(cost_before, s->c0, k * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && cost_after)
+        e = cudaMemcpyAsync(cost_after, s->best_c, k * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "refine");
     return IH_OK;
 }
 

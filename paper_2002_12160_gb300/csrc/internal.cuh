@@ -303,12 +303,42 @@ struct AdjArgs {
     float *scratch;           // [n][stride] floats
     size_t stride;
     int iters_max;
+    int forward_only;         // 1: cost (and end state) only, no reverse sweep
+    float4 *out_pose, *out_vel;   // [N][2] end state of each environment (forward_only), or null
 };
+
+// Gradient refinement of the elites (adjoint.cu): accept or reject the last
+// trial of every elite, then step from its best state.
+struct RefineArgs {
+    int k;
+    const int *elite;             // [k] environments
+    float4 *tr_pose;              // [N][2] trial states (elites' entries)
+    float2 *tr_params;            // [N]
+    float4 *best_pose;            // [k][2]
+    float2 *best_params;          // [k]
+    float *best_grad;             // [k][8]
+    double *best_c, *c0;          // [k] best cost so far, cost of the unrefined state
+    float *scale;                 // [k] step multiplier (halved on a rejected trial)
+    const double *cost;           // [k] cost at the trial
+    const float *grad;            // [k][8] gradient at the trial
+    float eta[8];                 // step length per coordinate
+    float m_lo, m_hi, mu_lo, mu_hi;
+    int step;                     // 0: the first evaluation (of the unrefined state)
+    int last;                     // 1: restore the best state instead of stepping
+};
+cudaError_t launch_refine(const RefineArgs &r, cudaStream_t s);
+// copy refined elites (end state, parameters, window cost) into the live state
+cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, const double *c0,
+                                 const float2 *best_params, const float4 *end_pose, const float4 *end_vel,
+                                 float4 *pose, float4 *vel, float2 *params, double *c_sum, double *c_mean,
+                                 const int *n_window, cudaStream_t s);
 size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max);
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
 cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
+// the optimizer's first stage alone: elite flags, ranks and elite_env (index order), i*
+cudaError_t launch_select(const OptArgs &a, cudaStream_t s);
 
 }  // namespace ih

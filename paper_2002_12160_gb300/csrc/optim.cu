@@ -361,6 +361,11 @@ cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s) {
 
 int opt_blocks(int N) { return (N + kOptBlock - 1) / kOptBlock; }
 
+cudaError_t launch_select(const OptArgs &a, cudaStream_t s) {
+    select_kernel<<<1, kSel, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
     // the elite count, computed exactly as select_kernel does
     int k = (int)floor((double)a.elite_frac * (double)a.N);

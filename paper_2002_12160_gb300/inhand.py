@@ -53,7 +53,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
-           "cost_eval_static", "sim_adjoint"]
+           "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites"]
 
 
 def lib() -> C.CDLL:
@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
             "sim_step_track": [P, I, P, P, P, P],
             "sim_track_window": [P, I, I, P, P, U32, P, P],
             "sim_adjoint": [P, I, I, I, P, P, I, C.c_float, C.c_float, P, P, P],
+            "sim_mark_window": [P],
+            "sim_refine_elites": [P, I, I, P, P, I, C.c_float, C.c_float, C.c_float, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -281,6 +283,25 @@ class Sim:
         self._call("sim_adjoint", frame0, H, checkpoint_every, _ptr(obs), _ptr(envs), n, C.c_float(beta),
                    C.c_float(width), _ptr(cost), _ptr(grad), _ptr(grad_quat))
         return cost, grad, grad_quat
+
+    def sim_mark_window(self):
+        self._call("sim_mark_window")
+
+    def sim_refine_elites(self, frame0: int, obs, opt, steps: int = 3, step_scale: float = 0.5,
+                          beta: float = 1e3, width: float = 1e-3, report: bool = False):
+        """Refine the window's elites (see include/inhand.h). With report=True
+        returns (elites int32[k], cost_before float64[k], cost_after float64[k])."""
+        T = obs.shape[0]
+        _check(obs, torch.float32, (T, self.n_pads, 3), "obs")
+        out = (None, None, None)
+        if report:
+            k = max(1, min(self.n, int(np.floor(np.float64(np.float32(opt.elite_frac)) * self.n))))
+            dev = torch.device("cuda", torch.cuda.current_device())
+            out = (torch.empty(k, dtype=torch.int32, device=dev), torch.empty(k, dtype=torch.float64, device=dev),
+                   torch.empty(k, dtype=torch.float64, device=dev))
+        self._call("sim_refine_elites", frame0, T, _ptr(obs), C.byref(_opt(opt)), steps, C.c_float(step_scale),
+                   C.c_float(beta), C.c_float(width), *(_ptr(t) for t in out))
+        return out if report else None
 
 
 def step_variants():

@@ -86,6 +86,22 @@ class Tracker:
                 step_events[k][1].record()
         self.sim.optimizer_update(self.wl.opt, w)
 
+    def window_refined(self, w: int, steps: int = 3, step_scale: float = 0.5, report: bool = False):
+        """The window with a gradient refinement of its elites before the
+        optimizer update: mark the window start, step and score its T frames,
+        refine the elites' window-start states along the adjoint gradient of
+        the window's cost, then resample."""
+        T = self.T
+        f0 = w * T
+        self.sim.sim_mark_window()
+        for k in range(T):
+            f = f0 + k
+            self.sim.sim_step_track(f, self.obs[f], None, self.argmin[f:f + 1], self.est[f])
+        rep = self.sim.sim_refine_elites(f0, self.obs[f0:f0 + T], self.wl.opt, steps, step_scale,
+                                         report=report)
+        self.sim.optimizer_update(self.wl.opt, w)
+        return rep
+
     def e2e_windows(self, w0: int, count: int):
         """Windows driven through the public API from pinned host buffers: per window
         the commands and observations go host -> device, the estimates come back."""
@@ -121,6 +137,7 @@ class Tracker:
         gt = self.gt_pose.cpu().numpy().astype(np.float64)
         used = frames if frames is not None else int((np.abs(est).sum(1) > 0).sum())
         pts = self.wl.scene.shapes[0][:, :3]
+        pts = pts - pts.mean(0)   # the pose is the centroid's
 
         def world(p):
             w, x, y, z = p[4:]
