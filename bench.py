@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--workload", default="tracking_cyl64")
     p.add_argument("--n-envs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip the adjoint throughput and the refinement-vs-plain tracking study")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     p.add_argument("--sweep", default=None,
                    help="comma-separated N values: also time the workload at each N (tracking frames/s)")
@@ -186,31 +188,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(workload, budget_s=12.0):
-    """Oracle env-steps/s on the host, single thread, on a bounded sample."""
+def cpu_baseline(workload, budget_s=15.0):
+    """Oracle env-steps/s on the host, single thread, on a bounded sample: the
+    workload's first 300 frames (windows of 10 + optimizer) replayed from fresh
+    initial samples until the time budget is spent."""
     import oracle as O
     from paper_2002_12160_gb300 import workloads as W
-    T, n_sample = 10, 32
-    wl = W.make_workload(workload, n_envs=n_sample, frames=400)
+    T, n_sample, n_frames = 10, 32, 300
+    wl = W.make_workload(workload, n_envs=n_sample, frames=n_frames)
     osc = O.OracleScene(wl.scene)
-    pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed)
-    st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
     frames = 0
-    t0 = time.perf_counter()
-    f = 0
     upd = 0
-    while time.perf_counter() - t0 < budget_s and f + T < 400:
-        c_sum = np.zeros(n_sample)
-        for k in range(T):
-            forces, _ = O.step(osc, wl.sim, st, wl.q_traj, f, 1)
-            _, c_mean, _ = O.cost(wl.sim, forces, forces[0], st.status, c_sum, k + 1)
-            f += 1
-            frames += 1
-        O.optimizer(wl.opt, st, c_mean, wl.seed, upd)
-        upd += 1
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed + upd)
+        st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
+        f = 0
+        while f + T <= n_frames and time.perf_counter() - t0 < budget_s:
+            c_sum = np.zeros(n_sample)
+            for k in range(T):
+                forces, _ = O.step(osc, wl.sim, st, wl.q_traj, f, 1)
+                _, c_mean, _ = O.cost(wl.sim, forces, forces[0], st.status, c_sum, k + 1)
+                f += 1
+                frames += 1
+            O.optimizer(wl.opt, st, c_mean, wl.seed, upd)
+            upd += 1
     el = time.perf_counter() - t0
     return {"value": n_sample * frames / el, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_sample} envs x {frames} frames of {workload} (windows of {T} + optimizer), {el:.1f} s"}
+            "sample": f"{n_sample} envs x {frames} frames of {workload} (its first {n_frames} frames replayed "
+                      f"from fresh samples; windows of {T} + optimizer), single thread, {el:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -282,6 +288,106 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e
     return out
 
 
+def measure_adjoint(local, n_envs=1024, horizon=30, checkpoint_every=10, reps=3):
+    """Forward + adjoint of the horizon cost (sim_adjoint) for every environment
+    of the differentiable-tracking workload (box / cylinder, H = 30 frames,
+    checkpoints every 10): CUDA-event time per call after one warm-up call."""
+    import torch
+    from paper_2002_12160_gb300 import tracking, workloads as W
+    torch.cuda.set_device(local)
+    out = {}
+    for name in ["tracking_cyl64", "tracking_box27"]:
+        wl = W.make_workload(name, n_envs=n_envs, frames=20 + horizon + 2)
+        tr = tracking.Tracker(wl, n_envs=n_envs)
+        tr.prepare()
+        for w in range(2):
+            tr.window(w)          # contacts established, the population converging
+        f0 = 20
+        obs = tr.obs[f0:f0 + horizon].contiguous()
+        tr.sim.sim_adjoint(f0, obs, checkpoint_every=checkpoint_every)   # warm-up (scratch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            e0.record()
+            cost, grad, _ = tr.sim.sim_adjoint(f0, obs, checkpoint_every=checkpoint_every)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        fin = torch.isfinite(cost)
+        out[name] = {"n_envs": n_envs, "horizon": horizon, "checkpoint_every": checkpoint_every,
+                     "ms_per_call": t, "env_steps_per_s": n_envs * horizon / (t / 1e3),
+                     "finite_envs": int(fin.sum().item()),
+                     "mean_grad_norm": float(grad[fin].norm(dim=1).mean().item()) if fin.any() else None}
+        tr.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def refine_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_refined=1024, steps=3):
+    """Tracking error (ADD of the argmin estimate, mm, over `frames` frames) of
+    the plain update against the update preceded by 3 gradient-refinement steps
+    of the elites, at equal wall time: the refined run has N = n_refined; the
+    plain run gets the N whose window takes as long (measured), and is also
+    shown at N = n_refined. Median and mean over seeded trajectories."""
+    import torch
+    from paper_2002_12160_gb300 import tracking, workloads as W
+    torch.cuda.set_device(local)
+
+    def run(name, n, seed, refined, n_frames):
+        wl = W.make_workload(name, n_envs=n, frames=n_frames, seed=seed)
+        tr = tracking.Tracker(wl, n_envs=n)
+        tr.prepare()
+        nw = n_frames // tr.T
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for w in range(nw):
+            if refined:
+                tr.window_refined(w, steps=steps)
+            else:
+                tr.window(w)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nw
+        add = tr.add_mm(nw * tr.T)
+        tr.close()
+        return ms, add
+
+    out = {}
+    for name in ["tracking_cyl64", "tracking_box27"]:
+        run(name, n_refined, seeds[0], True, 40)    # warm-up: scratch allocation, first captures
+        ms_r = statistics.median(run(name, n_refined, seeds[0], True, 60)[0] for _ in range(2))
+        # the plain window's time as a function of N; the equal-time N by interpolation
+        grid = [1024, 2048, 4096, 8192, 16384, 32768]
+        t_plain = [run(name, n, seeds[0], False, 60)[0] for n in grid]
+        n_eq = grid[0]
+        for a, b, ta, tb in zip(grid, grid[1:], t_plain, t_plain[1:]):
+            if ta <= ms_r:
+                n_eq = a if tb <= ta else int(a + (b - a) * min(1.0, (ms_r - ta) / (tb - ta)))
+        n_eq = max(grid[0], min(grid[-1], 256 * (n_eq // 256)))
+        res = {"refined": [], "plain_same_n": [], "plain_equal_time": []}
+        times = {"refined": [], "plain_equal_time": []}
+        for seed in seeds:
+            ms, add = run(name, n_refined, seed, True, frames)
+            res["refined"].append(add); times["refined"].append(ms)
+            res["plain_same_n"].append(run(name, n_refined, seed, False, frames)[1])
+            ms, add = run(name, n_eq, seed, False, frames)
+            res["plain_equal_time"].append(add); times["plain_equal_time"].append(ms)
+        out[name] = {
+            "n_refined": n_refined, "n_plain_equal_time": n_eq, "refine_steps": steps, "frames": frames,
+            "seeds": list(seeds),
+            "ms_per_window": {k: statistics.median(v) for k, v in times.items()},
+            "plain_ms_per_window_by_n": {str(n): t for n, t in zip(grid, t_plain)},
+            "add_mm_median": {k: statistics.median(v) for k, v in res.items()},
+            "add_mm_mean": {k: float(np.mean(v)) for k, v in res.items()},
+            "add_mm": res,
+            "refined_le_plain_equal_time": statistics.median(res["refined"]) <= statistics.median(res["plain_equal_time"])}
+    torch.cuda.empty_cache()
+    return out
+
+
 def flops_of(work, wl):
     return (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * max(len(s) for s in wl.scene.shapes)) +
             work["pairs"] * FLOP_PER_PAIR + work["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
@@ -333,6 +439,12 @@ def run_ours(args, rank, world, local):
         line["sweep"] = sweep
         ok = [x for x in sweep if x["tracking_frames_per_s"] >= 30.0]
         line["largest_n_measured_at_30hz"] = max((x["n_envs"] for x in ok), default=None)
+    if not args.no_adjoint:
+        adj = measure_adjoint(local)
+        line["adjoint"] = {"what": "forward + reverse-mode gradient of the horizon cost (sim_adjoint), "
+                                   "every environment, H = 30 frames, checkpoints every 10",
+                           "forward_env_steps_per_s": value / world, **adj}
+        line["refinement"] = refine_study(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:

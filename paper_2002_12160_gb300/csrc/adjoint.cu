@@ -667,7 +667,10 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     const size_t tab_frame = (size_t)(ns + 1) * Lk * kLinkStride;
     const float4 *tab0 = a.link_tab + (size_t)a.frame0 * tab_frame;
 
-    // -- pass 1: the cost, and the state at every K-th frame
+    // -- pass 1: the cost, the state at every K-th frame, and the substep
+    //    states and frame forces of the last segment (the first one reversed)
+    const int nck = (a.H + a.K - 1) / a.K;
+    const int f_last = (nck - 1) * a.K;
     double cost = 0.0;
     Body b = b0;
     for (int f = 0; f < a.H && !(st & kDiverged); ++f) {
@@ -676,9 +679,12 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
         __syncwarp();
         const float4 *tab = tab0 + (size_t)f * tab_frame;
         for (int s = 0; s < ns; ++s) {
+            if (f >= f_last && lane == 0) store_body(sp.sg + 4 * ((f - f_last) * ns + s), b);
             const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
             fwd_substep<PL, false>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st);
         }
+        if (f >= f_last)
+            for (int k = lane; k < 3 * P; k += 32) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
         if (!all_finite(b.x, b.q, b.v, b.w)) st |= IH_ENV_NONFINITE;
         else if (dot(b.x, b.x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
         if (lane == 0) {   // frame cost in FP64, in pad order, as the scored step
@@ -700,13 +706,13 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
         }
         __syncwarp();
     }
+    if (a.out_pose && lane == 0) {   // the horizon's end state (not meaningful when diverged)
+        a.out_pose[2 * slot] = make_float4(b.x.x, b.x.y, b.x.z, 0.0f);
+        a.out_pose[2 * slot + 1] = make_float4(b.q.w, b.q.x, b.q.y, b.q.z);
+        a.out_vel[2 * slot] = make_float4(b.v.x, b.v.y, b.v.z, 0.0f);
+        a.out_vel[2 * slot + 1] = make_float4(b.w.x, b.w.y, b.w.z, 0.0f);
+    }
     if (a.forward_only) {
-        if (!(st & kDiverged) && a.out_pose && lane == 0) {
-            a.out_pose[2 * env] = make_float4(b.x.x, b.x.y, b.x.z, 0.0f);
-            a.out_pose[2 * env + 1] = make_float4(b.q.w, b.q.x, b.q.y, b.q.z);
-            a.out_vel[2 * env] = make_float4(b.v.x, b.v.y, b.v.z, 0.0f);
-            a.out_vel[2 * env + 1] = make_float4(b.w.x, b.w.y, b.w.z, 0.0f);
-        }
         if (lane == 0 && a.cost) a.cost[slot] = (st & kDiverged) ? INFINITY : cost;
         return;
     }
@@ -720,12 +726,11 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     // -- pass 2: segments in reverse
     Adj ad = {mk(0, 0, 0), Q4{0, 0, 0, 0}, mk(0, 0, 0), mk(0, 0, 0)};
     float invm_b = 0.0f, mu_b = 0.0f;
-    const int nck = (a.H + a.K - 1) / a.K;
     const float wf2 = 2.0f * cfg.w_force * inv_h * inv_ns;
     for (int seg = nck - 1; seg >= 0; --seg) {
         const int fb = seg * a.K, fe = min(a.H, fb + a.K);
         b = load_body(sp.ck + 4 * seg);
-        for (int f = fb; f < fe; ++f) {   // substep start states and frame forces of the segment
+        for (int f = fb; f < fe && seg < nck - 1; ++f) {   // substep start states and frame forces
             for (int k = lane; k < 3 * P; k += 32) S.padacc[k] = 0.0f;
             __syncwarp();
             const float4 *tab = tab0 + (size_t)f * tab_frame;
@@ -794,6 +799,10 @@ __global__ void refine_kernel(const RefineArgs r) {
     if (r.step == 0 || c < r.best_c[i]) {
         r.best_pose[2 * i] = r.tr_pose[2 * env];
         r.best_pose[2 * i + 1] = r.tr_pose[2 * env + 1];
+        for (int q = 0; q < 2; ++q) {
+            r.best_end_pose[2 * i + q] = r.end_pose[2 * i + q];
+            r.best_end_vel[2 * i + q] = r.end_vel[2 * i + q];
+        }
         r.best_params[i] = r.tr_params[env];
         for (int d = 0; d < 8; ++d) r.best_grad[8 * i + d] = r.grad[8 * i + d];
         r.best_c[i] = c;
@@ -841,10 +850,10 @@ __global__ void refine_commit_kernel(int k, const int *elite, const double *best
     const double c = best_c[i];
     if (!(c < c0[i])) return;   // not improved: the live state stays the scored one
     const int env = elite[i];
-    pose[2 * env] = end_pose[2 * env];
-    pose[2 * env + 1] = end_pose[2 * env + 1];
-    vel[2 * env] = end_vel[2 * env];
-    vel[2 * env + 1] = end_vel[2 * env + 1];
+    pose[2 * env] = end_pose[2 * i];
+    pose[2 * env + 1] = end_pose[2 * i + 1];
+    vel[2 * env] = end_vel[2 * i];
+    vel[2 * env + 1] = end_vel[2 * i + 1];
     params[env] = best_params[i];
     const int nw = *n_window;
     c_sum[env] = c;

@@ -57,7 +57,7 @@ struct ih_sim {
     bool rf_alloc = false, ws_valid = false;
     int ws_frames = 0;
     float4 *ws_pose = nullptr, *ws_vel = nullptr, *tr_pose = nullptr, *end_pose = nullptr, *end_vel = nullptr,
-           *best_pose = nullptr;
+           *best_pose = nullptr, *best_end_pose = nullptr, *best_end_vel = nullptr;
     float2 *ws_params = nullptr, *tr_params = nullptr, *best_params = nullptr;
     float *best_grad = nullptr, *scale = nullptr, *r_grad = nullptr;
     double *best_c = nullptr, *c0 = nullptr, *r_cost = nullptr;
@@ -724,6 +724,7 @@ cudaError_t refine_alloc(ih_sim *s) {
     A(dalloc(s, &s->ws_pose, 2 * N)); A(dalloc(s, &s->ws_vel, 2 * N)); A(dalloc(s, &s->ws_params, N));
     A(dalloc(s, &s->tr_pose, 2 * N)); A(dalloc(s, &s->tr_params, N));
     A(dalloc(s, &s->end_pose, 2 * N)); A(dalloc(s, &s->end_vel, 2 * N));
+    A(dalloc(s, &s->best_end_pose, 2 * N)); A(dalloc(s, &s->best_end_vel, 2 * N));
     A(dalloc(s, &s->best_pose, 2 * N)); A(dalloc(s, &s->best_params, N)); A(dalloc(s, &s->best_grad, 8 * N));
     A(dalloc(s, &s->scale, N)); A(dalloc(s, &s->r_grad, 8 * N));
     A(dalloc(s, &s->best_c, N)); A(dalloc(s, &s->c0, N)); A(dalloc(s, &s->r_cost, N));
@@ -780,10 +781,13 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
     AdjArgs a = adjoint_args(s, frame0, T, T, obs, beta, width);
     a.n = k; a.envs = s->elite_env; a.pose = s->tr_pose; a.vel = s->ws_vel; a.params = s->tr_params;
     a.cost = s->r_cost; a.grad = s->r_grad; a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
+    a.out_pose = s->end_pose; a.out_vel = s->end_vel;
     RefineArgs ra;
     ra.k = k; ra.elite = s->elite_env; ra.tr_pose = s->tr_pose; ra.tr_params = s->tr_params;
     ra.best_pose = s->best_pose; ra.best_params = s->best_params; ra.best_grad = s->best_grad;
     ra.best_c = s->best_c; ra.c0 = s->c0; ra.scale = s->scale; ra.cost = s->r_cost; ra.grad = s->r_grad;
+    ra.end_pose = s->end_pose; ra.end_vel = s->end_vel;
+    ra.best_end_pose = s->best_end_pose; ra.best_end_vel = s->best_end_vel;
     for (int d = 0; d < 8; ++d) ra.eta[d] = step_scale * opt->floor_std[d];
     ra.m_lo = opt->m_lo; ra.m_hi = opt->m_hi; ra.mu_lo = opt->mu_lo; ra.mu_hi = opt->mu_hi;
     for (int it = 0; it <= steps && e == cudaSuccess; ++it) {
@@ -793,11 +797,9 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
         ra.last = it == steps ? 1 : 0;
         if (e == cudaSuccess) e = launch_refine(ra, st);
     }
-    // the best state of each elite, simulated to the window's end, replaces the scored one
-    a.forward_only = 1; a.out_pose = s->end_pose; a.out_vel = s->end_vel;
-    if (e == cudaSuccess) e = launch_adjoint(a, st);
+    // the window's end state of each improved elite's best trial replaces the scored one
     if (e == cudaSuccess)
-        e = launch_refine_commit(k, s->elite_env, s->best_c, s->c0, s->best_params, s->end_pose, s->end_vel, s->pose,
+        e = launch_refine_commit(k, s->elite_env, s->best_c, s->c0, s->best_params, s->best_end_pose, s->best_end_vel, s->pose,
                                  s->vel, s->params, s->c_sum, s->c_mean, s->n_window, st);
     if (e == cudaSuccess && elite_out)
         e = cudaMemcpyAsync(elite_out, s->elite_env, k * sizeof(int), cudaMemcpyDeviceToDevice, st);

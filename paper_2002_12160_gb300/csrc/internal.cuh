@@ -304,7 +304,7 @@ struct AdjArgs {
     size_t stride;
     int iters_max;
     int forward_only;         // 1: cost (and end state) only, no reverse sweep
-    float4 *out_pose, *out_vel;   // [N][2] end state of each environment (forward_only), or null
+    float4 *out_pose, *out_vel;   // [n][2] end state of each slot, or null
 };
 
 // Gradient refinement of the elites (adjoint.cu): accept or reject the last
@@ -321,13 +321,15 @@ struct RefineArgs {
     float *scale;                 // [k] step multiplier (halved on a rejected trial)
     const double *cost;           // [k] cost at the trial
     const float *grad;            // [k][8] gradient at the trial
+    const float4 *end_pose, *end_vel;    // [k][2] end state of the trial's window
+    float4 *best_end_pose, *best_end_vel;  // [k][2] end state of the best trial
     float eta[8];                 // step length per coordinate
     float m_lo, m_hi, mu_lo, mu_hi;
     int step;                     // 0: the first evaluation (of the unrefined state)
     int last;                     // 1: restore the best state instead of stepping
 };
 cudaError_t launch_refine(const RefineArgs &r, cudaStream_t s);
-// copy refined elites (end state, parameters, window cost) into the live state
+// copy refined elites (end state [k][2], parameters, window cost) into the live state
 cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, const double *c0,
                                  const float2 *best_params, const float4 *end_pose, const float4 *end_vel,
                                  float4 *pose, float4 *vel, float2 *params, double *c_sum, double *c_mean,
