@@ -44,6 +44,30 @@ FLOP_PER_CONTACT_ITER = 62     # relative velocity, normal/tangent update,
                                # cone clamp, relaxation, impulse/moment sums
 FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
                                # the body velocity update
+# DRAM traffic of one step_kernel launch (dram__bytes_read.sum +
+# dram__bytes_write.sum) from the ncu capture summarised in
+# profiles/step_kernel_tracking_cyl64.md, valid for the kernel sources whose
+# hash is recorded with it; reported as null once they change.
+STEP_TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
+STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/contact.cuh",
+                "paper_2002_12160_gb300/csrc/internal.cuh"]
+
+
+def step_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def step_traffic():
+    if STEP_TRAFFIC["bytes_per_launch"] is None or STEP_TRAFFIC["sources_sha256"] != step_sources_sha():
+        return None
+    return STEP_TRAFFIC["bytes_per_launch"]
+
+
 # bytes of HBM traffic per env-frame the step must move: state in/out
 # (pose, vel 64 B each way), params (8 B), shape/iters/status (12 B), forces
 STATE_BYTES_PER_ENV = 64 + 64 + 8 + 12 + 4
@@ -60,6 +84,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the adjoint throughput and the refinement-vs-plain tracking study")
+    p.add_argument("--part", choices=["all", "adjoint"], default="all",
+                   help="adjoint: only the forward+adjoint throughput block (for profiling)")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     p.add_argument("--sweep", default=None,
                    help="comma-separated N values: also time the workload at each N (tracking frames/s)")
@@ -419,7 +445,8 @@ def run_ours(args, rank, world, local):
                                       "autotune_ms": {f"{a}x{b}": round(v, 4) for (a, b), v in tune_ms.items()}}},
             "tracking_frames_per_s": T / (ms / 1e3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "step_kernel (fused step + score)",
+                         "frac": achieved / peak, "traffic": step_traffic(), "traffic_unit": "bytes per launch",
+                         "kernel": "step_kernel (fused step + score)",
                          "step_kernel_ms": step_ms, "flop_per_launch": per_launch_flops,
                          "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"},
             "hbm": {"step_bytes_per_launch": step_bytes, "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
@@ -454,6 +481,10 @@ def run_ours(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.part == "adjoint":
+        if rank == 0:
+            print(json.dumps({"part": "adjoint", "adjoint": measure_adjoint(local)}), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         backend = "nccl" if args.impl == "ours" else "gloo"

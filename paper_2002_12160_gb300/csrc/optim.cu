@@ -42,18 +42,28 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// block-wide inclusive scan of one unsigned per thread (Hillis-Steele)
+// block-wide inclusive scan of one unsigned per thread: warp scans, then a
+// scan of the warp totals by the first warp (buf holds kWarps + 1 entries)
 __device__ unsigned block_scan(unsigned v, unsigned *buf) {
-    const int t = threadIdx.x;
-    buf[t] = v;
-    __syncthreads();
-    for (int o = 1; o < kSel; o <<= 1) {
-        const unsigned add = (t >= o) ? buf[t - o] : 0u;
-        __syncthreads();
-        buf[t] += add;
-        __syncthreads();
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
-    const unsigned r = buf[t];
+    if (lane == 31) buf[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        unsigned x = lane < kWarps ? buf[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane < kWarps) buf[lane] = x;
+    }
+    __syncthreads();
+    const unsigned r = v + (w > 0 ? buf[w - 1] : 0u);
     __syncthreads();
     return r;
 }
@@ -73,7 +83,7 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
     __shared__ unsigned int hist[256];
     __shared__ unsigned long long s_prefix;
     __shared__ unsigned int s_rem;
-    __shared__ unsigned int s_scan[kSel];
+    __shared__ unsigned int s_scan[kWarps + 1];
     __shared__ double red[kWarps];
     __shared__ double s_val[2];
     __shared__ unsigned long long s_min_key;
@@ -98,15 +108,31 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
             if ((key & hmask) == pre) atomicAdd(&hist[(key >> shift) & 0xff], 1u);
         }
         __syncthreads();
-        if (t == 0) {
-            unsigned rem = s_rem, acc = 0;
-            int b = 0;
-            for (; b < 255; ++b) {
-                if (acc + hist[b] >= rem) break;
-                acc += hist[b];
+        if (t < 32) {   // the first bin whose running count reaches rem (warp-parallel scan)
+            const unsigned rem = s_rem;
+            unsigned c8[8], sum = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { c8[q] = hist[8 * t + q]; sum += c8[q]; }
+            unsigned inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (t >= o) inc += u;
             }
-            s_rem = rem - acc;
-            s_prefix = pre | ((unsigned long long)b << shift);
+            const unsigned excl = inc - sum;
+            // lanes whose range holds the crossing (the last lane holds bin 255 as the fallback)
+            const bool here = (excl < rem && inc >= rem) || (t == 31 && inc < rem);
+            const unsigned who = __ballot_sync(0xffffffffu, here);
+            if (t == __ffs(who) - 1) {
+                unsigned acc = excl;
+                int b = 8 * t;
+                for (int q = 0; q < 7; ++q, ++b) {
+                    if (acc + c8[q] >= rem) break;
+                    acc += c8[q];
+                }
+                s_rem = rem - acc;
+                s_prefix = pre | ((unsigned long long)b << shift);
+            }
         }
         __syncthreads();
     }
@@ -233,69 +259,109 @@ __global__ void __launch_bounds__(kOptBlock) stats_kernel(const OptArgs a) {
     }
     if (j < k) a.elite_w[j] = pre;
     if (threadIdx.x == 31) a.block_w[blockIdx.x] = pre;
+    // block sums of the moments: transposed through shared memory, moment q
+    // summed over the block's threads in index order by thread q
+    __shared__ double tm[kOptBlock][kMoments + 1];
 #pragma unroll
-    for (int q = 0; q < kMoments; ++q) mom[q] = warp_sum(mom[q]);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < kMoments; ++q) a.moments[(size_t)blockIdx.x * kMoments + q] = mom[q];
+    for (int q = 0; q < kMoments; ++q) tm[threadIdx.x][q] = mom[q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kMoments; q += kOptBlock) {
+        double sacc = 0.0;
+        for (int r = 0; r < kOptBlock; ++r) sacc += tm[r][q];
+        a.moments[(size_t)blockIdx.x * kMoments + q] = sacc;
+    }
 }
 
 __global__ void __launch_bounds__(kSel) finalize_kernel(const OptArgs a, int nblocks) {
-    __shared__ double buf[kSel];
     __shared__ double sm[kMoments];
-    const int t = threadIdx.x;
+    __shared__ double cv[8][8];
+    __shared__ double wtot[kWarps];
+    __shared__ double s_carry;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     // moments: thread q < 45 sums its moment over the blocks in block order
     if (t < kMoments) {
         double s = 0.0;
         for (int b = 0; b < nblocks; ++b) s += a.moments[(size_t)b * kMoments + t];
         sm[t] = s;
     }
-    // exclusive offsets of the per-block weight sums (block-wide scan in chunks)
-    double carry = 0.0;
+    // exclusive offsets of the per-block weight sums, in chunks of kSel blocks:
+    // warp scans, then the warp totals in warp order by the first warp
+    if (t == 0) s_carry = 0.0;
+    __syncthreads();
     for (int base = 0; base < nblocks; base += kSel) {
         const int b = base + t;
         const double v = (b < nblocks) ? a.block_w[b] : 0.0;
-        buf[t] = v;
-        __syncthreads();
-        for (int o = 1; o < kSel; o <<= 1) {
-            const double add = (t >= o) ? buf[t - o] : 0.0;
-            __syncthreads();
-            buf[t] += add;
-            __syncthreads();
+        double inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
         }
-        if (b < nblocks) a.block_w[b] = carry + buf[t] - v;
-        carry += buf[kSel - 1];
+        if (lane == 31) wtot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            double x = wtot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double u = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += u;
+            }
+            wtot[lane] = x;
+        }
+        __syncthreads();
+        const double carry = s_carry;
+        const double before = (wid > 0 ? wtot[wid - 1] : 0.0) + (inc - v);
+        if (b < nblocks) a.block_w[b] = carry + before;
+        __syncthreads();
+        if (t == 0) s_carry = carry + wtot[kWarps - 1];
         __syncthreads();
     }
-    if (t == 0) {
-        const double wsum = sm[0];
-        double mu[8], C[8][8], L[8][8];
-        for (int r = 0; r < 8; ++r) mu[r] = sm[1 + r] / wsum;
-        int q = 9;
-        for (int r = 0; r < 8; ++r)
-            for (int c = 0; c <= r; ++c) {
-                C[r][c] = sm[q++] / wsum - mu[r] * mu[c];
-                C[c][r] = C[r][c];
-            }
-        for (int r = 0; r < 8; ++r) C[r][r] += a.floor_var[r];
+    // weighted covariance (36 entries in parallel) plus the floor
+    const double wsum = sm[0];
+    if (t < 64) {
+        const int r = t >> 3, c = t & 7;
+        const int hi = r > c ? r : c, lo = r > c ? c : r;
+        const double mr = sm[1 + r] / wsum, mc = sm[1 + c] / wsum;
+        double v = sm[9 + hi * (hi + 1) / 2 + lo] / wsum - mr * mc;
+        if (r == c) v += a.floor_var[r];
+        cv[r][c] = v;
+    }
+    __syncthreads();
+    // Cholesky by the first warp: lane i < 8 holds row i of L; column j in
+    // turn, s = C_ij - sum_{m<j} L_im L_jm in m order, L_jj = sqrt(s_jj),
+    // L_ij = s_ij / L_jj
+    if (wid == 0) {
+        double L[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) L[c] = 0.0;
         bool ok = wsum > 0.0;
-        for (int r = 0; r < 8; ++r)
-            for (int c = 0; c < 8; ++c) L[r][c] = 0.0;
-        for (int i = 0; i < 8 && ok; ++i)
-            for (int j = 0; j <= i; ++j) {
-                double s = C[i][j];
-                for (int m = 0; m < j; ++m) s -= L[i][m] * L[j][m];
-                if (i == j) {
-                    if (!(s > 0.0)) { ok = false; break; }
-                    L[i][i] = sqrt(s);
-                } else {
-                    L[i][j] = s / L[j][j];
-                }
+        const int i = lane;
+        const bool row = i < 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            double sj = (row && i >= j) ? cv[i][j] : 0.0;
+#pragma unroll
+            for (int m = 0; m < j; ++m) {
+                const double ljm = __shfl_sync(0xffffffffu, L[m], j);
+                if (row && i >= j) sj -= L[m] * ljm;
             }
-        for (int r = 0; r < 8; ++r)
-            for (int c = 0; c < 8; ++c) a.misc[8 * r + c] = L[r][c];
-        a.misc[M_OK] = ok ? 1.0 : 0.0;
-        a.misc[M_WSUM] = carry;
-        a.misc[M_NBLK] = (double)nblocks;
+            const double djj = __shfl_sync(0xffffffffu, sj, j);
+            if (!(djj > 0.0)) ok = false;
+            const double ljj = ok ? sqrt(djj) : 0.0;
+            if (row && i == j) L[j] = ljj;
+            else if (row && i > j) L[j] = ok ? sj / ljj : 0.0;
+        }
+        if (!ok) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) L[c] = 0.0;
+        }
+        if (i < 8)
+            for (int c = 0; c < 8; ++c) a.misc[8 * i + c] = L[c];
+        if (lane == 0) {
+            a.misc[M_OK] = ok ? 1.0 : 0.0;
+            a.misc[M_WSUM] = s_carry;
+            a.misc[M_NBLK] = (double)nblocks;
+        }
     }
 }
 
@@ -303,10 +369,19 @@ __device__ __forceinline__ double cum_w(const OptArgs &a, int j) {
     return a.block_w[j / kOptBlock] + a.elite_w[j];
 }
 
+constexpr int kCdfSmem = 2048;   // elites whose CDF apply_kernel stages in shared memory
+
 // One thread per environment.
 __global__ void __launch_bounds__(kOptBlock) apply_kernel(const OptArgs a) {
+    __shared__ double cdf[kCdfSmem];
     const int i = blockIdx.x * kOptBlock + threadIdx.x;
     const int N = a.N;
+    const int k = (int)a.misc[M_K];
+    const bool staged = k <= kCdfSmem;
+    if (staged) {   // the block's binary searches read the CDF from shared memory
+        for (int j = threadIdx.x; j < k; j += kOptBlock) cdf[j] = cum_w(a, j);
+        __syncthreads();
+    }
     if (i >= N) return;
     if (i == 0) *a.n_window = 0;
     a.c_sum[i] = 0.0;
@@ -314,7 +389,6 @@ __global__ void __launch_bounds__(kOptBlock) apply_kernel(const OptArgs a) {
         if (a.parent_out) a.parent_out[i] = i;
         return;
     }
-    const int k = (int)a.misc[M_K];
     const double u = a.misc[M_U], wsum = a.misc[M_WSUM];
     const bool ok = a.misc[M_OK] != 0.0;
     const int M = N - k;
@@ -323,7 +397,7 @@ __global__ void __launch_bounds__(kOptBlock) apply_kernel(const OptArgs a) {
     int lo = 0, hi = k - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (pos < cum_w(a, mid)) hi = mid; else lo = mid + 1;
+        if (pos < (staged ? cdf[mid] : cum_w(a, mid))) hi = mid; else lo = mid + 1;
     }
     const int par = a.elite_env[lo];
     if (a.parent_out) a.parent_out[i] = par;
