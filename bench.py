@@ -260,18 +260,20 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e
     seed = wl.seed + 7919 * rank   # independent replicas per rank
     tr = tracking.Tracker(wl, seed=seed)
     tr.prepare()
-    if shape:
-        a, b = (int(v) for v in shape.lower().split("x"))
-        tr.sim.sim_set_variant(a, b)
-        chosen, tune_ms = (a, b), {}
-    else:
-        # pick the step kernel's shape on the first frames (the state is restored)
-        chosen, tune_ms = tr.sim.sim_autotune(0, 2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for w in range(warmup):
         tr.window(w)
+    torch.cuda.synchronize()
+    if shape:
+        a, b = (int(v) for v in shape.lower().split("x"))
+        tr.sim.sim_set_variant(a, b)
+        chosen, tune_ms = (a, b), {}
+    else:
+        # pick the step kernel's shape on the frames after the warm-up windows, where
+        # the contacts have settled (the autotuner restores the state after each trial)
+        chosen, tune_ms = tr.sim.sim_autotune(warmup * T, 4)
     torch.cuda.synchronize()
     tr.sim.sim_work_counters(reset=True)
     barrier(world)
