@@ -181,9 +181,26 @@ ih_status sim_step(ih_sim *sim, int32_t frame0, int32_t n_frames);
 ih_status sim_step_track(ih_sim *sim, int32_t frame, const float *obs, double *cost_mean,
                          int32_t *argmin, float *est_pose);
 
+/* T scored frames [frame0, frame0 + T) in one kernel launch: for every
+ * environment, T frames of sim_step, each followed by its frame cost, window
+ * sum and window mean as in sim_step_track (same arithmetic, same order); the
+ * mean and the pose after every frame are kept in the handle for
+ * sim_frames_argmin. The environments need no argmin to advance, so the T
+ * frames run without a grid-wide step in between. obs is device
+ * float[T][P][3]. Passages: Sec. III-A, Sec. III-C, Algorithm 1. */
+ih_status sim_step_frames(ih_sim *sim, int32_t frame0, int32_t T, const float *obs);
+
+/* The argmin i*_f (NaN = +inf, ties to the lowest index) and the pose of i*_f
+ * after frame f, for each frame of the last sim_step_frames call; outputs
+ * (device, may be NULL): est_pose float[T][8], argmin int32[T]. Results equal
+ * T calls of sim_step_track bit for bit. IH_ERR_STATE without a preceding
+ * sim_step_frames. */
+ih_status sim_frames_argmin(ih_sim *sim, float *est_pose, int32_t *argmin);
+
 /* One tracking window of Algorithm 1: for k = 0..T-1, sim_step_track(frame0
  * + k, obs + k P 3, ...) writing est_pose[k] and argmin[k], then
- * optimizer_update(opt, update_index). obs is device float[T][P][3];
+ * optimizer_update(opt, update_index), launched as sim_step_frames,
+ * sim_frames_argmin and the optimizer's kernels. obs is device float[T][P][3];
  * est_pose (float[T][8]) and argmin (int32[T]) are device outputs (may be
  * NULL). The window's launches are captured once into a CUDA graph and
  * replayed on later calls with the same T, step shape and optimizer

@@ -66,6 +66,10 @@ struct ih_sim {
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int win_T = 0;
+    double *wf_cm = nullptr;        // [T][N] window means of every frame (window-mode launches)
+    float4 *wf_pose = nullptr;      // [T][N][2] poses of every frame
+    int wf_T = 0;
+    int frames_T = 0;               // frames of the last sim_step_frames call, not yet scored
     StepVariant win_variant{0, 0, 0};
     ih_opt_config win_opt{};
     // host bookkeeping
@@ -289,6 +293,8 @@ ih_status sim_destroy(ih_sim *s) {
     if (s->ev_out) cudaEventDestroy(s->ev_out);
     for (void *p : s->owned) cudaFree(p);
     if (s->adj_scratch) cudaFree(s->adj_scratch);
+    if (s->wf_cm) cudaFree(s->wf_cm);
+    if (s->wf_pose) cudaFree(s->wf_pose);
     delete s;
     return IH_OK;
 }
@@ -374,6 +380,7 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window; a.cost_mean = nullptr;
     a.argmin_state = s->argmin; a.argmin_out = nullptr; a.est_pose_out = nullptr;
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
+    a.cm_frames = nullptr; a.pose_frames = nullptr;
     cudaError_t e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->stepped = true;
@@ -391,6 +398,7 @@ StepArgs scored_args(ih_sim *s, int frame, const float *obs, double *cost_mean, 
     a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window; a.cost_mean = cost_mean;
     a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est;
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
+    a.cm_frames = nullptr; a.pose_frames = nullptr;
     return a;
 }
 
@@ -432,6 +440,58 @@ ih_status sim_step_track(ih_sim *s, int32_t frame, const float *obs, double *cos
     return IH_OK;
 }
 
+namespace {
+// per-frame window means and poses of a window-mode launch, grown to T frames
+cudaError_t window_buffers(ih_sim *s, int T) {
+    if (T <= s->wf_T) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (s->cap_stream && e == cudaSuccess) e = cudaStreamSynchronize(s->cap_stream);
+    if (e != cudaSuccess) return e;
+    if (s->wf_cm) cudaFree(s->wf_cm);
+    if (s->wf_pose) cudaFree(s->wf_pose);
+    s->wf_cm = nullptr; s->wf_pose = nullptr; s->wf_T = 0;
+    void *p1 = nullptr, *p2 = nullptr;
+    e = cudaMalloc(&p1, (size_t)T * s->cfg.n_envs * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p2, (size_t)T * s->cfg.n_envs * 2 * sizeof(float4));
+    if (e != cudaSuccess) { if (p1) cudaFree(p1); return e; }
+    s->wf_cm = static_cast<double *>(p1);
+    s->wf_pose = static_cast<float4 *>(p2);
+    s->wf_T = T;
+    return cudaSuccess;
+}
+}  // namespace
+
+ih_status sim_step_frames(ih_sim *s, int32_t frame0, int32_t T, const float *obs) {
+    if (!s) return IH_ERR_ARG;
+    if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
+    if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + T);
+    for (int f = frame0; f < frame0 + T; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    cudaError_t e = window_buffers(s, T);
+    if (e != cudaSuccess) return cuda_fail(s, e, "window buffers");
+    StepArgs a = scored_args(s, frame0, obs, nullptr, nullptr, nullptr);
+    a.n_frames = T;
+    a.cm_frames = s->wf_cm;
+    a.pose_frames = s->wf_pose;
+    e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    s->stepped = true;
+    s->frames_T = T;
+    return IH_OK;
+}
+
+ih_status sim_frames_argmin(ih_sim *s, float *est_pose, int32_t *argmin) {
+    if (!s) return IH_ERR_ARG;
+    if (s->frames_T < 1) return fail(s, IH_ERR_STATE, "no sim_step_frames call to score");
+    cudaError_t e = launch_window_argmin(s->cfg.n_envs, s->frames_T, s->wf_cm, s->wf_pose, nullptr, argmin, est_pose,
+                                         s->argmin, s->n_window, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "argmin launch");
+    s->window_frames += s->frames_T;
+    s->frames_T = 0;
+    return IH_OK;
+}
+
 ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *obs, const ih_opt_config *opt,
                            uint32_t update_index, float *est_pose, int32_t *argmin) {
     if (!s) return IH_ERR_ARG;
@@ -460,15 +520,23 @@ ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *ob
                       s->win_variant.cpl == s->variant.cpl && std::memcmp(&s->win_opt, opt, sizeof *opt) == 0;
     if (!same) {
         if (s->win_exec) { cudaGraphExecDestroy(s->win_exec); s->win_exec = nullptr; }
+        e = window_buffers(s, T);   // outside the capture
+        if (e != cudaSuccess) return cuda_fail(s, e, "window buffers");
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
         cudaError_t le = cudaSuccess;
-        for (int k = 0; k < T && le == cudaSuccess; ++k) {
+        {   // the window's T frames in one launch, then every frame's argmin and estimate
             StepArgs a = scored_args(s, frame0, nullptr, nullptr, nullptr, nullptr);
             a.win = s->win;
-            a.win_k = k;
+            a.win_k = 0;
+            a.n_frames = T;
+            a.cm_frames = s->wf_cm;
+            a.pose_frames = s->wf_pose;
             le = launch_step(a, s->variant, s->step_grid, s->s_max, st);
+            if (le == cudaSuccess)
+                le = launch_window_argmin(s->cfg.n_envs, T, s->wf_cm, s->wf_pose, s->win, nullptr, nullptr, s->argmin,
+                                          s->n_window, st);
         }
         if (le == cudaSuccess) {
             OptArgs oa = opt_args(s, opt, update_index, nullptr, nullptr);

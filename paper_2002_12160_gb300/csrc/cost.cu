@@ -104,4 +104,68 @@ cudaError_t launch_cost(const CostArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+// One block per frame of a window-mode launch: the lowest (C_i, i) of that
+// frame's window means (NaN = +inf), the pose of that environment after the
+// frame, and -- for the window's last frame -- the handle's i*.
+__global__ void __launch_bounds__(1024) window_argmin_kernel(int N, int T, const double *cm_frames,
+                                                              const float4 *pose_frames, const WinDesc *win,
+                                                              int *argmin_out, float *est_out, int *argmin_state,
+                                                              int *n_window) {
+    __shared__ double sc[32];
+    __shared__ int si[32];
+    __shared__ int best_s;
+    const int f = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    double bc = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = t; i < N; i += blockDim.x) {
+        double c = cm_frames[(size_t)f * N + i];
+        if (isnan(c)) c = INFINITY;
+        if (c < bc || (c == bc && i < bi)) { bc = c; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oc < bc || (oc == bc && oi < bi)) { bc = oc; bi = oi; }
+    }
+    if (lane == 0) { sc[wid] = bc; si[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        bc = lane < nw ? sc[lane] : INFINITY;
+        bi = lane < nw ? si[lane] : 0x7fffffff;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oc < bc || (oc == bc && oi < bi)) { bc = oc; bi = oi; }
+        }
+        if (lane == 0) {
+            const int best = (bi == 0x7fffffff) ? 0 : bi;
+            best_s = best;
+            int *am = win ? win->argmin : argmin_out;
+            if (am) am[f] = best;
+            if (f == T - 1) *argmin_state = best;
+            if (f == 0) *n_window += T;
+        }
+    }
+    __syncthreads();
+    float *est = win ? win->est : est_out;
+    if (est && t < 8) {
+        const float4 p = pose_frames[2 * ((size_t)f * N + best_s) + (t >> 2)];
+        const float v[4] = {p.x, p.y, p.z, p.w};
+        est[8 * f + t] = v[t & 3];
+    }
+}
+}  // namespace
+
+cudaError_t launch_window_argmin(int N, int T, const double *cm_frames, const float4 *pose_frames,
+                                 const WinDesc *win, int *argmin_out, float *est_out, int *argmin_state,
+                                 int *n_window, cudaStream_t s) {
+    window_argmin_kernel<<<T, 1024, 0, s>>>(N, T, cm_frames, pose_frames, win, argmin_out, est_out, argmin_state,
+                                            n_window);
+    return cudaGetLastError();
+}
+
 }  // namespace ih

@@ -218,6 +218,11 @@ struct StepArgs {
     double *part_c;           // [grid] scratch
     int *part_i;              // [grid] scratch
     unsigned int *done;       // ticket
+    // window mode (cm_frames != null): n_frames scored frames in one launch; each
+    // environment writes its window mean and pose after every frame, and
+    // launch_window_argmin takes each frame's argmin afterwards
+    double *cm_frames;        // [n_frames][N]
+    float4 *pose_frames;      // [n_frames][N][2]
 };
 struct StepVariant {
     int group;        // lanes per environment
@@ -250,6 +255,12 @@ struct CostArgs {
 };
 cudaError_t launch_cost(const CostArgs &a, cudaStream_t s);
 int cost_blocks(int N);
+// argmin and estimate of every frame of a window-mode step launch (outputs from
+// win when set, else argmin_out [T] / est_out [T][8], either may be null);
+// advances the window counter by T and sets the handle's i* to the last frame's
+cudaError_t launch_window_argmin(int N, int T, const double *cm_frames, const float4 *pose_frames,
+                                 const WinDesc *win, int *argmin_out, float *est_out, int *argmin_state,
+                                 int *n_window, cudaStream_t s);
 
 constexpr int kOptBlock = 32;   // elites / environments per block in the grid kernels
 constexpr int kMoments = 45;    // sum w, sum w d (8), sum w d d^T (36, lower triangle)

@@ -160,8 +160,10 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         frame0 = a.win->frame0 + a.win_k;
         obs = a.win->obs ? a.win->obs + (size_t)a.win_k * P * 3 : nullptr;
     }
+    const bool window_mode = a.cm_frames != nullptr;   // every frame scored, argmin afterwards
     const bool scored = obs != nullptr;
-    const int n_win = scored ? *a.n_window + 1 : 0;
+    const int n_win0 = scored ? *a.n_window : 0;       // frames in the window before this launch
+    const int n_win = n_win0 + 1;
 
     // block-wide tables: the pads of each link (in pad order) and their intervals
     unsigned char *pl_cnt = smem;
@@ -212,6 +214,40 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         const int ncl = (NS + kCluster - 1) / kCluster;
         const float inv_ncl = 1.0f / (float)ncl;
         const int cfirst = __ldg(sc.cl_first + shp);
+        double c_sum_env = (window_mode && G.tid == 0) ? a.c_sum[env] : 0.0;
+        // cost of the frame just stepped against observation ob (Sec. III-C),
+        // FP64 without contraction, pads in order; valid in the group's thread 0
+        auto frame_cost = [&](const float *ob, int stt) -> double {
+            const float inv_ns_f = 1.0f / (float)ns;
+            G.sync();
+            const double tau = (double)cfg.tau, wf = (double)cfg.w_force;
+            const double tau2 = __dmul_rn(tau, tau);
+            for (int p = G.tid; p < P; p += TPE) {
+                const double fx = S.padacc[3 * p] * inv_ns_f, fy = S.padacc[3 * p + 1] * inv_ns_f,
+                             fz = S.padacc[3 * p + 2] * inv_ns_f;
+                const double ox = ob[3 * p], oy = ob[3 * p + 1], oz = ob[3 * p + 2];
+                const double dx = __dsub_rn(fx, ox), dy = __dsub_rn(fy, oy), dz = __dsub_rn(fz, oz);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                S.term[p] = __dmul_rn(wf, d2);
+                const double ns2 = __dadd_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)), __dmul_rn(fz, fz));
+                const double no2 = __dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz));
+                S.flag[p] = (ns2 > tau2) != (no2 > tau2);
+            }
+            G.sync();
+            double c = 0.0;
+            if (G.tid == 0) {
+                if (stt & kDiverged) {
+                    c = INFINITY;
+                } else {
+                    for (int p = 0; p < P; ++p) {
+                        c = __dadd_rn(c, S.term[p]);
+                        if (S.flag[p]) c = __dadd_rn(c, (double)cfg.w_contact);
+                    }
+                }
+            }
+            G.sync();   // S.term / S.flag are reused by the next frame
+            return c;
+        };
 
         for (int fr = 0; fr < a.n_frames; ++fr) {
             for (int k = G.tid; k < 3 * P; k += TPE) S.padacc[k] = 0.0f;
@@ -488,36 +524,28 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 if (!all_finite(x, q, v, w)) st |= IH_ENV_NONFINITE;
                 else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
             }
+            if (window_mode) {   // this frame's cost, window sum and mean, and pose
+                const double c = frame_cost(obs + (size_t)fr * P * 3, st);
+                if (G.tid == 0) {
+                    c_sum_env = __dadd_rn(c_sum_env, c);
+                    const double cm = __ddiv_rn(c_sum_env, (double)(n_win0 + fr + 1));
+                    a.cm_frames[(size_t)fr * a.N + env] = cm;
+                    float4 *pf = a.pose_frames + 2 * ((size_t)fr * a.N + env);
+                    pf[0] = make_float4(x.x, x.y, x.z, 0.0f);
+                    pf[1] = make_float4(q.w, q.x, q.y, q.z);
+                    if (fr == a.n_frames - 1) {
+                        a.c_sum[env] = c_sum_env;
+                        a.c_mean[env] = cm;
+                        if (a.cost_mean) a.cost_mean[env] = cm;
+                    }
+                }
+            }
         }
         // frame cost against the observation (Sec. III-C), FP64, in pad order,
         // on exactly the forces written out below
-        if (scored) {
-            const float inv_ns_f = 1.0f / (float)ns;
-            G.sync();
-            const double tau = (double)cfg.tau, wf = (double)cfg.w_force;
-            const double tau2 = __dmul_rn(tau, tau);
-            for (int p = G.tid; p < P; p += TPE) {
-                const double fx = S.padacc[3 * p] * inv_ns_f, fy = S.padacc[3 * p + 1] * inv_ns_f,
-                             fz = S.padacc[3 * p + 2] * inv_ns_f;
-                const double ox = obs[3 * p], oy = obs[3 * p + 1], oz = obs[3 * p + 2];
-                const double dx = __dsub_rn(fx, ox), dy = __dsub_rn(fy, oy), dz = __dsub_rn(fz, oz);
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                S.term[p] = __dmul_rn(wf, d2);
-                const double ns2 = __dadd_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)), __dmul_rn(fz, fz));
-                const double no2 = __dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz));
-                S.flag[p] = (ns2 > tau2) != (no2 > tau2);
-            }
-            G.sync();
+        if (scored && !window_mode) {
+            const double c = frame_cost(obs, st);
             if (G.tid == 0) {
-                double c = 0.0;
-                if (st & kDiverged) {
-                    c = INFINITY;
-                } else {
-                    for (int p = 0; p < P; ++p) {
-                        c = __dadd_rn(c, S.term[p]);
-                        if (S.flag[p]) c = __dadd_rn(c, (double)cfg.w_contact);
-                    }
-                }
                 const double sum = __dadd_rn(a.c_sum[env], c);
                 a.c_sum[env] = sum;
                 double cm = __ddiv_rn(sum, (double)n_win);
@@ -544,7 +572,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
     if (G.tid == 0 && a.work)
         for (int k = 0; k < 6; ++k)
             if (S.work[k]) atomicAdd(a.work + k, S.work[k]);
-    if (!scored) return;
+    if (!scored || window_mode) return;
     // argmin (C_i, i) over the grid: per-block candidate, then the last block
     __shared__ bool last;
     __shared__ int best_env;

@@ -53,7 +53,8 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "sim_set_state", "sim_get_state", "sim_step", "sim_read_sensors", "cost_eval",
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
-           "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites"]
+           "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
+           "sim_step_frames", "sim_frames_argmin"]
 
 
 def lib() -> C.CDLL:
@@ -86,6 +87,8 @@ def lib() -> C.CDLL:
             "sim_track_window": [P, I, I, P, P, U32, P, P],
             "sim_adjoint": [P, I, I, I, P, P, I, C.c_float, C.c_float, P, P, P],
             "sim_mark_window": [P],
+            "sim_step_frames": [P, I, I, P],
+            "sim_frames_argmin": [P, P, P],
             "sim_refine_elites": [P, I, I, P, P, I, C.c_float, C.c_float, C.c_float, P, P, P],
         }
         for name, args in sig.items():
@@ -226,6 +229,14 @@ class Sim:
         _check(argmin, torch.int32, (1,), "argmin")
         _check(est_pose, torch.float32, (8,), "est_pose")
         self._call("sim_step_track", frame, _ptr(obs), _ptr(cost_mean), _ptr(argmin), _ptr(est_pose))
+
+    def sim_step_frames(self, frame0: int, obs):
+        T = obs.shape[0]
+        _check(obs, torch.float32, (T, self.n_pads, 3), "obs")
+        self._call("sim_step_frames", frame0, T, _ptr(obs))
+
+    def sim_frames_argmin(self, est_pose=None, argmin=None):
+        self._call("sim_frames_argmin", _ptr(est_pose), _ptr(argmin))
 
     def sim_track_window(self, frame0: int, obs, opt, update_index: int, est_pose=None, argmin=None):
         T = obs.shape[0]

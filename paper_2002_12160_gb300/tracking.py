@@ -74,16 +74,17 @@ class Tracker:
                                   self.argmin[f0:f0 + T])
 
     def window_unfused(self, w: int, step_events=None):
-        """The same window as separate launches (each step bracketed by events
-        when given), for timing the step kernel alone."""
+        """The same window as separate calls -- the T-frame step launch (bracketed
+        by `step_events` when given), the per-frame argmin, the optimizer -- for
+        timing the step kernel alone."""
         T = self.T
-        for k in range(T):
-            f = w * T + k
-            if step_events is not None:
-                step_events[k][0].record()
-            self.sim.sim_step_track(f, self.obs[f], None, self.argmin[f:f + 1], self.est[f])
-            if step_events is not None:
-                step_events[k][1].record()
+        f0 = w * T
+        if step_events is not None:
+            step_events[0].record()
+        self.sim.sim_step_frames(f0, self.obs[f0:f0 + T])
+        if step_events is not None:
+            step_events[1].record()
+        self.sim.sim_frames_argmin(self.est[f0:f0 + T], self.argmin[f0:f0 + T])
         self.sim.optimizer_update(self.wl.opt, w)
 
     def window_refined(self, w: int, steps: int = 3, step_scale: float = 0.5, report: bool = False):

@@ -290,3 +290,36 @@ def test_replayed_window_equals_the_separate_calls():
     assert torch.equal(est_a, est_b) and torch.equal(am_a, am_b)
     for x, y in zip(a.sim_get_state(), b.sim_get_state()):
         assert torch.equal(x, y)
+
+
+def test_multi_frame_launch_equals_the_separate_calls():
+    """sim_step_frames + sim_frames_argmin (the window's frames in one launch,
+    the per-frame argmin afterwards) equal T calls of sim_step_track bit for bit,
+    including the cost means handed to the optimizer and a second window."""
+    T = 5
+    wl, a, b = _twin("uneven_mixed", 333, 2 * T)
+    d = dev()
+    obs = torch.rand((2 * T, wl.scene.n_pads, 3), dtype=torch.float32, device=d) * 0.3
+    est_a = torch.zeros((2 * T, 8), dtype=torch.float32, device=d)
+    est_b = torch.zeros_like(est_a)
+    am_a = torch.zeros((2 * T,), dtype=torch.int32, device=d)
+    am_b = torch.zeros_like(am_a)
+    par_a = torch.zeros((a.n,), dtype=torch.int32, device=d)
+    par_b = torch.zeros_like(par_a)
+    cm_a = torch.zeros((a.n,), dtype=torch.float64, device=d)
+    for w in range(2):
+        for k in range(T):
+            f = w * T + k
+            a.sim_step_track(f, obs[f], cm_a, am_a[f:f + 1], est_a[f])
+        b.sim_step_frames(w * T, obs[w * T:(w + 1) * T])
+        b.sim_frames_argmin(est_b[w * T:(w + 1) * T], am_b[w * T:(w + 1) * T])
+        a.optimizer_update(wl.opt, w, None, par_a)
+        b.optimizer_update(wl.opt, w, None, par_b)
+        assert torch.equal(par_a, par_b), w
+    assert torch.equal(est_a, est_b) and torch.equal(am_a, am_b)
+    for x, y in zip(a.sim_get_state(), b.sim_get_state()):
+        assert torch.equal(x, y)
+    from paper_2002_12160_gb300 import inhand
+    with pytest.raises(inhand.InhandError) as e:
+        b.sim_frames_argmin()
+    assert e.value.code == inhand.IH_ERR_STATE
