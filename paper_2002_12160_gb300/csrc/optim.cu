@@ -25,8 +25,11 @@
 namespace ih {
 namespace {
 
-constexpr int kSel = 1024;
+constexpr int kSel = 1024;            // threads of the select kernel for large N
+constexpr int kSelSmall = 256;        // ... for N <= kKeys * kSelSmall
+constexpr int kKeys = 8;              // keys per thread held in registers
 constexpr int kWarps = kSel / 32;
+constexpr int kFin = 128;             // threads of the finalize kernel
 
 enum { M_K = 64, M_U, M_ISTAR, M_OK, M_WSUM, M_CMIN, M_SD, M_NFIN, M_NBLK };
 
@@ -43,8 +46,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // block-wide inclusive scan of one unsigned per thread: warp scans, then a
-// scan of the warp totals by the first warp (buf holds kWarps + 1 entries)
+// scan of the warp totals by the first warp (buf holds NT / 32 + 1 entries)
+template <int NT>
 __device__ unsigned block_scan(unsigned v, unsigned *buf) {
+    constexpr int kWarps = NT / 32;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -68,7 +73,9 @@ __device__ unsigned block_scan(unsigned v, unsigned *buf) {
     return r;
 }
 
+template <int NT>
 __device__ double block_sum(double v, double *red) {
+    constexpr int kWarps = NT / 32;
     v = warp_sum(v);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -79,7 +86,9 @@ __device__ double block_sum(double v, double *red) {
     return s;   // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
+    constexpr int kSel = NT, kWarps = NT / 32;
     __shared__ unsigned int hist[256];
     __shared__ unsigned long long s_prefix;
     __shared__ unsigned int s_rem;
@@ -95,7 +104,14 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
     const int chunk = (N + kSel - 1) / kSel;
     const int lo = min(N, t * chunk), hi = min(N, lo + chunk);
 
-    // ---- radix select of the k-th smallest key
+    // ---- radix select of the k-th smallest key (keys held in registers when N <= 8 kSel)
+    const bool in_regs = N <= kKeys * kSel;
+    unsigned long long kreg[kKeys];
+#pragma unroll
+    for (int q = 0; q < kKeys; ++q) {
+        const int i = t + q * kSel;
+        kreg[q] = (in_regs && i < N) ? order_key(a.c_mean[i]) : 0ull;
+    }
     if (t == 0) { s_prefix = 0ull; s_rem = (unsigned)k; }
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 56 - 8 * pass;
@@ -103,9 +119,21 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
         __syncthreads();
         const unsigned long long pre = s_prefix;
         const unsigned long long hmask = (pass == 0) ? 0ull : (~0ull << (shift + 8));
-        for (int i = t; i < N; i += kSel) {
-            const unsigned long long key = order_key(a.c_mean[i]);
-            if ((key & hmask) == pre) atomicAdd(&hist[(key >> shift) & 0xff], 1u);
+        // histogram of the next digit; lanes of a warp with the same digit add
+        // once (leading bytes of similar costs all fall in one bin)
+        auto count = [&](bool valid, unsigned long long key) {
+            const unsigned bin = valid && (key & hmask) == pre ? (unsigned)((key >> shift) & 0xff) : 0x100u;
+            const unsigned same = __match_any_sync(0xffffffffu, bin);
+            if (bin < 0x100u && (__ffs(same) - 1) == (t & 31)) atomicAdd(&hist[bin], (unsigned)__popc(same));
+        };
+        if (in_regs) {
+#pragma unroll
+            for (int q = 0; q < kKeys; ++q) count(t + q * kSel < N, kreg[q]);
+        } else {
+            for (int i0 = 0; i0 < N; i0 += kSel) {
+                const int i = i0 + t;
+                count(i < N, i < N ? order_key(a.c_mean[i]) : 0ull);
+            }
         }
         __syncthreads();
         if (t < 32) {   // the first bin whose running count reaches rem (warp-parallel scan)
@@ -142,7 +170,7 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
     // ---- elite flags in index order
     unsigned eq_local = 0;
     for (int i = lo; i < hi; ++i) eq_local += (order_key(a.c_mean[i]) == T);
-    unsigned eq_before = block_scan(eq_local, s_scan) - eq_local;
+    unsigned eq_before = block_scan<NT>(eq_local, s_scan) - eq_local;
     unsigned el_local = 0;
     for (int i = lo; i < hi; ++i) {
         const unsigned long long key = order_key(a.c_mean[i]);
@@ -152,7 +180,7 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
         el_local += e;
     }
     {
-        unsigned er = block_scan(el_local, s_scan) - el_local;   // elites before my chunk
+        unsigned er = block_scan<NT>(el_local, s_scan) - el_local;   // elites before my chunk
         unsigned nr = (unsigned)lo - er;                          // non-elites before my chunk
         for (int i = lo; i < hi; ++i) {
             if (a.is_elite[i]) { a.rank[i] = (int)er; a.elite_env[er] = i; ++er; }
@@ -187,8 +215,8 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
         if (isfinite(c)) { sum += c; cnt += 1.0; }
     }
     __syncthreads();
-    const double tot = block_sum(sum, red);
-    const double nfin = block_sum(cnt, red);
+    const double tot = block_sum<NT>(sum, red);
+    const double nfin = block_sum<NT>(cnt, red);
     if (t == 0) { s_val[0] = tot; s_val[1] = nfin; }
     __syncthreads();
     const double mean = s_val[1] > 0 ? s_val[0] / s_val[1] : 0.0;
@@ -197,7 +225,7 @@ __global__ void __launch_bounds__(kSel) select_kernel(const OptArgs a) {
         const double c = a.c_mean[a.elite_env[j]];
         if (isfinite(c)) sq += (c - mean) * (c - mean);
     }
-    const double ss = block_sum(sq, red);
+    const double ss = block_sum<NT>(sq, red);
     if (t == 0) {
         const double nf = s_val[1];
         const double c0 = a.c_mean[istar];
@@ -272,10 +300,11 @@ __global__ void __launch_bounds__(kOptBlock) stats_kernel(const OptArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kSel) finalize_kernel(const OptArgs a, int nblocks) {
+__global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nblocks) {
+    constexpr int kSel = kFin, kWarps = kFin / 32;
     __shared__ double sm[kMoments];
     __shared__ double cv[8][8];
-    __shared__ double wtot[kWarps];
+    __shared__ double wtot[32];
     __shared__ double s_carry;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     // moments: thread q < 45 sums its moment over the blocks in block order
@@ -300,13 +329,13 @@ __global__ void __launch_bounds__(kSel) finalize_kernel(const OptArgs a, int nbl
         if (lane == 31) wtot[wid] = inc;
         __syncthreads();
         if (wid == 0) {
-            double x = wtot[lane];
+            double x = lane < kWarps ? wtot[lane] : 0.0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const double u = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += u;
             }
-            wtot[lane] = x;
+            if (lane < kWarps) wtot[lane] = x;
         }
         __syncthreads();
         const double carry = s_carry;
@@ -371,46 +400,72 @@ __device__ __forceinline__ double cum_w(const OptArgs &a, int j) {
 
 constexpr int kCdfSmem = 2048;   // elites whose CDF apply_kernel stages in shared memory
 
-// One thread per environment.
-__global__ void __launch_bounds__(kOptBlock) apply_kernel(const OptArgs a) {
+// Four lanes per environment (a quad): each draws one Box-Muller pair and two
+// rows of L eps, so every warp's FP64 chain is a quarter as long; the quad's
+// first lane does the resampling search and writes the state.
+constexpr int kApplyLanes = 4;
+
+__global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const OptArgs a) {
     __shared__ double cdf[kCdfSmem];
-    const int i = blockIdx.x * kOptBlock + threadIdx.x;
+    const int sub = threadIdx.x & (kApplyLanes - 1);
+    const int i = blockIdx.x * kOptBlock + (int)(threadIdx.x / kApplyLanes);
+    const unsigned qmask = 0xfu << (threadIdx.x & 28u);   // this quad's lanes
     const int N = a.N;
     const int k = (int)a.misc[M_K];
     const bool staged = k <= kCdfSmem;
     if (staged) {   // the block's binary searches read the CDF from shared memory
-        for (int j = threadIdx.x; j < k; j += kOptBlock) cdf[j] = cum_w(a, j);
+        for (int j = threadIdx.x; j < k; j += blockDim.x) cdf[j] = cum_w(a, j);
         __syncthreads();
     }
-    if (i >= N) return;
-    if (i == 0) *a.n_window = 0;
-    a.c_sum[i] = 0.0;
+    if (i >= N) return;   // whole quads
+    if (sub == 0) {
+        if (i == 0) *a.n_window = 0;
+        a.c_sum[i] = 0.0;
+    }
     if (a.is_elite[i]) {
-        if (a.parent_out) a.parent_out[i] = i;
+        if (sub == 0 && a.parent_out) a.parent_out[i] = i;
         return;
     }
-    const double u = a.misc[M_U], wsum = a.misc[M_WSUM];
     const bool ok = a.misc[M_OK] != 0.0;
-    const int M = N - k;
-    // position (u + r)/M of the normalised CDF, compared on the unnormalised one
-    const double pos = __ddiv_rn(u + (double)a.rank[i], (double)M) * wsum;
-    int lo = 0, hi = k - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (pos < (staged ? cdf[mid] : cum_w(a, mid))) hi = mid; else lo = mid + 1;
+    int par = 0;
+    if (sub == 0) {
+        const double u = a.misc[M_U], wsum = a.misc[M_WSUM];
+        const int M = N - k;
+        // position (u + r)/M of the normalised CDF, compared on the unnormalised one
+        const double pos = __ddiv_rn(u + (double)a.rank[i], (double)M) * wsum;
+        int lo = 0, hi = k - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pos < (staged ? cdf[mid] : cum_w(a, mid))) hi = mid; else lo = mid + 1;
+        }
+        par = a.elite_env[lo];
+        if (a.parent_out) a.parent_out[i] = par;
     }
-    const int par = a.elite_env[lo];
-    if (a.parent_out) a.parent_out[i] = par;
     if (!ok) return;
-    double eps[8], d[8];
+    double e0, e1;
     const uint32_t upd = a.win ? a.win->update_index : a.update_index;
-    for (int b = 0; b < 4; ++b)
-        gauss2(rng_words(a.seed, 1, upd, (uint32_t)i, (uint32_t)b), eps[2 * b], eps[2 * b + 1]);
-    for (int r = 0; r < 8; ++r) {
-        double s = 0.0;
-        for (int c = 0; c <= r; ++c) s += a.misc[8 * r + c] * eps[c];
-        d[r] = s;
+    gauss2(rng_words(a.seed, 1, upd, (uint32_t)i, (uint32_t)sub), e0, e1);
+    double eps[8];
+#pragma unroll
+    for (int b = 0; b < kApplyLanes; ++b) {
+        eps[2 * b] = __shfl_sync(qmask, e0, b, kApplyLanes);
+        eps[2 * b + 1] = __shfl_sync(qmask, e1, b, kApplyLanes);
     }
+    double dr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {   // rows 2 sub and 2 sub + 1 of L eps
+        const int r = 2 * sub + h;
+        double sacc = 0.0;
+        for (int c = 0; c <= r; ++c) sacc += a.misc[8 * r + c] * eps[c];
+        dr[h] = sacc;
+    }
+    double d[8];
+#pragma unroll
+    for (int b = 0; b < kApplyLanes; ++b) {
+        d[2 * b] = __shfl_sync(qmask, dr[0], b, kApplyLanes);
+        d[2 * b + 1] = __shfl_sync(qmask, dr[1], b, kApplyLanes);
+    }
+    if (sub != 0) return;
     const float4 p0 = a.pose[2 * par], p1 = a.pose[2 * par + 1];
     const Q4d qn = qnorm_d(qmul_d(qexp_d(d[3], d[4], d[5]), {p1.x, p1.y, p1.z, p1.w}));
     a.pose[2 * i] = make_float4((float)(p0.x + d[0]), (float)(p0.y + d[1]), (float)(p0.z + d[2]), 0.0f);
@@ -436,7 +491,8 @@ cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s) {
 int opt_blocks(int N) { return (N + kOptBlock - 1) / kOptBlock; }
 
 cudaError_t launch_select(const OptArgs &a, cudaStream_t s) {
-    select_kernel<<<1, kSel, 0, s>>>(a);
+    if (a.N <= kKeys * kSelSmall) select_kernel<kSelSmall><<<1, kSelSmall, 0, s>>>(a);
+    else select_kernel<kSel><<<1, kSel, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -445,10 +501,11 @@ cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
     int k = (int)floor((double)a.elite_frac * (double)a.N);
     k = k < 1 ? 1 : (k > a.N ? a.N : k);
     const int kb = opt_blocks(k), nb = opt_blocks(a.N);
-    select_kernel<<<1, kSel, 0, s>>>(a);
+    if (a.N <= kKeys * kSelSmall) select_kernel<kSelSmall><<<1, kSelSmall, 0, s>>>(a);
+    else select_kernel<kSel><<<1, kSel, 0, s>>>(a);
     stats_kernel<<<kb, kOptBlock, 0, s>>>(a);
-    finalize_kernel<<<1, kSel, 0, s>>>(a, kb);
-    apply_kernel<<<nb, kOptBlock, 0, s>>>(a);
+    finalize_kernel<<<1, kFin, 0, s>>>(a, kb);
+    apply_kernel<<<nb, kOptBlock * kApplyLanes, 0, s>>>(a);
     return cudaGetLastError();
 }
 
