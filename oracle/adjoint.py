@@ -122,7 +122,7 @@ class Model:
     """One environment's frame step and cost in FP64 torch (see the module doc)."""
 
     def __init__(self, scene, sim, shape: int = 0, beta: float = 1e3, width: float = 1e-3,
-                 smooth_forward: bool = False):
+                 smooth_forward: bool = False, record_regimes: bool = False):
         self.osc = OracleScene(scene)
         self.scene = scene
         self.sim = sim
@@ -132,6 +132,7 @@ class Model:
         self.rad = torch.tensor(rows[:, 3], dtype=DT)                  # (S,)
         self.Jinv = torch.tensor(np.linalg.inv(unit_inertia(self.osc, shape)), dtype=DT)
         self.beta, self.width, self.smooth = beta, width, smooth_forward
+        self.record_regimes = record_regimes   # add the projections' active sets to the signature
         self.n_links = scene.n_links
         self.P = scene.n_pads
         self.h = sim.frame_dt / sim.substeps
@@ -271,8 +272,13 @@ class Model:
                 u = vv[None] + torch.cross(ww[None].expand_as(r), r, dim=-1) - cc
                 un = (u * n).sum(-1)
                 l_old = (lam * n).sum(-1)
-                ln = _Max0.apply(l_old - un * ikn, self.beta, self.smooth)
+                zn = l_old - un * ikn
+                ln = _Max0.apply(zn, self.beta, self.smooth)
                 zt = (lam - n * l_old[:, None]) - (u - n * un[:, None]) * ikt[:, None]
+                if self.record_regimes:   # which side of each projection every contact is on
+                    nz = torch.sqrt((zt.detach() ** 2).sum(-1))
+                    self.signature.append(tuple((zn.detach() > 0).tolist()) +
+                                          tuple((nz > (mu * ln).detach()).tolist()))
                 lt = _Disk.apply(zt, mu * ln, self.width, self.smooth)
                 lp = n * ln[:, None] + lt
                 lam = lam + (lp - lam) / nc
@@ -305,14 +311,14 @@ class Model:
 
 
 def horizon(scene, sim, pose7, vel6, theta, q_traj, frame0, H, obs, shape=0, iters=None,
-            beta=1e3, width=1e-3, smooth_forward=False, delta=None):
+            beta=1e3, width=1e-3, smooth_forward=False, delta=None, record_regimes=False):
     """Cost over frames [frame0, frame0 + H) and its gradient w.r.t. the
     initial state's position (3), rotation tangent (3, world frame, applied on
     the left), mass and friction. Returns (cost, grad[8] in the order x y z,
     rx ry rz, m, mu, final state (x, q, v, w), per-frame forces, branch
     signature). With `delta` given, no gradient is taken and the initial
     state is offset by it (for finite differences)."""
-    model = Model(scene, sim, shape, beta, width, smooth_forward)
+    model = Model(scene, sim, shape, beta, width, smooth_forward, record_regimes)
     dlt = torch.zeros(8, dtype=DT, requires_grad=True) if delta is None else torch.as_tensor(delta, dtype=DT)
     p = torch.as_tensor(pose7, dtype=DT)
     x = p[:3] + dlt[:3]

@@ -87,3 +87,36 @@ def test_smoothed_gradient_equals_central_differences():
             assert abs(fd - grad[c]) <= 1e-6 * max(abs(grad[c]), abs(fd)) + 1e-8 * max(1.0, abs(cost)), (i, c, fd, grad[c])
             checked += 1
     assert checked >= 20
+
+
+def test_unsmoothed_limit_equals_finite_differences_of_the_exact_forward():
+    """With the smoothing taken to its limit (beta = 1e8 (N s)^-1, width 1e-8)
+    the backward-smoothed gradient is the derivative of the exact,
+    non-smooth forward: on components whose contact set, clamps and every
+    projection's active side (normal clamp, disk clamp, per contact and
+    iteration) stay unchanged within the step, it equals central finite
+    differences of the exact forward (steps 1e-7 and 5e-8, Richardson) to
+    1e-5 relative."""
+    warm, H = 18, 5
+    wl, osc, st = _case(n=4, frames=warm + H + 2, warm=warm, name="tracking_cyl64")
+    obs_state = O.State(st.pose[:1], st.vel[:1], np.array([wl.theta_gt]))
+    obs = np.array([O.step(osc, wl.sim, obs_state, wl.q_traj, warm + k, 1)[0][0] for k in range(H)])
+    checked = 0
+    for i in (0, 3):
+        args = (wl.scene, wl.sim, st.pose[i], st.vel[i], st.theta[i], wl.q_traj, warm, H, obs)
+        cost, grad, _, _, sig = A.horizon(*args, beta=1e8, width=1e-8, record_regimes=True)
+        for c in range(8):
+            fds, stable = [], True
+            for h in (1e-7, 5e-8):
+                e = np.zeros(8)
+                e[c] = h
+                cp = A.horizon(*args, delta=e, record_regimes=True)
+                cm = A.horizon(*args, delta=-e, record_regimes=True)
+                stable &= cp[4] == sig and cm[4] == sig
+                fds.append((cp[0] - cm[0]) / (2 * h))
+            if not stable:
+                continue
+            fd = (4 * fds[1] - fds[0]) / 3
+            assert abs(fd - grad[c]) <= 1e-5 * max(abs(grad[c]), abs(fd)) + 1e-9, (i, c, fd, grad[c])
+            checked += 1
+    assert checked >= 12
