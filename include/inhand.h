@@ -365,6 +365,17 @@ ih_status sim_adjoint(ih_sim *sim, int32_t frame0, int32_t horizon, int32_t chec
                       const float *obs, const int32_t *envs, int32_t n, float beta, float width,
                       double *cost, float *grad, float *grad_quat);
 
+/* Memory the adjoint may use to keep the tape (the Jacobi impulses of every
+ * iteration) of all substeps of a checkpoint segment at once, in bytes
+ * (default 16 GiB). Within the budget each substep of the forward is run twice
+ * per gradient (the pass that computes the cost and checkpoints, and the
+ * segment's recomputation, which records the tape); beyond it the tape of a
+ * single substep is kept and each substep runs a third time just before its
+ * reverse sweep. Results are the same bit for bit. 0 always takes the
+ * smaller mode. Not a passage of the paper: a memory/time trade of this
+ * library's checkpointing. */
+ih_status sim_set_adjoint_memory(ih_sim *sim, uint64_t bytes);
+
 /* Snapshot every environment's state (pose, velocity, parameters) into the
  * handle: the start of a tracking window, for sim_refine_elites. */
 ih_status sim_mark_window(ih_sim *sim);

@@ -69,22 +69,30 @@ struct WarpSm {
     unsigned short lbeg[32], lend[32];
 };
 
-// Per-slot scratch layout in floats (every part starts on a float4 boundary).
+// Per-slot scratch layout in floats (every part starts on a float4 boundary):
+// checkpoints, a segment's substep start states and frame forces, the final
+// impulses of an untaped pass, the contact count of every taped substep, then
+// nblk tape blocks of (contact records, impulse after each iteration,
+// iteration sums): one block per substep of a segment when the whole segment
+// is taped, else a single block re-filled substep by substep.
 struct SlotLayout {
-    size_t ck, sg, sf, rec, lamh, lamf, sh, total;
+    size_t ck, sg, sf, lamf, ncs, tape, blk_rec, blk_lamh, blk_sh, blk_stride, total;
 };
 __host__ __device__ inline size_t round4(size_t x) { return (x + 3) & ~size_t(3); }
-__host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, int cap, int iters_max) {
+__host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, int cap, int iters_max, int nblk) {
     SlotLayout L;
     size_t o = 0;
     const size_t nck = (size_t)((H + K - 1) / K);
     L.ck = o;   o += round4(nck * 16);                        // checkpoint states
     L.sg = o;   o += round4((size_t)K * ns * 16);             // substep start states of a segment
     L.sf = o;   o += round4((size_t)K * P * 3);               // pad forces of a segment's frames
-    L.rec = o;  o += round4((size_t)cap * 16);                // contact records
-    L.lamh = o; o += round4((size_t)iters_max * cap * 4);     // impulse after each iteration
-    L.lamf = o; o += round4((size_t)cap * 4);                 // final impulses (untaped passes)
-    L.sh = o;   o += round4((size_t)(iters_max > 0 ? iters_max : 1) * 8);   // sums after each iteration
+    L.lamf = o; o += round4((size_t)cap * 4);                 // final impulses of a pass
+    L.ncs = o;  o += round4((size_t)K * ns);                  // contacts of each taped substep (int)
+    L.blk_rec = 0;
+    L.blk_lamh = round4((size_t)cap * 16);                                   // contact records
+    L.blk_sh = L.blk_lamh + round4((size_t)iters_max * cap * 4);             // impulse after each iteration
+    L.blk_stride = L.blk_sh + round4((size_t)(iters_max > 0 ? iters_max : 1) * 8);   // sums after each iteration
+    L.tape = o; o += (size_t)nblk * L.blk_stride;
     L.total = o;
     return L;
 }
@@ -92,6 +100,18 @@ __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, i
 struct SlotPtr {
     float4 *ck, *sg, *rec, *lamh, *lamf;
     float *sf, *sh;
+    int *ncs;
+    float *tape;
+    size_t blk_lamh, blk_sh, blk_stride;
+    // the same slot with its tape pointers on block b
+    __device__ SlotPtr blk(int b) const {
+        SlotPtr q = *this;
+        float *t = tape + (size_t)b * blk_stride;
+        q.rec = reinterpret_cast<float4 *>(t);
+        q.lamh = reinterpret_cast<float4 *>(t + blk_lamh);
+        q.sh = t + blk_sh;
+        return q;
+    }
 };
 
 // Per-environment constants.
@@ -107,11 +127,15 @@ __device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y)
 
 // One substep of one environment (the arithmetic of step.cu, contacts in the
 // same order: link, then sphere). With TAPE the impulses after every
-// iteration and the iteration sums are recorded; without, the pad forces of
-// the substep are added to S.padacc. Returns the contact count (0 on overflow).
-template <int PL, bool TAPE>
-__device__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4 *L0, const float4 *L1,
-                           const SlotPtr &sp, WarpSm &S, int lane, int &st) {
+// iteration and the iteration sums are recorded in the slot's current tape
+// block; with PADS the pad forces of the substep are added to S.padacc.
+// Returns the contact count (0 on overflow). Not inlined, with the two flags
+// as arguments: every pass (cost, recomputation, tape) then runs the same
+// compiled arithmetic, so a recorded tape is bit for bit the forward's.
+template <int PL>
+__device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4 *L0,
+                                        const float4 *L1, const SlotPtr &sp, WarpSm &S, int lane, int &st,
+                                        const bool TAPE, const bool PADS) {
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
     const int Lk = sc.n_links, P = sc.n_pads, cap = cfg.c_max;
@@ -230,7 +254,7 @@ __device__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4
         const float kq = (wn > 0.0f) ? sn / wn : 0.5f * h;
         b.q = qnorm(qmul({cs, b.w.x * kq, b.w.y * kq, b.w.z * kq}, b.q));
     }
-    if (!TAPE) {
+    if (PADS) {
         // pad forces -lambda / h, each pad summing the contacts of its link in order
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
@@ -634,16 +658,20 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
         if (lane == 0 && a.cost) a.cost[slot] = NAN;
         return;
     }
-    const SlotLayout Ly = slot_layout(a.H, a.K, ns, P, cap, a.iters_max);
+    const bool seg_tape = a.seg_tape != 0;   // every substep of a segment keeps its tape
+    const SlotLayout Ly = slot_layout(a.H, a.K, ns, P, cap, a.iters_max, seg_tape ? a.K * ns : 1);
     float *base = a.scratch + (size_t)slot * a.stride;
-    SlotPtr sp;
-    sp.ck = reinterpret_cast<float4 *>(base + Ly.ck);
-    sp.sg = reinterpret_cast<float4 *>(base + Ly.sg);
-    sp.sf = base + Ly.sf;
-    sp.rec = reinterpret_cast<float4 *>(base + Ly.rec);
-    sp.lamh = reinterpret_cast<float4 *>(base + Ly.lamh);
-    sp.lamf = reinterpret_cast<float4 *>(base + Ly.lamf);
-    sp.sh = base + Ly.sh;
+    SlotPtr sp0;
+    sp0.ck = reinterpret_cast<float4 *>(base + Ly.ck);
+    sp0.sg = reinterpret_cast<float4 *>(base + Ly.sg);
+    sp0.sf = base + Ly.sf;
+    sp0.lamf = reinterpret_cast<float4 *>(base + Ly.lamf);
+    sp0.ncs = reinterpret_cast<int *>(base + Ly.ncs);
+    sp0.tape = base + Ly.tape;
+    sp0.blk_lamh = Ly.blk_lamh;
+    sp0.blk_sh = Ly.blk_sh;
+    sp0.blk_stride = Ly.blk_stride;
+    const SlotPtr sp = sp0.blk(0);
 
     const float4 P0 = a.pose[2 * env], P1 = a.pose[2 * env + 1];
     const float4 V0 = a.vel[2 * env], V1 = a.vel[2 * env + 1];
@@ -679,9 +707,17 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
         __syncwarp();
         const float4 *tab = tab0 + (size_t)f * tab_frame;
         for (int s = 0; s < ns; ++s) {
-            if (f >= f_last && lane == 0) store_body(sp.sg + 4 * ((f - f_last) * ns + s), b);
             const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
-            fwd_substep<PL, false>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st);
+            if (f >= f_last) {
+                const int blk = (f - f_last) * ns + s;
+                if (lane == 0) store_body(sp.sg + 4 * blk, b);
+                if (seg_tape && !a.forward_only) {   // the last segment's tape, recorded on the way
+                    const int nc = fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, lane, st, true, true);
+                    if (lane == 0) sp.ncs[blk] = nc;
+                    continue;
+                }
+            }
+            fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st, false, true);
         }
         if (f >= f_last)
             for (int k = lane; k < 3 * P; k += 32) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
@@ -735,9 +771,15 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
             __syncwarp();
             const float4 *tab = tab0 + (size_t)f * tab_frame;
             for (int s = 0; s < ns; ++s) {
-                if (lane == 0) store_body(sp.sg + 4 * ((f - fb) * ns + s), b);
+                const int blk = (f - fb) * ns + s;
+                if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
-                fwd_substep<PL, false>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st);
+                if (seg_tape) {
+                    const int nc = fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, lane, st, true, true);
+                    if (lane == 0) sp.ncs[blk] = nc;
+                } else {
+                    fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st, false, true);
+                }
             }
             for (int k = lane; k < 3 * P; k += 32) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
             __syncwarp();
@@ -751,11 +793,17 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
             for (int s = ns - 1; s >= 0; --s) {
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
                 const float4 *L1 = L0 + Lk * kLinkStride;
-                const Body bs = load_body(sp.sg + 4 * ((f - fb) * ns + s));
-                Body bt = bs;
-                int st2 = 0;
-                const int nc = fwd_substep<PL, true>(a, E, bt, L0, L1, sp, S, lane, st2);
-                rev_substep<PL>(a, E, bs, L0, L1, nc, sp, S, lane, ad, invm_b, mu_b);
+                const int blk = (f - fb) * ns + s;
+                const Body bs = load_body(sp.sg + 4 * blk);
+                if (seg_tape) {
+                    __syncwarp();
+                    rev_substep<PL>(a, E, bs, L0, L1, sp.ncs[blk], sp.blk(blk), S, lane, ad, invm_b, mu_b);
+                } else {   // re-run the substep once more, recording its tape
+                    Body bt = bs;
+                    int st2 = 0;
+                    const int nc = fwd_substep<PL>(a, E, bt, L0, L1, sp, S, lane, st2, true, false);
+                    rev_substep<PL>(a, E, bs, L0, L1, nc, sp, S, lane, ad, invm_b, mu_b);
+                }
             }
             __syncwarp();
         }
@@ -878,8 +926,8 @@ __global__ void iters_max_kernel(int n, int N, const int *envs, const int *iters
 
 }  // namespace
 
-size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max) {
-    return slot_layout(H, K, substeps, n_pads, c_max, iters_max).total;
+size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max, bool seg_tape) {
+    return slot_layout(H, K, substeps, n_pads, c_max, iters_max, seg_tape ? K * substeps : 1).total;
 }
 
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s) {

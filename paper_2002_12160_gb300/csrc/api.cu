@@ -52,6 +52,8 @@ struct ih_sim {
     // adjoint scratch (grown on demand, freed in sim_destroy)
     float *adj_scratch = nullptr;
     size_t adj_floats = 0;
+    size_t adj_budget = (size_t)16 << 30;   // bytes of adjoint scratch for whole-segment taping
+    bool adj_seg = false;
     int *adj_word = nullptr;
     // gradient refinement: window-start snapshot, trial, best and end states (allocated on first use)
     bool rf_alloc = false, ws_valid = false;
@@ -721,7 +723,10 @@ ih_status adjoint_prepare(ih_sim *s, int n, const int32_t *envs, int horizon, in
     if (e == cudaSuccess) e = cudaMemcpyAsync(&m, s->adj_word, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(s, e, "adjoint sizing");
-    const size_t str = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, m);
+    // tape whole segments when that fits the handle's budget, else substep by substep
+    size_t str = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, m, true);
+    bool seg = str * (size_t)n * sizeof(float) <= s->adj_budget;
+    if (!seg) str = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, m, false);
     const size_t need = str * (size_t)n;
     if (need > s->adj_floats) {
         if (s->adj_scratch) cudaFree(s->adj_scratch);   // the stream is idle (synchronised above)
@@ -735,6 +740,7 @@ ih_status adjoint_prepare(ih_sim *s, int n, const int32_t *envs, int horizon, in
     }
     *stride = str;
     *imax = m;
+    s->adj_seg = seg;
     return IH_OK;
 }
 
@@ -754,7 +760,7 @@ AdjArgs adjoint_args(ih_sim *s, int32_t frame0, int32_t horizon, int K, const fl
     a.status = s->status; a.obs = obs; a.beta_s = beta; a.width = width;
     a.cost = nullptr; a.grad = nullptr; a.grad_quat = nullptr;
     a.scratch = s->adj_scratch; a.stride = 0; a.iters_max = 0;
-    a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr;
+    a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr; a.seg_tape = 0;
     return a;
 }
 }  // namespace
@@ -777,7 +783,7 @@ ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkp
     if (r != IH_OK) return r;
     AdjArgs a = adjoint_args(s, frame0, horizon, K, obs, beta, width);
     a.n = n; a.envs = envs; a.cost = cost; a.grad = grad; a.grad_quat = grad_quat;
-    a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
+    a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax; a.seg_tape = s->adj_seg ? 1 : 0;
     cudaError_t e = launch_adjoint(a, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "adjoint launch");
     return IH_OK;
@@ -800,6 +806,12 @@ cudaError_t refine_alloc(ih_sim *s) {
     return e;
 }
 }  // namespace
+
+ih_status sim_set_adjoint_memory(ih_sim *s, uint64_t bytes) {
+    if (!s) return IH_ERR_ARG;
+    s->adj_budget = (size_t)bytes;
+    return IH_OK;
+}
 
 ih_status sim_mark_window(ih_sim *s) {
     if (!s) return IH_ERR_ARG;
@@ -849,7 +861,7 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
     AdjArgs a = adjoint_args(s, frame0, T, T, obs, beta, width);
     a.n = k; a.envs = s->elite_env; a.pose = s->tr_pose; a.vel = s->ws_vel; a.params = s->tr_params;
     a.cost = s->r_cost; a.grad = s->r_grad; a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
-    a.out_pose = s->end_pose; a.out_vel = s->end_vel;
+    a.out_pose = s->end_pose; a.out_vel = s->end_vel; a.seg_tape = s->adj_seg ? 1 : 0;
     RefineArgs ra;
     ra.k = k; ra.elite = s->elite_env; ra.tr_pose = s->tr_pose; ra.tr_params = s->tr_params;
     ra.best_pose = s->best_pose; ra.best_params = s->best_params; ra.best_grad = s->best_grad;

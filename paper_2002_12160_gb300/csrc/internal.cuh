@@ -315,6 +315,7 @@ struct AdjArgs {
     size_t stride;
     int iters_max;
     int forward_only;         // 1: cost (and end state) only, no reverse sweep
+    int seg_tape;             // 1: tape every substep of a segment (else re-run each substep to tape it)
     float4 *out_pose, *out_vel;   // [n][2] end state of each slot, or null
 };
 
@@ -345,7 +346,7 @@ cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, 
                                  const float2 *best_params, const float4 *end_pose, const float4 *end_vel,
                                  float4 *pose, float4 *vel, float2 *params, double *c_sum, double *c_mean,
                                  const int *n_window, cudaStream_t s);
-size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max);
+size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max, bool seg_tape);
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);

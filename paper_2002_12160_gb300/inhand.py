@@ -54,7 +54,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
            "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
-           "sim_step_frames", "sim_frames_argmin"]
+           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory"]
 
 
 def lib() -> C.CDLL:
@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
             "sim_track_window": [P, I, I, P, P, U32, P, P],
             "sim_adjoint": [P, I, I, I, P, P, I, C.c_float, C.c_float, P, P, P],
             "sim_mark_window": [P],
+            "sim_set_adjoint_memory": [P, C.c_uint64],
             "sim_step_frames": [P, I, I, P],
             "sim_frames_argmin": [P, P, P],
             "sim_refine_elites": [P, I, I, P, P, I, C.c_float, C.c_float, C.c_float, P, P, P],
@@ -294,6 +295,9 @@ class Sim:
         self._call("sim_adjoint", frame0, H, checkpoint_every, _ptr(obs), _ptr(envs), n, C.c_float(beta),
                    C.c_float(width), _ptr(cost), _ptr(grad), _ptr(grad_quat))
         return cost, grad, grad_quat
+
+    def sim_set_adjoint_memory(self, nbytes: int):
+        self._call("sim_set_adjoint_memory", C.c_uint64(nbytes))
 
     def sim_mark_window(self):
         self._call("sim_mark_window")

@@ -63,7 +63,7 @@ def test_adjoint_matches_oracle():
     assert checked >= 3
 
 
-def test_checkpoint_interval_and_subset_do_not_change_results():
+def test_checkpoint_interval_tape_mode_and_subset_do_not_change_results():
     wl, sim, st, sc, sm, obs, fragile = _setup()
     d = dev()
     o = torch.from_numpy(obs).to(d)
@@ -71,6 +71,12 @@ def test_checkpoint_interval_and_subset_do_not_change_results():
     for K in (1, 2, 3):
         c, g, q = sim.sim_adjoint(WARM, o, checkpoint_every=K, want_quat=True)
         assert torch.equal(c, ref_c) and torch.equal(g, ref_g) and torch.equal(q, ref_q), K
+    # taping substep by substep (no memory for whole segments) gives the same bits
+    sim.sim_set_adjoint_memory(0)
+    for K in (2, 10):
+        c, g, q = sim.sim_adjoint(WARM, o, checkpoint_every=K, want_quat=True)
+        assert torch.equal(c, ref_c) and torch.equal(g, ref_g) and torch.equal(q, ref_q), K
+    sim.sim_set_adjoint_memory(16 << 30)
     envs = torch.tensor([3, 1], dtype=torch.int32, device=d)
     c, g, _ = sim.sim_adjoint(WARM, o, envs=envs, checkpoint_every=2)
     assert torch.equal(c, ref_c[[3, 1]]) and torch.equal(g, ref_g[[3, 1]])
