@@ -136,3 +136,68 @@ def test_autograd_function_and_invalid_env():
     c2, g2, _ = sim.sim_adjoint(WARM, o)
     assert torch.isinf(c2[1]) and torch.all(g2[1] == 0)
     assert torch.isfinite(c2[[0, 2, 3]]).all()
+
+
+def test_adjoint_matches_oracle_on_uneven_batch():
+    """Per-environment shapes (16, 27, 64, 256 spheres; the 256-sphere
+    composite runs the 8-slot register path) and iteration counts (10, 20,
+    40): each environment's gradient against the oracle adjoint of its own
+    shape and iteration count."""
+    warm, H = 12, 3
+    n = 6
+    wl = W.make_workload("uneven_mixed", n_envs=n, frames=warm + H + 2)
+    sim = start(wl, n=n, frames=warm + H + 2)
+    sim.sim_step(0, warm)
+    st = oracle_state(sim.sim_get_state())
+    sc, sm = scene32(wl.scene), sim32(wl.sim)
+    osc = O.OracleScene(sc)
+    obs = np.zeros((H, wl.scene.n_pads, 3), np.float32)
+    probe = O.State(st.pose, st.vel, st.theta, wl.shape_id[:n].astype(np.int32), wl.iters[:n].astype(np.int32))
+    fragile = np.zeros(n, bool)
+    for k in range(H):
+        _, diag = O.step(osc, sm, probe, wl.q_traj, warm + k, 1)
+        fragile |= (diag[:, 2] < FRAGILE) | (diag[:, 3] < FRAGILE) | (diag[:, 4] < FRAGILE)
+    d = dev()
+    cost, grad, _ = sim.sim_adjoint(warm, torch.from_numpy(obs).to(d), checkpoint_every=2)
+    cost, grad = cost.cpu().numpy(), grad.cpu().numpy().astype(np.float64)
+    checked, shapes = 0, set()
+    for i in range(n):
+        if fragile[i] or not np.isfinite(cost[i]):
+            continue
+        c_or, g_or, _, _, _ = A.horizon(sc, sm, st.pose[i], st.vel[i], st.theta[i], wl.q_traj, warm, H,
+                                        obs.astype(np.float64), shape=int(wl.shape_id[i]), iters=int(wl.iters[i]))
+        assert abs(cost[i] - c_or) <= 1e-3 * abs(c_or) + 1e-6, (i, cost[i], c_or)
+        if c_or == 0.0:
+            assert np.all(grad[i] == 0)
+            continue
+        floor = 1e-3 * max(np.linalg.norm(g_or[b]) for b in BLOCKS)
+        for b in BLOCKS:
+            err = np.linalg.norm(grad[i, b] - g_or[b])
+            assert err <= 1e-3 * np.linalg.norm(g_or[b]) + floor, (i, b, grad[i, b], g_or[b])
+        checked += 1
+        shapes.add(int(wl.shape_id[i]))
+    assert checked >= 3 and len(shapes) >= 2
+
+
+def test_adjoint_of_an_environment_out_of_reach_is_zero():
+    """No contact over the horizon: the pad forces are zero whatever the
+    initial state, so the cost is sum |o|^2 and every derivative is 0."""
+    wl, sim, st, sc, sm, obs, fragile = _setup()
+    d = dev()
+    pose, vel, params, _ = sim.sim_get_state()
+    pose = pose.clone()
+    # 12 cm to the side (beyond the palm and the fingers' reach) and 15 cm up:
+    # 5 frames of free fall drop it 14 cm, still clear of the hand and inside
+    # the 0.3 m escape radius
+    pose[0, 0] += 0.12
+    pose[0, 2] += 0.15
+    vel = torch.zeros_like(vel)
+    sim.sim_set_state(pose, vel, params)
+    o = torch.from_numpy(obs).to(d)
+    cost, grad, gq = sim.sim_adjoint(WARM, o, want_quat=True)
+    o64 = obs.astype(np.float64)
+    n2 = np.sum(o64 ** 2, axis=2)
+    tau = float(np.float32(sm.tau))
+    expect = float(np.sum(n2)) * sm.w_force + float(np.sum(n2 > tau * tau)) * sm.w_contact
+    assert abs(cost[0].item() - expect) <= 1e-12 * expect, (cost[0].item(), expect)
+    assert torch.all(grad[0] == 0) and torch.all(gq[0] == 0)
