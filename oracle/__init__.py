@@ -75,6 +75,9 @@ def lib():
                                              C.c_double, C.c_double, C.c_double, C.c_uint64, P, P]
             L.orc_cholesky8.argtypes = [P, P]
             L.orc_optimizer.argtypes = [P, C.c_int, P, P, P, P, P, C.c_uint64, C.c_uint32, P, P]
+            L.orc_softmax_update.argtypes = [P, C.c_int, P, P, P, P, P, C.c_uint64, C.c_uint32, P, P]
+            L.orc_reps_eta.argtypes = [C.c_int, P, C.c_double, C.POINTER(C.c_int)]
+            L.orc_reps_eta.restype = C.c_double
             L.orc_add.argtypes = [P, C.c_int, P, P]
             L.orc_add.restype = C.c_double
             L.orc_quat_exp.argtypes = [P, P]
@@ -248,6 +251,41 @@ def optimizer(opt, st: State, C_mean, seed: int, update_index: int):
     return i, parent, {"mean": stats[:8].copy(), "cov": stats[8:72].reshape(8, 8).copy(),
                        "L": stats[72:136].reshape(8, 8).copy(), "k": int(stats[136]),
                        "istar": int(stats[137]), "sd": float(stats[138])}
+
+
+class SoftOpt(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lam", C.c_double), ("epsilon", C.c_double),
+                ("sigma_pose", C.c_double * 6), ("sigma_theta", C.c_double * 2),
+                ("explore_velocity", C.c_int32), ("sigma_vel", C.c_double * 6),
+                ("m_lo", C.c_double), ("m_hi", C.c_double), ("mu_lo", C.c_double), ("mu_hi", C.c_double)]
+
+
+def make_soft_opt(opt) -> SoftOpt:
+    kind = {"wrs": 1, "reps": 2}[opt.kind]
+    return SoftOpt(kind, opt.wrs_lambda, opt.reps_epsilon, (C.c_double * 6)(*opt.sigma_pose),
+                   (C.c_double * 2)(*opt.sigma_theta), 1 if opt.explore == "velocity" else 0,
+                   (C.c_double * 6)(*opt.sigma_vel), opt.m_range[0], opt.m_range[1], opt.mu_range[0],
+                   opt.mu_range[1])
+
+
+def softmax_update(opt, st: State, C_mean, seed: int, update_index: int):
+    """WRS / REPS update of st in place (Sec. III-D); returns (i*, parent, stats)."""
+    o = make_soft_opt(opt)
+    Cm = np.ascontiguousarray(C_mean, np.float64)
+    parent = np.zeros(st.n, np.int32)
+    stats = np.zeros(7)
+    i = lib().orc_softmax_update(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
+                                 _p(st.status), seed, update_index, _p(parent), _p(stats))
+    return i, parent, {"eta": stats[0], "wsum": stats[1], "kl": stats[2], "n_finite": int(stats[3]),
+                       "cmin": stats[4], "cmax": stats[5], "iters": int(stats[6])}
+
+
+def reps_eta(C_mean, epsilon: float):
+    """REPS temperature eta* minimising the dual (+inf: uniform; 0: on the minima)."""
+    Cm = np.ascontiguousarray(C_mean, np.float64)
+    it = C.c_int(0)
+    eta = lib().orc_reps_eta(len(Cm), _p(Cm), C.c_double(epsilon), C.byref(it))
+    return eta, it.value
 
 
 def add(osc: OracleScene, shape: int, pose_a7, pose_b7) -> float:

@@ -970,6 +970,185 @@ int orc_optimizer(const orc_opt *op, int N, const double *C, double *pose, doubl
 }
 
 /* ------------------------------------------------------------------------- */
+/* WRS and REPS updates (Sec. III-D): a PMF over all simulations, K draws     */
+/* with replacement, exploration of every simulation                          */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t kind;             /* 1 = WRS, 2 = REPS */
+    double lambda;            /* WRS temperature */
+    double epsilon;           /* REPS bound on KL(P || uniform) */
+    double sigma_pose[6];     /* exploration: x y z (m), rotation (rad) x3 */
+    double sigma_theta[2];    /* exploration: m (kg), mu */
+    int32_t explore_velocity; /* 0: perturb the pose; 1: perturb the velocity instead */
+    double sigma_vel[6];      /* velocity kick: linear (m/s) x3, angular (rad/s) x3 */
+    double m_lo, m_hi, mu_lo, mu_hi;
+} orc_soft_opt;
+
+/* REPS sums over the finite costs at temperature eta: with D_i = C_min - C_i,
+ * e_i = exp(D_i / eta): S0 = sum e_i, S1 = sum e_i D_i, S2 = sum e_i D_i^2 */
+static void reps_sums(int N, const double *C, double cmin, double eta, double *S0, double *S1, double *S2) {
+    double a = 0, b = 0, c = 0;
+    for (int i = 0; i < N; i++) {
+        if (!isfinite(C[i])) continue;
+        double d = cmin - C[i], e = exp(d / eta);
+        a += e; b += e * d; c += e * d * d;
+    }
+    *S0 = a; *S1 = b; *S2 = c;
+}
+
+/* d/d eta of the REPS dual g(eta) = eta eps + eta log((1/K) sum exp(R_i/eta)),
+ * R_i = C_max + C_min - C_i (so R_i - max R = D_i):
+ *   g'(eta) = eps + log(S0/K) - S1 / (eta S0) */
+static double reps_dg(double eps, double K, double S0, double S1, double eta) {
+    return eps + log(S0 / K) - S1 / (eta * S0);
+}
+
+/*
+ * eta* = argmin_{eta > 0} g(eta) for the finite costs C (K = their count).
+ * g is convex; g' rises from eps + log(n_min/K) (eta -> 0, n_min = number of
+ * costs equal to C_min) to eps (eta -> inf). Returns +inf when every finite
+ * cost is equal (any eta gives the uniform PMF) and 0 when
+ * eps >= log(K/n_min) (the PMF concentrates on the minima). Otherwise the root
+ * of g' by Newton steps in t = log(eta) (dg'/dt = Var_w(D)/eta^2), kept inside
+ * a bracket that every step shrinks, bisecting when Newton leaves it.
+ */
+double orc_reps_eta(int N, const double *C, double eps, int *iters_out) {
+    double cmin = INFINITY, cmax = -INFINITY;
+    int K = 0;
+    for (int i = 0; i < N; i++)
+        if (isfinite(C[i])) { K++; if (C[i] < cmin) cmin = C[i]; if (C[i] > cmax) cmax = C[i]; }
+    if (iters_out) *iters_out = 0;
+    if (K == 0 || !(cmax > cmin)) return INFINITY;
+    int nmin = 0;
+    for (int i = 0; i < N; i++) if (isfinite(C[i]) && C[i] == cmin) nmin++;
+    if (eps >= log((double)K / nmin)) return 0.0;
+    const double range = cmax - cmin;
+    double tlo = log(range) - 50.0, thi = log(range) + 50.0;   /* g'(e^tlo) < 0 < g'(e^thi) */
+    double S0, S1, S2;
+    for (int k = 0; k < 200; k++) {   /* widen the bracket until it holds the root */
+        reps_sums(N, C, cmin, exp(tlo), &S0, &S1, &S2);
+        if (reps_dg(eps, K, S0, S1, exp(tlo)) < 0) break;
+        tlo -= 50.0;
+    }
+    double t = 0.5 * (tlo + thi);
+    int it = 0;
+    for (; it < 200; it++) {
+        const double eta = exp(t);
+        reps_sums(N, C, cmin, eta, &S0, &S1, &S2);
+        const double g1 = reps_dg(eps, K, S0, S1, eta);
+        if (g1 < 0) tlo = t; else thi = t;
+        const double mean = S1 / S0, var = S2 / S0 - mean * mean;
+        const double slope = var / (eta * eta);   /* dg'/dt */
+        double tn = (slope > 0) ? t - g1 / slope : 0.5 * (tlo + thi);
+        if (!(tn > tlo && tn < thi)) tn = 0.5 * (tlo + thi);
+        if (fabs(tn - t) <= 1e-13 * (1.0 + fabs(t)) || thi - tlo <= 1e-13 * (1.0 + fabs(t))) { t = tn; it++; break; }
+        t = tn;
+    }
+    if (iters_out) *iters_out = it;
+    return exp(t);
+}
+
+/*
+ * One WRS or REPS update over N environments with window-mean costs C [N]:
+ *  1. the PMF over the finite-cost simulations (diverged ones get 0):
+ *     WRS  P(i) ~ exp(-lambda (C_i - C_min));
+ *     REPS P(i) ~ exp(R_i / eta*) = exp(-(C_i - C_min) / eta*), eta* from
+ *          orc_reps_eta (uniform when eta* = +inf, on the minima when eta* = 0);
+ *     every cost non-finite: uniform over all;
+ *  2. K = N draws with replacement: environment i takes the parent at the
+ *     inverse CDF (index order) of u_i, u_i from stream 3 (update_index, i);
+ *  3. each environment copies its parent's pose, velocity, parameters and
+ *     status (from the state before the update) and explores with eps ~ N(0, I_8)
+ *     from stream 1 (update_index, i): m += s_m eps_6, mu += s_mu eps_7
+ *     (clamped); pose: x += s_p,0..2 eps_0..2, R <- exp([s_r,0..2 eps_3..5]x) R,
+ *     or with explore_velocity v += s_v,0..2 eps_0..2, w += s_v,3..5 eps_3..5.
+ * i* = lowest (C, index). Outputs: parent [N]; stats (may be NULL): eta*,
+ * sum of weights, KL(P || uniform over the finite ones), number finite,
+ * C_min, C_max, Newton iterations. Returns i*.
+ */
+int orc_softmax_update(const orc_soft_opt *op, int N, const double *C, double *pose, double *vel,
+                       double *theta, int32_t *status, uint64_t seed, uint32_t update_index,
+                       int32_t *parent, double *stats) {
+    int istar = 0;
+    for (int i = 1; i < N; i++) if (cmp_idx_cost(C, i, istar) < 0) istar = i;
+    double cmin = INFINITY, cmax = -INFINITY;
+    int K = 0;
+    for (int i = 0; i < N; i++)
+        if (isfinite(C[i])) { K++; if (C[i] < cmin) cmin = C[i]; if (C[i] > cmax) cmax = C[i]; }
+    double *w = (double *)malloc(sizeof(double) * N);
+    double eta = NAN;
+    int iters = 0;
+    if (K == 0) {
+        for (int i = 0; i < N; i++) w[i] = 1.0;
+    } else if (op->kind == 2) {
+        eta = orc_reps_eta(N, C, op->epsilon, &iters);
+        for (int i = 0; i < N; i++) {
+            if (!isfinite(C[i])) w[i] = 0.0;
+            else if (isinf(eta)) w[i] = 1.0;
+            else if (eta == 0.0) w[i] = (C[i] == cmin) ? 1.0 : 0.0;
+            else w[i] = exp((cmin - C[i]) / eta);
+        }
+    } else {
+        for (int i = 0; i < N; i++) w[i] = isfinite(C[i]) ? exp(-op->lambda * (C[i] - cmin)) : 0.0;
+    }
+    double W = 0;
+    for (int i = 0; i < N; i++) W += w[i];
+    double kl = 0;
+    for (int i = 0; i < N; i++)
+        if (w[i] > 0) kl += (w[i] / W) * log((w[i] / W) * (K > 0 ? K : N));
+    /* the state before the update: every environment is replaced */
+    double *p0 = (double *)malloc(sizeof(double) * 7 * N);
+    double *v0 = (double *)malloc(sizeof(double) * 6 * N);
+    double *t0 = (double *)malloc(sizeof(double) * 2 * N);
+    int32_t *s0 = (int32_t *)malloc(sizeof(int32_t) * N);
+    memcpy(p0, pose, sizeof(double) * 7 * N);
+    memcpy(v0, vel, sizeof(double) * 6 * N);
+    memcpy(t0, theta, sizeof(double) * 2 * N);
+    memcpy(s0, status, sizeof(int32_t) * N);
+    for (int i = 0; i < N; i++) {
+        double u[2];
+        orc_uniforms(seed, 3, update_index, (uint32_t)i, 0, u);
+        const double pos = u[0] * W;
+        double cum = 0;
+        int par = N - 1;
+        while (par > 0 && w[par] == 0) par--;   /* the last positive weight, if pos reaches W */
+        for (int j = 0; j < N; j++) {
+            cum += w[j];
+            if (pos < cum) { par = j; break; }
+        }
+        if (parent) parent[i] = par;
+        double eps[8];
+        orc_normals(seed, 1, update_index, (uint32_t)i, 8, eps);
+        const double *pp = p0 + 7 * (size_t)par;
+        double *pi = pose + 7 * (size_t)i;
+        double *vi = vel + 6 * (size_t)i;
+        for (int a = 0; a < 6; a++) vi[a] = v0[6 * (size_t)par + a];
+        if (op->explore_velocity) {
+            for (int a = 0; a < 7; a++) pi[a] = pp[a];
+            for (int a = 0; a < 6; a++) vi[a] += op->sigma_vel[a] * eps[a];
+        } else {
+            pi[0] = pp[0] + op->sigma_pose[0] * eps[0];
+            pi[1] = pp[1] + op->sigma_pose[1] * eps[1];
+            pi[2] = pp[2] + op->sigma_pose[2] * eps[2];
+            quat qp = {pp[3], pp[4], pp[5], pp[6]};
+            quat qn = qnormalize(qmul(quat_exp(v3(op->sigma_pose[3] * eps[3], op->sigma_pose[4] * eps[4],
+                                                  op->sigma_pose[5] * eps[5])), qp));
+            pi[3] = qn.w; pi[4] = qn.x; pi[5] = qn.y; pi[6] = qn.z;
+        }
+        theta[2 * i] = fmin(fmax(t0[2 * par] + op->sigma_theta[0] * eps[6], op->m_lo), op->m_hi);
+        theta[2 * i + 1] = fmin(fmax(t0[2 * par + 1] + op->sigma_theta[1] * eps[7], op->mu_lo), op->mu_hi);
+        status[i] = s0[par];
+    }
+    if (stats) {
+        stats[0] = eta; stats[1] = W; stats[2] = kl; stats[3] = K; stats[4] = cmin; stats[5] = cmax;
+        stats[6] = iters;
+    }
+    free(w); free(p0); free(v0); free(t0); free(s0);
+    return istar;
+}
+
+/* ------------------------------------------------------------------------- */
 /* ADD (Sec. IV): mean distance of the object's points at two poses           */
 /* ------------------------------------------------------------------------- */
 double orc_add(const orc_scene *sc, int shape, const double *pose_a7, const double *pose_b7) {

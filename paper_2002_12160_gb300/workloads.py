@@ -201,13 +201,27 @@ class SimConfig:
 
 @dataclasses.dataclass
 class OptConfig:
-    """Elite-weighted Gaussian resample (run every `window` frames)."""
+    """Optimizer run every `window` frames.
+
+    kind "elite": elite-weighted Gaussian resample (the configuration's PBO
+    variant); "wrs" / "reps": a PMF over all simulations (softmax of the costs
+    with temperature wrs_lambda, or the REPS temperature for the KL bound
+    reps_epsilon), N draws with replacement, and isotropic exploration of every
+    simulation: parameters by sigma_theta, and the pose by sigma_pose
+    (explore "pose") or the velocity by sigma_vel (explore "velocity")."""
 
     window: int = 10
     elite_frac: float = 0.1
     floor_std: tuple = (0.001, 0.001, 0.001, 0.01, 0.01, 0.01, 0.005, 0.02)
     m_range: tuple = (0.01, 1.0)
     mu_range: tuple = (0.05, 2.0)
+    kind: str = "elite"
+    wrs_lambda: float = 1.0
+    reps_epsilon: float = 0.5
+    sigma_pose: tuple = (0.001, 0.001, 0.001, 0.01, 0.01, 0.01)
+    sigma_theta: tuple = (0.005, 0.02)
+    explore: str = "pose"
+    sigma_vel: tuple = (0.01, 0.01, 0.01, 0.1, 0.1, 0.1)
 
 
 @dataclasses.dataclass
