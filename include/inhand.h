@@ -101,12 +101,26 @@ typedef struct {
     float escape_radius;   /* |x| beyond this marks the env escaped */
 } ih_config;
 
-/* Optimizer constants (elite-weighted Gaussian resample). */
+/* Optimizer kinds (Sec. III-D). */
+enum { IH_OPT_ELITE = 0, IH_OPT_WRS = 1, IH_OPT_REPS = 2 };
+
+/* Optimizer constants. IH_OPT_ELITE: elite-weighted Gaussian resample (uses
+ * elite_frac, floor_std and the clamps). IH_OPT_WRS / IH_OPT_REPS: a PMF over
+ * all simulations, N draws with replacement and isotropic exploration of every
+ * simulation (uses wrs_lambda or reps_epsilon, the sigma_* fields and the
+ * clamps). */
 typedef struct {
     float elite_frac;      /* k = max(1, floor(elite_frac N)) elites */
     float floor_std[8];    /* exploration floor: x y z (m), rotation (rad) x3, m (kg), mu */
     float m_lo, m_hi;      /* clamp of the perturbed mass */
     float mu_lo, mu_hi;    /* clamp of the perturbed friction */
+    int32_t kind;          /* IH_OPT_ELITE, IH_OPT_WRS or IH_OPT_REPS */
+    float wrs_lambda;      /* WRS temperature lambda > 0 */
+    float reps_epsilon;    /* REPS bound epsilon > 0 on KL(P || uniform) */
+    float sigma_pose[6];   /* exploration of the pose: x y z (m), rotation (rad) x3 */
+    float sigma_theta[2];  /* exploration of m (kg) and mu */
+    int32_t explore_velocity;  /* 1: explore the velocity by sigma_vel instead of the pose */
+    float sigma_vel[6];    /* linear (m/s) x3, angular (rad/s) x3 */
 } ih_opt_config;
 
 /* Create a simulator for cfg->n_envs environments on the current device.
@@ -242,8 +256,24 @@ ih_status cost_eval(ih_sim *sim, const float *obs, double *cost_mean, int32_t *a
  *  5. each non-elite copies its parent's pose, velocity, parameters and
  *     status and adds L eps (eps from counter (1, update_index, i, 0..3)):
  *     x += d_0..2, R <- exp([d_3..5]x) R, m += d_6, mu += d_7, then clamps.
- * Elites are unchanged. The cost window is reset. Outputs (device, may be
- * NULL): argmin int32[1] = i*, parent int32[N] (self for elites).
+ * Elites are unchanged. The cost window is reset.
+ * With opt->kind IH_OPT_WRS or IH_OPT_REPS instead (Sec. III-D, WRS and REPS):
+ *  1. over the simulations with a finite C_i (the others get weight 0; all
+ *     of them when none is finite), WRS P(i) ~ exp(-lambda (C_i - C_min));
+ *     REPS P(i) ~ exp(R_i / eta*), R_i = C_max + C_min - C_i, eta* the
+ *     minimiser of the dual eta eps + eta log((1/K) sum exp(R_i / eta)) (K
+ *     finite simulations), by Newton steps on log eta inside a shrinking
+ *     bracket, in FP64 (equal costs: uniform; eps >= log(K / #minima): the
+ *     minima only);
+ *  2. every simulation i takes the parent at the inverse CDF (index order) of
+ *     u_i from Philox counter (3, update_index, i, 0) -- N draws with
+ *     replacement -- and copies its state as it was before the update;
+ *  3. explores with eps from counter (1, update_index, i, 0..3): m, mu +=
+ *     sigma_theta eps_6,7 (clamped), and x += sigma_pose eps_0..2, R <-
+ *     exp([sigma_pose eps_3..5]x) R, or with explore_velocity v, w +=
+ *     sigma_vel eps_0..5 (the pose then changes only through the dynamics).
+ * Outputs (device, may be NULL): argmin int32[1] = i*, parent int32[N]
+ * (self for elites).
  * Errors: IH_ERR_ARG for elite_frac outside (0, 1] or bad clamps;
  * IH_ERR_STATE when no frame has been scored since the last reset. */
 ih_status optimizer_update(ih_sim *sim, const ih_opt_config *opt, uint32_t update_index,

@@ -63,6 +63,10 @@ struct ih_sim {
     float2 *ws_params = nullptr, *tr_params = nullptr, *best_params = nullptr;
     float *best_grad = nullptr, *scale = nullptr, *r_grad = nullptr;
     double *best_c = nullptr, *c0 = nullptr, *r_cost = nullptr;
+    // WRS / REPS: the state before an update
+    float4 *sn_pose = nullptr, *sn_vel = nullptr;
+    float2 *sn_params = nullptr;
+    int *sn_status = nullptr;
     // captured tracking window (replayed by sim_track_window)
     cudaGraphExec_t win_exec = nullptr;
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
@@ -414,6 +418,11 @@ OptArgs opt_args(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int
     a.status = s->status; a.is_elite = s->is_elite; a.rank = s->rank; a.elite_env = s->elite_env;
     a.elite_w = s->elite_w; a.block_w = s->block_w; a.moments = s->moments; a.misc = s->misc;
     a.argmin_state = s->argmin; a.argmin_out = argmin; a.parent_out = parent; a.win = nullptr;
+    a.kind = opt->kind; a.wrs_lambda = opt->wrs_lambda; a.reps_epsilon = opt->reps_epsilon;
+    for (int k = 0; k < 6; ++k) { a.sigma_pose[k] = opt->sigma_pose[k]; a.sigma_vel[k] = opt->sigma_vel[k]; }
+    a.sigma_theta[0] = opt->sigma_theta[0]; a.sigma_theta[1] = opt->sigma_theta[1];
+    a.explore_velocity = opt->explore_velocity;
+    a.sn_pose = s->sn_pose; a.sn_vel = s->sn_vel; a.sn_params = s->sn_params; a.sn_status = s->sn_status;
     return a;
 }
 
@@ -424,6 +433,29 @@ ih_status check_opt(ih_sim *s, const ih_opt_config *opt) {
     for (int k = 0; k < 8; ++k)
         if (!(opt->floor_std[k] >= 0.0f) || !std::isfinite(opt->floor_std[k]))
             return fail(s, IH_ERR_ARG, "floor_std[%d] is invalid", k);
+    if (opt->kind < IH_OPT_ELITE || opt->kind > IH_OPT_REPS) return fail(s, IH_ERR_ARG, "unknown optimizer kind");
+    if (opt->kind != IH_OPT_ELITE) {
+        if (opt->kind == IH_OPT_WRS && !(opt->wrs_lambda > 0.0f && std::isfinite(opt->wrs_lambda)))
+            return fail(s, IH_ERR_ARG, "wrs_lambda must be positive");
+        if (opt->kind == IH_OPT_REPS && !(opt->reps_epsilon > 0.0f && std::isfinite(opt->reps_epsilon)))
+            return fail(s, IH_ERR_ARG, "reps_epsilon must be positive");
+        for (int k = 0; k < 6; ++k)
+            if (!(opt->sigma_pose[k] >= 0.0f) || !std::isfinite(opt->sigma_pose[k]) || !(opt->sigma_vel[k] >= 0.0f) ||
+                !std::isfinite(opt->sigma_vel[k]))
+                return fail(s, IH_ERR_ARG, "exploration sigma %d is invalid", k);
+        if (!(opt->sigma_theta[0] >= 0.0f) || !(opt->sigma_theta[1] >= 0.0f) || !std::isfinite(opt->sigma_theta[0]) ||
+            !std::isfinite(opt->sigma_theta[1]))
+            return fail(s, IH_ERR_ARG, "sigma_theta is invalid");
+        // the state before the update, for draws with replacement (allocated once, outside any capture)
+        if (!s->sn_pose) {
+            const size_t N = s->cfg.n_envs;
+            cudaError_t e = cudaSuccess;
+            auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+            A(dalloc(s, &s->sn_pose, 2 * N)); A(dalloc(s, &s->sn_vel, 2 * N));
+            A(dalloc(s, &s->sn_params, N)); A(dalloc(s, &s->sn_status, N));
+            if (e != cudaSuccess) return cuda_fail(s, e, "optimizer snapshot");
+        }
+    }
     return IH_OK;
 }
 }  // namespace

@@ -290,6 +290,14 @@ struct OptArgs {
     int *argmin_out;
     int *parent_out;
     const WinDesc *win;       // when set, update_index comes from win
+    // WRS / REPS (kind 1 / 2): PMF over all simulations, draws with replacement
+    int kind;
+    double wrs_lambda, reps_epsilon;
+    float sigma_pose[6], sigma_theta[2], sigma_vel[6];
+    int explore_velocity;
+    float4 *sn_pose, *sn_vel; // [N][2] state before the update
+    float2 *sn_params;        // [N]
+    int *sn_status;           // [N]
 };
 int opt_blocks(int N);
 

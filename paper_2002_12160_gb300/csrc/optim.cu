@@ -479,6 +479,220 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
     a.status[i] = a.status[par];
 }
 
+// ---------------------------------------------------------------- WRS / REPS
+// (Sec. III-D): a PMF over all simulations, N draws with replacement,
+// isotropic exploration of every simulation.
+constexpr int kSoft = 1024;
+
+// sums of three doubles over the block, in warp order (every thread gets them)
+__device__ void block_sum3(double &x, double &y, double &z, double (*red)[3]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = x; red[threadIdx.x >> 5][1] = y; red[threadIdx.x >> 5][2] = z; }
+    __syncthreads();
+    x = y = z = 0.0;
+    for (int w = 0; w < kSoft / 32; ++w) { x += red[w][0]; y += red[w][1]; z += red[w][2]; }
+    __syncthreads();
+}
+
+// S0 = sum e_i, S1 = sum e_i D_i, S2 = sum e_i D_i^2 over the finite costs,
+// D_i = C_min - C_i, e_i = exp(D_i / eta)
+__device__ void reps_sums(const OptArgs &a, double cmin, double eta, double &S0, double &S1, double &S2,
+                          double (*red)[3]) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < a.N; i += kSoft) {
+        const double c = a.c_mean[i];
+        if (!isfinite(c)) continue;
+        const double d = cmin - c, e = exp(d / eta);
+        s0 += e; s1 += e * d; s2 += e * d * d;
+    }
+    block_sum3(s0, s1, s2, red);
+    S0 = s0; S1 = s1; S2 = s2;
+}
+
+// One CTA: C_min, C_max and the number K of finite window means, i*, the REPS
+// temperature, the weights and their inclusive CDF in index order (elite_w),
+// the total (misc[M_WSUM]).
+__global__ void __launch_bounds__(kSoft) soft_weights_kernel(const OptArgs a) {
+    __shared__ double red[kSoft / 32][3];
+    __shared__ unsigned long long s_min_key;
+    __shared__ int s_min_idx;
+    const int N = a.N, t = threadIdx.x;
+    double lo = INFINITY, hi = -INFINITY, cnt = 0.0;
+    unsigned long long bk = ~0ull;
+    int bi = 0x7fffffff;
+    for (int i = t; i < N; i += kSoft) {
+        const double c = a.c_mean[i];
+        if (isfinite(c)) { lo = fmin(lo, c); hi = fmax(hi, c); cnt += 1.0; }
+        const unsigned long long key = order_key(c);
+        if (key < bk || (key == bk && i < bi)) { bk = key; bi = i; }
+    }
+    // min and max as sums of one-hot terms would be inexact: reduce them directly
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ok < bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+    }
+    if (t == 0) { s_min_key = ~0ull; s_min_idx = 0x7fffffff; }
+    if ((t & 31) == 0) { red[t >> 5][0] = lo; red[t >> 5][1] = hi; red[t >> 5][2] = cnt; }
+    __syncthreads();
+    if ((t & 31) == 0) atomicMin(&s_min_key, bk);
+    double cmin = INFINITY, cmax = -INFINITY, K = 0.0;
+    for (int w = 0; w < kSoft / 32; ++w) { cmin = fmin(cmin, red[w][0]); cmax = fmax(cmax, red[w][1]); K += red[w][2]; }
+    __syncthreads();
+    if ((t & 31) == 0 && bk == s_min_key) atomicMin(&s_min_idx, bi);
+    double nmin = 0.0;
+    for (int i = t; i < N; i += kSoft) nmin += (a.c_mean[i] == cmin) ? 1.0 : 0.0;
+    double z0 = 0.0, z1 = 0.0;
+    block_sum3(nmin, z0, z1, red);
+    const int istar = s_min_idx;
+
+    // REPS temperature: the root of g'(eta) = eps + log(S0/K) - S1/(eta S0) by
+    // Newton steps in t = log(eta) (dg'/dt = Var_w(D)/eta^2) inside a
+    // shrinking bracket, bisecting when a step leaves it
+    double eta = NAN;
+    if (a.kind == 2 && K > 0.0) {
+        const double eps = a.reps_epsilon;
+        if (!(cmax > cmin)) {
+            eta = INFINITY;
+        } else if (eps >= log(K / nmin)) {
+            eta = 0.0;
+        } else {
+            double S0, S1, S2;
+            const double lr = log(cmax - cmin);
+            double tlo = lr - 50.0, thi = lr + 50.0;
+            for (int k = 0; k < 200; ++k) {
+                reps_sums(a, cmin, exp(tlo), S0, S1, S2, red);
+                if (eps + log(S0 / K) - S1 / (exp(tlo) * S0) < 0.0) break;
+                tlo -= 50.0;
+            }
+            double tt = 0.5 * (tlo + thi);
+            for (int it = 0; it < 200; ++it) {
+                const double e = exp(tt);
+                reps_sums(a, cmin, e, S0, S1, S2, red);
+                const double g1 = eps + log(S0 / K) - S1 / (e * S0);
+                if (g1 < 0.0) tlo = tt; else thi = tt;
+                const double mean = S1 / S0, var = S2 / S0 - mean * mean;
+                const double slope = var / (e * e);
+                double tn = (slope > 0.0) ? tt - g1 / slope : 0.5 * (tlo + thi);
+                if (!(tn > tlo && tn < thi)) tn = 0.5 * (tlo + thi);
+                if (fabs(tn - tt) <= 1e-13 * (1.0 + fabs(tt)) || thi - tlo <= 1e-13 * (1.0 + fabs(tt))) {
+                    tt = tn;
+                    break;
+                }
+                tt = tn;
+            }
+            eta = exp(tt);
+        }
+    }
+    // weights and their inclusive CDF in index order (chunks of kSoft, carried)
+    double carry = 0.0;
+    const int lane = t & 31, wid = t >> 5;
+    for (int base = 0; base < N; base += kSoft) {
+        const int i = base + t;
+        double w = 0.0;
+        if (i < N) {
+            const double c = a.c_mean[i];
+            if (K == 0.0) w = 1.0;
+            else if (!isfinite(c)) w = 0.0;
+            else if (a.kind == 1) w = exp(-a.wrs_lambda * (c - cmin));
+            else if (isinf(eta)) w = 1.0;
+            else if (eta == 0.0) w = (c == cmin) ? 1.0 : 0.0;
+            else w = exp((cmin - c) / eta);
+        }
+        double inc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) red[wid][0] = inc;
+        __syncthreads();
+        double before = 0.0, total = 0.0;
+        for (int q = 0; q < kSoft / 32; ++q) {
+            if (q < wid) before += red[q][0];
+            total += red[q][0];
+        }
+        if (i < N) a.elite_w[i] = carry + (before + inc);
+        carry += total;
+        __syncthreads();
+    }
+    if (t == 0) {
+        a.misc[M_WSUM] = carry;
+        a.misc[M_U] = eta;
+        a.misc[M_ISTAR] = (double)istar;
+        *a.argmin_state = istar;
+        if (a.argmin_out) *a.argmin_out = istar;
+    }
+}
+
+// Four lanes per environment: lane 0 draws the parent (inverse CDF), every
+// lane one Box-Muller pair of the exploration noise; lane 0 writes the state.
+__global__ void __launch_bounds__(kOptBlock * kApplyLanes) soft_apply_kernel(const OptArgs a) {
+    const int sub = threadIdx.x & (kApplyLanes - 1);
+    const int i = blockIdx.x * kOptBlock + (int)(threadIdx.x / kApplyLanes);
+    const unsigned qmask = 0xfu << (threadIdx.x & 28u);
+    const int N = a.N;
+    if (i >= N) return;   // whole quads
+    const uint32_t upd = a.win ? a.win->update_index : a.update_index;
+    int par = 0;
+    if (sub == 0) {
+        if (i == 0) *a.n_window = 0;
+        a.c_sum[i] = 0.0;
+        const uint4 uw = rng_words(a.seed, 3, upd, (uint32_t)i, 0);
+        const double pos = unit53(uw.x, uw.y) * a.misc[M_WSUM];
+        int lo = 0, hi = N - 1;   // first j with pos < CDF_j
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pos < a.elite_w[mid]) hi = mid; else lo = mid + 1;
+        }
+        par = lo;
+        if (a.parent_out) a.parent_out[i] = par;
+    }
+    double e0, e1;
+    gauss2(rng_words(a.seed, 1, upd, (uint32_t)i, (uint32_t)sub), e0, e1);
+    double eps[8];
+#pragma unroll
+    for (int b = 0; b < kApplyLanes; ++b) {
+        eps[2 * b] = __shfl_sync(qmask, e0, b, kApplyLanes);
+        eps[2 * b + 1] = __shfl_sync(qmask, e1, b, kApplyLanes);
+    }
+    if (sub != 0) return;
+    const float4 p0 = a.sn_pose[2 * par], p1 = a.sn_pose[2 * par + 1];
+    float4 v0 = a.sn_vel[2 * par], v1 = a.sn_vel[2 * par + 1];
+    if (a.explore_velocity) {
+        a.pose[2 * i] = p0;
+        a.pose[2 * i + 1] = p1;
+        v0 = make_float4((float)(v0.x + (double)a.sigma_vel[0] * eps[0]), (float)(v0.y + (double)a.sigma_vel[1] * eps[1]),
+                         (float)(v0.z + (double)a.sigma_vel[2] * eps[2]), 0.0f);
+        v1 = make_float4((float)(v1.x + (double)a.sigma_vel[3] * eps[3]), (float)(v1.y + (double)a.sigma_vel[4] * eps[4]),
+                         (float)(v1.z + (double)a.sigma_vel[5] * eps[5]), 0.0f);
+    } else {
+        const Q4d qn = qnorm_d(qmul_d(qexp_d((double)a.sigma_pose[3] * eps[3], (double)a.sigma_pose[4] * eps[4],
+                                             (double)a.sigma_pose[5] * eps[5]),
+                                      {p1.x, p1.y, p1.z, p1.w}));
+        a.pose[2 * i] = make_float4((float)(p0.x + (double)a.sigma_pose[0] * eps[0]),
+                                    (float)(p0.y + (double)a.sigma_pose[1] * eps[1]),
+                                    (float)(p0.z + (double)a.sigma_pose[2] * eps[2]), 0.0f);
+        a.pose[2 * i + 1] = make_float4((float)qn.w, (float)qn.x, (float)qn.y, (float)qn.z);
+    }
+    a.vel[2 * i] = v0;
+    a.vel[2 * i + 1] = v1;
+    const float2 th = a.sn_params[par];
+    const double m = fmin(fmax((double)th.x + (double)a.sigma_theta[0] * eps[6], (double)a.m_lo), (double)a.m_hi);
+    const double mu = fmin(fmax((double)th.y + (double)a.sigma_theta[1] * eps[7], (double)a.mu_lo), (double)a.mu_hi);
+    a.params[i] = make_float2((float)m, (float)mu);
+    a.status[i] = a.sn_status[par];
+}
+
 __global__ void win_desc_kernel(WinDesc *d, WinDesc v) { *d = v; }
 
 }  // namespace
@@ -497,6 +711,17 @@ cudaError_t launch_select(const OptArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
+    if (a.kind != 0) {   // WRS / REPS: weights, snapshot of the state, draws and exploration
+        const size_t N = a.N;
+        soft_weights_kernel<<<1, kSoft, 0, s>>>(a);
+        cudaError_t e = cudaMemcpyAsync(a.sn_pose, a.pose, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_vel, a.vel, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_params, a.params, N * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_status, a.status, N * sizeof(int), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        soft_apply_kernel<<<opt_blocks(a.N), kOptBlock * kApplyLanes, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     // the elite count, computed exactly as select_kernel does
     int k = (int)floor((double)a.elite_frac * (double)a.N);
     k = k < 1 ? 1 : (k > a.N ? a.N : k);

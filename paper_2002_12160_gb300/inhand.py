@@ -45,7 +45,12 @@ class IHConfig(C.Structure):
 
 class IHOptConfig(C.Structure):
     _fields_ = [("elite_frac", C.c_float), ("floor_std", C.c_float * 8), ("m_lo", C.c_float),
-                ("m_hi", C.c_float), ("mu_lo", C.c_float), ("mu_hi", C.c_float)]
+                ("m_hi", C.c_float), ("mu_lo", C.c_float), ("mu_hi", C.c_float), ("kind", C.c_int32),
+                ("wrs_lambda", C.c_float), ("reps_epsilon", C.c_float), ("sigma_pose", C.c_float * 6),
+                ("sigma_theta", C.c_float * 2), ("explore_velocity", C.c_int32), ("sigma_vel", C.c_float * 6)]
+
+
+OPT_KINDS = {"elite": 0, "wrs": 1, "reps": 2}
 
 
 _lib = None
@@ -121,7 +126,9 @@ def _check(t, dtype, shape, name):
 
 def _opt(opt) -> IHOptConfig:
     return IHOptConfig(opt.elite_frac, (C.c_float * 8)(*opt.floor_std), opt.m_range[0],
-                       opt.m_range[1], opt.mu_range[0], opt.mu_range[1])
+                       opt.m_range[1], opt.mu_range[0], opt.mu_range[1], OPT_KINDS[opt.kind], opt.wrs_lambda,
+                       opt.reps_epsilon, (C.c_float * 6)(*opt.sigma_pose), (C.c_float * 2)(*opt.sigma_theta),
+                       1 if opt.explore == "velocity" else 0, (C.c_float * 6)(*opt.sigma_vel))
 
 
 def _stream():

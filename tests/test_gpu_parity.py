@@ -323,3 +323,80 @@ def test_multi_frame_launch_equals_the_separate_calls():
     with pytest.raises(inhand.InhandError) as e:
         b.sim_frames_argmin()
     assert e.value.code == inhand.IH_ERR_STATE
+
+
+def _opt32(opt):
+    """The optimizer constants as the GPU receives them (FP32), widened exactly."""
+    import dataclasses
+    f = lambda v: tuple(float(np.float32(x)) for x in v)
+    return dataclasses.replace(opt, wrs_lambda=float(np.float32(opt.wrs_lambda)),
+                               reps_epsilon=float(np.float32(opt.reps_epsilon)), sigma_pose=f(opt.sigma_pose),
+                               sigma_theta=f(opt.sigma_theta), sigma_vel=f(opt.sigma_vel), m_range=f(opt.m_range),
+                               mu_range=f(opt.mu_range))
+
+
+@pytest.mark.parametrize("kind,explore", [("wrs", "pose"), ("reps", "pose"), ("reps", "velocity"), ("wrs", "velocity")])
+def test_wrs_and_reps_updates_match_oracle(kind, explore):
+    """WRS / REPS on the GPU (one CTA for the weights and the REPS temperature,
+    then draws with replacement and exploration) against the oracle: i* and
+    every parent exactly, states to FP32 rounding; a diverged environment is
+    never drawn."""
+    import dataclasses
+    n = 517
+    wl = W.make_workload("tracking_cyl64", n_envs=n, frames=6)
+    sim = start(wl, n=n, frames=6)
+    d = dev()
+    cm = torch.empty(n, dtype=torch.float64, device=d)
+    for f in range(5):
+        sim.sim_step(f, 1)
+        forces, _ = sim.sim_read_sensors()
+        sim.cost_eval(forces[7].clone(), cm)
+    # environment 5 made invalid before the last frame: its window mean is +inf
+    pose, vel, params, _ = sim.sim_get_state()
+    params = params.clone()
+    params[5, 0] = -1.0
+    sim.sim_set_state(pose, vel, params)
+    sim.sim_step(5, 1)
+    forces, _ = sim.sim_read_sensors()
+    sim.cost_eval(forces[7].clone(), cm)
+    before = oracle_state(sim.sim_get_state())
+    C = cm.cpu().numpy().copy()
+    assert np.isinf(C[5]) and np.isfinite(np.delete(C, 5)).all()
+    opt = dataclasses.replace(wl.opt, kind=kind, explore=explore, wrs_lambda=0.8, reps_epsilon=0.7)
+    am = torch.empty(1, dtype=torch.int32, device=d)
+    par = torch.empty(n, dtype=torch.int32, device=d)
+    sim.optimizer_update(opt, 9, am, par)
+    after = oracle_state(sim.sim_get_state())
+    istar, parent, stats = O.softmax_update(_opt32(opt), before, C, wl.seed, 9)
+    assert int(am.item()) == istar
+    np.testing.assert_array_equal(par.cpu().numpy(), parent)
+    assert len(np.unique(parent)) > 5 and not np.any(parent == 5)
+    np.testing.assert_allclose(after.pose[:, :3], before.pose[:, :3], atol=2e-7)
+    assert rot_close(after.pose, before.pose, 2e-6)
+    np.testing.assert_allclose(after.theta, before.theta, rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(after.vel, before.vel, atol=2e-6)
+    np.testing.assert_array_equal(after.status, before.status)
+    # the window restarts
+    sim.sim_step(0, 1)
+    forces, status = sim.sim_read_sensors()
+    sim.cost_eval(forces[7].clone(), cm)
+    _, c_one, _ = O.cost(sim32(wl.sim), forces.cpu().numpy().astype(np.float64),
+                         forces[7].cpu().numpy().astype(np.float64), status.cpu().numpy(), np.zeros(n), 1)
+    np.testing.assert_array_equal(cm.cpu().numpy(), c_one)
+
+
+def test_reps_window_replay_equals_the_separate_calls():
+    """A REPS window captured in a graph equals the separate calls bit for bit."""
+    import dataclasses
+    T = 3
+    wl, a, b = _twin("tracking_box27", 96, 2 * T)
+    d = dev()
+    opt = dataclasses.replace(wl.opt, kind="reps", explore="velocity")
+    obs = torch.rand((2 * T, wl.scene.n_pads, 3), dtype=torch.float32, device=d) * 0.2
+    for w in range(2):
+        for k in range(T):
+            a.sim_step_track(w * T + k, obs[w * T + k])
+        a.optimizer_update(opt, w)
+        b.sim_track_window(w * T, obs[w * T:(w + 1) * T], opt, w)
+    for x, y in zip(a.sim_get_state(), b.sim_get_state()):
+        assert torch.equal(x, y)
