@@ -84,8 +84,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the adjoint throughput and the refinement-vs-plain tracking study")
-    p.add_argument("--part", choices=["all", "adjoint"], default="all",
-                   help="adjoint: only the forward+adjoint throughput block (for profiling)")
+    p.add_argument("--part", choices=["all", "adjoint", "optimizers"], default="all",
+                   help="adjoint / optimizers: only that block (profiling, studies)")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     p.add_argument("--sweep", default=None,
                    help="comma-separated N values: also time the workload at each N (tracking frames/s)")
@@ -416,6 +416,46 @@ def refine_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_refined=10
     return out
 
 
+def optimizer_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024):
+    """Tracking error (median ADD of the argmin estimate over seeded
+    trajectories, mm) and window time of each optimizer of Sec. III-D at the
+    same N: the elite-weighted Gaussian resample, WRS, REPS, and REPS with
+    exploration by velocity kicks instead of pose noise."""
+    import dataclasses
+    import torch
+    from paper_2002_12160_gb300 import tracking, workloads as W
+    torch.cuda.set_device(local)
+    variants = {"elite": {"kind": "elite"}, "wrs": {"kind": "wrs"}, "reps": {"kind": "reps"},
+                "reps_velocity": {"kind": "reps", "explore": "velocity"}}
+    out = {}
+    for name in ["tracking_cyl64", "tracking_box27"]:
+        res = {}
+        for label, kw in variants.items():
+            adds, times = [], []
+            for seed in seeds:
+                wl = W.make_workload(name, n_envs=n_envs, frames=frames, seed=seed)
+                wl.opt = dataclasses.replace(wl.opt, **kw)
+                tr = tracking.Tracker(wl, n_envs=n_envs)
+                tr.prepare()
+                nw = frames // tr.T
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                tr.window(0)   # capture
+                torch.cuda.synchronize()
+                e0.record()
+                for w in range(1, nw):
+                    tr.window(w)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / (nw - 1))
+                adds.append(tr.add_mm(nw * tr.T))
+                tr.close()
+            res[label] = {"add_mm_median": statistics.median(adds), "add_mm_mean": float(np.mean(adds)),
+                          "ms_per_window": statistics.median(times), "add_mm": adds}
+        out[name] = res
+    torch.cuda.empty_cache()
+    return {"n_envs": n_envs, "frames": frames, "seeds": list(seeds), **out}
+
+
 def flops_of(work, wl):
     return (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * max(len(s) for s in wl.scene.shapes)) +
             work["pairs"] * FLOP_PER_PAIR + work["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
@@ -476,6 +516,7 @@ def run_ours(args, rank, world, local):
                                    "every environment, H = 30 frames, checkpoints every 10",
                            "forward_env_steps_per_s": value / world, **adj}
         line["refinement"] = refine_study(local)
+        line["optimizers"] = optimizer_study(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
@@ -488,6 +529,10 @@ def main():
     if args.part == "adjoint":
         if rank == 0:
             print(json.dumps({"part": "adjoint", "adjoint": measure_adjoint(local)}), flush=True)
+        return
+    if args.part == "optimizers":
+        if rank == 0:
+            print(json.dumps({"part": "optimizers", "optimizers": optimizer_study(local)}), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

@@ -28,7 +28,6 @@ namespace {
 constexpr int kSel = 1024;            // threads of the select kernel for large N
 constexpr int kSelSmall = 256;        // ... for N <= kKeys * kSelSmall
 constexpr int kKeys = 8;              // keys per thread held in registers
-constexpr int kWarps = kSel / 32;
 constexpr int kFin = 128;             // threads of the finalize kernel
 
 enum { M_K = 64, M_U, M_ISTAR, M_OK, M_WSUM, M_CMIN, M_SD, M_NFIN, M_NBLK };
@@ -484,7 +483,9 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
 // isotropic exploration of every simulation.
 constexpr int kSoft = 1024;
 
-// sums of three doubles over the block, in warp order (every thread gets them)
+// sums of three doubles over the block (every thread gets them): warp sums,
+// then the first warp sums the warps' partials and broadcasts the totals
+// through shared memory (FP64 adds are scarce on this part: one warp does them)
 __device__ void block_sum3(double &x, double &y, double &z, double (*red)[3]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -492,22 +493,38 @@ __device__ void block_sum3(double &x, double &y, double &z, double (*red)[3]) {
         y += __shfl_xor_sync(0xffffffffu, y, o);
         z += __shfl_xor_sync(0xffffffffu, z, o);
     }
-    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = x; red[threadIdx.x >> 5][1] = y; red[threadIdx.x >> 5][2] = z; }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[wid][0] = x; red[wid][1] = y; red[wid][2] = z; }
     __syncthreads();
-    x = y = z = 0.0;
-    for (int w = 0; w < kSoft / 32; ++w) { x += red[w][0]; y += red[w][1]; z += red[w][2]; }
+    if (wid == 0) {
+        double a = red[lane][0], b = red[lane][1], c = red[lane][2];   // kSoft / 32 == 32 partials
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        __syncwarp();
+        if (lane == 0) { red[0][0] = a; red[0][1] = b; red[0][2] = c; }
+    }
+    __syncthreads();
+    x = red[0][0]; y = red[0][1]; z = red[0][2];
     __syncthreads();
 }
 
 // S0 = sum e_i, S1 = sum e_i D_i, S2 = sum e_i D_i^2 over the finite costs,
 // D_i = C_min - C_i, e_i = exp(D_i / eta)
-__device__ void reps_sums(const OptArgs &a, double cmin, double eta, double &S0, double &S1, double &S2,
+// (FP32 exponentials, FP64 sums, for the search; FP64 throughout for the
+// final step)
+template <bool FP32_EXP>
+__device__ void reps_sums(const OptArgs &a, double cmin, double inv_eta, double &S0, double &S1, double &S2,
                           double (*red)[3]) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int i = threadIdx.x; i < a.N; i += kSoft) {
         const double c = a.c_mean[i];
         if (!isfinite(c)) continue;
-        const double d = cmin - c, e = exp(d / eta);
+        const double d = cmin - c;
+        const double e = FP32_EXP ? (double)__expf((float)(d * inv_eta)) : exp(d * inv_eta);
         s0 += e; s1 += e * d; s2 += e * d * d;
     }
     block_sum3(s0, s1, s2, red);
@@ -545,8 +562,19 @@ __global__ void __launch_bounds__(kSoft) soft_weights_kernel(const OptArgs a) {
     if ((t & 31) == 0) { red[t >> 5][0] = lo; red[t >> 5][1] = hi; red[t >> 5][2] = cnt; }
     __syncthreads();
     if ((t & 31) == 0) atomicMin(&s_min_key, bk);
-    double cmin = INFINITY, cmax = -INFINITY, K = 0.0;
-    for (int w = 0; w < kSoft / 32; ++w) { cmin = fmin(cmin, red[w][0]); cmax = fmax(cmax, red[w][1]); K += red[w][2]; }
+    if (t < 32) {   // the first warp combines the warps' partials
+        double mn = red[t][0], mx = red[t][1], ct = red[t][2];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            ct += __shfl_xor_sync(0xffffffffu, ct, o);
+        }
+        __syncwarp();
+        if (t == 0) { red[0][0] = mn; red[0][1] = mx; red[0][2] = ct; }
+    }
+    __syncthreads();
+    const double cmin = red[0][0], cmax = red[0][1], K = red[0][2];
     __syncthreads();
     if ((t & 31) == 0 && bk == s_min_key) atomicMin(&s_min_idx, bi);
     double nmin = 0.0;
@@ -566,48 +594,96 @@ __global__ void __launch_bounds__(kSoft) soft_weights_kernel(const OptArgs a) {
         } else if (eps >= log(K / nmin)) {
             eta = 0.0;
         } else {
+            // the scalar steps run in thread 0 and reach the block through
+            // shared memory (FP64 transcendentals are costly on this part)
+            __shared__ double s_sc[4];   // e^t, 1/e^t, t, done flag
             double S0, S1, S2;
-            const double lr = log(cmax - cmin);
-            double tlo = lr - 50.0, thi = lr + 50.0;
-            for (int k = 0; k < 200; ++k) {
-                reps_sums(a, cmin, exp(tlo), S0, S1, S2, red);
-                if (eps + log(S0 / K) - S1 / (exp(tlo) * S0) < 0.0) break;
-                tlo -= 50.0;
+            double tlo = 0.0, thi = 0.0, tt = 0.0;
+            if (t == 0) {
+                const double lr = log(cmax - cmin);
+                tlo = lr - 50.0;
+                thi = lr + 50.0;
+                s_sc[0] = exp(tlo); s_sc[1] = 1.0 / s_sc[0];
             }
-            double tt = 0.5 * (tlo + thi);
-            for (int it = 0; it < 200; ++it) {
-                const double e = exp(tt);
-                reps_sums(a, cmin, e, S0, S1, S2, red);
-                const double g1 = eps + log(S0 / K) - S1 / (e * S0);
-                if (g1 < 0.0) tlo = tt; else thi = tt;
-                const double mean = S1 / S0, var = S2 / S0 - mean * mean;
-                const double slope = var / (e * e);
-                double tn = (slope > 0.0) ? tt - g1 / slope : 0.5 * (tlo + thi);
-                if (!(tn > tlo && tn < thi)) tn = 0.5 * (tlo + thi);
-                if (fabs(tn - tt) <= 1e-13 * (1.0 + fabs(tt)) || thi - tlo <= 1e-13 * (1.0 + fabs(tt))) {
-                    tt = tn;
-                    break;
+            __syncthreads();
+            for (int k = 0; k < 200; ++k) {   // widen the bracket until g'(e^tlo) < 0 (a sign: FP32 will do)
+                reps_sums<true>(a, cmin, s_sc[1], S0, S1, S2, red);
+                if (t == 0) {
+                    const bool below = eps + log(S0 / K) - S1 / (s_sc[0] * S0) < 0.0;
+                    if (!below) { tlo -= 50.0; s_sc[0] = exp(tlo); s_sc[1] = 1.0 / s_sc[0]; }
+                    s_sc[3] = below ? 1.0 : 0.0;
                 }
-                tt = tn;
+                __syncthreads();
+                const bool done = s_sc[3] != 0.0;
+                __syncthreads();
+                if (done) break;
             }
-            eta = exp(tt);
+            if (t == 0) { tt = 0.5 * (tlo + thi); s_sc[0] = exp(tt); s_sc[1] = 1.0 / s_sc[0]; s_sc[2] = tt; s_sc[3] = 0.0; }
+            __syncthreads();
+            // Newton steps with FP32 exponentials down to FP32 accuracy, then
+            // one step with FP64 sums: Newton's quadratic convergence takes
+            // the ~1e-7 error of the FP32 root to ~1e-14
+            for (int it = 0; it < 201; ++it) {
+                const bool last = s_sc[3] == 2.0;
+                if (last) reps_sums<false>(a, cmin, s_sc[1], S0, S1, S2, red);
+                else reps_sums<true>(a, cmin, s_sc[1], S0, S1, S2, red);
+                if (t == 0) {
+                    const double e = s_sc[0];
+                    const double g1 = eps + log(S0 / K) - S1 / (e * S0);
+                    if (g1 < 0.0) tlo = tt; else thi = tt;
+                    const double mean = S1 / S0, var = S2 / S0 - mean * mean;
+                    const double slope = var / (e * e);
+                    double tn = (slope > 0.0) ? tt - g1 / slope : 0.5 * (tlo + thi);
+                    if (!(tn > tlo && tn < thi)) tn = 0.5 * (tlo + thi);
+                    const bool near = fabs(tn - tt) <= 1e-6 * (1.0 + fabs(tt)) || thi - tlo <= 1e-6 * (1.0 + fabs(tt));
+                    tt = tn;
+                    s_sc[0] = exp(tt); s_sc[1] = 1.0 / s_sc[0]; s_sc[2] = tt;
+                    s_sc[3] = last ? 1.0 : (near || it == 199 ? 2.0 : 0.0);
+                }
+                __syncthreads();
+                const bool done = s_sc[3] == 1.0;
+                __syncthreads();
+                if (done) break;
+            }
+            eta = s_sc[0];
         }
     }
-    // weights and their inclusive CDF in index order (chunks of kSoft, carried)
+    if (t == 0) {   // for the weights (grid) and the CDF
+        a.misc[M_U] = eta;
+        a.misc[M_CMIN] = cmin;
+        a.misc[M_NFIN] = K;
+        a.misc[M_ISTAR] = (double)istar;
+        *a.argmin_state = istar;
+        if (a.argmin_out) *a.argmin_out = istar;
+    }
+}
+
+// One thread per environment: its weight (FP64), into elite_w.
+__global__ void soft_w_kernel(const OptArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const double eta = a.misc[M_U], cmin = a.misc[M_CMIN], K = a.misc[M_NFIN];
+    const double c = a.c_mean[i];
+    double w;
+    if (K == 0.0) w = 1.0;
+    else if (!isfinite(c)) w = 0.0;
+    else if (a.kind == 1) w = exp(-a.wrs_lambda * (c - cmin));
+    else if (isinf(eta)) w = 1.0;
+    else if (eta == 0.0) w = (c == cmin) ? 1.0 : 0.0;
+    else w = exp((cmin - c) / eta);
+    a.elite_w[i] = w;
+}
+
+// One CTA: the inclusive CDF of the weights in index order (chunks of kSoft,
+// carried), in place, and the total (misc[M_WSUM]).
+__global__ void __launch_bounds__(kSoft) soft_cdf_kernel(const OptArgs a) {
+    __shared__ double red[kSoft / 32][3];
+    const int N = a.N, t = threadIdx.x;
     double carry = 0.0;
     const int lane = t & 31, wid = t >> 5;
     for (int base = 0; base < N; base += kSoft) {
         const int i = base + t;
-        double w = 0.0;
-        if (i < N) {
-            const double c = a.c_mean[i];
-            if (K == 0.0) w = 1.0;
-            else if (!isfinite(c)) w = 0.0;
-            else if (a.kind == 1) w = exp(-a.wrs_lambda * (c - cmin));
-            else if (isinf(eta)) w = 1.0;
-            else if (eta == 0.0) w = (c == cmin) ? 1.0 : 0.0;
-            else w = exp((cmin - c) / eta);
-        }
+        const double w = (i < N) ? a.elite_w[i] : 0.0;
         double inc = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -616,22 +692,24 @@ __global__ void __launch_bounds__(kSoft) soft_weights_kernel(const OptArgs a) {
         }
         if (lane == 31) red[wid][0] = inc;
         __syncthreads();
-        double before = 0.0, total = 0.0;
-        for (int q = 0; q < kSoft / 32; ++q) {
-            if (q < wid) before += red[q][0];
-            total += red[q][0];
+        if (wid == 0) {   // exclusive scan of the warps' totals by the first warp
+            const double v = red[lane][0];
+            double x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double u = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += u;
+            }
+            __syncwarp();
+            red[lane][1] = x - v;
+            if (lane == 31) red[0][2] = x;
         }
-        if (i < N) a.elite_w[i] = carry + (before + inc);
-        carry += total;
+        __syncthreads();
+        if (i < N) a.elite_w[i] = carry + (red[wid][1] + inc);
+        carry += red[0][2];
         __syncthreads();
     }
-    if (t == 0) {
-        a.misc[M_WSUM] = carry;
-        a.misc[M_U] = eta;
-        a.misc[M_ISTAR] = (double)istar;
-        *a.argmin_state = istar;
-        if (a.argmin_out) *a.argmin_out = istar;
-    }
+    if (t == 0) a.misc[M_WSUM] = carry;
 }
 
 // Four lanes per environment: lane 0 draws the parent (inverse CDF), every
@@ -714,6 +792,8 @@ cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
     if (a.kind != 0) {   // WRS / REPS: weights, snapshot of the state, draws and exploration
         const size_t N = a.N;
         soft_weights_kernel<<<1, kSoft, 0, s>>>(a);
+        soft_w_kernel<<<(a.N + 127) / 128, 128, 0, s>>>(a);
+        soft_cdf_kernel<<<1, kSoft, 0, s>>>(a);
         cudaError_t e = cudaMemcpyAsync(a.sn_pose, a.pose, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_vel, a.vel, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_params, a.params, N * sizeof(float2), cudaMemcpyDeviceToDevice, s);
