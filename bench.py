@@ -187,7 +187,7 @@ def run_reference(args, rank, world):
     osc = O.OracleScene(wl.scene)
     pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed)
     st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
-    gt = O.State(O.pose8_to7(wl.nominal_pose)[None], np.zeros((1, 6)), np.array([wl.theta_gt]))
+    gt = O.State(O.pose8_to7(wl.gt_pose)[None], np.zeros((1, 6)), np.array([wl.theta_gt]))
     times = []
     frame = 0
     for s in range(args.warmup + args.steps):
@@ -420,30 +420,39 @@ def optimizer_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=10
     """Tracking error (median ADD of the argmin estimate over seeded
     trajectories, mm) and window time of each optimizer of Sec. III-D at the
     same N: the elite-weighted Gaussian resample, WRS, REPS, and REPS with
-    exploration by velocity kicks instead of pose noise."""
+    exploration by velocity kicks instead of pose noise; and the paper's two
+    baselines (Sec. IV): EYE (the same N noisy samples, no updates) and OLP
+    (one simulation from the nominal pose)."""
     import dataclasses
     import torch
     from paper_2002_12160_gb300 import tracking, workloads as W
     torch.cuda.set_device(local)
     variants = {"elite": {"kind": "elite"}, "wrs": {"kind": "wrs"}, "reps": {"kind": "reps"},
-                "reps_velocity": {"kind": "reps", "explore": "velocity"}}
+                "reps_velocity": {"kind": "reps", "explore": "velocity"},
+                "eye": {"baseline": "eye"}, "olp": {"baseline": "olp"}}
     out = {}
     for name in ["tracking_cyl64", "tracking_box27"]:
         res = {}
         for label, kw in variants.items():
+            kw = dict(kw)
+            baseline = kw.pop("baseline", None)
+            n = 1 if baseline == "olp" else n_envs
             adds, times = [], []
             for seed in seeds:
-                wl = W.make_workload(name, n_envs=n_envs, frames=frames, seed=seed)
+                wl = W.make_workload(name, n_envs=n, frames=frames, seed=seed)
                 wl.opt = dataclasses.replace(wl.opt, **kw)
-                tr = tracking.Tracker(wl, n_envs=n_envs)
+                tr = tracking.Tracker(wl, n_envs=n)
                 tr.prepare()
+                if baseline == "olp":
+                    tr.prepare_open_loop()
+                step = tr.window_eye if baseline else tr.window
                 nw = frames // tr.T
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                tr.window(0)   # capture
+                step(0)   # capture
                 torch.cuda.synchronize()
                 e0.record()
                 for w in range(1, nw):
-                    tr.window(w)
+                    step(w)
                 e1.record()
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1) / (nw - 1))

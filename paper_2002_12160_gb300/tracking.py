@@ -1,7 +1,7 @@
 """Algorithm 1 (sample-based optimization for in-hand pose tracking) on the GPU.
 
 The tracker holds two handles of the C ABI: the N tracking environments and
-one ground-truth environment (nominal pose, hidden mass and friction) whose
+one ground-truth environment (its true initial pose, hidden mass and friction) whose
 pad forces stand in for the real robot's observations o_t^(gt) (Sec. IV-A
 uses a simulated ground truth the same way). A window is T frames of
 "step all environments, score them, take i* = argmin C_i", followed by the
@@ -39,7 +39,8 @@ class Tracker:
         q = torch.from_numpy(wl.q_traj).contiguous().to(self.dev)
         self.sim.sim_set_commands(0, q)
         self.gt.sim_set_commands(0, q)
-        pose = torch.from_numpy(wl.nominal_pose[None].copy()).to(self.dev)
+        gt0 = wl.gt_pose if wl.gt_pose is not None else wl.nominal_pose
+        pose = torch.from_numpy(gt0[None].copy()).to(self.dev)
         vel = torch.zeros((1, 8), dtype=torch.float32, device=self.dev)
         par = torch.tensor([wl.theta_gt], dtype=torch.float32, device=self.dev)
         self.gt.sim_set_state(pose, vel, par)
@@ -72,6 +73,29 @@ class Tracker:
         f0 = w * T
         self.sim.sim_track_window(f0, self.obs[f0:f0 + T], self.wl.opt, w, self.est[f0:f0 + T],
                                   self.argmin[f0:f0 + T])
+
+    def window_eye(self, w: int):
+        """The identity baseline (EYE, Sec. IV): the window's frames stepped,
+        scored and argmin'd, with no optimizer update -- the simulations keep
+        their initial samples and the window mean runs from the start."""
+        T = self.T
+        f0 = w * T
+        self.sim.sim_step_frames(f0, self.obs[f0:f0 + T])
+        self.sim.sim_frames_argmin(self.est[f0:f0 + T], self.argmin[f0:f0 + T])
+
+    def prepare_open_loop(self):
+        """The open-loop baseline (OLP, Sec. IV): one simulation from the
+        nominal pose with the parameter ranges' midpoints; run it with
+        window_eye (its estimate is its own pose)."""
+        assert self.n == 1, "open loop tracks with one simulation"
+        wl = self.wl
+        pose = torch.from_numpy(wl.nominal_pose[None].copy()).to(self.dev)
+        vel = torch.zeros((1, 8), dtype=torch.float32, device=self.dev)
+        par = torch.tensor([[0.5 * (wl.init.m_range[0] + wl.init.m_range[1]),
+                             0.5 * (wl.init.mu_range[0] + wl.init.mu_range[1])]], dtype=torch.float32,
+                           device=self.dev)
+        self.sim.sim_set_state(pose, vel, par)
+        torch.cuda.synchronize()
 
     def window_unfused(self, w: int, step_events=None):
         """The same window as separate calls -- the T-frame step launch (bracketed

@@ -319,9 +319,10 @@ class Workload:
     q_traj: np.ndarray            # (frames + 1, D) float32
     shape_id: np.ndarray          # (N,) int32
     iters: np.ndarray             # (N,) int32
-    nominal_pose: np.ndarray      # (8,) float32: x y z pad, qw qx qy qz
+    nominal_pose: np.ndarray      # (8,) float32: x y z pad, qw qx qy qz -- the initial estimate
     theta_gt: tuple
     seed: int
+    gt_pose: np.ndarray = None    # (8,) float32: the true initial pose (the estimate's error applied)
 
     def describe(self) -> dict:
         s = [len(x) for x in self.scene.shapes]
@@ -405,7 +406,30 @@ def make_workload(name: str, n_envs: int | None = None, frames: int | None = Non
     theta_gt = theta_draw(seed + 1, init.m_range, init.mu_range)
     return Workload(name=name, scene=scene, sim=sim, opt=opt, init=init, n_envs=n,
                     frames=fr, q_traj=q, shape_id=sid, iters=iters,
-                    nominal_pose=nominal, theta_gt=theta_gt, seed=seed)
+                    nominal_pose=nominal, theta_gt=theta_gt, seed=seed,
+                    gt_pose=estimate_error(nominal, init, seed + 2))
+
+
+def estimate_error(nominal: np.ndarray, init: InitSampling, seed: int) -> np.ndarray:
+    """The true initial pose: the initial estimate (`nominal`) off by one draw
+    of the same noise the simulations are sampled with (translation
+    N(0, sigma_p^2) per axis; rotation by a world-frame rotation vector
+    N(0, sigma_r^2) per axis, applied on the left), so that the truth is
+    not the centre of the samples (the paper's initial pose noise, Sec. IV)."""
+    rng = np.random.default_rng(seed)
+    dp = rng.normal(0.0, init.sigma_p, 3)
+    w = rng.normal(0.0, init.sigma_r, 3)
+    th = float(np.linalg.norm(w))
+    axis = w / th if th > 0 else np.array([1.0, 0.0, 0.0])
+    qd = np.array([math.cos(th / 2), *(math.sin(th / 2) * axis)])
+    q0 = nominal[4:8].astype(np.float64)
+    qw = np.array([qd[0] * q0[0] - qd[1:] @ q0[1:],
+                   *(qd[0] * q0[1:] + q0[0] * qd[1:] + np.cross(qd[1:], q0[1:]))])
+    qw /= np.linalg.norm(qw)
+    out = nominal.astype(np.float64).copy()
+    out[:3] += dp
+    out[4:8] = qw
+    return out.astype(np.float32)
 
 
 def nominal_pose_for(scene: Scene, shape: int, palm_top: float = 0.01) -> np.ndarray:
