@@ -519,7 +519,7 @@ def run_ours(args, rank, world, local):
         line["sweep"] = sweep
         ok = [x for x in sweep if x["tracking_frames_per_s"] >= 30.0]
         line["largest_n_measured_at_30hz"] = max((x["n_envs"] for x in ok), default=None)
-    if not args.no_adjoint:
+    if not args.no_adjoint and world == 1:   # the studies run on single-GPU runs only
         adj = measure_adjoint(local)
         line["adjoint"] = {"what": "forward + reverse-mode gradient of the horizon cost (sim_adjoint), "
                                    "every environment, H = 30 frames, checkpoints every 10",

@@ -201,7 +201,10 @@ ih_status sim_step_track(ih_sim *sim, int32_t frame, const float *obs, double *c
  * mean and the pose after every frame are kept in the handle for
  * sim_frames_argmin. The environments need no argmin to advance, so the T
  * frames run without a grid-wide step in between. obs is device
- * float[T][P][3]. Passages: Sec. III-A, Sec. III-C, Algorithm 1. */
+ * float[T][P][3]. sim_frames_argmin must follow before any other scored call
+ * (sim_step_track, sim_step_frames, cost_eval, optimizer_update,
+ * sim_track_window), which return IH_ERR_STATE until it has. Passages:
+ * Sec. III-A, Sec. III-C, Algorithm 1. */
 ih_status sim_step_frames(ih_sim *sim, int32_t frame0, int32_t T, const float *obs);
 
 /* The argmin i*_f (NaN = +inf, ties to the lowest index) and the pose of i*_f

@@ -104,6 +104,14 @@ ih_status cuda_fail(ih_sim *s, cudaError_t e, const char *what) {
                 cudaGetErrorString(e));
 }
 
+// frames scored by sim_step_frames wait for sim_frames_argmin (which advances
+// the window counter); no other scored call may come in between
+ih_status check_no_pending(ih_sim *s) {
+    if (s->frames_T > 0)
+        return fail(s, IH_ERR_STATE, "sim_frames_argmin must follow sim_step_frames before further scoring");
+    return IH_OK;
+}
+
 template <typename T>
 cudaError_t dalloc(ih_sim *s, T **p, size_t count) {
     void *q = nullptr;
@@ -463,6 +471,7 @@ ih_status check_opt(ih_sim *s, const ih_opt_config *opt) {
 ih_status sim_step_track(ih_sim *s, int32_t frame, const float *obs, double *cost_mean, int32_t *argmin,
                          float *est_pose) {
     if (!s) return IH_ERR_ARG;
+    if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     if (frame < 0 || frame >= s->cfg.max_frames || !s->frame_ready[frame])
         return fail(s, IH_ERR_ARG, "no commands for frame %d", frame);
@@ -497,6 +506,7 @@ cudaError_t window_buffers(ih_sim *s, int T) {
 
 ih_status sim_step_frames(ih_sim *s, int32_t frame0, int32_t T, const float *obs) {
     if (!s) return IH_ERR_ARG;
+    if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
         return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + T);
@@ -529,6 +539,7 @@ ih_status sim_frames_argmin(ih_sim *s, float *est_pose, int32_t *argmin) {
 ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *obs, const ih_opt_config *opt,
                            uint32_t update_index, float *est_pose, int32_t *argmin) {
     if (!s) return IH_ERR_ARG;
+    if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
         return fail(s, IH_ERR_ARG, "window [%d, %d) outside the table", frame0, frame0 + T);
@@ -613,6 +624,7 @@ ih_status sim_read_sensors(ih_sim *s, float *forces, int32_t *env_status) {
 
 ih_status cost_eval(ih_sim *s, const float *obs, double *cost_mean, int32_t *argmin, float *est_pose) {
     if (!s) return IH_ERR_ARG;
+    if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     CostArgs a;
     a.N = s->cfg.n_envs; a.P = s->n_pads; a.cfg = s->dcfg; a.forces = s->forces; a.obs = obs;
@@ -629,6 +641,7 @@ ih_status cost_eval(ih_sim *s, const float *obs, double *cost_mean, int32_t *arg
 ih_status optimizer_update(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int32_t *argmin,
                            int32_t *parent) {
     if (!s) return IH_ERR_ARG;
+    if (ih_status rp = check_no_pending(s)) return rp;
     ih_status r = check_opt(s, opt);
     if (r != IH_OK) return r;
     if (s->window_frames < 1) return fail(s, IH_ERR_STATE, "no frame scored since the last update");

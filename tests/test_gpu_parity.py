@@ -312,6 +312,11 @@ def test_multi_frame_launch_equals_the_separate_calls():
             f = w * T + k
             a.sim_step_track(f, obs[f], cm_a, am_a[f:f + 1], est_a[f])
         b.sim_step_frames(w * T, obs[w * T:(w + 1) * T])
+        if w == 0:   # the frames' argmin comes before any further scoring
+            from paper_2002_12160_gb300 import inhand
+            with pytest.raises(inhand.InhandError) as e:
+                b.sim_step_track(T, obs[T])
+            assert e.value.code == inhand.IH_ERR_STATE
         b.sim_frames_argmin(est_b[w * T:(w + 1) * T], am_b[w * T:(w + 1) * T])
         a.optimizer_update(wl.opt, w, None, par_a)
         b.optimizer_update(wl.opt, w, None, par_b)
