@@ -65,7 +65,7 @@ def lib():
             L.orc_fk.argtypes = [P, P, P]
             L.orc_contacts.argtypes = [P, P, C.c_int, P, P, C.c_int, P]
             L.orc_unit_inertia.argtypes = [P, C.c_int, P]
-            L.orc_step.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P]
+            L.orc_step.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P, C.c_int]
             L.orc_cost.argtypes = [P, C.c_int, C.c_int, P, P, P, P, C.c_int, P, P]
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_philox4x32_10.restype = None
@@ -173,8 +173,25 @@ class State:
         return self.pose.shape[0]
 
     def subset(self, idx):
-        return State(self.pose[idx], self.vel[idx], self.theta[idx], self.shape[idx],
-                     None if self.iters is None else self.iters[idx], self.status[idx])
+        s = State(self.pose[idx], self.vel[idx], self.theta[idx], self.shape[idx],
+                  None if self.iters is None else self.iters[idx], self.status[idx])
+        if self.cache_n is not None:
+            s.cache_n, s.cache_id, s.cache_lam = (a[idx].copy() for a in (self.cache_n, self.cache_id, self.cache_lam))
+        return s
+
+    cache_n = cache_id = cache_lam = None
+
+    def warm_cache(self, cap: int):
+        """Start a (cold) warm-start cache of `cap` pairs per environment."""
+        self.cache_n = np.zeros(self.n, np.int32)
+        self.cache_id = np.zeros((self.n, cap), np.int32)
+        self.cache_lam = np.zeros((self.n, cap, 3))
+        return self
+
+    def drop_cache(self, envs):
+        """Environments whose state was replaced start cold again."""
+        if self.cache_n is not None:
+            self.cache_n[envs] = 0
 
 
 def step(osc: OracleScene, sim, st: State, q_traj, frame0: int, n_frames: int = 1):
@@ -183,9 +200,13 @@ def step(osc: OracleScene, sim, st: State, q_traj, frame0: int, n_frames: int = 
     q = np.ascontiguousarray(q_traj, np.float64)
     forces = np.zeros((st.n, osc.n_pads, 3))
     diag = np.zeros((st.n, DIAG))
+    warm = getattr(sim, "warm_start", False)
+    if warm and st.cache_n is None:
+        st.warm_cache(int(sim.c_max))
+    cache = (_p(st.cache_n), _p(st.cache_id), _p(st.cache_lam), st.cache_id.shape[1]) if warm else (None, None, None, 0)
     lib().orc_step(C.byref(osc.rec), C.byref(cfg), st.n, _p(q), frame0, n_frames, _p(st.pose),
                    _p(st.vel), _p(st.theta), _p(st.shape),
-                   None if st.iters is None else _p(st.iters), _p(st.status), _p(forces), _p(diag))
+                   None if st.iters is None else _p(st.iters), _p(st.status), _p(forces), _p(diag), *cache)
     return forces, diag
 
 
@@ -248,6 +269,7 @@ def optimizer(opt, st: State, C_mean, seed: int, update_index: int):
     stats = np.zeros(139)
     i = lib().orc_optimizer(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
                             _p(st.status), seed, update_index, _p(parent), _p(stats))
+    st.drop_cache(parent != np.arange(st.n))   # replaced environments start cold
     return i, parent, {"mean": stats[:8].copy(), "cov": stats[8:72].reshape(8, 8).copy(),
                        "L": stats[72:136].reshape(8, 8).copy(), "k": int(stats[136]),
                        "istar": int(stats[137]), "sd": float(stats[138])}
@@ -276,6 +298,7 @@ def softmax_update(opt, st: State, C_mean, seed: int, update_index: int):
     stats = np.zeros(7)
     i = lib().orc_softmax_update(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
                                  _p(st.status), seed, update_index, _p(parent), _p(stats))
+    st.drop_cache(np.arange(st.n))   # every environment is replaced
     return i, parent, {"eta": stats[0], "wsum": stats[1], "kl": stats[2], "n_finite": int(stats[3]),
                        "cmin": stats[4], "cmax": stats[5], "iters": int(stats[6])}
 

@@ -452,9 +452,26 @@ typedef struct {
     double inv_kt;   /* 1 / ((tr K - n^T K n) / 2): tangential step */
     double b;        /* velocity bias along n */
     int pad;
+    int id;          /* pair id: link << 8 | sphere */
     vec3 lam;        /* accumulated impulse on the object */
     vec3 lam_next;   /* this iteration's update (Jacobi: applied after all k) */
 } contact_t;
+
+/* Warm start: the final impulses of the environment's previous substep, by
+ * pair id (n entries). Each contact of the next substep starts from its
+ * pair's impulse if the pair was a contact then, else from zero. */
+typedef struct {
+    int32_t *n;       /* entries */
+    int32_t *id;      /* [cap] pair ids */
+    double *lam;      /* [cap][3] impulses */
+    int cap;
+} lam_cache;
+
+static vec3 cache_lookup(const lam_cache *c, int id) {
+    for (int k = 0; k < *c->n; k++)
+        if (c->id[k] == id) return v3(c->lam[3 * k], c->lam[3 * k + 1], c->lam[3 * k + 2]);
+    return v3(0, 0, 0);
+}
 
 /*
  * One contact's projected update from the current impulse lam and relative
@@ -490,7 +507,7 @@ static double contact_bias(const orc_config *cfg, double d, double h) {
 static void step_env(const orc_scene *sc, const orc_config *cfg, const double *lp_all,
                      int ns, double *pose7, double *vel6, const double *theta,
                      int shape, int iters, int32_t *status, double *forces, double *diag,
-                     contact_t *ct, int ct_cap) {
+                     contact_t *ct, int ct_cap, const lam_cache *cache) {
     const int n_links = 1 + 4 * sc->n_fingers;
     const int P = sc->n_pads;
     const double h = cfg->frame_dt / ns;
@@ -572,7 +589,8 @@ static void step_env(const orc_scene *sc, const orc_config *cfg, const double *l
                         vec3 p1 = vadd(B.p, mvmul(B.R, pl));         /* carried to the end */
                         k->vl = vscale(vsub(p1, p), 1.0 / h);
                     }
-                    k->lam = v3(0, 0, 0);
+                    k->id = (l << 8) | j;
+                    k->lam = cache ? cache_lookup(cache, k->id) : v3(0, 0, 0);
                 }
                 nc++;
             }
@@ -619,6 +637,15 @@ static void step_env(const orc_scene *sc, const orc_config *cfg, const double *l
             double *fp = forces + 3 * ct[k].pad;
             fp[0] -= ct[k].lam.x / h; fp[1] -= ct[k].lam.y / h; fp[2] -= ct[k].lam.z / h;
         }
+        /* the warm-start cache: this substep's contacts and final impulses */
+        if (cache) {
+            int nk = nc < cache->cap ? nc : cache->cap;
+            for (int k = 0; k < nk; k++) {
+                cache->id[k] = ct[k].id;
+                cache->lam[3 * k] = ct[k].lam.x; cache->lam[3 * k + 1] = ct[k].lam.y; cache->lam[3 * k + 2] = ct[k].lam.z;
+            }
+            *cache->n = nk;
+        }
     }
     for (int k = 0; k < 3 * P; k++) forces[k] /= ns;
 
@@ -640,12 +667,16 @@ static void step_env(const orc_scene *sc, const orc_config *cfg, const double *l
  * pose [N][7] (xyz, wxyz), vel [N][6] (linear, angular, world frame),
  * theta [N][2] (mass, friction), shape [N], iters [N] or NULL (cfg->iters),
  * status [N] (sticky bits), forces [N][P][3] of the last frame stepped,
- * diag [N][ORC_DIAG] of the last frame stepped.
+ * diag [N][ORC_DIAG] of the last frame stepped. With cache_n non-NULL the
+ * solver is warm-started: cache_n [N], cache_id [N][cache_cap] and
+ * cache_lam [N][cache_cap][3] carry each environment's last substep's
+ * contacts (pair id = link << 8 | sphere) and final impulses, read at the
+ * next substep and rewritten after it.
  */
 int orc_step(const orc_scene *sc, const orc_config *cfg, int N, const double *q_traj,
              int frame0, int n_frames, double *pose, double *vel, const double *theta,
              const int32_t *shape, const int32_t *iters, int32_t *status, double *forces,
-             double *diag) {
+             double *diag, int32_t *cache_n, int32_t *cache_id, double *cache_lam, int cache_cap) {
     const int D = 4 * sc->n_fingers, n_links = 1 + 4 * sc->n_fingers, ns = cfg->substeps;
     const int P = sc->n_pads;
     double *lp = (double *)malloc(sizeof(double) * 7 * n_links * (ns + 1));
@@ -664,9 +695,12 @@ int orc_step(const orc_scene *sc, const orc_config *cfg, int N, const double *q_
         }
         for (int i = 0; i < N; i++) {
             int it = iters ? iters[i] : cfg->iters;
+            lam_cache c = {cache_n + i, cache_id + (size_t)i * cache_cap, cache_lam + (size_t)i * 3 * cache_cap,
+                           cache_cap};
             step_env(sc, cfg, lp, ns, pose + 7 * (size_t)i, vel + 6 * (size_t)i,
                      theta + 2 * (size_t)i, shape ? shape[i] : 0, it, status + i,
-                     forces + (size_t)i * 3 * P, diag + (size_t)i * ORC_DIAG, ct, cap);
+                     forces + (size_t)i * 3 * P, diag + (size_t)i * ORC_DIAG, ct, cap,
+                     cache_n ? &c : NULL);
         }
     }
     free(lp); free(qk); free(ct);

@@ -197,6 +197,7 @@ class SimConfig:
     w_contact: float = 1.0       # weight of the contact-mismatch term
     c_max: int = 128             # contacts per environment per substep
     escape_radius: float = 0.3   # object farther than this from the palm = diverged
+    warm_start: bool = False     # start each contact's impulse from its pair's last substep
 
 
 @dataclasses.dataclass
