@@ -5,9 +5,10 @@ pairs).
 - the fixed point is unchanged: a resting box settles to a support force of
   exactly m g with no drift, as with cold starts;
 - warm starting carries the solve across substeps: with one Jacobi iteration
-  per substep the resting box still converges to m g (the impulses accumulate
-  from substep to substep), while cold starts stay far from it (one relaxed
-  step from zero reaches only about 1/n_c of the impulse);
+  per substep the resting box comes to rest carrying m g within the slop
+  (the impulses accumulate from substep to substep), while the cold-started
+  one (one relaxed step from zero reaches only about 1/n_c of the impulse)
+  sinks more than ten times the slop before the bias makes up the rest;
 - the cache holds exactly the last substep's contact pairs (distinct ids that
   decode to valid (link, sphere) pairs), and an optimizer update drops the
   cache of every environment it replaces.
@@ -46,11 +47,18 @@ def test_warm_start_keeps_the_fixed_point():
 
 
 def test_warm_start_converges_across_substeps_with_one_iteration():
-    f_warm, st_w, m, _ = _resting(1, True, 300)
-    f_cold, _, _, _ = _resting(1, False, 300)
-    assert abs(f_warm[2] + m * G) < 1e-3 * m * G, f_warm
-    assert abs(f_cold[2] + m * G) > 0.1 * m * G, f_cold
-    assert np.all(np.abs(st_w.vel[0]) < 1e-6)
+    # At rest both carry m g, but where they come to rest differs: the warm
+    # solve accumulates the support impulse over substeps and stops inside the
+    # zero-bias band [-slop, 0]; one relaxed step from zero delivers only about
+    # 1/n_c of it, so the cold-started box sinks until the penetration bias
+    # makes up the rest, more than ten times the slop deep. (Left running much
+    # longer, that deep equilibrium turns out to be unstable: it tips over.)
+    f_warm, st_w, m, z0 = _resting(1, True, 150)
+    _, st_c, _, _ = _resting(1, False, 150)
+    assert abs(f_warm[2] + m * G) < 1e-6 * m * G, f_warm
+    assert -SIM.slop - 1e-9 <= st_w.pose[0, 2] - z0 <= 0.0
+    assert st_c.pose[0, 2] - z0 < -10 * SIM.slop
+    assert np.all(np.abs(st_w.vel[0]) < 1e-9)
 
 
 def test_cache_holds_the_last_contacts_and_the_optimizer_drops_replaced_ones():
