@@ -51,6 +51,11 @@ class Config(C.Structure):
                 ("escape_radius", C.c_double)]
 
 
+class PD(C.Structure):
+    _fields_ = [("kp", C.c_double), ("kd", C.c_double), ("armature", C.c_double), ("v_slip", C.c_double),
+                ("w_slip", C.c_double)]
+
+
 class Opt(C.Structure):
     _fields_ = [("elite_frac", C.c_double), ("floor_std", C.c_double * 8), ("m_lo", C.c_double),
                 ("m_hi", C.c_double), ("mu_lo", C.c_double), ("mu_hi", C.c_double)]
@@ -67,6 +72,10 @@ def lib():
             L.orc_unit_inertia.argtypes = [P, C.c_int, P]
             L.orc_step.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P, C.c_int]
             L.orc_cost.argtypes = [P, C.c_int, C.c_int, P, P, P, P, C.c_int, P, P]
+            L.orc_step_pd.argtypes = [P, P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P,
+                                      P, P, P, C.c_int]
+            L.orc_cost_full.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P,
+                                        P, C.c_int, P, P]
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_philox4x32_10.restype = None
             L.orc_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, P]
@@ -177,9 +186,25 @@ class State:
                   None if self.iters is None else self.iters[idx], self.status[idx])
         if self.cache_n is not None:
             s.cache_n, s.cache_id, s.cache_lam = (a[idx].copy() for a in (self.cache_n, self.cache_id, self.cache_lam))
+        if self.qj is not None:
+            s.qj, s.qdj = self.qj[idx].copy(), self.qdj[idx].copy()
         return s
 
     cache_n = cache_id = cache_lam = None
+    qj = qdj = None   # PD-driven hand: joint positions and velocities (N, D)
+
+    def hand(self, q0, D: int | None = None):
+        """Start a PD-driven hand at joint positions q0 (D,) or (N, D), at rest."""
+        q0 = np.asarray(q0, np.float64)
+        self.qj = np.ascontiguousarray(np.broadcast_to(q0, (self.n, q0.shape[-1])), np.float64).copy()
+        self.qdj = np.zeros_like(self.qj)
+        return self
+
+    def copy_hand(self, parent):
+        """Replaced environments take their parent's hand state with the rest of it."""
+        if self.qj is not None:
+            self.qj = self.qj[parent].copy()
+            self.qdj = self.qdj[parent].copy()
 
     def warm_cache(self, cap: int):
         """Start a (cold) warm-start cache of `cap` pairs per environment."""
@@ -208,6 +233,67 @@ def step(osc: OracleScene, sim, st: State, q_traj, frame0: int, n_frames: int = 
                    _p(st.vel), _p(st.theta), _p(st.shape),
                    None if st.iters is None else _p(st.iters), _p(st.status), _p(forces), _p(diag), *cache)
     return forces, diag
+
+
+def make_pd(sim) -> PD:
+    return PD(sim.kp, sim.kd, sim.armature, sim.v_slip, sim.w_slip)
+
+
+class Obs:
+    """Observation o_t of N environments with the PD-driven hand (Sec. III-A):
+    q (N, D), pad pose (N, P, 7: position, wxyz), force (N, P, 3), slip
+    direction (N, P, 2) and flags (N, P: bit 0 translational slip, bit 1
+    rotational slip, bit 2 spin > 0)."""
+
+    def __init__(self, q, pad_pose, forces, slip_d, flags):
+        self.q, self.pad_pose, self.forces, self.slip_d, self.flags = q, pad_pose, forces, slip_d, flags
+
+    def env(self, i) -> "Obs":
+        return Obs(*(a[i:i + 1].copy() for a in (self.q, self.pad_pose, self.forces, self.slip_d, self.flags)))
+
+
+def step_pd(osc: OracleScene, sim, st: State, q_traj, frame0: int, n_frames: int = 1, last_cap: int = 0):
+    """Advance `st` (with st.qj, st.qdj) in place with the PD-driven hand.
+    Returns (Obs of the last frame, diag (N, 6)) and, with last_cap > 0, the
+    last substep's contacts (N, last_cap, 7: link, point, impulse) and counts."""
+    assert st.qj is not None, "the state has no hand joints: State.hand(q0)"
+    cfg = make_config(sim)
+    pd = make_pd(sim)
+    q = np.ascontiguousarray(q_traj, np.float64)
+    n, P = st.n, osc.n_pads
+    forces = np.zeros((n, P, 3))
+    pad_pose = np.zeros((n, P, 7))
+    slip_d = np.zeros((n, P, 2))
+    flags = np.zeros((n, P), np.int32)
+    diag = np.zeros((n, DIAG))
+    last = np.zeros((n, max(last_cap, 1), 7))
+    last_n = np.zeros(n, np.int32)
+    lib().orc_step_pd(C.byref(osc.rec), C.byref(cfg), C.byref(pd), n, _p(q), frame0, n_frames, _p(st.pose),
+                      _p(st.vel), _p(st.theta), _p(st.shape), None if st.iters is None else _p(st.iters),
+                      _p(st.status), _p(st.qj), _p(st.qdj), _p(forces), _p(pad_pose), _p(slip_d), _p(flags),
+                      _p(diag), _p(last) if last_cap > 0 else None, _p(last_n) if last_cap > 0 else None, last_cap)
+    obs = Obs(st.qj.copy(), pad_pose, forces, slip_d, flags)
+    if last_cap > 0:
+        return obs, diag, last, last_n
+    return obs, diag
+
+
+def cost_full(sim, obs: Obs, gt: Obs, status, c_sum, n_window: int):
+    """Full cost of Sec. III-C (all ten terms) of every environment against the
+    ground-truth observation `gt` (one environment); accumulates into c_sum in
+    place and returns (i*, c_mean, frame cost)."""
+    w = np.ascontiguousarray(sim.w_full, np.float64)
+    n, D = obs.q.shape
+    P = obs.forces.shape[1]
+    arr = lambda a, t=np.float64: np.ascontiguousarray(a, t)
+    o = [arr(obs.q), arr(obs.pad_pose), arr(obs.forces), arr(obs.slip_d), arr(obs.flags, np.int32)]
+    g = [arr(gt.q), arr(gt.pad_pose), arr(gt.forces), arr(gt.slip_d), arr(gt.flags, np.int32)]
+    status = arr(status, np.int32)
+    c_mean = np.zeros(n)
+    c_frame = np.zeros(n)
+    i = lib().orc_cost_full(_p(w), C.c_double(sim.tau), n, D, P, *[_p(a) for a in o], *[_p(a) for a in g],
+                            _p(status), _p(c_sum), n_window, _p(c_mean), _p(c_frame))
+    return i, c_mean, c_frame
 
 
 def cost(sim, forces, obs, status, c_sum, n_window: int):
@@ -270,6 +356,7 @@ def optimizer(opt, st: State, C_mean, seed: int, update_index: int):
     i = lib().orc_optimizer(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
                             _p(st.status), seed, update_index, _p(parent), _p(stats))
     st.drop_cache(parent != np.arange(st.n))   # replaced environments start cold
+    st.copy_hand(parent)
     return i, parent, {"mean": stats[:8].copy(), "cov": stats[8:72].reshape(8, 8).copy(),
                        "L": stats[72:136].reshape(8, 8).copy(), "k": int(stats[136]),
                        "istar": int(stats[137]), "sd": float(stats[138])}
@@ -299,6 +386,7 @@ def softmax_update(opt, st: State, C_mean, seed: int, update_index: int):
     i = lib().orc_softmax_update(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
                                  _p(st.status), seed, update_index, _p(parent), _p(stats))
     st.drop_cache(np.arange(st.n))   # every environment is replaced
+    st.copy_hand(parent)
     return i, parent, {"eta": stats[0], "wsum": stats[1], "kl": stats[2], "n_finite": int(stats[3]),
                        "cmin": stats[4], "cmax": stats[5], "iters": int(stats[6])}
 

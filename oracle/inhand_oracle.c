@@ -1216,3 +1216,426 @@ int orc_quat_log(const double *q4, double *w3) {
     w3[0] = w.x; w3[1] = w.y; w3[2] = w.z;
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* PD-driven articulated hand (the robot's joints as dynamic bodies)          */
+/* ------------------------------------------------------------------------- */
+/*
+ * The hand's state is part of s_t (Sec. III-A: joint angles of articulated
+ * bodies) and the action u_t is the desired joint position, tracked by a
+ * joint-angle PD controller (Sec. IV). Every finger joint is a revolute joint
+ * with a scalar inertia I (the joint-space mass matrix is taken diagonal; the
+ * hand's own gravity and velocity-product terms are left to the controller).
+ * The PD force is integrated implicitly over a substep of length h,
+ *     I (qd' - qd) = h [kp (u - q - h qd') - kd qd'] + (contact impulses),
+ * so without contact qd* = (I qd + h kp (u - q)) / M with M = I + h kd + h^2 kp,
+ * and an impulse lambda on the object at the link point p acts as -lambda on
+ * the link: joint a of the link's finger, proximal to (or at) the link, gets
+ * -(J_a . lambda) / M with J_a = z_a x (p - o_a) (axis z_a through o_a). The
+ * link point then moves with v_l = sum_a J_a qd_a, and the contact's
+ * effective mass gains sum_a J_a J_a^T / M. After the solve, q += h qd.
+ *
+ * Observation of each pad l at the end of a frame (o_t, Sec. III-A):
+ *   q_t; the pad's position P (link origin + the middle of its axial interval
+ *   along the capsule; the palm's top centre) and rotation R (the link's);
+ *   c (as in the kinematic step); slip: over the frame's substeps, the
+ *   normal-impulse-weighted mean of the object's tangential velocity
+ *   relative to the link at the pad's contacts, v_t, of the mean normal n,
+ *   and of the relative spin (w - w_link) . n. The pad slips translationally
+ *   when |v_t| > v_slip, with direction d = the unit 2-vector of v_t in the
+ *   pad's contact plane (e1 = the link's axis projected into the plane,
+ *   e2 = n x e1); it slips rotationally when |spin| > w_slip, r = [spin > 0].
+ */
+typedef struct {
+    double kp, kd, armature;  /* N m/rad, N m s/rad, kg m^2 */
+    double v_slip, w_slip;    /* m/s, rad/s */
+} orc_pd;
+
+typedef struct { vec3 z, o; } joint_t;
+
+/* axis and origin of every finger joint from the link poses of orc_fk:
+   joint 0 turns about the world z at the finger root (Rz(yaw + q0)), joint
+   j >= 1 by -q_j about the y axis of link j's frame, through link j's origin */
+static void joint_frames(const orc_scene *sc, const double *lp, joint_t *J) {
+    for (int f = 0; f < sc->n_fingers; f++) {
+        const double *rt = sc->finger_root + 4 * f;
+        J[4 * f].z = v3(0, 0, 1);
+        J[4 * f].o = v3(rt[0], rt[1], rt[2]);
+        for (int j = 1; j < 4; j++) {
+            pose_t P = pose_from7(lp + 7 * (1 + 4 * f + j));
+            J[4 * f + j].z = v3(-P.R.m[0][1], -P.R.m[1][1], -P.R.m[2][1]);
+            J[4 * f + j].o = P.p;
+        }
+    }
+}
+
+typedef struct {
+    contact_t c;
+    vec3 p;          /* world contact point (on the object's sphere) */
+    int j0, nj;      /* joints j0 .. j0 + nj - 1 move the contact's link */
+    vec3 J[4];       /* J_a = z_a x (p - o_a) */
+} pd_contact_t;
+
+/* link point velocity of a contact for joint velocities qd */
+static vec3 pd_link_vel(const pd_contact_t *k, const double *qd) {
+    vec3 v = v3(0, 0, 0);
+    for (int a = 0; a < k->nj; a++) v = vadd(v, vscale(k->J[a], qd[k->j0 + a]));
+    return v;
+}
+
+/* joint velocities for the current impulses: qd* - M^-1 sum_k J_k^T lambda_k */
+static void pd_joint_vel(const pd_contact_t *ct, int nc, const double *qd_star, double M, int D, double *qd) {
+    for (int a = 0; a < D; a++) qd[a] = qd_star[a];
+    for (int k = 0; k < nc; k++)
+        for (int a = 0; a < ct[k].nj; a++) qd[ct[k].j0 + a] -= vdot(ct[k].J[a], ct[k].c.lam) / M;
+}
+
+/* pad pose from link poses: position and quaternion (7 doubles) */
+static void pad_pose_of(const orc_scene *sc, int pad, const double *lp, double *out7) {
+    int l = sc->pad_link[pad];
+    pose_t P = pose_from7(lp + 7 * l);
+    vec3 c;
+    if (l == 0) {
+        c = vadd(P.p, mvmul(P.R, v3(0, 0, sc->palm_half[2])));
+    } else {
+        double s1 = sc->pad_s1[pad] < 1.0 ? sc->pad_s1[pad] : 1.0;
+        double s0 = sc->pad_s0[pad] > 0.0 ? sc->pad_s0[pad] : 0.0;
+        c = vadd(P.p, mvmul(P.R, v3(0.5 * (s0 + s1) * sc->link_len, 0, 0)));
+    }
+    out7[0] = c.x; out7[1] = c.y; out7[2] = c.z;
+    out7[3] = P.q.w; out7[4] = P.q.x; out7[5] = P.q.y; out7[6] = P.q.z;
+}
+
+/* one environment over one frame; u_all [ns+1][D] are the desired joint
+   positions at the substep boundaries */
+static void step_env_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd *pd, const double *u_all,
+                        int ns, double *pose7, double *vel6, const double *theta, int shape, int iters,
+                        int32_t *status, double *qj, double *qdj, double *forces, double *pad_pose,
+                        double *slip_d, int32_t *slip_flags, double *diag, pd_contact_t *ct, int ct_cap,
+                        double *last_ct, int32_t *last_n, int last_cap) {
+    const int n_links = 1 + 4 * sc->n_fingers, D = 4 * sc->n_fingers;
+    const int P = sc->n_pads;
+    const double h = cfg->frame_dt / ns;
+    const double m = theta[0], mu = theta[1];
+    const vec3 g = v3(cfg->gravity[0], cfg->gravity[1], cfg->gravity[2]);
+    const double M = pd->armature + h * pd->kd + h * h * pd->kp;
+    double *lp = (double *)malloc(sizeof(double) * 7 * n_links);
+    joint_t *JF = (joint_t *)malloc(sizeof(joint_t) * (D > 0 ? D : 1));
+    double *qd_star = (double *)malloc(sizeof(double) * (D > 0 ? D : 1));
+    double *qd = (double *)malloc(sizeof(double) * (D > 0 ? D : 1));
+    double *acc = (double *)calloc((size_t)P * 8, sizeof(double));   /* per pad: w, vt(3), n(3), spin */
+    for (int k = 0; k < 3 * P; k++) forces[k] = 0;
+    for (int k = 0; k < 2 * P; k++) slip_d[k] = 0;
+    for (int k = 0; k < P; k++) slip_flags[k] = 0;
+    diag[0] = 0; diag[1] = 0; diag[2] = INFINITY; diag[3] = INFINITY; diag[4] = INFINITY; diag[5] = 0;
+    if (last_n) *last_n = 0;
+
+    if (!(*status & ORC_DIVERGED)) {
+        int first = sc->shape_first[shape], cnt = sc->shape_count[shape];
+        vec3 cen = v3(0, 0, 0);
+        for (int j = 0; j < cnt; j++) {
+            const double *s = sc->spheres + 4 * (first + j);
+            cen = vadd(cen, v3(s[0], s[1], s[2]));
+        }
+        cen = vscale(cen, 1.0 / cnt);
+        double J9[9];
+        orc_unit_inertia(sc, shape, J9);
+        mat3 Jb;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) Jb.m[a][b] = J9[3 * a + b];
+        mat3 Jinv = minv(Jb);
+        vec3 x = v3(pose7[0], pose7[1], pose7[2]);
+        quat q = {pose7[3], pose7[4], pose7[5], pose7[6]};
+        vec3 v = v3(vel6[0], vel6[1], vel6[2]);
+        vec3 w = v3(vel6[3], vel6[4], vel6[5]);
+
+        for (int s = 0; s < ns; s++) {
+            const double *u1 = u_all + (size_t)(s + 1) * D;
+            orc_fk(sc, qj, lp);              /* the hand at the substep start */
+            joint_frames(sc, lp, JF);
+            for (int a = 0; a < D; a++)
+                qd_star[a] = (pd->armature * qdj[a] + h * pd->kp * (u1[a] - qj[a])) / M;
+            vec3 v_pred = vadd(v, vscale(g, h));
+            vec3 w_pred = w;
+            mat3 R = qmat(q);
+            mat3 W = mmul(mmul(R, Jinv), mtrans(R));
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) W.m[a][b] /= m;
+
+            int nc = 0;
+            for (int j = 0; j < cnt; j++) {
+                const double *sp = sc->spheres + 4 * (first + j);
+                vec3 c = vadd(x, mvmul(R, vsub(v3(sp[0], sp[1], sp[2]), cen)));
+                for (int l = 0; l < n_links; l++) {
+                    np_hit hh = link_hit(sc, l, lp, c, sp[3]);
+                    diag[1] += 1;
+                    double gap = fabs(hh.d - cfg->margin);
+                    if (gap < diag[2]) diag[2] = gap;
+                    if (!(hh.d < cfg->margin)) continue;
+                    if (hh.face_gap < diag[4]) diag[4] = hh.face_gap;
+                    double pg = pad_boundary_gap(sc, l, hh.t);
+                    if (pg < diag[3]) diag[3] = pg;
+                    if (nc < ct_cap) {
+                        pd_contact_t *k = &ct[nc];
+                        vec3 p = vsub(c, vscale(hh.n, sp[3]));
+                        k->p = p;
+                        k->c.r = vsub(p, x);
+                        k->c.n = hh.n;
+                        k->c.pad = pad_of(sc, l, hh.t);
+                        k->c.id = (l << 8) | j;
+                        k->c.lam = v3(0, 0, 0);
+                        k->c.b = contact_bias(cfg, hh.d, h);
+                        k->j0 = 0; k->nj = 0;
+                        if (l > 0) {
+                            k->j0 = 4 * ((l - 1) / 4);
+                            k->nj = (l - 1) % 4 + 1;
+                            for (int a = 0; a < k->nj; a++)
+                                k->J[a] = vcross(JF[k->j0 + a].z, vsub(p, JF[k->j0 + a].o));
+                        }
+                        /* K = (1/m) I - [r]x W [r]x + sum_a J_a J_a^T / M */
+                        mat3 S = skew(k->c.r);
+                        mat3 K = mmul(mmul(S, W), S);
+                        for (int a = 0; a < 3; a++)
+                            for (int b = 0; b < 3; b++) K.m[a][b] = ((a == b) ? 1.0 / m : 0.0) - K.m[a][b];
+                        for (int a = 0; a < k->nj; a++) {
+                            double Ja[3] = {k->J[a].x, k->J[a].y, k->J[a].z};
+                            for (int r1 = 0; r1 < 3; r1++)
+                                for (int r2 = 0; r2 < 3; r2++) K.m[r1][r2] += Ja[r1] * Ja[r2] / M;
+                        }
+                        double kn = vdot(k->c.n, mvmul(K, k->c.n));
+                        double kt = 0.5 * (K.m[0][0] + K.m[1][1] + K.m[2][2] - kn);
+                        k->c.inv_kn = 1.0 / kn;
+                        k->c.inv_kt = 1.0 / kt;
+                    }
+                    nc++;
+                }
+            }
+            diag[0] += nc;
+            if (nc > cfg->c_max) {
+                *status |= ORC_OVERFLOW;
+                nc = 0;
+            }
+
+            /* Jacobi iterations over object and joint velocities together */
+            for (int it = 0; it < iters && nc > 0; it++) {
+                vec3 F = v3(0, 0, 0), Tq = v3(0, 0, 0);
+                for (int k = 0; k < nc; k++) {
+                    F = vadd(F, ct[k].c.lam);
+                    Tq = vadd(Tq, vcross(ct[k].c.r, ct[k].c.lam));
+                }
+                vec3 vi = vadd(v_pred, vscale(F, 1.0 / m));
+                vec3 wi = vadd(w_pred, mvmul(W, Tq));
+                pd_joint_vel(ct, nc, qd_star, M, D, qd);
+                for (int k = 0; k < nc; k++) {
+                    contact_t *c = &ct[k].c;
+                    vec3 u = vsub(vadd(vi, vcross(wi, c->r)), pd_link_vel(&ct[k], qd));
+                    vec3 lproj = contact_update(c->lam, u, c->n, c->b, c->inv_kn, c->inv_kt, mu);
+                    c->lam_next = vadd(c->lam, vscale(vsub(lproj, c->lam), 1.0 / nc));
+                }
+                for (int k = 0; k < nc; k++) ct[k].c.lam = ct[k].c.lam_next;
+                diag[5] += 1;
+            }
+            vec3 F = v3(0, 0, 0), Tq = v3(0, 0, 0);
+            for (int k = 0; k < nc; k++) {
+                F = vadd(F, ct[k].c.lam);
+                Tq = vadd(Tq, vcross(ct[k].c.r, ct[k].c.lam));
+            }
+            v = vadd(v_pred, vscale(F, 1.0 / m));
+            w = vadd(w_pred, mvmul(W, Tq));
+            pd_joint_vel(ct, nc, qd_star, M, D, qd);
+
+            x = vadd(x, vscale(v, h));
+            q = qnormalize(qmul(quat_exp(vscale(w, h)), q));
+            for (int a = 0; a < D; a++) {
+                qdj[a] = qd[a];
+                qj[a] += h * qd[a];
+            }
+
+            for (int k = 0; k < nc; k++) {
+                const contact_t *c = &ct[k].c;
+                if (c->pad < 0) continue;
+                double *fp = forces + 3 * c->pad;
+                fp[0] -= c->lam.x / h; fp[1] -= c->lam.y / h; fp[2] -= c->lam.z / h;
+                double ln = vdot(c->lam, c->n);
+                if (!(ln > 0)) continue;
+                vec3 vrel = vsub(vadd(v, vcross(w, c->r)), pd_link_vel(&ct[k], qd));
+                vec3 vt = vsub(vrel, vscale(c->n, vdot(vrel, c->n)));
+                vec3 wl = v3(0, 0, 0);
+                for (int a = 0; a < ct[k].nj; a++) wl = vadd(wl, vscale(JF[ct[k].j0 + a].z, qd[ct[k].j0 + a]));
+                double spin = vdot(vsub(w, wl), c->n);
+                double *A = acc + 8 * c->pad;
+                A[0] += ln;
+                A[1] += ln * vt.x; A[2] += ln * vt.y; A[3] += ln * vt.z;
+                A[4] += ln * c->n.x; A[5] += ln * c->n.y; A[6] += ln * c->n.z;
+                A[7] += ln * spin;
+            }
+            if (last_n) {   /* the last substep's contacts: link, point, impulse */
+                int nk = nc < last_cap ? nc : last_cap;
+                for (int k = 0; k < nk; k++) {
+                    double *o = last_ct + 7 * k;
+                    o[0] = ct[k].c.id >> 8;
+                    o[1] = ct[k].p.x; o[2] = ct[k].p.y; o[3] = ct[k].p.z;
+                    o[4] = ct[k].c.lam.x; o[5] = ct[k].c.lam.y; o[6] = ct[k].c.lam.z;
+                }
+                *last_n = nk;
+            }
+        }
+        pose7[0] = x.x; pose7[1] = x.y; pose7[2] = x.z;
+        pose7[3] = q.w; pose7[4] = q.x; pose7[5] = q.y; pose7[6] = q.z;
+        vel6[0] = v.x; vel6[1] = v.y; vel6[2] = v.z; vel6[3] = w.x; vel6[4] = w.y; vel6[5] = w.z;
+        int finite = 1;
+        for (int k = 0; k < 7; k++) finite &= isfinite(pose7[k]);
+        for (int k = 0; k < 6; k++) finite &= isfinite(vel6[k]);
+        for (int a = 0; a < D; a++) finite &= isfinite(qj[a]) && isfinite(qdj[a]);
+        if (!finite) *status |= ORC_NONFINITE;
+        else if (vnorm(x) > cfg->escape_radius) *status |= ORC_ESCAPED;
+    }
+    for (int k = 0; k < 3 * P; k++) forces[k] /= ns;
+
+    /* the hand's sensors at the end of the frame */
+    orc_fk(sc, qj, lp);
+    for (int l = 0; l < P; l++) {
+        pad_pose_of(sc, l, lp, pad_pose + 7 * l);
+        const double *A = acc + 8 * l;
+        if (!(A[0] > 0)) continue;
+        vec3 vt = vscale(v3(A[1], A[2], A[3]), 1.0 / A[0]);
+        vec3 nb = v3(A[4], A[5], A[6]);
+        nb = vscale(nb, 1.0 / vnorm(nb));
+        double spin = A[7] / A[0];
+        int flags = 0;
+        if (vnorm(vt) > pd->v_slip) {
+            pose_t Lk = pose_from7(lp + 7 * sc->pad_link[l]);
+            vec3 ax = v3(Lk.R.m[0][0], Lk.R.m[1][0], Lk.R.m[2][0]);
+            vec3 e1 = vsub(ax, vscale(nb, vdot(ax, nb)));
+            e1 = vscale(e1, 1.0 / vnorm(e1));
+            vec3 e2 = vcross(nb, e1);
+            double d1 = vdot(vt, e1), d2 = vdot(vt, e2), dn = sqrt(d1 * d1 + d2 * d2);
+            slip_d[2 * l] = d1 / dn; slip_d[2 * l + 1] = d2 / dn;
+            flags |= 1;
+        }
+        if (fabs(spin) > pd->w_slip) {
+            flags |= 2;
+            if (spin > 0) flags |= 4;
+        }
+        slip_flags[l] = flags;
+    }
+    free(lp); free(JF); free(qd_star); free(qd); free(acc);
+}
+
+/*
+ * Advance N environments with the PD-driven hand over n_frames frames. qj, qdj
+ * [N][D] are the joint positions and velocities (in/out). Outputs of the last
+ * frame: forces [N][P][3], pad_pose [N][P][7], slip_d [N][P][2], slip_flags
+ * [N][P] (bit 0 translational slip, bit 1 rotational slip, bit 2 spin > 0),
+ * diag [N][ORC_DIAG]; with last_n non-NULL, the last substep's contacts
+ * last_ct [N][last_cap][7] (link, world point, impulse on the object) and
+ * their count last_n [N].
+ */
+int orc_step_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd *pd, int N, const double *q_traj,
+                int frame0, int n_frames, double *pose, double *vel, const double *theta, const int32_t *shape,
+                const int32_t *iters, int32_t *status, double *qj, double *qdj, double *forces,
+                double *pad_pose, double *slip_d, int32_t *slip_flags, double *diag, double *last_ct,
+                int32_t *last_n, int last_cap) {
+    const int D = 4 * sc->n_fingers, n_links = 1 + 4 * sc->n_fingers, ns = cfg->substeps;
+    const int P = sc->n_pads;
+    double *u_all = (double *)malloc(sizeof(double) * (D > 0 ? D : 1) * (ns + 1));
+    int cap = 1;
+    for (int s = 0; s < sc->n_shapes; s++) cap = cap > sc->shape_count[s] ? cap : sc->shape_count[s];
+    cap = cap * n_links + 1;
+    pd_contact_t *ct = (pd_contact_t *)malloc(sizeof(pd_contact_t) * cap);
+    for (int f = frame0; f < frame0 + n_frames; f++) {
+        for (int k = 0; k <= ns; k++)
+            for (int j = 0; j < D; j++) {
+                double q0 = q_traj[(size_t)f * D + j], q1 = q_traj[(size_t)(f + 1) * D + j];
+                u_all[(size_t)k * D + j] = q0 + ((double)k / ns) * (q1 - q0);
+            }
+        for (int i = 0; i < N; i++) {
+            int it = iters ? iters[i] : cfg->iters;
+            step_env_pd(sc, cfg, pd, u_all, ns, pose + 7 * (size_t)i, vel + 6 * (size_t)i,
+                        theta + 2 * (size_t)i, shape ? shape[i] : 0, it, status + i, qj + (size_t)i * D,
+                        qdj + (size_t)i * D, forces + (size_t)i * 3 * P, pad_pose + (size_t)i * 7 * P,
+                        slip_d + (size_t)i * 2 * P, slip_flags + (size_t)i * P, diag + (size_t)i * ORC_DIAG,
+                        ct, cap, last_n ? last_ct + (size_t)i * 7 * last_cap : NULL, last_n ? last_n + i : NULL,
+                        last_cap);
+        }
+    }
+    free(u_all); free(ct);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* the full cost of Sec. III-C over the PD hand's observation                 */
+/* ------------------------------------------------------------------------- */
+/*
+ * C = w1 |q - q_gt| + sum_l [ w2 |P - P_gt| + w3 |angle(R^-1 R_gt)|
+ *       + w4 (1 - alpha) + alpha (w5 | |c| - |c_gt| | + w6 angle(c, c_gt))
+ *       + w7 (1 - beta) + beta w8 angle(d, d_gt)
+ *       + w9 (1 - gamma) + gamma w10 |r - r_gt| ]
+ * alpha, beta, gamma = 1 when the two agree on contact (|c| > tau), on
+ * translational slip and on rotational slip. Angles between force vectors
+ * count only when both pads are in contact, between slip directions only
+ * when both slip, and |r - r_gt| only when both slip rotationally (the angle
+ * or direction of an absent contact or slip is undefined).
+ */
+static double vangle(vec3 a, vec3 b) { return atan2(vnorm(vcross(a, b)), vdot(a, b)); }
+
+static double frame_cost_full(const double *wt, double tau, int D, int P, const double *q_a, const double *q_b,
+                              const double *pp_a, const double *pp_b, const double *c_a, const double *c_b,
+                              const double *d_a, const double *d_b, const int32_t *f_a, const int32_t *f_b) {
+    double dq = 0;
+    for (int j = 0; j < D; j++) dq += (q_a[j] - q_b[j]) * (q_a[j] - q_b[j]);
+    double cost = wt[0] * sqrt(dq);
+    for (int l = 0; l < P; l++) {
+        const double *pa = pp_a + 7 * l, *pb = pp_b + 7 * l;
+        cost += wt[1] * vnorm(v3(pa[0] - pb[0], pa[1] - pb[1], pa[2] - pb[2]));
+        quat qa = {pa[3], pa[4], pa[5], pa[6]}, qb = {pb[3], pb[4], pb[5], pb[6]};
+        quat rel = qmul(qconj(qa), qb);
+        cost += wt[2] * 2.0 * atan2(vnorm(v3(rel.x, rel.y, rel.z)), fabs(rel.w));
+        vec3 ca = v3(c_a[3 * l], c_a[3 * l + 1], c_a[3 * l + 2]), cb = v3(c_b[3 * l], c_b[3 * l + 1], c_b[3 * l + 2]);
+        double ma = vnorm(ca), mb = vnorm(cb);
+        int in_a = ma > tau, in_b = mb > tau;
+        if (in_a != in_b) {
+            cost += wt[3];
+        } else {
+            cost += wt[4] * fabs(ma - mb);
+            if (in_a) cost += wt[5] * vangle(ca, cb);
+        }
+        int ta = f_a[l] & 1, tb = f_b[l] & 1;
+        if (ta != tb) {
+            cost += wt[6];
+        } else if (ta) {
+            const double *da = d_a + 2 * l, *db = d_b + 2 * l;
+            cost += wt[7] * atan2(fabs(da[0] * db[1] - da[1] * db[0]), da[0] * db[0] + da[1] * db[1]);
+        }
+        int ra = (f_a[l] >> 1) & 1, rb = (f_b[l] >> 1) & 1;
+        if (ra != rb) {
+            cost += wt[8];
+        } else if (ra) {
+            cost += wt[9] * fabs((double)((f_a[l] >> 2) & 1) - (double)((f_b[l] >> 2) & 1));
+        }
+    }
+    return cost;
+}
+
+/* running window mean and argmin of the full cost, as orc_cost */
+int orc_cost_full(const double *wt, double tau, int N, int D, int P, const double *qj, const double *pad_pose,
+                  const double *forces, const double *slip_d, const int32_t *slip_flags, const double *g_q,
+                  const double *g_pose, const double *g_forces, const double *g_d, const int32_t *g_flags,
+                  const int32_t *status, double *c_sum, int n_window, double *c_mean, double *cost_out) {
+    int best = 0;
+    double best_c = INFINITY;
+    for (int i = 0; i < N; i++) {
+        double c = (status[i] & ORC_DIVERGED)
+                       ? INFINITY
+                       : frame_cost_full(wt, tau, D, P, qj + (size_t)D * i, g_q, pad_pose + (size_t)7 * P * i, g_pose,
+                                         forces + (size_t)3 * P * i, g_forces, slip_d + (size_t)2 * P * i, g_d,
+                                         slip_flags + (size_t)P * i, g_flags);
+        if (cost_out) cost_out[i] = c;
+        c_sum[i] += c;
+        double cm = c_sum[i] / n_window;
+        if (c_mean) c_mean[i] = cm;
+        if (isnan(cm)) cm = INFINITY;
+        if (cm < best_c || (i == 0)) { best_c = cm; best = i; }
+    }
+    return best;
+}

@@ -198,6 +198,18 @@ class SimConfig:
     c_max: int = 128             # contacts per environment per substep
     escape_radius: float = 0.3   # object farther than this from the palm = diverged
     warm_start: bool = False     # start each contact's impulse from its pair's last substep
+    # the hand: "kinematic" (joints follow u_t exactly) or "pd" (joint-angle PD
+    # controller toward u_t, joints pushed back by the contacts)
+    hand: str = "kinematic"
+    kp: float = 2.0              # PD stiffness (N m/rad)
+    kd: float = 0.05             # PD damping (N m s/rad)
+    armature: float = 1e-3       # joint inertia (kg m^2)
+    v_slip: float = 0.005        # translational slip threshold (m/s)
+    w_slip: float = 0.1          # rotational slip threshold (rad/s)
+    # weights w1..w10 of the full cost (PD hand): q, pad position, pad rotation,
+    # contact mismatch, force magnitude, force angle, slip mismatch, slip angle,
+    # rotational-slip mismatch, rotational-slip direction
+    w_full: tuple = (10.0, 100.0, 10.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
 
 
 @dataclasses.dataclass
