@@ -47,10 +47,11 @@ FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
 # DRAM traffic of one step_kernel launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu capture summarised in
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
-# sources (step.cu, contact.cuh) whose hash is recorded with it; reported as
+# sources (step.cu, step_kernel.cuh, contact.cuh) whose hash is recorded with it; reported as
 # null once they change.
-STEP_TRAFFIC = {"bytes_per_launch": 202496, "sources_sha256": "7c0830992f7e662e4ef9ee649d974de8e49c5df0c31f0dfce629375ea6325639"}
-STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/contact.cuh"]
+STEP_TRAFFIC = {"bytes_per_launch": 229120, "sources_sha256": "926988f1ffaca0be836ce2282b8815d3aff84e2908883d83e06a3ad64a199e43"}
+STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/step_kernel.cuh",
+                "paper_2002_12160_gb300/csrc/contact.cuh"]
 
 
 def step_sources_sha():
@@ -84,8 +85,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the adjoint throughput and the refinement-vs-plain tracking study")
-    p.add_argument("--part", choices=["all", "adjoint", "optimizers"], default="all",
-                   help="adjoint / optimizers: only that block (profiling, studies)")
+    p.add_argument("--part", choices=["all", "adjoint", "optimizers", "warm"], default="all",
+                   help="adjoint / optimizers / warm: only that block (profiling, studies)")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     p.add_argument("--sweep", default=None,
                    help="comma-separated N values: also time the workload at each N (tracking frames/s)")
@@ -465,6 +466,75 @@ def optimizer_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=10
     return {"n_envs": n_envs, "frames": frames, "seeds": list(seeds), **out}
 
 
+def warm_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, n_conv=256, conv_frames=60):
+    """The warm-started solver (each contact starts from its (link, sphere)
+    pair's final impulse of the previous substep):
+    - convergence at a fixed iteration count I: pad forces of n_conv sampled
+      cylinder states over conv_frames frames against a 200-iteration solve
+      from the same states (relative L1 error over all pads and frames);
+    - tracking (median ADD over seeded trajectories, mm) and window time with
+      the elite optimizer at I = 5 and 10, warm and cold, the ground truth
+      always the default 20-iteration cold solve."""
+    import dataclasses
+    import torch
+    from paper_2002_12160_gb300 import inhand, tracking, workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    conv = {}
+    wl = W.make_workload("tracking_cyl64", n_envs=n_conv, frames=conv_frames)
+    q = torch.from_numpy(wl.q_traj[:conv_frames + 1]).contiguous().to(dev)
+
+    def run(iters, warm):
+        w2 = dataclasses.replace(wl, sim=dataclasses.replace(wl.sim, iters=iters, warm_start=warm))
+        sim = inhand.make_sim(w2, n_envs=n_conv, max_frames=conv_frames)
+        sim.sim_set_commands(0, q)
+        sim.sim_sample_initial(wl.nominal_pose, wl.init.sigma_p, wl.init.sigma_r, wl.init.m_range, wl.init.mu_range)
+        out = []
+        for f in range(conv_frames):
+            sim.sim_step(f, 1)
+            out.append(sim.sim_read_sensors()[0].clone())
+        sim.close()
+        return torch.stack(out).double()
+
+    ref = run(200, False)
+    scale = ref.abs().sum().item()
+    for iters in (1, 2, 5, 10, 20):
+        conv[str(iters)] = {mode: (run(iters, mode == "warm") - ref).abs().sum().item() / scale
+                            for mode in ("cold", "warm")}
+    track = {}
+    for name in ["tracking_cyl64", "tracking_box27"]:
+        res = {}
+        for label, iters, warm in [("cold_i20", 20, False), ("cold_i10", 10, False), ("warm_i10", 10, True),
+                                   ("cold_i5", 5, False), ("warm_i5", 5, True)]:
+            adds, times = [], []
+            for seed in seeds:
+                wl_t = W.make_workload(name, n_envs=n_envs, frames=frames, seed=seed)
+                gt_sim = wl_t.sim
+                wl_t.sim = dataclasses.replace(wl_t.sim, iters=iters, warm_start=warm)
+                wl_t.iters[:] = iters
+                tr = tracking.Tracker(wl_t, n_envs=n_envs, gt_sim=gt_sim)
+                tr.prepare()
+                nw = frames // tr.T
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                tr.window(0)
+                torch.cuda.synchronize()
+                e0.record()
+                for w in range(1, nw):
+                    tr.window(w)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / (nw - 1))
+                adds.append(tr.add_mm(nw * tr.T))
+                tr.close()
+            res[label] = {"add_mm_median": statistics.median(adds), "ms_per_window": statistics.median(times),
+                          "add_mm": adds}
+        track[name] = res
+    torch.cuda.empty_cache()
+    return {"convergence": {"what": f"relative L1 pad-force error vs a 200-iteration solve, {n_conv} sampled "
+                                    f"cylinder states, {conv_frames} frames", "by_iters": conv},
+            "tracking": {"n_envs": n_envs, "frames": frames, "seeds": list(seeds), **track}}
+
+
 def flops_of(work, wl):
     return (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * max(len(s) for s in wl.scene.shapes)) +
             work["pairs"] * FLOP_PER_PAIR + work["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
@@ -526,6 +596,7 @@ def run_ours(args, rank, world, local):
                            "forward_env_steps_per_s": value / world, **adj}
         line["refinement"] = refine_study(local)
         line["optimizers"] = optimizer_study(local)
+        line["warm_start"] = warm_study(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
@@ -542,6 +613,10 @@ def main():
     if args.part == "optimizers":
         if rank == 0:
             print(json.dumps({"part": "optimizers", "optimizers": optimizer_study(local)}), flush=True)
+        return
+    if args.part == "warm":
+        if rank == 0:
+            print(json.dumps({"part": "warm", "warm_start": warm_study(local)}), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

@@ -99,6 +99,14 @@ typedef struct {
     float w_contact;       /* weight of each on/off mismatch */
     int32_t c_max;         /* contacts per env per substep, <= IH_MAX_CONTACTS */
     float escape_radius;   /* |x| beyond this marks the env escaped */
+    int32_t warm_start;    /* 0: every substep's solve starts from zero impulses;
+                              1: each contact starts from the final impulse of the
+                              same (link, sphere) pair in the environment's
+                              previous substep (cache per environment, carried
+                              across launches; emptied by sim_sample_initial,
+                              sim_set_state and when the optimizer replaces the
+                              environment). sim_adjoint and sim_refine_elites
+                              refuse a warm-started handle (IH_ERR_ARG). */
 } ih_config;
 
 /* Optimizer kinds (Sec. III-D). */
@@ -171,6 +179,15 @@ ih_status sim_set_state(ih_sim *sim, const float *pose, const float *vel, const 
 
 /* Copy the state out to device arrays; any pointer may be NULL. */
 ih_status sim_get_state(ih_sim *sim, float *pose, float *vel, float *params, int32_t *env_status);
+
+/* Copy the warm-start cache out (a handle created with warm_start = 1; any
+ * other handle gives IH_ERR_ARG) to device arrays: count int32[N], the number
+ * of contacts of each environment's last stepped substep, and entries
+ * float[N][c_max][4], per contact in pair order its final impulse (x, y, z, in
+ * N s) and, in the fourth float, the bits of its int32 pair id
+ * (link << 8 | sphere). Entries past count are unspecified. entries must be
+ * 16-byte aligned. Asynchronous on the handle's stream. */
+ih_status sim_get_warm_cache(ih_sim *sim, int32_t *count, float *entries);
 
 /* Advance every environment over frames [frame0, frame0 + n_frames) with the
  * commands set by sim_set_commands (Algorithm 1, "step simulation"). Per

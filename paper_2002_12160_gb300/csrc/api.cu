@@ -67,6 +67,9 @@ struct ih_sim {
     float4 *sn_pose = nullptr, *sn_vel = nullptr;
     float2 *sn_params = nullptr;
     int *sn_status = nullptr;
+    // warm-started solver: per environment the last substep's contacts (impulse, pair id)
+    float4 *cache = nullptr;
+    int *cache_n = nullptr;
     // captured tracking window (replayed by sim_track_window)
     cudaGraphExec_t win_exec = nullptr;
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
@@ -193,7 +196,8 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     if (cfg->n_envs < 1 || cfg->max_frames < 1 || cfg->substeps < 1 || cfg->iters < 0 ||
         !finite_pos(cfg->frame_dt) || !(cfg->margin >= 0.0f) || !(cfg->beta >= 0.0f) ||
         !(cfg->slop >= 0.0f) || !(cfg->vmax >= 0.0f) || !(cfg->tau >= 0.0f) ||
-        cfg->c_max < 1 || cfg->c_max > IH_MAX_CONTACTS || !finite_pos(cfg->escape_radius))
+        cfg->c_max < 1 || cfg->c_max > IH_MAX_CONTACTS || !finite_pos(cfg->escape_radius) ||
+        (cfg->warm_start != 0 && cfg->warm_start != 1))
         return fail(nullptr, IH_ERR_ARG, "invalid config");
 
     ih_sim *s = new ih_sim();
@@ -212,6 +216,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     d.gx = cfg->gravity[0]; d.gy = cfg->gravity[1]; d.gz = cfg->gravity[2];
     d.tau = cfg->tau; d.w_force = cfg->w_force; d.w_contact = cfg->w_contact;
     d.c_max = cfg->c_max; d.escape_radius = cfg->escape_radius;
+    d.warm = cfg->warm_start;
     s->variant = default_variant(cfg->n_envs, cfg->c_max);
     const int N = cfg->n_envs, P = sc->n_pads, F = sc->n_fingers;
 
@@ -242,6 +247,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
     A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
     A(dalloc(s, &s->moments, (size_t)opt_blocks(N) * kMoments)); A(dalloc(s, &s->misc, 80));
+    if (d.warm) { A(dalloc(s, &s->cache, (size_t)N * cfg->c_max)); A(dalloc(s, &s->cache_n, N)); }
     if (e != cudaSuccess) {
         ih_status st = cuda_fail(nullptr, e, "sim_create allocation");
         sim_destroy(s);
@@ -277,6 +283,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemsetAsync(s->argmin, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->done, 0, sizeof(unsigned int), st));
     A(cudaMemsetAsync(s->work, 0, 6 * sizeof(unsigned long long), st));
+    if (d.warm) A(cudaMemsetAsync(s->cache_n, 0, (size_t)N * sizeof(int), st));
     A(launch_shape_setup(s->spheres_raw, s->spheres, s->shape_first, s->shape_count, sc->n_shapes,
                          s->shape_jinv, s->shape_bound, s->cl_first, s->clusters, st));
     A(launch_lpt_order(N, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, st));
@@ -288,7 +295,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     }
     s->frame_ready.assign(cfg->max_frames, 0);
     s->step_grid = grid_for(s->variant, N);
-    e = step_prepare(s->variant, s->s_max, s->cfg.c_max);
+    e = step_prepare(s->variant, s->s_max, s->cfg.c_max, s->dcfg.warm != 0);
     if (e != cudaSuccess) {
         ih_status r = cuda_fail(nullptr, e, "sim_create step setup");
         sim_destroy(s);
@@ -343,6 +350,7 @@ ih_status sim_sample_initial(ih_sim *s, const float *nominal, float sigma_p, flo
                                           s->seed, s->pose, s->vel, s->params, s->status, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->c_sum, 0, s->cfg.n_envs * sizeof(double), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->n_window, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess && s->cache_n) e = cudaMemsetAsync(s->cache_n, 0, s->cfg.n_envs * sizeof(int), s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "sample_initial");
     s->window_frames = 0;
     s->ws_valid = false;
@@ -359,6 +367,7 @@ ih_status sim_set_state(ih_sim *s, const float *pose, const float *vel, const fl
                                      s->pose, s->vel, s->params, s->shape, s->iters, s->status, s->stream);
     if (e == cudaSuccess && (shape_id || iters))
         e = launch_lpt_order(s->cfg.n_envs, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, s->stream);
+    if (e == cudaSuccess && s->cache_n) e = cudaMemsetAsync(s->cache_n, 0, s->cfg.n_envs * sizeof(int), s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
     s->ws_valid = false;
     return IH_OK;
@@ -379,6 +388,18 @@ ih_status sim_get_state(ih_sim *s, float *pose, float *vel, float *params, int32
     return IH_OK;
 }
 
+ih_status sim_get_warm_cache(ih_sim *s, int32_t *count, float *entries) {
+    if (!s) return IH_ERR_ARG;
+    if (!s->cache) return fail(s, IH_ERR_ARG, "the handle was created without warm_start");
+    if (!count || !entries || !aligned16(entries)) return fail(s, IH_ERR_ARG, "count and 16-byte aligned entries are required");
+    const size_t N = s->cfg.n_envs;
+    cudaError_t e = cudaMemcpyAsync(count, s->cache_n, N * sizeof(int), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(entries, s->cache, N * s->cfg.c_max * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "get_warm_cache");
+    return IH_OK;
+}
+
 ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     if (!s) return IH_ERR_ARG;
     if (n_frames < 1 || frame0 < 0 || frame0 + n_frames > s->cfg.max_frames)
@@ -395,6 +416,7 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     a.argmin_state = s->argmin; a.argmin_out = nullptr; a.est_pose_out = nullptr;
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
     a.cm_frames = nullptr; a.pose_frames = nullptr;
+    a.cache = s->cache; a.cache_n = s->cache_n;
     cudaError_t e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->stepped = true;
@@ -413,6 +435,7 @@ StepArgs scored_args(ih_sim *s, int frame, const float *obs, double *cost_mean, 
     a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est;
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
     a.cm_frames = nullptr; a.pose_frames = nullptr;
+    a.cache = s->cache; a.cache_n = s->cache_n;
     return a;
 }
 
@@ -431,6 +454,7 @@ OptArgs opt_args(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int
     a.sigma_theta[0] = opt->sigma_theta[0]; a.sigma_theta[1] = opt->sigma_theta[1];
     a.explore_velocity = opt->explore_velocity;
     a.sn_pose = s->sn_pose; a.sn_vel = s->sn_vel; a.sn_params = s->sn_params; a.sn_status = s->sn_status;
+    a.cache_n = s->cache_n;
     return a;
 }
 
@@ -670,7 +694,7 @@ ih_status sim_set_variant(ih_sim *s, int32_t tpe, int32_t cpl) {
     if (!step_variant_supported(v)) return fail(s, IH_ERR_ARG, "unsupported step shape %d x %d", tpe, cpl);
     if (step_variant_max_contacts(v) < s->cfg.c_max)
         return fail(s, IH_ERR_ARG, "shape %d x %d holds fewer than c_max = %d contacts", tpe, cpl, s->cfg.c_max);
-    cudaError_t e = step_prepare(v, s->s_max, s->cfg.c_max);
+    cudaError_t e = step_prepare(v, s->s_max, s->cfg.c_max, s->dcfg.warm != 0);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_variant");
     s->variant = v;
     s->step_grid = grid_for(v, s->cfg.n_envs);
@@ -692,9 +716,12 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
         if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
     const size_t N = s->cfg.n_envs, P = s->n_pads;
     // scratch copy of everything a step writes
-    void *bp = nullptr, *bv = nullptr, *bs = nullptr, *bf = nullptr;
+    void *bp = nullptr, *bv = nullptr, *bs = nullptr, *bf = nullptr, *bc = nullptr, *bn = nullptr;
     unsigned long long wsave[6];
+    const size_t cache_bytes = s->cache ? N * s->cfg.c_max * sizeof(float4) : 0;
     cudaError_t e = cudaMalloc(&bp, N * 2 * sizeof(float4));
+    if (e == cudaSuccess && s->cache) e = cudaMalloc(&bc, cache_bytes);
+    if (e == cudaSuccess && s->cache) e = cudaMalloc(&bn, N * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&bv, N * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&bs, N * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&bf, N * P * 3 * sizeof(float));
@@ -705,6 +732,10 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
         cudaMemcpyAsync(bs, s->status, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(bf, s->forces, N * P * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(wsave, s->work, sizeof wsave, cudaMemcpyDeviceToHost, st);
+        if (bc) {
+            cudaMemcpyAsync(bc, s->cache, cache_bytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(bn, s->cache_n, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+        }
     };
     auto restore = [&]() {
         cudaMemcpyAsync(s->pose, bp, N * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, st);
@@ -712,6 +743,10 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
         cudaMemcpyAsync(s->status, bs, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(s->forces, bf, N * P * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(s->work, wsave, sizeof wsave, cudaMemcpyHostToDevice, st);
+        if (bc) {
+            cudaMemcpyAsync(s->cache, bc, cache_bytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(s->cache_n, bn, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+        }
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -724,7 +759,7 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     if (e == cudaSuccess) { save(); e = cudaStreamSynchronize(st); }
     for (int k = 0; k < nv && e == cudaSuccess; ++k) {
         float ms = NAN;
-        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && step_prepare(cand[k], s->s_max, s->cfg.c_max) == cudaSuccess) {
+        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && step_prepare(cand[k], s->s_max, s->cfg.c_max, s->dcfg.warm != 0) == cudaSuccess) {
             s->variant = cand[k];
             s->step_grid = grid_for(cand[k], (int)N);
             ih_status r = sim_step(s, frame0, n_frames);   // warm-up (and first-use setup)
@@ -747,6 +782,8 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(bp); cudaFree(bv); cudaFree(bs); cudaFree(bf);
+    if (bc) cudaFree(bc);
+    if (bn) cudaFree(bn);
     if (e != cudaSuccess) {
         s->variant = keep;
         s->step_grid = grid_for(keep, (int)N);
@@ -814,6 +851,7 @@ ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkp
                       const int32_t *envs, int32_t n, float beta, float width, double *cost, float *grad,
                       float *grad_quat) {
     if (!s) return IH_ERR_ARG;
+    if (s->dcfg.warm) return fail(s, IH_ERR_ARG, "the adjoint differentiates the cold-started solver only");
     if (!obs || !grad) return fail(s, IH_ERR_ARG, "obs and grad are required");
     ih_status r = check_horizon(s, frame0, horizon);
     if (r != IH_OK) return r;
@@ -876,6 +914,7 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
                             int32_t steps, float step_scale, float beta, float width, int32_t *elite_out,
                             double *cost_before, double *cost_after) {
     if (!s) return IH_ERR_ARG;
+    if (s->dcfg.warm) return fail(s, IH_ERR_ARG, "the adjoint differentiates the cold-started solver only");
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     ih_status r = check_opt(s, opt);
     if (r != IH_OK) return r;

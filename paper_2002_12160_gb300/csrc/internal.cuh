@@ -39,6 +39,7 @@ struct DevConfig {
     float tau, w_force, w_contact;
     int c_max;
     float escape_radius;
+    int warm;           // warm-started solver (impulse cache per environment)
 };
 
 // ---------------------------------------------------------------- FP32 math
@@ -223,6 +224,9 @@ struct StepArgs {
     // launch_window_argmin takes each frame's argmin afterwards
     double *cm_frames;        // [n_frames][N]
     float4 *pose_frames;      // [n_frames][N][2]
+    // warm start (cfg.warm): per environment the last substep's contacts
+    float4 *cache;            // [N][c_max]: final impulse xyz, pair id (link << 8 | sphere) in w
+    int *cache_n;             // [N]
 };
 struct StepVariant {
     int group;        // lanes per environment
@@ -232,7 +236,7 @@ struct StepVariant {
 cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s);
 int step_variant_max_contacts(const StepVariant &v);
 bool step_variant_supported(const StepVariant &v);
-size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max);
+size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max, bool warm);
 int step_variant_list(StepVariant *out, int cap);
 
 struct CostArgs {
@@ -298,6 +302,7 @@ struct OptArgs {
     float4 *sn_pose, *sn_vel; // [N][2] state before the update
     float2 *sn_params;        // [N]
     int *sn_status;           // [N]
+    int *cache_n;             // warm-start cache counts, or null: a replaced environment starts cold
 };
 int opt_blocks(int N);
 
@@ -358,7 +363,11 @@ size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max,
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
-cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max);
+cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max, bool warm);
+// the warm-started instances (step_warm.cu)
+size_t step_smem_bytes_warm(const StepVariant &v, int s_max, int c_max);
+cudaError_t step_prepare_warm(const StepVariant &v, int s_max, int c_max);
+cudaError_t launch_step_warm(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
 // the optimizer's first stage alone: elite flags, ranks and elite_env (index order), i*
 cudaError_t launch_select(const OptArgs &a, cudaStream_t s);

@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
         if (sub == 0 && a.parent_out) a.parent_out[i] = i;
         return;
     }
+    if (sub == 0 && a.cache_n) a.cache_n[i] = 0;   // replaced: its solver starts cold
     const bool ok = a.misc[M_OK] != 0.0;
     int par = 0;
     if (sub == 0) {
@@ -725,6 +726,7 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) soft_apply_kernel(con
     if (sub == 0) {
         if (i == 0) *a.n_window = 0;
         a.c_sum[i] = 0.0;
+        if (a.cache_n) a.cache_n[i] = 0;   // replaced: its solver starts cold
         const uint4 uw = rng_words(a.seed, 3, upd, (uint32_t)i, 0);
         const double pos = unit53(uw.x, uw.y) * a.misc[M_WSUM];
         int lo = 0, hi = N - 1;   // first j with pos < CDF_j

@@ -40,7 +40,8 @@ class IHConfig(C.Structure):
                 ("substeps", C.c_int32), ("iters", C.c_int32), ("margin", C.c_float),
                 ("beta", C.c_float), ("slop", C.c_float), ("vmax", C.c_float),
                 ("gravity", C.c_float * 3), ("tau", C.c_float), ("w_force", C.c_float),
-                ("w_contact", C.c_float), ("c_max", C.c_int32), ("escape_radius", C.c_float)]
+                ("w_contact", C.c_float), ("c_max", C.c_int32), ("escape_radius", C.c_float),
+                ("warm_start", C.c_int32)]
 
 
 class IHOptConfig(C.Structure):
@@ -59,7 +60,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
            "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
-           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory"]
+           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_get_warm_cache"]
 
 
 def lib() -> C.CDLL:
@@ -79,6 +80,7 @@ def lib() -> C.CDLL:
             "sim_sample_initial": [P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
             "sim_set_state": [P, P, P, P, P, P],
             "sim_get_state": [P, P, P, P, P],
+            "sim_get_warm_cache": [P, P, P],
             "sim_step": [P, I, I],
             "sim_read_sensors": [P, P, P],
             "cost_eval": [P, P, P, P, P],
@@ -155,11 +157,14 @@ class Sim:
         self._cfg = IHConfig(n_envs, max_frames, sim_cfg.frame_dt, sim_cfg.substeps, sim_cfg.iters,
                              sim_cfg.margin, sim_cfg.beta, sim_cfg.slop, sim_cfg.vmax,
                              (C.c_float * 3)(*sim_cfg.gravity), sim_cfg.tau, sim_cfg.w_force,
-                             sim_cfg.w_contact, sim_cfg.c_max, sim_cfg.escape_radius)
+                             sim_cfg.w_contact, sim_cfg.c_max, sim_cfg.escape_radius,
+                             int(bool(sim_cfg.warm_start)))
         self.n = n_envs
         self.n_pads = scene.n_pads
         self.n_joints = scene.n_joints
         self.max_frames = max_frames
+        self.c_max = sim_cfg.c_max
+        self.warm_start = bool(sim_cfg.warm_start)
         h = C.c_void_p()
         rc = L.sim_create(C.byref(self._scene), C.byref(self._cfg), seed, _stream(), C.byref(h))
         if rc != IH_OK:
@@ -214,6 +219,15 @@ class Sim:
 
     def sim_step(self, frame0: int, n_frames: int = 1):
         self._call("sim_step", frame0, n_frames)
+
+    def sim_get_warm_cache(self):
+        """(count int32[N], impulse float32[N, c_max, 3], pair id int32[N, c_max]) of a
+        warm-started handle: each environment's last substep's contacts."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        count = torch.empty((self.n,), dtype=torch.int32, device=dev)
+        ent = torch.empty((self.n, self.c_max, 4), dtype=torch.float32, device=dev)
+        self._call("sim_get_warm_cache", _ptr(count), _ptr(ent))
+        return count, ent[..., :3], ent[..., 3].contiguous().view(torch.int32)
 
     def sim_read_sensors(self, forces=None, status=None):
         dev = torch.device("cuda", torch.cuda.current_device())

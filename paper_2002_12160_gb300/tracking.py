@@ -10,6 +10,7 @@ orders the calls and moves buffers.
 """
 from __future__ import annotations
 
+import dataclasses
 import time
 
 import numpy as np
@@ -19,13 +20,17 @@ from . import inhand, workloads as W
 
 
 class Tracker:
-    def __init__(self, wl: W.Workload, seed: int | None = None, n_envs: int | None = None):
+    def __init__(self, wl: W.Workload, seed: int | None = None, n_envs: int | None = None,
+                 gt_sim: W.SimConfig | None = None):
+        """`gt_sim`: the ground truth's solver settings when they differ from the
+        tracking environments' (e.g. a converged solve behind a cheaper one)."""
         self.wl = wl
         self.T = wl.opt.window
         self.seed = wl.seed if seed is None else seed
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.sim = inhand.make_sim(wl, n_envs=n_envs, max_frames=wl.frames, seed=self.seed)
-        self.gt = inhand.make_sim(wl, n_envs=1, max_frames=wl.frames, seed=self.seed + 1)
+        gt_wl = wl if gt_sim is None else dataclasses.replace(wl, sim=gt_sim)
+        self.gt = inhand.make_sim(gt_wl, n_envs=1, max_frames=wl.frames, seed=self.seed + 1)
         self.n = self.sim.n
         P = wl.scene.n_pads
         self.obs = torch.zeros((wl.frames, P, 3), dtype=torch.float32, device=self.dev)

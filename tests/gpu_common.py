@@ -77,12 +77,26 @@ def start(wl, n=None, frames=None):
     return sim
 
 
+def oracle_cache(sim, st):
+    """Put the GPU's warm-start cache, widened exactly to FP64, onto an oracle State."""
+    n, lam, ids = (t.cpu().numpy() for t in sim.sim_get_warm_cache())
+    st.cache_n = n.astype(np.int32).copy()
+    st.cache_id = ids.astype(np.int32).copy()
+    st.cache_lam = lam.astype(np.float64).copy()
+    return st
+
+
 def compare_frame(wl, sim, frame, envs=None):
-    """Step the GPU one frame and the oracle one frame from the GPU's state; return a report."""
+    """Step the GPU one frame and the oracle one frame from the GPU's state; return a report.
+    A warm-started handle hands its impulse cache to the oracle too, and the
+    report carries both caches after the frame."""
     nn = sim.n
     shape = wl.shape_id[:nn].astype(np.int32)
     iters = wl.iters[:nn].astype(np.int32)
     st = oracle_state(sim.sim_get_state(), shape, iters)
+    warm = getattr(sim, "warm_start", False)
+    if warm:
+        oracle_cache(sim, st)
     if envs is not None:
         st = st.subset(envs)
     osc = O.OracleScene(scene32(wl.scene))
@@ -105,9 +119,17 @@ def compare_frame(wl, sim, frame, envs=None):
     fe = np.linalg.norm(forces - f_or, axis=2)
     fmag = np.linalg.norm(f_or, axis=2)
     f_bad = fe > FORCE_REL * fmag + FORCE_ABS
-    return {"ok": ok, "pos_err": pos_err, "rot_err": rot_err, "force_bad": f_bad, "force_err": fe,
-            "status_gpu": status, "status_or": st.status, "contacts_or": diag[:, 0].sum(),
-            "work": work, "diag": diag, "vel_err": np.abs(g.vel - st.vel).max(axis=1)}
+    rep = {"ok": ok, "pos_err": pos_err, "rot_err": rot_err, "force_bad": f_bad, "force_err": fe,
+           "status_gpu": status, "status_or": st.status, "contacts_or": diag[:, 0].sum(),
+           "work": work, "diag": diag, "vel_err": np.abs(g.vel - st.vel).max(axis=1)}
+    if warm:
+        n, lam, ids = (t.cpu().numpy() for t in sim.sim_get_warm_cache())
+        if envs is not None:
+            n, lam, ids = n[envs], lam[envs], ids[envs]
+        rep["cache_gpu"] = (n, ids, lam.astype(np.float64))
+        rep["cache_or"] = (st.cache_n, st.cache_id, st.cache_lam)
+        rep["h"] = wl.sim.frame_dt / wl.sim.substeps
+    return rep
 
 
 def assert_report(rep, min_ok_frac=0.75):
@@ -117,3 +139,17 @@ def assert_report(rep, min_ok_frac=0.75):
     assert rep["pos_err"][ok].max(initial=0) < POS_TOL, rep["pos_err"][ok].max()
     assert rep["rot_err"][ok].max(initial=0) < ROT_TOL, rep["rot_err"][ok].max()
     assert not rep["force_bad"][ok].any(), rep["force_err"][ok].max()
+    if "cache_gpu" in rep:
+        # the caches hold the same contact pairs (the GPU's in (link, sphere)
+        # order, the oracle's in its enumeration order) with the same final
+        # impulses (compared as forces lambda / h, pad-force tolerance)
+        (ng, ig, lg), (no, io, lo) = rep["cache_gpu"], rep["cache_or"]
+        np.testing.assert_array_equal(ng[ok], no[ok])
+        for i in np.nonzero(ok)[0]:
+            k = int(no[i])
+            sg, so = np.argsort(ig[i, :k]), np.argsort(io[i, :k])
+            np.testing.assert_array_equal(ig[i, :k][sg], io[i, :k][so])
+            assert np.all(np.diff(ig[i, :k]) > 0)
+            fg, fo = lg[i, :k][sg] / rep["h"], lo[i, :k][so] / rep["h"]
+            err = np.linalg.norm(fg - fo, axis=1)
+            assert np.all(err <= FORCE_REL * np.linalg.norm(fo, axis=1) + FORCE_ABS), (i, err.max())
