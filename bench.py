@@ -85,8 +85,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the adjoint throughput and the refinement-vs-plain tracking study")
-    p.add_argument("--part", choices=["all", "adjoint", "optimizers", "warm"], default="all",
-                   help="adjoint / optimizers / warm: only that block (profiling, studies)")
+    p.add_argument("--part", choices=["all", "adjoint", "optimizers", "warm", "pd", "pd_speed"], default="all",
+                   help="adjoint / optimizers / warm / pd (pd_speed: its throughput only): only that block (profiling, studies)")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     p.add_argument("--sweep", default=None,
                    help="comma-separated N values: also time the workload at each N (tracking frames/s)")
@@ -466,72 +466,205 @@ def optimizer_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=10
     return {"n_envs": n_envs, "frames": frames, "seeds": list(seeds), **out}
 
 
-def warm_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, n_conv=256, conv_frames=60):
+def warm_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, n_conv=256, hold_at=40,
+               hold_frames=90):
     """The warm-started solver (each contact starts from its (link, sphere)
     pair's final impulse of the previous substep):
-    - convergence at a fixed iteration count I: pad forces of n_conv sampled
-      cylinder states over conv_frames frames against a 200-iteration solve
-      from the same states (relative L1 error over all pads and frames);
+    - convergence at a fixed iteration count I, in a held grasp (the command
+      frozen at frame `hold_at` for `hold_frames` frames, n_conv sampled
+      cylinder states): the object's residual speed (creep of an unconverged
+      solve) and its distance from where a 200-iteration solve holds it;
     - tracking (median ADD over seeded trajectories, mm) and window time with
-      the elite optimizer at I = 5 and 10, warm and cold, the ground truth
-      always the default 20-iteration cold solve."""
+      the elite optimizer at I = 5, 10 and 20, warm and cold, against a ground
+      truth simulated with a converged (200-iteration) solve."""
     import dataclasses
     import torch
     from paper_2002_12160_gb300 import inhand, tracking, workloads as W
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     conv = {}
-    wl = W.make_workload("tracking_cyl64", n_envs=n_conv, frames=conv_frames)
-    q = torch.from_numpy(wl.q_traj[:conv_frames + 1]).contiguous().to(dev)
+    nf = hold_at + hold_frames
+    wl = W.make_workload("tracking_cyl64", n_envs=n_conv, frames=nf)
+    qh = wl.q_traj[:nf + 1].copy()
+    qh[hold_at:] = qh[hold_at]
+    q = torch.from_numpy(qh).contiguous().to(dev)
 
-    def run(iters, warm):
+    def held(iters, warm):
         w2 = dataclasses.replace(wl, sim=dataclasses.replace(wl.sim, iters=iters, warm_start=warm))
-        sim = inhand.make_sim(w2, n_envs=n_conv, max_frames=conv_frames)
+        sim = inhand.make_sim(w2, n_envs=n_conv, max_frames=nf)
         sim.sim_set_commands(0, q)
         sim.sim_sample_initial(wl.nominal_pose, wl.init.sigma_p, wl.init.sigma_r, wl.init.m_range, wl.init.mu_range)
-        out = []
-        for f in range(conv_frames):
-            sim.sim_step(f, 1)
-            out.append(sim.sim_read_sensors()[0].clone())
+        sim.sim_step(0, nf)
+        pose, vel, _, status = (t.double() for t in sim.sim_get_state())
         sim.close()
-        return torch.stack(out).double()
+        return pose[:, :3], vel[:, :3].norm(dim=1), status
 
-    ref = run(200, False)
-    scale = ref.abs().sum().item()
-    for iters in (1, 2, 5, 10, 20):
-        conv[str(iters)] = {mode: (run(iters, mode == "warm") - ref).abs().sum().item() / scale
-                            for mode in ("cold", "warm")}
+    x_ref, _, st_ref = held(200, False)
+    for iters in (2, 5, 10, 20):
+        row = {}
+        for mode in ("cold", "warm"):
+            x, speed, st = held(iters, mode == "warm")
+            ok = (st == 0) & (st_ref == 0)
+            row[mode] = {"creep_mm_per_s": 1e3 * speed[ok].mean().item(),
+                         "offset_mm": 1e3 * (x - x_ref)[ok].norm(dim=1).median().item(),
+                         "envs": int(ok.sum().item())}
+        conv[str(iters)] = row
     track = {}
     for name in ["tracking_cyl64", "tracking_box27"]:
         res = {}
-        for label, iters, warm in [("cold_i20", 20, False), ("cold_i10", 10, False), ("warm_i10", 10, True),
-                                   ("cold_i5", 5, False), ("warm_i5", 5, True)]:
-            adds, times = [], []
-            for seed in seeds:
-                wl_t = W.make_workload(name, n_envs=n_envs, frames=frames, seed=seed)
-                gt_sim = wl_t.sim
-                wl_t.sim = dataclasses.replace(wl_t.sim, iters=iters, warm_start=warm)
-                wl_t.iters[:] = iters
-                tr = tracking.Tracker(wl_t, n_envs=n_envs, gt_sim=gt_sim)
-                tr.prepare()
-                nw = frames // tr.T
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                tr.window(0)
-                torch.cuda.synchronize()
-                e0.record()
-                for w in range(1, nw):
-                    tr.window(w)
-                e1.record()
-                torch.cuda.synchronize()
-                times.append(e0.elapsed_time(e1) / (nw - 1))
-                adds.append(tr.add_mm(nw * tr.T))
-                tr.close()
-            res[label] = {"add_mm_median": statistics.median(adds), "ms_per_window": statistics.median(times),
-                          "add_mm": adds}
+        for iters in (5, 10, 20):
+            for warm in (False, True):
+                adds, times = [], []
+                for seed in seeds:
+                    wl_t = W.make_workload(name, n_envs=n_envs, frames=frames, seed=seed)
+                    gt_sim = dataclasses.replace(wl_t.sim, iters=200)
+                    wl_t.sim = dataclasses.replace(wl_t.sim, iters=iters, warm_start=warm)
+                    wl_t.iters[:] = iters
+                    tr = tracking.Tracker(wl_t, n_envs=n_envs, gt_sim=gt_sim)
+                    tr.prepare()
+                    nw = frames // tr.T
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    tr.window(0)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    for w in range(1, nw):
+                        tr.window(w)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1) / (nw - 1))
+                    adds.append(tr.add_mm(nw * tr.T))
+                    tr.close()
+                res[f"{'warm' if warm else 'cold'}_i{iters}"] = {
+                    "add_mm_median": statistics.median(adds), "ms_per_window": statistics.median(times),
+                    "add_mm": adds}
         track[name] = res
     torch.cuda.empty_cache()
-    return {"convergence": {"what": f"relative L1 pad-force error vs a 200-iteration solve, {n_conv} sampled "
-                                    f"cylinder states, {conv_frames} frames", "by_iters": conv},
+    return {"convergence": {"what": f"held grasp (command frozen at frame {hold_at} for {hold_frames} frames), "
+                                    f"{n_conv} sampled cylinder states: mean object speed and median offset "
+                                    "from a 200-iteration solve", "by_iters": conv},
+            "tracking": {"n_envs": n_envs, "frames": frames, "seeds": list(seeds),
+                         "ground_truth": "200-iteration cold solve", **track}}
+
+
+# Work model of the PD-hand step kernel (step_pd.cu), counted from its source
+# the same way (FMA = 2, a sincos = 20): per env-substep the fingers'
+# kinematics (570 per finger: quaternion chain, link axes, joint axes), the PD
+# prediction (9 per joint), link culling (25 per link) and the object's
+# prediction and inertia (145); per pair tested 30; per contact the set-up with
+# its joints' share (140) and the pad and slip sums (45); per contact-iteration
+# the update against the link twist and the per-link sums (103); per
+# env-iteration the link twists (52 per link) and the joint updates (36 per joint).
+def pd_flops(work, scene, spheres):
+    F, D, Lk = scene.n_fingers, scene.n_joints, scene.n_links
+    per_substep = 570 * F + 9 * D + 25 * Lk + 145 + 15 * spheres
+    return (work["env_substeps"] * per_substep + work["pairs"] * 30 + work["contacts"] * 185 +
+            work["contact_iters"] * 103 + work["env_iters"] * (52 * Lk + 36 * D + 30))
+
+
+def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, windows=5, budget_s=10.0,
+             speed_only=False):
+    """The PD-driven hand (joints as state, full observation, full cost):
+    - throughput on the cylinder trajectory at N = n_envs: per window of T
+      frames one PD step launch and one full-cost launch per frame and the
+      optimizer, timed with CUDA events (L2 flushed before every window), the
+      step launches separately, their counted work against the FP32 peak;
+    - the oracle's PD step on the host, single thread, on a bounded sample;
+    - tracking error (median ADD over seeded trajectories, mm) with the full
+      cost, without the slip terms, and with the force and contact terms only
+      (the paper's ablation of contact and slip feedback), ground truth and
+      trackers all with the PD hand."""
+    import dataclasses
+    import torch
+    import oracle as O
+    from paper_2002_12160_gb300 import tracking, workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    wl = W.make_workload("tracking_cyl64", n_envs=n_envs, frames=frames, seed=seeds[0])
+    wl.sim = dataclasses.replace(wl.sim, hand="pd")
+    tr = tracking.Tracker(wl, n_envs=n_envs)
+    tr.prepare()
+    T = tr.T
+    for w in range(2):   # warm-up windows
+        tr.window_pd(w)
+    torch.cuda.synchronize()
+    tr.sim.sim_work_counters(reset=True)
+    win_ms, step_ms = [], []
+    st_stream = torch.cuda.current_stream()
+    for w in range(2, 2 + windows):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T + 2)]
+        ev[0].record(st_stream)
+        for k in range(T):
+            f = w * T + k
+            ev[1 + 2 * k].record(st_stream)
+            tr.sim.sim_step(f, 1)
+            ev[2 + 2 * k].record(st_stream)
+            tr.sim.cost_eval_full(tr.obs_q[f], tr.obs_pp[f], tr.obs[f], tr.obs_slip[f], None,
+                                  tr.argmin[f:f + 1], tr.est[f])
+        tr.sim.optimizer_update(wl.opt, w)
+        ev[-1].record(st_stream)
+        torch.cuda.synchronize()
+        win_ms.append(ev[0].elapsed_time(ev[-1]))
+        step_ms.append(sum(ev[1 + 2 * k].elapsed_time(ev[2 + 2 * k]) for k in range(T)) / T)
+    work = tr.sim.sim_work_counters()
+    tr.close()
+    n_launch = windows * T
+    flop = pd_flops(work, wl.scene, max(len(x) for x in wl.scene.shapes)) / n_launch
+    ms_win, ms_step = statistics.median(win_ms), statistics.median(step_ms)
+    clocks_max = 2070.0
+    peak = 152 * 128 * 2 * clocks_max * 1e6 / 1e12
+    achieved = flop / (ms_step / 1e3) / 1e12
+    throughput = {"env_steps_per_s": n_envs * T / (ms_win / 1e3), "ms_per_window": ms_win,
+                  "step_kernel_ms_per_frame": ms_step, "tracking_frames_per_s": T / (ms_win / 1e3),
+                  "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                               "frac": achieved / peak, "flop_per_launch": flop,
+                               "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                  "work_per_launch": {k: v / n_launch for k, v in work.items()}}
+    if speed_only:
+        del flush
+        return {"throughput": throughput}
+    # the oracle's PD step, bounded sample
+    n_s = 16
+    wl_s = W.make_workload("tracking_cyl64", n_envs=n_s, frames=frames, seed=seeds[0])
+    sim_s = dataclasses.replace(wl_s.sim, hand="pd")
+    osc = O.OracleScene(wl_s.scene)
+    pose, theta = O.sample_initial(n_s, O.pose8_to7(wl_s.nominal_pose), wl_s.init, wl_s.seed)
+    st = O.State(pose, np.zeros((n_s, 6)), theta).hand(wl_s.q_traj[0])
+    t0, done = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and done < frames:
+        O.step_pd(osc, sim_s, st, wl_s.q_traj, done, 1)
+        done += 1
+    el = time.perf_counter() - t0
+    cpu = {"value": n_s * done / el, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n_s} envs x {done} frames of the cylinder trajectory with the PD hand, single thread, {el:.1f} s"}
+    # tracking error by cost terms
+    variants = {"full": None, "no_slip": (6, 7, 8, 9), "force_and_contact": (0, 1, 2, 6, 7, 8, 9)}
+    track = {}
+    for name in ["tracking_cyl64", "tracking_box27"]:
+        res = {}
+        for label, zero in variants.items():
+            adds = []
+            for seed in seeds:
+                wl_t = W.make_workload(name, n_envs=n_envs, frames=frames, seed=seed)
+                w_full = list(W.SimConfig().w_full)
+                for k in (zero or ()):
+                    w_full[k] = 0.0
+                wl_t.sim = dataclasses.replace(wl_t.sim, hand="pd", w_full=tuple(w_full))
+                tr = tracking.Tracker(wl_t, n_envs=n_envs)
+                tr.prepare()
+                nw = frames // tr.T
+                for w in range(nw):
+                    tr.window_pd(w)
+                torch.cuda.synchronize()
+                adds.append(tr.add_mm(nw * tr.T))
+                tr.close()
+            res[label] = {"add_mm_median": statistics.median(adds), "add_mm": adds}
+        track[name] = res
+    del flush
+    torch.cuda.empty_cache()
+    return {"workload": f"tracking_cyl64 with the PD hand, N = {n_envs}, windows of {T} frames",
+            "throughput": throughput, "cpu_baseline": cpu,
             "tracking": {"n_envs": n_envs, "frames": frames, "seeds": list(seeds), **track}}
 
 
@@ -597,6 +730,7 @@ def run_ours(args, rank, world, local):
         line["refinement"] = refine_study(local)
         line["optimizers"] = optimizer_study(local)
         line["warm_start"] = warm_study(local)
+        line["pd_hand"] = pd_study(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
@@ -613,6 +747,11 @@ def main():
     if args.part == "optimizers":
         if rank == 0:
             print(json.dumps({"part": "optimizers", "optimizers": optimizer_study(local)}), flush=True)
+        return
+    if args.part in ("pd", "pd_speed"):
+        if rank == 0:
+            print(json.dumps({"part": args.part, "pd_hand": pd_study(local, speed_only=args.part == "pd_speed")}),
+                  flush=True)
         return
     if args.part == "warm":
         if rank == 0:

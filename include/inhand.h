@@ -107,7 +107,28 @@ typedef struct {
                               sim_set_state and when the optimizer replaces the
                               environment). sim_adjoint and sim_refine_elites
                               refuse a warm-started handle (IH_ERR_ARG). */
+    /* The hand (Sec. III-A: s_t holds the joint angles of articulated bodies;
+     * u_t are desired joint positions; Sec. IV: a joint-angle PD controller).
+     * hand = IH_HAND_KINEMATIC: the joints follow u_t exactly (shared by all
+     * environments). hand = IH_HAND_PD: each environment's joints are state,
+     * each a revolute joint of inertia `armature` driven toward u_t by
+     * kp (u - q) - kd qd, integrated implicitly per substep, and pushed back
+     * by the contacts (the solve updates the object and the joints together);
+     * the handle then also reports the full observation (sim_read_observation)
+     * and scores it with all ten cost terms (cost_eval_full). With IH_HAND_PD,
+     * warm_start must be 0, and sim_step_track, sim_step_frames,
+     * sim_track_window, sim_autotune, sim_set_variant, sim_adjoint and
+     * sim_refine_elites return IH_ERR_ARG. */
+    int32_t hand;
+    float kp, kd, armature;  /* N m/rad, N m s/rad, kg m^2 (armature > 0) */
+    float v_slip, w_slip;    /* a pad slips when its mean relative tangential
+                                speed exceeds v_slip (m/s); it slips rotationally
+                                when its relative spin about the normal exceeds
+                                w_slip (rad/s) */
+    float w_full[10];        /* w1..w10 of the full cost (cost_eval_full) */
 } ih_config;
+
+enum { IH_HAND_KINEMATIC = 0, IH_HAND_PD = 1 };
 
 /* Optimizer kinds (Sec. III-D). */
 enum { IH_OPT_ELITE = 0, IH_OPT_WRS = 1, IH_OPT_REPS = 2 };
@@ -250,6 +271,49 @@ ih_status sim_track_window(ih_sim *sim, int32_t frame0, int32_t T, const float *
  * averaged over the frame's substeps: the observation c_t^(l) of Sec. III-A)
  * and the status bits (device int32[N]); either may be NULL. */
 ih_status sim_read_sensors(ih_sim *sim, float *forces, int32_t *env_status);
+
+/* PD hand only (IH_HAND_PD; IH_ERR_ARG otherwise): the last frame's full
+ * observation o_t of Sec. III-A besides the forces, to device arrays (any may
+ * be NULL):
+ *   q        float[N][D]      joint angles q_t (D = 4 n_fingers)
+ *   pad_pose float[N][P][8]   each pad's position (x y z, 0) -- the link's
+ *                             origin plus the middle of the pad's axial interval
+ *                             along the capsule, or the palm's top centre --
+ *                             and the link's rotation (w x y z): P_t, R_t
+ *   slip     float[N][P][4]   (d_x, d_y, flags, 0): flags are int32 bits stored
+ *                             in the float (bit 0: translational slip, bit 1:
+ *                             rotational slip, bit 2: spin about the normal is
+ *                             positive); d is the unit slip direction in the
+ *                             pad's contact plane (first axis: the link's axis
+ *                             projected into the plane; second: normal x
+ *                             first), zero without translational slip. The slip
+ *                             is the normal-impulse-weighted mean of the
+ *                             object's velocity relative to the link at the
+ *                             pad's contacts over the frame's substeps.
+ * pad_pose and slip must be 16-byte aligned. */
+ih_status sim_read_observation(ih_sim *sim, float *q, float *pad_pose, float *slip);
+
+/* PD hand only: set (q, qd device float[N][D], qd may be NULL for rest) or
+ * read (either may be NULL) every environment's joint angles and velocities.
+ * sim_sample_initial and sim_set_state put each hand at rest at the frame-0
+ * command when commands for frame 0 have been uploaded, else at q = 0. */
+ih_status sim_set_hand(ih_sim *sim, const float *q, const float *qd);
+ih_status sim_get_hand(ih_sim *sim, float *q, float *qd);
+
+/* PD hand only: score the last stepped frame with the full cost of Sec. III-C
+ * against the ground truth's observation (device arrays in the layouts of
+ * sim_read_observation for one environment: q float[D], pad_pose float[P][8],
+ * forces float[P][3], slip float[P][4]):
+ *   cost_i = w1 |q - q_gt| + sum_l [ w2 |P - P_gt| + w3 angle(R^-1 R_gt)
+ *            + w4 (1 - alpha) + alpha (w5 | |c| - |c_gt| | + w6 angle(c, c_gt))
+ *            + w7 (1 - beta) + beta w8 angle(d, d_gt)
+ *            + w9 (1 - gamma) + gamma w10 |r - r_gt| ]
+ * alpha, beta, gamma = 1 when the pads agree on contact (|c| > tau), on
+ * translational and on rotational slip; the force angle counts only when both
+ * are in contact, the slip angle only when both slip, |r - r_gt| only when
+ * both slip rotationally. FP64; window mean, argmin and outputs as cost_eval. */
+ih_status cost_eval_full(ih_sim *sim, const float *q, const float *pad_pose, const float *forces,
+                         const float *slip, double *cost_mean, int32_t *argmin, float *est_pose);
 
 /* Score the last stepped frame against the observation (Sec. III-C, force and
  * contact-state terms; Eqs. 1-2 with the running mean of Algorithm 1):

@@ -73,7 +73,7 @@ def lib():
             L.orc_step.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P, C.c_int]
             L.orc_cost.argtypes = [P, C.c_int, C.c_int, P, P, P, P, C.c_int, P, P]
             L.orc_step_pd.argtypes = [P, P, P, C.c_int, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P,
-                                      P, P, P, C.c_int]
+                                      P, P, P, P, C.c_int]
             L.orc_cost_full.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P,
                                         P, C.c_int, P, P]
             L.orc_philox4x32_10.argtypes = [P, P, P]
@@ -245,8 +245,9 @@ class Obs:
     direction (N, P, 2) and flags (N, P: bit 0 translational slip, bit 1
     rotational slip, bit 2 spin > 0)."""
 
-    def __init__(self, q, pad_pose, forces, slip_d, flags):
+    def __init__(self, q, pad_pose, forces, slip_d, flags, slip_mag=None):
         self.q, self.pad_pose, self.forces, self.slip_d, self.flags = q, pad_pose, forces, slip_d, flags
+        self.slip_mag = slip_mag   # (N, P, 2): mean relative tangential speed and spin (oracle only)
 
     def env(self, i) -> "Obs":
         return Obs(*(a[i:i + 1].copy() for a in (self.q, self.pad_pose, self.forces, self.slip_d, self.flags)))
@@ -265,14 +266,15 @@ def step_pd(osc: OracleScene, sim, st: State, q_traj, frame0: int, n_frames: int
     pad_pose = np.zeros((n, P, 7))
     slip_d = np.zeros((n, P, 2))
     flags = np.zeros((n, P), np.int32)
+    slip_mag = np.zeros((n, P, 2))
     diag = np.zeros((n, DIAG))
     last = np.zeros((n, max(last_cap, 1), 7))
     last_n = np.zeros(n, np.int32)
     lib().orc_step_pd(C.byref(osc.rec), C.byref(cfg), C.byref(pd), n, _p(q), frame0, n_frames, _p(st.pose),
                       _p(st.vel), _p(st.theta), _p(st.shape), None if st.iters is None else _p(st.iters),
                       _p(st.status), _p(st.qj), _p(st.qdj), _p(forces), _p(pad_pose), _p(slip_d), _p(flags),
-                      _p(diag), _p(last) if last_cap > 0 else None, _p(last_n) if last_cap > 0 else None, last_cap)
-    obs = Obs(st.qj.copy(), pad_pose, forces, slip_d, flags)
+                      _p(slip_mag), _p(diag), _p(last) if last_cap > 0 else None, _p(last_n) if last_cap > 0 else None, last_cap)
+    obs = Obs(st.qj.copy(), pad_pose, forces, slip_d, flags, slip_mag)
     if last_cap > 0:
         return obs, diag, last, last_n
     return obs, diag
@@ -356,7 +358,8 @@ def optimizer(opt, st: State, C_mean, seed: int, update_index: int):
     i = lib().orc_optimizer(C.byref(o), st.n, _p(Cm), _p(st.pose), _p(st.vel), _p(st.theta),
                             _p(st.status), seed, update_index, _p(parent), _p(stats))
     st.drop_cache(parent != np.arange(st.n))   # replaced environments start cold
-    st.copy_hand(parent)
+    if i >= 0:
+        st.copy_hand(parent)
     return i, parent, {"mean": stats[:8].copy(), "cov": stats[8:72].reshape(8, 8).copy(),
                        "L": stats[72:136].reshape(8, 8).copy(), "k": int(stats[136]),
                        "istar": int(stats[137]), "sd": float(stats[138])}

@@ -1311,8 +1311,8 @@ static void pad_pose_of(const orc_scene *sc, int pad, const double *lp, double *
 static void step_env_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd *pd, const double *u_all,
                         int ns, double *pose7, double *vel6, const double *theta, int shape, int iters,
                         int32_t *status, double *qj, double *qdj, double *forces, double *pad_pose,
-                        double *slip_d, int32_t *slip_flags, double *diag, pd_contact_t *ct, int ct_cap,
-                        double *last_ct, int32_t *last_n, int last_cap) {
+                        double *slip_d, int32_t *slip_flags, double *slip_mag, double *diag, pd_contact_t *ct,
+                        int ct_cap, double *last_ct, int32_t *last_n, int last_cap) {
     const int n_links = 1 + 4 * sc->n_fingers, D = 4 * sc->n_fingers;
     const int P = sc->n_pads;
     const double h = cfg->frame_dt / ns;
@@ -1327,6 +1327,7 @@ static void step_env_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd
     for (int k = 0; k < 3 * P; k++) forces[k] = 0;
     for (int k = 0; k < 2 * P; k++) slip_d[k] = 0;
     for (int k = 0; k < P; k++) slip_flags[k] = 0;
+    for (int k = 0; k < 2 * P; k++) slip_mag[k] = 0;
     diag[0] = 0; diag[1] = 0; diag[2] = INFINITY; diag[3] = INFINITY; diag[4] = INFINITY; diag[5] = 0;
     if (last_n) *last_n = 0;
 
@@ -1502,6 +1503,8 @@ static void step_env_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd
         vec3 nb = v3(A[4], A[5], A[6]);
         nb = vscale(nb, 1.0 / vnorm(nb));
         double spin = A[7] / A[0];
+        slip_mag[2 * l] = vnorm(vt);
+        slip_mag[2 * l + 1] = spin;
         int flags = 0;
         if (vnorm(vt) > pd->v_slip) {
             pose_t Lk = pose_from7(lp + 7 * sc->pad_link[l]);
@@ -1527,15 +1530,16 @@ static void step_env_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd
  * [N][D] are the joint positions and velocities (in/out). Outputs of the last
  * frame: forces [N][P][3], pad_pose [N][P][7], slip_d [N][P][2], slip_flags
  * [N][P] (bit 0 translational slip, bit 1 rotational slip, bit 2 spin > 0),
- * diag [N][ORC_DIAG]; with last_n non-NULL, the last substep's contacts
+ * slip_mag [N][P][2] (mean relative tangential speed, mean relative spin;
+ * zero for a pad without contact), diag [N][ORC_DIAG]; with last_n non-NULL, the last substep's contacts
  * last_ct [N][last_cap][7] (link, world point, impulse on the object) and
  * their count last_n [N].
  */
 int orc_step_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd *pd, int N, const double *q_traj,
                 int frame0, int n_frames, double *pose, double *vel, const double *theta, const int32_t *shape,
                 const int32_t *iters, int32_t *status, double *qj, double *qdj, double *forces,
-                double *pad_pose, double *slip_d, int32_t *slip_flags, double *diag, double *last_ct,
-                int32_t *last_n, int last_cap) {
+                double *pad_pose, double *slip_d, int32_t *slip_flags, double *slip_mag, double *diag,
+                double *last_ct, int32_t *last_n, int last_cap) {
     const int D = 4 * sc->n_fingers, n_links = 1 + 4 * sc->n_fingers, ns = cfg->substeps;
     const int P = sc->n_pads;
     double *u_all = (double *)malloc(sizeof(double) * (D > 0 ? D : 1) * (ns + 1));
@@ -1554,8 +1558,8 @@ int orc_step_pd(const orc_scene *sc, const orc_config *cfg, const orc_pd *pd, in
             step_env_pd(sc, cfg, pd, u_all, ns, pose + 7 * (size_t)i, vel + 6 * (size_t)i,
                         theta + 2 * (size_t)i, shape ? shape[i] : 0, it, status + i, qj + (size_t)i * D,
                         qdj + (size_t)i * D, forces + (size_t)i * 3 * P, pad_pose + (size_t)i * 7 * P,
-                        slip_d + (size_t)i * 2 * P, slip_flags + (size_t)i * P, diag + (size_t)i * ORC_DIAG,
-                        ct, cap, last_n ? last_ct + (size_t)i * 7 * last_cap : NULL, last_n ? last_n + i : NULL,
+                        slip_d + (size_t)i * 2 * P, slip_flags + (size_t)i * P, slip_mag + (size_t)i * 2 * P,
+                        diag + (size_t)i * ORC_DIAG, ct, cap, last_n ? last_ct + (size_t)i * 7 * last_cap : NULL, last_n ? last_n + i : NULL,
                         last_cap);
         }
     }

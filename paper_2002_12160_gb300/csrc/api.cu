@@ -70,6 +70,14 @@ struct ih_sim {
     // warm-started solver: per environment the last substep's contacts (impulse, pair id)
     float4 *cache = nullptr;
     int *cache_n = nullptr;
+    // PD-driven hand: commands, joints, the full observation
+    bool pd = false;
+    float *cmd = nullptr;               // [max_frames + 1][D] desired joint positions
+    float *qj = nullptr, *qdj = nullptr; // [N][D]
+    float4 *pad_pose = nullptr;         // [N][P][2]
+    float4 *slip = nullptr;             // [N][P]
+    float *sn_qj = nullptr, *sn_qdj = nullptr;
+    int pd_grid = 0;
     // captured tracking window (replayed by sim_track_window)
     cudaGraphExec_t win_exec = nullptr;
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
@@ -105,6 +113,10 @@ ih_status fail(ih_sim *s, ih_status code, const char *fmt, ...) {
 ih_status cuda_fail(ih_sim *s, cudaError_t e, const char *what) {
     return fail(s, e == cudaErrorMemoryAllocation ? IH_ERR_OOM : IH_ERR_CUDA, "%s: %s", what,
                 cudaGetErrorString(e));
+}
+
+ih_status refuse_pd(ih_sim *s, const char *what) {
+    return fail(s, IH_ERR_ARG, "%s is not available with the PD-driven hand (use sim_step and cost_eval_full)", what);
 }
 
 // frames scored by sim_step_frames wait for sim_frames_argmin (which advances
@@ -199,6 +211,16 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
         cfg->c_max < 1 || cfg->c_max > IH_MAX_CONTACTS || !finite_pos(cfg->escape_radius) ||
         (cfg->warm_start != 0 && cfg->warm_start != 1))
         return fail(nullptr, IH_ERR_ARG, "invalid config");
+    if (cfg->hand != IH_HAND_KINEMATIC && cfg->hand != IH_HAND_PD) return fail(nullptr, IH_ERR_ARG, "unknown hand");
+    if (cfg->hand == IH_HAND_PD) {
+        if (!(cfg->kp >= 0.0f) || !(cfg->kd >= 0.0f) || !finite_pos(cfg->armature) || !std::isfinite(cfg->kp) ||
+            !std::isfinite(cfg->kd) || !(cfg->v_slip >= 0.0f) || !(cfg->w_slip >= 0.0f))
+            return fail(nullptr, IH_ERR_ARG, "invalid PD hand constants");
+        if (cfg->warm_start) return fail(nullptr, IH_ERR_ARG, "warm_start is not available with the PD-driven hand");
+        for (int k = 0; k < 10; ++k)
+            if (!(cfg->w_full[k] >= 0.0f) || !std::isfinite(cfg->w_full[k]))
+                return fail(nullptr, IH_ERR_ARG, "w_full[%d] is invalid", k);
+    }
 
     ih_sim *s = new ih_sim();
     s->n_shapes = sc->n_shapes; s->n_fingers = sc->n_fingers; s->n_links = n_links;
@@ -217,6 +239,10 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     d.tau = cfg->tau; d.w_force = cfg->w_force; d.w_contact = cfg->w_contact;
     d.c_max = cfg->c_max; d.escape_radius = cfg->escape_radius;
     d.warm = cfg->warm_start;
+    d.hand = cfg->hand;
+    d.kp = cfg->kp; d.kd = cfg->kd; d.armature = cfg->armature; d.v_slip = cfg->v_slip; d.w_slip = cfg->w_slip;
+    for (int k = 0; k < 10; ++k) d.w_full[k] = cfg->w_full[k];
+    s->pd = cfg->hand == IH_HAND_PD;
     s->variant = default_variant(cfg->n_envs, cfg->c_max);
     const int N = cfg->n_envs, P = sc->n_pads, F = sc->n_fingers;
 
@@ -248,6 +274,12 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
     A(dalloc(s, &s->moments, (size_t)opt_blocks(N) * kMoments)); A(dalloc(s, &s->misc, 80));
     if (d.warm) { A(dalloc(s, &s->cache, (size_t)N * cfg->c_max)); A(dalloc(s, &s->cache_n, N)); }
+    if (s->pd) {
+        const size_t Dj = 4 * (size_t)sc->n_fingers;
+        A(dalloc(s, &s->cmd, ((size_t)cfg->max_frames + 1) * Dj)); A(dalloc(s, &s->qj, (size_t)N * Dj));
+        A(dalloc(s, &s->qdj, (size_t)N * Dj)); A(dalloc(s, &s->pad_pose, 2 * (size_t)N * P));
+        A(dalloc(s, &s->slip, (size_t)N * P));
+    }
     if (e != cudaSuccess) {
         ih_status st = cuda_fail(nullptr, e, "sim_create allocation");
         sim_destroy(s);
@@ -284,6 +316,11 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemsetAsync(s->done, 0, sizeof(unsigned int), st));
     A(cudaMemsetAsync(s->work, 0, 6 * sizeof(unsigned long long), st));
     if (d.warm) A(cudaMemsetAsync(s->cache_n, 0, (size_t)N * sizeof(int), st));
+    if (s->pd) {
+        A(launch_hand_rest(N, 4 * sc->n_fingers, nullptr, s->qj, s->qdj, st));
+        A(cudaMemsetAsync(s->pad_pose, 0, 2 * (size_t)N * P * sizeof(float4), st));
+        A(cudaMemsetAsync(s->slip, 0, (size_t)N * P * sizeof(float4), st));
+    }
     A(launch_shape_setup(s->spheres_raw, s->spheres, s->shape_first, s->shape_count, sc->n_shapes,
                          s->shape_jinv, s->shape_bound, s->cl_first, s->clusters, st));
     A(launch_lpt_order(N, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, st));
@@ -296,6 +333,13 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     s->frame_ready.assign(cfg->max_frames, 0);
     s->step_grid = grid_for(s->variant, N);
     e = step_prepare(s->variant, s->s_max, s->cfg.c_max, s->dcfg.warm != 0);
+    if (e == cudaSuccess && s->pd) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = pd_step_prepare(s->s_max, s->cfg.c_max);
+        s->pd_grid = pd_step_grid(N, sms > 0 ? sms : 1);
+    }
     if (e != cudaSuccess) {
         ih_status r = cuda_fail(nullptr, e, "sim_create step setup");
         sim_destroy(s);
@@ -333,6 +377,9 @@ ih_status sim_set_commands(ih_sim *s, int32_t frame0, int32_t n_frames, const fl
                     s->cfg.max_frames);
     float4 *tab = s->link_tab + (size_t)frame0 * (s->cfg.substeps + 1) * s->n_links * kLinkStride;
     cudaError_t e = launch_fk(dev_scene(s), q, n_frames, s->cfg.substeps, tab, s->stream);
+    if (e == cudaSuccess && s->pd && s->n_joints > 0)
+        e = cudaMemcpyAsync(s->cmd + (size_t)frame0 * s->n_joints, q, ((size_t)n_frames + 1) * s->n_joints * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "fk launch");
     for (int f = frame0; f < frame0 + n_frames; ++f) s->frame_ready[f] = 1;
     return IH_OK;
@@ -351,6 +398,8 @@ ih_status sim_sample_initial(ih_sim *s, const float *nominal, float sigma_p, flo
     if (e == cudaSuccess) e = cudaMemsetAsync(s->c_sum, 0, s->cfg.n_envs * sizeof(double), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->n_window, 0, sizeof(int), s->stream);
     if (e == cudaSuccess && s->cache_n) e = cudaMemsetAsync(s->cache_n, 0, s->cfg.n_envs * sizeof(int), s->stream);
+    if (e == cudaSuccess && s->pd)
+        e = launch_hand_rest(s->cfg.n_envs, s->n_joints, s->frame_ready[0] ? s->cmd : nullptr, s->qj, s->qdj, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "sample_initial");
     s->window_frames = 0;
     s->ws_valid = false;
@@ -368,6 +417,8 @@ ih_status sim_set_state(ih_sim *s, const float *pose, const float *vel, const fl
     if (e == cudaSuccess && (shape_id || iters))
         e = launch_lpt_order(s->cfg.n_envs, s->shape_count, s->shape, s->iters, s->lpt_scratch, s->order, s->stream);
     if (e == cudaSuccess && s->cache_n) e = cudaMemsetAsync(s->cache_n, 0, s->cfg.n_envs * sizeof(int), s->stream);
+    if (e == cudaSuccess && s->pd)
+        e = launch_hand_rest(s->cfg.n_envs, s->n_joints, s->frame_ready[0] ? s->cmd : nullptr, s->qj, s->qdj, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
     s->ws_valid = false;
     return IH_OK;
@@ -406,6 +457,18 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
         return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + n_frames);
     for (int f = frame0; f < frame0 + n_frames; ++f)
         if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    if (s->pd) {
+        PdArgs p;
+        p.sc = dev_scene(s); p.cfg = s->dcfg; p.N = s->cfg.n_envs; p.cmd = s->cmd;
+        p.frame0 = frame0; p.n_frames = n_frames; p.pose = s->pose; p.vel = s->vel; p.params = s->params;
+        p.shape = s->shape; p.iters = s->iters; p.order = s->order; p.status = s->status;
+        p.qj = s->qj; p.qdj = s->qdj; p.forces = s->forces; p.pad_pose = s->pad_pose; p.slip = s->slip;
+        p.work = s->work;
+        cudaError_t e = launch_pd_step(p, s->pd_grid, s->s_max, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "PD step launch");
+        s->stepped = true;
+        return IH_OK;
+    }
     StepArgs a;
     a.sc = dev_scene(s); a.cfg = s->dcfg; a.N = s->cfg.n_envs; a.link_tab = s->link_tab;
     a.frame0 = frame0; a.n_frames = n_frames; a.pose = s->pose; a.vel = s->vel; a.params = s->params;
@@ -455,6 +518,7 @@ OptArgs opt_args(ih_sim *s, const ih_opt_config *opt, uint32_t update_index, int
     a.explore_velocity = opt->explore_velocity;
     a.sn_pose = s->sn_pose; a.sn_vel = s->sn_vel; a.sn_params = s->sn_params; a.sn_status = s->sn_status;
     a.cache_n = s->cache_n;
+    a.qj = s->qj; a.qdj = s->qdj; a.D = s->n_joints; a.sn_qj = s->sn_qj; a.sn_qdj = s->sn_qdj;
     return a;
 }
 
@@ -485,6 +549,7 @@ ih_status check_opt(ih_sim *s, const ih_opt_config *opt) {
             auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
             A(dalloc(s, &s->sn_pose, 2 * N)); A(dalloc(s, &s->sn_vel, 2 * N));
             A(dalloc(s, &s->sn_params, N)); A(dalloc(s, &s->sn_status, N));
+            if (s->pd) { A(dalloc(s, &s->sn_qj, N * s->n_joints)); A(dalloc(s, &s->sn_qdj, N * s->n_joints)); }
             if (e != cudaSuccess) return cuda_fail(s, e, "optimizer snapshot");
         }
     }
@@ -495,6 +560,7 @@ ih_status check_opt(ih_sim *s, const ih_opt_config *opt) {
 ih_status sim_step_track(ih_sim *s, int32_t frame, const float *obs, double *cost_mean, int32_t *argmin,
                          float *est_pose) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_step_track");
     if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     if (frame < 0 || frame >= s->cfg.max_frames || !s->frame_ready[frame])
@@ -530,6 +596,7 @@ cudaError_t window_buffers(ih_sim *s, int T) {
 
 ih_status sim_step_frames(ih_sim *s, int32_t frame0, int32_t T, const float *obs) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_step_frames");
     if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
@@ -563,6 +630,7 @@ ih_status sim_frames_argmin(ih_sim *s, float *est_pose, int32_t *argmin) {
 ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *obs, const ih_opt_config *opt,
                            uint32_t update_index, float *est_pose, int32_t *argmin) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_track_window");
     if (ih_status rp = check_no_pending(s)) return rp;
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
@@ -656,9 +724,74 @@ ih_status cost_eval(ih_sim *s, const float *obs, double *cost_mean, int32_t *arg
     a.cost_mean = cost_mean;
     a.pose = s->pose; a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est_pose;
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
+    a.qj = nullptr; a.pad_pose = nullptr; a.slip = nullptr; a.g_q = nullptr; a.g_pose = nullptr; a.g_slip = nullptr;
+    a.D = 0;
     cudaError_t e = launch_cost(a, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "cost launch");
     s->window_frames += 1;
+    return IH_OK;
+}
+
+ih_status cost_eval_full(ih_sim *s, const float *q, const float *pad_pose, const float *forces, const float *slip,
+                         double *cost_mean, int32_t *argmin, float *est_pose) {
+    if (!s) return IH_ERR_ARG;
+    if (!s->pd) return fail(s, IH_ERR_ARG, "cost_eval_full needs the PD-driven hand");
+    if (ih_status rp = check_no_pending(s)) return rp;
+    if ((!q && s->n_joints > 0) || !pad_pose || !forces || !slip)
+        return fail(s, IH_ERR_ARG, "the ground truth's q, pad_pose, forces and slip are required");
+    if (!aligned16(pad_pose) || !aligned16(slip)) return fail(s, IH_ERR_ARG, "pad_pose and slip must be 16-byte aligned");
+    CostArgs a;
+    a.N = s->cfg.n_envs; a.P = s->n_pads; a.cfg = s->dcfg; a.forces = s->forces; a.obs = forces;
+    a.status = s->status; a.c_sum = s->c_sum; a.c_mean = s->c_mean; a.n_window = s->n_window;
+    a.cost_mean = cost_mean;
+    a.pose = s->pose; a.argmin_state = s->argmin; a.argmin_out = argmin; a.est_pose_out = est_pose;
+    a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
+    a.qj = s->qj; a.pad_pose = s->pad_pose; a.slip = s->slip; a.D = s->n_joints;
+    a.g_q = q; a.g_pose = reinterpret_cast<const float4 *>(pad_pose); a.g_slip = reinterpret_cast<const float4 *>(slip);
+    cudaError_t e = launch_cost(a, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cost launch");
+    s->window_frames += 1;
+    return IH_OK;
+}
+
+ih_status sim_read_observation(ih_sim *s, float *q, float *pad_pose, float *slip) {
+    if (!s) return IH_ERR_ARG;
+    if (!s->pd) return fail(s, IH_ERR_ARG, "the full observation needs the PD-driven hand");
+    if ((pad_pose && !aligned16(pad_pose)) || (slip && !aligned16(slip)))
+        return fail(s, IH_ERR_ARG, "pad_pose and slip must be 16-byte aligned");
+    const size_t N = s->cfg.n_envs, P = s->n_pads, D = s->n_joints;
+    cudaError_t e = cudaSuccess;
+    if (q && D > 0) e = cudaMemcpyAsync(q, s->qj, N * D * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && pad_pose)
+        e = cudaMemcpyAsync(pad_pose, s->pad_pose, 2 * N * P * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && slip)
+        e = cudaMemcpyAsync(slip, s->slip, N * P * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read_observation");
+    return IH_OK;
+}
+
+ih_status sim_set_hand(ih_sim *s, const float *q, const float *qd) {
+    if (!s) return IH_ERR_ARG;
+    if (!s->pd) return fail(s, IH_ERR_ARG, "the hand's joints are state only with the PD-driven hand");
+    const size_t bytes = (size_t)s->cfg.n_envs * s->n_joints * sizeof(float);
+    if (bytes == 0) return IH_OK;
+    if (!q) return fail(s, IH_ERR_ARG, "q is required");
+    cudaError_t e = cudaMemcpyAsync(s->qj, q, bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = qd ? cudaMemcpyAsync(s->qdj, qd, bytes, cudaMemcpyDeviceToDevice, s->stream)
+               : cudaMemsetAsync(s->qdj, 0, bytes, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set_hand");
+    return IH_OK;
+}
+
+ih_status sim_get_hand(ih_sim *s, float *q, float *qd) {
+    if (!s) return IH_ERR_ARG;
+    if (!s->pd) return fail(s, IH_ERR_ARG, "the hand's joints are state only with the PD-driven hand");
+    const size_t bytes = (size_t)s->cfg.n_envs * s->n_joints * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (q && bytes) e = cudaMemcpyAsync(q, s->qj, bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && qd && bytes) e = cudaMemcpyAsync(qd, s->qdj, bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "get_hand");
     return IH_OK;
 }
 
@@ -690,6 +823,7 @@ ih_status sim_work_counters(ih_sim *s, uint64_t *out, int32_t reset) {
 
 ih_status sim_set_variant(ih_sim *s, int32_t tpe, int32_t cpl) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_set_variant");
     StepVariant v{tpe, cpl, 128};
     if (!step_variant_supported(v)) return fail(s, IH_ERR_ARG, "unsupported step shape %d x %d", tpe, cpl);
     if (step_variant_max_contacts(v) < s->cfg.c_max)
@@ -710,6 +844,7 @@ int32_t sim_step_variants(int32_t *out, int32_t cap) {
 
 ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *chosen, float *ms_out) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_autotune");
     if (n_frames < 1 || frame0 < 0 || frame0 + n_frames > s->cfg.max_frames)
         return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + n_frames);
     for (int f = frame0; f < frame0 + n_frames; ++f)
@@ -851,6 +986,7 @@ ih_status sim_adjoint(ih_sim *s, int32_t frame0, int32_t horizon, int32_t checkp
                       const int32_t *envs, int32_t n, float beta, float width, double *cost, float *grad,
                       float *grad_quat) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_adjoint");
     if (s->dcfg.warm) return fail(s, IH_ERR_ARG, "the adjoint differentiates the cold-started solver only");
     if (!obs || !grad) return fail(s, IH_ERR_ARG, "obs and grad are required");
     ih_status r = check_horizon(s, frame0, horizon);
@@ -914,6 +1050,7 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
                             int32_t steps, float step_scale, float beta, float width, int32_t *elite_out,
                             double *cost_before, double *cost_after) {
     if (!s) return IH_ERR_ARG;
+    if (s->pd) return refuse_pd(s, "sim_refine_elites");
     if (s->dcfg.warm) return fail(s, IH_ERR_ARG, "the adjoint differentiates the cold-started solver only");
     if (!obs) return fail(s, IH_ERR_ARG, "obs is required");
     ih_status r = check_opt(s, opt);

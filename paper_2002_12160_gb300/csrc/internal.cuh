@@ -40,6 +40,10 @@ struct DevConfig {
     int c_max;
     float escape_radius;
     int warm;           // warm-started solver (impulse cache per environment)
+    int hand;           // 0: kinematic hand, 1: PD-driven joints
+    float kp, kd, armature;   // joint PD gains and joint inertia
+    float v_slip, w_slip;     // translational / rotational slip thresholds
+    float w_full[10];         // weights of the full cost (PD hand)
 };
 
 // ---------------------------------------------------------------- FP32 math
@@ -228,6 +232,30 @@ struct StepArgs {
     float4 *cache;            // [N][c_max]: final impulse xyz, pair id (link << 8 | sphere) in w
     int *cache_n;             // [N]
 };
+// The step with the PD-driven hand (step_pd.cu): the joints are state.
+struct PdArgs {
+    DevScene sc;
+    DevConfig cfg;
+    int N;
+    const float *cmd;         // [frames + 1][D] desired joint positions at frame boundaries
+    int frame0, n_frames;
+    float4 *pose, *vel;       // [N][2]
+    const float2 *params;
+    const int *shape, *iters;
+    const int *order;         // [N] or null
+    int *status;
+    float *qj, *qdj;          // [N][D] joint angles and velocities
+    float *forces;            // [N][P][3]
+    float4 *pad_pose;         // [N][P][2]: (position, 0), (quaternion w x y z)
+    float4 *slip;             // [N][P]: (d_x, d_y, flag bits, 0)
+    unsigned long long *work; // [6]
+};
+size_t pd_step_smem_bytes(int s_max, int c_max);
+cudaError_t pd_step_prepare(int s_max, int c_max);
+int pd_step_grid(int N, int sms);
+cudaError_t launch_pd_step(const PdArgs &a, int grid, int s_max, cudaStream_t s);
+cudaError_t launch_hand_rest(int N, int D, const float *q0, float *qj, float *qdj, cudaStream_t s);
+
 struct StepVariant {
     int group;        // lanes per environment
     int cpl;          // register-resident contacts per lane
@@ -256,6 +284,15 @@ struct CostArgs {
     double *part_c;          // [blocks] scratch
     int *part_i;             // [blocks] scratch
     unsigned int *done;      // scratch ticket (zero between launches)
+    // full cost (qj non-null, PD hand): the environments' observation against
+    // the ground truth's (obs holds its forces)
+    const float *qj;         // [N][D]
+    const float4 *pad_pose;  // [N][P][2]
+    const float4 *slip;      // [N][P]
+    const float *g_q;        // [D]
+    const float4 *g_pose;    // [P][2]
+    const float4 *g_slip;    // [P]
+    int D;
 };
 cudaError_t launch_cost(const CostArgs &a, cudaStream_t s);
 int cost_blocks(int N);
@@ -303,6 +340,10 @@ struct OptArgs {
     float2 *sn_params;        // [N]
     int *sn_status;           // [N]
     int *cache_n;             // warm-start cache counts, or null: a replaced environment starts cold
+    // PD-driven hand: a replaced environment takes its parent's joints (null: kinematic hand)
+    float *qj, *qdj;          // [N][D]
+    int D;
+    float *sn_qj, *sn_qdj;    // [N][D] joints before the update (WRS / REPS)
 };
 int opt_blocks(int N);
 

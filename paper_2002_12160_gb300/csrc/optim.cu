@@ -477,6 +477,13 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
     const double mu = fmin(fmax((double)th.y + d[7], (double)a.mu_lo), (double)a.mu_hi);
     a.params[i] = make_float2((float)m, (float)mu);
     a.status[i] = a.status[par];
+    if (a.qj) {   // the parent's hand (elites are not written by this kernel)
+        const int D = a.D;
+        for (int j = 0; j < D; ++j) {
+            a.qj[(size_t)i * D + j] = a.qj[(size_t)par * D + j];
+            a.qdj[(size_t)i * D + j] = a.qdj[(size_t)par * D + j];
+        }
+    }
 }
 
 // ---------------------------------------------------------------- WRS / REPS
@@ -771,6 +778,13 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) soft_apply_kernel(con
     const double mu = fmin(fmax((double)th.y + (double)a.sigma_theta[1] * eps[7], (double)a.mu_lo), (double)a.mu_hi);
     a.params[i] = make_float2((float)m, (float)mu);
     a.status[i] = a.sn_status[par];
+    if (a.qj) {   // the parent's hand, from the snapshot
+        const int D = a.D;
+        for (int j = 0; j < D; ++j) {
+            a.qj[(size_t)i * D + j] = a.sn_qj[(size_t)par * D + j];
+            a.qdj[(size_t)i * D + j] = a.sn_qdj[(size_t)par * D + j];
+        }
+    }
 }
 
 __global__ void win_desc_kernel(WinDesc *d, WinDesc v) { *d = v; }
@@ -800,6 +814,11 @@ cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_vel, a.vel, 2 * N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_params, a.params, N * sizeof(float2), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_status, a.status, N * sizeof(int), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && a.qj) {
+            const size_t hb = N * (size_t)a.D * sizeof(float);
+            e = cudaMemcpyAsync(a.sn_qj, a.qj, hb, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(a.sn_qdj, a.qdj, hb, cudaMemcpyDeviceToDevice, s);
+        }
         if (e != cudaSuccess) return e;
         soft_apply_kernel<<<opt_blocks(a.N), kOptBlock * kApplyLanes, 0, s>>>(a);
         return cudaGetLastError();

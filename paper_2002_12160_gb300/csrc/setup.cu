@@ -3,6 +3,7 @@
 // block of commanded frames (the robot state driven by u_t, Sec. III-A); the
 // initial sampling of pose, mass and friction (Sec. III-D, Algorithm 1
 // initialisation); and the validated upload of a caller's state.
+#include "hand.cuh"
 #include "internal.cuh"
 
 namespace ih {
@@ -113,25 +114,7 @@ __global__ void fk_kernel(const DevScene sc, const float *q, int n_frames, int n
         const float q0 = q[(size_t)fr * D + 4 * f + j], q1 = q[(size_t)(fr + 1) * D + 4 * f + j];
         qf[j] = q0 + frac * (q1 - q0);
     }
-    const float4 root = sc.finger_root[f];
-    float sz, cz, sy, cy;
-    sincosf(0.5f * (root.w + qf[0]), &sz, &cz);
-    const float hs = 0.70710678118654752f;   // sin(pi/4) = cos(pi/4)
-    // qz(yaw + q0) * qy(-pi/2)
-    Q4 Q = qmul({cz, 0.0f, 0.0f, sz}, {hs, 0.0f, -hs, 0.0f});
-    V3 a = mk(root.x, root.y, root.z);
-    for (int j = 0; j < 4; ++j) {
-        if (j > 0) {
-            a = a + qrot(Q, mk(sc.link_len, 0, 0));
-            sincosf(-0.5f * qf[j], &sy, &cy);
-            Q = qnorm(qmul(Q, {cy, 0.0f, sy, 0.0f}));
-        }
-        const V3 ax = qrot(Q, mk(1, 0, 0));
-        float4 *lo = o + (1 + 4 * f + j) * kLinkStride;
-        lo[0] = make_float4(a.x, a.y, a.z, 0.0f);
-        lo[1] = make_float4(ax.x, ax.y, ax.z, 0.0f);
-        lo[2] = make_float4(Q.w, Q.x, Q.y, Q.z);
-    }
+    finger_fk(sc, f, qf, o + (1 + 4 * f) * kLinkStride);
 }
 
 // One thread per environment: x = x0 + sigma_p n_{0..2}, R = exp(sigma_r n_{3..5}) R0,

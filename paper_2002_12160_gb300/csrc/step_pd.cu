@@ -1,0 +1,493 @@
+// step_pd.cu -- the dynamics step with a PD-driven articulated hand: the
+// hand's joint angles are part of each environment's state (Sec. III-A, s_t
+// holds the joint angles of articulated bodies) and follow the desired joint
+// positions u_t through a joint-angle PD controller (Sec. IV), pushed back by
+// the contacts. Each environment also reports the full observation o_t: the
+// joint angles q_t, every pad's pose (P_t, R_t), its force c_t, and its
+// translational slip direction d_t and rotational slip r_t (Sec. III-A).
+//
+// One warp owns one environment at a time (grid-stride, LPT order). Per
+// substep the warp
+//   1. runs the fingers' kinematics from the environment's own joint angles
+//      (one lane per finger) into shared memory, with every joint's axis and
+//      origin, and predicts the joints' velocities under the PD force alone:
+//      qd* = (I qd + h kp (u - q)) / M, M = I + h kd + h^2 kp (implicit PD);
+//   2. culls links against the object's bounding sphere, tests every
+//      (surviving link, sphere) pair and compacts contacts in pair order;
+//   3. sets each contact up: effective masses gain the joints' share
+//      sum_a (J_a . n)^2 / M, J_a = z_a x (p - o_a) over the joints that move
+//      the contact's link;
+//   4. runs the Jacobi iterations on the object and the joints together: each
+//      contact updates against the object velocity and its link's velocity
+//      (link twist w_l x p + c_l from the joints), the warp sums the object's
+//      impulse and moment, one lane per link sums that link's impulses and
+//      moments about the origin, and one lane per joint turns them into
+//      qd_a = qd*_a - z_a . sum_{links moved by a} (T_l - o_a x F_l) / M;
+//   5. integrates the object and the joints (q += h qd), and adds each
+//      contact's impulse to its pad, with the impulse-weighted relative slip
+//      velocity, normal and spin for the slip sensing.
+// At the end of a frame the fingers' kinematics at the final joint angles give
+// the pads' poses, and the slip sums give d_t and r_t.
+#include <cstddef>
+
+#include "contact.cuh"
+#include "hand.cuh"
+#include "internal.cuh"
+
+namespace ih {
+namespace {
+
+constexpr int kPdBlock = 128;                 // four environments per block
+constexpr int kPdWarps = kPdBlock / 32;
+constexpr int kPdMaxLinks = 1 + 4 * IH_MAX_FINGERS;
+constexpr int kPdMaxJoints = 4 * IH_MAX_FINGERS;
+constexpr int kPdPadsPerLink = 4;
+
+// per-warp (per-environment) records
+struct PdWarp {
+    float4 link[kPdMaxLinks][kLinkStride];    // link poses: (a, 0), (axis, 0), (quat)
+    float4 zax[kPdMaxJoints], org[kPdMaxJoints];
+    float4 tw[kPdMaxLinks][2];                // link twist: w_l, c_l (v(p) = w_l x p + c_l)
+    float4 ls[kPdMaxLinks][2];                // per link: sum lambda, sum p x lambda
+    float qd_star[kPdMaxJoints], qd[kPdMaxJoints], qj[kPdMaxJoints];
+    float padf[3 * IH_MAX_PADS];              // force sums over the frame's substeps
+    float slip[8 * IH_MAX_PADS];              // per pad: w, w vt (3), w n (3), w spin
+    unsigned short lbeg[kPdMaxLinks], lend[kPdMaxLinks];
+    unsigned char links[kPdMaxLinks];
+    int pad_;
+};
+static_assert(sizeof(PdWarp) % 16 == 0, "warp records keep 16-byte alignment");
+
+__host__ __device__ constexpr size_t pd_align16(size_t b) { return (b + 15) & ~size_t(15); }
+// block tables: pads per link and their axial intervals
+__host__ __device__ constexpr size_t pd_block_bytes() {
+    return pd_align16(kPdMaxLinks) + pd_align16(kPdMaxLinks * kPdPadsPerLink) + 2 * pd_align16(4 * IH_MAX_PADS);
+}
+// per warp: the record, then c_max contacts x 4 float4 and s_max spheres
+__host__ __device__ inline size_t pd_warp_bytes(int s_max, int c_max) {
+    return sizeof(PdWarp) + (4 * (size_t)c_max + (size_t)s_max) * sizeof(float4);
+}
+
+// the link's bounding capsule (or the palm box) inflated by the object's
+// bound and the margin, from the shared-memory link table
+__device__ __forceinline__ bool pd_link_reaches(const DevScene &sc, const DevConfig &cfg, const float4 (*L)[3],
+                                                int l, V3 x, float bound) {
+    const V3 xa = x - xyz(L[l][0]);
+    if (l == 0) {
+        const float4 qq = L[0][2];
+        const V3 cl = qrot_inv({qq.x, qq.y, qq.z, qq.w}, xa);
+        const V3 k3 = mk(fminf(fmaxf(cl.x, -sc.palm_hx), sc.palm_hx), fminf(fmaxf(cl.y, -sc.palm_hy), sc.palm_hy),
+                         fminf(fmaxf(cl.z, -sc.palm_hz), sc.palm_hz));
+        const V3 dd = cl - k3;
+        const float reach = bound + cfg.margin;
+        return dot(dd, dd) < reach * reach;
+    }
+    const V3 ld = xyz(L[l][1]);
+    const float t = fminf(fmaxf(dot(xa, ld), 0.0f), sc.link_len);
+    const V3 dd = xa - ld * t;
+    const float reach = bound + sc.link_rad + cfg.margin;
+    return dot(dd, dd) < reach * reach;
+}
+
+// the fingers' kinematics at the warp's joint angles W.qj (one lane per finger)
+__device__ __forceinline__ void pd_fk(const DevScene &sc, PdWarp &W, int lane) {
+    if (lane == 0) {   // palm: identity pose at the origin
+        W.link[0][0] = make_float4(0, 0, 0, 0);
+        W.link[0][1] = make_float4(1, 0, 0, 0);
+        W.link[0][2] = make_float4(1, 0, 0, 0);
+    }
+    if (lane < sc.n_fingers) {
+        const float qf[4] = {W.qj[4 * lane], W.qj[4 * lane + 1], W.qj[4 * lane + 2], W.qj[4 * lane + 3]};
+        finger_fk(sc, lane, qf, &W.link[1 + 4 * lane][0], &W.zax[4 * lane], &W.org[4 * lane]);
+    }
+}
+
+// twist of link l (>= 1) from the joint velocities of its finger
+__device__ __forceinline__ void pd_twist(PdWarp &W, int l) {
+    V3 wl = mk(0, 0, 0), cl = mk(0, 0, 0);
+    if (l >= 1) {
+        const int f = (l - 1) >> 2, j = (l - 1) & 3;
+        for (int a = 0; a <= j; ++a) {
+            const int ja = 4 * f + a;
+            const V3 z = xyz(W.zax[ja]);
+            const float qd = W.qd[ja];
+            wl = wl + z * qd;
+            cl = cl - cross(z, xyz(W.org[ja])) * qd;
+        }
+    }
+    W.tw[l][0] = make_float4(wl.x, wl.y, wl.z, 0.0f);
+    W.tw[l][1] = make_float4(cl.x, cl.y, cl.z, 0.0f);
+}
+
+__global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevScene &sc = a.sc;
+    const DevConfig &cfg = a.cfg;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads, D = sc.n_joints, F = sc.n_fingers;
+    const float h = cfg.h, inv_h = 1.0f / h, inv_L = 1.0f / sc.link_len;
+    const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
+    const float Mj = cfg.armature + h * cfg.kd + h * h * cfg.kp, inv_Mj = 1.0f / Mj;
+    const int cap = cfg.c_max;
+
+    unsigned char *pl_cnt = smem;
+    unsigned char *pl_id = smem + pd_align16(kPdMaxLinks);
+    float *p_s0 = reinterpret_cast<float *>(smem + pd_align16(kPdMaxLinks) + pd_align16(kPdMaxLinks * kPdPadsPerLink));
+    float *p_s1 = p_s0 + IH_MAX_PADS;
+    unsigned char *wbase = smem + pd_block_bytes() + wid * pd_warp_bytes(s_max, cap);
+    PdWarp &W = *reinterpret_cast<PdWarp *>(wbase);
+    // contacts: [0] (r, 0), [1] (n, link | pad << 8 | sphere << 16), [2] (b, 1/k_n, 1/k_t, 0), [3] lambda
+    float4 (*stage)[4] = reinterpret_cast<float4 (*)[4]>(wbase + sizeof(PdWarp));
+    float4 *sph = &stage[cap][0];
+
+    if (threadIdx.x < kPdMaxLinks) {
+        int c = 0;
+        for (int p = 0; p < P && c < kPdPadsPerLink; ++p)
+            if (__ldg(sc.pad_link + p) == (int)threadIdx.x) pl_id[threadIdx.x * kPdPadsPerLink + c++] = (unsigned char)p;
+        pl_cnt[threadIdx.x] = (unsigned char)c;
+    }
+    for (int p = threadIdx.x; p < P; p += kPdBlock) {
+        p_s0[p] = __ldg(sc.pad_s0 + p);
+        p_s1[p] = __ldg(sc.pad_s1 + p);
+    }
+    __syncthreads();
+
+    unsigned long long work[6] = {0, 0, 0, 0, 0, 0};
+    for (int slot = blockIdx.x * kPdWarps + wid; slot < a.N; slot += gridDim.x * kPdWarps) {
+        const int env = a.order ? __ldg(a.order + slot) : slot;
+        int st = a.status[env];
+        const float4 P0 = a.pose[2 * env], P1 = a.pose[2 * env + 1];
+        const float4 V0 = a.vel[2 * env], V1 = a.vel[2 * env + 1];
+        const float2 th = a.params[env];
+        const int shp = a.shape[env];
+        const int iters = a.iters[env];
+        V3 x = xyz(P0);
+        Q4 q = {P1.x, P1.y, P1.z, P1.w};
+        V3 v = xyz(V0), w = xyz(V1);
+        const float m = th.x, mu = th.y, inv_m = 1.0f / m;
+        const int sfirst = __ldg(sc.shape_first + shp), NS = __ldg(sc.shape_count + shp);
+        const float bound = __ldg(sc.shape_bound + shp);
+        for (int k = lane; k < D; k += 32) {
+            W.qj[k] = a.qj[(size_t)env * D + k];
+            W.qd[k] = a.qdj[(size_t)env * D + k];
+        }
+        __syncwarp();
+
+        for (int fr = 0; fr < a.n_frames; ++fr) {
+            for (int k = lane; k < 3 * P; k += 32) W.padf[k] = 0.0f;
+            for (int k = lane; k < 8 * P; k += 32) W.slip[k] = 0.0f;
+            const int frame = a.frame0 + fr;
+            const bool skip = (st & kDiverged) != 0;
+            for (int s = 0; s < ns && !skip; ++s) {
+                // -- 1. the hand at the substep start; the joints under the PD force alone
+                pd_fk(sc, W, lane);
+                const float frac = (float)(s + 1) / (float)ns;
+                for (int k = lane; k < D; k += 32) {
+                    const float u0 = __ldg(a.cmd + (size_t)frame * D + k), u1 = __ldg(a.cmd + (size_t)(frame + 1) * D + k);
+                    const float u = u0 + frac * (u1 - u0);
+                    W.qd_star[k] = (cfg.armature * W.qd[k] + h * cfg.kp * (u - W.qj[k])) * inv_Mj;
+                }
+                const V3 v_pred = v + grav;
+                const V3 w_pred = w;
+                const M3 R = qmat(q);
+                S6 Jb;
+                Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
+                Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
+                Jb.xz = __ldg(sc.shape_jinv + 6 * shp + 4); Jb.yz = __ldg(sc.shape_jinv + 6 * shp + 5);
+                const S6 Wi = world_inv_inertia(R, Jb, inv_m);
+                for (int j = lane; j < NS; j += 32) {
+                    const float4 sp = __ldg(sc.spheres + sfirst + j);
+                    const V3 cr = mmul(R, xyz(sp));
+                    sph[j] = make_float4(cr.x, cr.y, cr.z, sp.w);
+                }
+                __syncwarp();
+                for (int k = lane; k < D; k += 32) W.qd[k] = W.qd_star[k];
+
+                // -- 2. cull links, then every (surviving link, sphere) pair in pair order
+                const unsigned ml = __ballot_sync(0xffffffffu, lane < Lk && pd_link_reaches(sc, cfg, W.link, lane, x, bound));
+                const int nsurv = __popc(ml);
+                if (lane < Lk && ((ml >> lane) & 1u)) W.links[__popc(ml & ((1u << lane) - 1u))] = (unsigned char)lane;
+                __syncwarp();
+                const int npairs = nsurv * NS;
+                int nc = 0;
+                for (int p0 = 0; p0 < npairs; p0 += 32) {
+                    const int p = p0 + lane;
+                    bool hit = false;
+                    Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
+                    V3 r = mk(0, 0, 0);
+                    int l = 0, j = 0;
+                    if (p < npairs) {
+                        const int li = p / NS;
+                        j = p - li * NS;
+                        l = W.links[li];
+                        const float4 sp = sph[j];
+                        const V3 cr = xyz(sp);
+                        const float4 A0 = W.link[l][0], Aq = W.link[l][2];
+                        const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+                        if (l == 0) {
+                            hh = hit_box(x + cr, sp.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                        } else {
+                            hh = hit_capsule((x - xyz(A0)) + cr, sp.w, xyz(W.link[l][1]), sc.link_len, inv_L,
+                                             sc.link_rad, lq);
+                        }
+                        r = cr - hh.n * sp.w;
+                        hit = hh.gap < cfg.margin;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                    const int idx = nc + __popc(bal & ((1u << lane) - 1u));
+                    if (hit && idx < cap) {
+                        int pad = -1;
+                        const int npl = pl_cnt[l];
+                        for (int k = 0; k < npl; ++k) {
+                            const int pp = pl_id[l * kPdPadsPerLink + k];
+                            if (l == 0) { pad = pp; break; }
+                            const float s0 = p_s0[pp], s1 = p_s1[pp];
+                            if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
+                        }
+                        stage[idx][0] = make_float4(r.x, r.y, r.z, hh.gap);
+                        stage[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z,
+                                                    __int_as_float(l | ((pad & 0xff) << 8) | (j << 16)));
+                    }
+                    nc += __popc(bal);
+                }
+                __syncwarp();
+                if (nc > cap) {   // more contacts than the per-env capacity
+                    st |= IH_ENV_OVERFLOW;
+                    nc = 0;
+                }
+                if (lane == 0) {
+                    work[0] += (unsigned long long)npairs;
+                    work[1] += nc;
+                    work[2] += nc > 0 ? (unsigned long long)nc * iters : 0ull;
+                    work[3] += 1;
+                    work[4] += nc > 0 ? iters : 0;
+                }
+
+                // -- 3. contact setup; each link's contact range (empty for links without contacts)
+                if (lane < Lk) { W.lbeg[lane] = 0; W.lend[lane] = 0; }
+                __syncwarp();
+                const float trW = Wi.xx + Wi.yy + Wi.zz;
+                for (int ci = lane; ci < nc; ci += 32) {
+                    const float4 s0 = stage[ci][0], s1 = stage[ci][1];
+                    const int l = __float_as_int(s1.w) & 0xff;
+                    if (ci == 0 || (__float_as_int(stage[ci - 1][1].w) & 0xff) != l) W.lbeg[l] = (unsigned short)ci;
+                    if (ci == nc - 1 || (__float_as_int(stage[ci + 1][1].w) & 0xff) != l) W.lend[l] = (unsigned short)(ci + 1);
+                    const V3 r = xyz(s0), n = xyz(s1);
+                    const V3 rn = cross(r, n);
+                    float kn = inv_m + dot(rn, smul(Wi, rn));
+                    float trK = 3.0f * inv_m + dot(r, r) * trW - dot(r, smul(Wi, r));
+                    if (l >= 1) {   // the joints that move the link
+                        const int f = (l - 1) >> 2, jl = (l - 1) & 3;
+                        const V3 p = x + r;
+                        for (int aa = 0; aa <= jl; ++aa) {
+                            const int ja = 4 * f + aa;
+                            const V3 J = cross(xyz(W.zax[ja]), p - xyz(W.org[ja]));
+                            const float jn = dot(J, n);
+                            kn += jn * jn * inv_Mj;
+                            trK += dot(J, J) * inv_Mj;
+                        }
+                    }
+                    stage[ci][2] = make_float4(contact_bias(cfg, s0.w), 1.0f / kn, 2.0f / (trK - kn), 0.0f);
+                    stage[ci][3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+                __syncwarp();
+
+                // -- 4. Jacobi iterations over the object and the joints
+                V3 vv = v_pred, ww = w_pred;
+                if (nc > 0) {
+                    const float inv_nc = 1.0f / (float)nc;
+                    for (int it = 0; it < iters; ++it) {
+                        if (lane < Lk) pd_twist(W, lane);
+                        __syncwarp();
+                        float acc[6] = {0, 0, 0, 0, 0, 0};
+                        for (int ci = lane; ci < nc; ci += 32) {
+                            const float4 s0 = stage[ci][0], s1 = stage[ci][1], s2 = stage[ci][2], s3 = stage[ci][3];
+                            const int l = __float_as_int(s1.w) & 0xff;
+                            const V3 r = xyz(s0), n = xyz(s1);
+                            const V3 vl = cross(xyz(W.tw[l][0]), x + r) + xyz(W.tw[l][1]);
+                            const V3 cc = vl - n * s2.x;
+                            const V3 lam = update_contact(xyz(s3), r, n, cc, s2.y, s2.z, vv, ww, mu, inv_nc);
+                            stage[ci][3] = make_float4(lam.x, lam.y, lam.z, 0.0f);
+                            const V3 tq = cross(r, lam);
+                            acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
+                            acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                        }
+                        width_sum6<32>(acc, 0xffffffffu, lane);
+                        vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
+                        ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
+                        __syncwarp();
+                        if (lane >= 1 && lane < Lk) {   // per link: sum lambda, sum p x lambda
+                            V3 Fl = mk(0, 0, 0), Tl = mk(0, 0, 0);
+                            const int e = W.lend[lane];
+                            for (int ci = W.lbeg[lane]; ci < e; ++ci) {
+                                const V3 lam = xyz(stage[ci][3]);
+                                Fl = Fl + lam;
+                                Tl = Tl + cross(x + xyz(stage[ci][0]), lam);
+                            }
+                            W.ls[lane][0] = make_float4(Fl.x, Fl.y, Fl.z, 0.0f);
+                            W.ls[lane][1] = make_float4(Tl.x, Tl.y, Tl.z, 0.0f);
+                        }
+                        __syncwarp();
+                        if (lane < D) {   // qd_a = qd*_a - z_a . sum_{links at or beyond a} (T_l - o_a x F_l) / M
+                            const int f = lane >> 2, ja = lane & 3;
+                            V3 Fs = mk(0, 0, 0), Ts = mk(0, 0, 0);
+                            for (int jl = ja; jl < 4; ++jl) {
+                                const int l = 1 + 4 * f + jl;
+                                Fs = Fs + xyz(W.ls[l][0]);
+                                Ts = Ts + xyz(W.ls[l][1]);
+                            }
+                            const float g = dot(xyz(W.zax[lane]), Ts - cross(xyz(W.org[lane]), Fs));
+                            W.qd[lane] = W.qd_star[lane] - g * inv_Mj;
+                        }
+                        __syncwarp();
+                    }
+                }
+                v = vv;
+                w = ww;
+
+                // -- 5. integrate the object and the joints (contact points stay
+                //       those of the substep start: p = x_s + r)
+                const V3 x_s = x;
+                x = x + v * h;
+                {
+                    const float wn = sqrtf(dot(w, w));
+                    float sn, cs;
+                    sincosf(0.5f * wn * h, &sn, &cs);
+                    const float kq = (wn > 0.0f) ? sn / wn : 0.5f * h;
+                    q = qnorm(qmul({cs, w.x * kq, w.y * kq, w.z * kq}, q));
+                }
+                if (lane < Lk) pd_twist(W, lane);   // the links' final velocities, for the slip sensing
+                __syncwarp();
+                for (int k = lane; k < D; k += 32) W.qj[k] += h * W.qd[k];
+                // pads: force -lambda / h per contact, and the slip sums weighted
+                // by the normal impulse
+                for (int p = lane; p < P; p += 32) {
+                    const int l = __ldg(sc.pad_link + p);
+                    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+                    float sw = 0.0f, s1x = 0.0f, s1y = 0.0f, s1z = 0.0f, snx = 0.0f, sny = 0.0f, snz = 0.0f, ssp = 0.0f;
+                    const V3 wl = xyz(W.tw[l][0]), cl = xyz(W.tw[l][1]);
+                    const int e = W.lend[l];
+                    for (int ci = W.lbeg[l]; ci < e; ++ci) {
+                        if (((__float_as_int(stage[ci][1].w) >> 8) & 0xff) != p) continue;
+                        const V3 lam = xyz(stage[ci][3]), r = xyz(stage[ci][0]), n = xyz(stage[ci][1]);
+                        fx -= lam.x * inv_h; fy -= lam.y * inv_h; fz -= lam.z * inv_h;
+                        const float ln = dot(lam, n);
+                        if (!(ln > 0.0f)) continue;
+                        const V3 vrel = (v + cross(w, r)) - (cross(wl, x_s + r) + cl);
+                        const V3 vt = vrel - n * dot(vrel, n);
+                        const float spin = dot(w - wl, n);
+                        sw += ln;
+                        s1x += ln * vt.x; s1y += ln * vt.y; s1z += ln * vt.z;
+                        snx += ln * n.x; sny += ln * n.y; snz += ln * n.z;
+                        ssp += ln * spin;
+                    }
+                    W.padf[3 * p] += fx; W.padf[3 * p + 1] += fy; W.padf[3 * p + 2] += fz;
+                    float *A = W.slip + 8 * p;
+                    A[0] += sw; A[1] += s1x; A[2] += s1y; A[3] += s1z; A[4] += snx; A[5] += sny; A[6] += snz; A[7] += ssp;
+                }
+                __syncwarp();
+            }
+            if (!skip) {
+                bool fin = all_finite(x, q, v, w);
+                for (int k = lane; k < D; k += 32) fin = fin && isfinite(W.qj[k]) && isfinite(W.qd[k]);
+                fin = __all_sync(0xffffffffu, fin);
+                if (!fin) st |= IH_ENV_NONFINITE;
+                else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
+            }
+        }
+        // the observation of the last frame: forces, pad poses, slip
+        pd_fk(sc, W, lane);
+        __syncwarp();
+        const float inv_ns = 1.0f / (float)ns;
+        for (int k = lane; k < 3 * P; k += 32) a.forces[(size_t)env * P * 3 + k] = W.padf[k] * inv_ns;
+        for (int p = lane; p < P; p += 32) {
+            const int l = __ldg(sc.pad_link + p);
+            const float4 A0 = W.link[l][0], Aq = W.link[l][2];
+            const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+            V3 c;
+            if (l == 0) {
+                c = xyz(A0) + qrot(lq, mk(0, 0, sc.palm_hz));
+            } else {
+                const float s1 = fminf(p_s1[p], 1.0f), s0 = fmaxf(p_s0[p], 0.0f);
+                c = xyz(A0) + qrot(lq, mk(0.5f * (s0 + s1) * sc.link_len, 0, 0));
+            }
+            a.pad_pose[2 * ((size_t)env * P + p)] = make_float4(c.x, c.y, c.z, 0.0f);
+            a.pad_pose[2 * ((size_t)env * P + p) + 1] = Aq;
+            const float *S = W.slip + 8 * p;
+            float dx = 0.0f, dy = 0.0f;
+            int flags = 0;
+            if (S[0] > 0.0f) {
+                const float iw = 1.0f / S[0];
+                const V3 vt = mk(S[1], S[2], S[3]) * iw;
+                V3 nb = mk(S[4], S[5], S[6]);
+                nb = nb * rsqrtf(dot(nb, nb));
+                const float spin = S[7] * iw;
+                if (sqrtf(dot(vt, vt)) > cfg.v_slip) {
+                    const V3 ax = xyz(W.link[l][1]);
+                    V3 e1 = ax - nb * dot(ax, nb);
+                    e1 = e1 * rsqrtf(dot(e1, e1));
+                    const V3 e2 = cross(nb, e1);
+                    const float d1 = dot(vt, e1), d2 = dot(vt, e2), idn = rsqrtf(d1 * d1 + d2 * d2);
+                    dx = d1 * idn;
+                    dy = d2 * idn;
+                    flags |= 1;
+                }
+                if (fabsf(spin) > cfg.w_slip) flags |= (spin > 0.0f) ? 6 : 2;
+            }
+            a.slip[(size_t)env * P + p] = make_float4(dx, dy, __int_as_float(flags), 0.0f);
+        }
+        for (int k = lane; k < D; k += 32) {
+            a.qj[(size_t)env * D + k] = W.qj[k];
+            a.qdj[(size_t)env * D + k] = W.qd[k];
+        }
+        if (lane == 0) {
+            a.pose[2 * env] = make_float4(x.x, x.y, x.z, 0.0f);
+            a.pose[2 * env + 1] = make_float4(q.w, q.x, q.y, q.z);
+            a.vel[2 * env] = make_float4(v.x, v.y, v.z, 0.0f);
+            a.vel[2 * env + 1] = make_float4(w.x, w.y, w.z, 0.0f);
+            a.status[env] = st;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && a.work)
+        for (int k = 0; k < 6; ++k)
+            if (work[k]) atomicAdd(a.work + k, work[k]);
+}
+
+// every environment's hand at rest at q0 (D values; null: zero)
+__global__ void hand_rest_kernel(int N, int D, const float *q0, float *qj, float *qdj) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)N * D) return;
+    qj[k] = q0 ? q0[k % D] : 0.0f;
+    qdj[k] = 0.0f;
+}
+
+}  // namespace
+
+cudaError_t launch_hand_rest(int N, int D, const float *q0, float *qj, float *qdj, cudaStream_t s) {
+    const size_t n = (size_t)N * D;
+    if (n == 0) return cudaSuccess;
+    hand_rest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, D, q0, qj, qdj);
+    return cudaGetLastError();
+}
+
+size_t pd_step_smem_bytes(int s_max, int c_max) { return pd_block_bytes() + kPdWarps * pd_warp_bytes(s_max, c_max); }
+
+cudaError_t pd_step_prepare(int s_max, int c_max) {
+    const size_t bytes = pd_step_smem_bytes(s_max, c_max);
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(pd_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// one warp per environment, at most four blocks per SM (grid-stride beyond)
+int pd_step_grid(int N, int sms) {
+    const int need = (N + kPdWarps - 1) / kPdWarps;
+    return need < 4 * sms ? need : 4 * sms;
+}
+
+cudaError_t launch_pd_step(const PdArgs &a, int grid, int s_max, cudaStream_t s) {
+    pd_step_kernel<<<grid, kPdBlock, pd_step_smem_bytes(s_max, a.cfg.c_max), s>>>(a, s_max);
+    return cudaGetLastError();
+}
+
+}  // namespace ih

@@ -41,7 +41,11 @@ class IHConfig(C.Structure):
                 ("beta", C.c_float), ("slop", C.c_float), ("vmax", C.c_float),
                 ("gravity", C.c_float * 3), ("tau", C.c_float), ("w_force", C.c_float),
                 ("w_contact", C.c_float), ("c_max", C.c_int32), ("escape_radius", C.c_float),
-                ("warm_start", C.c_int32)]
+                ("warm_start", C.c_int32), ("hand", C.c_int32), ("kp", C.c_float), ("kd", C.c_float),
+                ("armature", C.c_float), ("v_slip", C.c_float), ("w_slip", C.c_float),
+                ("w_full", C.c_float * 10)]
+
+HANDS = {"kinematic": 0, "pd": 1}
 
 
 class IHOptConfig(C.Structure):
@@ -60,7 +64,8 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
            "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
-           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_get_warm_cache"]
+           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_get_warm_cache",
+           "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full"]
 
 
 def lib() -> C.CDLL:
@@ -81,6 +86,10 @@ def lib() -> C.CDLL:
             "sim_set_state": [P, P, P, P, P, P],
             "sim_get_state": [P, P, P, P, P],
             "sim_get_warm_cache": [P, P, P],
+            "sim_read_observation": [P, P, P, P],
+            "sim_set_hand": [P, P, P],
+            "sim_get_hand": [P, P, P],
+            "cost_eval_full": [P, P, P, P, P, P, P, P],
             "sim_step": [P, I, I],
             "sim_read_sensors": [P, P, P],
             "cost_eval": [P, P, P, P, P],
@@ -158,13 +167,15 @@ class Sim:
                              sim_cfg.margin, sim_cfg.beta, sim_cfg.slop, sim_cfg.vmax,
                              (C.c_float * 3)(*sim_cfg.gravity), sim_cfg.tau, sim_cfg.w_force,
                              sim_cfg.w_contact, sim_cfg.c_max, sim_cfg.escape_radius,
-                             int(bool(sim_cfg.warm_start)))
+                             int(bool(sim_cfg.warm_start)), HANDS[sim_cfg.hand], sim_cfg.kp, sim_cfg.kd,
+                             sim_cfg.armature, sim_cfg.v_slip, sim_cfg.w_slip, (C.c_float * 10)(*sim_cfg.w_full))
         self.n = n_envs
         self.n_pads = scene.n_pads
         self.n_joints = scene.n_joints
         self.max_frames = max_frames
         self.c_max = sim_cfg.c_max
         self.warm_start = bool(sim_cfg.warm_start)
+        self.pd = sim_cfg.hand == "pd"
         h = C.c_void_p()
         rc = L.sim_create(C.byref(self._scene), C.byref(self._cfg), seed, _stream(), C.byref(h))
         if rc != IH_OK:
@@ -244,6 +255,43 @@ class Sim:
         _check(argmin, torch.int32, (1,), "argmin")
         _check(est_pose, torch.float32, (8,), "est_pose")
         self._call("cost_eval", _ptr(obs), _ptr(cost_mean), _ptr(argmin), _ptr(est_pose))
+
+    def sim_read_observation(self, q=None, pad_pose=None, slip=None):
+        """PD hand: (q float32[N, D], pad_pose float32[N, P, 8], slip float32[N, P, 4]) of the last frame."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if q is None:
+            q = torch.empty((self.n, self.n_joints), dtype=torch.float32, device=dev)
+        if pad_pose is None:
+            pad_pose = torch.empty((self.n, self.n_pads, 8), dtype=torch.float32, device=dev)
+        if slip is None:
+            slip = torch.empty((self.n, self.n_pads, 4), dtype=torch.float32, device=dev)
+        self._call("sim_read_observation", _ptr(q), _ptr(pad_pose), _ptr(slip))
+        return q, pad_pose, slip
+
+    def sim_set_hand(self, q, qd=None):
+        _check(q, torch.float32, (self.n, self.n_joints), "q")
+        _check(qd, torch.float32, (self.n, self.n_joints), "qd")
+        self._call("sim_set_hand", _ptr(q), _ptr(qd))
+
+    def sim_get_hand(self):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        q = torch.empty((self.n, self.n_joints), dtype=torch.float32, device=dev)
+        qd = torch.empty_like(q)
+        self._call("sim_get_hand", _ptr(q), _ptr(qd))
+        return q, qd
+
+    def cost_eval_full(self, q, pad_pose, forces, slip, cost_mean=None, argmin=None, est_pose=None):
+        """PD hand: the full ten-term cost against the ground truth's observation
+        (q [D], pad_pose [P, 8], forces [P, 3], slip [P, 4])."""
+        _check(q, torch.float32, (self.n_joints,), "q")
+        _check(pad_pose, torch.float32, (self.n_pads, 8), "pad_pose")
+        _check(forces, torch.float32, (self.n_pads, 3), "forces")
+        _check(slip, torch.float32, (self.n_pads, 4), "slip")
+        _check(cost_mean, torch.float64, (self.n,), "cost_mean")
+        _check(argmin, torch.int32, (1,), "argmin")
+        _check(est_pose, torch.float32, (8,), "est_pose")
+        self._call("cost_eval_full", _ptr(q), _ptr(pad_pose), _ptr(forces), _ptr(slip), _ptr(cost_mean),
+                   _ptr(argmin), _ptr(est_pose))
 
     def sim_step_track(self, frame: int, obs, cost_mean=None, argmin=None, est_pose=None):
         _check(obs, torch.float32, (self.n_pads, 3), "obs")

@@ -37,6 +37,12 @@ class Tracker:
         self.gt_pose = torch.zeros((wl.frames, 8), dtype=torch.float32, device=self.dev)
         self.argmin = torch.zeros((wl.frames,), dtype=torch.int32, device=self.dev)
         self.est = torch.zeros((wl.frames, 8), dtype=torch.float32, device=self.dev)
+        self.pd = self.sim.pd
+        if self.pd:   # the ground truth's full observation of every frame
+            D = wl.scene.n_joints
+            self.obs_q = torch.zeros((wl.frames, D), dtype=torch.float32, device=self.dev)
+            self.obs_pp = torch.zeros((wl.frames, P, 8), dtype=torch.float32, device=self.dev)
+            self.obs_slip = torch.zeros((wl.frames, P, 4), dtype=torch.float32, device=self.dev)
 
     def prepare(self):
         """Commands for every frame, the ground-truth run, and the initial samples."""
@@ -56,6 +62,11 @@ class Tracker:
             self.gt.sim_read_sensors(f_buf, st_buf)
             self.obs[f].copy_(f_buf[0])
             self.gt_pose[f].copy_(self.gt.sim_get_state()[0][0])
+            if self.pd:
+                q, pp, slip = self.gt.sim_read_observation()
+                self.obs_q[f].copy_(q[0])
+                self.obs_pp[f].copy_(pp[0])
+                self.obs_slip[f].copy_(slip[0])
         self.sim.sim_sample_initial(wl.nominal_pose, wl.init.sigma_p, wl.init.sigma_r,
                                     wl.init.m_range, wl.init.mu_range)
         n = self.n
@@ -78,6 +89,18 @@ class Tracker:
         f0 = w * T
         self.sim.sim_track_window(f0, self.obs[f0:f0 + T], self.wl.opt, w, self.est[f0:f0 + T],
                                   self.argmin[f0:f0 + T])
+
+    def window_pd(self, w: int):
+        """A window with the PD-driven hand: per frame one step launch and the
+        full ten-term cost against the ground truth's observation (argmin and
+        estimate), then the optimizer update."""
+        T = self.T
+        for k in range(T):
+            f = w * T + k
+            self.sim.sim_step(f, 1)
+            self.sim.cost_eval_full(self.obs_q[f], self.obs_pp[f], self.obs[f], self.obs_slip[f], None,
+                                    self.argmin[f:f + 1], self.est[f])
+        self.sim.optimizer_update(self.wl.opt, w)
 
     def window_eye(self, w: int):
         """The identity baseline (EYE, Sec. IV): the window's frames stepped,

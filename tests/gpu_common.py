@@ -37,6 +37,9 @@ def sim32(sim: W.SimConfig) -> W.SimConfig:
     for name in ["frame_dt", "margin", "beta", "slop", "vmax", "tau", "w_force", "w_contact", "escape_radius"]:
         setattr(c, name, float(np.float32(getattr(c, name))))
     c.gravity = tuple(float(np.float32(g)) for g in c.gravity)
+    for name in ["kp", "kd", "armature", "v_slip", "w_slip"]:
+        setattr(c, name, float(np.float32(getattr(c, name))))
+    c.w_full = tuple(float(np.float32(w)) for w in c.w_full)
     return c
 
 
