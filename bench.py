@@ -550,21 +550,22 @@ def warm_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, n
 # the same way (FMA = 2, a sincos = 20): per env-substep the fingers'
 # kinematics (570 per finger: quaternion chain, link axes, joint axes), the PD
 # prediction (9 per joint), link culling (25 per link) and the object's
-# prediction and inertia (145); per pair tested 30; per contact the set-up with
+# prediction and inertia (145); per cluster test 25 (centre to world and the
+# reach test); per pair tested 30; per contact the set-up with
 # its joints' share (140) and the pad and slip sums (45); per contact-iteration
 # the update against the link twist and the per-link sums (103); per
 # env-iteration the link twists (52 per link) and the joint updates (36 per joint).
 def pd_flops(work, scene, spheres):
     F, D, Lk = scene.n_fingers, scene.n_joints, scene.n_links
     per_substep = 570 * F + 9 * D + 25 * Lk + 145 + 15 * spheres
-    return (work["env_substeps"] * per_substep + work["pairs"] * 30 + work["contacts"] * 185 +
+    return (work["env_substeps"] * per_substep + work["cluster_tests"] * 25 + work["pairs"] * 30 + work["contacts"] * 185 +
             work["contact_iters"] * 103 + work["env_iters"] * (52 * Lk + 36 * D + 30))
 
 
 def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, windows=5, budget_s=10.0,
              speed_only=False):
     """The PD-driven hand (joints as state, full observation, full cost):
-    - throughput on the cylinder trajectory at N = n_envs: per window of T
+    - throughput on the cylinder trajectory at N = n_envs and 8 n_envs: per window of T
       frames one PD step launch and one full-cost launch per frame and the
       optimizer, timed with CUDA events (L2 flushed before every window), the
       step launches separately, their counted work against the FP32 peak;
@@ -580,50 +581,54 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    wl = W.make_workload("tracking_cyl64", n_envs=n_envs, frames=frames, seed=seeds[0])
-    wl.sim = dataclasses.replace(wl.sim, hand="pd")
-    tr = tracking.Tracker(wl, n_envs=n_envs)
-    tr.prepare()
-    T = tr.T
-    for w in range(2):   # warm-up windows
-        tr.window_pd(w)
-    torch.cuda.synchronize()
-    tr.sim.sim_work_counters(reset=True)
-    win_ms, step_ms = [], []
-    st_stream = torch.cuda.current_stream()
-    for w in range(2, 2 + windows):
-        flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T + 2)]
-        ev[0].record(st_stream)
-        for k in range(T):
-            f = w * T + k
-            ev[1 + 2 * k].record(st_stream)
-            tr.sim.sim_step(f, 1)
-            ev[2 + 2 * k].record(st_stream)
-            tr.sim.cost_eval_full(tr.obs_q[f], tr.obs_pp[f], tr.obs[f], tr.obs_slip[f], None,
-                                  tr.argmin[f:f + 1], tr.est[f])
-        tr.sim.optimizer_update(wl.opt, w)
-        ev[-1].record(st_stream)
+
+    def throughput_at(n):
+        wl = W.make_workload("tracking_cyl64", n_envs=n, frames=frames, seed=seeds[0])
+        wl.sim = dataclasses.replace(wl.sim, hand="pd")
+        tr = tracking.Tracker(wl, n_envs=n)
+        tr.prepare()
+        T = tr.T
+        for w in range(2):   # warm-up windows
+            tr.window_pd(w)
         torch.cuda.synchronize()
-        win_ms.append(ev[0].elapsed_time(ev[-1]))
-        step_ms.append(sum(ev[1 + 2 * k].elapsed_time(ev[2 + 2 * k]) for k in range(T)) / T)
-    work = tr.sim.sim_work_counters()
-    tr.close()
-    n_launch = windows * T
-    flop = pd_flops(work, wl.scene, max(len(x) for x in wl.scene.shapes)) / n_launch
-    ms_win, ms_step = statistics.median(win_ms), statistics.median(step_ms)
-    clocks_max = 2070.0
-    peak = 152 * 128 * 2 * clocks_max * 1e6 / 1e12
-    achieved = flop / (ms_step / 1e3) / 1e12
-    throughput = {"env_steps_per_s": n_envs * T / (ms_win / 1e3), "ms_per_window": ms_win,
-                  "step_kernel_ms_per_frame": ms_step, "tracking_frames_per_s": T / (ms_win / 1e3),
-                  "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                               "frac": achieved / peak, "flop_per_launch": flop,
-                               "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
-                  "work_per_launch": {k: v / n_launch for k, v in work.items()}}
+        tr.sim.sim_work_counters(reset=True)
+        win_ms, step_ms = [], []
+        st_stream = torch.cuda.current_stream()
+        for w in range(2, 2 + windows):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T + 2)]
+            ev[0].record(st_stream)
+            for k in range(T):
+                f = w * T + k
+                ev[1 + 2 * k].record(st_stream)
+                tr.sim.sim_step(f, 1)
+                ev[2 + 2 * k].record(st_stream)
+                tr.sim.cost_eval_full(tr.obs_q[f], tr.obs_pp[f], tr.obs[f], tr.obs_slip[f], None,
+                                      tr.argmin[f:f + 1], tr.est[f])
+            tr.sim.optimizer_update(wl.opt, w)
+            ev[-1].record(st_stream)
+            torch.cuda.synchronize()
+            win_ms.append(ev[0].elapsed_time(ev[-1]))
+            step_ms.append(sum(ev[1 + 2 * k].elapsed_time(ev[2 + 2 * k]) for k in range(T)) / T)
+        work = tr.sim.sim_work_counters()
+        tr.close()
+        n_launch = windows * T
+        flop = pd_flops(work, wl.scene, max(len(x) for x in wl.scene.shapes)) / n_launch
+        ms_win, ms_step = statistics.median(win_ms), statistics.median(step_ms)
+        peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+        achieved = flop / (ms_step / 1e3) / 1e12
+        return T, {"n_envs": n, "env_steps_per_s": n * T / (ms_win / 1e3), "ms_per_window": ms_win,
+                   "step_kernel_ms_per_frame": ms_step, "tracking_frames_per_s": T / (ms_win / 1e3),
+                   "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                "frac": achieved / peak, "flop_per_launch": flop,
+                                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                   "work_per_launch": {k: v / n_launch for k, v in work.items()}}
+
+    T, throughput = throughput_at(n_envs)
+    _, throughput_large = throughput_at(8 * n_envs)
     if speed_only:
         del flush
-        return {"throughput": throughput}
+        return {"throughput": throughput, "throughput_large_n": throughput_large}
     # the oracle's PD step, bounded sample
     n_s = 16
     wl_s = W.make_workload("tracking_cyl64", n_envs=n_s, frames=frames, seed=seeds[0])
@@ -664,7 +669,7 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
     del flush
     torch.cuda.empty_cache()
     return {"workload": f"tracking_cyl64 with the PD hand, N = {n_envs}, windows of {T} frames",
-            "throughput": throughput, "cpu_baseline": cpu,
+            "throughput": throughput, "throughput_large_n": throughput_large, "cpu_baseline": cpu,
             "tracking": {"n_envs": n_envs, "frames": frames, "seeds": list(seeds), **track}}
 
 

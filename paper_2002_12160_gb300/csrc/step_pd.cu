@@ -12,8 +12,9 @@
 //      (one lane per finger) into shared memory, with every joint's axis and
 //      origin, and predicts the joints' velocities under the PD force alone:
 //      qd* = (I qd + h kp (u - q)) / M, M = I + h kd + h^2 kp (implicit PD);
-//   2. culls links against the object's bounding sphere, tests every
-//      (surviving link, sphere) pair and compacts contacts in pair order;
+//   2. culls links against the object's bounding sphere, then (link, 8-sphere
+//      cluster) pairs by the clusters' enclosing spheres, tests the spheres of
+//      the surviving pairs and compacts contacts in pair order;
 //   3. sets each contact up: effective masses gain the joints' share
 //      sum_a (J_a . n)^2 / M, J_a = z_a x (p - o_a) over the joints that move
 //      the contact's link;
@@ -55,6 +56,8 @@ struct PdWarp {
     unsigned short lbeg[kPdMaxLinks], lend[kPdMaxLinks];
     unsigned char links[kPdMaxLinks];
     int pad_;
+    float4 clc[IH_MAX_SPHERES / kCluster];    // cluster centres (world-rotated, relative to x), radius
+    unsigned short clp[kPdMaxLinks * (IH_MAX_SPHERES / kCluster)];   // surviving (link, cluster) pairs
 };
 static_assert(sizeof(PdWarp) % 16 == 0, "warp records keep 16-byte alignment");
 
@@ -167,6 +170,8 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
         const float m = th.x, mu = th.y, inv_m = 1.0f / m;
         const int sfirst = __ldg(sc.shape_first + shp), NS = __ldg(sc.shape_count + shp);
         const float bound = __ldg(sc.shape_bound + shp);
+        const int ncl = (NS + kCluster - 1) / kCluster;
+        const int cfirst = __ldg(sc.cl_first + shp);
         for (int k = lane; k < D; k += 32) {
             W.qj[k] = a.qj[(size_t)env * D + k];
             W.qd[k] = a.qdj[(size_t)env * D + k];
@@ -200,15 +205,38 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
                     const V3 cr = mmul(R, xyz(sp));
                     sph[j] = make_float4(cr.x, cr.y, cr.z, sp.w);
                 }
+                for (int k = lane; k < ncl; k += 32) {
+                    const float4 cl = __ldg(sc.clusters + cfirst + k);
+                    const V3 cr = mmul(R, xyz(cl));
+                    W.clc[k] = make_float4(cr.x, cr.y, cr.z, cl.w);
+                }
                 __syncwarp();
                 for (int k = lane; k < D; k += 32) W.qd[k] = W.qd_star[k];
 
-                // -- 2. cull links, then every (surviving link, sphere) pair in pair order
+                // -- 2. cull links, then (surviving link, cluster) pairs by the clusters'
+                //       enclosing spheres, then the spheres of the surviving pairs in pair order
                 const unsigned ml = __ballot_sync(0xffffffffu, lane < Lk && pd_link_reaches(sc, cfg, W.link, lane, x, bound));
                 const int nsurv = __popc(ml);
                 if (lane < Lk && ((ml >> lane) & 1u)) W.links[__popc(ml & ((1u << lane) - 1u))] = (unsigned char)lane;
                 __syncwarp();
-                const int npairs = nsurv * NS;
+                const int ncp = nsurv * ncl;
+                int nclp = 0;
+                for (int p0 = 0; p0 < ncp; p0 += 32) {
+                    const int p = p0 + lane;
+                    bool keep = false;
+                    int li = 0, k = 0;
+                    if (p < ncp) {
+                        li = p / ncl;
+                        k = p - li * ncl;
+                        const float4 cc = W.clc[k];
+                        keep = pd_link_reaches(sc, cfg, W.link, W.links[li], x + xyz(cc), cc.w);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    if (keep) W.clp[nclp + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)((li << 8) | k);
+                    nclp += __popc(bal);
+                }
+                __syncwarp();
+                const int npairs = nclp * kCluster;
                 int nc = 0;
                 for (int p0 = 0; p0 < npairs; p0 += 32) {
                     const int p = p0 + lane;
@@ -217,9 +245,11 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
                     V3 r = mk(0, 0, 0);
                     int l = 0, j = 0;
                     if (p < npairs) {
-                        const int li = p / NS;
-                        j = p - li * NS;
-                        l = W.links[li];
+                        const int e = W.clp[p / kCluster];
+                        j = (e & 0xff) * kCluster + (p % kCluster);
+                        l = W.links[e >> 8];
+                    }
+                    if (p < npairs && j < NS) {   // (j >= NS: padding of the shape's last cluster)
                         const float4 sp = sph[j];
                         const V3 cr = xyz(sp);
                         const float4 A0 = W.link[l][0], Aq = W.link[l][2];
@@ -257,6 +287,7 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
                 }
                 if (lane == 0) {
                     work[0] += (unsigned long long)npairs;
+                    work[5] += (unsigned long long)ncp;
                     work[1] += nc;
                     work[2] += nc > 0 ? (unsigned long long)nc * iters : 0ull;
                     work[3] += 1;
