@@ -195,3 +195,52 @@ def test_pd_refuses_unsupported_calls():
     cold = start(W.make_workload("tracking_box27", n_envs=4, frames=4), n=4, frames=4)
     with pytest.raises(inhand.InhandError):
         cold.sim_read_observation()
+
+
+@pytest.mark.parametrize("v0,w0", [((0.3, 0.0, 0.0), (0.0, 0.0, 2.0)), ((0.0, -0.3, 0.0), (0.0, 0.0, -2.0))])
+def test_pd_palm_pad_slip_without_fingers(v0, w0):
+    """A hand with no fingers (no joints): a slab sliding and spinning on the
+    palm pad, one frame, against the oracle."""
+    from paper_2002_12160_gb300 import inhand
+    d = dev()
+    rows = W.slab9()
+    scene = W.ground_scene(rows)
+    cfg = dataclasses.replace(W.SimConfig(), hand="pd")
+    sim = inhand.Sim(scene, cfg, 3, 2, seed=1)
+    sim.sim_set_commands(0, torch.zeros((3, 0), dtype=torch.float32, device=d))
+    z0 = 0.01 + W.bottom_depth(rows)
+    pose = torch.tensor([[0, 0, z0 - 0.0005, 0, 1, 0, 0, 0]] * 3, dtype=torch.float32, device=d)
+    vel = torch.tensor([[*v0, 0, *w0, 0], [0.5 * v0[0], 0.5 * v0[1], 0, 0, 0, 0, 0, 0], [0] * 8],
+                       dtype=torch.float32, device=d)
+    sim.sim_set_state(pose, vel, torch.tensor([[0.1, 0.3]] * 3, dtype=torch.float32, device=d))
+    st = oracle_state(sim.sim_get_state()).hand(np.zeros(0))
+    ob, _ = O.step_pd(O.OracleScene(scene32(scene)), sim32(cfg), st, np.zeros((3, 0)), 0, 1)
+    sim.sim_step(0, 1)
+    go, status = _gpu_obs(sim)
+    np.testing.assert_array_equal(go.flags, ob.flags)
+    assert go.flags[0, 0] & 1 and go.flags[0, 0] & 2 and go.flags[2, 0] == 0
+    np.testing.assert_allclose(go.slip_d, ob.slip_d, atol=5e-3)
+    fe = np.linalg.norm(go.forces - ob.forces, axis=2)
+    assert (fe <= FORCE_REL * np.linalg.norm(ob.forces, axis=2) + FORCE_ABS).all()
+    np.testing.assert_allclose(go.pad_pose[:, 0], [[0, 0, 0.01, 1, 0, 0, 0]] * 3, atol=1e-7)
+
+
+def test_pd_overflow_and_escape_flags_match_oracle():
+    wl = _pd("tracking_cyl64", 4, 3, c_max=8)
+    sim = start(wl, n=4, frames=3)
+    pose, vel, params, _ = sim.sim_get_state()
+    pose[3, 2] = 0.29
+    vel[3, 2] = 3.0
+    q, qd = sim.sim_get_hand()
+    sim.sim_set_state(pose, vel, params)
+    sim.sim_set_hand(q, qd)
+    st = _hand_state(sim, wl.shape_id[:4].astype(np.int32), wl.iters[:4].astype(np.int32))
+    O.step_pd(O.OracleScene(scene32(wl.scene)), sim32(wl.sim), st, wl.q_traj, 0, 1)
+    sim.sim_step(0, 1)
+    status = sim.sim_get_state()[3].cpu().numpy()
+    np.testing.assert_array_equal(status, st.status)
+    assert status[3] & 2 and (status[:3] & 4).all()
+    # the flagged environments are no longer stepped
+    before = sim.sim_get_state()[0].clone()
+    sim.sim_step(1, 1)
+    assert torch.equal(sim.sim_get_state()[0], before)
