@@ -49,7 +49,7 @@ FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
 # sources (step.cu, step_kernel.cuh, contact.cuh) whose hash is recorded with it; reported as
 # null once they change.
-STEP_TRAFFIC = {"bytes_per_launch": 229120, "sources_sha256": "926988f1ffaca0be836ce2282b8815d3aff84e2908883d83e06a3ad64a199e43"}
+STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "37271d030f9cb1294acc42bf808ae68a2e9df45e7ea92fb761bbae330d0d50a2"}
 STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/step_kernel.cuh",
                 "paper_2002_12160_gb300/csrc/contact.cuh"]
 
@@ -565,10 +565,12 @@ def pd_flops(work, scene, spheres):
 def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, windows=5, budget_s=10.0,
              speed_only=False):
     """The PD-driven hand (joints as state, full observation, full cost):
-    - throughput on the cylinder trajectory at N = n_envs and 8 n_envs: per window of T
-      frames one PD step launch and one full-cost launch per frame and the
-      optimizer, timed with CUDA events (L2 flushed before every window), the
-      step launches separately, their counted work against the FP32 peak;
+    - throughput on the cylinder trajectory at N = n_envs and 8 n_envs: per
+      window one T-frame PD step launch scoring every frame with the full
+      cost, the per-frame argmin and the optimizer, timed with CUDA events
+      (L2 flushed before every window), the step launch separately with its
+      counted work against the FP32 peak; and the same window as per-frame
+      step and full-cost launches;
     - the oracle's PD step on the host, single thread, on a bounded sample;
     - tracking error (median ADD over seeded trajectories, mm) with the full
       cost, without the slip terms, and with the force and contact terms only
@@ -594,31 +596,40 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
         tr.sim.sim_work_counters(reset=True)
         win_ms, step_ms = [], []
         st_stream = torch.cuda.current_stream()
-        for w in range(2, 2 + windows):
+        for w in range(2, 2 + windows):   # the window: one T-frame step launch, argmin, optimizer
             flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T + 2)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            f0 = w * T
             ev[0].record(st_stream)
-            for k in range(T):
-                f = w * T + k
-                ev[1 + 2 * k].record(st_stream)
-                tr.sim.sim_step(f, 1)
-                ev[2 + 2 * k].record(st_stream)
-                tr.sim.cost_eval_full(tr.obs_q[f], tr.obs_pp[f], tr.obs[f], tr.obs_slip[f], None,
-                                      tr.argmin[f:f + 1], tr.est[f])
+            tr.sim.sim_step_frames_full(f0, tr.obs_q[f0:f0 + T], tr.obs_pp[f0:f0 + T], tr.obs[f0:f0 + T],
+                                        tr.obs_slip[f0:f0 + T])
+            ev[1].record(st_stream)
+            tr.sim.sim_frames_argmin(tr.est[f0:f0 + T], tr.argmin[f0:f0 + T])
             tr.sim.optimizer_update(wl.opt, w)
-            ev[-1].record(st_stream)
+            ev[2].record(st_stream)
             torch.cuda.synchronize()
-            win_ms.append(ev[0].elapsed_time(ev[-1]))
-            step_ms.append(sum(ev[1 + 2 * k].elapsed_time(ev[2 + 2 * k]) for k in range(T)) / T)
+            win_ms.append(ev[0].elapsed_time(ev[2]))
+            step_ms.append(ev[0].elapsed_time(ev[1]))
         work = tr.sim.sim_work_counters()
+        unfused = []
+        for w in range(2 + windows, 2 + 2 * windows):   # the same window as per-frame launches
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st_stream)
+            tr.window_pd_unfused(w)
+            e1.record(st_stream)
+            torch.cuda.synchronize()
+            unfused.append(e0.elapsed_time(e1))
         tr.close()
-        n_launch = windows * T
+        n_launch = windows
         flop = pd_flops(work, wl.scene, max(len(x) for x in wl.scene.shapes)) / n_launch
         ms_win, ms_step = statistics.median(win_ms), statistics.median(step_ms)
         peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
         achieved = flop / (ms_step / 1e3) / 1e12
         return T, {"n_envs": n, "env_steps_per_s": n * T / (ms_win / 1e3), "ms_per_window": ms_win,
-                   "step_kernel_ms_per_frame": ms_step, "tracking_frames_per_s": T / (ms_win / 1e3),
+                   "step_kernel_ms_per_launch": ms_step, "frames_per_launch": T,
+                   "tracking_frames_per_s": T / (ms_win / 1e3),
+                   "unfused_ms_per_window": statistics.median(unfused),
                    "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                 "frac": achieved / peak, "flop_per_launch": flop,
                                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},

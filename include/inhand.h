@@ -315,6 +315,16 @@ ih_status sim_get_hand(ih_sim *sim, float *q, float *qd);
 ih_status cost_eval_full(ih_sim *sim, const float *q, const float *pad_pose, const float *forces,
                          const float *slip, double *cost_mean, int32_t *argmin, float *est_pose);
 
+/* PD hand only: T frames from frame0 in one launch, each scored with the full
+ * cost (as cost_eval_full) against the ground truth's observation of that
+ * frame: q float[T][D], pad_pose float[T][P][8], forces float[T][P][3], slip
+ * float[T][P][4] (device; pad_pose and slip 16-byte aligned). As with
+ * sim_step_frames, sim_frames_argmin must follow (IH_ERR_STATE otherwise) and
+ * gives every frame's argmin and estimate; results equal T calls of sim_step
+ * and cost_eval_full. */
+ih_status sim_step_frames_full(ih_sim *sim, int32_t frame0, int32_t T, const float *q, const float *pad_pose,
+                               const float *forces, const float *slip);
+
 /* Score the last stepped frame against the observation (Sec. III-C, force and
  * contact-state terms; Eqs. 1-2 with the running mean of Algorithm 1):
  *   cost_i = sum_l [ w_force |c_il - o_l|^2 + w_contact ((|c_il| > tau) != (|o_l| > tau)) ]

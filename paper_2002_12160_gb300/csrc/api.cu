@@ -464,6 +464,9 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
         p.shape = s->shape; p.iters = s->iters; p.order = s->order; p.status = s->status;
         p.qj = s->qj; p.qdj = s->qdj; p.forces = s->forces; p.pad_pose = s->pad_pose; p.slip = s->slip;
         p.work = s->work;
+        p.g_q = nullptr; p.g_pose = nullptr; p.g_forces = nullptr; p.g_slip = nullptr;
+        p.c_sum = nullptr; p.c_mean = nullptr; p.cost_mean = nullptr; p.n_window = nullptr;
+        p.cm_frames = nullptr; p.pose_frames = nullptr;
         cudaError_t e = launch_pd_step(p, s->pd_grid, s->s_max, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "PD step launch");
         s->stepped = true;
@@ -611,6 +614,37 @@ ih_status sim_step_frames(ih_sim *s, int32_t frame0, int32_t T, const float *obs
     a.pose_frames = s->wf_pose;
     e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    s->stepped = true;
+    s->frames_T = T;
+    return IH_OK;
+}
+
+ih_status sim_step_frames_full(ih_sim *s, int32_t frame0, int32_t T, const float *q, const float *pad_pose,
+                               const float *forces, const float *slip) {
+    if (!s) return IH_ERR_ARG;
+    if (!s->pd) return fail(s, IH_ERR_ARG, "sim_step_frames_full needs the PD-driven hand");
+    if (ih_status rp = check_no_pending(s)) return rp;
+    if ((!q && s->n_joints > 0) || !pad_pose || !forces || !slip)
+        return fail(s, IH_ERR_ARG, "the ground truth's q, pad_pose, forces and slip are required");
+    if (!aligned16(pad_pose) || !aligned16(slip)) return fail(s, IH_ERR_ARG, "pad_pose and slip must be 16-byte aligned");
+    if (T < 1 || frame0 < 0 || frame0 + T > s->cfg.max_frames)
+        return fail(s, IH_ERR_ARG, "frames [%d, %d) outside the table", frame0, frame0 + T);
+    for (int f = frame0; f < frame0 + T; ++f)
+        if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
+    cudaError_t e = window_buffers(s, T);
+    if (e != cudaSuccess) return cuda_fail(s, e, "window buffers");
+    PdArgs p;
+    p.sc = dev_scene(s); p.cfg = s->dcfg; p.N = s->cfg.n_envs; p.cmd = s->cmd;
+    p.frame0 = frame0; p.n_frames = T; p.pose = s->pose; p.vel = s->vel; p.params = s->params;
+    p.shape = s->shape; p.iters = s->iters; p.order = s->order; p.status = s->status;
+    p.qj = s->qj; p.qdj = s->qdj; p.forces = s->forces; p.pad_pose = s->pad_pose; p.slip = s->slip;
+    p.work = s->work;
+    p.g_q = q; p.g_pose = reinterpret_cast<const float4 *>(pad_pose); p.g_forces = forces;
+    p.g_slip = reinterpret_cast<const float4 *>(slip);
+    p.c_sum = s->c_sum; p.c_mean = s->c_mean; p.cost_mean = nullptr; p.n_window = s->n_window;
+    p.cm_frames = s->wf_cm; p.pose_frames = s->wf_pose;
+    e = launch_pd_step(p, s->pd_grid, s->s_max, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "PD step launch");
     s->stepped = true;
     s->frames_T = T;
     return IH_OK;

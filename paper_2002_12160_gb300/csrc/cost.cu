@@ -9,6 +9,7 @@
 // (C_i, i) to its minimum with shuffles and leaves it in scratch; the last
 // warp to finish (atomic ticket) reduces the partials, publishes i*, copies
 // the pose of i*, advances the window count and re-arms the ticket.
+#include "full_cost.cuh"
 #include "internal.cuh"
 
 namespace ih {
@@ -29,64 +30,18 @@ __device__ __forceinline__ void warp_min(double &c, int &i) {
     }
 }
 
-// angle between two vectors, atan2(|a x b|, a . b), FP64
-__device__ __forceinline__ double angle_d(double ax, double ay, double az, double bx, double by, double bz) {
-    const double cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-    return atan2(sqrt(cx * cx + cy * cy + cz * cz), ax * bx + ay * by + az * bz);
-}
-
-// The full cost of Sec. III-C for the PD hand's observation, FP64:
-//   w1 |q - q_gt| + sum_l [ w2 |P - P_gt| + w3 angle(R^-1 R_gt)
-//     + w4 (1 - alpha) + alpha (w5 | |c| - |c_gt| | + w6 angle(c, c_gt))
-//     + w7 (1 - beta) + beta w8 angle(d, d_gt) + w9 (1 - gamma) + gamma w10 |r - r_gt| ]
-// with the force angle only when both pads are in contact, the slip angle only
-// when both slip and |r - r_gt| only when both slip rotationally.
+// The full cost of the PD hand's observation (full_cost.cuh): the joints'
+// term, then each pad's terms in pad order.
 __device__ double frame_cost_full(const CostArgs &a, int i) {
     const int D = a.D, P = a.P;
     double w[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) w[k] = (double)a.cfg.w_full[k];
-    const double tau = (double)a.cfg.tau;
-    double dq = 0.0;
-    for (int j = 0; j < D; ++j) {
-        const double d = (double)a.qj[(size_t)i * D + j] - (double)a.g_q[j];
-        dq += d * d;
-    }
-    double c = w[0] * sqrt(dq);
+    double c = full_cost_joints(a.qj + (size_t)i * D, a.g_q, D, w[0]);
     for (int l = 0; l < P; ++l) {
-        const float4 pa = a.pad_pose[2 * ((size_t)i * P + l)], qa = a.pad_pose[2 * ((size_t)i * P + l) + 1];
-        const float4 pb = a.g_pose[2 * l], qb = a.g_pose[2 * l + 1];
-        const double dx = (double)pa.x - pb.x, dy = (double)pa.y - pb.y, dz = (double)pa.z - pb.z;
-        c += w[1] * sqrt(dx * dx + dy * dy + dz * dz);
-        // conj(qa) * qb
-        const Q4d rel = qmul_d({(double)qa.x, -(double)qa.y, -(double)qa.z, -(double)qa.w},
-                               {(double)qb.x, (double)qb.y, (double)qb.z, (double)qb.w});
-        c += w[2] * 2.0 * atan2(sqrt(rel.x * rel.x + rel.y * rel.y + rel.z * rel.z), fabs(rel.w));
-        const float *fa = a.forces + ((size_t)i * P + l) * 3, *fb = a.obs + 3 * l;
-        const double ax = fa[0], ay = fa[1], az = fa[2], bx = fb[0], by = fb[1], bz = fb[2];
-        const double ma = sqrt(ax * ax + ay * ay + az * az), mb = sqrt(bx * bx + by * by + bz * bz);
-        const bool in_a = ma > tau, in_b = mb > tau;
-        if (in_a != in_b) {
-            c += w[3];
-        } else {
-            c += w[4] * fabs(ma - mb);
-            if (in_a) c += w[5] * angle_d(ax, ay, az, bx, by, bz);
-        }
-        const float4 sa = a.slip[(size_t)i * P + l], sb = a.g_slip[l];
-        const int fa_ = __float_as_int(sa.z), fb_ = __float_as_int(sb.z);
-        const int ta = fa_ & 1, tb = fb_ & 1;
-        if (ta != tb) {
-            c += w[6];
-        } else if (ta) {
-            const double d0 = sa.x, d1 = sa.y, e0 = sb.x, e1 = sb.y;
-            c += w[7] * atan2(fabs(d0 * e1 - d1 * e0), d0 * e0 + d1 * e1);
-        }
-        const int ra = (fa_ >> 1) & 1, rb = (fb_ >> 1) & 1;
-        if (ra != rb) {
-            c += w[8];
-        } else if (ra) {
-            c += w[9] * fabs((double)((fa_ >> 2) & 1) - (double)((fb_ >> 2) & 1));
-        }
+        const size_t o = (size_t)i * P + l;
+        c = __dadd_rn(c, full_cost_pad(w, (double)a.cfg.tau, a.pad_pose[2 * o], a.pad_pose[2 * o + 1], a.g_pose[2 * l],
+                                       a.g_pose[2 * l + 1], a.forces + 3 * o, a.obs + 3 * l, a.slip[o], a.g_slip[l]));
     }
     return c;
 }

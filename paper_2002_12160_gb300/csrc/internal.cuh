@@ -249,6 +249,16 @@ struct PdArgs {
     float4 *pad_pose;         // [N][P][2]: (position, 0), (quaternion w x y z)
     float4 *slip;             // [N][P]: (d_x, d_y, flag bits, 0)
     unsigned long long *work; // [6]
+    // window mode (cm_frames != null): n_frames frames, each scored with the
+    // full cost against the truth's observation of that frame
+    const float *g_q;         // [n_frames][D]
+    const float4 *g_pose;     // [n_frames][P][2]
+    const float *g_forces;    // [n_frames][P][3]
+    const float4 *g_slip;     // [n_frames][P]
+    double *c_sum, *c_mean, *cost_mean;   // [N] (cost_mean may be null)
+    const int *n_window;
+    double *cm_frames;        // [n_frames][N]
+    float4 *pose_frames;      // [n_frames][N][2]
 };
 size_t pd_step_smem_bytes(int s_max, int c_max);
 cudaError_t pd_step_prepare(int s_max, int c_max);

@@ -486,11 +486,12 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 V3 vv = v_pred, ww = w_pred;
                 if (nc > 0) {
                     const float inv_nc = 1.0f / (float)nc;
+                    const int slot_off = TPE > 32 ? 32 * G.wid : 0;   // this warp's first contact of a slot
                     if (warm) {   // the cached impulses act from the first iteration on
                         float acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
                         for (int k = 0; k < CPL; ++k) {
-                            if (k * TPE < nc) {
+                            if (k * TPE + slot_off < nc) {
                                 const V3 tq = cross(cr_[k], lam_[k]);
                                 acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
                                 acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
@@ -509,13 +510,15 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                     for (int it = 0; it < iters; ++it) {
                         float acc[6] = {0, 0, 0, 0, 0, 0};
                         // a register slot is skipped only when it is empty in every
-                        // lane of the group (a uniform branch); otherwise all lanes
-                        // update it without a branch so the slots' chains interleave:
+                        // lane of the warp (a warp-uniform branch: in a wider group the
+                        // warps holding only empty slots skip it and free issue slots);
+                        // otherwise all lanes update it without a branch so the slots'
+                        // chains interleave:
                         // an empty slot (r = c = 0, n = z, 1/k = 0, lambda = 0) keeps
                         // lambda = 0 and adds zeros
 #pragma unroll
                         for (int k = 0; k < CPL; ++k) {
-                            if (k * TPE < nc) {
+                            if (k * TPE + slot_off < nc) {
                                 lam_[k] = update_contact(lam_[k], cr_[k], cn_[k], cc_[k], ikn_[k], ikt_[k], vv, ww, mu, inv_nc);
                                 const V3 tq = cross(cr_[k], lam_[k]);
                                 acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;

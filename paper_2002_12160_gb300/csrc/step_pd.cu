@@ -32,6 +32,7 @@
 #include <cstddef>
 
 #include "contact.cuh"
+#include "full_cost.cuh"
 #include "hand.cuh"
 #include "internal.cuh"
 
@@ -58,6 +59,9 @@ struct PdWarp {
     int pad_;
     float4 clc[IH_MAX_SPHERES / kCluster];    // cluster centres (world-rotated, relative to x), radius
     unsigned short clp[kPdMaxLinks * (IH_MAX_SPHERES / kCluster)];   // surviving (link, cluster) pairs
+    float4 opp[IH_MAX_PADS][2];               // the frame's pad poses: (position, 0), (quaternion)
+    float4 osl[IH_MAX_PADS];                  // the frame's slip records: (d_x, d_y, flag bits, 0)
+    double pterm[IH_MAX_PADS];                // window mode: each pad's cost terms
 };
 static_assert(sizeof(PdWarp) % 16 == 0, "warp records keep 16-byte alignment");
 
@@ -132,6 +136,11 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
     const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
     const float Mj = cfg.armature + h * cfg.kd + h * h * cfg.kp, inv_Mj = 1.0f / Mj;
     const int cap = cfg.c_max;
+    const float inv_ns = 1.0f / (float)ns;
+    // window mode (cm_frames != null): every frame scored against the truth's
+    // observation with the full cost, the argmin taken afterwards
+    const bool window_mode = a.cm_frames != nullptr;
+    const int n_win0 = window_mode ? *a.n_window : 0;
 
     unsigned char *pl_cnt = smem;
     unsigned char *pl_id = smem + pd_align16(kPdMaxLinks);
@@ -177,6 +186,50 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
             W.qd[k] = a.qdj[(size_t)env * D + k];
         }
         __syncwarp();
+        // the observation of the frame just stepped (pad poses from the joints
+        // at its end, slip from the frame's sums) into W.opp / W.osl
+        auto frame_obs = [&]() {
+            pd_fk(sc, W, lane);
+            __syncwarp();
+            for (int p = lane; p < P; p += 32) {
+                const int l = __ldg(sc.pad_link + p);
+                const float4 A0 = W.link[l][0], Aq = W.link[l][2];
+                const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+                V3 c;
+                if (l == 0) {
+                    c = xyz(A0) + qrot(lq, mk(0, 0, sc.palm_hz));
+                } else {
+                    const float s1 = fminf(p_s1[p], 1.0f), s0 = fmaxf(p_s0[p], 0.0f);
+                    c = xyz(A0) + qrot(lq, mk(0.5f * (s0 + s1) * sc.link_len, 0, 0));
+                }
+                W.opp[p][0] = make_float4(c.x, c.y, c.z, 0.0f);
+                W.opp[p][1] = Aq;
+                const float *S = W.slip + 8 * p;
+                float dx = 0.0f, dy = 0.0f;
+                int flags = 0;
+                if (S[0] > 0.0f) {
+                    const float iw = 1.0f / S[0];
+                    const V3 vt = mk(S[1], S[2], S[3]) * iw;
+                    V3 nb = mk(S[4], S[5], S[6]);
+                    nb = nb * rsqrtf(dot(nb, nb));
+                    const float spin = S[7] * iw;
+                    if (sqrtf(dot(vt, vt)) > cfg.v_slip) {
+                        const V3 ax = xyz(W.link[l][1]);
+                        V3 e1 = ax - nb * dot(ax, nb);
+                        e1 = e1 * rsqrtf(dot(e1, e1));
+                        const V3 e2 = cross(nb, e1);
+                        const float d1 = dot(vt, e1), d2 = dot(vt, e2), idn = rsqrtf(d1 * d1 + d2 * d2);
+                        dx = d1 * idn;
+                        dy = d2 * idn;
+                        flags |= 1;
+                    }
+                    if (fabsf(spin) > cfg.w_slip) flags |= (spin > 0.0f) ? 6 : 2;
+                }
+                W.osl[p] = make_float4(dx, dy, __int_as_float(flags), 0.0f);
+            }
+            __syncwarp();
+        };
+        double c_sum_env = (window_mode && lane == 0) ? a.c_sum[env] : 0.0;
 
         for (int fr = 0; fr < a.n_frames; ++fr) {
             for (int k = lane; k < 3 * P; k += 32) W.padf[k] = 0.0f;
@@ -425,47 +478,47 @@ __global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s
                 if (!fin) st |= IH_ENV_NONFINITE;
                 else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
             }
+            if (window_mode) {   // this frame's full cost against the truth's observation
+                frame_obs();
+                const double tau = (double)cfg.tau;
+                double wf[10];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) wf[k] = (double)cfg.w_full[k];
+                for (int p = lane; p < P; p += 32) {
+                    const float fa[3] = {W.padf[3 * p] * inv_ns, W.padf[3 * p + 1] * inv_ns, W.padf[3 * p + 2] * inv_ns};
+                    const size_t o = (size_t)fr * P + p;
+                    W.pterm[p] = full_cost_pad(wf, tau, W.opp[p][0], W.opp[p][1], a.g_pose[2 * o], a.g_pose[2 * o + 1],
+                                               fa, a.g_forces + 3 * o, W.osl[p], a.g_slip[o]);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    double c = INFINITY;
+                    if (!(st & kDiverged)) {
+                        c = full_cost_joints(W.qj, a.g_q + (size_t)fr * D, D, wf[0]);
+                        for (int p = 0; p < P; ++p) c = __dadd_rn(c, W.pterm[p]);
+                    }
+                    c_sum_env = __dadd_rn(c_sum_env, c);
+                    const double cm = __ddiv_rn(c_sum_env, (double)(n_win0 + fr + 1));
+                    a.cm_frames[(size_t)fr * a.N + env] = cm;
+                    float4 *pf = a.pose_frames + 2 * ((size_t)fr * a.N + env);
+                    pf[0] = make_float4(x.x, x.y, x.z, 0.0f);
+                    pf[1] = make_float4(q.w, q.x, q.y, q.z);
+                    if (fr == a.n_frames - 1) {
+                        a.c_sum[env] = c_sum_env;
+                        a.c_mean[env] = cm;
+                        if (a.cost_mean) a.cost_mean[env] = cm;
+                    }
+                }
+                __syncwarp();
+            }
         }
         // the observation of the last frame: forces, pad poses, slip
-        pd_fk(sc, W, lane);
-        __syncwarp();
-        const float inv_ns = 1.0f / (float)ns;
+        if (!window_mode) frame_obs();
         for (int k = lane; k < 3 * P; k += 32) a.forces[(size_t)env * P * 3 + k] = W.padf[k] * inv_ns;
         for (int p = lane; p < P; p += 32) {
-            const int l = __ldg(sc.pad_link + p);
-            const float4 A0 = W.link[l][0], Aq = W.link[l][2];
-            const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
-            V3 c;
-            if (l == 0) {
-                c = xyz(A0) + qrot(lq, mk(0, 0, sc.palm_hz));
-            } else {
-                const float s1 = fminf(p_s1[p], 1.0f), s0 = fmaxf(p_s0[p], 0.0f);
-                c = xyz(A0) + qrot(lq, mk(0.5f * (s0 + s1) * sc.link_len, 0, 0));
-            }
-            a.pad_pose[2 * ((size_t)env * P + p)] = make_float4(c.x, c.y, c.z, 0.0f);
-            a.pad_pose[2 * ((size_t)env * P + p) + 1] = Aq;
-            const float *S = W.slip + 8 * p;
-            float dx = 0.0f, dy = 0.0f;
-            int flags = 0;
-            if (S[0] > 0.0f) {
-                const float iw = 1.0f / S[0];
-                const V3 vt = mk(S[1], S[2], S[3]) * iw;
-                V3 nb = mk(S[4], S[5], S[6]);
-                nb = nb * rsqrtf(dot(nb, nb));
-                const float spin = S[7] * iw;
-                if (sqrtf(dot(vt, vt)) > cfg.v_slip) {
-                    const V3 ax = xyz(W.link[l][1]);
-                    V3 e1 = ax - nb * dot(ax, nb);
-                    e1 = e1 * rsqrtf(dot(e1, e1));
-                    const V3 e2 = cross(nb, e1);
-                    const float d1 = dot(vt, e1), d2 = dot(vt, e2), idn = rsqrtf(d1 * d1 + d2 * d2);
-                    dx = d1 * idn;
-                    dy = d2 * idn;
-                    flags |= 1;
-                }
-                if (fabsf(spin) > cfg.w_slip) flags |= (spin > 0.0f) ? 6 : 2;
-            }
-            a.slip[(size_t)env * P + p] = make_float4(dx, dy, __int_as_float(flags), 0.0f);
+            a.pad_pose[2 * ((size_t)env * P + p)] = W.opp[p][0];
+            a.pad_pose[2 * ((size_t)env * P + p) + 1] = W.opp[p][1];
+            a.slip[(size_t)env * P + p] = W.osl[p];
         }
         for (int k = lane; k < D; k += 32) {
             a.qj[(size_t)env * D + k] = W.qj[k];

@@ -65,7 +65,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
            "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
            "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_get_warm_cache",
-           "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full"]
+           "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full", "sim_step_frames_full"]
 
 
 def lib() -> C.CDLL:
@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
             "sim_set_hand": [P, P, P],
             "sim_get_hand": [P, P, P],
             "cost_eval_full": [P, P, P, P, P, P, P, P],
+            "sim_step_frames_full": [P, I, I, P, P, P, P],
             "sim_step": [P, I, I],
             "sim_read_sensors": [P, P, P],
             "cost_eval": [P, P, P, P, P],
@@ -292,6 +293,17 @@ class Sim:
         _check(est_pose, torch.float32, (8,), "est_pose")
         self._call("cost_eval_full", _ptr(q), _ptr(pad_pose), _ptr(forces), _ptr(slip), _ptr(cost_mean),
                    _ptr(argmin), _ptr(est_pose))
+
+    def sim_step_frames_full(self, frame0: int, q, pad_pose, forces, slip):
+        """PD hand: T frames in one launch, each scored with the full cost against
+        the truth's observation (q [T, D], pad_pose [T, P, 8], forces [T, P, 3],
+        slip [T, P, 4]); follow with sim_frames_argmin."""
+        T = forces.shape[0]
+        _check(q, torch.float32, (T, self.n_joints), "q")
+        _check(pad_pose, torch.float32, (T, self.n_pads, 8), "pad_pose")
+        _check(forces, torch.float32, (T, self.n_pads, 3), "forces")
+        _check(slip, torch.float32, (T, self.n_pads, 4), "slip")
+        self._call("sim_step_frames_full", frame0, T, _ptr(q), _ptr(pad_pose), _ptr(forces), _ptr(slip))
 
     def sim_step_track(self, frame: int, obs, cost_mean=None, argmin=None, est_pose=None):
         _check(obs, torch.float32, (self.n_pads, 3), "obs")

@@ -90,10 +90,30 @@ class Tracker:
         self.sim.sim_track_window(f0, self.obs[f0:f0 + T], self.wl.opt, w, self.est[f0:f0 + T],
                                   self.argmin[f0:f0 + T])
 
+    # The PD window's T frames in one launch (cost inside it) is faster while the
+    # environments fit in about one wave (N = 1024: 1.53 against 2.03 ms per
+    # window); with several waves the cost's FP64 work lengthens every
+    # environment's chain and the separate cost launches win (N = 8192: 10.7
+    # against 9.3 ms).
+    PD_FUSED_MAX_N = 4096
+
     def window_pd(self, w: int):
-        """A window with the PD-driven hand: per frame one step launch and the
-        full ten-term cost against the ground truth's observation (argmin and
-        estimate), then the optimizer update."""
+        """A window with the PD-driven hand: its T frames in one step launch,
+        each scored with the full ten-term cost against the ground truth's
+        observation, every frame's argmin and estimate, then the optimizer
+        update (per-frame launches above PD_FUSED_MAX_N environments)."""
+        if self.n > self.PD_FUSED_MAX_N:
+            return self.window_pd_unfused(w)
+        T = self.T
+        f0 = w * T
+        self.sim.sim_step_frames_full(f0, self.obs_q[f0:f0 + T], self.obs_pp[f0:f0 + T], self.obs[f0:f0 + T],
+                                      self.obs_slip[f0:f0 + T])
+        self.sim.sim_frames_argmin(self.est[f0:f0 + T], self.argmin[f0:f0 + T])
+        self.sim.optimizer_update(self.wl.opt, w)
+
+    def window_pd_unfused(self, w: int):
+        """The same window as per-frame calls: one step launch and one full-cost
+        launch per frame, then the optimizer update."""
         T = self.T
         for k in range(T):
             f = w * T + k
