@@ -295,3 +295,49 @@ def test_pd_window_launch_equals_the_separate_calls():
         assert torch.equal(x, y)
     for x, y in zip(a.sim_read_observation(), b.sim_read_observation()):
         assert torch.equal(x, y)
+
+
+def test_pd_full_size_window_launch_sampled_parity():
+    """At the benchmark's size (N = 1024 cylinders) and in the launch the
+    benchmark times (a window launch with the full cost inside), a sample of
+    environments checked one by one against the oracle's step, and the
+    launch's argmin and estimate against the oracle's full cost of the GPU's
+    observation."""
+    n = 1024
+    wl = _pd("tracking_cyl64", n, 8)
+    sim = start(wl, n=n, frames=8)
+    d = dev()
+    sim.sim_step(0, 5)
+    q, pp, slip = sim.sim_read_observation()
+    forces, _ = sim.sim_read_sensors()
+    gt = [t[17:18].clone() for t in (q, pp, forces, slip)]   # one environment's observation as the truth
+    shape = wl.shape_id[:n].astype(np.int32)
+    iters = wl.iters[:n].astype(np.int32)
+    rng = np.random.default_rng(0)
+    envs = np.sort(rng.choice(n, 24, replace=False))
+    envs[-1] = n - 1
+    st = _hand_state(sim, shape, iters).subset(envs)
+    ob, diag = O.step_pd(O.OracleScene(scene32(wl.scene)), sim32(wl.sim), st, wl.q_traj, 5, 1)
+    sim.sim_step_frames_full(5, *gt)
+    est = torch.empty((1, 8), dtype=torch.float32, device=d)
+    am = torch.empty(1, dtype=torch.int32, device=d)
+    sim.sim_frames_argmin(est, am)
+    g = _hand_state(sim, shape, iters).subset(envs)
+    ok = ~((diag[:, 2] < FRAGILE) | (diag[:, 3] < FRAGILE) | (diag[:, 4] < FRAGILE))
+    assert ok.mean() >= 0.75
+    np.testing.assert_array_equal(g.status[ok], st.status[ok])
+    assert np.linalg.norm(g.pose[ok, :3] - st.pose[ok, :3], axis=1).max() < POS_TOL
+    assert rot_angle(g.pose[ok], st.pose[ok]).max() < ROT_TOL
+    np.testing.assert_allclose(g.qj[ok], st.qj[ok], atol=1e-5)
+    # the cost means the launch left for the optimizer, against the oracle's
+    # cost of the GPU's own observation (FP64 on both sides, same inputs)
+    go, status = _gpu_obs(sim)
+    gq, gpp, gf, gs = (t.cpu().numpy()[0] for t in gt)
+    truth = O.Obs(gq[None].astype(np.float64), np.concatenate([gpp[:, :3], gpp[:, 4:8]], -1)[None].astype(np.float64),
+                  gf[None].astype(np.float64), gs[None, :, :2].astype(np.float64), gs[None, :, 2].copy().view(np.int32))
+    c_sum = np.zeros(n)
+    i_or, c_mean, _ = O.cost_full(sim32(wl.sim), go, truth, status, c_sum, 1)
+    assert int(am.item()) == i_or
+    # the estimate is the argmin environment's pose after the frame
+    pose = sim.sim_get_state()[0]
+    assert torch.equal(est[0], pose[i_or])
