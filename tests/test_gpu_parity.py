@@ -95,11 +95,12 @@ def test_cost_and_argmin_match_oracle_bit_for_bit():
         np.testing.assert_array_equal(est.cpu().numpy(), pose[i_or].cpu().numpy())
 
 
-def test_optimizer_update_matches_oracle():
-    wl = W.make_workload("tracking_cyl64", n_envs=300, frames=6)
-    sim = start(wl, n=300, frames=6)
+@pytest.mark.parametrize("n", [300, 3000])   # one CTA for select + statistics + Cholesky; separate launches
+def test_optimizer_update_matches_oracle(n):
+    wl = W.make_workload("tracking_cyl64", n_envs=n, frames=6)
+    sim = start(wl, n=n, frames=6)
     d = dev()
-    cm = torch.empty(300, dtype=torch.float64, device=d)
+    cm = torch.empty(n, dtype=torch.float64, device=d)
     for f in range(6):
         sim.sim_step(f, 1)
         forces, _ = sim.sim_read_sensors()
@@ -107,7 +108,7 @@ def test_optimizer_update_matches_oracle():
     before = oracle_state(sim.sim_get_state())
     C = cm.cpu().numpy()
     am = torch.empty(1, dtype=torch.int32, device=d)
-    par = torch.empty(300, dtype=torch.int32, device=d)
+    par = torch.empty(n, dtype=torch.int32, device=d)
     sim.optimizer_update(wl.opt, 5, am, par)
     after = oracle_state(sim.sim_get_state())
     istar, parent, stats = O.optimizer(wl.opt, before, C, wl.seed, 5)
@@ -123,7 +124,7 @@ def test_optimizer_update_matches_oracle():
     forces, status = sim.sim_read_sensors()
     sim.cost_eval(forces[7].clone(), cm)
     _, c_one, _ = O.cost(sim32(wl.sim), forces.cpu().numpy().astype(np.float64),
-                         forces[7].cpu().numpy().astype(np.float64), status.cpu().numpy(), np.zeros(300), 1)
+                         forces[7].cpu().numpy().astype(np.float64), status.cpu().numpy(), np.zeros(n), 1)
     np.testing.assert_array_equal(cm.cpu().numpy(), c_one)
 
 
