@@ -255,7 +255,7 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e
     dev = torch.device("cuda", local)
     T = 10
     n_timing = 3 if with_timing else 0
-    n_e2e = 2 if with_e2e else 0
+    n_e2e = 6 if with_e2e else 0   # three pipelined windows, three with the host waiting for each
     n_windows = warmup + steps + n_timing + n_e2e
     wl = W.make_workload(workload, n_envs=n_envs, frames=n_windows * T)
     seed = wl.seed + 7919 * rank   # independent replicas per rank
