@@ -126,7 +126,7 @@ __device__ __forceinline__ void pd_twist(PdWarp &W, int l) {
     W.tw[l][1] = make_float4(cl.x, cl.y, cl.z, 0.0f);
 }
 
-__global__ void __launch_bounds__(kPdBlock) pd_step_kernel(const PdArgs a, int s_max) {
+__global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, int s_max) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
