@@ -49,7 +49,7 @@ FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
 # sources (step.cu, step_kernel.cuh, contact.cuh) whose hash is recorded with it; reported as
 # null once they change.
-STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "ffa6d2370c33435c15ebb5a2e015ca4b8db0ba3420ff7801ee2ae553b5df23b5"}
+STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "abe9db5ac5a3b1248b2c13cf1273ae96199e0b3e53cbf4e515a41a7a9a603c68"}
 STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/step_kernel.cuh",
                 "paper_2002_12160_gb300/csrc/contact.cuh"]
 

@@ -142,11 +142,12 @@ __device__ __forceinline__ void group_sum6(float (&v)[6], const Group<TPE> &G, f
 }
 
 // Resident blocks per SM each shape is compiled for (caps its registers):
-// one register-resident contact per thread fits 5 blocks without spilling,
-// two fit 4, four fit 3.
+// one or two register-resident contacts per thread at 4 blocks (128
+// registers: with one contact a cap of 5 blocks spilled and ran 6 % slower on
+// large batches), four at 3.
 template <int TPE, int CPL>
 struct MinBlocks {
-    static constexpr int value = CPL <= 1 ? 5 : (CPL <= 2 ? 4 : (CPL <= 4 ? 3 : 2));
+    static constexpr int value = CPL <= 2 ? 4 : (CPL <= 4 ? 3 : 2);
 };
 
 template <int TPE, int CPL, bool WARM>
