@@ -184,21 +184,32 @@ class Tracker:
         read-back (the timed region spans all of them). Also reported: the same
         windows with the host waiting for each window's read-back."""
         T, D, P = self.T, self.wl.scene.n_joints, self.wl.scene.n_pads
-        q_host = torch.from_numpy(self.wl.q_traj).pin_memory()
-        obs_host = self.obs.cpu().pin_memory()
-        est_host = torch.empty((count, T, 8), dtype=torch.float32).pin_memory()
-        am_host = torch.empty((count, T), dtype=torch.int32).pin_memory()
-        q_dev = torch.empty((T + 1, D), dtype=torch.float32, device=self.dev)
-        obs_dev = torch.empty((T, P, 3), dtype=torch.float32, device=self.dev)
+        n_in, n_out = (T + 1) * D + T * P * 3, T * 8 + T
+        frames = self.wl.frames
+        # each window's inputs (commands of its T + 1 frame boundaries, then the
+        # observations of its T frames) packed in one pinned host block, and its
+        # outputs (estimates, then argmins) in one device block: one copy each way
+        in_host = torch.empty((frames // T, n_in), dtype=torch.float32).pin_memory()
+        q_all = torch.from_numpy(self.wl.q_traj)
+        obs_all = self.obs.cpu()
+        for w in range(w0, w0 + count):
+            f0 = w * T
+            in_host[w, :(T + 1) * D] = q_all[f0:f0 + T + 1].reshape(-1)
+            in_host[w, (T + 1) * D:] = obs_all[f0:f0 + T].reshape(-1)
+        out_host = torch.empty((count, n_out), dtype=torch.float32).pin_memory()
+        in_dev = torch.empty((n_in,), dtype=torch.float32, device=self.dev)
+        out_dev = torch.empty((n_out,), dtype=torch.float32, device=self.dev)
+        q_dev = in_dev[:(T + 1) * D].view(T + 1, D)
+        obs_dev = in_dev[(T + 1) * D:].view(T, P, 3)
+        est_dev = out_dev[:T * 8].view(T, 8)
+        am_dev = out_dev[T * 8:].view(torch.int32)
 
         def window(i, w):
             f0 = w * T
-            q_dev.copy_(q_host[f0:f0 + T + 1], non_blocking=True)
-            obs_dev.copy_(obs_host[f0:f0 + T], non_blocking=True)
+            in_dev.copy_(in_host[w], non_blocking=True)
             self.sim.sim_set_commands(f0, q_dev)
-            self.sim.sim_track_window(f0, obs_dev, self.wl.opt, w, self.est[f0:f0 + T], self.argmin[f0:f0 + T])
-            est_host[i].copy_(self.est[f0:f0 + T], non_blocking=True)
-            am_host[i].copy_(self.argmin[f0:f0 + T], non_blocking=True)
+            self.sim.sim_track_window(f0, obs_dev, self.wl.opt, w, est_dev, am_dev)
+            out_host[i].copy_(out_dev, non_blocking=True)
 
         half = count // 2
         torch.cuda.synchronize()
@@ -215,9 +226,12 @@ class Tracker:
             torch.cuda.synchronize()
             sync_times.append(time.perf_counter() - t1)
         ms_sync = 1e3 * sum(sync_times) / len(sync_times)
+        for i, w in enumerate(range(w0, w0 + count)):   # the estimates as the tracker keeps them
+            f0 = w * T
+            self.est[f0:f0 + T].copy_(out_host[i, :T * 8].view(T, 8))
+            self.argmin[f0:f0 + T].copy_(out_host[i, T * 8:].view(torch.int32))
         return {"value": self.n * T / (ms / 1e3), "unit": "env-steps/s", "ms_per_step": ms,
-                "h2d_bytes_per_step": (T + 1) * D * 4 + T * P * 3 * 4,
-                "d2h_bytes_per_step": T * 8 * 4 + T * 4, "windows": half, "pipelined": True,
+                "h2d_bytes_per_step": n_in * 4, "d2h_bytes_per_step": n_out * 4, "windows": half, "pipelined": True,
                 "host_waits_each_window": {"value": self.n * T / (ms_sync / 1e3), "ms_per_step": ms_sync,
                                            "windows": count - half}}
 
