@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads, D = sc.n_joints, F = sc.n_fingers;
+    const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads, D = sc.n_joints;
     const float h = cfg.h, inv_h = 1.0f / h, inv_L = 1.0f / sc.link_len;
     const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
     const float Mj = cfg.armature + h * cfg.kd + h * h * cfg.kp, inv_Mj = 1.0f / Mj;
