@@ -554,12 +554,13 @@ def warm_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, n
 # reach test); per pair tested 30; per contact the set-up with
 # its joints' share (140) and the pad and slip sums (45); per contact-iteration
 # the update against the link twist and the per-link sums (103); per
-# env-iteration the link twists (52 per link) and the joint updates (36 per joint).
+# env-iteration the joint updates (36 per joint) and the links' twists from
+# them (24 per joint: each joint's contribution and a 4-lane prefix).
 def pd_flops(work, scene, spheres):
     F, D, Lk = scene.n_fingers, scene.n_joints, scene.n_links
     per_substep = 570 * F + 9 * D + 25 * Lk + 145 + 15 * spheres
     return (work["env_substeps"] * per_substep + work["cluster_tests"] * 25 + work["pairs"] * 30 + work["contacts"] * 185 +
-            work["contact_iters"] * 103 + work["env_iters"] * (52 * Lk + 36 * D + 30))
+            work["contact_iters"] * 103 + work["env_iters"] * (60 * D + 30))
 
 
 def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, windows=5, budget_s=10.0,

@@ -109,21 +109,32 @@ __device__ __forceinline__ void pd_fk(const DevScene &sc, PdWarp &W, int lane) {
     }
 }
 
-// twist of link l (>= 1) from the joint velocities of its finger
-__device__ __forceinline__ void pd_twist(PdWarp &W, int l) {
-    V3 wl = mk(0, 0, 0), cl = mk(0, 0, 0);
-    if (l >= 1) {
-        const int f = (l - 1) >> 2, j = (l - 1) & 3;
-        for (int a = 0; a <= j; ++a) {
-            const int ja = 4 * f + a;
-            const V3 z = xyz(W.zax[ja]);
-            const float qd = W.qd[ja];
-            wl = wl + z * qd;
-            cl = cl - cross(z, xyz(W.org[ja])) * qd;
+// Every link's twist from the joint velocities, one lane per joint (lane a =
+// 4 f + j holds joint j of finger f with velocity qd): joint a adds
+// (qd z_a, -qd z_a x o_a) to the twist of every link it moves, so the twist of
+// link a + 1 is the inclusive prefix over the finger's lanes 4 f .. a (two
+// shuffle levels). Every lane of the warp takes part; lanes >= D hold zeros.
+__device__ __forceinline__ void pd_joint_twists(PdWarp &W, int lane, int D, float qd) {
+    V3 wv = mk(0, 0, 0), cv = mk(0, 0, 0);
+    if (lane < D) {
+        const V3 z = xyz(W.zax[lane]);
+        wv = z * qd;
+        cv = cross(z, xyz(W.org[lane])) * (-qd);
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+        const float a0 = __shfl_up_sync(0xffffffffu, wv.x, off), a1 = __shfl_up_sync(0xffffffffu, wv.y, off),
+                    a2 = __shfl_up_sync(0xffffffffu, wv.z, off), b0 = __shfl_up_sync(0xffffffffu, cv.x, off),
+                    b1 = __shfl_up_sync(0xffffffffu, cv.y, off), b2 = __shfl_up_sync(0xffffffffu, cv.z, off);
+        if ((lane & 3) >= off) {
+            wv = wv + mk(a0, a1, a2);
+            cv = cv + mk(b0, b1, b2);
         }
     }
-    W.tw[l][0] = make_float4(wl.x, wl.y, wl.z, 0.0f);
-    W.tw[l][1] = make_float4(cl.x, cl.y, cl.z, 0.0f);
+    if (lane < D) {
+        W.tw[lane + 1][0] = make_float4(wv.x, wv.y, wv.z, 0.0f);
+        W.tw[lane + 1][1] = make_float4(cv.x, cv.y, cv.z, 0.0f);
+    }
 }
 
 __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, int s_max) {
@@ -380,9 +391,14 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                 V3 vv = v_pred, ww = w_pred;
                 if (nc > 0) {
                     const float inv_nc = 1.0f / (float)nc;
+                    // the links' twists under the PD prediction alone (palm: at rest)
+                    if (lane == 0) {
+                        W.tw[0][0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        W.tw[0][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+                    pd_joint_twists(W, lane, D, lane < D ? W.qd_star[lane] : 0.0f);
+                    __syncwarp();
                     for (int it = 0; it < iters; ++it) {
-                        if (lane < Lk) pd_twist(W, lane);
-                        __syncwarp();
                         float acc[6] = {0, 0, 0, 0, 0, 0};
                         for (int ci = lane; ci < nc; ci += 32) {
                             const float4 s0 = stage[ci][0], s1 = stage[ci][1], s2 = stage[ci][2], s3 = stage[ci][3];
@@ -412,6 +428,7 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                             W.ls[lane][1] = make_float4(Tl.x, Tl.y, Tl.z, 0.0f);
                         }
                         __syncwarp();
+                        float qd_new = 0.0f;
                         if (lane < D) {   // qd_a = qd*_a - z_a . sum_{links at or beyond a} (T_l - o_a x F_l) / M
                             const int f = lane >> 2, ja = lane & 3;
                             V3 Fs = mk(0, 0, 0), Ts = mk(0, 0, 0);
@@ -421,8 +438,10 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                                 Ts = Ts + xyz(W.ls[l][1]);
                             }
                             const float g = dot(xyz(W.zax[lane]), Ts - cross(xyz(W.org[lane]), Fs));
-                            W.qd[lane] = W.qd_star[lane] - g * inv_Mj;
+                            qd_new = W.qd_star[lane] - g * inv_Mj;
+                            W.qd[lane] = qd_new;
                         }
+                        pd_joint_twists(W, lane, D, qd_new);   // for the next iteration and the slip sensing
                         __syncwarp();
                     }
                 }
@@ -440,8 +459,7 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                     const float kq = (wn > 0.0f) ? sn / wn : 0.5f * h;
                     q = qnorm(qmul({cs, w.x * kq, w.y * kq, w.z * kq}, q));
                 }
-                if (lane < Lk) pd_twist(W, lane);   // the links' final velocities, for the slip sensing
-                __syncwarp();
+                // (W.tw holds the links' twists at the final joint velocities)
                 for (int k = lane; k < D; k += 32) W.qj[k] += h * W.qd[k];
                 // pads: force -lambda / h per contact, and the slip sums weighted
                 // by the normal impulse
