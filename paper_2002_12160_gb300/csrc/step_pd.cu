@@ -21,9 +21,10 @@
 //   4. runs the Jacobi iterations on the object and the joints together: each
 //      contact updates against the object velocity and its link's velocity
 //      (link twist w_l x p + c_l from the joints), the warp sums the object's
-//      impulse and moment, one lane per link sums that link's impulses and
-//      moments about the origin, and one lane per joint turns them into
-//      qd_a = qd*_a - z_a . sum_{links moved by a} (T_l - o_a x F_l) / M;
+//      impulse and moment, the lane of each joint sums the impulses of the
+//      link it ends at and their moments about the origin, a suffix over the
+//      finger's lanes gives it qd_a = qd*_a - z_a . sum_{links moved by a}
+//      (T_l - o_a x F_l) / M, and a prefix over them the links' new twists;
 //   5. integrates the object and the joints (q += h qd), and adds each
 //      contact's impulse to its pad, with the impulse-weighted relative slip
 //      velocity, normal and spin for the slip sensing.
@@ -50,7 +51,6 @@ struct PdWarp {
     float4 link[kPdMaxLinks][kLinkStride];    // link poses: (a, 0), (axis, 0), (quat)
     float4 zax[kPdMaxJoints], org[kPdMaxJoints];
     float4 tw[kPdMaxLinks][2];                // link twist: w_l, c_l (v(p) = w_l x p + c_l)
-    float4 ls[kPdMaxLinks][2];                // per link: sum lambda, sum p x lambda
     float qd_star[kPdMaxJoints], qd[kPdMaxJoints], qj[kPdMaxJoints];
     float padf[3 * IH_MAX_PADS];              // force sums over the frame's substeps
     float slip[8 * IH_MAX_PADS];              // per pad: w, w vt (3), w n (3), w spin
@@ -416,27 +416,33 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                         vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
                         ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
                         __syncwarp();
-                        if (lane >= 1 && lane < Lk) {   // per link: sum lambda, sum p x lambda
-                            V3 Fl = mk(0, 0, 0), Tl = mk(0, 0, 0);
-                            const int e = W.lend[lane];
-                            for (int ci = W.lbeg[lane]; ci < e; ++ci) {
+                        // lane a = 4 f + j sums the contacts of link a + 1 (its impulses and
+                        // their moments about the origin), then a suffix over the finger's
+                        // four lanes gives joint a the links it moves, and
+                        // qd_a = qd*_a - z_a . sum_{links at or beyond a} (T_l - o_a x F_l) / M
+                        float sv[6] = {0, 0, 0, 0, 0, 0};
+                        if (lane < D) {
+                            const int e = W.lend[lane + 1];
+                            for (int ci = W.lbeg[lane + 1]; ci < e; ++ci) {
                                 const V3 lam = xyz(stage[ci][3]);
-                                Fl = Fl + lam;
-                                Tl = Tl + cross(x + xyz(stage[ci][0]), lam);
+                                const V3 t = cross(x + xyz(stage[ci][0]), lam);
+                                sv[0] += lam.x; sv[1] += lam.y; sv[2] += lam.z;
+                                sv[3] += t.x; sv[4] += t.y; sv[5] += t.z;
                             }
-                            W.ls[lane][0] = make_float4(Fl.x, Fl.y, Fl.z, 0.0f);
-                            W.ls[lane][1] = make_float4(Tl.x, Tl.y, Tl.z, 0.0f);
                         }
-                        __syncwarp();
-                        float qd_new = 0.0f;
-                        if (lane < D) {   // qd_a = qd*_a - z_a . sum_{links at or beyond a} (T_l - o_a x F_l) / M
-                            const int f = lane >> 2, ja = lane & 3;
-                            V3 Fs = mk(0, 0, 0), Ts = mk(0, 0, 0);
-                            for (int jl = ja; jl < 4; ++jl) {
-                                const int l = 1 + 4 * f + jl;
-                                Fs = Fs + xyz(W.ls[l][0]);
-                                Ts = Ts + xyz(W.ls[l][1]);
+#pragma unroll
+                        for (int off = 1; off < 4; off <<= 1) {
+                            float o[6];
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) o[k] = __shfl_down_sync(0xffffffffu, sv[k], off);
+                            if ((lane & 3) + off < 4) {
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) sv[k] += o[k];
                             }
+                        }
+                        float qd_new = 0.0f;
+                        if (lane < D) {
+                            const V3 Fs = mk(sv[0], sv[1], sv[2]), Ts = mk(sv[3], sv[4], sv[5]);
                             const float g = dot(xyz(W.zax[lane]), Ts - cross(xyz(W.org[lane]), Fs));
                             qd_new = W.qd_star[lane] - g * inv_Mj;
                             W.qd[lane] = qd_new;
