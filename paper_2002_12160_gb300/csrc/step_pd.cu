@@ -110,17 +110,13 @@ __device__ __forceinline__ void pd_fk(const DevScene &sc, PdWarp &W, int lane) {
 }
 
 // Every link's twist from the joint velocities, one lane per joint (lane a =
-// 4 f + j holds joint j of finger f with velocity qd): joint a adds
+// 4 f + j holds joint j of finger f with velocity qd, axis z = z_a and
+// zo = z_a x o_a, kept in registers over a substep's iterations): joint a adds
 // (qd z_a, -qd z_a x o_a) to the twist of every link it moves, so the twist of
 // link a + 1 is the inclusive prefix over the finger's lanes 4 f .. a (two
 // shuffle levels). Every lane of the warp takes part; lanes >= D hold zeros.
-__device__ __forceinline__ void pd_joint_twists(PdWarp &W, int lane, int D, float qd) {
-    V3 wv = mk(0, 0, 0), cv = mk(0, 0, 0);
-    if (lane < D) {
-        const V3 z = xyz(W.zax[lane]);
-        wv = z * qd;
-        cv = cross(z, xyz(W.org[lane])) * (-qd);
-    }
+__device__ __forceinline__ void pd_joint_twists(PdWarp &W, int lane, int D, V3 z, V3 zo, float qd) {
+    V3 wv = z * qd, cv = zo * (-qd);
 #pragma unroll
     for (int off = 1; off < 4; off <<= 1) {
         const float a0 = __shfl_up_sync(0xffffffffu, wv.x, off), a1 = __shfl_up_sync(0xffffffffu, wv.y, off),
@@ -396,8 +392,19 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                         W.tw[0][0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                         W.tw[0][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     }
-                    pd_joint_twists(W, lane, D, lane < D ? W.qd_star[lane] : 0.0f);
+                    // the joint's axis, z_a x o_a and qd*_a stay in registers over the iterations
+                    V3 jz = mk(0, 0, 0), jzo = mk(0, 0, 0);
+                    float jqs = 0.0f;
+                    if (lane < D) {
+                        jz = xyz(W.zax[lane]);
+                        jzo = cross(jz, xyz(W.org[lane]));
+                        jqs = W.qd_star[lane];
+                    }
+                    pd_joint_twists(W, lane, D, jz, jzo, jqs);
                     __syncwarp();
+                    // with at most 16 joints, lanes a and a + 16 split link a + 1's contacts
+                    const bool split = D <= 16;
+                    const int ja = split ? (lane & 15) : lane, part = split ? (lane >> 4) : 0, stride = split ? 2 : 1;
                     for (int it = 0; it < iters; ++it) {
                         float acc[6] = {0, 0, 0, 0, 0, 0};
                         for (int ci = lane; ci < nc; ci += 32) {
@@ -421,14 +428,18 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                         // four lanes gives joint a the links it moves, and
                         // qd_a = qd*_a - z_a . sum_{links at or beyond a} (T_l - o_a x F_l) / M
                         float sv[6] = {0, 0, 0, 0, 0, 0};
-                        if (lane < D) {
-                            const int e = W.lend[lane + 1];
-                            for (int ci = W.lbeg[lane + 1]; ci < e; ++ci) {
+                        if (ja < D) {
+                            const int e = W.lend[ja + 1];
+                            for (int ci = W.lbeg[ja + 1] + part; ci < e; ci += stride) {
                                 const V3 lam = xyz(stage[ci][3]);
                                 const V3 t = cross(x + xyz(stage[ci][0]), lam);
                                 sv[0] += lam.x; sv[1] += lam.y; sv[2] += lam.z;
                                 sv[3] += t.x; sv[4] += t.y; sv[5] += t.z;
                             }
+                        }
+                        if (split) {
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) sv[k] += __shfl_down_sync(0xffffffffu, sv[k], 16);
                         }
 #pragma unroll
                         for (int off = 1; off < 4; off <<= 1) {
@@ -443,11 +454,12 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                         float qd_new = 0.0f;
                         if (lane < D) {
                             const V3 Fs = mk(sv[0], sv[1], sv[2]), Ts = mk(sv[3], sv[4], sv[5]);
-                            const float g = dot(xyz(W.zax[lane]), Ts - cross(xyz(W.org[lane]), Fs));
-                            qd_new = W.qd_star[lane] - g * inv_Mj;
+                            // z . (T - o x F) = z . T - F . (z x o)
+                            const float g = dot(jz, Ts) - dot(Fs, jzo);
+                            qd_new = jqs - g * inv_Mj;
                             W.qd[lane] = qd_new;
                         }
-                        pd_joint_twists(W, lane, D, qd_new);   // for the next iteration and the slip sensing
+                        pd_joint_twists(W, lane, D, jz, jzo, qd_new);   // for the next iteration and the slip sensing
                         __syncwarp();
                     }
                 }
