@@ -64,6 +64,11 @@ struct PdWarp {
     double pterm[IH_MAX_PADS];                // window mode: each pad's cost terms
 };
 static_assert(sizeof(PdWarp) % 16 == 0, "warp records keep 16-byte alignment");
+static_assert(sizeof(PdWarp::slip) >= 4 * IH_MAX_PADS * sizeof(double) &&
+                  sizeof(PdWarp::clc) >= 2 * IH_MAX_PADS * sizeof(double),
+              "the window cost reuses the slip sums and cluster centres as scratch");
+static_assert(offsetof(PdWarp, slip) % sizeof(double) == 0 && offsetof(PdWarp, clc) % sizeof(double) == 0,
+              "doubles in the reused scratch stay aligned");
 
 __host__ __device__ constexpr size_t pd_align16(size_t b) { return (b + 15) & ~size_t(15); }
 // block tables: pads per link and their axial intervals
@@ -520,17 +525,40 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                 double wf[10];
 #pragma unroll
                 for (int k = 0; k < 10; ++k) wf[k] = (double)cfg.w_full[k];
-                for (int p = lane; p < P; p += 32) {
-                    const float fa[3] = {W.padf[3 * p] * inv_ns, W.padf[3 * p + 1] * inv_ns, W.padf[3 * p + 2] * inv_ns};
+                // four lanes per pad form its four quantities, then one lane per pad
+                // adds its terms and lane 0 the joints' term and the pads' in pad order
+                // (the cost kernel's bits: the same functions on the same values)
+                double *tq = reinterpret_cast<double *>(W.slip);   // [pad][k]; the frame's slip sums are spent
+                double *fm = reinterpret_cast<double *>(W.clc);    // [pad][2]: force magnitudes
+                for (int u = lane; u < 4 * P; u += 32) {
+                    const int p = u >> 2, k = u & 3;
                     const size_t o = (size_t)fr * P + p;
-                    W.pterm[p] = full_cost_pad(wf, tau, W.opp[p][0], W.opp[p][1], a.g_pose[2 * o], a.g_pose[2 * o + 1],
-                                               fa, a.g_forces + 3 * o, W.osl[p], a.g_slip[o]);
+                    const float fa[3] = {W.padf[3 * p] * inv_ns, W.padf[3 * p + 1] * inv_ns, W.padf[3 * p + 2] * inv_ns};
+                    double na, nb;
+                    tq[u] = fc_pad_term(k, W.opp[p][0], W.opp[p][1], a.g_pose[2 * o], a.g_pose[2 * o + 1], fa,
+                                        a.g_forces + 3 * o, W.osl[p], a.g_slip[o], na, nb);
+                    if (k == 1) {
+                        fm[2 * p] = na;
+                        fm[2 * p + 1] = nb;
+                    }
                 }
+                // the joints' squared differences (one lane each), summed in joint order
+                double sq = 0.0;
+                if (lane < D) {
+                    const double d = __dsub_rn((double)W.qj[lane], (double)a.g_q[(size_t)fr * D + lane]);
+                    sq = __dmul_rn(d, d);
+                }
+                double dq = 0.0;
+                for (int j = 0; j < D; ++j) dq = __dadd_rn(dq, __shfl_sync(0xffffffffu, sq, j));
+                __syncwarp();
+                for (int p = lane; p < P; p += 32)
+                    W.pterm[p] = fc_pad_combine(wf, tau, tq + 4 * p, fm[2 * p], fm[2 * p + 1], W.osl[p].z,
+                                                a.g_slip[(size_t)fr * P + p].z);
                 __syncwarp();
                 if (lane == 0) {
                     double c = INFINITY;
                     if (!(st & kDiverged)) {
-                        c = full_cost_joints(W.qj, a.g_q + (size_t)fr * D, D, wf[0]);
+                        c = __dmul_rn(wf[0], sqrt(dq));   // full_cost_joints
                         for (int p = 0; p < P; ++p) c = __dadd_rn(c, W.pterm[p]);
                     }
                     c_sum_env = __dadd_rn(c_sum_env, c);
