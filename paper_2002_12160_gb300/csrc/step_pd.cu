@@ -18,7 +18,8 @@
 //   3. sets each contact up: effective masses gain the joints' share
 //      sum_a (J_a . n)^2 / M, J_a = z_a x (p - o_a) over the joints that move
 //      the contact's link;
-//   4. runs the Jacobi iterations on the object and the joints together: each
+//   4. runs the Jacobi iterations on the object and the joints together (the
+//      first 96 contacts held in registers, three per lane): each
 //      contact updates against the object velocity and its link's velocity
 //      (link twist w_l x p + c_l from the joints), the warp sums the object's
 //      impulse and moment, the lane of each joint sums the impulses of the
@@ -45,6 +46,7 @@ constexpr int kPdWarps = kPdBlock / 32;
 constexpr int kPdMaxLinks = 1 + 4 * IH_MAX_FINGERS;
 constexpr int kPdMaxJoints = 4 * IH_MAX_FINGERS;
 constexpr int kPdPadsPerLink = 4;
+constexpr int kPdSlots = 3;                   // register-resident contacts per lane
 
 // per-warp (per-environment) records
 struct PdWarp {
@@ -138,7 +140,8 @@ __device__ __forceinline__ void pd_joint_twists(PdWarp &W, int lane, int D, V3 z
     }
 }
 
-__global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, int s_max) {
+// (a budget of two blocks per SM: the register-resident contacts need it)
+__global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, int s_max) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
@@ -410,9 +413,40 @@ __global__ void __launch_bounds__(kPdBlock, 3) pd_step_kernel(const PdArgs a, in
                     // with at most 16 joints, lanes a and a + 16 split link a + 1's contacts
                     const bool split = D <= 16;
                     const int ja = split ? (lane & 15) : lane, part = split ? (lane >> 4) : 0, stride = split ? 2 : 1;
+                    // the first kPdSlots x 32 contacts held in registers over the iterations
+                    // (contact ci = lane + 32 k in slot k); an empty slot (link 0 at rest,
+                    // r = 0, n = z, bias and 1/k 0, lambda 0) keeps lambda = 0 and adds zeros
+                    V3 sr[kPdSlots], sn[kPdSlots], slam[kPdSlots];
+                    float sbias[kPdSlots], sikn[kPdSlots], sikt[kPdSlots];
+                    int slink[kPdSlots];
+#pragma unroll
+                    for (int k = 0; k < kPdSlots; ++k) {
+                        const int ci = lane + 32 * k;
+                        sr[k] = mk(0, 0, 0); sn[k] = mk(0, 0, 1); slam[k] = mk(0, 0, 0);
+                        sbias[k] = 0.0f; sikn[k] = 0.0f; sikt[k] = 0.0f; slink[k] = 0;
+                        if (ci < nc) {
+                            const float4 s0 = stage[ci][0], s1 = stage[ci][1], s2 = stage[ci][2];
+                            sr[k] = xyz(s0); sn[k] = xyz(s1); slink[k] = __float_as_int(s1.w) & 0xff;
+                            sbias[k] = s2.x; sikn[k] = s2.y; sikt[k] = s2.z;
+                        }
+                    }
                     for (int it = 0; it < iters; ++it) {
                         float acc[6] = {0, 0, 0, 0, 0, 0};
-                        for (int ci = lane; ci < nc; ci += 32) {
+#pragma unroll
+                        for (int k = 0; k < kPdSlots; ++k) {
+                            if (32 * k < nc) {   // the same for the whole warp
+                                const int l = slink[k];
+                                const V3 vl = cross(xyz(W.tw[l][0]), x + sr[k]) + xyz(W.tw[l][1]);
+                                const V3 cc = vl - sn[k] * sbias[k];
+                                slam[k] = update_contact(slam[k], sr[k], sn[k], cc, sikn[k], sikt[k], vv, ww, mu, inv_nc);
+                                if (lane + 32 * k < nc)
+                                    stage[lane + 32 * k][3] = make_float4(slam[k].x, slam[k].y, slam[k].z, 0.0f);
+                                const V3 tq = cross(sr[k], slam[k]);
+                                acc[0] += slam[k].x; acc[1] += slam[k].y; acc[2] += slam[k].z;
+                                acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                            }
+                        }
+                        for (int ci = 32 * kPdSlots + lane; ci < nc; ci += 32) {
                             const float4 s0 = stage[ci][0], s1 = stage[ci][1], s2 = stage[ci][2], s3 = stage[ci][3];
                             const int l = __float_as_int(s1.w) & 0xff;
                             const V3 r = xyz(s0), n = xyz(s1);
