@@ -91,10 +91,10 @@ class Tracker:
                                   self.argmin[f0:f0 + T])
 
     # The PD window's T frames in one launch (cost inside it) is faster while the
-    # environments fit in about one wave (N = 1024: 1.53 against 2.03 ms per
-    # window); with several waves the cost's FP64 work lengthens every
-    # environment's chain and the separate cost launches win (N = 8192: 10.7
-    # against 9.3 ms).
+    # environments fit in about one wave (cylinder, N = 1024: 1.02 against
+    # 1.90 ms per window); with several waves the cost's FP64 work lengthens
+    # every environment's chain and per-frame step and cost launches win
+    # (N = 8192: 6.52 against 6.96 ms).
     PD_FUSED_MAX_N = 4096
 
     def window_pd(self, w: int):
