@@ -89,8 +89,9 @@ template <int NT>
 __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     constexpr int kSel = NT, kWarps = NT / 32;
     __shared__ unsigned int hist[256];
-    __shared__ unsigned long long s_prefix;
+    __shared__ unsigned long long s_prefix, s_mask;
     __shared__ unsigned int s_rem;
+    __shared__ int s_done;
     __shared__ unsigned int s_scan[kWarps + 1];
     __shared__ double red[kWarps];
     __shared__ double s_val[2];
@@ -111,7 +112,10 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
         const int i = t + q * kSel;
         kreg[q] = (in_regs && i < N) ? order_key(a.c_mean[i]) : 0ull;
     }
-    if (t == 0) { s_prefix = 0ull; s_rem = (unsigned)k; }
+    if (t == 0) { s_prefix = 0ull; s_mask = 0ull; s_rem = (unsigned)k; s_done = 0; }
+    // The passes stop early once every key whose leading digits equal the
+    // prefix found so far is needed: the elites are then exactly the keys whose
+    // leading digits are at most the prefix, whatever their remaining digits.
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 56 - 8 * pass;
         if (t < 256) hist[t] = 0u;
@@ -151,28 +155,35 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
             const bool here = (excl < rem && inc >= rem) || (t == 31 && inc < rem);
             const unsigned who = __ballot_sync(0xffffffffu, here);
             if (t == __ffs(who) - 1) {
-                unsigned acc = excl;
-                int b = 8 * t;
-                for (int q = 0; q < 7; ++q, ++b) {
-                    if (acc + c8[q] >= rem) break;
-                    acc += c8[q];
+                // the first of the lane's bins whose running count reaches rem (else its last)
+                unsigned acc = excl, cb = c8[7];
+                int b = 8 * t + 7;
+                bool found = false;
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    if (found) continue;
+                    if (acc + c8[q] >= rem) { found = true; b = 8 * t + q; cb = c8[q]; }
+                    else acc += c8[q];
                 }
                 s_rem = rem - acc;
                 s_prefix = pre | ((unsigned long long)b << shift);
+                s_mask = ~0ull << shift;
+                if (cb == rem - acc) s_done = 1;
             }
         }
         __syncthreads();
+        if (s_done) break;
     }
-    const unsigned long long T = s_prefix;
-    const unsigned need_eq = s_rem;   // elites among the keys equal to T, lowest index first
+    const unsigned long long T = s_prefix, M = s_mask;   // M: the digits decided (all 64 after 8 passes)
+    const unsigned need_eq = s_rem;   // elites among the keys whose digits under M equal T, lowest index first
 
     // ---- elite flags in index order
     unsigned eq_local = 0;
-    for (int i = lo; i < hi; ++i) eq_local += (order_key(a.c_mean[i]) == T);
+    for (int i = lo; i < hi; ++i) eq_local += ((order_key(a.c_mean[i]) & M) == T);
     unsigned eq_before = block_scan<NT>(eq_local, s_scan) - eq_local;
     unsigned el_local = 0;
     for (int i = lo; i < hi; ++i) {
-        const unsigned long long key = order_key(a.c_mean[i]);
+        const unsigned long long key = order_key(a.c_mean[i]) & M;
         bool e = key < T;
         if (key == T) { e = eq_before < need_eq; ++eq_before; }
         a.is_elite[i] = e;
