@@ -86,6 +86,12 @@ struct ih_sim {
     double *wf_cm = nullptr;        // [T][N] window means of every frame (window-mode launches)
     float4 *wf_pose = nullptr;      // [T][N][2] poses of every frame
     int wf_T = 0;
+    // PD window launches: every frame's observation and status, the cost terms
+    float *fo_q = nullptr, *fo_forces = nullptr;
+    float4 *fo_pp = nullptr, *fo_slip = nullptr;
+    int *fo_status = nullptr;
+    double *fo_terms = nullptr;
+    int fo_T = 0;
     int frames_T = 0;               // frames of the last sim_step_frames call, not yet scored
     StepVariant win_variant{0, 0, 0};
     ih_opt_config win_opt{};
@@ -360,6 +366,9 @@ ih_status sim_destroy(ih_sim *s) {
     if (s->adj_scratch) cudaFree(s->adj_scratch);
     if (s->wf_cm) cudaFree(s->wf_cm);
     if (s->wf_pose) cudaFree(s->wf_pose);
+    for (void *q : {(void *)s->fo_q, (void *)s->fo_forces, (void *)s->fo_pp, (void *)s->fo_slip, (void *)s->fo_status,
+                    (void *)s->fo_terms})
+        if (q) cudaFree(q);
     delete s;
     return IH_OK;
 }
@@ -464,9 +473,8 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
         p.shape = s->shape; p.iters = s->iters; p.order = s->order; p.status = s->status;
         p.qj = s->qj; p.qdj = s->qdj; p.forces = s->forces; p.pad_pose = s->pad_pose; p.slip = s->slip;
         p.work = s->work;
-        p.g_q = nullptr; p.g_pose = nullptr; p.g_forces = nullptr; p.g_slip = nullptr;
-        p.c_sum = nullptr; p.c_mean = nullptr; p.cost_mean = nullptr; p.n_window = nullptr;
-        p.cm_frames = nullptr; p.pose_frames = nullptr;
+        p.fo_q = nullptr; p.fo_pp = nullptr; p.fo_forces = nullptr; p.fo_slip = nullptr; p.fo_status = nullptr;
+        p.pose_frames = nullptr;
         cudaError_t e = launch_pd_step(p, s->pd_grid, s->s_max, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "PD step launch");
         s->stepped = true;
@@ -595,6 +603,29 @@ cudaError_t window_buffers(ih_sim *s, int T) {
     s->wf_T = T;
     return cudaSuccess;
 }
+
+// the PD window's per-frame observation, status and cost-term buffers, grown to T frames
+cudaError_t pd_frame_buffers(ih_sim *s, int T) {
+    if (T <= s->fo_T) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return e;
+    void **bufs[6] = {(void **)&s->fo_q, (void **)&s->fo_forces, (void **)&s->fo_pp, (void **)&s->fo_slip,
+                      (void **)&s->fo_status, (void **)&s->fo_terms};
+    for (void **b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    s->fo_T = 0;
+    const size_t ef = (size_t)T * s->cfg.n_envs, P = (size_t)s->n_pads, D = (size_t)s->n_joints;
+    const size_t bytes[6] = {ef * D * sizeof(float), ef * P * 3 * sizeof(float), ef * P * 2 * sizeof(float4),
+                             ef * P * sizeof(float4), ef * sizeof(int), ef * (P + 1) * sizeof(double)};
+    for (int k = 0; k < 6; ++k) {
+        e = cudaMalloc(bufs[k], bytes[k] > 0 ? bytes[k] : 16);
+        if (e != cudaSuccess) return e;   // what was allocated is freed with the handle
+    }
+    s->fo_T = T;
+    return cudaSuccess;
+}
 }  // namespace
 
 ih_status sim_step_frames(ih_sim *s, int32_t frame0, int32_t T, const float *obs) {
@@ -632,6 +663,7 @@ ih_status sim_step_frames_full(ih_sim *s, int32_t frame0, int32_t T, const float
     for (int f = frame0; f < frame0 + T; ++f)
         if (!s->frame_ready[f]) return fail(s, IH_ERR_ARG, "no commands for frame %d", f);
     cudaError_t e = window_buffers(s, T);
+    if (e == cudaSuccess) e = pd_frame_buffers(s, T);
     if (e != cudaSuccess) return cuda_fail(s, e, "window buffers");
     PdArgs p;
     p.sc = dev_scene(s); p.cfg = s->dcfg; p.N = s->cfg.n_envs; p.cmd = s->cmd;
@@ -639,12 +671,20 @@ ih_status sim_step_frames_full(ih_sim *s, int32_t frame0, int32_t T, const float
     p.shape = s->shape; p.iters = s->iters; p.order = s->order; p.status = s->status;
     p.qj = s->qj; p.qdj = s->qdj; p.forces = s->forces; p.pad_pose = s->pad_pose; p.slip = s->slip;
     p.work = s->work;
-    p.g_q = q; p.g_pose = reinterpret_cast<const float4 *>(pad_pose); p.g_forces = forces;
-    p.g_slip = reinterpret_cast<const float4 *>(slip);
-    p.c_sum = s->c_sum; p.c_mean = s->c_mean; p.cost_mean = nullptr; p.n_window = s->n_window;
-    p.cm_frames = s->wf_cm; p.pose_frames = s->wf_pose;
+    p.fo_q = s->fo_q; p.fo_pp = s->fo_pp; p.fo_forces = s->fo_forces; p.fo_slip = s->fo_slip;
+    p.fo_status = s->fo_status; p.pose_frames = s->wf_pose;
     e = launch_pd_step(p, s->pd_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "PD step launch");
+    FramesCostArgs c;
+    c.N = s->cfg.n_envs; c.P = s->n_pads; c.D = s->n_joints; c.T = T; c.cfg = s->dcfg;
+    c.fo_q = s->fo_q; c.fo_pp = s->fo_pp; c.fo_forces = s->fo_forces; c.fo_slip = s->fo_slip;
+    c.fo_status = s->fo_status;
+    c.g_q = q; c.g_pose = reinterpret_cast<const float4 *>(pad_pose); c.g_forces = forces;
+    c.g_slip = reinterpret_cast<const float4 *>(slip);
+    c.terms = s->fo_terms; c.c_sum = s->c_sum; c.c_mean = s->c_mean; c.n_window = s->n_window;
+    c.cm_frames = s->wf_cm;
+    e = launch_frames_cost_full(c, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "frames cost launch");
     s->stepped = true;
     s->frames_T = T;
     return IH_OK;

@@ -118,6 +118,68 @@ __global__ void __launch_bounds__(kCostBlock) cost_kernel(const CostArgs a) {
 
 int cost_blocks(int N) { return (N + kCostBlock - 1) / kCostBlock; }
 
+namespace {
+// One thread per (frame, environment, term) of a PD window: term p < P is pad
+// p's terms, term P the joints' term (skipped for an environment diverged by
+// that frame, which scores +inf).
+constexpr int kTermsBlock = 128;
+__global__ void __launch_bounds__(kTermsBlock) frames_terms_kernel(const FramesCostArgs a) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int P1 = a.P + 1;
+    if (k >= (size_t)a.T * a.N * P1) return;
+    const int p = (int)(k % P1);
+    const size_t ef = k / P1;   // frame * N + environment
+    const int f = (int)(ef / a.N);
+    if (a.fo_status[ef] & kDiverged) return;
+    double w[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) w[q] = (double)a.cfg.w_full[q];
+    double t;
+    if (p == a.P) {
+        t = full_cost_joints(a.fo_q + ef * a.D, a.g_q + (size_t)f * a.D, a.D, w[0]);
+    } else {
+        const size_t o = ef * a.P + p, g = (size_t)f * a.P + p;
+        t = full_cost_pad(w, (double)a.cfg.tau, a.fo_pp[2 * o], a.fo_pp[2 * o + 1], a.g_pose[2 * g],
+                          a.g_pose[2 * g + 1], a.fo_forces + 3 * o, a.g_forces + 3 * g, a.fo_slip[o], a.g_slip[g]);
+    }
+    a.terms[k] = t;
+}
+
+// One thread per environment: each frame's cost (the joints' term, then the
+// pads' in pad order, as frame_cost_full adds them), then the window sum and
+// mean in frame order (as cost_kernel does frame by frame).
+__global__ void __launch_bounds__(kCostBlock) frames_mean_kernel(const FramesCostArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n0 = *a.n_window, P1 = a.P + 1;
+    double s = a.c_sum[i], cm = 0.0;
+    for (int f = 0; f < a.T; ++f) {
+        const size_t ef = (size_t)f * a.N + i;
+        double c = INFINITY;
+        if (!(a.fo_status[ef] & kDiverged)) {
+            const double *t = a.terms + ef * P1;
+            c = t[a.P];
+            for (int p = 0; p < a.P; ++p) c = __dadd_rn(c, t[p]);
+        }
+        s = __dadd_rn(s, c);
+        cm = __ddiv_rn(s, (double)(n0 + f + 1));
+        a.cm_frames[ef] = cm;
+    }
+    a.c_sum[i] = s;
+    a.c_mean[i] = cm;
+}
+}  // namespace
+
+cudaError_t launch_frames_cost_full(const FramesCostArgs &a, cudaStream_t s) {
+    if (a.N < 1 || a.T < 1) return cudaSuccess;
+    const size_t total = (size_t)a.T * a.N * (a.P + 1);
+    frames_terms_kernel<<<(unsigned)((total + kTermsBlock - 1) / kTermsBlock), kTermsBlock, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    frames_mean_kernel<<<cost_blocks(a.N), kCostBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cost(const CostArgs &a, cudaStream_t s) {
     cost_kernel<<<cost_blocks(a.N), kCostBlock, 0, s>>>(a);
     return cudaGetLastError();

@@ -249,17 +249,38 @@ struct PdArgs {
     float4 *pad_pose;         // [N][P][2]: (position, 0), (quaternion w x y z)
     float4 *slip;             // [N][P]: (d_x, d_y, flag bits, 0)
     unsigned long long *work; // [6]
-    // window mode (cm_frames != null): n_frames frames, each scored with the
-    // full cost against the truth's observation of that frame
-    const float *g_q;         // [n_frames][D]
-    const float4 *g_pose;     // [n_frames][P][2]
-    const float *g_forces;    // [n_frames][P][3]
-    const float4 *g_slip;     // [n_frames][P]
-    double *c_sum, *c_mean, *cost_mean;   // [N] (cost_mean may be null)
-    const int *n_window;
-    double *cm_frames;        // [n_frames][N]
+    // window mode (pose_frames != null): n_frames frames, each frame's
+    // observation, status and pose written out for the frames' cost launches
+    float *fo_q;              // [n_frames][N][D]
+    float4 *fo_pp;            // [n_frames][N][P][2]
+    float *fo_forces;         // [n_frames][N][P][3]
+    float4 *fo_slip;          // [n_frames][N][P]
+    int *fo_status;           // [n_frames][N]
     float4 *pose_frames;      // [n_frames][N][2]
 };
+// The full cost of every frame of a PD window launch against the truth's
+// observation of that frame: one thread per (frame, environment, term) forms
+// a pad's terms (or the joints' term), then one thread per environment adds
+// each frame's terms (joints first, pads in order) and the window sum and mean
+// in frame order -- the cost kernel's functions in the cost kernel's order.
+struct FramesCostArgs {
+    int N, P, D, T;
+    DevConfig cfg;
+    const float *fo_q;        // [T][N][D]
+    const float4 *fo_pp;      // [T][N][P][2]
+    const float *fo_forces;   // [T][N][P][3]
+    const float4 *fo_slip;    // [T][N][P]
+    const int *fo_status;     // [T][N]
+    const float *g_q;         // [T][D]
+    const float4 *g_pose;     // [T][P][2]
+    const float *g_forces;    // [T][P][3]
+    const float4 *g_slip;     // [T][P]
+    double *terms;            // [T][N][P + 1] scratch
+    double *c_sum, *c_mean;   // [N]
+    const int *n_window;
+    double *cm_frames;        // [T][N]
+};
+cudaError_t launch_frames_cost_full(const FramesCostArgs &a, cudaStream_t s);
 size_t pd_step_smem_bytes(int s_max, int c_max);
 cudaError_t pd_step_prepare(int s_max, int c_max);
 int pd_step_grid(int N, int sms);

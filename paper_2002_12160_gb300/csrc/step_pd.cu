@@ -34,7 +34,6 @@
 #include <cstddef>
 
 #include "contact.cuh"
-#include "full_cost.cuh"
 #include "hand.cuh"
 #include "internal.cuh"
 
@@ -66,11 +65,6 @@ struct PdWarp {
     double pterm[IH_MAX_PADS];                // window mode: each pad's cost terms
 };
 static_assert(sizeof(PdWarp) % 16 == 0, "warp records keep 16-byte alignment");
-static_assert(sizeof(PdWarp::slip) >= 4 * IH_MAX_PADS * sizeof(double) &&
-                  sizeof(PdWarp::clc) >= 2 * IH_MAX_PADS * sizeof(double),
-              "the window cost reuses the slip sums and cluster centres as scratch");
-static_assert(offsetof(PdWarp, slip) % sizeof(double) == 0 && offsetof(PdWarp, clc) % sizeof(double) == 0,
-              "doubles in the reused scratch stay aligned");
 
 __host__ __device__ constexpr size_t pd_align16(size_t b) { return (b + 15) & ~size_t(15); }
 // block tables: pads per link and their axial intervals
@@ -152,10 +146,9 @@ __global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, in
     const float Mj = cfg.armature + h * cfg.kd + h * h * cfg.kp, inv_Mj = 1.0f / Mj;
     const int cap = cfg.c_max;
     const float inv_ns = 1.0f / (float)ns;
-    // window mode (cm_frames != null): every frame scored against the truth's
-    // observation with the full cost, the argmin taken afterwards
-    const bool window_mode = a.cm_frames != nullptr;
-    const int n_win0 = window_mode ? *a.n_window : 0;
+    // window mode (pose_frames != null): every frame's observation written out
+    // for the frames' cost launches, the argmin taken afterwards
+    const bool window_mode = a.pose_frames != nullptr;
 
     unsigned char *pl_cnt = smem;
     unsigned char *pl_id = smem + pd_align16(kPdMaxLinks);
@@ -244,7 +237,6 @@ __global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, in
             }
             __syncwarp();
         };
-        double c_sum_env = (window_mode && lane == 0) ? a.c_sum[env] : 0.0;
 
         for (int fr = 0; fr < a.n_frames; ++fr) {
             for (int k = lane; k < 3 * P; k += 32) W.padf[k] = 0.0f;
@@ -553,59 +545,20 @@ __global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, in
                 if (!fin) st |= IH_ENV_NONFINITE;
                 else if (dot(x, x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
             }
-            if (window_mode) {   // this frame's full cost against the truth's observation
+            if (window_mode) {   // this frame's observation, status and pose
                 frame_obs();
-                const double tau = (double)cfg.tau;
-                double wf[10];
-#pragma unroll
-                for (int k = 0; k < 10; ++k) wf[k] = (double)cfg.w_full[k];
-                // four lanes per pad form its four quantities, then one lane per pad
-                // adds its terms and lane 0 the joints' term and the pads' in pad order
-                // (the cost kernel's bits: the same functions on the same values)
-                double *tq = reinterpret_cast<double *>(W.slip);   // [pad][k]; the frame's slip sums are spent
-                double *fm = reinterpret_cast<double *>(W.clc);    // [pad][2]: force magnitudes
-                for (int u = lane; u < 4 * P; u += 32) {
-                    const int p = u >> 2, k = u & 3;
-                    const size_t o = (size_t)fr * P + p;
-                    const float fa[3] = {W.padf[3 * p] * inv_ns, W.padf[3 * p + 1] * inv_ns, W.padf[3 * p + 2] * inv_ns};
-                    double na, nb;
-                    tq[u] = fc_pad_term(k, W.opp[p][0], W.opp[p][1], a.g_pose[2 * o], a.g_pose[2 * o + 1], fa,
-                                        a.g_forces + 3 * o, W.osl[p], a.g_slip[o], na, nb);
-                    if (k == 1) {
-                        fm[2 * p] = na;
-                        fm[2 * p + 1] = nb;
-                    }
+                const size_t ef = (size_t)fr * a.N + env;
+                for (int p = lane; p < P; p += 32) {
+                    a.fo_pp[2 * (ef * P + p)] = W.opp[p][0];
+                    a.fo_pp[2 * (ef * P + p) + 1] = W.opp[p][1];
+                    a.fo_slip[ef * P + p] = W.osl[p];
                 }
-                // the joints' squared differences (one lane each), summed in joint order
-                double sq = 0.0;
-                if (lane < D) {
-                    const double d = __dsub_rn((double)W.qj[lane], (double)a.g_q[(size_t)fr * D + lane]);
-                    sq = __dmul_rn(d, d);
-                }
-                double dq = 0.0;
-                for (int j = 0; j < D; ++j) dq = __dadd_rn(dq, __shfl_sync(0xffffffffu, sq, j));
-                __syncwarp();
-                for (int p = lane; p < P; p += 32)
-                    W.pterm[p] = fc_pad_combine(wf, tau, tq + 4 * p, fm[2 * p], fm[2 * p + 1], W.osl[p].z,
-                                                a.g_slip[(size_t)fr * P + p].z);
-                __syncwarp();
+                for (int k = lane; k < 3 * P; k += 32) a.fo_forces[ef * 3 * P + k] = W.padf[k] * inv_ns;
+                for (int k = lane; k < D; k += 32) a.fo_q[ef * D + k] = W.qj[k];
                 if (lane == 0) {
-                    double c = INFINITY;
-                    if (!(st & kDiverged)) {
-                        c = __dmul_rn(wf[0], sqrt(dq));   // full_cost_joints
-                        for (int p = 0; p < P; ++p) c = __dadd_rn(c, W.pterm[p]);
-                    }
-                    c_sum_env = __dadd_rn(c_sum_env, c);
-                    const double cm = __ddiv_rn(c_sum_env, (double)(n_win0 + fr + 1));
-                    a.cm_frames[(size_t)fr * a.N + env] = cm;
-                    float4 *pf = a.pose_frames + 2 * ((size_t)fr * a.N + env);
-                    pf[0] = make_float4(x.x, x.y, x.z, 0.0f);
-                    pf[1] = make_float4(q.w, q.x, q.y, q.z);
-                    if (fr == a.n_frames - 1) {
-                        a.c_sum[env] = c_sum_env;
-                        a.c_mean[env] = cm;
-                        if (a.cost_mean) a.cost_mean[env] = cm;
-                    }
+                    a.fo_status[ef] = st;
+                    a.pose_frames[2 * ef] = make_float4(x.x, x.y, x.z, 0.0f);
+                    a.pose_frames[2 * ef + 1] = make_float4(q.w, q.x, q.y, q.z);
                 }
                 __syncwarp();
             }
