@@ -568,11 +568,12 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
              speed_only=False):
     """The PD-driven hand (joints as state, full observation, full cost):
     - throughput on the cylinder trajectory at N = n_envs and 8 n_envs: per
-      window one T-frame PD step launch scoring every frame with the full
-      cost, the per-frame argmin and the optimizer, timed with CUDA events
-      (L2 flushed before every window), the step launch separately with its
-      counted work against the FP32 peak; and the same window as per-frame
-      step and full-cost launches;
+      window one T-frame PD step launch, then the full cost of every frame
+      (two launches), the per-frame argmin and the optimizer, timed with CUDA
+      events (L2 flushed before every window), the step call (the step launch
+      and its cost launches) separately with its counted work against the
+      FP32 peak; and the same window as per-frame step and full-cost
+      launches;
     - the oracle's PD step on the host, single thread, on a bounded sample;
     - tracking error (median ADD over seeded trajectories, mm) with the full
       cost, without the slip terms, and with the force and contact terms only

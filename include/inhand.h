@@ -315,9 +315,11 @@ ih_status sim_get_hand(ih_sim *sim, float *q, float *qd);
 ih_status cost_eval_full(ih_sim *sim, const float *q, const float *pad_pose, const float *forces,
                          const float *slip, double *cost_mean, int32_t *argmin, float *est_pose);
 
-/* PD hand only: T frames from frame0 in one launch, each scored with the full
- * cost (as cost_eval_full) against the ground truth's observation of that
- * frame: q float[T][D], pad_pose float[T][P][8], forces float[T][P][3], slip
+/* PD hand only: T frames from frame0 in one step launch, each frame's
+ * observation kept and then scored with the full cost (as cost_eval_full)
+ * against the ground truth's observation of that frame by two further
+ * launches (the pads' and joints' terms in parallel, then each environment's
+ * sums and window means): q float[T][D], pad_pose float[T][P][8], forces float[T][P][3], slip
  * float[T][P][4] (device; pad_pose and slip 16-byte aligned). As with
  * sim_step_frames, sim_frames_argmin must follow (IH_ERR_STATE otherwise) and
  * gives every frame's argmin and estimate; results equal T calls of sim_step

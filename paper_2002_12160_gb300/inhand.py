@@ -295,8 +295,8 @@ class Sim:
                    _ptr(argmin), _ptr(est_pose))
 
     def sim_step_frames_full(self, frame0: int, q, pad_pose, forces, slip):
-        """PD hand: T frames in one launch, each scored with the full cost against
-        the truth's observation (q [T, D], pad_pose [T, P, 8], forces [T, P, 3],
+        """PD hand: T frames in one step launch, each then scored with the full
+        cost against the truth's observation (q [T, D], pad_pose [T, P, 8], forces [T, P, 3],
         slip [T, P, 4]); follow with sim_frames_argmin."""
         T = forces.shape[0]
         _check(q, torch.float32, (T, self.n_joints), "q")

@@ -90,16 +90,15 @@ class Tracker:
         self.sim.sim_track_window(f0, self.obs[f0:f0 + T], self.wl.opt, w, self.est[f0:f0 + T],
                                   self.argmin[f0:f0 + T])
 
-    # The PD window's T frames in one launch (cost inside it) is faster while the
-    # environments fit in about one wave (cylinder, N = 1024: 1.02 against
-    # 1.90 ms per window); with several waves the cost's FP64 work lengthens
-    # every environment's chain and per-frame step and cost launches win
-    # (N = 8192: 6.52 against 6.96 ms).
+    # The PD window's T frames in one step launch (then scored by two launches)
+    # is faster while the environments fit in about one wave (cylinder,
+    # N = 1024: 0.97 against 1.77 ms per window); with several waves per-frame
+    # step and cost launches win (N = 8192: 6.37 against 6.57 ms).
     PD_FUSED_MAX_N = 4096
 
     def window_pd(self, w: int):
         """A window with the PD-driven hand: its T frames in one step launch,
-        each scored with the full ten-term cost against the ground truth's
+        each then scored with the full ten-term cost against the ground truth's
         observation, every frame's argmin and estimate, then the optimizer
         update (per-frame launches above PD_FUSED_MAX_N environments)."""
         if self.n > self.PD_FUSED_MAX_N:
