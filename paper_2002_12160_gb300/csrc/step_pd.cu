@@ -450,10 +450,7 @@ __global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, in
                             acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
                             acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                         }
-                        width_sum6<32>(acc, 0xffffffffu, lane);
-                        vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
-                        ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
-                        __syncwarp();
+                        __syncwarp();   // this iteration's impulses, for the joints' lanes
                         // lane a = 4 f + j sums the contacts of link a + 1 (its impulses and
                         // their moments about the origin), then a suffix over the finger's
                         // four lanes gives joint a the links it moves, and
@@ -468,9 +465,13 @@ __global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, in
                                 sv[3] += t.x; sv[4] += t.y; sv[5] += t.z;
                             }
                         }
-                        if (split) {
+                        // the object's sums over the warp and the joints' shares are two
+                        // independent chains of shuffles, kept in one straight stretch of code
+                        width_sum6<32>(acc, 0xffffffffu, lane);
 #pragma unroll
-                            for (int k = 0; k < 6; ++k) sv[k] += __shfl_down_sync(0xffffffffu, sv[k], 16);
+                        for (int k = 0; k < 6; ++k) {
+                            const float o = __shfl_down_sync(0xffffffffu, sv[k], 16);
+                            sv[k] += split ? o : 0.0f;
                         }
 #pragma unroll
                         for (int off = 1; off < 4; off <<= 1) {
@@ -490,6 +491,8 @@ __global__ void __launch_bounds__(kPdBlock, 2) pd_step_kernel(const PdArgs a, in
                             qd_new = jqs - g * inv_Mj;
                             W.qd[lane] = qd_new;
                         }
+                        vv = v_pred + mk(acc[0], acc[1], acc[2]) * inv_m;
+                        ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
                         pd_joint_twists(W, lane, D, jz, jzo, qd_new);   // for the next iteration and the slip sensing
                         __syncwarp();
                     }
