@@ -93,7 +93,7 @@ class Tracker:
     # The PD window's T frames in one step launch (then scored by two launches)
     # is faster while the environments fit in about one wave (cylinder,
     # N = 1024: 0.97 against 1.77 ms per window); with several waves per-frame
-    # step and cost launches win (N = 8192: 6.37 against 6.57 ms).
+    # step and cost launches win (N = 8192: 6.27 against 6.48 ms).
     PD_FUSED_MAX_N = 4096
 
     def window_pd(self, w: int):
