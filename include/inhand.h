@@ -325,8 +325,9 @@ ih_status cost_eval_full(ih_sim *sim, const float *q, const float *pad_pose, con
  * gives every frame's argmin and estimate; results equal T calls of sim_step
  * and cost_eval_full. The handle allocates (on the first call, or for a larger
  * T, after synchronising its stream) device buffers of about
- * T x N x (4 D + 60 P + 12 + 8 (P + 1)) bytes for the frames' observations,
- * statuses, window means and cost terms; they are freed with the handle. */
+ * T x N x (4 D + 60 P + 44 + 8 (P + 1)) bytes for the frames' observations,
+ * statuses, poses, window means and cost terms; they are freed with the
+ * handle. */
 ih_status sim_step_frames_full(ih_sim *sim, int32_t frame0, int32_t T, const float *q, const float *pad_pose,
                                const float *forces, const float *slip);
 
