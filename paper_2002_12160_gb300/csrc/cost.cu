@@ -145,28 +145,44 @@ __global__ void __launch_bounds__(kTermsBlock) frames_terms_kernel(const FramesC
     a.terms[k] = t;
 }
 
-// One thread per environment: each frame's cost (the joints' term, then the
-// pads' in pad order, as frame_cost_full adds them), then the window sum and
-// mean in frame order (as cost_kernel does frame by frame).
-__global__ void __launch_bounds__(kCostBlock) frames_mean_kernel(const FramesCostArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
+// One warp per environment, lane f for frame f (32 frames per round): each
+// frame's cost (the joints' term, then the pads' in pad order, as
+// frame_cost_full adds them) on its lane, the window sum in frame order (every
+// lane runs the same chain of additions) and each frame's mean on its lane --
+// the additions and divisions cost_kernel makes frame by frame.
+constexpr int kMeanBlock = 128;
+__global__ void __launch_bounds__(kMeanBlock) frames_mean_kernel(const FramesCostArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.N) return;   // whole warps
     const int n0 = *a.n_window, P1 = a.P + 1;
-    double s = a.c_sum[i], cm = 0.0;
-    for (int f = 0; f < a.T; ++f) {
-        const size_t ef = (size_t)f * a.N + i;
+    double s = a.c_sum[i];
+    for (int f0 = 0; f0 < a.T; f0 += 32) {
+        const int f = f0 + lane;
         double c = INFINITY;
-        if (!(a.fo_status[ef] & kDiverged)) {
-            const double *t = a.terms + ef * P1;
-            c = t[a.P];
-            for (int p = 0; p < a.P; ++p) c = __dadd_rn(c, t[p]);
+        if (f < a.T) {
+            const size_t ef = (size_t)f * a.N + i;
+            if (!(a.fo_status[ef] & kDiverged)) {
+                const double *t = a.terms + ef * P1;
+                c = t[a.P];
+                for (int p = 0; p < a.P; ++p) c = __dadd_rn(c, t[p]);
+            }
         }
-        s = __dadd_rn(s, c);
-        cm = __ddiv_rn(s, (double)(n0 + f + 1));
-        a.cm_frames[ef] = cm;
+        const int nf = min(32, a.T - f0);
+        double sf = 0.0;   // the window sum after this lane's frame
+        for (int k = 0; k < nf; ++k) {
+            s = __dadd_rn(s, __shfl_sync(0xffffffffu, c, k));
+            if (lane == k) sf = s;
+        }
+        if (f < a.T) {
+            const double cm = __ddiv_rn(sf, (double)(n0 + f + 1));
+            a.cm_frames[(size_t)f * a.N + i] = cm;
+            if (f == a.T - 1) {
+                a.c_sum[i] = sf;
+                a.c_mean[i] = cm;
+            }
+        }
     }
-    a.c_sum[i] = s;
-    a.c_mean[i] = cm;
 }
 }  // namespace
 
@@ -176,7 +192,7 @@ cudaError_t launch_frames_cost_full(const FramesCostArgs &a, cudaStream_t s) {
     frames_terms_kernel<<<(unsigned)((total + kTermsBlock - 1) / kTermsBlock), kTermsBlock, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    frames_mean_kernel<<<cost_blocks(a.N), kCostBlock, 0, s>>>(a);
+    frames_mean_kernel<<<(unsigned)(((size_t)a.N * 32 + kMeanBlock - 1) / kMeanBlock), kMeanBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
