@@ -247,47 +247,50 @@ def test_pd_overflow_and_escape_flags_match_oracle():
 
 
 def test_pd_window_launch_equals_the_separate_calls():
-    """sim_step_frames_full + sim_frames_argmin (the window's frames in one launch,
-    each scored with the full cost inside it) equal T calls of sim_step and
-    cost_eval_full bit for bit: estimates, argmins, the optimizer's parents,
-    the state and the joints, over two windows."""
+    """sim_step_frames_full + sim_frames_argmin (the window's frames in one step
+    launch, then scored by the frames' cost launches) equal per-frame calls of
+    sim_step and cost_eval_full bit for bit: estimates, argmins, the optimizer's
+    parents, the state and the joints, over three windows of 3, 5 and 2
+    frames (the per-frame buffers grow, then are reused)."""
     from paper_2002_12160_gb300 import inhand
-    T, n = 5, 150
-    wl = _pd("tracking_cyl64", n, 2 * T)
+    lens, n = (3, 5, 2), 150
+    F = sum(lens)
+    wl = _pd("tracking_cyl64", n, F)
     d = dev()
-    g = start(wl, n=n, frames=2 * T)   # the truth's observations: environment 3 of another run
+    g = start(wl, n=n, frames=F)   # the truth's observations: environment 3 of another run
     D, P = wl.scene.n_joints, wl.scene.n_pads
-    oq = torch.empty((2 * T, D), dtype=torch.float32, device=d)
-    opp = torch.empty((2 * T, P, 8), dtype=torch.float32, device=d)
-    of = torch.empty((2 * T, P, 3), dtype=torch.float32, device=d)
-    osl = torch.empty((2 * T, P, 4), dtype=torch.float32, device=d)
-    for f in range(2 * T):
+    oq = torch.empty((F, D), dtype=torch.float32, device=d)
+    opp = torch.empty((F, P, 8), dtype=torch.float32, device=d)
+    of = torch.empty((F, P, 3), dtype=torch.float32, device=d)
+    osl = torch.empty((F, P, 4), dtype=torch.float32, device=d)
+    for f in range(F):
         g.sim_step(f, 1)
         q, pp, slip = g.sim_read_observation()
         forces, _ = g.sim_read_sensors()
         oq[f], opp[f], of[f], osl[f] = q[3], pp[3], forces[3], slip[3]
-    a = start(wl, n=n, frames=2 * T)
-    b = start(wl, n=n, frames=2 * T)
-    est_a = torch.zeros((2 * T, 8), dtype=torch.float32, device=d)
+    a = start(wl, n=n, frames=F)
+    b = start(wl, n=n, frames=F)
+    est_a = torch.zeros((F, 8), dtype=torch.float32, device=d)
     est_b = torch.zeros_like(est_a)
-    am_a = torch.zeros((2 * T,), dtype=torch.int32, device=d)
+    am_a = torch.zeros((F,), dtype=torch.int32, device=d)
     am_b = torch.zeros_like(am_a)
     par_a = torch.empty(n, dtype=torch.int32, device=d)
     par_b = torch.empty_like(par_a)
-    for w in range(2):
-        for k in range(T):
-            f = w * T + k
+    f0 = 0
+    for w, T in enumerate(lens):
+        for f in range(f0, f0 + T):
             a.sim_step(f, 1)
             a.cost_eval_full(oq[f], opp[f], of[f], osl[f], None, am_a[f:f + 1], est_a[f])
         a.optimizer_update(wl.opt, w, None, par_a)
-        s = slice(w * T, (w + 1) * T)
-        b.sim_step_frames_full(w * T, oq[s], opp[s], of[s], osl[s])
+        s = slice(f0, f0 + T)
+        b.sim_step_frames_full(f0, oq[s], opp[s], of[s], osl[s])
         if w == 0:   # scoring again before the argmin is refused
             with pytest.raises(inhand.InhandError):
                 b.cost_eval_full(oq[0], opp[0], of[0], osl[0])
         b.sim_frames_argmin(est_b[s], am_b[s])
         b.optimizer_update(wl.opt, w, None, par_b)
         assert torch.equal(par_a, par_b)
+        f0 += T
     assert torch.equal(est_a, est_b) and torch.equal(am_a, am_b)
     for x, y in zip(a.sim_get_state(), b.sim_get_state()):
         assert torch.equal(x, y)
@@ -299,7 +302,7 @@ def test_pd_window_launch_equals_the_separate_calls():
 
 def test_pd_full_size_window_launch_sampled_parity():
     """At the benchmark's size (N = 1024 cylinders) and in the launch the
-    benchmark times (a window launch with the full cost inside), a sample of
+    benchmark times (a window's step launch and its frames' cost launches), a sample of
     environments checked one by one against the oracle's step, and the
     launch's argmin and estimate against the oracle's full cost of the GPU's
     observation."""
