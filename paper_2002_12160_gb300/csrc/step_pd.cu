@@ -30,7 +30,10 @@
 //      contact's impulse to its pad, with the impulse-weighted relative slip
 //      velocity, normal and spin for the slip sensing.
 // At the end of a frame the fingers' kinematics at the final joint angles give
-// the pads' poses, and the slip sums give d_t and r_t.
+// the pads' poses, and the slip sums give d_t and r_t. A window launch (T
+// frames) writes every frame's observation, status and pose; the frames' full
+// cost and window means are then formed by launches of their own (cost.cu),
+// so this kernel does no FP64 work.
 #include <cstddef>
 
 #include "contact.cuh"
