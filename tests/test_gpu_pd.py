@@ -246,14 +246,16 @@ def test_pd_overflow_and_escape_flags_match_oracle():
     assert torch.equal(sim.sim_get_state()[0], before)
 
 
-@pytest.mark.parametrize("name,n,lens", [("tracking_cyl64", 150, (3, 5, 2)), ("tracking_box27", 40, (35, 4))])
+@pytest.mark.parametrize("name,n,lens", [("tracking_cyl64", 150, (3, 5, 2)), ("tracking_box27", 40, (35, 4)),
+                                         ("uneven_mixed", 67, (4, 3))])
 def test_pd_window_launch_equals_the_separate_calls(name, n, lens):
     """sim_step_frames_full + sim_frames_argmin (the window's frames in one step
     launch, then scored by the frames' cost launches) equal per-frame calls of
     sim_step and cost_eval_full bit for bit: estimates, argmins, the optimizer's
     parents, the state and the joints, over windows of 3, 5 and 2 frames (the
-    per-frame buffers grow, then are reused) and of 35 and 4 frames (the
-    window means run over more frames than a warp has lanes)."""
+    per-frame buffers grow, then are reused), of 35 and 4 frames (the window
+    means run over more frames than a warp has lanes), and on the uneven batch
+    (five fingers, 16 pads, mixed shapes and iteration counts)."""
     from paper_2002_12160_gb300 import inhand
     F = sum(lens)
     wl = _pd(name, n, F)
