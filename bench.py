@@ -11,7 +11,17 @@ iterations, 2 substeps at 30 Hz). Inputs are seeded and synthetic.
 Output: one JSON line (metric env-steps/s: environment-frames advanced per
 second including cost, argmin and the amortised optimizer update).
   --impl ours        the CUDA path through libinhand.so (default)
-  --impl reference   the FP64 CPU oracle on the same workload (bounded sample)
+  --impl reference   the FP64 CPU oracle on the same workload (bounded sample,
+                     one thread per host core)
+Besides the main line (with the step kernel's FP32 roofline against the
+measured FMA throughput of the GPU, and the end-to-end rate through the C ABI
+from pinned host buffers), a single-GPU run also measures the uneven batch
+(N = 8192, shapes of 16-256 spheres, 10/20/40 iterations), the mug sweep
+(N = 1024 ... 32768, forward and forward + adjoint) with a bounded search for
+the largest N that holds 30 tracking frames/s, the forward + adjoint of a
+30-frame horizon (N = 1024), the PD-driven hand's window, and the oracle on
+the host cores. The paper's studies (optimizer comparison, cost-term
+ablation, warm start, refined vs plain tracking) run with --part.
 """
 from __future__ import annotations
 
@@ -84,14 +94,28 @@ def parse():
     p.add_argument("--workload", default="tracking_cyl64")
     p.add_argument("--n-envs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-adjoint", action="store_true",
-                   help="skip the adjoint throughput and the refinement-vs-plain tracking study")
-    p.add_argument("--part", choices=["all", "adjoint", "optimizers", "warm", "pd", "pd_speed"], default="all",
-                   help="adjoint / optimizers / warm / pd (pd_speed: its throughput only): only that block (profiling, studies)")
+    p.add_argument("--main-only", action="store_true",
+                   help="only the main line (no uneven batch, mug sweep, largest-N search, adjoint, PD hand)")
+    p.add_argument("--part", choices=["all", "adjoint", "optimizers", "warm", "pd", "pd_speed", "refine"],
+                   default="all",
+                   help="the paper's studies, outside the default line: adjoint throughput, optimizer "
+                        "comparison, warm start, PD hand (with the cost-term ablation; pd_speed: throughput "
+                        "only), refined vs plain update at equal wall time")
     p.add_argument("--shape", default=None, help="force the step kernel shape, e.g. 64x2 (default: autotune)")
     p.add_argument("--sweep", default=None,
                    help="comma-separated N values: also time the workload at each N (tracking frames/s)")
     return p.parse_args()
+
+
+def hbm_peak():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json),
+    else the pool's earlier single measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "fallback (an earlier copy measurement on a GB300)"
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -176,88 +200,127 @@ def max_over_ranks(x, world):
 
 
 # ----------------------------------------------------------------------------- reference arm
-def run_reference(args, rank, world):
-    """The FP64 oracle as it stands on the host cores: whole tracking windows on
-    a bounded sample of environments of the same workload."""
-    if rank != 0:
-        return
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_tracking_rate(workload, threads, budget_s, n_per_thread=16, n_frames=300, T=10, max_windows=None):
+    """The FP64 oracle as it stands, tracking on the host: each of `threads`
+    threads runs its own `n_per_thread` environments of the workload (its first
+    `n_frames` frames replayed from fresh initial samples) through whole windows
+    -- every frame the ground-truth environment's step (the observation), the
+    samples' step and cost, then the optimizer -- until the time budget (or
+    `max_windows` windows per thread) is spent. The oracle is C called through
+    ctypes, which releases the interpreter lock, so the threads run on separate
+    cores. Returns (env-steps/s of the samples, windows timed, frames per thread)."""
+    import threading
     import oracle as O
     from paper_2002_12160_gb300 import workloads as W
-    T = 10
-    n_sample = 16
-    wl = W.make_workload(args.workload, n_envs=n_sample, frames=(args.warmup + args.steps) * T + 1)
+    wl = W.make_workload(workload, n_envs=n_per_thread, frames=n_frames)
     osc = O.OracleScene(wl.scene)
-    pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed)
-    st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
-    gt = O.State(O.pose8_to7(wl.gt_pose)[None], np.zeros((1, 6)), np.array([wl.theta_gt]))
-    times = []
-    frame = 0
-    for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        c_sum = np.zeros(n_sample)
-        for k in range(T):
-            obs, _ = O.step(osc, wl.sim, gt, wl.q_traj, frame, 1)
-            forces, _ = O.step(osc, wl.sim, st, wl.q_traj, frame, 1)
-            i, c_mean, _ = O.cost(wl.sim, forces, obs[0], st.status, c_sum, k + 1)
-            frame += 1
-        O.optimizer(wl.opt, st, c_mean, wl.seed, s)
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    ms = 1e3 * sum(times) / len(times)
-    value = n_sample * T / (ms / 1e3)
+    done = [0] * threads
+    wins = [0] * threads
+    deadline = [None]
+    start = threading.Barrier(threads + 1)
+
+    def worker(t):
+        gt0 = wl.gt_pose if wl.gt_pose is not None else wl.nominal_pose
+        upd = 0
+        start.wait()
+        while time.perf_counter() < deadline[0] and (max_windows is None or wins[t] < max_windows):
+            pose, theta = O.sample_initial(n_per_thread, O.pose8_to7(wl.nominal_pose), wl.init,
+                                           wl.seed + 1000 * t + upd)
+            st = O.State(pose, np.zeros((n_per_thread, 6)), theta, wl.shape_id, wl.iters)
+            gt = O.State(O.pose8_to7(gt0)[None], np.zeros((1, 6)), np.array([wl.theta_gt]))
+            f = 0
+            while f + T <= n_frames and time.perf_counter() < deadline[0] and \
+                    (max_windows is None or wins[t] < max_windows):
+                c_sum = np.zeros(n_per_thread)
+                for k in range(T):
+                    obs, _ = O.step(osc, wl.sim, gt, wl.q_traj, f, 1)
+                    forces, _ = O.step(osc, wl.sim, st, wl.q_traj, f, 1)
+                    _, c_mean, _ = O.cost(wl.sim, forces, obs[0], st.status, c_sum, k + 1)
+                    f += 1
+                    done[t] += 1
+                O.optimizer(wl.opt, st, c_mean, wl.seed + t, upd)
+                upd += 1
+                wins[t] += 1
+
+    th = [threading.Thread(target=worker, args=(t,), daemon=True) for t in range(threads)]
+    for x in th:
+        x.start()
+    deadline[0] = time.perf_counter() + budget_s
+    t0 = time.perf_counter()
+    start.wait()
+    for x in th:
+        x.join()
+    el = time.perf_counter() - t0
+    return n_per_thread * sum(done) / el, sum(wins), done, el
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle as it stands on the host cores, on the workload our arm
+    runs: whole tracking windows on a bounded sample of its environments (16
+    per host core). Rank 0 alone runs it."""
+    if rank != 0:
+        return
+    from paper_2002_12160_gb300 import workloads as W
+    T = 10
+    cores = host_cores()
+    n_per = 16
+    wl_full = W.make_workload(args.workload, n_envs=args.n_envs)
+    # each timed step: one window per core; warm-up steps first
+    _ = oracle_tracking_rate(args.workload, cores, 1e9, n_per_thread=n_per, max_windows=args.warmup)
+    value, wins, done, el = oracle_tracking_rate(args.workload, cores, 1e9, n_per_thread=n_per,
+                                                 max_windows=args.steps)
+    ms = 1e3 * el / max(1, args.steps)
+    sample = (f"{n_per} envs x {cores} threads (one per host core) of {args.workload}, whole {T}-frame windows "
+              f"incl. each thread's ground-truth env and the optimizer; {args.steps} windows per thread timed "
+              f"after {args.warmup} warm-up windows")
     line = {"impl": "reference", "metric": "env-steps/s", "value": value, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "n_envs_sampled": n_sample,
-                                            "window_frames": T},
-            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n_sample} envs x {T}-frame windows incl. the ground-truth env"},
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_envs": wl_full.n_envs, "window_frames": T,
+                       "links": wl_full.scene.n_links, "pads": wl_full.scene.n_pads,
+                       "substeps": wl_full.sim.substeps, "parallelism": f"replicas{args.gpus}"},
+            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(workload, budget_s=15.0):
-    """Oracle env-steps/s on the host, single thread, on a bounded sample: the
-    workload's first 300 frames (windows of 10 + optimizer) replayed from fresh
-    initial samples until the time budget is spent."""
-    import oracle as O
-    from paper_2002_12160_gb300 import workloads as W
-    T, n_sample, n_frames = 10, 32, 300
-    wl = W.make_workload(workload, n_envs=n_sample, frames=n_frames)
-    osc = O.OracleScene(wl.scene)
-    frames = 0
-    upd = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        pose, theta = O.sample_initial(n_sample, O.pose8_to7(wl.nominal_pose), wl.init, wl.seed + upd)
-        st = O.State(pose, np.zeros((n_sample, 6)), theta, wl.shape_id, wl.iters)
-        f = 0
-        while f + T <= n_frames and time.perf_counter() - t0 < budget_s:
-            c_sum = np.zeros(n_sample)
-            for k in range(T):
-                forces, _ = O.step(osc, wl.sim, st, wl.q_traj, f, 1)
-                _, c_mean, _ = O.cost(wl.sim, forces, forces[0], st.status, c_sum, k + 1)
-                f += 1
-                frames += 1
-            O.optimizer(wl.opt, st, c_mean, wl.seed, upd)
-            upd += 1
-    el = time.perf_counter() - t0
-    return {"value": n_sample * frames / el, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_sample} envs x {frames} frames of {workload} (its first {n_frames} frames replayed "
-                      f"from fresh samples; windows of {T} + optimizer), single thread, {el:.1f} s"}
+def cpu_baseline(workload, budget_s=8.0):
+    """The oracle's tracking throughput on the host (env-steps/s), all host
+    cores (one thread each) and one thread, each leg on a bounded sample."""
+    cores = host_cores()
+    multi, _, done_m, el_m = oracle_tracking_rate(workload, cores, budget_s)
+    single, _, done_s, el_s = oracle_tracking_rate(workload, 1, budget_s)
+    return {"value": multi, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"16 envs per thread x {cores} threads of {workload}, {sum(done_m)} thread-frames in "
+                      f"{el_m:.1f} s (first 300 frames replayed from fresh samples; windows of 10 incl. the "
+                      f"ground-truth env's step, cost, optimizer)",
+            "single_thread": {"value": single, "cores": 1,
+                              "sample": f"16 envs, {done_s[0]} frames in {el_s:.1f} s"}}
 
 
 # ----------------------------------------------------------------------------- our arm
-def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e=True, with_timing=True):
-    """Time `steps` tracking windows (graph replays) of a workload on this rank's GPU."""
+def measure(workload, n_envs, steps, warmup, shape, rank, world, local, n_timing=3, n_e2e=0, tune_frames=4,
+            adjoint_h=0):
+    """Time `steps` tracking windows (graph replays) of a workload on this rank's
+    GPU; then `n_timing` windows launched kernel by kernel (the step kernel's own
+    time and work), `n_e2e` windows end to end from pinned host buffers, and
+    (adjoint_h > 0) the forward + adjoint of an adjoint_h-frame horizon cost of
+    every environment from the state reached (checkpoints every 10 frames)."""
     import torch
     from paper_2002_12160_gb300 import tracking, workloads as W
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     T = 10
-    n_timing = 3 if with_timing else 0
-    n_e2e = 6 if with_e2e else 0   # three pipelined windows, three with the host waiting for each
-    n_windows = warmup + steps + n_timing + n_e2e
+    n_windows = warmup + steps + n_timing + n_e2e + (adjoint_h + T - 1) // T
     wl = W.make_workload(workload, n_envs=n_envs, frames=n_windows * T)
     seed = wl.seed + 7919 * rank   # independent replicas per rank
     tr = tracking.Tracker(wl, seed=seed)
@@ -269,13 +332,13 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e
         tr.window(w)
     torch.cuda.synchronize()
     if shape:
-        a, b = (int(v) for v in shape.lower().split("x"))
+        a, b = shape if isinstance(shape, tuple) else (int(v) for v in shape.lower().split("x"))
         tr.sim.sim_set_variant(a, b)
         chosen, tune_ms = (a, b), {}
     else:
         # pick the step kernel's shape on the frames after the warm-up windows, where
         # the contacts have settled (the autotuner restores the state after each trial)
-        chosen, tune_ms = tr.sim.sim_autotune(warmup * T, 4)
+        chosen, tune_ms = tr.sim.sim_autotune(warmup * T, tune_frames)
     torch.cuda.synchronize()
     tr.sim.sim_work_counters(reset=True)
     barrier(world)
@@ -295,7 +358,7 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e
     out = {"wl": wl, "n": tr.n, "T": T, "ms": ms, "work": work, "clocks": clk.summary(),
            "chosen": chosen, "tune_ms": tune_ms}
     w0 = warmup + steps
-    if with_timing:
+    if n_timing:
         # the dominant kernel alone: the same windows launched one kernel at a time,
         # every (fused) step bracketed by events on its stream, L2 flushed per window
         step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -309,8 +372,27 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, with_e2e
         lst = [a.elapsed_time(b) for (a, b) in step_ev]
         out["step_ms"] = sum(lst) / len(lst)
         out["step_launches"] = n_timing
-    if with_e2e:
+    if n_e2e:
         out["e2e"] = tr.e2e_windows(w0 + n_timing, n_e2e)
+    if adjoint_h:
+        f0 = (w0 + n_timing + n_e2e) * T
+        obs = tr.obs[f0:f0 + adjoint_h].contiguous()
+        tr.sim.sim_adjoint(f0, obs, checkpoint_every=min(10, adjoint_h))   # warm-up (sizes the scratch)
+        torch.cuda.synchronize()
+        lst = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            cost, grad, _ = tr.sim.sim_adjoint(f0, obs, checkpoint_every=min(10, adjoint_h))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lst.append(e0.elapsed_time(e1))
+        t = min(lst)
+        out["adjoint"] = {"horizon": adjoint_h, "checkpoint_every": min(10, adjoint_h), "ms_per_call": t,
+                          "env_steps_per_s": tr.n * adjoint_h / (t / 1e3),
+                          "finite_envs": int(torch.isfinite(cost).sum().item())}
+        del cost, grad
     out["add_mm"] = tr.add_mm()
     tr.close()
     del flush
@@ -565,7 +647,7 @@ def pd_flops(work, scene, spheres):
 
 
 def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, windows=5, budget_s=10.0,
-             speed_only=False):
+             speed_only=False, peak_tf=None):
     """The PD-driven hand (joints as state, full observation, full cost):
     - throughput on the cylinder trajectory at N = n_envs and 8 n_envs: per
       window one T-frame PD step launch, then the full cost of every frame
@@ -586,6 +668,8 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if peak_tf is None:
+        peak_tf = measure_fp32_peak(local)["tflops"]
 
     def throughput_at(n):
         wl = W.make_workload("tracking_cyl64", n_envs=n, frames=frames, seed=seeds[0])
@@ -627,7 +711,7 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
         n_launch = windows
         flop = pd_flops(work, wl.scene, max(len(x) for x in wl.scene.shapes)) / n_launch
         ms_win, ms_step = statistics.median(win_ms), statistics.median(step_ms)
-        peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+        peak = peak_tf
         achieved = flop / (ms_step / 1e3) / 1e12
         return T, {"n_envs": n, "env_steps_per_s": n * T / (ms_win / 1e3), "ms_per_window": ms_win,
                    "step_kernel_ms_per_launch": ms_step, "frames_per_launch": T,
@@ -635,7 +719,7 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
                    "unfused_ms_per_window": statistics.median(unfused),
                    "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                 "frac": achieved / peak, "flop_per_launch": flop,
-                                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                                "peak_note": "measured FP32 FMA throughput (ih_fp32_peak)"},
                    "work_per_launch": {k: v / n_launch for k, v in work.items()}}
 
     T, throughput = throughput_at(n_envs)
@@ -694,20 +778,97 @@ def flops_of(work, wl):
             work["env_iters"] * FLOP_PER_ENV_ITER)
 
 
-def run_ours(args, rank, world, local):
-    m = measure(args.workload, args.n_envs, args.steps, args.warmup, args.shape, rank, world, local)
+def measure_fp32_peak(local):
+    """FP32 FMA throughput of this GPU (ih_fp32_peak), with the SM clock sampled
+    while it runs: the denominator of the step kernels' ALU roofline."""
+    import torch
+    from paper_2002_12160_gb300 import inhand
+    torch.cuda.set_device(local)
+    inhand.fp32_peak(iters=256, reps=2)   # warm-up
+    with ClockSampler(local) as clk:
+        tf, ms, sms = inhand.fp32_peak(iters=2048, reps=60)
+    return {"tflops": tf, "ms_per_launch": ms, "sms": sms, "clocks": clk.summary(),
+            "what": "FMA-chain kernel (8 independent chains per thread, 2048 threads per SM), "
+                    "FMA = 2 flop, CUDA events over 60 launches"}
+
+
+def summarize(m, peak_tf, hbm_gbs, world=1):
+    """Throughput and roofline of one measured workload point: the window's
+    env-steps/s and tracking frames/s; the step kernel's counted flops and
+    algorithmic bytes per window-mode launch against its own CUDA-event time."""
     wl, n, T, ms = m["wl"], m["n"], m["T"], m["ms"]
-    value = world * n * T / (ms / 1e3)
-    per_launch_flops = flops_of(m["work_t"], wl) / m["step_launches"]
-    step_ms = m["step_ms"]
-    achieved = per_launch_flops / (step_ms / 1e3) / 1e12
+    out = {"n_envs": n, "ms_per_window": ms, "env_steps_per_s": world * n * T / (ms / 1e3),
+           "tracking_frames_per_s": T / (ms / 1e3),
+           "step_shape": {"threads_per_env": m["chosen"][0], "contacts_per_thread": m["chosen"][1]}}
+    if "step_ms" in m:
+        step_ms = m["step_ms"]
+        flop = flops_of(m["work_t"], wl) / m["step_launches"]
+        # one window-mode launch: state in/out once, the last frame's forces, the
+        # window sum, and every frame's window mean (8 B) and pose (32 B)
+        step_bytes = n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12 + n * 16 + T * n * 40
+        out.update({"step_kernel_ms": step_ms, "flop_per_launch": flop,
+                    "fp32": {"achieved_tflops": flop / (step_ms / 1e3) / 1e12,
+                             "frac": flop / (step_ms / 1e3) / 1e12 / peak_tf},
+                    "hbm": {"bytes_per_launch": step_bytes, "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
+                            "frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm_gbs},
+                    "work_per_env_frame": {k: v / (m["step_launches"] * T * n) for k, v in m["work_t"].items()}})
+    if "adjoint" in m:
+        out["forward_adjoint"] = m["adjoint"]
+    return out
+
+
+def largest_n_at_30hz(workload, local, shape, rate_hint, floor_n, step=8192, max_points=5):
+    """Bounded search for the largest N whose tracking window holds >= 30
+    tracking frames/s: start from the saturated throughput's prediction
+    (rate / 30), then bisect between the largest passing and the smallest
+    failing N on a grid of `step` environments, at most `max_points` points."""
+    import torch
+    pts = []
+
+    def fps(n):
+        r = measure(workload, n, 3, 2, shape, 0, 1, local, n_timing=0)
+        f = r["T"] / (r["ms"] / 1e3)
+        pts.append({"n_envs": n, "tracking_frames_per_s": f, "env_steps_per_s": n * f,
+                    "ms_per_window": r["ms"]})
+        torch.cuda.empty_cache()
+        return f
+
+    lo, hi = floor_n, None     # floor_n holds 30 Hz (measured in the sweep)
+    n = max(lo + step, step * int(rate_hint / 30.0 // step))
+    stride = max(step, step * int(0.04 * n // step))   # ~4 % moves until the boundary is bracketed
+    while len(pts) < max_points:
+        if fps(n) >= 30.0:
+            lo = max(lo, n)
+        else:
+            hi = n if hi is None else min(hi, n)
+        if hi is not None and hi - lo <= step:
+            break
+        if hi is None:
+            n = lo + stride
+        elif lo <= floor_n and n == hi:
+            n = max(floor_n + step, hi - stride)
+        else:
+            n = lo + step * max(1, (hi - lo) // (2 * step))
+    return {"largest_n_measured_at_30hz": lo, "smallest_n_measured_below_30hz": hi, "grid": step,
+            "points": pts, "step_shape": list(shape) if shape else None}
+
+
+def run_ours(args, rank, world, local):
+    hbm_gbs, hbm_note = hbm_peak()
+    peak = measure_fp32_peak(local)
+    peak_tf = peak["tflops"]
+    m = measure(args.workload, args.n_envs, args.steps, args.warmup, args.shape, rank, world, local,
+                n_timing=3, n_e2e=40)
+    main_pt = summarize(m, peak_tf, hbm_gbs, world)
+    wl, n, T, ms = m["wl"], m["n"], m["T"], m["ms"]
+    value = main_pt["env_steps_per_s"]
     clocks = m["clocks"]
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    # one window-mode launch: state in/out once, the last frame's forces, the
-    # window sum, and every frame's window mean (8 B) and pose (32 B)
-    step_bytes = n * STATE_BYTES_PER_ENV + n * wl.scene.n_pads * 12 + n * 16 + T * n * 40
     chosen, tune_ms = m["chosen"], m["tune_ms"]
+    e2e = m["e2e"]
+    e2e_line = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+    e2e_line["value"] *= world
+    e2e_line.update({"ms_per_step": e2e["ms_per_step"], "windows": e2e["windows"], "pipelined": True,
+                     "host_waits_each_window": e2e["host_waits_each_window"]})
     line = {"metric": "env-steps/s", "value": value, "unit": "env-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -718,38 +879,55 @@ def run_ours(args, rank, world, local):
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}",
                        "step_shape": {"threads_per_env": chosen[0], "contacts_per_thread": chosen[1],
                                       "autotune_ms": {f"{a}x{b}": round(v, 4) for (a, b), v in tune_ms.items()}}},
-            "tracking_frames_per_s": T / (ms / 1e3),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": step_traffic(), "traffic_unit": "bytes per launch",
+            "tracking_frames_per_s": main_pt["tracking_frames_per_s"],
+            "roofline": {"bound": "alu", "achieved": main_pt["fp32"]["achieved_tflops"], "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": main_pt["fp32"]["frac"], "traffic": step_traffic(),
+                         "traffic_unit": "bytes per launch",
                          "kernel": "step_kernel in window mode (one launch = the window's T scored frames)",
-                         "step_kernel_ms": step_ms, "flop_per_launch": per_launch_flops,
-                         "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"},
-            "hbm": {"step_bytes_per_launch": step_bytes, "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
-                    "peak_gbs": 6777.0, "frac": step_bytes / (step_ms / 1e3) / 1e9 / 6777.0},
-            "work_per_frame": {k: v / (args.steps * T) for k, v in m["work"].items()},
+                         "step_kernel_ms": main_pt["step_kernel_ms"], "flop_per_launch": main_pt["flop_per_launch"],
+                         "peak_note": f"measured FP32 FMA throughput of this GPU ({peak['sms']} SMs, "
+                                      f"SM clock median {peak['clocks'].get('sm_mhz')} MHz during the probe)"},
+            "hbm": {"step_bytes_per_launch": main_pt["hbm"]["bytes_per_launch"],
+                    "achieved_gbs": main_pt["hbm"]["achieved_gbs"], "peak_gbs": hbm_gbs,
+                    "frac": main_pt["hbm"]["frac"], "peak_note": hbm_note},
+            "fp32_peak": peak,
+            "work_per_env_frame": main_pt["work_per_env_frame"],
             "clocks": clocks,
             "gpu_launches": args.steps * 7,   # descriptor, T-frame step, per-frame argmin, 4 optimizer kernels
-            "e2e": m["e2e"],
+            "e2e": e2e_line,
             "add_mm_argmin_env": m["add_mm"]}
     if args.sweep:
         sweep = []
         for nn in [int(v) for v in args.sweep.split(",")]:
-            r = measure(args.workload, nn, 3, 2, args.shape, rank, world, local, with_e2e=False, with_timing=False)
+            r = measure(args.workload, nn, 3, 2, args.shape, rank, world, local, n_timing=0)
             fps = r["T"] / (r["ms"] / 1e3)
             sweep.append({"n_envs": nn, "ms_per_window": r["ms"], "tracking_frames_per_s": fps,
                           "env_steps_per_s": nn * fps, "step_shape": list(r["chosen"])})
         line["sweep"] = sweep
         ok = [x for x in sweep if x["tracking_frames_per_s"] >= 30.0]
         line["largest_n_measured_at_30hz"] = max((x["n_envs"] for x in ok), default=None)
-    if not args.no_adjoint and world == 1:   # the studies run on single-GPU runs only
-        adj = measure_adjoint(local)
+    if world == 1 and not args.main_only:
+        # config 2: the uneven batch in one launch per window, autotuned shape
+        line["uneven_mixed"] = summarize(measure("uneven_mixed", 8192, 5, 3, None, 0, 1, local, n_timing=2),
+                                         peak_tf, hbm_gbs)
+        # config 4: the mug sweep, forward-only and forward + adjoint (one 10-frame window's horizon)
+        sweep = []
+        for nn in (1024, 4096, 16384, 32768):
+            sweep.append(summarize(measure("sweep_mug128", nn, 5, 3, None, 0, 1, local, n_timing=2,
+                                           adjoint_h=10), peak_tf, hbm_gbs))
+        line["sweep_mug128"] = {"what": "mug of 128 spheres, 5 fingers, 16 pads, I = 40, 4 substeps; forward = the "
+                                        "tracking window; forward_adjoint = sim_adjoint of a 10-frame horizon on "
+                                        "every environment", "points": sweep}
+        sat = sweep[-1]
+        shp = (sat["step_shape"]["threads_per_env"], sat["step_shape"]["contacts_per_thread"])
+        ok = [p["n_envs"] for p in sweep if p["tracking_frames_per_s"] >= 30.0]
+        line["sweep_mug128"]["largest_n_at_30hz"] = largest_n_at_30hz(
+            "sweep_mug128", local, shp, sat["env_steps_per_s"], max(ok) if ok else 1024)
+        # config 3: forward + adjoint of a 30-frame horizon, N = 1024, box and cylinder
         line["adjoint"] = {"what": "forward + reverse-mode gradient of the horizon cost (sim_adjoint), "
                                    "every environment, H = 30 frames, checkpoints every 10",
-                           "forward_env_steps_per_s": value / world, **adj}
-        line["refinement"] = refine_study(local)
-        line["optimizers"] = optimizer_study(local)
-        line["warm_start"] = warm_study(local)
-        line["pd_hand"] = pd_study(local)
+                           "forward_env_steps_per_s": value / world, **measure_adjoint(local)}
+        line["pd_hand"] = pd_study(local, speed_only=True, peak_tf=peak_tf)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
@@ -759,22 +937,15 @@ def run_ours(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.part == "adjoint":
+    parts = {"adjoint": lambda: {"adjoint": measure_adjoint(local)},
+             "optimizers": lambda: {"optimizers": optimizer_study(local)},
+             "pd": lambda: {"pd_hand": pd_study(local)},
+             "pd_speed": lambda: {"pd_hand": pd_study(local, speed_only=True)},
+             "warm": lambda: {"warm_start": warm_study(local)},
+             "refine": lambda: {"refinement": refine_study(local)}}
+    if args.part in parts:
         if rank == 0:
-            print(json.dumps({"part": "adjoint", "adjoint": measure_adjoint(local)}), flush=True)
-        return
-    if args.part == "optimizers":
-        if rank == 0:
-            print(json.dumps({"part": "optimizers", "optimizers": optimizer_study(local)}), flush=True)
-        return
-    if args.part in ("pd", "pd_speed"):
-        if rank == 0:
-            print(json.dumps({"part": args.part, "pd_hand": pd_study(local, speed_only=args.part == "pd_speed")}),
-                  flush=True)
-        return
-    if args.part == "warm":
-        if rank == 0:
-            print(json.dumps({"part": "warm", "warm_start": warm_study(local)}), flush=True)
+            print(json.dumps({"part": args.part, **parts[args.part]()}), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

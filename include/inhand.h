@@ -408,6 +408,21 @@ ih_status sim_set_variant(ih_sim *sim, int32_t threads_per_env, int32_t contacts
  * many exist. */
 int32_t sim_step_variants(int32_t *out, int32_t cap);
 
+/* Measured FP32 throughput of the current device: the denominator of the
+ * step kernels' ALU roofline (their work is FP32 issue, not a dense
+ * contraction). Runs `reps` launches (after two warm-up launches) of a kernel
+ * in which every thread carries 8 independent FMA chains of 16 x iters FMAs,
+ * with 2048 threads on each SM (the SM count is read from the device), timed
+ * with CUDA events on `stream` (NULL = legacy default stream); an FMA counts
+ * as 2 flop. tflops (host double, required) receives the measured TFLOP/s,
+ * ms_per_launch and sm_count (host, may be NULL) the mean launch time and the
+ * SM count. Allocates and frees a small output buffer; synchronises the
+ * stream. Not a passage of the paper: a measurement of this GPU.
+ * Errors: IH_ERR_ARG (iters or reps < 1, null tflops), IH_ERR_OOM,
+ * IH_ERR_CUDA. */
+ih_status ih_fp32_peak(int32_t iters, int32_t reps, void *stream, double *tflops, double *ms_per_launch,
+                       int32_t *sm_count);
+
 /* cost_eval for callers that cannot allocate device memory.
  *
  * Some callers may not call cudaMalloc at all: code running inside another
@@ -531,13 +546,19 @@ ih_status sim_mark_window(ih_sim *sim);
  * Outputs (device, k entries each, any may be NULL): elite_out int32 (the
  * elites, index order), cost_before double (window cost of the unrefined
  * state, as the adjoint's forward computes it), cost_after double (the best
- * cost found; <= cost_before).
+ * cost found; <= cost_before), accepted_out uint64 (bit j set when evaluation
+ * j was kept: bit 0, the unrefined state, always; bit j >= 1, the j-th
+ * step), start_pose_out float[k][8] and start_params_out float[k][2] (the
+ * best window-start pose and parameters found, the unrefined ones when no
+ * step was kept).
  * Synchronises the stream once (adjoint scratch sizing).
- * Errors: IH_ERR_ARG (bad range or constant), IH_ERR_STATE (no mark, or not
- * exactly T frames scored since it), IH_ERR_OOM. */
+ * Errors: IH_ERR_ARG (bad range or constant; steps must be in [0, 63]),
+ * IH_ERR_STATE (no mark, or not exactly T frames scored since it),
+ * IH_ERR_OOM. */
 ih_status sim_refine_elites(ih_sim *sim, int32_t frame0, int32_t T, const float *obs,
                             const ih_opt_config *opt, int32_t steps, float step_scale, float beta,
-                            float width, int32_t *elite_out, double *cost_before, double *cost_after);
+                            float width, int32_t *elite_out, double *cost_before, double *cost_after,
+                            uint64_t *accepted_out, float *start_pose_out, float *start_params_out);
 
 /* Wait for the handle's stream; IH_ERR_CUDA if a kernel failed. */
 ih_status sim_sync(ih_sim *sim);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libinhand.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["step.cu", "step_warm.cu", "step_pd.cu", "adjoint.cu", "setup.cu", "cost.cu", "optim.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["step.cu", "step_warm.cu", "step_pd.cu", "adjoint.cu", "setup.cu", "cost.cu", "optim.cu", "api.cu", "noalloc.cu", "peak.cu"]
 
 
 def nvcc() -> str:

@@ -65,7 +65,8 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
            "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
            "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_get_warm_cache",
-           "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full", "sim_step_frames_full"]
+           "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full", "sim_step_frames_full",
+           "ih_fp32_peak"]
 
 
 def lib() -> C.CDLL:
@@ -107,7 +108,8 @@ def lib() -> C.CDLL:
             "sim_set_adjoint_memory": [P, C.c_uint64],
             "sim_step_frames": [P, I, I, P],
             "sim_frames_argmin": [P, P, P],
-            "sim_refine_elites": [P, I, I, P, P, I, C.c_float, C.c_float, C.c_float, P, P, P],
+            "sim_refine_elites": [P, I, I, P, P, I, C.c_float, C.c_float, C.c_float, P, P, P, P, P, P],
+            "ih_fp32_peak": [I, I, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -384,20 +386,39 @@ class Sim:
         self._call("sim_mark_window")
 
     def sim_refine_elites(self, frame0: int, obs, opt, steps: int = 3, step_scale: float = 0.5,
-                          beta: float = 1e3, width: float = 1e-3, report: bool = False):
+                          beta: float = 1e3, width: float = 1e-3, report: bool = False, detail: bool = False):
         """Refine the window's elites (see include/inhand.h). With report=True
-        returns (elites int32[k], cost_before float64[k], cost_after float64[k])."""
+        returns (elites int32[k], cost_before float64[k], cost_after float64[k]);
+        with detail=True also (accepted int64[k] decision bits, start_pose
+        float32[k][8], start_params float32[k][2])."""
         T = obs.shape[0]
         _check(obs, torch.float32, (T, self.n_pads, 3), "obs")
         out = (None, None, None)
-        if report:
+        more = (None, None, None)
+        if report or detail:
             k = max(1, min(self.n, int(np.floor(np.float64(np.float32(opt.elite_frac)) * self.n))))
             dev = torch.device("cuda", torch.cuda.current_device())
             out = (torch.empty(k, dtype=torch.int32, device=dev), torch.empty(k, dtype=torch.float64, device=dev),
                    torch.empty(k, dtype=torch.float64, device=dev))
+            if detail:
+                more = (torch.empty(k, dtype=torch.int64, device=dev),
+                        torch.empty((k, 8), dtype=torch.float32, device=dev),
+                        torch.empty((k, 2), dtype=torch.float32, device=dev))
         self._call("sim_refine_elites", frame0, T, _ptr(obs), C.byref(_opt(opt)), steps, C.c_float(step_scale),
-                   C.c_float(beta), C.c_float(width), *(_ptr(t) for t in out))
+                   C.c_float(beta), C.c_float(width), *(_ptr(t) for t in out), *(_ptr(t) for t in more))
+        if detail:
+            return out + more
         return out if report else None
+
+
+def fp32_peak(iters: int = 2048, reps: int = 40):
+    """Measured FP32 FMA throughput of the current device (ih_fp32_peak):
+    (TFLOP/s, ms per launch, SM count)."""
+    tf, ms, sms = C.c_double(), C.c_double(), C.c_int32()
+    code = lib().ih_fp32_peak(iters, reps, _stream(), C.byref(tf), C.byref(ms), C.byref(sms))
+    if code != IH_OK:
+        raise InhandError("ih_fp32_peak", code, "FP32 peak probe failed")
+    return tf.value, ms.value, sms.value
 
 
 def step_variants():
