@@ -90,6 +90,8 @@ def lib():
             L.orc_add.argtypes = [P, C.c_int, P, P]
             L.orc_add.restype = C.c_double
             L.orc_quat_exp.argtypes = [P, P]
+            L.orc_link_point_velocity.argtypes = [P, P, P, C.c_double, P]
+            L.orc_link_point_velocity.restype = None
             L.orc_quat_log.argtypes = [P, P]
             _lib = L
     return _lib
@@ -157,6 +159,17 @@ def contacts(osc: OracleScene, sim, shape: int, pose7, link_pose, max_out: int =
     out = np.zeros((max_out, 12))
     n = lib().orc_contacts(C.byref(osc.rec), C.byref(cfg), shape, _p(pose7), _p(lp), max_out, _p(out))
     return out[:min(n, max_out)]
+
+
+def link_point_velocity(pose_a7, pose_b7, p, h: float) -> np.ndarray:
+    """Velocity of the point p carried rigidly by a link from pose A to pose B
+    over a substep h (the contact's link velocity of the kinematic hand)."""
+    a = np.ascontiguousarray(pose_a7, np.float64)
+    b = np.ascontiguousarray(pose_b7, np.float64)
+    pp = np.ascontiguousarray(p, np.float64)
+    out = np.zeros(3)
+    lib().orc_link_point_velocity(_p(a), _p(b), _p(pp), h, _p(out))
+    return out
 
 
 def unit_inertia(osc: OracleScene, shape: int) -> np.ndarray:

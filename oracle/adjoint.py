@@ -341,3 +341,96 @@ def horizon(scene, sim, pose7, vel6, theta, q_traj, frame0, H, obs, shape=0, ite
         grad = np.zeros(8) if grad is None else grad.numpy()
     fin = np.concatenate([t.detach().numpy() for t in state])
     return float(total.detach()), grad, fin, np.array(forces_all), model.signature
+
+
+# ------------------------------------------------------------------ refinement of the elites
+def _qexp_np(w):
+    """Unit quaternion (w x y z) of a rotation vector, numpy FP64."""
+    th = float(np.linalg.norm(w))
+    if th == 0.0:
+        return np.array([1.0, 0.0, 0.0, 0.0])
+    return np.concatenate([[math.cos(0.5 * th)], math.sin(0.5 * th) * np.asarray(w) / th])
+
+
+def _qmul_np(a, b):
+    return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                     a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                     a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                     a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+
+
+def refine_step(pose7, theta, grad, eta, scale, m_range, mu_range):
+    """One step of the refinement from the state (pose7, theta) with gradient
+    `grad` (x y z, left rotation vector, m, mu): in coordinates scaled by eta
+    the step is the steepest descent of length `scale`,
+        s = eta * g,   dz = -scale * eta * s / |s|,
+    applied as x += dz[0:3], R <- exp([dz[3:6]]x) R (world frame, on the
+    left), m += dz[6], mu += dz[7], with m and mu clamped to the optimizer's
+    ranges. A zero or non-finite |s| leaves the state where it is."""
+    eta = np.asarray(eta, np.float64)
+    s = eta * np.asarray(grad, np.float64)
+    nrm = float(np.sqrt(np.sum(s * s)))
+    dz = np.zeros(8)
+    if nrm > 0.0 and math.isfinite(nrm):
+        dz = -scale * eta * s / nrm
+    p = np.asarray(pose7, np.float64).copy()
+    p[:3] += dz[:3]
+    q = _qmul_np(_qexp_np(dz[3:6]), p[3:7])
+    p[3:7] = q / np.linalg.norm(q)
+    th = np.asarray(theta, np.float64).copy()
+    th[0] = min(max(th[0] + dz[6], m_range[0]), m_range[1])
+    th[1] = min(max(th[1] + dz[7], mu_range[0]), mu_range[1])
+    return p, th
+
+
+def refine_rule(evaluate, pose7, theta, eta, steps, m_range, mu_range):
+    """The refinement's accept/halve rule on one elite (an addition to the
+    derivative-free update of Sec. III-D, run on the elites before it).
+
+    evaluate(pose7, theta) -> (cost, grad[8], end) scores a window-start
+    state over the window. Evaluation 0 is the elite's own state and is always
+    kept; evaluation j >= 1 is the step from the best state so far with the
+    current scale (starting at 1); it is kept when its cost is strictly lower
+    than the best cost, otherwise the scale halves. After `steps` steps the
+    best state, its cost, gradient and end state are returned together with the
+    per-evaluation decisions."""
+    scale = 1.0
+    trial_p, trial_t = np.asarray(pose7, np.float64).copy(), np.asarray(theta, np.float64).copy()
+    accepted, costs, scales, trials = [], [], [], []
+    best = None
+    for it in range(steps + 1):
+        c, g, end = evaluate(trial_p, trial_t)
+        costs.append(c)
+        trials.append((trial_p, trial_t))
+        keep = it == 0 or c < best["cost"]
+        accepted.append(bool(keep))
+        if keep:
+            best = {"cost": c, "grad": np.asarray(g, np.float64), "pose7": trial_p, "theta": trial_t, "end": end}
+        else:
+            scale *= 0.5
+        scales.append(scale)
+        if it == steps:
+            break
+        trial_p, trial_t = refine_step(best["pose7"], best["theta"], best["grad"], eta, scale, m_range, mu_range)
+    return {"c0": costs[0], "best_c": best["cost"], "accepted": accepted, "costs": costs, "scales": scales,
+            "trials": trials, "pose7": best["pose7"], "theta": best["theta"], "end": best["end"], "grad": best["grad"],
+            "improved": best["cost"] < costs[0]}
+
+
+def refine_elite(scene, sim, opt, pose7, vel6, theta, q_traj, frame0, T, obs, steps=3, step_scale=0.5,
+                 beta=1e3, width=1e-3, shape=0, iters=None):
+    """Gradient refinement of one elite's window-start state over the window of
+    T frames [frame0, frame0 + T): the window cost and its gradient come from
+    horizon() (the same backward-only smoothing), the velocity stays the
+    window-start velocity, eta = step_scale * floor_std per coordinate. When
+    the best cost is lower than the unrefined one, the elite's state at the
+    window's end becomes the simulation's state, with the best parameters and
+    the best cost as its window sum (returned as "end", "theta", "best_c")."""
+    eta = step_scale * np.asarray(opt.floor_std, np.float64)
+
+    def evaluate(p, th):
+        c, g, fin, _, _ = horizon(scene, sim, p, vel6, th, q_traj, frame0, T, obs, shape=shape, iters=iters,
+                                  beta=beta, width=width)
+        return c, g, fin
+
+    return refine_rule(evaluate, pose7, theta, eta, steps, opt.m_range, opt.mu_range)

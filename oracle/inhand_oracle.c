@@ -500,6 +500,21 @@ static double contact_bias(const orc_config *cfg, double d, double h) {
     return fmax(b, -cfg->vmax);
 }
 
+/*
+ * Velocity of a point p on a link over a substep of length h: the point is
+ * carried rigidly from the link's pose A (substep start, 7 doubles: position,
+ * quaternion w x y z) to its pose B (substep end), and the velocity is the
+ * displacement over h:  v = (p_B - p) / h,  p_B = B.p + B.R A.R^T (p - A.p).
+ */
+void orc_link_point_velocity(const double *A7, const double *B7, const double *p3, double h, double *out3) {
+    pose_t A = pose_from7(A7), B = pose_from7(B7);
+    vec3 p = v3(p3[0], p3[1], p3[2]);
+    vec3 pl = mtvmul(A.R, vsub(p, A.p));         /* in link coords */
+    vec3 p1 = vadd(B.p, mvmul(B.R, pl));         /* carried to the end */
+    vec3 v = vscale(vsub(p1, p), 1.0 / h);
+    out3[0] = v.x; out3[1] = v.y; out3[2] = v.z;
+}
+
 /* per-environment diagnostics written by orc_step (doubles per env) */
 #define ORC_DIAG 6  /* contacts (sum over substeps), pair tests, min|d-margin|,
                        min pad-boundary gap (m), min face gap (m), iterations */
@@ -584,10 +599,9 @@ static void step_env(const orc_scene *sc, const orc_config *cfg, const double *l
                     if (l == 0) {
                         k->vl = v3(0, 0, 0);
                     } else {
-                        pose_t A = pose_from7(lp0 + 7 * l), B = pose_from7(lp1 + 7 * l);
-                        vec3 pl = mtvmul(A.R, vsub(p, A.p));         /* in link coords */
-                        vec3 p1 = vadd(B.p, mvmul(B.R, pl));         /* carried to the end */
-                        k->vl = vscale(vsub(p1, p), 1.0 / h);
+                        double pp[3] = {p.x, p.y, p.z}, vv[3];
+                        orc_link_point_velocity(lp0 + 7 * l, lp1 + 7 * l, pp, h, vv);
+                        k->vl = v3(vv[0], vv[1], vv[2]);
                     }
                     k->id = (l << 8) | j;
                     k->lam = cache ? cache_lookup(cache, k->id) : v3(0, 0, 0);

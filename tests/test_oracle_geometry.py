@@ -236,3 +236,53 @@ def test_add_translation_and_rotation_closed_forms():
     c[3:] = Rotation.from_rotvec([0, 0, th]).as_quat(scalar_first=True)
     rho = np.hypot(rows[:, 0], rows[:, 1])
     assert abs(O.add(osc, 0, a, c) - np.mean(2 * math.sin(th / 2) * rho)) < 1e-15
+
+
+@pytest.mark.parametrize("joint", [0, 1, 2, 3])
+def test_link_point_velocity_is_the_rigid_rotation_of_the_joint(joint):
+    """A contact's link velocity (the kinematic hand) is the displacement over
+    the substep of the link point carried rigidly from the link's start pose to
+    its end pose. When only joint `joint` of finger 1 turns, by d = w h, every
+    link at or after it turns rigidly by d about that joint's axis: the vertical
+    axis through the finger root for the abduction joint 0, the link frame's y
+    axis through the link origin (turning by -d) for a flexion joint. So
+      v = (Rot(a, +-d) (p - o) + o - p) / h   exactly,
+    which tends to w (a x (p - o)) with an error of (h/2) w^2 |a x (a x r)| +
+    O(h^2): halving h halves it."""
+    sc = _hand_scene()
+    osc = O.OracleScene(sc)
+    rng = np.random.default_rng(11 + joint)
+    f = 1
+    q = rng.uniform(-0.3, 0.8, sc.n_joints)
+    w = 2.7   # rad/s
+    k = 4 * f + joint
+    lp_a = O.fk(osc, q)
+    if joint == 0:
+        a, o, sgn = np.array([0.0, 0.0, 1.0]), sc.finger_root[f, :3], 1.0
+    else:
+        la = lp_a[1 + k]
+        a = Rotation.from_quat(la[3:], scalar_first=True).apply([0, 1, 0])
+        o, sgn = la[:3], -1.0
+    errs = []
+    for h in (1e-2, 5e-3, 2.5e-3):
+        dq = np.zeros(sc.n_joints)
+        dq[k] = w * h
+        lp_b = O.fk(osc, q + dq)
+        for j in range(joint, 4):
+            l = 1 + 4 * f + j
+            p = lp_a[l, :3] + rng.normal(scale=0.01, size=3)
+            v = O.link_point_velocity(lp_a[l], lp_b[l], p, h)
+            rot = Rotation.from_rotvec(sgn * w * h * a)
+            v_ref = (rot.apply(p - o) + o - p) / h
+            np.testing.assert_allclose(v, v_ref, rtol=0, atol=1e-12)
+            if j == 3:
+                r = p - o
+                lim = sgn * w * np.cross(a, r)
+                errs.append((np.linalg.norm(v - lim), 0.5 * h * w * w * np.linalg.norm(np.cross(a, np.cross(a, r)))))
+        # links before the joint do not move
+        for j in range(joint):
+            l = 1 + 4 * f + j
+            p = lp_a[l, :3]
+            np.testing.assert_allclose(O.link_point_velocity(lp_a[l], lp_b[l], p, h), 0.0, atol=1e-12)
+    for e, e_pred in errs:
+        assert abs(e - e_pred) <= 0.05 * e_pred, (e, e_pred)
