@@ -40,21 +40,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # Algorithmic FP32 operations of the step, counted from the kernel's source
-# per unit of work (an FMA counts as 2, a compare/min/max/select as 1, sqrt /
-# rsqrt / division / sin / cos as 1 each). The counts are attached to the
-# work counters the step kernel reports (pairs tested after culling, contacts,
-# contact-iterations, env-substeps).
-FLOP_PER_ENV_SUBSTEP = 150     # gravity, rotation matrix, world inverse inertia,
-                               # link cull, integration
-FLOP_PER_SPHERE = 15           # sphere centre to world, once per substep (counted
-                               # through the pair tests' spheres below)
-FLOP_PER_PAIR = 30             # sphere-capsule / sphere-box gap, normal, contact test
-FLOP_PER_CLUSTER_TEST = 25     # cluster centre to world (15) and its reach test (10)
-FLOP_PER_CONTACT = 95          # effective masses, bias, link velocity, pad sum
-FLOP_PER_CONTACT_ITER = 62     # relative velocity, normal/tangent update,
-                               # cone clamp, relaxation, impulse/moment sums
-FLOP_PER_ENV_ITER = 60         # 6-float group reduction (log2 G levels) and
-                               # the body velocity update
+# (an FMA counts as 2; an add, multiply, compare, min/max, select, sqrt,
+# rsqrt, division, sin or cos as 1), attached to the work counters the step
+# kernel reports (pairs tested after culling, contacts, contact-iterations,
+# env-substeps, env-iterations with contacts, (link, cluster) tests):
+#   env-substep   gravity 3, rotation matrix 39, world inverse inertia 81,
+#                 integration with the rotation exponential 61; link cull 25
+#                 per link, cluster centre to world 15 per cluster, sphere
+#                 centre to world 15 per sphere
+#   pair tested   sphere to link frame, closest point, gap and normal 34,
+#                 lever arm 6, contact test 1
+#   cluster test  offset 3, reach of the link's bounding capsule 25
+#   contact       r x n 9, k_n 21, tr K 29, inverses 3, bias 4, target
+#                 velocity 6, lever arm and pad membership 10, pad sum 9
+#                 (a finger contact's link point velocity, 108 more, is not
+#                 counted: the counters do not tell palm and finger apart)
+#   contact-iter  relative velocity 15, normal and tangential components and
+#                 steps 31, disk clamp 13, relaxation 15 (update_contact, 74);
+#                 its moment 9 and the impulse and moment sums 6
+#   env-iter      body velocity from the summed impulses and moments 24
+FLOP_PER_ENV_SUBSTEP = 184     # + 25 per link + 15 per cluster (flops_of)
+FLOP_PER_LINK = 25
+FLOP_PER_CLUSTER = 15
+FLOP_PER_SPHERE = 15
+FLOP_PER_PAIR = 41
+FLOP_PER_CLUSTER_TEST = 28
+FLOP_PER_CONTACT = 91
+FLOP_PER_CONTACT_ITER = 89
+FLOP_PER_ENV_ITER = 24
 # DRAM traffic of one step_kernel launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu capture summarised in
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
@@ -772,10 +785,12 @@ def pd_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_envs=1024, win
 
 
 def flops_of(work, wl):
-    return (work["env_substeps"] * (FLOP_PER_ENV_SUBSTEP + FLOP_PER_SPHERE * max(len(s) for s in wl.scene.shapes)) +
-            work["pairs"] * FLOP_PER_PAIR + work["cluster_tests"] * FLOP_PER_CLUSTER_TEST +
-            work["contacts"] * FLOP_PER_CONTACT + work["contact_iters"] * FLOP_PER_CONTACT_ITER +
-            work["env_iters"] * FLOP_PER_ENV_ITER)
+    S = max(len(x) for x in wl.scene.shapes)
+    per_substep = (FLOP_PER_ENV_SUBSTEP + FLOP_PER_LINK * wl.scene.n_links + FLOP_PER_CLUSTER * ((S + 7) // 8) +
+                   FLOP_PER_SPHERE * S)
+    return (work["env_substeps"] * per_substep + work["pairs"] * FLOP_PER_PAIR +
+            work["cluster_tests"] * FLOP_PER_CLUSTER_TEST + work["contacts"] * FLOP_PER_CONTACT +
+            work["contact_iters"] * FLOP_PER_CONTACT_ITER + work["env_iters"] * FLOP_PER_ENV_ITER)
 
 
 def measure_fp32_peak(local):
@@ -799,7 +814,8 @@ def summarize(m, peak_tf, hbm_gbs, world=1):
     wl, n, T, ms = m["wl"], m["n"], m["T"], m["ms"]
     out = {"n_envs": n, "ms_per_window": ms, "env_steps_per_s": world * n * T / (ms / 1e3),
            "tracking_frames_per_s": T / (ms / 1e3),
-           "step_shape": {"threads_per_env": m["chosen"][0], "contacts_per_thread": m["chosen"][1]}}
+           "step_shape": {"threads_per_env": m["chosen"][0], "contacts_per_thread": m["chosen"][1],
+                          "autotune_ms": {f"{a}x{b}": round(v, 4) for (a, b), v in m["tune_ms"].items()}}}
     if "step_ms" in m:
         step_ms = m["step_ms"]
         flop = flops_of(m["work_t"], wl) / m["step_launches"]

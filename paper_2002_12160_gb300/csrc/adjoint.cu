@@ -845,6 +845,7 @@ __global__ void refine_kernel(const RefineArgs r) {
     const int env = r.elite[i];
     const double c = r.cost[i];
     if (r.step == 0 || c < r.best_c[i]) {
+        r.accepted[i] = (r.step == 0 ? 0ull : r.accepted[i]) | (1ull << r.step);
         r.best_pose[2 * i] = r.tr_pose[2 * env];
         r.best_pose[2 * i + 1] = r.tr_pose[2 * env + 1];
         for (int q = 0; q < 2; ++q) {

@@ -26,6 +26,11 @@ struct ih_sim {
     StepVariant variant{32, 4, 128};
     int step_grid = 0;
     int s_max = 1;   // most spheres in one shape
+    int sms = 1;     // SMs of the device
+    int stage_cap = 0, clp_cap = 0;   // the step shape's shared-memory staging; (link, cluster) pair capacity
+    float4 *spill = nullptr;          // contacts beyond the staging capacity, per resident group
+    size_t spill_f4 = 0;              // its size in float4
+    int *queue = nullptr;             // the step's work queue (head, finished blocks)
     // device buffers
     float4 *spheres_raw = nullptr, *spheres = nullptr, *finger_root = nullptr;
     int *shape_first = nullptr, *shape_count = nullptr, *pad_link = nullptr;
@@ -63,6 +68,7 @@ struct ih_sim {
     float2 *ws_params = nullptr, *tr_params = nullptr, *best_params = nullptr;
     float *best_grad = nullptr, *scale = nullptr, *r_grad = nullptr;
     double *best_c = nullptr, *c0 = nullptr, *r_cost = nullptr;
+    unsigned long long *r_acc = nullptr;
     // WRS / REPS: the state before an update
     float4 *sn_pose = nullptr, *sn_vel = nullptr;
     float2 *sn_params = nullptr;
@@ -173,6 +179,37 @@ int grid_for(const StepVariant &v, int N) {
     return need > 0 ? need : 1;
 }
 
+// Make v the step shape: shared-memory opt-in, a persistent grid of at most the
+// blocks that fit on the device at once (the groups take environments from the
+// launch's work queue), and a spill area for the contacts beyond the shape's
+// shared-memory staging, grown when needed (cudaFree synchronises the device,
+// so no launch still uses the old one).
+cudaError_t use_variant(ih_sim *s, const StepVariant &v) {
+    int bps = 0;
+    cudaError_t e = step_prepare(v, s->s_max, s->cfg.c_max, s->dcfg.warm != 0, s->clp_cap, &bps);
+    if (e != cudaSuccess) return e;
+    const int resident = std::max(1, bps) * std::max(1, s->sms);
+    const int grid = std::min(grid_for(v, s->cfg.n_envs), resident);
+    const int sc = step_stage_capacity(v, s->cfg.c_max);
+    const size_t need = (size_t)grid * (v.block / v.group) * (size_t)(s->cfg.c_max - sc) * 4;
+    if (need > s->spill_f4) {
+        // a captured window graph holds the old spill pointer: let it finish, capture again
+        if (s->cap_stream) cudaStreamSynchronize(s->cap_stream);
+        cudaStreamSynchronize(s->stream);
+        if (s->win_exec) { cudaGraphExecDestroy(s->win_exec); s->win_exec = nullptr; }
+        if (s->spill) cudaFree(s->spill);
+        s->spill = nullptr;
+        s->spill_f4 = 0;
+        e = cudaMalloc(&s->spill, need * sizeof(float4));
+        if (e != cudaSuccess) { s->spill = nullptr; return e; }
+        s->spill_f4 = need;
+    }
+    s->variant = v;
+    s->step_grid = grid;
+    s->stage_cap = sc;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -276,6 +313,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(dalloc(s, &s->part_c, std::max(N, cost_blocks(N)))); A(dalloc(s, &s->part_i, std::max(N, cost_blocks(N))));
     A(dalloc(s, &s->win, 1));
     A(dalloc(s, &s->done, 1)); A(dalloc(s, &s->work, 6)); A(dalloc(s, &s->adj_word, 1));
+    A(dalloc(s, &s->queue, 2));
     A(dalloc(s, &s->is_elite, N)); A(dalloc(s, &s->rank, N)); A(dalloc(s, &s->elite_env, N));
     A(dalloc(s, &s->elite_w, N)); A(dalloc(s, &s->block_w, opt_blocks(N)));
     A(dalloc(s, &s->moments, (size_t)opt_blocks(N) * kMoments)); A(dalloc(s, &s->misc, 80));
@@ -320,6 +358,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemsetAsync(s->n_window, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->argmin, 0, sizeof(int), st));
     A(cudaMemsetAsync(s->done, 0, sizeof(unsigned int), st));
+    A(cudaMemsetAsync(s->queue, 0, 2 * sizeof(int), st));
     A(cudaMemsetAsync(s->work, 0, 6 * sizeof(unsigned long long), st));
     if (d.warm) A(cudaMemsetAsync(s->cache_n, 0, (size_t)N * sizeof(int), st));
     if (s->pd) {
@@ -337,14 +376,17 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
         return r;
     }
     s->frame_ready.assign(cfg->max_frames, 0);
-    s->step_grid = grid_for(s->variant, N);
-    e = step_prepare(s->variant, s->s_max, s->cfg.c_max, s->dcfg.warm != 0);
-    if (e == cudaSuccess && s->pd) {
+    {
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = pd_step_prepare(s->s_max, s->cfg.c_max);
-        s->pd_grid = pd_step_grid(N, sms > 0 ? sms : 1);
+        s->sms = sms > 0 ? sms : 1;
+    }
+    s->clp_cap = (1 + 4 * sc->n_fingers) * ((s->s_max + 7) / 8);
+    if (e == cudaSuccess) e = use_variant(s, s->variant);
+    if (e == cudaSuccess && s->pd) {
+        e = pd_step_prepare(s->s_max, s->cfg.c_max);
+        s->pd_grid = pd_step_grid(N, s->sms);
     }
     if (e != cudaSuccess) {
         ih_status r = cuda_fail(nullptr, e, "sim_create step setup");
@@ -364,6 +406,7 @@ ih_status sim_destroy(ih_sim *s) {
     if (s->ev_out) cudaEventDestroy(s->ev_out);
     for (void *p : s->owned) cudaFree(p);
     if (s->adj_scratch) cudaFree(s->adj_scratch);
+    if (s->spill) cudaFree(s->spill);
     if (s->wf_cm) cudaFree(s->wf_cm);
     if (s->wf_pose) cudaFree(s->wf_pose);
     for (void *q : {(void *)s->fo_q, (void *)s->fo_forces, (void *)s->fo_pp, (void *)s->fo_slip, (void *)s->fo_status,
@@ -491,6 +534,9 @@ ih_status sim_step(ih_sim *s, int32_t frame0, int32_t n_frames) {
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
     a.cm_frames = nullptr; a.pose_frames = nullptr;
     a.cache = s->cache; a.cache_n = s->cache_n;
+    a.stage_cap = s->stage_cap; a.spill = s->spill; a.clp_cap = s->clp_cap;
+    // the work queue only when the grid's groups are fewer than the environments
+    a.queue = (size_t)s->step_grid * (s->variant.block / s->variant.group) < (size_t)s->cfg.n_envs ? s->queue : nullptr;
     cudaError_t e = launch_step(a, s->variant, s->step_grid, s->s_max, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->stepped = true;
@@ -510,6 +556,9 @@ StepArgs scored_args(ih_sim *s, int frame, const float *obs, double *cost_mean, 
     a.part_c = s->part_c; a.part_i = s->part_i; a.done = s->done;
     a.cm_frames = nullptr; a.pose_frames = nullptr;
     a.cache = s->cache; a.cache_n = s->cache_n;
+    a.stage_cap = s->stage_cap; a.spill = s->spill; a.clp_cap = s->clp_cap;
+    // the work queue only when the grid's groups are fewer than the environments
+    a.queue = (size_t)s->step_grid * (s->variant.block / s->variant.group) < (size_t)s->cfg.n_envs ? s->queue : nullptr;
     return a;
 }
 
@@ -902,10 +951,8 @@ ih_status sim_set_variant(ih_sim *s, int32_t tpe, int32_t cpl) {
     if (!step_variant_supported(v)) return fail(s, IH_ERR_ARG, "unsupported step shape %d x %d", tpe, cpl);
     if (step_variant_max_contacts(v) < s->cfg.c_max)
         return fail(s, IH_ERR_ARG, "shape %d x %d holds fewer than c_max = %d contacts", tpe, cpl, s->cfg.c_max);
-    cudaError_t e = step_prepare(v, s->s_max, s->cfg.c_max, s->dcfg.warm != 0);
+    cudaError_t e = use_variant(s, v);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_variant");
-    s->variant = v;
-    s->step_grid = grid_for(v, s->cfg.n_envs);
     return IH_OK;
 }
 
@@ -968,9 +1015,7 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     if (e == cudaSuccess) { save(); e = cudaStreamSynchronize(st); }
     for (int k = 0; k < nv && e == cudaSuccess; ++k) {
         float ms = NAN;
-        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && step_prepare(cand[k], s->s_max, s->cfg.c_max, s->dcfg.warm != 0) == cudaSuccess) {
-            s->variant = cand[k];
-            s->step_grid = grid_for(cand[k], (int)N);
+        if (step_variant_max_contacts(cand[k]) >= s->cfg.c_max && use_variant(s, cand[k]) == cudaSuccess) {
             ih_status r = sim_step(s, frame0, n_frames);   // warm-up (and first-use setup)
             restore();
             for (int rep = 0; rep < 3 && r == IH_OK && e == cudaSuccess; ++rep) {
@@ -994,12 +1039,11 @@ ih_status sim_autotune(ih_sim *s, int32_t frame0, int32_t n_frames, int32_t *cho
     if (bc) cudaFree(bc);
     if (bn) cudaFree(bn);
     if (e != cudaSuccess) {
-        s->variant = keep;
-        s->step_grid = grid_for(keep, (int)N);
+        use_variant(s, keep);
         return cuda_fail(s, e, "autotune");
     }
-    s->variant = best;
-    s->step_grid = grid_for(best, (int)N);
+    e = use_variant(s, best);
+    if (e != cudaSuccess) return cuda_fail(s, e, "autotune");
     if (chosen) { chosen[0] = best.group; chosen[1] = best.cpl; }
     return IH_OK;
 }
@@ -1095,6 +1139,7 @@ cudaError_t refine_alloc(ih_sim *s) {
     A(dalloc(s, &s->best_pose, 2 * N)); A(dalloc(s, &s->best_params, N)); A(dalloc(s, &s->best_grad, 8 * N));
     A(dalloc(s, &s->scale, N)); A(dalloc(s, &s->r_grad, 8 * N));
     A(dalloc(s, &s->best_c, N)); A(dalloc(s, &s->c0, N)); A(dalloc(s, &s->r_cost, N));
+    A(dalloc(s, &s->r_acc, N));
     if (e == cudaSuccess) s->rf_alloc = true;
     return e;
 }
@@ -1122,7 +1167,8 @@ ih_status sim_mark_window(ih_sim *s) {
 
 ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *obs, const ih_opt_config *opt,
                             int32_t steps, float step_scale, float beta, float width, int32_t *elite_out,
-                            double *cost_before, double *cost_after) {
+                            double *cost_before, double *cost_after, uint64_t *accepted_out, float *start_pose_out,
+                            float *start_params_out) {
     if (!s) return IH_ERR_ARG;
     if (s->pd) return refuse_pd(s, "sim_refine_elites");
     if (s->dcfg.warm) return fail(s, IH_ERR_ARG, "the adjoint differentiates the cold-started solver only");
@@ -1131,8 +1177,8 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
     if (r != IH_OK) return r;
     r = check_horizon(s, frame0, T);
     if (r != IH_OK) return r;
-    if (steps < 0 || steps > 64 || !(step_scale > 0.0f) || !std::isfinite(step_scale))
-        return fail(s, IH_ERR_ARG, "steps must be in [0, 64] and step_scale positive");
+    if (steps < 0 || steps > 63 || !(step_scale > 0.0f) || !std::isfinite(step_scale))
+        return fail(s, IH_ERR_ARG, "steps must be in [0, 63] and step_scale positive");
     if (!(beta > 0.0f) || !std::isfinite(beta) || !(width > 0.0f) || !std::isfinite(width))
         return fail(s, IH_ERR_ARG, "beta and width must be positive");
     if (!s->ws_valid) return fail(s, IH_ERR_STATE, "no window start marked (sim_mark_window)");
@@ -1162,7 +1208,7 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
     ra.best_pose = s->best_pose; ra.best_params = s->best_params; ra.best_grad = s->best_grad;
     ra.best_c = s->best_c; ra.c0 = s->c0; ra.scale = s->scale; ra.cost = s->r_cost; ra.grad = s->r_grad;
     ra.end_pose = s->end_pose; ra.end_vel = s->end_vel;
-    ra.best_end_pose = s->best_end_pose; ra.best_end_vel = s->best_end_vel;
+    ra.best_end_pose = s->best_end_pose; ra.best_end_vel = s->best_end_vel; ra.accepted = s->r_acc;
     for (int d = 0; d < 8; ++d) ra.eta[d] = step_scale * opt->floor_std[d];
     ra.m_lo = opt->m_lo; ra.m_hi = opt->m_hi; ra.mu_lo = opt->mu_lo; ra.mu_hi = opt->mu_hi;
     for (int it = 0; it <= steps && e == cudaSuccess; ++it) {
@@ -1182,6 +1228,12 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
         e = cudaMemcpyAsync(cost_before, s->c0, k * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && cost_after)
         e = cudaMemcpyAsync(cost_after, s->best_c, k * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && accepted_out)
+        e = cudaMemcpyAsync(accepted_out, s->r_acc, k * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && start_pose_out)
+        e = cudaMemcpyAsync(start_pose_out, s->best_pose, 2 * (size_t)k * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && start_params_out)
+        e = cudaMemcpyAsync(start_params_out, s->best_params, (size_t)k * sizeof(float2), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "refine");
     return IH_OK;
 }

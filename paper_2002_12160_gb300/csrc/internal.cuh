@@ -231,6 +231,13 @@ struct StepArgs {
     // warm start (cfg.warm): per environment the last substep's contacts
     float4 *cache;            // [N][c_max]: final impulse xyz, pair id (link << 8 | sphere) in w
     int *cache_n;             // [N]
+    // contact staging: the first stage_cap contacts of an environment's substep
+    // in shared memory, the rest (up to c_max) in a global spill area of
+    // (c_max - stage_cap) x 4 float4 per resident group
+    int stage_cap;
+    float4 *spill;            // [grid * groups per block][c_max - stage_cap][4] or null
+    int clp_cap;              // (link, cluster) pairs a group can hold
+    int *queue;               // [2] work queue head, finished blocks (zero between launches) or null
 };
 // The step with the PD-driven hand (step_pd.cu): the joints are state.
 struct PdArgs {
@@ -295,7 +302,9 @@ struct StepVariant {
 cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s);
 int step_variant_max_contacts(const StepVariant &v);
 bool step_variant_supported(const StepVariant &v);
-size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max, bool warm);
+size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max, bool warm, int clp_cap);
+// contacts a shape stages in shared memory (the rest of c_max spill to global memory)
+int step_stage_capacity(const StepVariant &v, int c_max);
 int step_variant_list(StepVariant *out, int cap);
 
 struct CostArgs {
@@ -420,6 +429,7 @@ struct RefineArgs {
     const float *grad;            // [k][8] gradient at the trial
     const float4 *end_pose, *end_vel;    // [k][2] end state of the trial's window
     float4 *best_end_pose, *best_end_vel;  // [k][2] end state of the best trial
+    unsigned long long *accepted; // [k] bit j set when evaluation j was kept
     float eta[8];                 // step length per coordinate
     float m_lo, m_hi, mu_lo, mu_hi;
     int step;                     // 0: the first evaluation (of the unrefined state)
@@ -435,10 +445,11 @@ size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max,
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
-cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max, bool warm);
+// shared-memory opt-in of a shape; blocks_per_sm (may be null) receives its occupancy
+cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max, bool warm, int clp_cap, int *blocks_per_sm);
 // the warm-started instances (step_warm.cu)
-size_t step_smem_bytes_warm(const StepVariant &v, int s_max, int c_max);
-cudaError_t step_prepare_warm(const StepVariant &v, int s_max, int c_max);
+size_t step_smem_bytes_warm(const StepVariant &v, int s_max, int c_max, int clp_cap);
+cudaError_t step_prepare_warm(const StepVariant &v, int s_max, int c_max, int clp_cap, int *blocks_per_sm);
 cudaError_t launch_step_warm(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s);
 cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s);
 // the optimizer's first stage alone: elite flags, ranks and elite_env (index order), i*

@@ -5,7 +5,8 @@
 #include "step_kernel.cuh"
 
 namespace ih {
-// every shape holds any c_max <= IH_MAX_CONTACTS (contacts beyond its registers live in shared memory)
+// every shape holds any c_max <= IH_MAX_CONTACTS (contacts beyond its registers
+// live in shared memory, and beyond the shape's staging capacity in the spill area)
 int step_variant_max_contacts(const StepVariant &v) { return v.group > 0 ? IH_MAX_CONTACTS : 0; }
 
 bool step_variant_supported(const StepVariant &v) {
@@ -24,12 +25,17 @@ int step_variant_list(StepVariant *out, int cap) {
     return n;
 }
 
-size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max, bool warm) {
-    return warm ? step_smem_bytes_warm(v, s_max, c_max) : smem_bytes_w<false>(v, s_max, c_max);
+size_t step_smem_bytes(const StepVariant &v, int s_max, int c_max, bool warm, int clp_cap) {
+    return warm ? step_smem_bytes_warm(v, s_max, c_max, clp_cap) : smem_bytes_w<false>(v, s_max, c_max, clp_cap);
 }
 
-cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max, bool warm) {
-    return warm ? step_prepare_warm(v, s_max, c_max) : prepare_w<false>(v, s_max, c_max);
+cudaError_t step_prepare(const StepVariant &v, int s_max, int c_max, bool warm, int clp_cap, int *blocks_per_sm) {
+    return warm ? step_prepare_warm(v, s_max, c_max, clp_cap, blocks_per_sm)
+                : prepare_w<false>(v, s_max, c_max, clp_cap, blocks_per_sm);
+}
+
+int step_stage_capacity(const StepVariant &v, int c_max) {
+    return stage_capacity(v.group * v.cpl, c_max, v.block / v.group);
 }
 
 cudaError_t launch_step(const StepArgs &a, const StepVariant &v, int grid, int s_max, cudaStream_t s) {

@@ -77,9 +77,9 @@ struct Group {
     __device__ __forceinline__ int lane_in_warp() const { return TPE < 32 ? tid : lane; }
 };
 
-// Shared memory of one group. Everything has a fixed size except the cache
-// of world-frame sphere and cluster centres, which follows the group records.
-constexpr int kMaxClp = 32 * 32;   // (surviving link, cluster) pairs: 29 links x 32 clusters
+// Shared memory of one group. Everything has a fixed size except the contact
+// staging, the cache of world-frame sphere and cluster centres and the list of
+// surviving (link, cluster) pairs, which follow the group records.
 
 template <int W>
 struct alignas(16) GSm {   // 16-byte aligned: red is read as float4
@@ -90,13 +90,13 @@ struct alignas(16) GSm {   // 16-byte aligned: red is read as float4
     int flag[IH_MAX_PADS];           // contact-state mismatch of each pad (scoring)
     double best_c;                   // best (C, env) of this group so far
     int best_i;
+    int next;                        // work-queue slot handed to the group (groups wider than a warp)
     unsigned long long work[6];      // this group's work counters (see sim_work_counters)
     unsigned surv;                   // surviving-link mask
     int n_clp;
     int n_prev;                      // warm start: contacts of the last substep (cache entries)
     unsigned char links[32];         // surviving links in order
     unsigned short lbeg[32], lend[32];   // contact range of each link
-    unsigned short clp[kMaxClp];     // surviving (link index << 8 | cluster) pairs in order
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -108,11 +108,20 @@ __host__ __device__ constexpr size_t gsm_bytes() { return align16(sizeof(GSm<W>)
 static_assert(sizeof(GSm<1>) % 16 == 0 && sizeof(GSm<2>) % 16 == 0 && sizeof(GSm<4>) % 16 == 0,
               "group records must keep 16-byte alignment");
 static_assert(offsetof(GSm<2>, red) % 16 == 0, "red is read as float4");
-// dynamic part of a group: the contact staging (4 float4 per contact, c_max
-// contacts) then the cache of sphere and cluster centres
-// (and, for a warm-started solver, the cache of the last substep's contacts)
-__host__ __device__ inline size_t group_dyn_floats4(int s_max, int c_max, bool warm) {
-    return 4 * (size_t)c_max + s_max + 32 + (warm ? (size_t)c_max : 0);
+// dynamic part of a group: the contact staging (4 float4 per contact, the
+// first stage_cap contacts; the rest of up to c_max spill to global memory),
+// the cache of sphere and cluster centres, for a warm-started solver the cache
+// of the last substep's contacts, and the surviving (link, cluster) pairs
+__host__ __device__ inline size_t group_dyn_floats4(int s_max, int stage_cap, int c_max, bool warm, int clp_cap) {
+    return 4 * (size_t)stage_cap + s_max + 32 + (warm ? (size_t)c_max : 0) + ((size_t)clp_cap * 2 + 15) / 16;
+}
+// contacts a group stages in shared memory: at least its register-resident
+// ones, and 64 (32 for the narrow shapes, eight or more groups to a block,
+// whose staging would otherwise cap the blocks an SM holds), at most c_max
+__host__ __device__ constexpr int stage_capacity(int rcap, int c_max, int groups_per_block) {
+    return c_max < (rcap > (groups_per_block >= 8 ? 32 : 64) ? rcap : (groups_per_block >= 8 ? 32 : 64))
+               ? c_max
+               : (rcap > (groups_per_block >= 8 ? 32 : 64) ? rcap : (groups_per_block >= 8 ? 32 : 64));
 }
 
 template <int TPE>
@@ -145,9 +154,12 @@ __device__ __forceinline__ void group_sum6(float (&v)[6], const Group<TPE> &G, f
 // one or two register-resident contacts per thread at 4 blocks (128
 // registers: with one contact a cap of 5 blocks spilled and ran 6 % slower on
 // large batches), four at 3.
+#ifndef IH_STEP_MIN_BLOCKS_CPL2
+#define IH_STEP_MIN_BLOCKS_CPL2 4
+#endif
 template <int TPE, int CPL>
 struct MinBlocks {
-    static constexpr int value = CPL <= 2 ? 4 : (CPL <= 4 ? 3 : 2);
+    static constexpr int value = CPL <= 2 ? IH_STEP_MIN_BLOCKS_CPL2 : (CPL <= 4 ? 3 : 2);
 };
 
 template <int TPE, int CPL, bool WARM>
@@ -180,15 +192,21 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
     float *p_s1 = p_s0 + IH_MAX_PADS;
     GSm<W> &S = *reinterpret_cast<GSm<W> *>(smem + block_smem_bytes() + G.grp * gsm_bytes<W>());
     const int cap = cfg.c_max;
+    const int SC = a.stage_cap;   // contacts staged in shared memory; the rest spill to global memory
     // contact staging: [0] (r, gap -> 1/k_t), [1] (n, link | pad << 8), [2] (c, 1/k_n), [3] (lambda)
     float4 (*stage)[4] = reinterpret_cast<float4 (*)[4]>(
         reinterpret_cast<float4 *>(smem + block_smem_bytes() + GPB * gsm_bytes<W>()) +
-        G.grp * group_dyn_floats4(s_max, cap, WARM));
-    float4 *sph = &stage[cap][0];
+        G.grp * group_dyn_floats4(s_max, SC, cap, WARM, a.clp_cap));
+    float4 *sph = &stage[SC][0];
     float4 *clc = sph + s_max;   // cluster centres follow the spheres
     // warm start: final impulse (xyz) and pair id (w, link << 8 | sphere) of the
     // environment's last substep's contacts, in pair order
     float4 *prev = clc + 32;
+    // surviving (link index << 8 | cluster) pairs in order
+    unsigned short *clp = reinterpret_cast<unsigned short *>(prev + (WARM ? cap : 0));
+    // contacts SC .. c_max - 1 of the group's environment: its slot of the spill area
+    float4 *spill_g = a.spill ? a.spill + (size_t)(blockIdx.x * GPB + G.grp) * (size_t)(cap - SC) * 4 : nullptr;
+    auto cslot = [&](int ci) -> float4 * { return ci < SC ? stage[ci] : spill_g + (size_t)(ci - SC) * 4; };
     constexpr bool warm = WARM;
     if (threadIdx.x < kMaxLinks) {
         int c = 0;
@@ -209,7 +227,23 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
         for (int k = 0; k < 6; ++k) S.work[k] = 0ull;
     }
 
-    for (int slot = blockIdx.x * GPB + G.grp; slot < a.N; slot += gridDim.x * GPB) {
+    // the next work slot of the group: from the launch's work queue (slots in
+    // LPT order, taken one environment at a time by whichever group is free),
+    // else grid-stride
+    auto fetch = [&](int last) -> int {
+        if (!a.queue) return last < 0 ? (int)blockIdx.x * GPB + G.grp : last + (int)gridDim.x * GPB;
+        int v = 0;
+        if constexpr (TPE <= 32) {
+            if (G.tid == 0) v = atomicAdd(a.queue, 1);
+            v = __shfl_sync(G.mask, v, G.shift);
+        } else {
+            if (G.tid == 0) S.next = atomicAdd(a.queue, 1);
+            G.sync();   // S.next is written again only after the body's closing barrier
+            v = S.next;
+        }
+        return v;
+    };
+    for (int slot = fetch(-1); slot < a.N; slot = fetch(slot)) {
         const int env = a.order ? __ldg(a.order + slot) : slot;
         int st = a.status[env];
         const float4 P0 = a.pose[2 * env], P1 = a.pose[2 * env + 1];
@@ -349,7 +383,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                     } else {
                         tot = __popc(bal);
                     }
-                    if (keep) S.clp[off + __popc(bal & ((1u << G.lane_in_warp()) - 1u))] = (unsigned short)((li << 8) | k);
+                    if (keep) clp[off + __popc(bal & ((1u << G.lane_in_warp()) - 1u))] = (unsigned short)((li << 8) | k);
                     nclp += tot;
                 }
                 G.sync();
@@ -360,7 +394,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 const int npairs = nclp * kCluster;
                 auto test_pair = [&](int p, Hit &hh, V3 &r, int &l, int &j) -> bool {
                     if (p >= npairs) return false;
-                    const int e = S.clp[p / kCluster];
+                    const int e = clp[p / kCluster];
                     j = (e & 0xff) * kCluster + (p % kCluster);
                     l = S.links[e >> 8];
                     if (j >= NS) return false;
@@ -388,8 +422,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                         const float s0 = p_s0[pp], s1 = p_s1[pp];
                         if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
                     }
-                    stage[idx][0] = make_float4(r.x, r.y, r.z, hh.gap);
-                    stage[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, __int_as_float(l | ((pad & 0xff) << 8) | (j << 16)));
+                    float4 *c4 = cslot(idx);
+                    c4[0] = make_float4(r.x, r.y, r.z, hh.gap);
+                    c4[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, __int_as_float(l | ((pad & 0xff) << 8) | (j << 16)));
                 };
                 for (int p0 = 0; p0 < npairs; p0 += 2 * TPE) {
                     Hit ha = {0.0f, mk(0, 0, 1), 0.0f}, hb = {0.0f, mk(0, 0, 1), 0.0f};
@@ -438,7 +473,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 }
 
                 // -- 4. contact setup: the first TPE*CPL contacts in registers, the rest in
-                //       shared memory; the contact range of each link
+                //       shared memory (and beyond SC in the spill area); the contact
+                //       range of each link
                 V3 cr_[CPL], cn_[CPL], cc_[CPL], lam_[CPL];
                 float ikn_[CPL], ikt_[CPL];
                 const float trW = Wi.xx + Wi.yy + Wi.zz;
@@ -465,22 +501,23 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                         const float4 s0 = stage[ci][0], s1 = stage[ci][1];
                         const int l = __float_as_int(s1.w) & 0xff;
                         if (ci == 0 || (__float_as_int(stage[ci - 1][1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
-                        if (ci == nc - 1 || (__float_as_int(stage[ci + 1][1].w) & 0xff) != l) S.lend[l] = (unsigned short)(ci + 1);
+                        if (ci == nc - 1 || (__float_as_int(cslot(ci + 1)[1].w) & 0xff) != l) S.lend[l] = (unsigned short)(ci + 1);
                         const CSetup cs = setup_contact(xyz(s0), xyz(s1), s0.w, l, Wi, trW, inv_m, cfg, L0, L1, x, inv_h);
                         cr_[k] = xyz(s0); cn_[k] = xyz(s1); cc_[k] = cs.cc; ikn_[k] = cs.ikn; ikt_[k] = cs.ikt;
                         if (warm) lam_[k] = warm_lam(s1.w);
                     }
                 }
                 for (int ci = RCAP + G.tid; ci < nc; ci += TPE) {
-                    const float4 s0 = stage[ci][0], s1 = stage[ci][1];
+                    float4 *c4 = cslot(ci);
+                    const float4 s0 = c4[0], s1 = c4[1];
                     const int l = __float_as_int(s1.w) & 0xff;
-                    if ((__float_as_int(stage[ci - 1][1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
-                    if (ci == nc - 1 || (__float_as_int(stage[ci + 1][1].w) & 0xff) != l) S.lend[l] = (unsigned short)(ci + 1);
+                    if ((__float_as_int(cslot(ci - 1)[1].w) & 0xff) != l) S.lbeg[l] = (unsigned short)ci;
+                    if (ci == nc - 1 || (__float_as_int(cslot(ci + 1)[1].w) & 0xff) != l) S.lend[l] = (unsigned short)(ci + 1);
                     const CSetup cs = setup_contact(xyz(s0), xyz(s1), s0.w, l, Wi, trW, inv_m, cfg, L0, L1, x, inv_h);
-                    stage[ci][0].w = cs.ikt;
-                    stage[ci][2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikn);
+                    c4[0].w = cs.ikt;
+                    c4[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikn);
                     const V3 l0 = warm ? warm_lam(s1.w) : mk(0, 0, 0);
-                    stage[ci][3] = make_float4(l0.x, l0.y, l0.z, 0.0f);
+                    c4[3] = make_float4(l0.x, l0.y, l0.z, 0.0f);
                 }
 
                 // -- 5. Jacobi projected-impulse iterations
@@ -499,7 +536,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                             }
                         }
                         for (int ci = RCAP + G.tid; ci < nc; ci += TPE) {
-                            const V3 lam = xyz(stage[ci][3]), tq = cross(xyz(stage[ci][0]), lam);
+                            const float4 *c4 = cslot(ci);
+                            const V3 lam = xyz(c4[3]), tq = cross(xyz(c4[0]), lam);
                             acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
                             acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                         }
@@ -526,13 +564,29 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                                 acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                             }
                         }
-                        for (int ci = RCAP + G.tid; ci < nc; ci += TPE) {
+                        // staged contacts: shared memory, then the spill area (this
+                        // lane's sequence RCAP + tid, + TPE, ... continued past SC)
+                        const int ncs = min(nc, SC);
+                        for (int ci = RCAP + G.tid; ci < ncs; ci += TPE) {
                             const float4 s0 = stage[ci][0], s1 = stage[ci][1], s2 = stage[ci][2], s3 = stage[ci][3];
                             const V3 lam = update_contact(xyz(s3), xyz(s0), xyz(s1), xyz(s2), s2.w, s0.w, vv, ww, mu, inv_nc);
                             stage[ci][3] = make_float4(lam.x, lam.y, lam.z, 0.0f);
                             const V3 tq = cross(xyz(s0), lam);
                             acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
                             acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                        }
+                        if (nc > SC) {
+                            int ci = RCAP + G.tid;
+                            if (ci < SC) ci += ((SC - ci + TPE - 1) / TPE) * TPE;
+                            for (; ci < nc; ci += TPE) {
+                                float4 *c4 = spill_g + (size_t)(ci - SC) * 4;
+                                const float4 s0 = c4[0], s1 = c4[1], s2 = c4[2], s3 = c4[3];
+                                const V3 lam = update_contact(xyz(s3), xyz(s0), xyz(s1), xyz(s2), s2.w, s0.w, vv, ww, mu, inv_nc);
+                                c4[3] = make_float4(lam.x, lam.y, lam.z, 0.0f);
+                                const V3 tq = cross(xyz(s0), lam);
+                                acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
+                                acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                            }
                         }
                         group_sum6<TPE>(acc, G, &S.red[0][0][0], parity);
                         parity ^= 1;
@@ -557,7 +611,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const int ci = G.tid + k * TPE;
-                    if (ci < nc) stage[ci][3] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
+                    if (ci < nc) cslot(ci)[3] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
                 }
                 G.sync();
                 for (int p = G.tid; p < P; p += TPE) {
@@ -565,8 +619,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
                     const int e = S.lend[l];
                     for (int ci = S.lbeg[l]; ci < e; ++ci) {
-                        if (((__float_as_int(stage[ci][1].w) >> 8) & 0xff) != p) continue;
-                        const float4 s3 = stage[ci][3];
+                        const float4 *c4 = cslot(ci);
+                        if (((__float_as_int(c4[1].w) >> 8) & 0xff) != p) continue;
+                        const float4 s3 = c4[3];
                         fx -= s3.x * inv_h; fy -= s3.y * inv_h; fz -= s3.z * inv_h;
                     }
                     S.padacc[3 * p + 0] += fx;
@@ -575,8 +630,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
                 }
                 if (warm) {   // this substep's contacts and final impulses, for the next one
                     for (int ci = G.tid; ci < nc; ci += TPE) {
-                        const int wb = __float_as_int(stage[ci][1].w);
-                        const float4 l3 = stage[ci][3];
+                        const float4 *c4 = cslot(ci);
+                        const int wb = __float_as_int(c4[1].w);
+                        const float4 l3 = c4[3];
                         prev[ci] = make_float4(l3.x, l3.y, l3.z, __int_as_float((wb & 0xff) << 8 | ((wb >> 16) & 0xff)));
                     }
                     if (G.tid == 0) S.n_prev = nc;
@@ -640,6 +696,16 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
     if (G.tid == 0 && a.work)
         for (int k = 0; k < 6; ++k)
             if (S.work[k]) atomicAdd(a.work + k, S.work[k]);
+    if (a.queue) {   // the last block to finish empties the queue for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();   // this block's queue draws, before its finish ticket
+            if (atomicAdd(a.queue + 1, 1) == (int)gridDim.x - 1) {
+                atomicExch(a.queue, 0);
+                atomicExch(a.queue + 1, 0);
+            }
+        }
+    }
     if (!scored || window_mode) return;
     // argmin (C_i, i) over the grid: per-block candidate, then the last block
     __shared__ bool last;
@@ -699,21 +765,28 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<TPE, CPL>::value) step_kerne
 }
 
 template <int TPE, int CPL, bool WARM>
-size_t bytes_t(int s_max, int c_max) {
+size_t bytes_t(int s_max, int c_max, int clp_cap) {
     constexpr int GPB = Group<TPE>::GPB;
-    return block_smem_bytes() + GPB * gsm_bytes<Group<TPE>::W>() + GPB * group_dyn_floats4(s_max, c_max, WARM) * sizeof(float4);
+    const int sc = stage_capacity(TPE * CPL, c_max, GPB);
+    return block_smem_bytes() + GPB * gsm_bytes<Group<TPE>::W>() +
+           GPB * group_dyn_floats4(s_max, sc, c_max, WARM, clp_cap) * sizeof(float4);
 }
 
+// Shared-memory opt-in, and the blocks of this shape that fit on one SM
 template <int TPE, int CPL, bool WARM>
-cudaError_t prepare_t(int s_max, int c_max) {
-    const size_t bytes = bytes_t<TPE, CPL, WARM>(s_max, c_max);
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(step_kernel<TPE, CPL, WARM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t prepare_t(int s_max, int c_max, int clp_cap, int *blocks_per_sm) {
+    const size_t bytes = bytes_t<TPE, CPL, WARM>(s_max, c_max, clp_cap);
+    cudaError_t e = cudaSuccess;
+    if (bytes > 48 * 1024)
+        e = cudaFuncSetAttribute(step_kernel<TPE, CPL, WARM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && blocks_per_sm)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_kernel<TPE, CPL, WARM>, kBlock, bytes);
+    return e;
 }
 
 template <int TPE, int CPL, bool WARM>
 cudaError_t launch_t(const StepArgs &a, int grid, int s_max, cudaStream_t s) {
-    step_kernel<TPE, CPL, WARM><<<grid, kBlock, bytes_t<TPE, CPL, WARM>(s_max, a.cfg.c_max), s>>>(a, s_max);
+    step_kernel<TPE, CPL, WARM><<<grid, kBlock, bytes_t<TPE, CPL, WARM>(s_max, a.cfg.c_max, a.clp_cap), s>>>(a, s_max);
     return cudaGetLastError();
 }
 
@@ -721,16 +794,16 @@ cudaError_t launch_t(const StepArgs &a, int grid, int s_max, cudaStream_t s) {
 // warm-started (WARM = true) solver; each is instantiated in its own
 // translation unit so the two build in parallel.
 template <bool WARM>
-size_t smem_bytes_w(const StepVariant &v, int s_max, int c_max) {
-#define IH_BYTES(T, C) if (v.group == T && v.cpl == C) return bytes_t<T, C, WARM>(s_max, c_max);
+size_t smem_bytes_w(const StepVariant &v, int s_max, int c_max, int clp_cap) {
+#define IH_BYTES(T, C) if (v.group == T && v.cpl == C) return bytes_t<T, C, WARM>(s_max, c_max, clp_cap);
     IH_STEP_VARIANTS(IH_BYTES)
 #undef IH_BYTES
     return 0;
 }
 
 template <bool WARM>
-cudaError_t prepare_w(const StepVariant &v, int s_max, int c_max) {
-#define IH_PREP(T, C) if (v.group == T && v.cpl == C) return prepare_t<T, C, WARM>(s_max, c_max);
+cudaError_t prepare_w(const StepVariant &v, int s_max, int c_max, int clp_cap, int *blocks_per_sm) {
+#define IH_PREP(T, C) if (v.group == T && v.cpl == C) return prepare_t<T, C, WARM>(s_max, c_max, clp_cap, blocks_per_sm);
     IH_STEP_VARIANTS(IH_PREP)
 #undef IH_PREP
     return cudaErrorInvalidValue;

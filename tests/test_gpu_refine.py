@@ -9,6 +9,7 @@ deterministic; and it refuses a window it did not see start.
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2002_12160_gb300 import inhand, workloads as W
 
 from gpu_common import dev, start, torch
@@ -18,7 +19,7 @@ pytestmark = pytest.mark.gpu
 T = 10
 
 
-def _window(n=64, warm=20, name="tracking_cyl64"):
+def _window(n=64, warm=20, name="tracking_cyl64", T=T):
     wl = W.make_workload(name, n_envs=n, frames=warm + T + 2)
     sim = start(wl, n=n, frames=warm + T + 2)
     sim.sim_step(0, warm)
@@ -42,6 +43,7 @@ def _window(n=64, warm=20, name="tracking_cyl64"):
     sim.optimizer_update(opt, 99)
     sim.sim_set_state(pose, vel, params)
     sim.sim_mark_window()
+    sim._window_start = (pose, vel, params)
     cm = torch.empty(sim.n, dtype=torch.float64, device=d)
     for k in range(T):
         sim.sim_step_track(warm + k, obs[k], cm)
@@ -100,3 +102,100 @@ def test_refinement_is_deterministic_and_checks_its_window():
         sim.close()
     assert torch.equal(runs[0][0], runs[1][0])
     assert all(torch.equal(a, b) for a, b in zip(runs[0][1], runs[1][1]))
+
+
+# --------------------------------------------------------------- parity with the refinement oracle
+# A window of several frames tests ~10^4 sphere-link gaps, so its closest gap to
+# the contact margin is typically ~1e-6 m: the one-frame threshold (FRAGILE)
+# would leave out most windows. What can flip a branch is the FP32 state's
+# distance from the FP64 one, ~3e-9 m after a frame (one-frame parity): a
+# window is left out when a gap comes within 1e-7 m of a threshold.
+WINDOW_FRAGILE = 1e-7
+
+
+def _fragile_window(osc, sm, q_traj, f0, T, pose7, vel6, theta):
+    """True when the oracle's window from this start passes within
+    WINDOW_FRAGILE of a contact-set, pad-membership or palm-face threshold in
+    some frame, or puts a pad force within 1e-3 of the contact threshold tau
+    (where FP32 and FP64 may take different branches or count a different
+    contact mismatch)."""
+    st = O.State(pose7[None], vel6[None], theta[None])
+    for k in range(T):
+        f, diag = O.step(osc, sm, st, q_traj, f0 + k, 1)
+        if diag[0, 2] < WINDOW_FRAGILE or diag[0, 3] < WINDOW_FRAGILE or diag[0, 4] < WINDOW_FRAGILE:
+            return True
+        mag = np.linalg.norm(f[0], axis=1)
+        if np.any(np.abs(mag - sm.tau) < 1e-3 * sm.tau):
+            return True
+    return False
+
+
+def test_refinement_matches_oracle():
+    """sim_refine_elites against the FP64 refinement oracle, elite by elite,
+    from the GPU's window-start state widened exactly to FP64: the elites, the
+    accept/halve decision of every evaluation, the refined window-start state
+    (1e-5 m, 1e-5 rad, 1e-3 relative in m and mu), the unrefined and best window
+    costs (1e-3 relative), and what is committed: an improved elite's live state
+    is its best trial's window-end state (5e-5 m / rad after the window's five
+    frames), its parameters the best ones and its window sum the best cost; the
+    others keep their scored state bit for bit. Elites whose decisions are not
+    decisive (a trial's cost within 1e-3 of the best before it) or whose trial
+    windows pass near a branch threshold are skipped and counted."""
+    from oracle import adjoint as A
+    from gpu_common import POS_TOL, ROT_TOL, rot_angle, scene32, sim32
+    n, T5, steps = 64, 5, 3
+    wl, sim, obs, opt, warm, cm = _window(n=n, T=T5)
+    k = 16   # elite_frac 0.25 of 64
+    pose0, vel0, par0 = (t.clone() for t in sim._window_start)
+    before = [t.clone() for t in sim.sim_get_state()]
+    el, c0, c1, acc, sp, spar = sim.sim_refine_elites(warm, obs, opt, steps=steps, detail=True)
+    after = sim.sim_get_state()
+    el, c0, c1, acc = (t.cpu().numpy() for t in (el, c0, c1, acc))
+    sp, spar = sp.cpu().numpy().astype(np.float64), spar.cpu().numpy().astype(np.float64)
+    cm = cm.cpu().numpy()
+    np.testing.assert_array_equal(el, np.sort(np.argsort(cm, kind="stable")[:k]))
+    # the oracle sees what the GPU computes with: FP32 scene, constants, observations and eta
+    sc, sm = scene32(wl.scene), sim32(wl.sim)
+    osc = O.OracleScene(sc)
+    o32 = W.OptConfig(floor_std=tuple(float(np.float32(np.float32(0.5) * np.float32(v))) / 0.5
+                                      for v in opt.floor_std),
+                      m_range=tuple(float(np.float32(v)) for v in opt.m_range),
+                      mu_range=tuple(float(np.float32(v)) for v in opt.mu_range))
+    obs64 = obs.cpu().numpy().astype(np.float64)
+    p7 = O.pose8_to7(pose0.cpu().numpy())
+    v6 = O.vel8_to6(vel0.cpu().numpy())
+    th = par0.cpu().numpy().astype(np.float64)
+    live_p = O.pose8_to7(after[0].cpu().numpy())
+    live_v = O.vel8_to6(after[1].cpu().numpy())
+    live_th = after[2].cpu().numpy().astype(np.float64)
+    checked, skipped = 0, 0
+    for i, e in enumerate(el):
+        r = A.refine_elite(sc, sm, o32, p7[e], v6[e], th[e], wl.q_traj, warm, T5, obs64, steps=steps,
+                           step_scale=0.5, beta=1e3, width=float(np.float32(1e-3)))
+        best_before = np.minimum.accumulate(r["costs"])
+        decisive = all(abs(r["costs"][j] - best_before[j - 1]) > 1e-3 * abs(best_before[j - 1])
+                       for j in range(1, steps + 1))
+        if not decisive or any(_fragile_window(osc, sm, wl.q_traj, warm, T5, tp, v6[e], tt)
+                               for tp, tt in r["trials"]):
+            skipped += 1
+            continue
+        bits = sum(1 << j for j, a in enumerate(r["accepted"]) if a)
+        assert int(acc[i]) == bits, (e, bin(int(acc[i])), r["accepted"], r["costs"])
+        assert abs(c0[i] - r["c0"]) <= 1e-3 * abs(r["c0"]), (e, c0[i], r["c0"])
+        assert abs(c1[i] - r["best_c"]) <= 1e-3 * abs(r["best_c"]), (e, c1[i], r["best_c"])
+        gp = O.pose8_to7(sp[i])
+        assert np.linalg.norm(gp[:3] - r["pose7"][:3]) < POS_TOL, (e, gp, r["pose7"])
+        assert rot_angle(gp, r["pose7"]) < ROT_TOL, (e, gp, r["pose7"])
+        np.testing.assert_allclose(spar[i], r["theta"], rtol=1e-3)
+        assert bool(c1[i] < c0[i]) == bool(r["improved"]), e
+        if r["improved"]:
+            end = r["end"]
+            assert np.linalg.norm(live_p[e, :3] - end[:3]) < 5e-5, (e, live_p[e], end[:7])
+            assert rot_angle(live_p[e], end[:7]) < 5e-5
+            np.testing.assert_allclose(live_th[e], r["theta"], rtol=1e-3)
+            assert np.allclose(live_v[e, :3], end[7:10], atol=5e-3)
+        else:
+            for a_, b_ in zip(before[:3], after[:3]):
+                assert torch.equal(a_[int(e)], b_[int(e)])
+        checked += 1
+    assert checked >= k // 2, (checked, skipped)
