@@ -450,7 +450,7 @@ def measure_adjoint(local, n_envs=1024, horizon=30, checkpoint_every=10, reps=3)
     return out
 
 
-def refine_study(local, seeds=(11, 12, 13, 14, 15, 16), frames=300, n_refined=1024, steps=3):
+def refine_study(local, seeds=tuple(range(11, 35)), frames=300, n_refined=1024, steps=3):
     """Tracking error (ADD of the argmin estimate, mm, over `frames` frames) of
     the plain update against the update preceded by 3 gradient-refinement steps
     of the elites, at equal wall time: the refined run has N = n_refined; the

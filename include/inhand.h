@@ -450,8 +450,10 @@ ih_status ih_fp32_peak(int32_t iters, int32_t reps, void *stream, double *tflops
  * Limits: n_envs <= 131072 (IH_ERR_OVERFLOW beyond it), n_pads <= IH_MAX_PADS.
  * Its scratch -- one partial per 32 environments and a counter, about 48 KiB --
  * is a fixed __device__ array that every GPU which loads this library holds
- * until the process exits. The first call on each device looks up that
- * array's device address; make that first call before any stream capture.
+ * until the process exits. Every call looks up that array's device address in
+ * the current device's context (so a device reset cannot leave a stale one);
+ * the first lookup on a device may load the library's device code, so make
+ * the first call on each device before any stream capture.
  * Every call shares the one array (each call re-zeroes its counter on the
  * stream), so calls that may overlap on the GPU -- on different streams, or
  * from different threads -- race and must be serialised by the caller.

@@ -21,8 +21,11 @@
 // Contact membership (gap < margin), the capsule's end clamps, the palm's face
 // or clamp pattern and the bias regimes are held fixed.
 //
-// Work layout: one warp per environment, contacts strided over the lanes in
-// contact order (lane k % 32 owns contact k). The state at every K-th frame is
+// Work layout: a group of GW warps (32 GW threads) per environment. The first
+// warp enumerates the contacts; then thread k % (32 GW) of the group owns
+// contact k for the setup, the Jacobi iterations and their reverse, and the
+// group sums impulses and derivatives by warp shuffles and a shared-memory
+// exchange between its warps. The state at every K-th frame is
 // kept (checkpoints). The reverse sweep walks the segments between checkpoints
 // backwards: it recomputes the segment's substep start states and pad forces
 // from its checkpoint, then for each substep in reverse order recomputes the
@@ -36,9 +39,32 @@
 namespace ih {
 namespace {
 
-constexpr int kAW = 4;   // environments (warps) per CTA
+constexpr int kAW = 4;   // warps per CTA
 constexpr int kABlock = 32 * kAW;
 constexpr unsigned kFull = 0xffffffffu;
+
+// The GW warps of one environment: group thread gt, lane, warp within the
+// group, group within the block; sync() is the group's barrier.
+template <int GW>
+struct AGroup {
+    static constexpr int T = 32 * GW;
+    int gt, lane, wg, gid;
+    __device__ AGroup() {
+        gt = threadIdx.x % T;
+        lane = threadIdx.x & 31;
+        wg = gt >> 5;
+        gid = threadIdx.x / T;
+    }
+    __device__ __forceinline__ void sync() const {
+        if constexpr (GW == 1) {
+            __syncwarp();
+        } else if constexpr (T == kABlock) {
+            __syncthreads();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(T) : "memory");
+        }
+    }
+};
 
 struct Body {
     V3 x;
@@ -63,11 +89,37 @@ __device__ __forceinline__ Body load_body(const float4 *p) {
 }
 __device__ __forceinline__ Q4 qconj(Q4 q) { return {q.w, -q.x, -q.y, -q.z}; }
 
-struct WarpSm {
+template <int GW>
+struct alignas(16) GroupSm {
     float padacc[IH_MAX_PADS * 3];
     float fbar[IH_MAX_PADS * 3];   // dL/dF_p / (h ns): minus the derivative w.r.t. a final impulse
+    float red[2][GW][8];           // partial sums of the group's warps (double-buffered)
     unsigned short lbeg[32], lend[32];
+    int nc;                        // the substep's contact count (from the enumerating warp)
+    int parity;
 };
+
+// Sum of 6 values over the group's threads, every thread receiving the sums:
+// within each warp by shuffles, then the warps' partials in warp order.
+template <int GW>
+__device__ __forceinline__ void gsum6(float (&v)[6], const AGroup<GW> &G, GroupSm<GW> &S, int &parity) {
+    if constexpr (GW == 1) {
+        width_sum6<32>(v, kFull, G.lane);
+    } else {
+        const float c = width_scatter6<32>(v, kFull, G.lane);
+        float *r = &S.red[parity][0][0];
+        const int k = G.lane >> 2;
+        if ((G.lane & 3) == 0 && k < 6) r[G.wg * 8 + k] = c;
+        G.sync();
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = r[q];
+#pragma unroll
+        for (int w = 1; w < GW; ++w)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[q] += r[w * 8 + q];
+        parity ^= 1;
+    }
+}
 
 // Per-slot scratch layout in floats (every part starts on a float4 boundary):
 // checkpoints, a segment's substep start states and frame forces, the final
@@ -116,7 +168,7 @@ struct SlotPtr {
 
 // Per-environment constants.
 struct Env {
-    int sfirst, NS, iters;
+    int sfirst, NS, iters, cfirst;
     float mu, inv_m, bound;
     S6 Jb;
 };
@@ -132,10 +184,11 @@ __device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y)
 // Returns the contact count (0 on overflow). Not inlined, with the two flags
 // as arguments: every pass (cost, recomputation, tape) then runs the same
 // compiled arithmetic, so a recorded tape is bit for bit the forward's.
-template <int PL>
+template <int GW, int PL>
 __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4 *L0,
-                                        const float4 *L1, const SlotPtr &sp, WarpSm &S, int lane, int &st,
-                                        const bool TAPE, const bool PADS) {
+                                        const float4 *L1, const SlotPtr &sp, GroupSm<GW> &S, const AGroup<GW> &G,
+                                        int &parity, int &st, const bool TAPE, const bool PADS) {
+    constexpr int T = AGroup<GW>::T;
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
     const int Lk = sc.n_links, P = sc.n_pads, cap = cfg.c_max;
@@ -145,7 +198,12 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
     const V3 w_pred = b.w;
     const M3 R = qmat(b.q);
     const S6 Wi = world_inv_inertia(R, E.Jb, E.inv_m);
+    const int lane = G.lane;
 
+    // contact enumeration, by the group's first warp: surviving links in order;
+    // per link the clusters within reach, then their spheres in order (the
+    // step's order: link, then sphere)
+    if (G.wg == 0) {
     const bool keep = lane < Lk && link_reaches(sc, cfg, L0, lane, b.x, E.bound);
     const unsigned surv = __ballot_sync(kFull, keep);
     S.lbeg[lane] = 0;
@@ -153,6 +211,14 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
     __syncwarp();
     int nc = 0;
     const unsigned below = (1u << lane) - 1u;
+    const int ncl = (E.NS + kCluster - 1) / kCluster;
+    V3 clw = mk(0, 0, 0);   // this lane's cluster centre (world, relative to x) and radius
+    float clr = 0.0f;
+    if (lane < ncl) {
+        const float4 cl = __ldg(sc.clusters + E.cfirst + lane);
+        clw = mmul(R, xyz(cl));
+        clr = cl.w;
+    }
     for (unsigned ms = surv; ms; ms &= ms - 1u) {
         const int l = __ffs(ms) - 1;
         const int first = nc;
@@ -160,8 +226,17 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
         const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
         const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
         const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-        for (int j0 = 0; j0 < E.NS; j0 += 32) {
-            const int j = j0 + lane;
+        const unsigned cm = __ballot_sync(kFull, lane < ncl && link_reaches(sc, cfg, L0, l, b.x + clw, clr));
+        const int nsc = __popc(cm);
+        // surviving clusters, four to a round of 32 lanes (eight spheres each)
+        for (int c0 = 0; c0 < nsc; c0 += 4) {
+            int cc = -1;
+            {   // the (c0 + lane / 8)-th set bit of cm
+                unsigned mm = cm;
+                for (int q = 0; q < c0 + (lane >> 3) && mm; ++q) mm &= mm - 1u;
+                if (mm && c0 + (lane >> 3) < nsc) cc = __ffs(mm) - 1;
+            }
+            const int j = cc >= 0 ? cc * kCluster + (lane & 7) : E.NS;
             bool hit = false;
             Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
             V3 r = mk(0, 0, 0);
@@ -195,19 +270,26 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
             S.lend[l] = (unsigned short)nc;
         }
     }
-    __syncwarp();
+    if (lane == 0) S.nc = nc;
+    }
+    G.sync();
+    int nc = S.nc;
     if (nc > cap) {   // more contacts than the per-env capacity: as the step, no contacts
         st |= IH_ENV_OVERFLOW;
         nc = 0;
     }
 
-    // contact setup, by the lane that owns the contact from here on
+    // contact setup, by the thread that owns the contact from here on; the
+    // constants stay in its registers for the iterations
     const float trW = Wi.xx + Wi.yy + Wi.zz;
-    V3 lam_[PL];
+    V3 lam_[PL], cr_[PL], cn_[PL], cc_[PL];
+    float ikn_[PL], ikt_[PL];
 #pragma unroll
     for (int k = 0; k < PL; ++k) {
         lam_[k] = mk(0, 0, 0);
-        const int ci = lane + 32 * k;
+        cr_[k] = mk(0, 0, 0); cn_[k] = mk(0, 0, 1); cc_[k] = mk(0, 0, 0);
+        ikn_[k] = ikt_[k] = 0.0f;
+        const int ci = G.gt + T * k;
         if (ci < nc) {
             float4 *rc = sp.rec + 4 * ci;
             const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
@@ -215,6 +297,7 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
                                             inv_h);
             rc[1] = make_float4(r1.x, r1.y, r1.z, cs.ikn);
             rc[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikt);
+            cr_[k] = xyz(r0); cn_[k] = xyz(r1); cc_[k] = cs.cc; ikn_[k] = cs.ikn; ikt_[k] = cs.ikt;
         }
     }
 
@@ -226,19 +309,17 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
             float acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int k = 0; k < PL; ++k) {
-                const int ci = lane + 32 * k;
+                const int ci = G.gt + T * k;
                 if (ci < nc) {
-                    const float4 *rc = sp.rec + 4 * ci;
-                    const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
-                    lam_[k] = update_contact(lam_[k], xyz(r0), xyz(r1), xyz(r2), r1.w, r2.w, vv, ww, E.mu, inv_nc);
-                    const V3 tq = cross(xyz(r0), lam_[k]);
+                    lam_[k] = update_contact(lam_[k], cr_[k], cn_[k], cc_[k], ikn_[k], ikt_[k], vv, ww, E.mu, inv_nc);
+                    const V3 tq = cross(cr_[k], lam_[k]);
                     acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
                     acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                     if (TAPE) sp.lamh[(size_t)it * cap + ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
                 }
             }
-            width_sum6<32>(acc, kFull, lane);
-            if (TAPE && lane == 0)
+            gsum6<GW>(acc, G, S, parity);
+            if (TAPE && G.gt == 0)
                 for (int q = 0; q < 6; ++q) sp.sh[8 * it + q] = acc[q];
             vv = v_pred + mk(acc[0], acc[1], acc[2]) * E.inv_m;
             ww = w_pred + smul(Wi, mk(acc[3], acc[4], acc[5]));
@@ -258,11 +339,11 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
         // pad forces -lambda / h, each pad summing the contacts of its link in order
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
-            const int ci = lane + 32 * k;
+            const int ci = G.gt + T * k;
             if (ci < nc) sp.lamf[ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
         }
-        __syncwarp();
-        if (lane < P && nc > 0) {
+        G.sync();
+        if (G.gt < P && nc > 0) {
             const int l = __ldg(sc.pad_link + lane);
             float fx = 0.0f, fy = 0.0f, fz = 0.0f;
             const int e = S.lend[l];
@@ -276,7 +357,7 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
             S.padacc[3 * lane + 2] += fz;
         }
     }
-    __syncwarp();
+    G.sync();
     return nc;
 }
 
@@ -371,10 +452,11 @@ __device__ __forceinline__ void outer_add(float (&M)[9], V3 a, V3 b, float s) {
 // been recomputed with a tape; nc contacts). On entry `ad` holds the
 // derivatives w.r.t. the substep's end state, on return those w.r.t. b.
 // invm_b (lane-uniform) and mu_b (per lane) accumulate d/d(1/m) and d/dmu.
-template <int PL>
+template <int GW, int PL>
 __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const float4 *L0, const float4 *L1,
-                            int nc, const SlotPtr &sp, const WarpSm &S, int lane, Adj &ad, float &invm_b,
-                            float &mu_b) {
+                            int nc, const SlotPtr &sp, GroupSm<GW> &S, const AGroup<GW> &G, int &parity, Adj &ad,
+                            float &invm_b, float &mu_b) {
+    constexpr int T = AGroup<GW>::T;
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
     const int cap = cfg.c_max, I = E.iters;
@@ -435,23 +517,55 @@ __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const
         const float inv_nc = 1.0f / (float)nc;
         V3 lb[PL], nb[PL], rb[PL], cb[PL];
         float iknb[PL], iktb[PL];
+        // the contacts' constants in registers, and the tape one iteration ahead:
+        // l1_ the impulse after iteration it, l0_ after it - 1 (zero before the
+        // first), sc_/sp_ the sums after it and it - 1
+        V3 r_[PL], n_[PL], c_[PL], l1_[PL], l0_[PL];
+        float ikn_[PL], ikt_[PL];
+        auto lam_at = [&](int it, int ci) -> V3 { return it >= 0 ? xyz(sp.lamh[(size_t)it * cap + ci]) : mk(0, 0, 0); };
+        auto sums_at = [&](int it, float4 &lo, float4 &hi) {
+            if (it >= 0) {
+                const float4 *q = reinterpret_cast<const float4 *>(sp.sh + 8 * it);
+                lo = q[0]; hi = q[1];
+            } else {
+                lo = hi = make_float4(0, 0, 0, 0);
+            }
+        };
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
             lb[k] = nb[k] = rb[k] = cb[k] = mk(0, 0, 0);
             iknb[k] = iktb[k] = 0.0f;
-            const int ci = lane + 32 * k;
+            r_[k] = n_[k] = c_[k] = l1_[k] = l0_[k] = mk(0, 0, 0);
+            ikn_[k] = ikt_[k] = 0.0f;
+            const int ci = G.gt + T * k;
             if (ci < nc) {
-                const int pad = rec_pad(sp.rec[4 * ci + 3]);
+                const float4 *rc = sp.rec + 4 * ci;
+                const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2], r3 = rc[3];
+                r_[k] = xyz(r0); n_[k] = xyz(r1); c_[k] = xyz(r2); ikn_[k] = r1.w; ikt_[k] = r2.w;
+                l1_[k] = lam_at(I - 1, ci);
+                l0_[k] = lam_at(I - 2, ci);
+                const int pad = rec_pad(r3);
                 if (pad < sc.n_pads) lb[k] = mk(-S.fbar[3 * pad], -S.fbar[3 * pad + 1], -S.fbar[3 * pad + 2]);
             }
         }
+        float4 sc_lo, sc_hi, sp_lo, sp_hi;
+        sums_at(I - 1, sc_lo, sc_hi);
+        sums_at(I - 2, sp_lo, sp_hi);
         for (int it = I - 1; it >= 0; --it) {
+            // the tape of iteration it - 2, for the next step, requested now
+            V3 pf_[PL];
+#pragma unroll
+            for (int k = 0; k < PL; ++k) {
+                const int ci = G.gt + T * k;
+                pf_[k] = (ci < nc) ? lam_at(it - 2, ci) : mk(0, 0, 0);
+            }
+            float4 pf_lo, pf_hi;
+            sums_at(it - 2, pf_lo, pf_hi);
             // (a) V^{it+1} = v_pred + S1 / m, W^{it+1} = w_pred + W S2, sums of the impulses after it
-            const float *s = sp.sh + 8 * it;
-            const V3 S1 = mk(s[0], s[1], s[2]), S2 = mk(s[3], s[4], s[5]);
+            const V3 S1 = mk(sc_lo.x, sc_lo.y, sc_lo.z), S2 = mk(sc_lo.w, sc_hi.x, sc_hi.y);
             vpb = vpb + Vb;
             wpb = wpb + Wb;
-            if (lane == 0) {
+            if (G.gt == 0) {
                 invm_l += dot(Vb, S1);
                 outer_add(Wbar, Wb, S2, 1.0f);
             }
@@ -459,31 +573,26 @@ __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const
             const V3 vm = Vb * E.inv_m;
 #pragma unroll
             for (int k = 0; k < PL; ++k) {
-                const int ci = lane + 32 * k;
+                const int ci = G.gt + T * k;
                 if (ci < nc) {
-                    const V3 r = xyz(sp.rec[4 * ci]);
-                    const V3 l1 = xyz(sp.lamh[(size_t)it * cap + ci]);
-                    lb[k] = lb[k] + vm + cross(g, r);
-                    rb[k] = rb[k] + cross(l1, g);
+                    lb[k] = lb[k] + vm + cross(g, r_[k]);
+                    rb[k] = rb[k] + cross(l1_[k], g);
                 }
             }
             // (b) the contact updates of iteration it, against V^it, W^it
             V3 Vi = v_pred, Wv = w_pred;
             if (it > 0) {
-                const float *s0 = sp.sh + 8 * (it - 1);
-                Vi = v_pred + mk(s0[0], s0[1], s0[2]) * E.inv_m;
-                Wv = w_pred + smul(Wi, mk(s0[3], s0[4], s0[5]));
+                Vi = v_pred + mk(sp_lo.x, sp_lo.y, sp_lo.z) * E.inv_m;
+                Wv = w_pred + smul(Wi, mk(sp_lo.w, sp_hi.x, sp_hi.y));
             }
             float acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int k = 0; k < PL; ++k) {
-                const int ci = lane + 32 * k;
+                const int ci = G.gt + T * k;
                 if (ci < nc) {
-                    const float4 *rc = sp.rec + 4 * ci;
-                    const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
-                    const V3 r = xyz(r0), n = xyz(r1), cc = xyz(r2);
-                    const float ikn = r1.w, ikt = r2.w;
-                    const V3 l0 = it > 0 ? xyz(sp.lamh[(size_t)(it - 1) * cap + ci]) : mk(0, 0, 0);
+                    const V3 r = r_[k], n = n_[k], cc = c_[k];
+                    const float ikn = ikn_[k], ikt = ikt_[k];
+                    const V3 l0 = l0_[k];
                     const V3 u = Vi + cross(Wv, r) - cc;
                     const float un = dot(u, n), lo = dot(l0, n);
                     const float zn = lo - un * ikn;
@@ -527,9 +636,16 @@ __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const
                     cb[k] = cb[k] - ub;
                 }
             }
-            width_sum6<32>(acc, kFull, lane);
+            gsum6<GW>(acc, G, S, parity);
             Vb = mk(acc[0], acc[1], acc[2]);
             Wb = mk(acc[3], acc[4], acc[5]);
+#pragma unroll
+            for (int k = 0; k < PL; ++k) {
+                l1_[k] = l0_[k];
+                l0_[k] = pf_[k];
+            }
+            sc_lo = sp_lo; sc_hi = sp_hi;
+            sp_lo = pf_lo; sp_hi = pf_hi;
         }
         vpb = vpb + Vb;   // V^0 = v_pred, W^0 = w_pred
         wpb = wpb + Wb;
@@ -537,7 +653,7 @@ __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const
         // contact setup and narrowphase, in reverse
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
-            const int ci = lane + 32 * k;
+            const int ci = G.gt + T * k;
             if (ci < nc) {
                 const float4 *rc = sp.rec + 4 * ci;
                 const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2], r3 = rc[3];
@@ -591,10 +707,10 @@ __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const
     float r2[6] = {Wbar[2], Wbar[3], Wbar[4], Wbar[5], Wbar[6], Wbar[7]};
     float r3[6] = {Wbar[8], Rbar[0], Rbar[1], Rbar[2], Rbar[3], Rbar[4]};
     float r4[6] = {Rbar[5], Rbar[6], Rbar[7], Rbar[8], 0.0f, 0.0f};
-    width_sum6<32>(r1, kFull, lane);
-    width_sum6<32>(r2, kFull, lane);
-    width_sum6<32>(r3, kFull, lane);
-    width_sum6<32>(r4, kFull, lane);
+    gsum6<GW>(r1, G, S, parity);
+    gsum6<GW>(r2, G, S, parity);
+    gsum6<GW>(r3, G, S, parity);
+    gsum6<GW>(r4, G, S, parity);
     const float Wt[9] = {r1[4], r1[5], r2[0], r2[1], r2[2], r2[3], r2[4], r2[5], r3[0]};
     float Rt[9] = {r3[1], r3[2], r3[3], r3[4], r3[5], r4[0], r4[1], r4[2], r4[3]};
     // W = R J R^T / m:  d/d(1/m) += <Wbar, R J R^T>,  Rbar += (Wbar + Wbar^T) R J / m
@@ -641,13 +757,16 @@ __device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const
     ad.w = wpb;
 }
 
-template <int PL>
+template <int GW, int PL>
 __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
-    __shared__ WarpSm sm[kAW];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * kAW + wid;
-    if (slot >= a.n) return;   // whole warps only
-    WarpSm &S = sm[wid];
+    constexpr int T = AGroup<GW>::T, GPB = kAW / GW;
+    __shared__ GroupSm<GW> sm[GPB];
+    const AGroup<GW> G;
+    const int lane = G.gt;   // the group's thread (0 .. 32 GW - 1)
+    const int slot = blockIdx.x * GPB + G.gid;
+    if (slot >= a.n) return;   // whole groups only
+    GroupSm<GW> &S = sm[G.gid];
+    int parity = 0;   // the group's reduction buffer
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
     const int ns = cfg.substeps, Lk = sc.n_links, P = sc.n_pads, cap = cfg.c_max;
@@ -684,6 +803,7 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     E.mu = th.y;
     E.inv_m = 1.0f / th.x;
     E.bound = __ldg(sc.shape_bound + shp);
+    E.cfirst = __ldg(sc.cl_first + shp);
     E.Jb.xx = __ldg(sc.shape_jinv + 6 * shp + 0); E.Jb.yy = __ldg(sc.shape_jinv + 6 * shp + 1);
     E.Jb.zz = __ldg(sc.shape_jinv + 6 * shp + 2); E.Jb.xy = __ldg(sc.shape_jinv + 6 * shp + 3);
     E.Jb.xz = __ldg(sc.shape_jinv + 6 * shp + 4); E.Jb.yz = __ldg(sc.shape_jinv + 6 * shp + 5);
@@ -703,8 +823,8 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     Body b = b0;
     for (int f = 0; f < a.H && !(st & kDiverged); ++f) {
         if (f % a.K == 0 && lane == 0) store_body(sp.ck + 4 * (f / a.K), b);
-        for (int k = lane; k < 3 * P; k += 32) S.padacc[k] = 0.0f;
-        __syncwarp();
+        for (int k = lane; k < 3 * P; k += T) S.padacc[k] = 0.0f;
+        G.sync();
         const float4 *tab = tab0 + (size_t)f * tab_frame;
         for (int s = 0; s < ns; ++s) {
             const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
@@ -712,15 +832,15 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 const int blk = (f - f_last) * ns + s;
                 if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 if (seg_tape && !a.forward_only) {   // the last segment's tape, recorded on the way
-                    const int nc = fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, lane, st, true, true);
+                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, G, parity, st, true, true);
                     if (lane == 0) sp.ncs[blk] = nc;
                     continue;
                 }
             }
-            fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st, false, true);
+            fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, G, parity, st, false, true);
         }
         if (f >= f_last)
-            for (int k = lane; k < 3 * P; k += 32) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
+            for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
         if (!all_finite(b.x, b.q, b.v, b.w)) st |= IH_ENV_NONFINITE;
         else if (dot(b.x, b.x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
         if (lane == 0) {   // frame cost in FP64, in pad order, as the scored step
@@ -740,7 +860,7 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
             }
             cost = __dadd_rn(cost, cf);
         }
-        __syncwarp();
+        G.sync();
     }
     if (a.out_pose && lane == 0) {   // the horizon's end state (not meaningful when diverged)
         a.out_pose[2 * slot] = make_float4(b.x.x, b.x.y, b.x.z, 0.0f);
@@ -767,28 +887,28 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
         const int fb = seg * a.K, fe = min(a.H, fb + a.K);
         b = load_body(sp.ck + 4 * seg);
         for (int f = fb; f < fe && seg < nck - 1; ++f) {   // substep start states and frame forces
-            for (int k = lane; k < 3 * P; k += 32) S.padacc[k] = 0.0f;
-            __syncwarp();
+            for (int k = lane; k < 3 * P; k += T) S.padacc[k] = 0.0f;
+            G.sync();
             const float4 *tab = tab0 + (size_t)f * tab_frame;
             for (int s = 0; s < ns; ++s) {
                 const int blk = (f - fb) * ns + s;
                 if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
                 if (seg_tape) {
-                    const int nc = fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, lane, st, true, true);
+                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, G, parity, st, true, true);
                     if (lane == 0) sp.ncs[blk] = nc;
                 } else {
-                    fwd_substep<PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, lane, st, false, true);
+                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, G, parity, st, false, true);
                 }
             }
-            for (int k = lane; k < 3 * P; k += 32) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
-            __syncwarp();
+            for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
+            G.sync();
         }
         for (int f = fe - 1; f >= fb; --f) {
             const float *o = a.obs + (size_t)f * P * 3;
-            for (int k = lane; k < 3 * P; k += 32)
+            for (int k = lane; k < 3 * P; k += T)
                 S.fbar[k] = wf2 * (sp.sf[(size_t)(f - fb) * 3 * P + k] - o[k]);
-            __syncwarp();
+            G.sync();
             const float4 *tab = tab0 + (size_t)f * tab_frame;
             for (int s = ns - 1; s >= 0; --s) {
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
@@ -796,20 +916,23 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 const int blk = (f - fb) * ns + s;
                 const Body bs = load_body(sp.sg + 4 * blk);
                 if (seg_tape) {
-                    __syncwarp();
-                    rev_substep<PL>(a, E, bs, L0, L1, sp.ncs[blk], sp.blk(blk), S, lane, ad, invm_b, mu_b);
+                    G.sync();
+                    rev_substep<GW, PL>(a, E, bs, L0, L1, sp.ncs[blk], sp.blk(blk), S, G, parity, ad, invm_b, mu_b);
                 } else {   // re-run the substep once more, recording its tape
                     Body bt = bs;
                     int st2 = 0;
-                    const int nc = fwd_substep<PL>(a, E, bt, L0, L1, sp, S, lane, st2, true, false);
-                    rev_substep<PL>(a, E, bs, L0, L1, nc, sp, S, lane, ad, invm_b, mu_b);
+                    const int nc = fwd_substep<GW, PL>(a, E, bt, L0, L1, sp, S, G, parity, st2, true, false);
+                    rev_substep<GW, PL>(a, E, bs, L0, L1, nc, sp, S, G, parity, ad, invm_b, mu_b);
                 }
             }
-            __syncwarp();
+            G.sync();
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mu_b += __shfl_xor_sync(kFull, mu_b, o);
+    {
+        float mv[6] = {mu_b, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        gsum6<GW>(mv, G, S, parity);
+        mu_b = mv[0];
+    }
     if (lane == 0) {
         // rotation tangent: q = exp(delta) q0, d/d delta at 0 = vec(qbar (x) conj(q0)) / 2
         const Q4 g = qmul(ad.q, qconj(b0.q));
@@ -826,9 +949,10 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     }
 }
 
-template <int PL>
+template <int GW, int PL>
 cudaError_t launch_pl(const AdjArgs &a, cudaStream_t s) {
-    adjoint_kernel<PL><<<(a.n + kAW - 1) / kAW, kABlock, 0, s>>>(a);
+    constexpr int GPB = kAW / GW;
+    adjoint_kernel<GW, PL><<<(a.n + GPB - 1) / GPB, kABlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -950,12 +1074,29 @@ cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, 
     return cudaGetLastError();
 }
 
+#ifndef IH_ADJ_GROUPS_PER_SM
+#define IH_ADJ_GROUPS_PER_SM 2
+#endif
+// Few environments (the refined elites, a small batch), at most two per SM --
+// the blocks of ~250 registers a thread that an SM holds: four warps each, so
+// that their contacts' chains run side by side. More: one warp each (no
+// barriers between the warps of an environment) while each thread holds at
+// most four contacts; two warps each beyond that (c_max > 128), where a
+// thread's eight contacts would not fit in its registers.
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s) {
-    const int pl = (a.cfg.c_max + 31) / 32;
-    if (pl <= 1) return launch_pl<1>(a, s);
-    if (pl <= 2) return launch_pl<2>(a, s);
-    if (pl <= 4) return launch_pl<4>(a, s);
-    return launch_pl<8>(a, s);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int cap = a.cfg.c_max;
+    if (a.n <= IH_ADJ_GROUPS_PER_SM * sms) {
+        if (cap <= 128) return launch_pl<4, 1>(a, s);
+        return launch_pl<4, 2>(a, s);
+    }
+    if (cap <= 32) return launch_pl<1, 1>(a, s);
+    if (cap <= 64) return launch_pl<1, 2>(a, s);
+    if (cap <= 128) return launch_pl<1, 4>(a, s);
+    return launch_pl<2, 4>(a, s);
 }
 
 }  // namespace ih

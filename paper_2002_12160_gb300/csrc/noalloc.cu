@@ -9,8 +9,6 @@
 // This entry point therefore keeps its scratch -- one partial (cost, index)
 // per block and the last-block ticket -- in a file-scope __device__ array of
 // fixed size that every GPU loading the library holds until the process exits.
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace ih {
@@ -29,11 +27,10 @@ struct NaScratch {
 };
 static __device__ __align__(256) NaScratch g_na_scratch;
 
-// Device addresses of g_na_scratch, resolved once per device (host code must
-// not pass the symbol itself: on the host it only stands in for the array).
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_mutex;
-NaScratch *g_na_ptr[kNaMaxDevices] = {};
+// Host code must not pass the symbol g_na_scratch itself to a kernel: on the
+// host it only stands in for the array. Its device address is looked up on
+// every call, in the current device's context (the lookup allocates nothing),
+// so a device reset or a new primary context cannot leave a stale address.
 
 __device__ __forceinline__ bool na_better(double ca, int ia, double cb, int ib) {
     return ca < cb || (ca == cb && ia < ib);
@@ -106,20 +103,12 @@ cost_static_kernel(const float *forces, const float *obs, const int *status, int
     }
 }
 
-// Resolve the scratch's device address on the current device (once per device).
+// The scratch's device address in the current device's context.
 ih_status na_scratch(NaScratch **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return IH_ERR_CUDA;
-    if (dev < 0 || dev >= kNaMaxDevices) return IH_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess || !p) return IH_ERR_CUDA;
-        g_na_ptr[dev] = static_cast<NaScratch *>(p);
-    }
-    *out = g_na_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess || !p) return IH_ERR_CUDA;
+    *out = static_cast<NaScratch *>(p);
     return IH_OK;
 }
 
