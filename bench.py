@@ -73,7 +73,7 @@ FLOP_PER_ENV_ITER = 24
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
 # sources (step.cu, step_kernel.cuh, contact.cuh) whose hash is recorded with it; reported as
 # null once they change.
-STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "abe9db5ac5a3b1248b2c13cf1273ae96199e0b3e53cbf4e515a41a7a9a603c68"}
+STEP_TRAFFIC = {"bytes_per_launch": 200448, "sources_sha256": "ce1c43c5f7d81e7c8d982d1eef7ca0f277675b24f82eb08f15099a0743e2105f"}
 STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/step_kernel.cuh",
                 "paper_2002_12160_gb300/csrc/contact.cuh"]
 
@@ -833,36 +833,39 @@ def summarize(m, peak_tf, hbm_gbs, world=1):
     return out
 
 
-def largest_n_at_30hz(workload, local, shape, rate_hint, floor_n, step=8192, max_points=5):
+def largest_n_at_30hz(workload, local, shape, rate_hint, floor_n, peak_tf, hbm_gbs, step=4096, max_points=5):
     """Bounded search for the largest N whose tracking window holds >= 30
-    tracking frames/s: start from the saturated throughput's prediction
-    (rate / 30), then bisect between the largest passing and the smallest
-    failing N on a grid of `step` environments, at most `max_points` points."""
+    tracking frames/s: each point predicts the boundary from its own measured
+    throughput (N = rate / 30 on a grid of `step` environments; one step
+    further when the prediction is the point itself), until the boundary is
+    bracketed within one grid step or `max_points` points are spent; each
+    point also times the step kernel alone (its FP32 and HBM roofline)."""
     import torch
     pts = []
 
-    def fps(n):
-        r = measure(workload, n, 3, 2, shape, 0, 1, local, n_timing=0)
-        f = r["T"] / (r["ms"] / 1e3)
-        pts.append({"n_envs": n, "tracking_frames_per_s": f, "env_steps_per_s": n * f,
-                    "ms_per_window": r["ms"]})
+    def point(n):
+        r = measure(workload, n, 3, 2, shape, 0, 1, local, n_timing=2)
+        p = summarize(r, peak_tf, hbm_gbs)
+        p.pop("work_per_env_frame", None)
+        pts.append(p)
         torch.cuda.empty_cache()
-        return f
+        return p["tracking_frames_per_s"], p["env_steps_per_s"]
 
     lo, hi = floor_n, None     # floor_n holds 30 Hz (measured in the sweep)
     n = max(lo + step, step * int(rate_hint / 30.0 // step))
-    stride = max(step, step * int(0.04 * n // step))   # ~4 % moves until the boundary is bracketed
     while len(pts) < max_points:
-        if fps(n) >= 30.0:
+        f, rate = point(n)
+        if f >= 30.0:
             lo = max(lo, n)
         else:
             hi = n if hi is None else min(hi, n)
         if hi is not None and hi - lo <= step:
             break
+        pred = step * int(rate / 30.0 // step)
         if hi is None:
-            n = lo + stride
-        elif lo <= floor_n and n == hi:
-            n = max(floor_n + step, hi - stride)
+            n = max(lo + step, pred)
+        elif lo <= floor_n:
+            n = max(floor_n + step, min(hi - step, pred))
         else:
             n = lo + step * max(1, (hi - lo) // (2 * step))
     return {"largest_n_measured_at_30hz": lo, "smallest_n_measured_below_30hz": hi, "grid": step,
@@ -938,7 +941,7 @@ def run_ours(args, rank, world, local):
         shp = (sat["step_shape"]["threads_per_env"], sat["step_shape"]["contacts_per_thread"])
         ok = [p["n_envs"] for p in sweep if p["tracking_frames_per_s"] >= 30.0]
         line["sweep_mug128"]["largest_n_at_30hz"] = largest_n_at_30hz(
-            "sweep_mug128", local, shp, sat["env_steps_per_s"], max(ok) if ok else 1024)
+            "sweep_mug128", local, shp, sat["env_steps_per_s"], max(ok) if ok else 1024, peak_tf, hbm_gbs)
         # config 3: forward + adjoint of a 30-frame horizon, N = 1024, box and cylinder
         line["adjoint"] = {"what": "forward + reverse-mode gradient of the horizon cost (sim_adjoint), "
                                    "every environment, H = 30 frames, checkpoints every 10",
