@@ -32,7 +32,7 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------- */
-/* records passed from Python (ctypes mirrors live in oracle/oracle.py)       */
+/* records passed from Python (ctypes mirrors live in oracle/__init__.py)    */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int32_t n_shapes;

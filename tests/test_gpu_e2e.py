@@ -11,11 +11,13 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("workload,n", [("tracking_box27", 64), ("tracking_cyl64", 300)])
 def test_end_to_end_windows_equal_the_device_windows(workload, n):
-    """Tracker.e2e_windows -- its pipelined half (two device buffers, uploads,
-    command kinematics and read-backs on a second stream) and its half with the
-    host waiting for every window -- gives the estimates and argmins of the
-    same windows launched from device-resident commands and observations, bit
-    for bit, and leaves the same state behind."""
+    """Tracker.e2e_windows -- its pipelined half (every window's packed inputs
+    copied up, its commands' kinematics, the window, its outputs copied back,
+    all enqueued on the handle's one stream with a single synchronisation at
+    the end) and its half with the host waiting for every window -- gives the
+    estimates and argmins of the same windows launched from device-resident
+    commands and observations, bit for bit, and leaves the same state
+    behind."""
     from paper_2002_12160_gb300 import tracking
     dev()
     count = 6
