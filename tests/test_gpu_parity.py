@@ -406,3 +406,50 @@ def test_reps_window_replay_equals_the_separate_calls():
         b.sim_track_window(w * T, obs[w * T:(w + 1) * T], opt, w)
     for x, y in zip(a.sim_get_state(), b.sim_get_state()):
         assert torch.equal(x, y)
+
+
+def test_maximum_sizes_match_oracle():
+    """The library's capacities at once: 7 fingers (29 links, every bit of a
+    warp's link mask but three), 32 sensor pads (distal and middle links split
+    in axial halves, three proximal links, the palm), the 256-sphere object
+    beside the mug, c_max = 256 contacts, iteration counts 10/20/40 -- one
+    frame against the oracle, on the default shape and on the narrowest and
+    widest groups."""
+    import dataclasses
+    n, frames, F = 45, 16, 7
+    base = W.make_workload("uneven_mixed", n_envs=n, frames=frames)
+    shapes = [W.l_composite256(), W.mug128()]
+    link, s0, s1 = [], [], []
+    for f in range(F):
+        for j in (3, 2):
+            link += [1 + 4 * f + j] * 2
+            s0 += [0.0, 0.5]
+            s1 += [0.5, 1.0]
+    for f in range(3):
+        link.append(1 + 4 * f + 1)
+        s0.append(0.0)
+        s1.append(1.0)
+    link.append(0)
+    s0.append(0.0)
+    s1.append(1.0)
+    assert len(link) == 32
+    root = W.make_hand(F, W._root_radius(shapes, base.scene.link_rad), palm_top=base.scene.palm_half[2])
+    scene = dataclasses.replace(base.scene, shapes=shapes, finger_root=root, pad_link=np.array(link, np.int32),
+                                pad_s0=np.array(s0), pad_s1=np.array(s1))
+    rng = np.random.default_rng(5)
+    wl = dataclasses.replace(base, scene=scene, q_traj=W.joint_trajectory(F, frames, base.sim.frame_dt, base.seed),
+                             shape_id=rng.integers(0, 2, n).astype(np.int32),
+                             iters=rng.choice(np.array([10, 20, 40], np.int32), n).astype(np.int32),
+                             nominal_pose=W.nominal_pose_for(scene, 0))
+    assert scene.n_links == 29 and scene.n_pads == 32 and wl.sim.c_max == 256
+    total = 0
+    for shape in (None, (16, 2), (128, 1)):
+        sim = start(wl, n=n, frames=frames)
+        if shape:
+            sim.sim_set_variant(*shape)
+        sim.sim_step(0, 12)
+        rep = compare_frame(wl, sim, 12)
+        assert_report(rep)
+        total += rep["contacts_or"]
+        sim.close()
+    assert total > 0
