@@ -91,13 +91,53 @@ __device__ __forceinline__ Q4 qconj(Q4 q) { return {q.w, -q.x, -q.y, -q.z}; }
 
 template <int GW>
 struct alignas(16) GroupSm {
+    float4 sph[IH_MAX_SPHERES];    // the substep's sphere centres (world rotation, relative to x), radius
+    float4 clc[IH_MAX_SPHERES / kCluster];   // cluster centres (likewise), enclosing radius
+    double term[IH_MAX_PADS];      // a frame's FP64 force term of each pad
     float padacc[IH_MAX_PADS * 3];
     float fbar[IH_MAX_PADS * 3];   // dL/dF_p / (h ns): minus the derivative w.r.t. a final impulse
     float red[2][GW][8];           // partial sums of the group's warps (double-buffered)
+    int cnt[2][GW];                // hits of each warp in a compaction round (double-buffered)
+    int flag[IH_MAX_PADS];         // a frame's contact-state mismatch of each pad
     unsigned short lbeg[32], lend[32];
-    int nc;                        // the substep's contact count (from the enumerating warp)
-    int parity;
+    unsigned short clp[32 * (IH_MAX_SPHERES / kCluster)];   // surviving (link index << 8 | cluster) pairs
+    unsigned char links[32];       // surviving links in order
+    unsigned surv;
 };
+
+// Block-wide pad tables: the pads of each link (in pad order) and their intervals.
+constexpr int kAPadsPerLink = 4;
+struct PadTab {
+    unsigned char cnt[32];
+    unsigned char id[32 * kAPadsPerLink];
+    float s0[IH_MAX_PADS], s1[IH_MAX_PADS];
+};
+
+// Positions of the group's hits in a round of order-preserving compaction:
+// `hit` of this thread; returns its slot (base + hits of the threads before
+// it in the group) and adds the round's hits to `base`.
+template <int GW>
+__device__ __forceinline__ int gcompact(bool hit, int &base, const AGroup<GW> &G, GroupSm<GW> &S, int &parity) {
+    const unsigned bal = __ballot_sync(kFull, hit);
+    int off = base + __popc(bal & ((1u << G.lane) - 1u));
+    if constexpr (GW == 1) {
+        base += __popc(bal);
+    } else {
+        int *c = S.cnt[parity];
+        if (G.lane == 0) c[G.wg] = __popc(bal);
+        G.sync();
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < GW; ++w) {
+            const int k = c[w];
+            if (w < G.wg) off += k;
+            tot += k;
+        }
+        base += tot;
+        parity ^= 1;
+    }
+    return off;
+}
 
 // Sum of 6 values over the group's threads, every thread receiving the sums:
 // within each warp by shuffles, then the warps' partials in warp order.
@@ -186,8 +226,13 @@ __device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y)
 // compiled arithmetic, so a recorded tape is bit for bit the forward's.
 template <int GW, int PL>
 __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4 *L0,
-                                        const float4 *L1, const SlotPtr &sp, GroupSm<GW> &S, const AGroup<GW> &G,
-                                        int &parity, int &st, const bool TAPE, const bool PADS) {
+                                        const float4 *L1, const SlotPtr &sp, GroupSm<GW> &S, const PadTab &PT,
+                                        const AGroup<GW> &G, int &parity, int &st, int tape_flag,
+                                        int pads_flag) {
+    // the flags are run-time values (the callers combine them with a.zero):
+    // one compiled body serves the cost pass, the recomputation and the tape,
+    // so a recorded tape is bit for bit the forward's
+    const bool TAPE = tape_flag != 0, PADS = pads_flag != 0;
     constexpr int T = AGroup<GW>::T;
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
@@ -200,84 +245,105 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
     const S6 Wi = world_inv_inertia(R, E.Jb, E.inv_m);
     const int lane = G.lane;
 
-    // contact enumeration, by the group's first warp: surviving links in order;
-    // per link the clusters within reach, then their spheres in order (the
-    // step's order: link, then sphere)
-    if (G.wg == 0) {
-    const bool keep = lane < Lk && link_reaches(sc, cfg, L0, lane, b.x, E.bound);
-    const unsigned surv = __ballot_sync(kFull, keep);
-    S.lbeg[lane] = 0;
-    S.lend[lane] = 0;
-    __syncwarp();
-    int nc = 0;
-    const unsigned below = (1u << lane) - 1u;
+    // contact enumeration by the whole group, in the step's order (link, then
+    // sphere): sphere and cluster centres to world, the link cull, the (link,
+    // cluster) cull by the clusters' enclosing spheres, then the spheres of the
+    // surviving pairs, one test per thread per round, compacted in order
+    const int gt = G.gt;
     const int ncl = (E.NS + kCluster - 1) / kCluster;
-    V3 clw = mk(0, 0, 0);   // this lane's cluster centre (world, relative to x) and radius
-    float clr = 0.0f;
-    if (lane < ncl) {
-        const float4 cl = __ldg(sc.clusters + E.cfirst + lane);
-        clw = mmul(R, xyz(cl));
-        clr = cl.w;
+    for (int j = gt; j < E.NS; j += T) {
+        const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
+        const V3 cr = mmul(R, xyz(s4));
+        S.sph[j] = make_float4(cr.x, cr.y, cr.z, s4.w);
     }
-    for (unsigned ms = surv; ms; ms &= ms - 1u) {
-        const int l = __ffs(ms) - 1;
-        const int first = nc;
-        const float4 A0 = __ldg(L0 + l * kLinkStride);
-        const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
-        const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
-        const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-        const unsigned cm = __ballot_sync(kFull, lane < ncl && link_reaches(sc, cfg, L0, l, b.x + clw, clr));
-        const int nsc = __popc(cm);
-        // surviving clusters, four to a round of 32 lanes (eight spheres each)
-        for (int c0 = 0; c0 < nsc; c0 += 4) {
-            int cc = -1;
-            {   // the (c0 + lane / 8)-th set bit of cm
-                unsigned mm = cm;
-                for (int q = 0; q < c0 + (lane >> 3) && mm; ++q) mm &= mm - 1u;
-                if (mm && c0 + (lane >> 3) < nsc) cc = __ffs(mm) - 1;
-            }
-            const int j = cc >= 0 ? cc * kCluster + (lane & 7) : E.NS;
-            bool hit = false;
-            Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
-            V3 r = mk(0, 0, 0);
-            if (j < E.NS) {
-                const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
-                const V3 cr = mmul(R, xyz(s4));
-                if (l == 0) hh = hit_box(b.x + cr, s4.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
-                else hh = hit_capsule((b.x - xyz(A0)) + cr, s4.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+    for (int k = gt; k < ncl; k += T) {
+        const float4 cl = __ldg(sc.clusters + E.cfirst + k);
+        const V3 cr = mmul(R, xyz(cl));
+        S.clc[k] = make_float4(cr.x, cr.y, cr.z, cl.w);
+    }
+    if (G.wg == 0) {
+        const bool keep = lane < Lk && link_reaches(sc, cfg, L0, lane, b.x, E.bound);
+        const unsigned surv = __ballot_sync(kFull, keep);
+        if (keep) S.links[__popc(surv & ((1u << lane) - 1u))] = (unsigned char)lane;
+        if (lane == 0) S.surv = surv;
+    }
+    for (int l = gt; l < 32; l += T) {
+        S.lbeg[l] = 0;
+        S.lend[l] = 0;
+    }
+    G.sync();
+    const int ncp = __popc(S.surv) * ncl;
+    int nclp = 0;
+    for (int p0 = 0; p0 < ncp; p0 += T) {
+        const int p = p0 + gt;
+        bool keep = false;
+        int li = 0, k = 0;
+        if (p < ncp) {
+            li = p / ncl;
+            k = p - li * ncl;
+            const float4 cc = S.clc[k];
+            keep = link_reaches(sc, cfg, L0, S.links[li], b.x + xyz(cc), cc.w);
+        }
+        const int off = gcompact<GW>(keep, nclp, G, S, parity);
+        if (keep) S.clp[off] = (unsigned short)((li << 8) | k);
+    }
+    G.sync();
+    const int npairs = nclp * kCluster;
+    int nc = 0;
+    for (int p0 = 0; p0 < npairs; p0 += T) {
+        const int p = p0 + gt;
+        bool hit = false;
+        Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
+        V3 r = mk(0, 0, 0);
+        int l = 0, j = 0;
+        if (p < npairs) {
+            const int e = S.clp[p / kCluster];
+            j = (e & 0xff) * kCluster + (p % kCluster);
+            l = S.links[e >> 8];
+            if (j < E.NS) {   // (j >= NS: padding of the shape's last cluster)
+                const float4 s4 = S.sph[j];
+                const V3 cr = xyz(s4);
+                const float4 A0 = __ldg(L0 + l * kLinkStride);
+                const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
+                const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+                if (l == 0) {
+                    hh = hit_box(b.x + cr, s4.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                } else {
+                    const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
+                    hh = hit_capsule((b.x - xyz(A0)) + cr, s4.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+                }
                 r = cr - hh.n * s4.w;
                 hit = hh.gap < cfg.margin;
             }
-            const unsigned bal = __ballot_sync(kFull, hit);
-            const int idx = nc + __popc(bal & below);
-            if (hit && idx < cap) {
-                int pad = -1;
-                for (int p = 0; p < P; ++p) {   // first pad of the link whose interval holds t
-                    if (__ldg(sc.pad_link + p) != l) continue;
-                    if (l == 0) { pad = p; break; }
-                    const float s0 = __ldg(sc.pad_s0 + p), s1 = __ldg(sc.pad_s1 + p);
-                    if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = p; break; }
-                }
-                float4 *rc = sp.rec + 4 * idx;
-                rc[0] = make_float4(r.x, r.y, r.z, hh.gap);
-                rc[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, 0.0f);
-                rc[3] = make_float4(hh.t, __int_as_float(l | ((pad & 0xff) << 8)), __int_as_float(j), 0.0f);
+        }
+        const int idx = gcompact<GW>(hit, nc, G, S, parity);
+        if (hit && idx < cap) {
+            int pad = -1;   // the first pad of the link whose interval holds t
+            const int npl = PT.cnt[l];
+            for (int k = 0; k < npl; ++k) {
+                const int pp = PT.id[l * kAPadsPerLink + k];
+                if (l == 0) { pad = pp; break; }
+                const float s0 = PT.s0[pp], s1 = PT.s1[pp];
+                if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
             }
-            nc += __popc(bal);
-        }
-        if (lane == 0) {
-            S.lbeg[l] = (unsigned short)first;
-            S.lend[l] = (unsigned short)nc;
+            float4 *rc = sp.rec + 4 * idx;
+            rc[0] = make_float4(r.x, r.y, r.z, hh.gap);
+            rc[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, 0.0f);
+            rc[3] = make_float4(hh.t, __int_as_float(l | ((pad & 0xff) << 8)), __int_as_float(j), 0.0f);
         }
     }
-    if (lane == 0) S.nc = nc;
-    }
-    G.sync();
-    int nc = S.nc;
+    G.sync();   // the records are written
     if (nc > cap) {   // more contacts than the per-env capacity: as the step, no contacts
         st |= IH_ENV_OVERFLOW;
         nc = 0;
     }
+    // each link's contact range (the contacts are in link order)
+    for (int ci = gt; ci < nc; ci += T) {
+        const int l = rec_link(sp.rec[4 * ci + 3]);
+        if (ci == 0 || rec_link(sp.rec[4 * (ci - 1) + 3]) != l) S.lbeg[l] = (unsigned short)ci;
+        if (ci == nc - 1 || rec_link(sp.rec[4 * (ci + 1) + 3]) != l) S.lend[l] = (unsigned short)(ci + 1);
+    }
+    G.sync();
 
     // contact setup, by the thread that owns the contact from here on; the
     // constants stay in its registers for the iterations
@@ -452,8 +518,10 @@ __device__ __forceinline__ void outer_add(float (&M)[9], V3 a, V3 b, float s) {
 // been recomputed with a tape; nc contacts). On entry `ad` holds the
 // derivatives w.r.t. the substep's end state, on return those w.r.t. b.
 // invm_b (lane-uniform) and mu_b (per lane) accumulate d/d(1/m) and d/dmu.
+// Not inlined: both tape modes then run the same compiled reverse, so their
+// gradients agree bit for bit.
 template <int GW, int PL>
-__device__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const float4 *L0, const float4 *L1,
+__device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const float4 *L0, const float4 *L1,
                             int nc, const SlotPtr &sp, GroupSm<GW> &S, const AGroup<GW> &G, int &parity, Adj &ad,
                             float &invm_b, float &mu_b) {
     constexpr int T = AGroup<GW>::T;
@@ -761,9 +829,21 @@ template <int GW, int PL>
 __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     constexpr int T = AGroup<GW>::T, GPB = kAW / GW;
     __shared__ GroupSm<GW> sm[GPB];
+    __shared__ PadTab PT;
     const AGroup<GW> G;
     const int lane = G.gt;   // the group's thread (0 .. 32 GW - 1)
     const int slot = blockIdx.x * GPB + G.gid;
+    if (threadIdx.x < 32) {   // the pads of each link, in pad order
+        int c = 0;
+        for (int p = 0; p < a.sc.n_pads && c < kAPadsPerLink; ++p)
+            if (__ldg(a.sc.pad_link + p) == (int)threadIdx.x) PT.id[threadIdx.x * kAPadsPerLink + c++] = (unsigned char)p;
+        PT.cnt[threadIdx.x] = (unsigned char)c;
+    }
+    for (int p = threadIdx.x; p < a.sc.n_pads; p += kABlock) {
+        PT.s0[p] = __ldg(a.sc.pad_s0 + p);
+        PT.s1[p] = __ldg(a.sc.pad_s1 + p);
+    }
+    __syncthreads();
     if (slot >= a.n) return;   // whole groups only
     GroupSm<GW> &S = sm[G.gid];
     int parity = 0;   // the group's reduction buffer
@@ -832,33 +912,40 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 const int blk = (f - f_last) * ns + s;
                 if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 if (seg_tape && !a.forward_only) {   // the last segment's tape, recorded on the way
-                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, G, parity, st, true, true);
+                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, PT, G, parity, st, 1 | a.zero, 1 | a.zero);
                     if (lane == 0) sp.ncs[blk] = nc;
                     continue;
                 }
             }
-            fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, G, parity, st, false, true);
+            fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero);
         }
         if (f >= f_last)
             for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
         if (!all_finite(b.x, b.q, b.v, b.w)) st |= IH_ENV_NONFINITE;
         else if (dot(b.x, b.x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
-        if (lane == 0) {   // frame cost in FP64, in pad order, as the scored step
+        {   // frame cost in FP64, as the scored step: each pad's terms in parallel, summed in pad order
             const float *o = a.obs + (size_t)f * P * 3;
             const double tau = (double)cfg.tau, tau2 = __dmul_rn(tau, tau), wf = (double)cfg.w_force;
-            double cf = 0.0;
-            for (int p = 0; p < P; ++p) {
+            for (int p = lane; p < P; p += T) {
                 const double fx = S.padacc[3 * p] * inv_ns, fy = S.padacc[3 * p + 1] * inv_ns,
                              fz = S.padacc[3 * p + 2] * inv_ns;
                 const double ox = o[3 * p], oy = o[3 * p + 1], oz = o[3 * p + 2];
                 const double dx = __dsub_rn(fx, ox), dy = __dsub_rn(fy, oy), dz = __dsub_rn(fz, oz);
                 const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                cf = __dadd_rn(cf, __dmul_rn(wf, d2));
+                S.term[p] = __dmul_rn(wf, d2);
                 const double n2 = __dadd_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)), __dmul_rn(fz, fz));
                 const double no = __dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz));
-                if ((n2 > tau2) != (no > tau2)) cf = __dadd_rn(cf, (double)cfg.w_contact);
+                S.flag[p] = (n2 > tau2) != (no > tau2);
             }
-            cost = __dadd_rn(cost, cf);
+            G.sync();
+            if (lane == 0) {
+                double cf = 0.0;
+                for (int p = 0; p < P; ++p) {
+                    cf = __dadd_rn(cf, S.term[p]);
+                    if (S.flag[p]) cf = __dadd_rn(cf, (double)cfg.w_contact);
+                }
+                cost = __dadd_rn(cost, cf);
+            }
         }
         G.sync();
     }
@@ -895,10 +982,10 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
                 if (seg_tape) {
-                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, G, parity, st, true, true);
+                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, PT, G, parity, st, 1 | a.zero, 1 | a.zero);
                     if (lane == 0) sp.ncs[blk] = nc;
                 } else {
-                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, G, parity, st, false, true);
+                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero);
                 }
             }
             for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
@@ -921,7 +1008,7 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 } else {   // re-run the substep once more, recording its tape
                     Body bt = bs;
                     int st2 = 0;
-                    const int nc = fwd_substep<GW, PL>(a, E, bt, L0, L1, sp, S, G, parity, st2, true, false);
+                    const int nc = fwd_substep<GW, PL>(a, E, bt, L0, L1, sp, S, PT, G, parity, st2, 1 | a.zero, a.zero);
                     rev_substep<GW, PL>(a, E, bs, L0, L1, nc, sp, S, G, parity, ad, invm_b, mu_b);
                 }
             }

@@ -1095,7 +1095,7 @@ AdjArgs adjoint_args(ih_sim *s, int32_t frame0, int32_t horizon, int K, const fl
     a.status = s->status; a.obs = obs; a.beta_s = beta; a.width = width;
     a.cost = nullptr; a.grad = nullptr; a.grad_quat = nullptr;
     a.scratch = s->adj_scratch; a.stride = 0; a.iters_max = 0;
-    a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr; a.seg_tape = 0;
+    a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr; a.seg_tape = 0; a.zero = 0;
     return a;
 }
 }  // namespace

@@ -410,6 +410,8 @@ struct AdjArgs {
     int iters_max;
     int forward_only;         // 1: cost (and end state) only, no reverse sweep
     int seg_tape;             // 1: tape every substep of a segment (else re-run each substep to tape it)
+    int zero;                 // always 0: combined with the forward substep's flags so that they are
+                              // run-time values and the substep is compiled once for every pass
     float4 *out_pose, *out_vel;   // [n][2] end state of each slot, or null
 };
 
