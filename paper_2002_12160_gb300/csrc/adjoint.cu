@@ -436,11 +436,18 @@ __device__ __forceinline__ float bias_slope(const DevConfig &cfg, float gap) {
     return (cfg.beta * z / cfg.h > -cfg.vmax) ? cfg.beta / cfg.h : 0.0f;
 }
 
-__device__ __forceinline__ float sigmoid(float x) { return 1.0f / (1.0f + expf(-x)); }
+// The reverse sweep's smoothing functions use the hardware's approximate
+// exponential, reciprocal and reciprocal square root (a few ulp each): they
+// sit at the head of every reverse iteration's dependent chain, and their
+// error is far inside the gradient's tolerance against the FP64 adjoint.
+__device__ __forceinline__ float sigmoid(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
 // Reverse of the smoothed radial clamp out = z smin(|z|, L) / |z| for the
 // incoming derivative g: returns dL/dz and dL/dL. At z = 0 exactly the
-// derivative of the exact clamp inside the disk (identity) is used.
+// derivative of the exact clamp inside the disk (identity) is used. With
+// Q = sqrt((a - L)^2 + (w L)^2), smin(a, L) = (a + L - Q) / 2 is evaluated as
+// L (4a - w^2 L) / (2 (a + L + Q)), the same value without the cancellation
+// of a + L - Q when the clamp does not bind (a << L).
 __device__ __forceinline__ void disk_bwd(V3 z, float L, V3 g, float w, V3 &zb, float &Lb) {
     const float a2 = dot(z, z);
     if (!(a2 > 0.0f)) {
@@ -448,15 +455,19 @@ __device__ __forceinline__ void disk_bwd(V3 z, float L, V3 g, float w, V3 &zb, f
         Lb = 0.0f;
         return;
     }
-    const float a = sqrtf(a2);
+    const float ia = rsqrtf(a2);
+    const float a = a2 * ia;
     const float dl = a - L;
-    const float Q = sqrtf(dl * dl + (w * L) * (w * L));
-    const float phi = 0.5f * (a + L - Q);
-    const float pa = 0.5f * (1.0f - dl / Q);
-    const float pb = 0.5f * (1.0f + (dl - w * w * L) / Q);
-    const V3 zh = z * (1.0f / a);
+    const float wL = w * L;
+    const float Q2 = fmaf(dl, dl, wL * wL);
+    const float iQ = rsqrtf(Q2);
+    const float Q = Q2 * iQ;
+    const float phi = __fdividef(L * fmaf(-w, wL, 4.0f * a), 2.0f * (a + L + Q));
+    const float pa = 0.5f * (1.0f - dl * iQ);
+    const float pb = 0.5f * (1.0f + (dl - w * wL) * iQ);
+    const V3 zh = z * ia;
     const float s = dot(zh, g);
-    const float ra = phi / a;
+    const float ra = phi * ia;
     zb = g * ra + zh * (s * (pa - ra));
     Lb = s * pb;
 }
