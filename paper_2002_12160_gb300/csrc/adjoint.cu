@@ -225,14 +225,20 @@ __device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y)
 // as arguments: every pass (cost, recomputation, tape) then runs the same
 // compiled arithmetic, so a recorded tape is bit for bit the forward's.
 template <int GW, int PL>
-__device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b, const float4 *L0,
-                                        const float4 *L1, const SlotPtr &sp, GroupSm<GW> &S, const PadTab &PT,
-                                        const AGroup<GW> &G, int &parity, int &st, int tape_flag,
+__device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b, const float4 *L0,
+                                        const float4 *L1, const SlotPtr &sp_, GroupSm<GW> &S, const PadTab &PT,
+                                        const AGroup<GW> &G_, int &parity_, int &st_, int tape_flag,
                                         int pads_flag) {
     // the flags are run-time values (the callers combine them with a.zero):
     // one compiled body serves the cost pass, the recomputation and the tape,
     // so a recorded tape is bit for bit the forward's
     const bool TAPE = tape_flag != 0, PADS = pads_flag != 0;
+    // by-value copies of what the loops read: through the references every
+    // store to the tape or to shared memory could alias them and force reloads
+    const Env E = E_;
+    const SlotPtr sp = sp_;
+    const AGroup<GW> G = G_;
+    int parity = parity_, st = st_;
     constexpr int T = AGroup<GW>::T;
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
@@ -424,6 +430,8 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E, Body &b,
         }
     }
     G.sync();
+    parity_ = parity;
+    st_ = st;
     return nc;
 }
 
@@ -532,10 +540,19 @@ __device__ __forceinline__ void outer_add(float (&M)[9], V3 a, V3 b, float s) {
 // Not inlined: both tape modes then run the same compiled reverse, so their
 // gradients agree bit for bit.
 template <int GW, int PL>
-__device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E, const Body &b, const float4 *L0, const float4 *L1,
-                            int nc, const SlotPtr &sp, GroupSm<GW> &S, const AGroup<GW> &G, int &parity, Adj &ad,
-                            float &invm_b, float &mu_b) {
+__device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const Body &b_, const float4 *L0,
+                                        const float4 *L1, int nc, const SlotPtr &sp_, GroupSm<GW> &S,
+                                        const AGroup<GW> &G_, int &parity_, Adj &ad_, float &invm_b_, float &mu_b_) {
     constexpr int T = AGroup<GW>::T;
+    // by-value copies (see fwd_substep), written back on return
+    const Env E = E_;
+    const Body b = b_;
+    const SlotPtr sp = sp_;
+    const AGroup<GW> G = G_;
+    int parity = parity_;
+    Adj ad = ad_;
+    float invm_b = invm_b_, mu_b = mu_b_;
+    const float width = a.width, beta_s = a.beta_s;
     const DevScene &sc = a.sc;
     const DevConfig &cfg = a.cfg;
     const int cap = cfg.c_max, I = E.iters;
@@ -686,10 +703,10 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E, const B
                     nb[k] = nb[k] + lpb * ln;
                     V3 ztb;
                     float Lb;
-                    disk_bwd(zt, L, lpb, a.width, ztb, Lb);
+                    disk_bwd(zt, L, lpb, width, ztb, Lb);
                     lnb += E.mu * Lb;
                     mu_b += ln * Lb;
-                    const float znb = lnb * sigmoid(a.beta_s * zn);
+                    const float znb = lnb * sigmoid(beta_s * zn);
                     float lob = znb;
                     float unb = -znb * ikn;
                     iknb[k] -= znb * un;
@@ -834,6 +851,10 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E, const B
     ad.q = qb;
     ad.v = vpb;
     ad.w = wpb;
+    ad_ = ad;
+    parity_ = parity;
+    invm_b_ = invm_b;
+    mu_b_ = mu_b;
 }
 
 template <int GW, int PL>
