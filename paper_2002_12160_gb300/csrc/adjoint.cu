@@ -240,8 +240,8 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
     const AGroup<GW> G = G_;
     int parity = parity_, st = st_;
     constexpr int T = AGroup<GW>::T;
-    const DevScene &sc = a.sc;
-    const DevConfig &cfg = a.cfg;
+    const DevScene sc = a.sc;   // by value, as E below
+    const DevConfig cfg = a.cfg;
     const int Lk = sc.n_links, P = sc.n_pads, cap = cfg.c_max;
     const float h = cfg.h, inv_h = 1.0f / h, inv_L = 1.0f / sc.link_len;
     const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
@@ -553,8 +553,8 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
     Adj ad = ad_;
     float invm_b = invm_b_, mu_b = mu_b_;
     const float width = a.width, beta_s = a.beta_s;
-    const DevScene &sc = a.sc;
-    const DevConfig &cfg = a.cfg;
+    const DevScene sc = a.sc;   // by value, as E below
+    const DevConfig cfg = a.cfg;
     const int cap = cfg.c_max, I = E.iters;
     const float h = cfg.h, inv_h = 1.0f / h;
     const V3 grav = mk(cfg.gx * h, cfg.gy * h, cfg.gz * h);
