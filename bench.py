@@ -413,10 +413,13 @@ def measure(workload, n_envs, steps, warmup, shape, rank, world, local, n_timing
     return out
 
 
-def measure_adjoint(local, n_envs=1024, horizon=30, checkpoint_every=10, reps=3):
+def measure_adjoint(local, n_envs=1024, horizon=30, checkpoint_every=10, reps=3, windows=4):
     """Forward + adjoint of the horizon cost (sim_adjoint) for every environment
     of the differentiable-tracking workload (box / cylinder, H = 30 frames,
-    checkpoints every 10): CUDA-event time per call after one warm-up call."""
+    checkpoints every 10): CUDA-event time per call after one warm-up call.
+    Then the refinement: `windows` tracking windows each followed by 3
+    gradient steps on its elites, against as many plain windows (CUDA-event
+    time per window, after one refined and one plain warm-up window)."""
     import torch
     from paper_2002_12160_gb300 import tracking, workloads as W
     torch.cuda.set_device(local)
@@ -445,6 +448,26 @@ def measure_adjoint(local, n_envs=1024, horizon=30, checkpoint_every=10, reps=3)
                      "ms_per_call": t, "env_steps_per_s": n_envs * horizon / (t / 1e3),
                      "finite_envs": int(fin.sum().item()),
                      "mean_grad_norm": float(grad[fin].norm(dim=1).mean().item()) if fin.any() else None}
+        tr.close()
+        wl = W.make_workload(name, n_envs=n_envs, frames=10 * (2 * windows + 2))
+        tr = tracking.Tracker(wl, n_envs=n_envs)
+        tr.prepare()
+        assert tr.T == 10
+        tr.window_refined(0)
+        tr.window(1)
+        e2 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for w in range(2, 2 + windows):
+            tr.window_refined(w)
+        e1.record()
+        for w in range(2 + windows, 2 + 2 * windows):
+            tr.window(w)
+        e2.record()
+        torch.cuda.synchronize()
+        ref_ms, plain_ms = e0.elapsed_time(e1) / windows, e1.elapsed_time(e2) / windows
+        out[name]["refined_window"] = {"steps": 3, "elites": int(wl.opt.elite_frac * n_envs), "ms": ref_ms,
+                                       "plain_window_ms": plain_ms, "ratio": ref_ms / plain_ms}
         tr.close()
     torch.cuda.empty_cache()
     return out

@@ -523,6 +523,18 @@ ih_status sim_adjoint(ih_sim *sim, int32_t frame0, int32_t horizon, int32_t chec
  * library's checkpointing. */
 ih_status sim_set_adjoint_memory(ih_sim *sim, uint64_t bytes);
 
+/* The adjoint kernel's shape for sim_adjoint and sim_refine_elites: warps
+ * per environment and contacts per thread held in registers over the Jacobi
+ * iterations and their reverse; a substep's contacts beyond those (up to
+ * c_max) run from the environment's scratch memory, in the same per-thread
+ * order. Supported: (4, 1), (1, 1), (1, 2); (0, 0) restores the automatic
+ * choice: (4, 1) while the environments are at most two per SM, else (1, 1)
+ * when no shape has more than 32 spheres and (1, 2) otherwise.
+ * Results of different shapes agree up to FP32 summation order.
+ * IH_ERR_ARG for another pair. Not a passage of the paper: a tuning choice of
+ * this library. */
+ih_status sim_set_adjoint_variant(ih_sim *sim, int32_t warps_per_env, int32_t contacts_per_thread);
+
 /* Snapshot every environment's state (pose, velocity, parameters) into the
  * handle: the start of a tracking window, for sim_refine_elites. */
 ih_status sim_mark_window(ih_sim *sim);

@@ -162,13 +162,15 @@ __device__ __forceinline__ void gsum6(float (&v)[6], const AGroup<GW> &G, GroupS
 }
 
 // Per-slot scratch layout in floats (every part starts on a float4 boundary):
-// checkpoints, a segment's substep start states and frame forces, the final
-// impulses of an untaped pass, the contact count of every taped substep, then
-// nblk tape blocks of (contact records, impulse after each iteration,
-// iteration sums): one block per substep of a segment when the whole segment
-// is taped, else a single block re-filled substep by substep.
+// checkpoints, a segment's substep start states and frame forces, the
+// impulses of a pass (final ones for the pad sums; the running ones of the
+// contacts past the register slots), the reverse state of the contacts past
+// the register slots, the contact count of every taped substep, then nblk tape
+// blocks of (contact records, impulse after each iteration, iteration sums):
+// one block per substep of a segment when the whole segment is taped, else a
+// single block re-filled substep by substep.
 struct SlotLayout {
-    size_t ck, sg, sf, lamf, ncs, tape, blk_rec, blk_lamh, blk_sh, blk_stride, total;
+    size_t ck, sg, sf, lamf, adj, ncs, tape, blk_rec, blk_lamh, blk_sh, blk_stride, total;
 };
 __host__ __device__ inline size_t round4(size_t x) { return (x + 3) & ~size_t(3); }
 __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, int cap, int iters_max, int nblk) {
@@ -178,7 +180,8 @@ __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, i
     L.ck = o;   o += round4(nck * 16);                        // checkpoint states
     L.sg = o;   o += round4((size_t)K * ns * 16);             // substep start states of a segment
     L.sf = o;   o += round4((size_t)K * P * 3);               // pad forces of a segment's frames
-    L.lamf = o; o += round4((size_t)cap * 4);                 // final impulses of a pass
+    L.lamf = o; o += round4((size_t)cap * 4);                 // impulses of a pass
+    L.adj = o;  o += round4((size_t)cap * 16);                // reverse state of the contacts in memory
     L.ncs = o;  o += round4((size_t)K * ns);                  // contacts of each taped substep (int)
     L.blk_rec = 0;
     L.blk_lamh = round4((size_t)cap * 16);                                   // contact records
@@ -191,6 +194,7 @@ __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, i
 
 struct SlotPtr {
     float4 *ck, *sg, *rec, *lamh, *lamf;
+    float4 *adjs;   // per contact past the register slots: (lb, 1/k_n bar), (nb, 1/k_t bar), (rb, -), (cb, -)
     float *sf, *sh;
     int *ncs;
     float *tape;
@@ -372,6 +376,17 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
             cr_[k] = xyz(r0); cn_[k] = xyz(r1); cc_[k] = cs.cc; ikn_[k] = cs.ikn; ikt_[k] = cs.ikt;
         }
     }
+    // contacts past the register slots (thread gt's slots PL, PL + 1, ... in
+    // the same order): constants in their records, impulse in sp.lamf
+    for (int ci = G.gt + T * PL; ci < nc; ci += T) {
+        float4 *rc = sp.rec + 4 * ci;
+        const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
+        const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, rec_link(r3), Wi, trW, E.inv_m, cfg, L0, L1, b.x,
+                                        inv_h);
+        rc[1] = make_float4(r1.x, r1.y, r1.z, cs.ikn);
+        rc[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikt);
+        sp.lamf[ci] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
 
     // Jacobi projected-impulse iterations
     V3 vv = v_pred, ww = w_pred;
@@ -389,6 +404,17 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
                     acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
                     if (TAPE) sp.lamh[(size_t)it * cap + ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
                 }
+            }
+            for (int ci = G.gt + T * PL; ci < nc; ci += T) {
+                const float4 *rc = sp.rec + 4 * ci;
+                const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
+                const V3 lam = update_contact(xyz(sp.lamf[ci]), xyz(r0), xyz(r1), xyz(r2), r1.w, r2.w, vv, ww, E.mu,
+                                              inv_nc);
+                sp.lamf[ci] = make_float4(lam.x, lam.y, lam.z, 0.0f);
+                const V3 tq = cross(xyz(r0), lam);
+                acc[0] += lam.x; acc[1] += lam.y; acc[2] += lam.z;
+                acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                if (TAPE) sp.lamh[(size_t)it * cap + ci] = make_float4(lam.x, lam.y, lam.z, 0.0f);
             }
             gsum6<GW>(acc, G, S, parity);
             if (TAPE && G.gt == 0)
@@ -408,7 +434,8 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
         b.q = qnorm(qmul({cs, b.w.x * kq, b.w.y * kq, b.w.z * kq}, b.q));
     }
     if (PADS) {
-        // pad forces -lambda / h, each pad summing the contacts of its link in order
+        // pad forces -lambda / h, each pad summing the contacts of its link in
+        // order (the contacts past the register slots have theirs in sp.lamf)
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
             const int ci = G.gt + T * k;
@@ -533,6 +560,108 @@ __device__ __forceinline__ void outer_add(float (&M)[9], V3 a, V3 b, float s) {
         for (int j = 0; j < 3; ++j) M[3 * i + j] += av[i] * bv[j];
 }
 
+// Reverse of one contact's setup and narrowphase (its record rc: r, gap; n,
+// 1/k_n; c, 1/k_t; link, sphere) given the derivatives w.r.t. its constants
+// nb, rb, cb, iknb, iktb: the thread's parts of d/dx, d/d(1/m), d/dW and d/dR
+// accumulate.
+__device__ __forceinline__ void contact_setup_bwd(const float4 *rc, V3 nb, V3 rb, V3 cb, float iknb, float iktb,
+                                                  const S6 &Wi, float trW, const M3 &R, V3 x, int sfirst,
+                                                  const DevScene &sc, const DevConfig &cfg, const float4 *L0,
+                                                  const float4 *L1, float inv_h, float (&Wbar)[9], float (&Rbar)[9],
+                                                  V3 &xb_l, float &invm_l) {
+    const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2], r3 = rc[3];
+    const V3 r = xyz(r0), n = xyz(r1);
+    const float gap = r0.w, ikn = r1.w, ikt = r2.w;
+    const int l = rec_link(r3), j = __float_as_int(r3.z);
+    // 1/k_n and 1/k_t = 2 / (tr K - k_n)
+    float knb = -iknb * ikn * ikn;
+    const float Db = -iktb * ikt * ikt * 0.5f;
+    const float trKb = Db;
+    knb -= Db;
+    // k_n = 1/m + (r x n) . W (r x n)
+    const V3 rn = cross(r, n);
+    const V3 rnb = smul(Wi, rn) * (2.0f * knb);
+    invm_l += knb + 3.0f * trKb;
+    outer_add(Wbar, rn, rn, knb);
+    rb = rb + cross(n, rnb);
+    nb = nb + cross(rnb, r);
+    // tr K = 3/m + |r|^2 tr W - r . W r
+    rb = rb + (r * (2.0f * trW) - smul(Wi, r) * 2.0f) * trKb;
+    const float rr = dot(r, r) * trKb;
+    Wbar[0] += rr; Wbar[4] += rr; Wbar[8] += rr;
+    outer_add(Wbar, r, r, -trKb);
+    // c = v_link - n b(gap)
+    const float bias = contact_bias(cfg, gap);
+    const float gb = -dot(n, cb) * bias_slope(cfg, gap);
+    nb = nb - cb * bias;
+    if (l != 0) {   // v_link = (T_end T_start^-1 p - p) / h, p = x + r
+        const float4 Aq = __ldg(L0 + l * kLinkStride + 2), Bq = __ldg(L1 + l * kLinkStride + 2);
+        const Q4 qa = {Aq.x, Aq.y, Aq.z, Aq.w}, qe = {Bq.x, Bq.y, Bq.z, Bq.w};
+        const V3 yb = (qrot(qa, qrot_inv(qe, cb)) - cb) * inv_h;
+        xb_l = xb_l + yb;
+        rb = rb + yb;
+    }
+    // r = R s_j - n r_j, gap and n from the sphere centre x + R s_j
+    const float4 s4 = __ldg(sc.spheres + sfirst + j);
+    nb = nb - rb * s4.w;
+    const V3 cr = mmul(R, xyz(s4));
+    const V3 hb = hit_bwd(sc, l, x, cr, L0, gb, nb);
+    xb_l = xb_l + hb;
+    outer_add(Rbar, rb + hb, xyz(s4), 1.0f);
+}
+
+// Reverse of one contact's update in a Jacobi iteration (update_contact with
+// constants r, n, c, 1/k_n, 1/k_t against the velocities Vi, Wv, from its
+// impulse l0 before the iteration): lb holds the derivative w.r.t. its impulse
+// after the iteration and leaves with the one before it; nb, rb, cb, iknb,
+// iktb, mu_b and the group's velocity and moment sums acc accumulate.
+__device__ __forceinline__ void contact_update_bwd(V3 r, V3 n, V3 cc, float ikn, float ikt, V3 l0, V3 Vi, V3 Wv,
+                                                   float mu, float inv_nc, float width, float beta_s, V3 &lb,
+                                                   V3 &nb, V3 &rb, V3 &cb, float &iknb, float &iktb, float &mu_b,
+                                                   float (&acc)[6]) {
+    const V3 u = Vi + cross(Wv, r) - cc;
+    const float un = dot(u, n), lo = dot(l0, n);
+    const float zn = lo - un * ikn;
+    const float ln = fmaxf(zn, 0.0f);
+    const V3 ut = u - n * un;
+    const V3 zt = (l0 - n * lo) - ut * ikt;
+    const float L = mu * ln;
+    // lambda' = lambda + (n ln + lt - lambda) / n_c
+    const V3 lpb = lb * inv_nc;
+    lb = lb * (1.0f - inv_nc);
+    float lnb = dot(n, lpb);
+    nb = nb + lpb * ln;
+    V3 ztb;
+    float Lb;
+    disk_bwd(zt, L, lpb, width, ztb, Lb);
+    lnb += mu * Lb;
+    mu_b += ln * Lb;
+    const float znb = lnb * sigmoid(beta_s * zn);
+    float lob = znb;
+    float unb = -znb * ikn;
+    iknb -= znb * un;
+    // zt = (l0 - n lo) - (u - n un) ikt
+    const float nzt = dot(n, ztb);
+    lb = lb + ztb;
+    nb = nb - ztb * lo;
+    lob -= nzt;
+    V3 ub = ztb * (-ikt);
+    nb = nb + ztb * (ikt * un);
+    unb += ikt * nzt;
+    iktb -= dot(ut, ztb);
+    // lo = l0 . n, un = u . n
+    lb = lb + n * lob;
+    nb = nb + l0 * lob;
+    ub = ub + n * unb;
+    nb = nb + u * unb;
+    // u = V + W x r - c
+    const V3 rxu = cross(r, ub);
+    acc[0] += ub.x; acc[1] += ub.y; acc[2] += ub.z;
+    acc[3] += rxu.x; acc[4] += rxu.y; acc[5] += rxu.z;
+    rb = rb + cross(ub, Wv);
+    cb = cb - ub;
+}
+
 // Reverse sweep of one substep from start state b (whose forward has just
 // been recomputed with a tape; nc contacts). On entry `ad` holds the
 // derivatives w.r.t. the substep's end state, on return those w.r.t. b.
@@ -644,6 +773,14 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
                 if (pad < sc.n_pads) lb[k] = mk(-S.fbar[3 * pad], -S.fbar[3 * pad + 1], -S.fbar[3 * pad + 2]);
             }
         }
+        // contacts past the register slots: their reverse state in sp.adjs
+        for (int ci = G.gt + T * PL; ci < nc; ci += T) {
+            const int pad = rec_pad(sp.rec[4 * ci + 3]);
+            float4 *A = sp.adjs + 4 * ci;
+            A[0] = (pad < sc.n_pads) ? make_float4(-S.fbar[3 * pad], -S.fbar[3 * pad + 1], -S.fbar[3 * pad + 2], 0.0f)
+                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            A[1] = A[2] = A[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
         float4 sc_lo, sc_hi, sp_lo, sp_hi;
         sums_at(I - 1, sc_lo, sc_hi);
         sums_at(I - 2, sp_lo, sp_hi);
@@ -686,51 +823,25 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
             for (int k = 0; k < PL; ++k) {
                 const int ci = G.gt + T * k;
                 if (ci < nc) {
-                    const V3 r = r_[k], n = n_[k], cc = c_[k];
-                    const float ikn = ikn_[k], ikt = ikt_[k];
-                    const V3 l0 = l0_[k];
-                    const V3 u = Vi + cross(Wv, r) - cc;
-                    const float un = dot(u, n), lo = dot(l0, n);
-                    const float zn = lo - un * ikn;
-                    const float ln = fmaxf(zn, 0.0f);
-                    const V3 ut = u - n * un;
-                    const V3 zt = (l0 - n * lo) - ut * ikt;
-                    const float L = E.mu * ln;
-                    // lambda' = lambda + (n ln + lt - lambda) / n_c
-                    const V3 lpb = lb[k] * inv_nc;
-                    lb[k] = lb[k] * (1.0f - inv_nc);
-                    float lnb = dot(n, lpb);
-                    nb[k] = nb[k] + lpb * ln;
-                    V3 ztb;
-                    float Lb;
-                    disk_bwd(zt, L, lpb, width, ztb, Lb);
-                    lnb += E.mu * Lb;
-                    mu_b += ln * Lb;
-                    const float znb = lnb * sigmoid(beta_s * zn);
-                    float lob = znb;
-                    float unb = -znb * ikn;
-                    iknb[k] -= znb * un;
-                    // zt = (l0 - n lo) - (u - n un) ikt
-                    const float nzt = dot(n, ztb);
-                    lb[k] = lb[k] + ztb;
-                    nb[k] = nb[k] - ztb * lo;
-                    lob -= nzt;
-                    V3 ub = ztb * (-ikt);
-                    nb[k] = nb[k] + ztb * (ikt * un);
-                    unb += ikt * nzt;
-                    iktb[k] -= dot(ut, ztb);
-                    // lo = l0 . n, un = u . n
-                    lb[k] = lb[k] + n * lob;
-                    nb[k] = nb[k] + l0 * lob;
-                    ub = ub + n * unb;
-                    nb[k] = nb[k] + u * unb;
-                    // u = V + W x r - c
-                    const V3 rxu = cross(r, ub);
-                    acc[0] += ub.x; acc[1] += ub.y; acc[2] += ub.z;
-                    acc[3] += rxu.x; acc[4] += rxu.y; acc[5] += rxu.z;
-                    rb[k] = rb[k] + cross(ub, Wv);
-                    cb[k] = cb[k] - ub;
+                    contact_update_bwd(r_[k], n_[k], c_[k], ikn_[k], ikt_[k], l0_[k], Vi, Wv, E.mu, inv_nc, width,
+                                       beta_s, lb[k], nb[k], rb[k], cb[k], iknb[k], iktb[k], mu_b, acc);
                 }
+            }
+            for (int ci = G.gt + T * PL; ci < nc; ci += T) {   // (a) and (b) of the contacts in memory
+                const float4 *rc = sp.rec + 4 * ci;
+                const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
+                float4 *A = sp.adjs + 4 * ci;
+                const float4 a0 = A[0], a1 = A[1], a2 = A[2], a3 = A[3];
+                const V3 r = xyz(r0);
+                V3 lbk = xyz(a0) + vm + cross(g, r), nbk = xyz(a1), rbk = xyz(a2) + cross(lam_at(it, ci), g),
+                   cbk = xyz(a3);
+                float iknbk = a0.w, iktbk = a1.w;
+                contact_update_bwd(r, xyz(r1), xyz(r2), r1.w, r2.w, lam_at(it - 1, ci), Vi, Wv, E.mu, inv_nc, width,
+                                   beta_s, lbk, nbk, rbk, cbk, iknbk, iktbk, mu_b, acc);
+                A[0] = make_float4(lbk.x, lbk.y, lbk.z, iknbk);
+                A[1] = make_float4(nbk.x, nbk.y, nbk.z, iktbk);
+                A[2] = make_float4(rbk.x, rbk.y, rbk.z, 0.0f);
+                A[3] = make_float4(cbk.x, cbk.y, cbk.z, 0.0f);
             }
             gsum6<GW>(acc, G, S, parity);
             Vb = mk(acc[0], acc[1], acc[2]);
@@ -751,47 +862,15 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
         for (int k = 0; k < PL; ++k) {
             const int ci = G.gt + T * k;
             if (ci < nc) {
-                const float4 *rc = sp.rec + 4 * ci;
-                const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2], r3 = rc[3];
-                const V3 r = xyz(r0), n = xyz(r1);
-                const float gap = r0.w, ikn = r1.w, ikt = r2.w;
-                const int l = rec_link(r3), j = __float_as_int(r3.z);
-                // 1/k_n and 1/k_t = 2 / (tr K - k_n)
-                float knb = -iknb[k] * ikn * ikn;
-                const float Db = -iktb[k] * ikt * ikt * 0.5f;
-                const float trKb = Db;
-                knb -= Db;
-                // k_n = 1/m + (r x n) . W (r x n)
-                const V3 rn = cross(r, n);
-                const V3 rnb = smul(Wi, rn) * (2.0f * knb);
-                invm_l += knb + 3.0f * trKb;
-                outer_add(Wbar, rn, rn, knb);
-                rb[k] = rb[k] + cross(n, rnb);
-                nb[k] = nb[k] + cross(rnb, r);
-                // tr K = 3/m + |r|^2 tr W - r . W r
-                rb[k] = rb[k] + (r * (2.0f * trW) - smul(Wi, r) * 2.0f) * trKb;
-                const float rr = dot(r, r) * trKb;
-                Wbar[0] += rr; Wbar[4] += rr; Wbar[8] += rr;
-                outer_add(Wbar, r, r, -trKb);
-                // c = v_link - n b(gap)
-                const float bias = contact_bias(cfg, gap);
-                const float gb = -dot(n, cb[k]) * bias_slope(cfg, gap);
-                nb[k] = nb[k] - cb[k] * bias;
-                if (l != 0) {   // v_link = (T_end T_start^-1 p - p) / h, p = x + r
-                    const float4 Aq = __ldg(L0 + l * kLinkStride + 2), Bq = __ldg(L1 + l * kLinkStride + 2);
-                    const Q4 qa = {Aq.x, Aq.y, Aq.z, Aq.w}, qe = {Bq.x, Bq.y, Bq.z, Bq.w};
-                    const V3 yb = (qrot(qa, qrot_inv(qe, cb[k])) - cb[k]) * inv_h;
-                    xb_l = xb_l + yb;
-                    rb[k] = rb[k] + yb;
-                }
-                // r = R s_j - n r_j, gap and n from the sphere centre x + R s_j
-                const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
-                nb[k] = nb[k] - rb[k] * s4.w;
-                const V3 cr = mmul(R, xyz(s4));
-                const V3 hb = hit_bwd(sc, l, b.x, cr, L0, gb, nb[k]);
-                xb_l = xb_l + hb;
-                outer_add(Rbar, rb[k] + hb, xyz(s4), 1.0f);
+                contact_setup_bwd(sp.rec + 4 * ci, nb[k], rb[k], cb[k], iknb[k], iktb[k], Wi, trW, R, b.x, E.sfirst, sc,
+                                  cfg, L0, L1, inv_h, Wbar, Rbar, xb_l, invm_l);
             }
+        }
+        for (int ci = G.gt + T * PL; ci < nc; ci += T) {
+            const float4 *A = sp.adjs + 4 * ci;
+            const float4 a0 = A[0], a1 = A[1], a2 = A[2], a3 = A[3];
+            contact_setup_bwd(sp.rec + 4 * ci, xyz(a1), xyz(a2), xyz(a3), a0.w, a1.w, Wi, trW, R, b.x, E.sfirst, sc, cfg,
+                              L0, L1, inv_h, Wbar, Rbar, xb_l, invm_l);
         }
     } else {
         vpb = vpb + Vb;
@@ -897,6 +976,7 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     sp0.sg = reinterpret_cast<float4 *>(base + Ly.sg);
     sp0.sf = base + Ly.sf;
     sp0.lamf = reinterpret_cast<float4 *>(base + Ly.lamf);
+    sp0.adjs = reinterpret_cast<float4 *>(base + Ly.adj);
     sp0.ncs = reinterpret_cast<int *>(base + Ly.ncs);
     sp0.tape = base + Ly.tape;
     sp0.blk_lamh = Ly.blk_lamh;
@@ -1196,26 +1276,30 @@ cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, 
 #ifndef IH_ADJ_GROUPS_PER_SM
 #define IH_ADJ_GROUPS_PER_SM 2
 #endif
-// Few environments (the refined elites, a small batch), at most two per SM --
-// the blocks of ~250 registers a thread that an SM holds: four warps each, so
-// that their contacts' chains run side by side. More: one warp each (no
-// barriers between the warps of an environment) while each thread holds at
-// most four contacts; two warps each beyond that (c_max > 128), where a
-// thread's eight contacts would not fit in its registers.
+bool adjoint_variant_supported(int gw, int pl) {
+    return (gw == 0 && pl == 0) || (gw == 4 && pl == 1) || (gw == 1 && (pl == 1 || pl == 2));
+}
+
+// Automatic shape. Few environments (the refined elites, a small batch), at
+// most two per SM -- the blocks of ~250 registers a thread that an SM holds:
+// four warps each, so that their contacts' chains run side by side, one
+// contact a thread in registers. More: one warp each (no barriers between the
+// warps of an environment) with one contact a thread in registers when no
+// shape has more than 32 spheres (a substep's contacts then rarely exceed a
+// warp: 22 at most for the 27-sphere box), else two (the 64-sphere cylinder
+// reaches ~100); four a thread spilled and ran slower. Contacts beyond the
+// register slots run from scratch memory.
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s) {
+    if (a.gw == 4 && a.pl == 1) return launch_pl<4, 1>(a, s);
+    if (a.gw == 1 && a.pl == 1) return launch_pl<1, 1>(a, s);
+    if (a.gw == 1 && a.pl == 2) return launch_pl<1, 2>(a, s);
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int cap = a.cfg.c_max;
-    if (a.n <= IH_ADJ_GROUPS_PER_SM * sms) {
-        if (cap <= 128) return launch_pl<4, 1>(a, s);
-        return launch_pl<4, 2>(a, s);
-    }
-    if (cap <= 32) return launch_pl<1, 1>(a, s);
-    if (cap <= 64) return launch_pl<1, 2>(a, s);
-    if (cap <= 128) return launch_pl<1, 4>(a, s);
-    return launch_pl<2, 4>(a, s);
+    if (a.n <= IH_ADJ_GROUPS_PER_SM * sms) return launch_pl<4, 1>(a, s);
+    if (a.s_max <= 32) return launch_pl<1, 1>(a, s);
+    return launch_pl<1, 2>(a, s);
 }
 
 }  // namespace ih

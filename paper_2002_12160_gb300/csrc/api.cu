@@ -59,6 +59,7 @@ struct ih_sim {
     size_t adj_floats = 0;
     size_t adj_budget = (size_t)16 << 30;   // bytes of adjoint scratch for whole-segment taping
     bool adj_seg = false;
+    int adj_gw = 0, adj_pl = 0;   // the adjoint kernel's shape (0, 0: automatic)
     int *adj_word = nullptr;
     // gradient refinement: window-start snapshot, trial, best and end states (allocated on first use)
     bool rf_alloc = false, ws_valid = false;
@@ -1096,6 +1097,7 @@ AdjArgs adjoint_args(ih_sim *s, int32_t frame0, int32_t horizon, int K, const fl
     a.cost = nullptr; a.grad = nullptr; a.grad_quat = nullptr;
     a.scratch = s->adj_scratch; a.stride = 0; a.iters_max = 0;
     a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr; a.seg_tape = 0; a.zero = 0;
+    a.gw = s->adj_gw; a.pl = s->adj_pl; a.s_max = s->s_max;
     return a;
 }
 }  // namespace
@@ -1148,6 +1150,15 @@ cudaError_t refine_alloc(ih_sim *s) {
 ih_status sim_set_adjoint_memory(ih_sim *s, uint64_t bytes) {
     if (!s) return IH_ERR_ARG;
     s->adj_budget = (size_t)bytes;
+    return IH_OK;
+}
+
+ih_status sim_set_adjoint_variant(ih_sim *s, int32_t gw, int32_t pl) {
+    if (!s) return IH_ERR_ARG;
+    if (!adjoint_variant_supported(gw, pl))
+        return fail(s, IH_ERR_ARG, "unsupported adjoint shape %d warps x %d contacts", gw, pl);
+    s->adj_gw = gw;
+    s->adj_pl = pl;
     return IH_OK;
 }
 

@@ -412,6 +412,8 @@ struct AdjArgs {
     int seg_tape;             // 1: tape every substep of a segment (else re-run each substep to tape it)
     int zero;                 // always 0: combined with the forward substep's flags so that they are
                               // run-time values and the substep is compiled once for every pass
+    int gw, pl;               // kernel shape: warps per environment, register contacts per thread (0, 0: automatic)
+    int s_max;                // most spheres in one shape of the scene
     float4 *out_pose, *out_vel;   // [n][2] end state of each slot, or null
 };
 
@@ -445,6 +447,7 @@ cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, 
                                  const int *n_window, cudaStream_t s);
 size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max, bool seg_tape);
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
+bool adjoint_variant_supported(int gw, int pl);   // (0, 0) = automatic
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s);
 cudaError_t launch_win_desc(WinDesc *d, WinDesc v, cudaStream_t s);
 // shared-memory opt-in of a shape; blocks_per_sm (may be null) receives its occupancy

@@ -64,8 +64,8 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_stream", "sim_set_commands", "s
            "optimizer_update", "sim_work_counters", "sim_sync", "sim_last_error", "sim_autotune",
            "sim_set_variant", "sim_step_variants", "sim_step_track", "sim_track_window",
            "cost_eval_static", "sim_adjoint", "sim_mark_window", "sim_refine_elites",
-           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_get_warm_cache",
-           "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full", "sim_step_frames_full",
+           "sim_step_frames", "sim_frames_argmin", "sim_set_adjoint_memory", "sim_set_adjoint_variant",
+           "sim_get_warm_cache", "sim_read_observation", "sim_set_hand", "sim_get_hand", "cost_eval_full", "sim_step_frames_full",
            "ih_fp32_peak"]
 
 
@@ -106,6 +106,7 @@ def lib() -> C.CDLL:
             "sim_adjoint": [P, I, I, I, P, P, I, C.c_float, C.c_float, P, P, P],
             "sim_mark_window": [P],
             "sim_set_adjoint_memory": [P, C.c_uint64],
+            "sim_set_adjoint_variant": [P, I, I],
             "sim_step_frames": [P, I, I, P],
             "sim_frames_argmin": [P, P, P],
             "sim_refine_elites": [P, I, I, P, P, I, C.c_float, C.c_float, C.c_float, P, P, P, P, P, P],
@@ -381,6 +382,10 @@ class Sim:
 
     def sim_set_adjoint_memory(self, nbytes: int):
         self._call("sim_set_adjoint_memory", C.c_uint64(nbytes))
+
+    def sim_set_adjoint_variant(self, warps_per_env: int = 0, contacts_per_thread: int = 0):
+        """The adjoint kernel's shape; (0, 0) = automatic."""
+        self._call("sim_set_adjoint_variant", warps_per_env, contacts_per_thread)
 
     def sim_mark_window(self):
         self._call("sim_mark_window")

@@ -7,6 +7,10 @@ tangent, mass and friction, with the same backward-only smoothing. Tolerance:
 1e-3 relative per block (position, rotation, m, mu), with an absolute floor of
 1e-3 of the environment's largest block norm. Environments whose horizon
 passes within 1e-6 m of a contact or pad threshold are excluded and counted.
+Every kernel shape is checked: four warps and one register contact per
+thread, and one warp with one or two -- the cylinder's 60-100 contacts per
+substep then also run the path that keeps the contacts past the register
+slots in scratch memory.
 """
 import numpy as np
 import pytest
@@ -34,39 +38,65 @@ def _setup(n=4, name="tracking_cyl64"):
     gt = O.State(st.pose[:1], st.vel[:1], np.array([wl.theta_gt], np.float64))
     obs, fragile = [], np.zeros(n, bool)
     probe = O.State(st.pose, st.vel, st.theta)
+    _setup.frame_contacts = np.zeros(n)   # most contacts of a frame (summed over its substeps) per env
     for k in range(H):
         f, _ = O.step(osc, sm, gt, wl.q_traj, WARM + k, 1)
         obs.append(f[0])
         _, diag = O.step(osc, sm, probe, wl.q_traj, WARM + k, 1)
         fragile |= (diag[:, 2] < FRAGILE) | (diag[:, 3] < FRAGILE) | (diag[:, 4] < FRAGILE)
+        _setup.frame_contacts = np.maximum(_setup.frame_contacts, diag[:, 0])
     obs = np.asarray(obs, np.float32)
     return wl, sim, st, sc, sm, obs, fragile
 
 
+SHAPES = [(4, 1), (1, 1), (1, 2)]   # (warps per environment, register contacts per thread)
+
+
 def test_adjoint_matches_oracle():
     wl, sim, st, sc, sm, obs, fragile = _setup()
+    # some substep holds more contacts than the one-warp shapes keep in registers
+    substeps = wl.sim.substeps
+    assert _setup.frame_contacts.max() > substeps * 32 * max(pl for gw, pl in SHAPES if gw == 1)
     d = dev()
-    cost, grad, _ = sim.sim_adjoint(WARM, torch.from_numpy(obs).to(d), checkpoint_every=2)
-    cost, grad = cost.cpu().numpy(), grad.cpu().numpy().astype(np.float64)
+    gpu = {}
+    for gw, pl in SHAPES:
+        sim.sim_set_adjoint_variant(gw, pl)
+        cost, grad, _ = sim.sim_adjoint(WARM, torch.from_numpy(obs).to(d), checkpoint_every=2)
+        gpu[gw, pl] = (cost.cpu().numpy(), grad.cpu().numpy().astype(np.float64))
+    sim.sim_set_adjoint_variant(0, 0)
     checked = 0
     for i in range(st.n):
         if fragile[i]:
             continue
         c_or, g_or, _, _, _ = A.horizon(sc, sm, st.pose[i], st.vel[i], st.theta[i], wl.q_traj, WARM, H,
                                         obs.astype(np.float64))
-        assert np.isfinite(cost[i]) and abs(cost[i] - c_or) <= 1e-3 * abs(c_or) + 1e-6, (i, cost[i], c_or)
         floor = 1e-3 * max(np.linalg.norm(g_or[b]) for b in BLOCKS)
-        for b in BLOCKS:
-            err = np.linalg.norm(grad[i, b] - g_or[b])
-            assert err <= 1e-3 * np.linalg.norm(g_or[b]) + floor, (i, b, grad[i, b], g_or[b])
+        for shape, (cost, grad) in gpu.items():
+            assert np.isfinite(cost[i]) and abs(cost[i] - c_or) <= 1e-3 * abs(c_or) + 1e-6, (shape, i, cost[i], c_or)
+            for b in BLOCKS:
+                err = np.linalg.norm(grad[i, b] - g_or[b])
+                assert err <= 1e-3 * np.linalg.norm(g_or[b]) + floor, (shape, i, b, grad[i, b], g_or[b])
         checked += 1
     assert checked >= 3
 
 
-def test_checkpoint_interval_tape_mode_and_subset_do_not_change_results():
+def test_adjoint_shape_arguments():
+    wl = W.make_workload("tracking_cyl64", n_envs=4, frames=4)
+    sim = start(wl, n=4, frames=4)
+    for gw, pl in [(2, 1), (4, 2), (1, 4), (1, 0), (0, 1), (-1, 1)]:
+        with pytest.raises(RuntimeError):
+            sim.sim_set_adjoint_variant(gw, pl)
+    for gw, pl in SHAPES + [(0, 0)]:
+        sim.sim_set_adjoint_variant(gw, pl)
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(0, 0), (1, 1)])
+def test_checkpoint_interval_tape_mode_and_subset_do_not_change_results(shape):
     wl, sim, st, sc, sm, obs, fragile = _setup()
     d = dev()
     o = torch.from_numpy(obs).to(d)
+    sim.sim_set_adjoint_variant(*shape)
     ref_c, ref_g, ref_q = sim.sim_adjoint(WARM, o, checkpoint_every=10, want_quat=True)
     for K in (1, 2, 3):
         c, g, q = sim.sim_adjoint(WARM, o, checkpoint_every=K, want_quat=True)
