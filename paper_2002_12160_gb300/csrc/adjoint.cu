@@ -394,16 +394,17 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
         const float inv_nc = 1.0f / (float)nc;
         for (int it = 0; it < E.iters; ++it) {
             float acc[6] = {0, 0, 0, 0, 0, 0};
+            // every register slot without a branch, so that the slots' chains
+            // interleave: an empty slot (r = c = 0, n = z, 1/k = 0) keeps a zero
+            // impulse and adds zeros
 #pragma unroll
             for (int k = 0; k < PL; ++k) {
                 const int ci = G.gt + T * k;
-                if (ci < nc) {
-                    lam_[k] = update_contact(lam_[k], cr_[k], cn_[k], cc_[k], ikn_[k], ikt_[k], vv, ww, E.mu, inv_nc);
-                    const V3 tq = cross(cr_[k], lam_[k]);
-                    acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
-                    acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
-                    if (TAPE) sp.lamh[(size_t)it * cap + ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
-                }
+                lam_[k] = update_contact(lam_[k], cr_[k], cn_[k], cc_[k], ikn_[k], ikt_[k], vv, ww, E.mu, inv_nc);
+                const V3 tq = cross(cr_[k], lam_[k]);
+                acc[0] += lam_[k].x; acc[1] += lam_[k].y; acc[2] += lam_[k].z;
+                acc[3] += tq.x; acc[4] += tq.y; acc[5] += tq.z;
+                if (TAPE && ci < nc) sp.lamh[(size_t)it * cap + ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
             }
             for (int ci = G.gt + T * PL; ci < nc; ci += T) {
                 const float4 *rc = sp.rec + 4 * ci;
@@ -484,12 +485,9 @@ __device__ __forceinline__ float sigmoid(float x) { return __fdividef(1.0f, 1.0f
 // L (4a - w^2 L) / (2 (a + L + Q)), the same value without the cancellation
 // of a + L - Q when the clamp does not bind (a << L).
 __device__ __forceinline__ void disk_bwd(V3 z, float L, V3 g, float w, V3 &zb, float &Lb) {
-    const float a2 = dot(z, z);
-    if (!(a2 > 0.0f)) {
-        zb = (L > 0.0f) ? g : mk(0, 0, 0);
-        Lb = 0.0f;
-        return;
-    }
+    const float a2z = dot(z, z);
+    const bool at0 = !(a2z > 0.0f);
+    const float a2 = at0 ? 1.0f : a2z;   // (without a branch: the values at z = 0 are selected below)
     const float ia = rsqrtf(a2);
     const float a = a2 * ia;
     const float dl = a - L;
@@ -503,8 +501,8 @@ __device__ __forceinline__ void disk_bwd(V3 z, float L, V3 g, float w, V3 &zb, f
     const V3 zh = z * ia;
     const float s = dot(zh, g);
     const float ra = phi * ia;
-    zb = g * ra + zh * (s * (pa - ra));
-    Lb = s * pb;
+    zb = at0 ? ((L > 0.0f) ? g : mk(0, 0, 0)) : g * ra + zh * (s * (pa - ra));
+    Lb = at0 ? 0.0f : s * pb;
 }
 
 // Reverse of the narrowphase (hit_box / hit_capsule) for the sphere centred
@@ -804,13 +802,13 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
             }
             const V3 g = smul(Wi, Wb);
             const V3 vm = Vb * E.inv_m;
+            // every register slot without a branch (an empty slot has r = l1 = 0
+            // and keeps lb = 0, so its reverse below adds zeros)
 #pragma unroll
             for (int k = 0; k < PL; ++k) {
-                const int ci = G.gt + T * k;
-                if (ci < nc) {
-                    lb[k] = lb[k] + vm + cross(g, r_[k]);
-                    rb[k] = rb[k] + cross(l1_[k], g);
-                }
+                const V3 lbk = lb[k] + vm + cross(g, r_[k]);
+                lb[k] = (G.gt + T * k < nc) ? lbk : lb[k];
+                rb[k] = rb[k] + cross(l1_[k], g);
             }
             // (b) the contact updates of iteration it, against V^it, W^it
             V3 Vi = v_pred, Wv = w_pred;
@@ -820,13 +818,9 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
             }
             float acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-            for (int k = 0; k < PL; ++k) {
-                const int ci = G.gt + T * k;
-                if (ci < nc) {
-                    contact_update_bwd(r_[k], n_[k], c_[k], ikn_[k], ikt_[k], l0_[k], Vi, Wv, E.mu, inv_nc, width,
-                                       beta_s, lb[k], nb[k], rb[k], cb[k], iknb[k], iktb[k], mu_b, acc);
-                }
-            }
+            for (int k = 0; k < PL; ++k)
+                contact_update_bwd(r_[k], n_[k], c_[k], ikn_[k], ikt_[k], l0_[k], Vi, Wv, E.mu, inv_nc, width, beta_s,
+                                   lb[k], nb[k], rb[k], cb[k], iknb[k], iktb[k], mu_b, acc);
             for (int ci = G.gt + T * PL; ci < nc; ci += T) {   // (a) and (b) of the contacts in memory
                 const float4 *rc = sp.rec + 4 * ci;
                 const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
