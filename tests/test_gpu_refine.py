@@ -130,22 +130,12 @@ def _fragile_window(osc, sm, q_traj, f0, T, pose7, vel6, theta):
     return False
 
 
-def test_refinement_matches_oracle():
-    """sim_refine_elites against the FP64 refinement oracle, elite by elite,
-    from the GPU's window-start state widened exactly to FP64: the elites, the
-    accept/halve decision of every evaluation, the refined window-start state
-    (1e-5 m, 1e-5 rad, 1e-3 relative in m and mu), the unrefined and best window
-    costs (1e-3 relative), and what is committed: an improved elite's live state
-    is its best trial's window-end state (5e-5 m / rad after the window's five
-    frames), its parameters the best ones and its window sum the best cost; the
-    others keep their scored state bit for bit. Elites whose decisions are not
-    decisive (a trial's cost within 1e-3 of the best before it) or whose trial
-    windows pass near a branch threshold are skipped and counted."""
+def _check_against_oracle(wl, sim, obs, opt, warm, cm, T, steps, k, order=None, max_checked=None):
+    """Refine the window's elites, then compare elites (in `order`, up to
+    max_checked of them) with the FP64 refinement oracle; returns (checked,
+    skipped)."""
     from oracle import adjoint as A
     from gpu_common import POS_TOL, ROT_TOL, rot_angle, scene32, sim32
-    n, T5, steps = 64, 5, 3
-    wl, sim, obs, opt, warm, cm = _window(n=n, T=T5)
-    k = 16   # elite_frac 0.25 of 64
     pose0, vel0, par0 = (t.clone() for t in sim._window_start)
     before = [t.clone() for t in sim.sim_get_state()]
     el, c0, c1, acc, sp, spar = sim.sim_refine_elites(warm, obs, opt, steps=steps, detail=True)
@@ -169,13 +159,16 @@ def test_refinement_matches_oracle():
     live_v = O.vel8_to6(after[1].cpu().numpy())
     live_th = after[2].cpu().numpy().astype(np.float64)
     checked, skipped = 0, 0
-    for i, e in enumerate(el):
-        r = A.refine_elite(sc, sm, o32, p7[e], v6[e], th[e], wl.q_traj, warm, T5, obs64, steps=steps,
+    for i in (range(len(el)) if order is None else order):
+        if max_checked is not None and checked >= max_checked:
+            break
+        e = el[i]
+        r = A.refine_elite(sc, sm, o32, p7[e], v6[e], th[e], wl.q_traj, warm, T, obs64, steps=steps,
                            step_scale=0.5, beta=1e3, width=float(np.float32(1e-3)))
         best_before = np.minimum.accumulate(r["costs"])
         decisive = all(abs(r["costs"][j] - best_before[j - 1]) > 1e-3 * abs(best_before[j - 1])
                        for j in range(1, steps + 1))
-        if not decisive or any(_fragile_window(osc, sm, wl.q_traj, warm, T5, tp, v6[e], tt)
+        if not decisive or any(_fragile_window(osc, sm, wl.q_traj, warm, T, tp, v6[e], tt)
                                for tp, tt in r["trials"]):
             skipped += 1
             continue
@@ -198,4 +191,36 @@ def test_refinement_matches_oracle():
             for a_, b_ in zip(before[:3], after[:3]):
                 assert torch.equal(a_[int(e)], b_[int(e)])
         checked += 1
+    return checked, skipped
+
+
+def test_refinement_matches_oracle():
+    """sim_refine_elites against the FP64 refinement oracle, elite by elite,
+    from the GPU's window-start state widened exactly to FP64: the elites, the
+    accept/halve decision of every evaluation, the refined window-start state
+    (1e-5 m, 1e-5 rad, 1e-3 relative in m and mu), the unrefined and best window
+    costs (1e-3 relative), and what is committed: an improved elite's live state
+    is its best trial's window-end state (5e-5 m / rad after the window's five
+    frames), its parameters the best ones and its window sum the best cost; the
+    others keep their scored state bit for bit. Elites whose decisions are not
+    decisive (a trial's cost within 1e-3 of the best before it) or whose trial
+    windows pass near a branch threshold are skipped and counted."""
+    n, T5, steps = 64, 5, 3
+    wl, sim, obs, opt, warm, cm = _window(n=n, T=T5)
+    k = 16   # elite_frac 0.25 of 64
+    checked, skipped = _check_against_oracle(wl, sim, obs, opt, warm, cm, T5, steps, k)
     assert checked >= k // 2, (checked, skipped)
+
+
+def test_full_size_refinement_matches_oracle_on_samples():
+    """The refinement as bench.py times it -- 1024 cylinders, a 10-frame
+    window, the optimizer's 10 % elites (102, four warps each), 3 steps --
+    against the FP64 refinement oracle on sampled elites, with the checks
+    and exclusions of the test above."""
+    n, steps = 1024, 3
+    wl, sim, obs, opt, warm, cm = _window(n=n, T=T)
+    opt.elite_frac = 0.1
+    k = int(np.floor(0.1 * n))
+    order = np.random.default_rng(7).permutation(k)
+    checked, skipped = _check_against_oracle(wl, sim, obs, opt, warm, cm, T, steps, k, order=order, max_checked=6)
+    assert checked >= 4, (checked, skipped)
