@@ -21,18 +21,23 @@
 // Contact membership (gap < margin), the capsule's end clamps, the palm's face
 // or clamp pattern and the bias regimes are held fixed.
 //
-// Work layout: a group of GW warps (32 GW threads) per environment. The first
-// warp enumerates the contacts; then thread k % (32 GW) of the group owns
-// contact k for the setup, the Jacobi iterations and their reverse, and the
-// group sums impulses and derivatives by warp shuffles and a shared-memory
-// exchange between its warps. The state at every K-th frame is
-// kept (checkpoints). The reverse sweep walks the segments between checkpoints
-// backwards: it recomputes the segment's substep start states and pad forces
-// from its checkpoint, then for each substep in reverse order recomputes the
-// substep once more while recording the impulses after every Jacobi iteration
-// and the per-iteration impulse sums (the tape), and runs that substep's
-// reverse sweep. Checkpoints, segment states and the tape live in a slice of
-// a scratch buffer owned by the handle, one slice per environment.
+// Work layout: a group of GW warps (32 GW threads) per environment. The
+// group enumerates the contacts together, in the step's order; thread
+// k % (32 GW) then owns contact k for the setup, the Jacobi iterations and
+// their reverse -- its first PL contacts in registers, the further ones in the
+// environment's scratch memory -- and the group sums impulses and derivatives
+// by warp shuffles and a shared-memory exchange between its warps. The state
+// at every K-th frame is kept (checkpoints). The reverse sweep walks the
+// segments between checkpoints backwards: it recomputes the segment's
+// substep start states and pad forces from its checkpoint while recording the
+// tape (the impulses after every Jacobi iteration and the per-iteration
+// impulse sums) of every substep of the segment, then runs the substeps'
+// reverse sweeps in reverse order. When the whole segment's tape does not fit
+// the handle's budget, each substep is run once more just before its reverse
+// sweep to record its tape alone; the results are the same bit for bit. (The
+// last segment's tape is recorded by the first pass itself.) Checkpoints,
+// segment states and the tape live in a slice of a scratch buffer owned by
+// the handle, one slice per environment.
 #include "contact.cuh"
 #include "internal.cuh"
 
