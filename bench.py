@@ -73,7 +73,7 @@ FLOP_PER_ENV_ITER = 24
 # profiles/step_kernel_tracking_cyl64.md, valid for the step kernel's own
 # sources (step.cu, step_kernel.cuh, contact.cuh) whose hash is recorded with it; reported as
 # null once they change.
-STEP_TRAFFIC = {"bytes_per_launch": 200448, "sources_sha256": "ce1c43c5f7d81e7c8d982d1eef7ca0f277675b24f82eb08f15099a0743e2105f"}
+STEP_TRAFFIC = {"bytes_per_launch": 200192, "sources_sha256": "91521be734c85a5a59a84b2be37a4cf619b2a3268b2665d3306d11e1368d318d"}
 STEP_SOURCES = ["paper_2002_12160_gb300/csrc/step.cu", "paper_2002_12160_gb300/csrc/step_kernel.cuh",
                 "paper_2002_12160_gb300/csrc/contact.cuh"]
 
