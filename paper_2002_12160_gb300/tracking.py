@@ -166,9 +166,10 @@ class Tracker:
         T = self.T
         f0 = w * T
         self.sim.sim_mark_window()
-        for k in range(T):
-            f = f0 + k
-            self.sim.sim_step_track(f, self.obs[f], None, self.argmin[f:f + 1], self.est[f])
+        # the window's T frames in one step launch, then each frame's argmin
+        # (the same results as T per-frame launches, bit for bit)
+        self.sim.sim_step_frames(f0, self.obs[f0:f0 + T])
+        self.sim.sim_frames_argmin(self.est[f0:f0 + T], self.argmin[f0:f0 + T])
         rep = self.sim.sim_refine_elites(f0, self.obs[f0:f0 + T], self.wl.opt, steps, step_scale,
                                          report=report)
         self.sim.optimizer_update(self.wl.opt, w)
