@@ -96,6 +96,11 @@ __device__ __forceinline__ Q4 qconj(Q4 q) { return {q.w, -q.x, -q.y, -q.z}; }
 
 template <int GW>
 struct alignas(16) GroupSm {
+    // contacts whose record (besides the slot's global one, which the tape
+    // keeps) the forward substep also holds here: the register slots' and more
+    static constexpr int kRC = GW == 1 ? 64 : 128;
+    float4 crec[kRC][2];           // (r, gap), (n, link | pad << 8 as int bits)
+    float4 clam[kRC];              // the pass's final impulses of the register slots (pad sums)
     float4 sph[IH_MAX_SPHERES];    // the substep's sphere centres (world rotation, relative to x), radius
     float4 clc[IH_MAX_SPHERES / kCluster];   // cluster centres (likewise), enclosing radius
     double term[IH_MAX_PADS];      // a frame's FP64 force term of each pad
@@ -242,6 +247,7 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
     // one compiled body serves the cost pass, the recomputation and the tape,
     // so a recorded tape is bit for bit the forward's
     const bool TAPE = tape_flag != 0, PADS = pads_flag != 0;
+    static_assert(AGroup<GW>::T * PL <= GroupSm<GW>::kRC, "the register slots' records are in shared memory");
     // by-value copies of what the loops read: through the references every
     // store to the tape or to shared memory could alias them and force reloads
     const Env E = E_;
@@ -342,9 +348,15 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
                 if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
             }
             float4 *rc = sp.rec + 4 * idx;
-            rc[0] = make_float4(r.x, r.y, r.z, hh.gap);
+            const float4 a0 = make_float4(r.x, r.y, r.z, hh.gap);
+            const float lp = __int_as_float(l | ((pad & 0xff) << 8));
+            rc[0] = a0;
             rc[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, 0.0f);
-            rc[3] = make_float4(hh.t, __int_as_float(l | ((pad & 0xff) << 8)), __int_as_float(j), 0.0f);
+            rc[3] = make_float4(hh.t, lp, __int_as_float(j), 0.0f);
+            if (idx < GroupSm<GW>::kRC) {
+                S.crec[idx][0] = a0;
+                S.crec[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, lp);
+            }
         }
     }
     G.sync();   // the records are written
@@ -353,10 +365,14 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
         nc = 0;
     }
     // each link's contact range (the contacts are in link order)
+    constexpr int RC = GroupSm<GW>::kRC;
+    auto link_of = [&](int c) -> int {
+        return c < RC ? (__float_as_int(S.crec[c][1].w) & 0xff) : rec_link(sp.rec[4 * c + 3]);
+    };
     for (int ci = gt; ci < nc; ci += T) {
-        const int l = rec_link(sp.rec[4 * ci + 3]);
-        if (ci == 0 || rec_link(sp.rec[4 * (ci - 1) + 3]) != l) S.lbeg[l] = (unsigned short)ci;
-        if (ci == nc - 1 || rec_link(sp.rec[4 * (ci + 1) + 3]) != l) S.lend[l] = (unsigned short)(ci + 1);
+        const int l = link_of(ci);
+        if (ci == 0 || link_of(ci - 1) != l) S.lbeg[l] = (unsigned short)ci;
+        if (ci == nc - 1 || link_of(ci + 1) != l) S.lend[l] = (unsigned short)(ci + 1);
     }
     G.sync();
 
@@ -371,11 +387,11 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
         cr_[k] = mk(0, 0, 0); cn_[k] = mk(0, 0, 1); cc_[k] = mk(0, 0, 0);
         ikn_[k] = ikt_[k] = 0.0f;
         const int ci = G.gt + T * k;
-        if (ci < nc) {
+        if (ci < nc) {   // (a register slot's record is in shared memory: T PL <= kRC)
             float4 *rc = sp.rec + 4 * ci;
-            const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
-            const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, rec_link(r3), Wi, trW, E.inv_m, cfg, L0, L1, b.x,
-                                            inv_h);
+            const float4 r0 = S.crec[ci][0], r1 = S.crec[ci][1];
+            const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, __float_as_int(r1.w) & 0xff, Wi, trW, E.inv_m, cfg,
+                                            L0, L1, b.x, inv_h);
             rc[1] = make_float4(r1.x, r1.y, r1.z, cs.ikn);
             rc[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikt);
             cr_[k] = xyz(r0); cn_[k] = xyz(r1); cc_[k] = cs.cc; ikn_[k] = cs.ikn; ikt_[k] = cs.ikt;
@@ -445,7 +461,7 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
 #pragma unroll
         for (int k = 0; k < PL; ++k) {
             const int ci = G.gt + T * k;
-            if (ci < nc) sp.lamf[ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
+            if (ci < nc) S.clam[ci] = make_float4(lam_[k].x, lam_[k].y, lam_[k].z, 0.0f);
         }
         G.sync();
         if (G.gt < P && nc > 0) {
@@ -453,8 +469,9 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
             float fx = 0.0f, fy = 0.0f, fz = 0.0f;
             const int e = S.lend[l];
             for (int ci = S.lbeg[l]; ci < e; ++ci) {
-                if (rec_pad(sp.rec[4 * ci + 3]) != lane) continue;
-                const float4 lf = sp.lamf[ci];
+                const int pd = ci < RC ? ((__float_as_int(S.crec[ci][1].w) >> 8) & 0xff) : rec_pad(sp.rec[4 * ci + 3]);
+                if (pd != lane) continue;
+                const float4 lf = ci < T * PL ? S.clam[ci] : sp.lamf[ci];
                 fx -= lf.x * inv_h; fy -= lf.y * inv_h; fz -= lf.z * inv_h;
             }
             S.padacc[3 * lane + 0] += fx;
