@@ -952,6 +952,80 @@ __device__ __noinline__ void rev_substep(const AdjArgs &a, const Env &E_, const 
     mu_b_ = mu_b;
 }
 
+// The refinement step of elite i, taken by the thread that wrote its trial's
+// cost (the group's first) at the end of the trial's adjoint launch. The trial
+// is accepted when it lowers the elite's cost (the first evaluation always
+// is); otherwise the step multiplier halves. Then the next trial steps from
+// the best state along the normalised steepest descent in coordinates scaled
+// by eta:
+//   s = eta * g,  dz = -scale * eta * s / |s|
+// (position += dz_0..2, R <- exp([dz_3..5]x) R, m += dz_6, mu += dz_7, with m
+// and mu clamped), or, after the last trial, the best state is restored and
+// an improved elite's live end state, parameters and window cost (sum and
+// mean) replace the scored ones. Not inlined: one copy for the kernel's three
+// exits keeps it out of the adjoint's own code.
+__device__ __noinline__ void refine_step(const RefineArgs &r, int i) {
+    const int env = r.elite[i];
+    const double c = r.cost[i];
+    const float4 *tp = r.step == 0 ? r.ws_pose : r.tr_pose;
+    const float2 *tq = r.step == 0 ? r.ws_params : r.tr_params;
+    if (r.step == 0 || c < r.best_c[i]) {
+        r.accepted[i] = (r.step == 0 ? 0ull : r.accepted[i]) | (1ull << r.step);
+        r.best_pose[2 * i] = tp[2 * env];
+        r.best_pose[2 * i + 1] = tp[2 * env + 1];
+        for (int q = 0; q < 2; ++q) {
+            r.best_end_pose[2 * i + q] = r.end_pose[2 * i + q];
+            r.best_end_vel[2 * i + q] = r.end_vel[2 * i + q];
+        }
+        r.best_params[i] = tq[env];
+        for (int d = 0; d < 8; ++d) r.best_grad[8 * i + d] = r.grad[8 * i + d];
+        r.best_c[i] = c;
+        if (r.step == 0) { r.c0[i] = c; r.scale[i] = 1.0f; }
+    } else {
+        r.scale[i] *= 0.5f;
+    }
+    const float4 p0 = r.best_pose[2 * i], p1 = r.best_pose[2 * i + 1];
+    float2 th = r.best_params[i];
+    if (r.last) {
+        r.tr_pose[2 * env] = p0;
+        r.tr_pose[2 * env + 1] = p1;
+        r.tr_params[env] = th;
+        const double cb = r.best_c[i];
+        if (cb < r.c0[i]) {   // improved: its best trial's window replaces the scored one
+            r.pose[2 * env] = r.best_end_pose[2 * i];
+            r.pose[2 * env + 1] = r.best_end_pose[2 * i + 1];
+            r.vel[2 * env] = r.best_end_vel[2 * i];
+            r.vel[2 * env + 1] = r.best_end_vel[2 * i + 1];
+            r.params[env] = th;
+            const int nw = *r.n_window;
+            r.c_sum[env] = cb;
+            r.c_mean[env] = nw > 0 ? cb / (double)nw : cb;
+        }
+        return;
+    }
+    float sv[8], nrm2 = 0.0f;
+    for (int d = 0; d < 8; ++d) {
+        sv[d] = r.eta[d] * r.best_grad[8 * i + d];
+        nrm2 += sv[d] * sv[d];
+    }
+    float dz[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (nrm2 > 0.0f && isfinite(nrm2)) {
+        const float f = -r.scale[i] * rsqrtf(nrm2);
+        for (int d = 0; d < 8; ++d) dz[d] = f * r.eta[d] * sv[d];
+    }
+    const float an = sqrtf(dz[3] * dz[3] + dz[4] * dz[4] + dz[5] * dz[5]);
+    float sn, cs;
+    sincosf(0.5f * an, &sn, &cs);
+    const float kq = an > 0.0f ? sn / an : 0.5f;
+    const Q4 e = {cs, dz[3] * kq, dz[4] * kq, dz[5] * kq};
+    const Q4 q = qnorm(qmul(e, Q4{p1.x, p1.y, p1.z, p1.w}));
+    th.x = fminf(fmaxf(th.x + dz[6], r.m_lo), r.m_hi);
+    th.y = fminf(fmaxf(th.y + dz[7], r.mu_lo), r.mu_hi);
+    r.tr_pose[2 * env] = make_float4(p0.x + dz[0], p0.y + dz[1], p0.z + dz[2], 0.0f);
+    r.tr_pose[2 * env + 1] = make_float4(q.w, q.x, q.y, q.z);
+    r.tr_params[env] = th;
+}
+
 template <int GW, int PL>
 __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     constexpr int T = AGroup<GW>::T, GPB = kAW / GW;
@@ -1085,12 +1159,15 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     }
     if (a.forward_only) {
         if (lane == 0 && a.cost) a.cost[slot] = (st & kDiverged) ? INFINITY : cost;
+        if (lane == 0 && a.refine) refine_step(a.rf, slot);
         return;
     }
     if (st & kDiverged) {   // no derivative of a diverged or invalid environment
         if (lane < 8) a.grad[8 * slot + lane] = 0.0f;
         if (a.grad_quat && lane < 4) a.grad_quat[4 * slot + lane] = 0.0f;
         if (lane == 0 && a.cost) a.cost[slot] = INFINITY;
+        __syncwarp();   // (the refinement step reads the whole gradient)
+        if (lane == 0 && a.refine) refine_step(a.rf, slot);
         return;
     }
 
@@ -1161,6 +1238,7 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
             a.grad_quat[4 * slot + 2] = ad.q.y; a.grad_quat[4 * slot + 3] = ad.q.z;
         }
         if (a.cost) a.cost[slot] = cost;
+        if (a.refine) refine_step(a.rf, slot);
     }
 }
 
@@ -1169,83 +1247,6 @@ cudaError_t launch_pl(const AdjArgs &a, cudaStream_t s) {
     constexpr int GPB = kAW / GW;
     adjoint_kernel<GW, PL><<<(a.n + GPB - 1) / GPB, kABlock, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-// One thread per elite. The trial just evaluated is accepted when it lowers
-// the elite's cost (the first evaluation always is); otherwise the step
-// multiplier halves. Then the next trial steps from the best state along the
-// normalised steepest descent in coordinates scaled by eta:
-//   s = eta * g,  dz = -scale * eta * s / |s|
-// (position += dz_0..2, R <- exp([dz_3..5]x) R, m += dz_6, mu += dz_7, with m
-// and mu clamped), or, on the last call, the best state is restored.
-__global__ void refine_kernel(const RefineArgs r) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= r.k) return;
-    const int env = r.elite[i];
-    const double c = r.cost[i];
-    if (r.step == 0 || c < r.best_c[i]) {
-        r.accepted[i] = (r.step == 0 ? 0ull : r.accepted[i]) | (1ull << r.step);
-        r.best_pose[2 * i] = r.tr_pose[2 * env];
-        r.best_pose[2 * i + 1] = r.tr_pose[2 * env + 1];
-        for (int q = 0; q < 2; ++q) {
-            r.best_end_pose[2 * i + q] = r.end_pose[2 * i + q];
-            r.best_end_vel[2 * i + q] = r.end_vel[2 * i + q];
-        }
-        r.best_params[i] = r.tr_params[env];
-        for (int d = 0; d < 8; ++d) r.best_grad[8 * i + d] = r.grad[8 * i + d];
-        r.best_c[i] = c;
-        if (r.step == 0) { r.c0[i] = c; r.scale[i] = 1.0f; }
-    } else {
-        r.scale[i] *= 0.5f;
-    }
-    const float4 p0 = r.best_pose[2 * i], p1 = r.best_pose[2 * i + 1];
-    float2 th = r.best_params[i];
-    if (r.last) {
-        r.tr_pose[2 * env] = p0;
-        r.tr_pose[2 * env + 1] = p1;
-        r.tr_params[env] = th;
-        return;
-    }
-    float sv[8], nrm2 = 0.0f;
-    for (int d = 0; d < 8; ++d) {
-        sv[d] = r.eta[d] * r.best_grad[8 * i + d];
-        nrm2 += sv[d] * sv[d];
-    }
-    float dz[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (nrm2 > 0.0f && isfinite(nrm2)) {
-        const float f = -r.scale[i] * rsqrtf(nrm2);
-        for (int d = 0; d < 8; ++d) dz[d] = f * r.eta[d] * sv[d];
-    }
-    const float an = sqrtf(dz[3] * dz[3] + dz[4] * dz[4] + dz[5] * dz[5]);
-    float sn, cs;
-    sincosf(0.5f * an, &sn, &cs);
-    const float kq = an > 0.0f ? sn / an : 0.5f;
-    const Q4 e = {cs, dz[3] * kq, dz[4] * kq, dz[5] * kq};
-    const Q4 q = qnorm(qmul(e, Q4{p1.x, p1.y, p1.z, p1.w}));
-    th.x = fminf(fmaxf(th.x + dz[6], r.m_lo), r.m_hi);
-    th.y = fminf(fmaxf(th.y + dz[7], r.mu_lo), r.mu_hi);
-    r.tr_pose[2 * env] = make_float4(p0.x + dz[0], p0.y + dz[1], p0.z + dz[2], 0.0f);
-    r.tr_pose[2 * env + 1] = make_float4(q.w, q.x, q.y, q.z);
-    r.tr_params[env] = th;
-}
-
-__global__ void refine_commit_kernel(int k, const int *elite, const double *best_c, const double *c0,
-                                     const float2 *best_params, const float4 *end_pose, const float4 *end_vel,
-                                     float4 *pose, float4 *vel, float2 *params, double *c_sum, double *c_mean,
-                                     const int *n_window) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k) return;
-    const double c = best_c[i];
-    if (!(c < c0[i])) return;   // not improved: the live state stays the scored one
-    const int env = elite[i];
-    pose[2 * env] = end_pose[2 * i];
-    pose[2 * env + 1] = end_pose[2 * i + 1];
-    vel[2 * env] = end_vel[2 * i];
-    vel[2 * env + 1] = end_vel[2 * i + 1];
-    params[env] = best_params[i];
-    const int nw = *n_window;
-    c_sum[env] = c;
-    c_mean[env] = nw > 0 ? c / (double)nw : c;
 }
 
 __global__ void iters_max_kernel(int n, int N, const int *envs, const int *iters, int *out) {
@@ -1272,20 +1273,6 @@ size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max,
 
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s) {
     iters_max_kernel<<<1, 256, 0, s>>>(n, N, envs, iters, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refine(const RefineArgs &r, cudaStream_t s) {
-    refine_kernel<<<(r.k + 127) / 128, 128, 0, s>>>(r);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, const double *c0,
-                                 const float2 *best_params, const float4 *end_pose, const float4 *end_vel,
-                                 float4 *pose, float4 *vel, float2 *params, double *c_sum, double *c_mean,
-                                 const int *n_window, cudaStream_t s) {
-    refine_commit_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, elite, best_c, c0, best_params, end_pose, end_vel, pose,
-                                                         vel, params, c_sum, c_mean, n_window);
     return cudaGetLastError();
 }
 

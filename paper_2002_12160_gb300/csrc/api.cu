@@ -1098,6 +1098,8 @@ AdjArgs adjoint_args(ih_sim *s, int32_t frame0, int32_t horizon, int K, const fl
     a.scratch = s->adj_scratch; a.stride = 0; a.iters_max = 0;
     a.forward_only = 0; a.out_pose = nullptr; a.out_vel = nullptr; a.seg_tape = 0; a.zero = 0;
     a.gw = s->adj_gw; a.pl = s->adj_pl; a.s_max = s->s_max;
+    a.refine = 0;
+    a.rf = RefineArgs{};
     return a;
 }
 }  // namespace
@@ -1200,18 +1202,17 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
     int k = (int)std::floor((double)opt->elite_frac * (double)N);
     k = std::max(1, std::min(k, N));
     cudaStream_t st = s->stream;
-    // elites of the window (the optimizer's own selection), trial states = window start
+    // elites of the window (the optimizer's own selection); the first trial is
+    // the window start itself
     OptArgs oa = opt_args(s, opt, 0, nullptr, nullptr);
     cudaError_t e = launch_select(oa, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->tr_pose, s->ws_pose, 2 * (size_t)N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->tr_params, s->ws_params, (size_t)N * sizeof(float2), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "refine select");
     size_t stride = 0;
     int imax = 0;
     r = adjoint_prepare(s, k, s->elite_env, T, T, &stride, &imax);
     if (r != IH_OK) return r;
     AdjArgs a = adjoint_args(s, frame0, T, T, obs, beta, width);
-    a.n = k; a.envs = s->elite_env; a.pose = s->tr_pose; a.vel = s->ws_vel; a.params = s->tr_params;
+    a.n = k; a.envs = s->elite_env; a.vel = s->ws_vel;
     a.cost = s->r_cost; a.grad = s->r_grad; a.scratch = s->adj_scratch; a.stride = stride; a.iters_max = imax;
     a.out_pose = s->end_pose; a.out_vel = s->end_vel; a.seg_tape = s->adj_seg ? 1 : 0;
     RefineArgs ra;
@@ -1222,17 +1223,22 @@ ih_status sim_refine_elites(ih_sim *s, int32_t frame0, int32_t T, const float *o
     ra.best_end_pose = s->best_end_pose; ra.best_end_vel = s->best_end_vel; ra.accepted = s->r_acc;
     for (int d = 0; d < 8; ++d) ra.eta[d] = step_scale * opt->floor_std[d];
     ra.m_lo = opt->m_lo; ra.m_hi = opt->m_hi; ra.mu_lo = opt->mu_lo; ra.mu_hi = opt->mu_hi;
+    ra.ws_pose = s->ws_pose; ra.ws_params = s->ws_params;
+    ra.pose = s->pose; ra.vel = s->vel; ra.params = s->params;
+    ra.c_sum = s->c_sum; ra.c_mean = s->c_mean; ra.n_window = s->n_window;
+    // each launch evaluates the elites' trials, and each elite's group then
+    // takes its refinement step; after the last trial (its cost only) the
+    // groups restore the best states and commit the improved elites' windows
+    a.refine = 1;
     for (int it = 0; it <= steps && e == cudaSuccess; ++it) {
-        a.forward_only = it == steps ? 1 : 0;   // the last trial needs its cost only
-        e = launch_adjoint(a, st);
+        a.forward_only = it == steps ? 1 : 0;
+        a.pose = it == 0 ? s->ws_pose : s->tr_pose;
+        a.params = it == 0 ? s->ws_params : s->tr_params;
         ra.step = it;
         ra.last = it == steps ? 1 : 0;
-        if (e == cudaSuccess) e = launch_refine(ra, st);
+        a.rf = ra;
+        e = launch_adjoint(a, st);
     }
-    // the window's end state of each improved elite's best trial replaces the scored one
-    if (e == cudaSuccess)
-        e = launch_refine_commit(k, s->elite_env, s->best_c, s->c0, s->best_params, s->best_end_pose, s->best_end_vel, s->pose,
-                                 s->vel, s->params, s->c_sum, s->c_mean, s->n_window, st);
     if (e == cudaSuccess && elite_out)
         e = cudaMemcpyAsync(elite_out, s->elite_env, k * sizeof(int), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && cost_before)

@@ -387,6 +387,36 @@ struct OptArgs {
 };
 int opt_blocks(int N);
 
+// One step of the refinement of the elites (sim_refine_elites), taken by the
+// adjoint launch that evaluated the step's trial.
+struct RefineArgs {
+    int k;
+    const int *elite;             // [k] environments
+    float4 *tr_pose;              // [N][2] trial states (elites' entries)
+    float2 *tr_params;            // [N]
+    float4 *best_pose;            // [k][2]
+    float2 *best_params;          // [k]
+    float *best_grad;             // [k][8]
+    double *best_c, *c0;          // [k] best cost so far, cost of the unrefined state
+    float *scale;                 // [k] step multiplier (halved on a rejected trial)
+    const double *cost;           // [k] cost at the trial
+    const float *grad;            // [k][8] gradient at the trial
+    const float4 *end_pose, *end_vel;    // [k][2] end state of the trial's window
+    float4 *best_end_pose, *best_end_vel;  // [k][2] end state of the best trial
+    unsigned long long *accepted; // [k] bit j set when evaluation j was kept
+    float eta[8];                 // step length per coordinate
+    float m_lo, m_hi, mu_lo, mu_hi;
+    int step;                     // 0: the first evaluation (of the unrefined state)
+    int last;                     // 1: restore the best state instead of stepping, then commit
+    const float4 *ws_pose;        // [N][2] window-start states: the first evaluation's trial
+    const float2 *ws_params;      // [N]
+    // the commit: an improved elite's live end state, parameters and window cost
+    float4 *pose, *vel;           // [N][2]
+    float2 *params;               // [N]
+    double *c_sum, *c_mean;       // [N]
+    const int *n_window;
+};
+
 // Reverse-mode derivative of the tracking cost over a horizon (adjoint.cu).
 struct AdjArgs {
     DevScene sc;
@@ -414,37 +444,14 @@ struct AdjArgs {
                               // run-time values and the substep is compiled once for every pass
     int gw, pl;               // kernel shape: warps per environment, register contacts per thread (0, 0: automatic)
     int s_max;                // most spheres in one shape of the scene
+    int refine;               // 1: each slot's group then takes the refinement step rf for its elite
+    RefineArgs rf;
     float4 *out_pose, *out_vel;   // [n][2] end state of each slot, or null
 };
 
 // Gradient refinement of the elites (adjoint.cu): accept or reject the last
 // trial of every elite, then step from its best state.
-struct RefineArgs {
-    int k;
-    const int *elite;             // [k] environments
-    float4 *tr_pose;              // [N][2] trial states (elites' entries)
-    float2 *tr_params;            // [N]
-    float4 *best_pose;            // [k][2]
-    float2 *best_params;          // [k]
-    float *best_grad;             // [k][8]
-    double *best_c, *c0;          // [k] best cost so far, cost of the unrefined state
-    float *scale;                 // [k] step multiplier (halved on a rejected trial)
-    const double *cost;           // [k] cost at the trial
-    const float *grad;            // [k][8] gradient at the trial
-    const float4 *end_pose, *end_vel;    // [k][2] end state of the trial's window
-    float4 *best_end_pose, *best_end_vel;  // [k][2] end state of the best trial
-    unsigned long long *accepted; // [k] bit j set when evaluation j was kept
-    float eta[8];                 // step length per coordinate
-    float m_lo, m_hi, mu_lo, mu_hi;
-    int step;                     // 0: the first evaluation (of the unrefined state)
-    int last;                     // 1: restore the best state instead of stepping
-};
-cudaError_t launch_refine(const RefineArgs &r, cudaStream_t s);
 // copy refined elites (end state [k][2], parameters, window cost) into the live state
-cudaError_t launch_refine_commit(int k, const int *elite, const double *best_c, const double *c0,
-                                 const float2 *best_params, const float4 *end_pose, const float4 *end_vel,
-                                 float4 *pose, float4 *vel, float2 *params, double *c_sum, double *c_mean,
-                                 const int *n_window, cudaStream_t s);
 size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max, bool seg_tape);
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t s);
 bool adjoint_variant_supported(int gw, int pl);   // (0, 0) = automatic
