@@ -175,15 +175,18 @@ __device__ __forceinline__ void gsum6(float (&v)[6], const AGroup<GW> &G, GroupS
 // checkpoints, a segment's substep start states and frame forces, the
 // impulses of a pass (final ones for the pad sums; the running ones of the
 // contacts past the register slots), the reverse state of the contacts past
-// the register slots, the contact count of every taped substep, then nblk tape
-// blocks of (contact records, impulse after each iteration, iteration sums):
-// one block per substep of a segment when the whole segment is taped, else a
-// single block re-filled substep by substep.
+// the register slots, the contact count of every taped substep, the contact
+// records and counts of the nrec substeps of the segments that are
+// recomputed (their recomputation replays them), then nblk tape blocks of
+// (contact records, impulse after each iteration, iteration sums): one block
+// per substep of a segment when the whole segment is taped, else a single
+// block re-filled substep by substep.
 struct SlotLayout {
-    size_t ck, sg, sf, lamf, adj, ncs, tape, blk_rec, blk_lamh, blk_sh, blk_stride, total;
+    size_t ck, sg, sf, lamf, adj, ncs, recs, nrc, tape, blk_rec, blk_lamh, blk_sh, blk_stride, total;
 };
 __host__ __device__ inline size_t round4(size_t x) { return (x + 3) & ~size_t(3); }
-__host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, int cap, int iters_max, int nblk) {
+__host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, int cap, int iters_max, int nblk,
+                                                  int nrec) {
     SlotLayout L;
     size_t o = 0;
     const size_t nck = (size_t)((H + K - 1) / K);
@@ -193,6 +196,8 @@ __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, i
     L.lamf = o; o += round4((size_t)cap * 4);                 // impulses of a pass
     L.adj = o;  o += round4((size_t)cap * 16);                // reverse state of the contacts in memory
     L.ncs = o;  o += round4((size_t)K * ns);                  // contacts of each taped substep (int)
+    L.recs = o; o += (size_t)nrec * cap * 16;                 // records of the recomputed segments' substeps
+    L.nrc = o;  o += round4((size_t)nrec);                    // their contact counts (int)
     L.blk_rec = 0;
     L.blk_lamh = round4((size_t)cap * 16);                                   // contact records
     L.blk_sh = L.blk_lamh + round4((size_t)iters_max * cap * 4);             // impulse after each iteration
@@ -204,6 +209,8 @@ __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, i
 
 struct SlotPtr {
     float4 *ck, *sg, *rec, *lamh, *lamf;
+    float4 *recs;   // records of substep q of the recomputed segments at recs + q * cap * 4
+    int *nrc;       // their contact counts
     float4 *adjs;   // per contact past the register slots: (lb, 1/k_n bar), (nb, 1/k_t bar), (rb, -), (cb, -)
     float *sf, *sh;
     int *ncs;
@@ -242,7 +249,7 @@ template <int GW, int PL>
 __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b, const float4 *L0,
                                         const float4 *L1, const SlotPtr &sp_, GroupSm<GW> &S, const PadTab &PT,
                                         const AGroup<GW> &G_, int &parity_, int &st_, int tape_flag,
-                                        int pads_flag) {
+                                        int pads_flag, int replay_nc) {
     // the flags are run-time values (the callers combine them with a.zero):
     // one compiled body serves the cost pass, the recomputation and the tape,
     // so a recorded tape is bit for bit the forward's
@@ -266,103 +273,122 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
     const S6 Wi = world_inv_inertia(R, E.Jb, E.inv_m);
     const int lane = G.lane;
 
-    // contact enumeration by the whole group, in the step's order (link, then
-    // sphere): sphere and cluster centres to world, the link cull, the (link,
-    // cluster) cull by the clusters' enclosing spheres, then the spheres of the
-    // surviving pairs, one test per thread per round, compacted in order
     const int gt = G.gt;
-    const int ncl = (E.NS + kCluster - 1) / kCluster;
-    for (int j = gt; j < E.NS; j += T) {
-        const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
-        const V3 cr = mmul(R, xyz(s4));
-        S.sph[j] = make_float4(cr.x, cr.y, cr.z, s4.w);
-    }
-    for (int k = gt; k < ncl; k += T) {
-        const float4 cl = __ldg(sc.clusters + E.cfirst + k);
-        const V3 cr = mmul(R, xyz(cl));
-        S.clc[k] = make_float4(cr.x, cr.y, cr.z, cl.w);
-    }
-    if (G.wg == 0) {
-        const bool keep = lane < Lk && link_reaches(sc, cfg, L0, lane, b.x, E.bound);
-        const unsigned surv = __ballot_sync(kFull, keep);
-        if (keep) S.links[__popc(surv & ((1u << lane) - 1u))] = (unsigned char)lane;
-        if (lane == 0) S.surv = surv;
-    }
-    for (int l = gt; l < 32; l += T) {
-        S.lbeg[l] = 0;
-        S.lend[l] = 0;
-    }
-    G.sync();
-    const int ncp = __popc(S.surv) * ncl;
-    int nclp = 0;
-    for (int p0 = 0; p0 < ncp; p0 += T) {
-        const int p = p0 + gt;
-        bool keep = false;
-        int li = 0, k = 0;
-        if (p < ncp) {
-            li = p / ncl;
-            k = p - li * ncl;
-            const float4 cc = S.clc[k];
-            keep = link_reaches(sc, cfg, L0, S.links[li], b.x + xyz(cc), cc.w);
-        }
-        const int off = gcompact<GW>(keep, nclp, G, S, parity);
-        if (keep) S.clp[off] = (unsigned short)((li << 8) | k);
-    }
-    G.sync();
-    const int npairs = nclp * kCluster;
     int nc = 0;
-    for (int p0 = 0; p0 < npairs; p0 += T) {
-        const int p = p0 + gt;
-        bool hit = false;
-        Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
-        V3 r = mk(0, 0, 0);
-        int l = 0, j = 0;
-        if (p < npairs) {
-            const int e = S.clp[p / kCluster];
-            j = (e & 0xff) * kCluster + (p % kCluster);
-            l = S.links[e >> 8];
-            if (j < E.NS) {   // (j >= NS: padding of the shape's last cluster)
-                const float4 s4 = S.sph[j];
-                const V3 cr = xyz(s4);
-                const float4 A0 = __ldg(L0 + l * kLinkStride);
-                const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
-                const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
-                if (l == 0) {
-                    hh = hit_box(b.x + cr, s4.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
-                } else {
-                    const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
-                    hh = hit_capsule((b.x - xyz(A0)) + cr, s4.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+    const bool replay = replay_nc >= 0;
+    if (replay) {
+        // the records this substep's first run left, setup included: no
+        // enumeration (the run is deterministic, so they are its own)
+        nc = replay_nc;
+        for (int ci = gt; ci < nc && ci < GroupSm<GW>::kRC; ci += T) {
+            const float4 *rc = sp.rec + 4 * ci;
+            const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
+            S.crec[ci][0] = r0;
+            S.crec[ci][1] = make_float4(r1.x, r1.y, r1.z, r3.y);
+        }
+        for (int l = gt; l < 32; l += T) {
+            S.lbeg[l] = 0;
+            S.lend[l] = 0;
+        }
+        G.sync();
+    } else {
+        // contact enumeration by the whole group, in the step's order (link,
+        // then sphere): sphere and cluster centres to world, the link cull, the
+        // (link, cluster) cull by the clusters' enclosing spheres, then the
+        // spheres of the surviving pairs, one test per thread per round,
+        // compacted in order
+        const int ncl = (E.NS + kCluster - 1) / kCluster;
+        for (int j = gt; j < E.NS; j += T) {
+            const float4 s4 = __ldg(sc.spheres + E.sfirst + j);
+            const V3 cr = mmul(R, xyz(s4));
+            S.sph[j] = make_float4(cr.x, cr.y, cr.z, s4.w);
+        }
+        for (int k = gt; k < ncl; k += T) {
+            const float4 cl = __ldg(sc.clusters + E.cfirst + k);
+            const V3 cr = mmul(R, xyz(cl));
+            S.clc[k] = make_float4(cr.x, cr.y, cr.z, cl.w);
+        }
+        if (G.wg == 0) {
+            const bool keep = lane < Lk && link_reaches(sc, cfg, L0, lane, b.x, E.bound);
+            const unsigned surv = __ballot_sync(kFull, keep);
+            if (keep) S.links[__popc(surv & ((1u << lane) - 1u))] = (unsigned char)lane;
+            if (lane == 0) S.surv = surv;
+        }
+        for (int l = gt; l < 32; l += T) {
+            S.lbeg[l] = 0;
+            S.lend[l] = 0;
+        }
+        G.sync();
+        const int ncp = __popc(S.surv) * ncl;
+        int nclp = 0;
+        for (int p0 = 0; p0 < ncp; p0 += T) {
+            const int p = p0 + gt;
+            bool keep = false;
+            int li = 0, k = 0;
+            if (p < ncp) {
+                li = p / ncl;
+                k = p - li * ncl;
+                const float4 cc = S.clc[k];
+                keep = link_reaches(sc, cfg, L0, S.links[li], b.x + xyz(cc), cc.w);
+            }
+            const int off = gcompact<GW>(keep, nclp, G, S, parity);
+            if (keep) S.clp[off] = (unsigned short)((li << 8) | k);
+        }
+        G.sync();
+        const int npairs = nclp * kCluster;
+        for (int p0 = 0; p0 < npairs; p0 += T) {
+            const int p = p0 + gt;
+            bool hit = false;
+            Hit hh = {0.0f, mk(0, 0, 1), 0.0f};
+            V3 r = mk(0, 0, 0);
+            int l = 0, j = 0;
+            if (p < npairs) {
+                const int e = S.clp[p / kCluster];
+                j = (e & 0xff) * kCluster + (p % kCluster);
+                l = S.links[e >> 8];
+                if (j < E.NS) {   // (j >= NS: padding of the shape's last cluster)
+                    const float4 s4 = S.sph[j];
+                    const V3 cr = xyz(s4);
+                    const float4 A0 = __ldg(L0 + l * kLinkStride);
+                    const float4 Aq = __ldg(L0 + l * kLinkStride + 2);
+                    const Q4 lq = {Aq.x, Aq.y, Aq.z, Aq.w};
+                    if (l == 0) {
+                        hh = hit_box(b.x + cr, s4.w, xyz(A0), lq, sc.palm_hx, sc.palm_hy, sc.palm_hz);
+                    } else {
+                        const V3 ld = xyz(__ldg(L0 + l * kLinkStride + 1));
+                        hh = hit_capsule((b.x - xyz(A0)) + cr, s4.w, ld, sc.link_len, inv_L, sc.link_rad, lq);
+                    }
+                    r = cr - hh.n * s4.w;
+                    hit = hh.gap < cfg.margin;
                 }
-                r = cr - hh.n * s4.w;
-                hit = hh.gap < cfg.margin;
+            }
+            const int idx = gcompact<GW>(hit, nc, G, S, parity);
+            if (hit && idx < cap) {
+                int pad = -1;   // the first pad of the link whose interval holds t
+                const int npl = PT.cnt[l];
+                for (int k = 0; k < npl; ++k) {
+                    const int pp = PT.id[l * kAPadsPerLink + k];
+                    if (l == 0) { pad = pp; break; }
+                    const float s0 = PT.s0[pp], s1 = PT.s1[pp];
+                    if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
+                }
+                float4 *rc = sp.rec + 4 * idx;
+                const float4 a0 = make_float4(r.x, r.y, r.z, hh.gap);
+                const float lp = __int_as_float(l | ((pad & 0xff) << 8));
+                rc[0] = a0;
+                rc[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, 0.0f);
+                rc[3] = make_float4(hh.t, lp, __int_as_float(j), 0.0f);
+                if (idx < GroupSm<GW>::kRC) {
+                    S.crec[idx][0] = a0;
+                    S.crec[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, lp);
+                }
             }
         }
-        const int idx = gcompact<GW>(hit, nc, G, S, parity);
-        if (hit && idx < cap) {
-            int pad = -1;   // the first pad of the link whose interval holds t
-            const int npl = PT.cnt[l];
-            for (int k = 0; k < npl; ++k) {
-                const int pp = PT.id[l * kAPadsPerLink + k];
-                if (l == 0) { pad = pp; break; }
-                const float s0 = PT.s0[pp], s1 = PT.s1[pp];
-                if (hh.t >= s0 && (hh.t < s1 || s1 >= 1.0f)) { pad = pp; break; }
-            }
-            float4 *rc = sp.rec + 4 * idx;
-            const float4 a0 = make_float4(r.x, r.y, r.z, hh.gap);
-            const float lp = __int_as_float(l | ((pad & 0xff) << 8));
-            rc[0] = a0;
-            rc[1] = make_float4(hh.n.x, hh.n.y, hh.n.z, 0.0f);
-            rc[3] = make_float4(hh.t, lp, __int_as_float(j), 0.0f);
-            if (idx < GroupSm<GW>::kRC) {
-                S.crec[idx][0] = a0;
-                S.crec[idx][1] = make_float4(hh.n.x, hh.n.y, hh.n.z, lp);
-            }
+        G.sync();   // the records are written
+        if (nc > cap) {   // more contacts than the per-env capacity: as the step, no contacts
+            st |= IH_ENV_OVERFLOW;
+            nc = 0;
         }
-    }
-    G.sync();   // the records are written
-    if (nc > cap) {   // more contacts than the per-env capacity: as the step, no contacts
-        st |= IH_ENV_OVERFLOW;
-        nc = 0;
     }
     // each link's contact range (the contacts are in link order)
     constexpr int RC = GroupSm<GW>::kRC;
@@ -387,7 +413,11 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
         cr_[k] = mk(0, 0, 0); cn_[k] = mk(0, 0, 1); cc_[k] = mk(0, 0, 0);
         ikn_[k] = ikt_[k] = 0.0f;
         const int ci = G.gt + T * k;
-        if (ci < nc) {   // (a register slot's record is in shared memory: T PL <= kRC)
+        if (ci < nc && replay) {   // the setup's results are in the records
+            const float4 *rc = sp.rec + 4 * ci;
+            const float4 r0 = rc[0], r1 = rc[1], r2 = rc[2];
+            cr_[k] = xyz(r0); cn_[k] = xyz(r1); cc_[k] = xyz(r2); ikn_[k] = r1.w; ikt_[k] = r2.w;
+        } else if (ci < nc) {   // (a register slot's record is in shared memory: T PL <= kRC)
             float4 *rc = sp.rec + 4 * ci;
             const float4 r0 = S.crec[ci][0], r1 = S.crec[ci][1];
             const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, __float_as_int(r1.w) & 0xff, Wi, trW, E.inv_m, cfg,
@@ -400,12 +430,14 @@ __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b
     // contacts past the register slots (thread gt's slots PL, PL + 1, ... in
     // the same order): constants in their records, impulse in sp.lamf
     for (int ci = G.gt + T * PL; ci < nc; ci += T) {
-        float4 *rc = sp.rec + 4 * ci;
-        const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
-        const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, rec_link(r3), Wi, trW, E.inv_m, cfg, L0, L1, b.x,
-                                        inv_h);
-        rc[1] = make_float4(r1.x, r1.y, r1.z, cs.ikn);
-        rc[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikt);
+        if (!replay) {
+            float4 *rc = sp.rec + 4 * ci;
+            const float4 r0 = rc[0], r1 = rc[1], r3 = rc[3];
+            const CSetup cs = setup_contact(xyz(r0), xyz(r1), r0.w, rec_link(r3), Wi, trW, E.inv_m, cfg, L0, L1, b.x,
+                                            inv_h);
+            rc[1] = make_float4(r1.x, r1.y, r1.z, cs.ikn);
+            rc[2] = make_float4(cs.cc.x, cs.cc.y, cs.cc.z, cs.ikt);
+        }
         sp.lamf[ci] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 
@@ -1059,7 +1091,12 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
         return;
     }
     const bool seg_tape = a.seg_tape != 0;   // every substep of a segment keeps its tape
-    const SlotLayout Ly = slot_layout(a.H, a.K, ns, P, cap, a.iters_max, seg_tape ? a.K * ns : 1);
+    const int nck = (a.H + a.K - 1) / a.K;
+    // with whole-segment tapes, the segments recomputed later keep their
+    // substeps' contact records from the first pass, and their recomputation
+    // replays them
+    const int nrec = seg_tape ? (nck - 1) * a.K * ns : 0;
+    const SlotLayout Ly = slot_layout(a.H, a.K, ns, P, cap, a.iters_max, seg_tape ? a.K * ns : 1, nrec);
     float *base = a.scratch + (size_t)slot * a.stride;
     SlotPtr sp0;
     sp0.ck = reinterpret_cast<float4 *>(base + Ly.ck);
@@ -1067,6 +1104,8 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     sp0.sf = base + Ly.sf;
     sp0.lamf = reinterpret_cast<float4 *>(base + Ly.lamf);
     sp0.adjs = reinterpret_cast<float4 *>(base + Ly.adj);
+    sp0.recs = reinterpret_cast<float4 *>(base + Ly.recs);
+    sp0.nrc = reinterpret_cast<int *>(base + Ly.nrc);
     sp0.ncs = reinterpret_cast<int *>(base + Ly.ncs);
     sp0.tape = base + Ly.tape;
     sp0.blk_lamh = Ly.blk_lamh;
@@ -1099,7 +1138,6 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
 
     // -- pass 1: the cost, the state at every K-th frame, and the substep
     //    states and frame forces of the last segment (the first one reversed)
-    const int nck = (a.H + a.K - 1) / a.K;
     const int f_last = (nck - 1) * a.K;
     double cost = 0.0;
     Body b = b0;
@@ -1114,12 +1152,22 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 const int blk = (f - f_last) * ns + s;
                 if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 if (seg_tape && !a.forward_only) {   // the last segment's tape, recorded on the way
-                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, PT, G, parity, st, 1 | a.zero, 1 | a.zero);
+                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, PT, G, parity,
+                                                       st, 1 | a.zero, 1 | a.zero, -1);
                     if (lane == 0) sp.ncs[blk] = nc;
                     continue;
                 }
             }
-            fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero);
+            if (nrec > 0 && f < f_last) {   // a segment recomputed later: keep this substep's records
+                const int q = f * ns + s;
+                SlotPtr sq = sp;
+                sq.rec = sp.recs + (size_t)q * cap * 4;
+                const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sq, S, PT, G, parity, st, a.zero,
+                                                   1 | a.zero, -1);
+                if (lane == 0) sp.nrc[q] = nc;
+                continue;
+            }
+            fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero, -1);
         }
         if (f >= f_last)
             for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
@@ -1186,11 +1234,16 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 const int blk = (f - fb) * ns + s;
                 if (lane == 0) store_body(sp.sg + 4 * blk, b);
                 const float4 *L0 = tab + (size_t)s * Lk * kLinkStride;
-                if (seg_tape) {
-                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp.blk(blk), S, PT, G, parity, st, 1 | a.zero, 1 | a.zero);
+                if (seg_tape) {   // replaying the first pass's records of the substep
+                    const int q = f * ns + s;
+                    SlotPtr sq = sp.blk(blk);
+                    sq.rec = sp.recs + (size_t)q * cap * 4;
+                    const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sq, S, PT, G, parity, st,
+                                                       1 | a.zero, 1 | a.zero, sp.nrc[q]);
                     if (lane == 0) sp.ncs[blk] = nc;
                 } else {
-                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero);
+                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero,
+                                        -1);
                 }
             }
             for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
@@ -1209,11 +1262,13 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                 const Body bs = load_body(sp.sg + 4 * blk);
                 if (seg_tape) {
                     G.sync();
-                    rev_substep<GW, PL>(a, E, bs, L0, L1, sp.ncs[blk], sp.blk(blk), S, G, parity, ad, invm_b, mu_b);
+                    SlotPtr sq = sp.blk(blk);
+                    if (seg < nck - 1) sq.rec = sp.recs + (size_t)(f * ns + s) * cap * 4;   // (the replayed records)
+                    rev_substep<GW, PL>(a, E, bs, L0, L1, sp.ncs[blk], sq, S, G, parity, ad, invm_b, mu_b);
                 } else {   // re-run the substep once more, recording its tape
                     Body bt = bs;
                     int st2 = 0;
-                    const int nc = fwd_substep<GW, PL>(a, E, bt, L0, L1, sp, S, PT, G, parity, st2, 1 | a.zero, a.zero);
+                    const int nc = fwd_substep<GW, PL>(a, E, bt, L0, L1, sp, S, PT, G, parity, st2, 1 | a.zero, a.zero, -1);
                     rev_substep<GW, PL>(a, E, bs, L0, L1, nc, sp, S, G, parity, ad, invm_b, mu_b);
                 }
             }
@@ -1268,7 +1323,9 @@ __global__ void iters_max_kernel(int n, int N, const int *envs, const int *iters
 }  // namespace
 
 size_t adjoint_scratch_floats(int H, int K, int substeps, int n_pads, int c_max, int iters_max, bool seg_tape) {
-    return slot_layout(H, K, substeps, n_pads, c_max, iters_max, seg_tape ? K * substeps : 1).total;
+    const int nck = (H + K - 1) / K;
+    return slot_layout(H, K, substeps, n_pads, c_max, iters_max, seg_tape ? K * substeps : 1,
+                       seg_tape ? (nck - 1) * K * substeps : 0).total;
 }
 
 cudaError_t launch_adjoint_iters_max(int n, int N, const int *envs, const int *iters, int *out, cudaStream_t s) {
