@@ -172,7 +172,7 @@ __device__ __forceinline__ void gsum6(float (&v)[6], const AGroup<GW> &G, GroupS
 }
 
 // Per-slot scratch layout in floats (every part starts on a float4 boundary):
-// checkpoints, a segment's substep start states and frame forces, the
+// checkpoints, a segment's substep start states, every frame's pad forces, the
 // impulses of a pass (final ones for the pad sums; the running ones of the
 // contacts past the register slots), the reverse state of the contacts past
 // the register slots, the contact count of every taped substep, the contact
@@ -192,7 +192,7 @@ __host__ __device__ inline SlotLayout slot_layout(int H, int K, int ns, int P, i
     const size_t nck = (size_t)((H + K - 1) / K);
     L.ck = o;   o += round4(nck * 16);                        // checkpoint states
     L.sg = o;   o += round4((size_t)K * ns * 16);             // substep start states of a segment
-    L.sf = o;   o += round4((size_t)K * P * 3);               // pad forces of a segment's frames
+    L.sf = o;   o += round4((size_t)H * P * 3);               // pad forces of every frame
     L.lamf = o; o += round4((size_t)cap * 4);                 // impulses of a pass
     L.adj = o;  o += round4((size_t)cap * 16);                // reverse state of the contacts in memory
     L.ncs = o;  o += round4((size_t)K * ns);                  // contacts of each taped substep (int)
@@ -1136,8 +1136,9 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     const size_t tab_frame = (size_t)(ns + 1) * Lk * kLinkStride;
     const float4 *tab0 = a.link_tab + (size_t)a.frame0 * tab_frame;
 
-    // -- pass 1: the cost, the state at every K-th frame, and the substep
-    //    states and frame forces of the last segment (the first one reversed)
+    // -- pass 1: the cost, the state at every K-th frame, every frame's pad
+    //    forces, the substep states of the last segment (the first one
+    //    reversed) and its tape, and the contact records of the others
     const int f_last = (nck - 1) * a.K;
     double cost = 0.0;
     Body b = b0;
@@ -1169,8 +1170,7 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
             }
             fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero, -1);
         }
-        if (f >= f_last)
-            for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - f_last) * 3 * P + k] = S.padacc[k] * inv_ns;
+        for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)f * 3 * P + k] = S.padacc[k] * inv_ns;
         if (!all_finite(b.x, b.q, b.v, b.w)) st |= IH_ENV_NONFINITE;
         else if (dot(b.x, b.x) > cfg.escape_radius * cfg.escape_radius) st |= IH_ENV_ESCAPED;
         {   // frame cost in FP64, as the scored step: each pad's terms in parallel, summed in pad order
@@ -1226,9 +1226,9 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
     for (int seg = nck - 1; seg >= 0; --seg) {
         const int fb = seg * a.K, fe = min(a.H, fb + a.K);
         b = load_body(sp.ck + 4 * seg);
-        for (int f = fb; f < fe && seg < nck - 1; ++f) {   // substep start states and frame forces
-            for (int k = lane; k < 3 * P; k += T) S.padacc[k] = 0.0f;
-            G.sync();
+        // the segment's substep start states and tapes (its frames' pad forces
+        // are the first pass's)
+        for (int f = fb; f < fe && seg < nck - 1; ++f) {
             const float4 *tab = tab0 + (size_t)f * tab_frame;
             for (int s = 0; s < ns; ++s) {
                 const int blk = (f - fb) * ns + s;
@@ -1239,20 +1239,18 @@ __global__ void __launch_bounds__(kABlock) adjoint_kernel(const AdjArgs a) {
                     SlotPtr sq = sp.blk(blk);
                     sq.rec = sp.recs + (size_t)q * cap * 4;
                     const int nc = fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sq, S, PT, G, parity, st,
-                                                       1 | a.zero, 1 | a.zero, sp.nrc[q]);
+                                                       1 | a.zero, a.zero, sp.nrc[q]);
                     if (lane == 0) sp.ncs[blk] = nc;
                 } else {
-                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, 1 | a.zero,
+                    fwd_substep<GW, PL>(a, E, b, L0, L0 + Lk * kLinkStride, sp, S, PT, G, parity, st, a.zero, a.zero,
                                         -1);
                 }
             }
-            for (int k = lane; k < 3 * P; k += T) sp.sf[(size_t)(f - fb) * 3 * P + k] = S.padacc[k] * inv_ns;
-            G.sync();
         }
         for (int f = fe - 1; f >= fb; --f) {
             const float *o = a.obs + (size_t)f * P * 3;
             for (int k = lane; k < 3 * P; k += T)
-                S.fbar[k] = wf2 * (sp.sf[(size_t)(f - fb) * 3 * P + k] - o[k]);
+                S.fbar[k] = wf2 * (sp.sf[(size_t)f * 3 * P + k] - o[k]);
             G.sync();
             const float4 *tab = tab0 + (size_t)f * tab_frame;
             for (int s = ns - 1; s >= 0; --s) {
