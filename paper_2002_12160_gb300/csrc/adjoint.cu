@@ -239,11 +239,14 @@ __device__ __forceinline__ int rec_link(float4 r3) { return __float_as_int(r3.y)
 __device__ __forceinline__ int rec_pad(float4 r3) { return (__float_as_int(r3.y) >> 8) & 0xff; }
 
 // One substep of one environment (the arithmetic of step_kernel.cuh, contacts in the
-// same order: link, then sphere). With TAPE the impulses after every
-// iteration and the iteration sums are recorded in the slot's current tape
-// block; with PADS the pad forces of the substep are added to S.padacc.
-// Returns the contact count (0 on overflow). Not inlined, with the two flags
-// as arguments: every pass (cost, recomputation, tape) then runs the same
+// same order: link, then sphere), its contact records written at sp.rec.
+// With TAPE the impulses after every iteration and the iteration sums are
+// recorded in the slot's current tape block; with PADS the pad forces of the
+// substep are added to S.padacc; with replay_nc >= 0 the substep's records
+// at sp.rec are those of an earlier run from the same state (replay_nc
+// contacts, setup included), which replaces the enumeration and the setup.
+// Returns the contact count (0 on overflow). Not inlined, with the flags as
+// arguments: every pass (cost, recomputation, tape) then runs the same
 // compiled arithmetic, so a recorded tape is bit for bit the forward's.
 template <int GW, int PL>
 __device__ __noinline__ int fwd_substep(const AdjArgs &a, const Env &E_, Body &b, const float4 *L0,
