@@ -60,6 +60,7 @@ struct ih_sim {
     size_t adj_budget = (size_t)16 << 30;   // bytes of adjoint scratch for whole-segment taping
     bool adj_seg = false;
     int adj_gw = 0, adj_pl = 0;   // the adjoint kernel's shape (0, 0: automatic)
+    int iters_max_all = -1;       // the largest iteration count of any environment (-1: to be read)
     int *adj_word = nullptr;
     // gradient refinement: window-start snapshot, trial, best and end states (allocated on first use)
     bool rf_alloc = false, ws_valid = false;
@@ -349,6 +350,7 @@ ih_status sim_create(const ih_scene *sc, const ih_config *cfg, uint64_t seed, vo
     A(cudaMemcpyAsync(s->pad_s1, sc->pad_s1, P * sizeof(float), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->shape, shp0.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
     A(cudaMemcpyAsync(s->iters, it0.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    s->iters_max_all = cfg->iters;
     A(cudaMemsetAsync(s->pose, 0, 2 * (size_t)N * sizeof(float4), st));
     A(cudaMemsetAsync(s->vel, 0, 2 * (size_t)N * sizeof(float4), st));
     A(cudaMemsetAsync(s->params, 0, (size_t)N * sizeof(float2), st));
@@ -474,6 +476,7 @@ ih_status sim_set_state(ih_sim *s, const float *pose, const float *vel, const fl
         e = launch_hand_rest(s->cfg.n_envs, s->n_joints, s->frame_ready[0] ? s->cmd : nullptr, s->qj, s->qdj, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
     s->ws_valid = false;
+    if (iters) s->iters_max_all = -1;
     return IH_OK;
 }
 
@@ -1053,19 +1056,30 @@ namespace {
 // Size (and grow) the adjoint scratch for n slots: reads back the largest
 // iteration count among the selected environments (synchronises the stream).
 ih_status adjoint_prepare(ih_sim *s, int n, const int32_t *envs, int horizon, int K, size_t *stride, int *imax) {
+    (void)envs;
     cudaStream_t st = s->stream;
-    int m = 0;
-    cudaError_t e = launch_adjoint_iters_max(n, s->cfg.n_envs, envs, s->iters, s->adj_word, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, s->adj_word, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(s, e, "adjoint sizing");
+    cudaError_t e = cudaSuccess;
+    // the tape holds the iterations of the largest count of any environment
+    // (it bounds every selection's); read back only after sim_set_state set
+    // new counts, so that the calls in between need no synchronisation
+    if (s->iters_max_all < 0) {
+        int m = 0;
+        e = launch_adjoint_iters_max(s->cfg.n_envs, s->cfg.n_envs, nullptr, s->iters, s->adj_word, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&m, s->adj_word, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(s, e, "adjoint sizing");
+        s->iters_max_all = m;
+    }
+    const int m = s->iters_max_all;
     // tape whole segments when that fits the handle's budget, else substep by substep
     size_t str = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, m, true);
     bool seg = str * (size_t)n * sizeof(float) <= s->adj_budget;
     if (!seg) str = adjoint_scratch_floats(horizon, K, s->cfg.substeps, s->n_pads, s->cfg.c_max, m, false);
     const size_t need = str * (size_t)n;
     if (need > s->adj_floats) {
-        if (s->adj_scratch) cudaFree(s->adj_scratch);   // the stream is idle (synchronised above)
+        e = cudaStreamSynchronize(st);   // the old scratch may still be in use
+        if (e != cudaSuccess) return cuda_fail(s, e, "adjoint sizing");
+        if (s->adj_scratch) cudaFree(s->adj_scratch);
         s->adj_scratch = nullptr;
         s->adj_floats = 0;
         void *p = nullptr;
