@@ -89,7 +89,8 @@ struct ih_sim {
     // captured tracking window (replayed by sim_track_window)
     cudaGraphExec_t win_exec = nullptr;
     cudaStream_t cap_stream = nullptr;          // private stream: capture and replay
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t cap_side = nullptr;            // the window graph's second branch (capture only)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
     int win_T = 0;
     double *wf_cm = nullptr;        // [T][N] window means of every frame (window-mode launches)
     float4 *wf_pose = nullptr;      // [T][N][2] poses of every frame
@@ -405,8 +406,11 @@ ih_status sim_destroy(ih_sim *s) {
     cudaStreamSynchronize(s->stream);
     if (s->win_exec) cudaGraphExecDestroy(s->win_exec);
     if (s->cap_stream) { cudaStreamSynchronize(s->cap_stream); cudaStreamDestroy(s->cap_stream); }
+    if (s->cap_side) cudaStreamDestroy(s->cap_side);
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_out) cudaEventDestroy(s->ev_out);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     for (void *p : s->owned) cudaFree(p);
     if (s->adj_scratch) cudaFree(s->adj_scratch);
     if (s->spill) cudaFree(s->spill);
@@ -771,6 +775,9 @@ ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *ob
         e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(s, e, "window stream");
     }
     // the caller's stream -> private stream -> back, so ordering follows the caller's stream
@@ -790,7 +797,7 @@ ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *ob
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
         cudaError_t le = cudaSuccess;
-        {   // the window's T frames in one launch, then every frame's argmin and estimate
+        {   // the window's T frames in one launch
             StepArgs a = scored_args(s, frame0, nullptr, nullptr, nullptr, nullptr);
             a.win = s->win;
             a.win_k = 0;
@@ -798,15 +805,23 @@ ih_status sim_track_window(ih_sim *s, int32_t frame0, int32_t T, const float *ob
             a.cm_frames = s->wf_cm;
             a.pose_frames = s->wf_pose;
             le = launch_step(a, s->variant, s->step_grid, s->s_max, st);
-            if (le == cudaSuccess)
-                le = launch_window_argmin(s->cfg.n_envs, T, s->wf_cm, s->wf_pose, s->win, nullptr, nullptr, s->argmin,
-                                          s->n_window, st);
         }
+        // then two branches: every frame's argmin and estimate (from the frame
+        // buffers, which nothing else writes) beside the optimizer update; the
+        // update sets the handle's i* and restarts the window count, so the
+        // argmin branch leaves both alone
+        if (le == cudaSuccess) le = cudaEventRecord(s->ev_fork, st);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(s->cap_side, s->ev_fork, 0);
+        if (le == cudaSuccess)
+            le = launch_window_argmin(s->cfg.n_envs, T, s->wf_cm, s->wf_pose, s->win, nullptr, nullptr, nullptr,
+                                      nullptr, s->cap_side);
         if (le == cudaSuccess) {
             OptArgs oa = opt_args(s, opt, update_index, nullptr, nullptr);
             oa.win = s->win;
             le = launch_optimizer(oa, st);
         }
+        if (le == cudaSuccess) le = cudaEventRecord(s->ev_join, s->cap_side);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(st, s->ev_join, 0);
         e = cudaStreamEndCapture(st, &g);
         if (le != cudaSuccess || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);

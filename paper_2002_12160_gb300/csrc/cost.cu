@@ -204,7 +204,8 @@ cudaError_t launch_cost(const CostArgs &a, cudaStream_t s) {
 namespace {
 // One block per frame of a window-mode launch: the lowest (C_i, i) of that
 // frame's window means (NaN = +inf), the pose of that environment after the
-// frame, and -- for the window's last frame -- the handle's i*.
+// frame, and -- for the window's last frame, when argmin_state is set -- the
+// handle's i*.
 __global__ void __launch_bounds__(1024) window_argmin_kernel(int N, int T, const double *cm_frames,
                                                               const float4 *pose_frames, const WinDesc *win,
                                                               int *argmin_out, float *est_out, int *argmin_state,
@@ -243,8 +244,8 @@ __global__ void __launch_bounds__(1024) window_argmin_kernel(int N, int T, const
             best_s = best;
             int *am = win ? win->argmin : argmin_out;
             if (am) am[f] = best;
-            if (f == T - 1) *argmin_state = best;
-            if (f == 0) *n_window += T;
+            if (f == T - 1 && argmin_state) *argmin_state = best;
+            if (f == 0 && n_window) *n_window += T;
         }
     }
     __syncthreads();

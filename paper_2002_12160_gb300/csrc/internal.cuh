@@ -142,11 +142,31 @@ __device__ __forceinline__ void gauss2(uint4 w, double &z0, double &z1) {
     z1 = rad * s;
 }
 
-// FP64 so(3) maps on (w, x, y, z) quaternions
+// FP64 so(3) maps on (w, x, y, z) quaternions. FP64 instructions are scarce
+// on this part (each warp instruction holds the pipe for many cycles), so the
+// maps keep their count down: below a rotation of 1 rad the exponential's two
+// factors come from their Taylor series, and each map divides once at most.
 struct Q4d { double w, x, y, z; };
 __device__ __forceinline__ Q4d qexp_d(double x, double y, double z) {
-    const double th = sqrt(x * x + y * y + z * z);
-    if (th < 1e-300) return {1.0, 0.0, 0.0, 0.0};
+    const double t2 = x * x + y * y + z * z;
+    if (t2 < 1.0) {
+        // with u = (th / 2)^2 <= 1/4: cos(th / 2) = sum_n (-u)^n / (2n)! and
+        // sin(th / 2) / th = (1/2) sum_n (-u)^n / (2n + 1)!, n <= 8 (the first
+        // omitted terms are below 1e-18 of the sums)
+        const double u = 0.25 * t2;
+        double c = 1.0 / 20922789888000.0, sk = 1.0 / 355687428096000.0;   // 1/16!, 1/17!
+        c = fma(c, -u, 1.0 / 87178291200.0);   sk = fma(sk, -u, 1.0 / 1307674368000.0);   // 1/14!, 1/15!
+        c = fma(c, -u, 1.0 / 479001600.0);     sk = fma(sk, -u, 1.0 / 6227020800.0);      // 1/12!, 1/13!
+        c = fma(c, -u, 1.0 / 3628800.0);       sk = fma(sk, -u, 1.0 / 39916800.0);        // 1/10!, 1/11!
+        c = fma(c, -u, 1.0 / 40320.0);         sk = fma(sk, -u, 1.0 / 362880.0);          // 1/8!, 1/9!
+        c = fma(c, -u, 1.0 / 720.0);           sk = fma(sk, -u, 1.0 / 5040.0);            // 1/6!, 1/7!
+        c = fma(c, -u, 1.0 / 24.0);            sk = fma(sk, -u, 1.0 / 120.0);             // 1/4!, 1/5!
+        c = fma(c, -u, 0.5);                   sk = fma(sk, -u, 1.0 / 6.0);               // 1/2!, 1/3!
+        c = fma(c, -u, 1.0);                   sk = fma(sk, -u, 1.0);
+        const double k = 0.5 * sk;
+        return {c, x * k, y * k, z * k};
+    }
+    const double th = sqrt(t2);
     double s, c;
     sincos(0.5 * th, &s, &c);
     const double k = s / th;
@@ -159,15 +179,15 @@ __device__ __forceinline__ Q4d qmul_d(Q4d a, Q4d b) {
             a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
 }
 __device__ __forceinline__ Q4d qnorm_d(Q4d q) {
-    const double n = sqrt(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
-    return {q.w / n, q.x / n, q.y / n, q.z / n};
+    const double r = rsqrt(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+    return {q.w * r, q.x * r, q.y * r, q.z * r};
 }
 __device__ __forceinline__ void qlog_d(Q4d q, double out[3]) {
     if (q.w < 0) { q.w = -q.w; q.x = -q.x; q.y = -q.y; q.z = -q.z; }
     const double s = sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
     if (s < 1e-300) { out[0] = out[1] = out[2] = 0.0; return; }
-    const double th = 2.0 * atan2(s, q.w);
-    out[0] = q.x * th / s; out[1] = q.y * th / s; out[2] = q.z * th / s;
+    const double k = 2.0 * atan2(s, q.w) / s;
+    out[0] = q.x * k; out[1] = q.y * k; out[2] = q.z * k;
 }
 
 // ---------------------------------------------------------------- launches
@@ -339,6 +359,7 @@ int cost_blocks(int N);
 // argmin and estimate of every frame of a window-mode step launch (outputs from
 // win when set, else argmin_out [T] / est_out [T][8], either may be null);
 // advances the window counter by T and sets the handle's i* to the last frame's
+// (each skipped when its pointer is null)
 cudaError_t launch_window_argmin(int N, int T, const double *cm_frames, const float4 *pose_frames,
                                  const WinDesc *win, int *argmin_out, float *est_out, int *argmin_state,
                                  int *n_window, cudaStream_t s);

@@ -32,9 +32,18 @@ constexpr int kFin = 128;             // threads of the finalize kernel
 
 enum { M_K = 64, M_U, M_ISTAR, M_OK, M_WSUM, M_CMIN, M_SD, M_NFIN, M_NBLK };
 
+// NaN and finiteness tests on the bits (integer instructions: FP64 compares
+// take the scarce FP64 pipe)
+__device__ __forceinline__ bool nan_bits(double c) {
+    return ((unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool finite_bits(double c) {
+    return ((unsigned long long)__double_as_longlong(c) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 __device__ __forceinline__ unsigned long long order_key(double c) {
-    if (isnan(c)) c = INFINITY;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(c);
+    const unsigned long long b =
+        nan_bits(c) ? 0x7ff0000000000000ull : (unsigned long long)__double_as_longlong(c);   // NaN = +inf
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
@@ -88,12 +97,19 @@ __device__ double block_sum(double v, double *red) {
 template <int NT>
 __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     constexpr int kSel = NT, kWarps = NT / 32;
+    // the small instance (N <= kKeys kSelSmall) stages the window means and
+    // the elite list in shared memory; the large one reads them from global
+    // memory (read-only here: c_mean through the non-coherent path)
+    constexpr bool kStage = NT == kSelSmall;
+    __shared__ double s_cost[kStage ? kKeys * kSelSmall : 1];
+    __shared__ int s_elite[kStage ? kKeys * kSelSmall : 1];
     __shared__ unsigned int hist[256];
     __shared__ unsigned long long s_prefix, s_mask;
     __shared__ unsigned int s_rem;
     __shared__ int s_done;
     __shared__ unsigned int s_scan[kWarps + 1];
     __shared__ double red[kWarps];
+    __shared__ int s_cnt[kWarps];
     __shared__ double s_val[2];
     __shared__ unsigned long long s_min_key;
     __shared__ int s_min_idx;
@@ -103,16 +119,48 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     k = max(1, min(k, N));
     const int chunk = (N + kSel - 1) / kSel;
     const int lo = min(N, t * chunk), hi = min(N, lo + chunk);
+    auto cost = [&](int i) -> double {
+        if constexpr (kStage) return s_cost[i];
+        else return __ldg(a.c_mean + i);
+    };
 
-    // ---- radix select of the k-th smallest key (keys held in registers when N <= 8 kSel)
+    // ---- keys (held in registers when N <= 8 kSel) and i* = smallest (key, index)
     const bool in_regs = N <= kKeys * kSel;
     unsigned long long kreg[kKeys];
+    unsigned long long bk = ~0ull;
+    int bi = 0x7fffffff;
 #pragma unroll
     for (int q = 0; q < kKeys; ++q) {
         const int i = t + q * kSel;
-        kreg[q] = (in_regs && i < N) ? order_key(a.c_mean[i]) : 0ull;
+        kreg[q] = 0ull;
+        if (in_regs && i < N) {
+            const double c = __ldg(a.c_mean + i);
+            if constexpr (kStage) s_cost[i] = c;
+            kreg[q] = order_key(c);
+            if (kreg[q] < bk) { bk = kreg[q]; bi = i; }   // (i ascending: the first of equal keys)
+        }
     }
-    if (t == 0) { s_prefix = 0ull; s_mask = 0ull; s_rem = (unsigned)k; s_done = 0; }
+    if (!in_regs) {
+        for (int i = t; i < N; i += kSel) {
+            const unsigned long long key = order_key(__ldg(a.c_mean + i));
+            if (key < bk) { bk = key; bi = i; }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ok < bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+    }
+    if (t == 0) {
+        s_min_key = ~0ull; s_min_idx = 0x7fffffff;
+        s_prefix = 0ull; s_mask = 0ull; s_rem = (unsigned)k; s_done = 0;
+    }
+    __syncthreads();
+    if ((t & 31) == 0) atomicMin(&s_min_key, bk);
+    __syncthreads();
+    if ((t & 31) == 0 && bk == s_min_key) atomicMin(&s_min_idx, bi);
+
+    // ---- radix select of the k-th smallest key
     // The passes stop early once every key whose leading digits equal the
     // prefix found so far is needed: the elites are then exactly the keys whose
     // leading digits are at most the prefix, whatever their remaining digits.
@@ -135,7 +183,7 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
         } else {
             for (int i0 = 0; i0 < N; i0 += kSel) {
                 const int i = i0 + t;
-                count(i < N, i < N ? order_key(a.c_mean[i]) : 0ull);
+                count(i < N, i < N ? order_key(__ldg(a.c_mean + i)) : 0ull);
             }
         }
         __syncthreads();
@@ -176,75 +224,80 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     }
     const unsigned long long T = s_prefix, M = s_mask;   // M: the digits decided (all 64 after 8 passes)
     const unsigned need_eq = s_rem;   // elites among the keys whose digits under M equal T, lowest index first
+    const int istar = s_min_idx;
 
-    // ---- elite flags in index order
+    // ---- elite flags in index order (the flag of a key equal to T under M
+    // depends on the equal keys before it), then ranks: elites and non-elites
+    // each numbered in index order
     unsigned eq_local = 0;
-    for (int i = lo; i < hi; ++i) eq_local += ((order_key(a.c_mean[i]) & M) == T);
-    unsigned eq_before = block_scan<NT>(eq_local, s_scan) - eq_local;
+    for (int i = lo; i < hi; ++i) eq_local += ((order_key(cost(i)) & M) == T);
+    const unsigned eq0 = block_scan<NT>(eq_local, s_scan) - eq_local;
     unsigned el_local = 0;
-    for (int i = lo; i < hi; ++i) {
-        const unsigned long long key = order_key(a.c_mean[i]) & M;
-        bool e = key < T;
-        if (key == T) { e = eq_before < need_eq; ++eq_before; }
-        a.is_elite[i] = e;
-        el_local += e;
+    {
+        unsigned eqb = eq0;
+        for (int i = lo; i < hi; ++i) {
+            const unsigned long long key = order_key(cost(i)) & M;
+            const bool e = key < T || (key == T && eqb++ < need_eq);
+            a.is_elite[i] = e;
+            el_local += e;
+        }
     }
     {
         unsigned er = block_scan<NT>(el_local, s_scan) - el_local;   // elites before my chunk
         unsigned nr = (unsigned)lo - er;                          // non-elites before my chunk
+        unsigned eqb = eq0;
         for (int i = lo; i < hi; ++i) {
-            if (a.is_elite[i]) { a.rank[i] = (int)er; a.elite_env[er] = i; ++er; }
-            else { a.rank[i] = (int)nr; ++nr; }
+            const unsigned long long key = order_key(cost(i)) & M;
+            if (key < T || (key == T && eqb++ < need_eq)) {
+                a.rank[i] = (int)er;
+                a.elite_env[er] = i;
+                if constexpr (kStage) s_elite[er] = i;
+                ++er;
+            } else {
+                a.rank[i] = (int)nr;
+                ++nr;
+            }
         }
     }
-
-    // ---- i* = smallest (key, index)
-    unsigned long long bk = ~0ull;
-    int bi = 0x7fffffff;
-    for (int i = t; i < N; i += kSel) {
-        const unsigned long long key = order_key(a.c_mean[i]);
-        if (key < bk || (key == bk && i < bi)) { bk = key; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ok < bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
-    }
-    if (t == 0) { s_min_key = ~0ull; s_min_idx = 0x7fffffff; }
-    __syncthreads();
-    if ((t & 31) == 0) atomicMin(&s_min_key, bk);
-    __syncthreads();
-    if ((t & 31) == 0 && bk == s_min_key) atomicMin(&s_min_idx, bi);
-    __syncthreads();
-    const int istar = s_min_idx;
+    __syncthreads();   // the elite list (global and staged) is complete
+    auto elite = [&](int j) -> int {
+        if constexpr (kStage) return s_elite[j];
+        else return a.elite_env[j];
+    };
 
     // ---- mean and population standard deviation of the finite elite costs
-    double sum = 0.0, cnt = 0.0;
+    double sum = 0.0;
+    int cnt = 0;
     for (int j = t; j < k; j += kSel) {
-        const double c = a.c_mean[a.elite_env[j]];
-        if (isfinite(c)) { sum += c; cnt += 1.0; }
+        const double c = cost(elite(j));
+        if (finite_bits(c)) { sum += c; ++cnt; }
     }
-    __syncthreads();
     const double tot = block_sum<NT>(sum, red);
-    const double nfin = block_sum<NT>(cnt, red);
-    if (t == 0) { s_val[0] = tot; s_val[1] = nfin; }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((t & 31) == 0) s_cnt[t >> 5] = cnt;
+    __syncthreads();
+    if (t == 0) {
+        int nf = 0;
+        for (int w = 0; w < kWarps; ++w) nf += s_cnt[w];
+        s_val[0] = tot; s_val[1] = (double)nf;
+    }
     __syncthreads();
     const double mean = s_val[1] > 0 ? s_val[0] / s_val[1] : 0.0;
     double sq = 0.0;
     for (int j = t; j < k; j += kSel) {
-        const double c = a.c_mean[a.elite_env[j]];
-        if (isfinite(c)) sq += (c - mean) * (c - mean);
+        const double c = cost(elite(j));
+        if (finite_bits(c)) sq += (c - mean) * (c - mean);
     }
     const double ss = block_sum<NT>(sq, red);
     if (t == 0) {
         const double nf = s_val[1];
-        const double c0 = a.c_mean[istar];
+        const double c0 = cost(istar);
         a.misc[M_K] = (double)k;
         const uint32_t upd = a.win ? a.win->update_index : a.update_index;
         const uint4 uw = rng_words(a.seed, 2, upd, 0, 0);
         a.misc[M_U] = unit53(uw.x, uw.y);
         a.misc[M_ISTAR] = (double)istar;
-        a.misc[M_CMIN] = isnan(c0) ? INFINITY : c0;
+        a.misc[M_CMIN] = nan_bits(c0) ? INFINITY : c0;
         a.misc[M_SD] = nf > 0 ? sqrt(ss / nf) : 0.0;
         a.misc[M_NFIN] = nf;
         *a.argmin_state = istar;
@@ -368,7 +421,9 @@ __global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nbl
     __syncthreads();
     // Cholesky by the first warp: lane i < 8 holds row i of L; column j in
     // turn, s = C_ij - sum_{m<j} L_im L_jm in m order, L_jj = sqrt(s_jj),
-    // L_ij = s_ij / L_jj
+    // L_ij = s_ij / L_jj, both through one reciprocal square root r = 1/L_jj
+    // (L_jj = s_jj r, L_ij = s_ij r: the column's chain of scarce FP64
+    // instructions is then one rsqrt long instead of a sqrt and a division)
     if (wid == 0) {
         double L[8];
 #pragma unroll
@@ -386,9 +441,9 @@ __global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nbl
             }
             const double djj = __shfl_sync(0xffffffffu, sj, j);
             if (!(djj > 0.0)) ok = false;
-            const double ljj = ok ? sqrt(djj) : 0.0;
-            if (row && i == j) L[j] = ljj;
-            else if (row && i > j) L[j] = ok ? sj / ljj : 0.0;
+            const double rj = ok ? rsqrt(djj) : 0.0;
+            if (row && i == j) L[j] = djj * rj;
+            else if (row && i > j) L[j] = sj * rj;
         }
         if (!ok) {
 #pragma unroll
