@@ -81,15 +81,19 @@ __device__ unsigned block_scan(unsigned v, unsigned *buf) {
     return r;
 }
 
+// block sum of one double per thread, where only the first nw warps can hold
+// nonzero values (the others issue no FP64 work): warp sums, then the warps'
+// partials in warp order by thread 0 (the omitted partials are zeros)
 template <int NT>
-__device__ double block_sum(double v, double *red) {
-    constexpr int kWarps = NT / 32;
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+__device__ double block_sum(double v, double *red, int nw = NT / 32) {
+    if ((int)(threadIdx.x >> 5) < nw) {
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    }
     __syncthreads();
     double s = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < kWarps; ++w) s += red[w];
+        for (int w = 0; w < nw; ++w) s += red[w];
     __syncthreads();
     return s;   // valid in thread 0
 }
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     __shared__ unsigned int s_scan[kWarps + 1];
     __shared__ double red[kWarps];
     __shared__ int s_cnt[kWarps];
-    __shared__ double s_val[2];
+    __shared__ double s_val[3];
     __shared__ unsigned long long s_min_key;
     __shared__ int s_min_idx;
 
@@ -266,13 +270,15 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     };
 
     // ---- mean and population standard deviation of the finite elite costs
+    // (the warps past the elites hold zeros and skip the sums)
+    const int nw = min(kWarps, (k + 31) / 32);
     double sum = 0.0;
     int cnt = 0;
     for (int j = t; j < k; j += kSel) {
         const double c = cost(elite(j));
         if (finite_bits(c)) { sum += c; ++cnt; }
     }
-    const double tot = block_sum<NT>(sum, red);
+    const double tot = block_sum<NT>(sum, red, nw);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     if ((t & 31) == 0) s_cnt[t >> 5] = cnt;
     __syncthreads();
@@ -280,15 +286,16 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
         int nf = 0;
         for (int w = 0; w < kWarps; ++w) nf += s_cnt[w];
         s_val[0] = tot; s_val[1] = (double)nf;
+        s_val[2] = nf > 0 ? tot / (double)nf : 0.0;   // the mean, divided once
     }
     __syncthreads();
-    const double mean = s_val[1] > 0 ? s_val[0] / s_val[1] : 0.0;
+    const double mean = s_val[2];
     double sq = 0.0;
     for (int j = t; j < k; j += kSel) {
         const double c = cost(elite(j));
         if (finite_bits(c)) sq += (c - mean) * (c - mean);
     }
-    const double ss = block_sum<NT>(sq, red);
+    const double ss = block_sum<NT>(sq, red, nw);
     if (t == 0) {
         const double nf = s_val[1];
         const double c0 = cost(istar);
@@ -305,61 +312,96 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     }
 }
 
-// One thread per elite (in index order).
-__global__ void __launch_bounds__(kOptBlock) stats_kernel(const OptArgs a) {
-    const int j = blockIdx.x * kOptBlock + threadIdx.x;
+// One elite per lane (index order), kOptBlock elites per block, four warps:
+// the weight and its in-block prefix (warp 0), the rotation offset through the
+// FP64 log map (warp 1) and the other offsets (warp 2) are formed side by
+// side, then each warp forms a quarter of the 45 moment products. FP64
+// instructions are scarce on this part; split so, each warp issues few.
+constexpr int kStatWarps = 4;
+// the factors of moment q: (a << 4) | b, with w = w e_0 e_0, w d_r = w e_{1+r}
+// e_0 and w d_r d_c = w e_{1+r} e_{1+c} (c <= r) in the order of kMoments
+__constant__ unsigned char c_mom_ab[kMoments] = {
+    0x00, 0x10, 0x20, 0x30, 0x40, 0x50, 0x60, 0x70, 0x80,
+    0x11,
+    0x21, 0x22,
+    0x31, 0x32, 0x33,
+    0x41, 0x42, 0x43, 0x44,
+    0x51, 0x52, 0x53, 0x54, 0x55,
+    0x61, 0x62, 0x63, 0x64, 0x65, 0x66,
+    0x71, 0x72, 0x73, 0x74, 0x75, 0x76, 0x77,
+    0x81, 0x82, 0x83, 0x84, 0x85, 0x86, 0x87, 0x88};
+__global__ void __launch_bounds__(kOptBlock * kStatWarps) stats_kernel(const OptArgs a) {
+    __shared__ double s_w[kOptBlock];
+    __shared__ double s_d[kOptBlock][9];   // (1, offsets): moment q = w e_{a(q)} e_{b(q)}
+    __shared__ double tm[kOptBlock][kMoments + 1];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int j = blockIdx.x * kOptBlock + lane;
     const int k = (int)a.misc[M_K];
     const int istar = (int)a.misc[M_ISTAR];
-    const double cmin = a.misc[M_CMIN], sd = a.misc[M_SD], nfin = a.misc[M_NFIN];
-    double mom[kMoments];
+    const bool valid = j < k;
+    const int e = valid ? a.elite_env[j] : 0;
+    if (wq == 0) {   // w = exp(-(C - C_min)/s)
+        const double cmin = a.misc[M_CMIN], sd = a.misc[M_SD], nfin = a.misc[M_NFIN];
+        double w = 0.0;
+        if (valid) {
+            const double c = a.c_mean[e];
+            if (nfin == 0.0) w = 1.0;
+            else if (!finite_bits(c)) w = 0.0;
+            else if (!(sd >= 1e-12)) w = 1.0;
+            else w = exp(-(c - cmin) / sd);
+        }
+        s_w[lane] = w;
+        // inclusive prefix of w within the block (index order), and the block total
+        double pre = w;
 #pragma unroll
-    for (int q = 0; q < kMoments; ++q) mom[q] = 0.0;
-    double w = 0.0;
-    if (j < k) {
-        const int e = a.elite_env[j];
-        const double c = a.c_mean[e];
-        if (nfin == 0.0) w = 1.0;
-        else if (!isfinite(c)) w = 0.0;
-        else if (!(sd >= 1e-12)) w = 1.0;
-        else w = exp(-(c - cmin) / sd);
-        if (w > 0.0) {
-            const float4 p0 = a.pose[2 * e], p1 = a.pose[2 * e + 1];
-            const float4 r0 = a.pose[2 * istar], r1 = a.pose[2 * istar + 1];
-            const float2 th = a.params[e], tr = a.params[istar];
-            double lr[3];
+        for (int o = 1; o < 32; o <<= 1) {
+            const double v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        if (valid) a.elite_w[j] = pre;
+        if (lane == 31) a.block_w[blockIdx.x] = pre;
+    } else if (wq == 1) {   // log(R R_{i*}^T): the offset of the rotation coordinate (0 at i*)
+        double lr[3] = {0.0, 0.0, 0.0};
+        if (valid) {
+            const float4 p1 = a.pose[2 * e + 1], r1 = a.pose[2 * istar + 1];
             qlog_d(qmul_d({p1.x, p1.y, p1.z, p1.w}, {r1.x, -r1.y, -r1.z, -r1.w}), lr);
-            // offsets from z_{i*} (whose rotation coordinate is 0)
-            const double d[8] = {(double)p0.x - r0.x, (double)p0.y - r0.y, (double)p0.z - r0.z,
-                                 lr[0], lr[1], lr[2], (double)th.x - tr.x, (double)th.y - tr.y};
-            mom[0] = w;
+        }
+        s_d[lane][4] = lr[0]; s_d[lane][5] = lr[1]; s_d[lane][6] = lr[2];
+    } else if (wq == 2) {   // position, mass and friction offsets from z_{i*}
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d6 = 0.0, d7 = 0.0;
+        if (valid) {
+            const float4 p0 = a.pose[2 * e], r0 = a.pose[2 * istar];
+            const float2 th = a.params[e], tr = a.params[istar];
+            d0 = (double)p0.x - r0.x; d1 = (double)p0.y - r0.y; d2 = (double)p0.z - r0.z;
+            d6 = (double)th.x - tr.x; d7 = (double)th.y - tr.y;
+        }
+        s_d[lane][0] = 1.0;
+        s_d[lane][1] = d0; s_d[lane][2] = d1; s_d[lane][3] = d2; s_d[lane][7] = d6; s_d[lane][8] = d7;
+    }
+    __syncthreads();
+    // moments (w, w d, w d d^T lower triangle; zero for an elite of weight 0):
+    // moment q = (w e_a) e_b with e = (1, d), warp wq forming q = wq, wq + 4, ...
+    // (the same code on every warp: no divergent branches to serialise)
+    {
+        const double w = s_w[lane];
+        const bool pos = valid && w > 0.0;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) mom[1 + r] = w * d[r];
-            int q = 9;
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int cc = 0; cc <= r; ++cc) mom[q++] = w * d[r] * d[cc];
+        for (int m = 0; m < (kMoments + kStatWarps - 1) / kStatWarps; ++m) {
+            const int q = wq + kStatWarps * m;
+            if (q < kMoments) {
+                const int ab = c_mom_ab[q];
+                const double v = w * s_d[lane][ab >> 4] * s_d[lane][ab & 15];
+                tm[lane][q] = pos ? v : 0.0;
+            }
         }
     }
-    // inclusive prefix of w within the block (index order), and the block total
-    double pre = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double v = __shfl_up_sync(0xffffffffu, pre, o);
-        if ((int)threadIdx.x >= o) pre += v;
-    }
-    if (j < k) a.elite_w[j] = pre;
-    if (threadIdx.x == 31) a.block_w[blockIdx.x] = pre;
-    // block sums of the moments: transposed through shared memory, moment q
-    // summed over the block's threads in index order by thread q
-    __shared__ double tm[kOptBlock][kMoments + 1];
-#pragma unroll
-    for (int q = 0; q < kMoments; ++q) tm[threadIdx.x][q] = mom[q];
     __syncthreads();
-    for (int q = threadIdx.x; q < kMoments; q += kOptBlock) {
+    // block sums of the moments: moment q summed over the block's elites in
+    // index order by thread q
+    if (threadIdx.x < kMoments) {
         double sacc = 0.0;
-        for (int r = 0; r < kOptBlock; ++r) sacc += tm[r][q];
-        a.moments[(size_t)blockIdx.x * kMoments + q] = sacc;
+        for (int r = 0; r < kOptBlock; ++r) sacc += tm[r][threadIdx.x];
+        a.moments[(size_t)blockIdx.x * kMoments + threadIdx.x] = sacc;
     }
 }
 
@@ -369,7 +411,12 @@ __global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nbl
     __shared__ double cv[8][8];
     __shared__ double wtot[32];
     __shared__ double s_carry;
+    __shared__ double nm[kMoments];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    // up to 32 blocks the first warp scans their weight sums alone (loaded
+    // here, beside the moments)
+    const bool one_warp = nblocks <= 32;
+    const double vw = (one_warp && t < nblocks) ? a.block_w[t] : 0.0;
     // moments: thread q < 45 sums its moment over the blocks in block order
     if (t < kMoments) {
         double s = 0.0;
@@ -380,7 +427,18 @@ __global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nbl
     // warp scans, then the warp totals in warp order by the first warp
     if (t == 0) s_carry = 0.0;
     __syncthreads();
-    for (int base = 0; base < nblocks; base += kSel) {
+    if (one_warp && wid == 0) {
+        double inc = vw;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (t < nblocks) a.block_w[t] = inc - vw;
+        const double total = __shfl_sync(0xffffffffu, inc, 31);
+        if (lane == 0) s_carry = total;
+    }
+    for (int base = 0; base < nblocks && !one_warp; base += kSel) {
         const int b = base + t;
         const double v = (b < nblocks) ? a.block_w[b] : 0.0;
         double inc = v;
@@ -408,13 +466,16 @@ __global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nbl
         if (t == 0) s_carry = carry + wtot[kWarps - 1];
         __syncthreads();
     }
-    // weighted covariance (36 entries in parallel) plus the floor
+    // weighted covariance (36 entries in parallel) plus the floor, from the
+    // moments divided by the weight sum once each
     const double wsum = sm[0];
+    if (t >= 1 && t < kMoments) nm[t] = sm[t] / wsum;
+    __syncthreads();
     if (t < 64) {
         const int r = t >> 3, c = t & 7;
         const int hi = r > c ? r : c, lo = r > c ? c : r;
-        const double mr = sm[1 + r] / wsum, mc = sm[1 + c] / wsum;
-        double v = sm[9 + hi * (hi + 1) / 2 + lo] / wsum - mr * mc;
+        const double mr = nm[1 + r], mc = nm[1 + c];
+        double v = nm[9 + hi * (hi + 1) / 2 + lo] - mr * mc;
         if (r == c) v += a.floor_var[r];
         cv[r][c] = v;
     }
@@ -494,6 +555,11 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
     if (sub == 0 && a.cache_n) a.cache_n[i] = 0;   // replaced: its solver starts cold
     const bool ok = a.misc[M_OK] != 0.0;
     int par = 0;
+    // the parent's state, requested as soon as the parent is known (elites
+    // are never written here)
+    float4 pp0, pp1, pv0, pv1;
+    float2 pth;
+    int pst;
     if (sub == 0) {
         const double u = a.misc[M_U], wsum = a.misc[M_WSUM];
         const int M = N - k;
@@ -506,6 +572,10 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
         }
         par = a.elite_env[lo];
         if (a.parent_out) a.parent_out[i] = par;
+        pp0 = a.pose[2 * par]; pp1 = a.pose[2 * par + 1];
+        pv0 = a.vel[2 * par]; pv1 = a.vel[2 * par + 1];
+        pth = a.params[par];
+        pst = a.status[par];
     }
     if (!ok) return;
     double e0, e1;
@@ -532,17 +602,17 @@ __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const Op
         d[2 * b + 1] = __shfl_sync(qmask, dr[1], b, kApplyLanes);
     }
     if (sub != 0) return;
-    const float4 p0 = a.pose[2 * par], p1 = a.pose[2 * par + 1];
+    const float4 p0 = pp0, p1 = pp1;
     const Q4d qn = qnorm_d(qmul_d(qexp_d(d[3], d[4], d[5]), {p1.x, p1.y, p1.z, p1.w}));
     a.pose[2 * i] = make_float4((float)(p0.x + d[0]), (float)(p0.y + d[1]), (float)(p0.z + d[2]), 0.0f);
     a.pose[2 * i + 1] = make_float4((float)qn.w, (float)qn.x, (float)qn.y, (float)qn.z);
-    a.vel[2 * i] = a.vel[2 * par];
-    a.vel[2 * i + 1] = a.vel[2 * par + 1];
-    const float2 th = a.params[par];
+    a.vel[2 * i] = pv0;
+    a.vel[2 * i + 1] = pv1;
+    const float2 th = pth;
     const double m = fmin(fmax((double)th.x + d[6], (double)a.m_lo), (double)a.m_hi);
     const double mu = fmin(fmax((double)th.y + d[7], (double)a.mu_lo), (double)a.mu_hi);
     a.params[i] = make_float2((float)m, (float)mu);
-    a.status[i] = a.status[par];
+    a.status[i] = pst;
     if (a.qj) {   // the parent's hand (elites are not written by this kernel)
         const int D = a.D;
         for (int j = 0; j < D; ++j) {
@@ -895,7 +965,7 @@ cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
     const int kb = opt_blocks(k), nb = opt_blocks(a.N);
     if (a.N <= kKeys * kSelSmall) select_kernel<kSelSmall><<<1, kSelSmall, 0, s>>>(a);
     else select_kernel<kSel><<<1, kSel, 0, s>>>(a);
-    stats_kernel<<<kb, kOptBlock, 0, s>>>(a);
+    stats_kernel<<<kb, kOptBlock * kStatWarps, 0, s>>>(a);
     finalize_kernel<<<1, kFin, 0, s>>>(a, kb);
     apply_kernel<<<nb, kOptBlock * kApplyLanes, 0, s>>>(a);
     return cudaGetLastError();
