@@ -32,6 +32,27 @@ constexpr int kFin = 128;             // threads of the finalize kernel
 
 enum { M_K = 64, M_U, M_ISTAR, M_OK, M_WSUM, M_CMIN, M_SD, M_NFIN, M_NBLK };
 
+// Programmatic dependent launch: the kernels of the update are launched so
+// that each may be scheduled while the one before it drains; each waits here,
+// before its first read of that kernel's results, until it has completed and
+// its writes are visible (at once when launched without the dependency).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*k)(P...), int grid, int block, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(grid);
+    c.blockDim = dim3(block);
+    c.dynamicSmemBytes = 0;
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    return cudaLaunchKernelEx(&c, k, args...);
+}
+
 // NaN and finiteness tests on the bits (integer instructions: FP64 compares
 // take the scarce FP64 pipe)
 __device__ __forceinline__ bool nan_bits(double c) {
@@ -118,9 +139,16 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     __shared__ unsigned long long s_min_key;
     __shared__ int s_min_idx;
 
+    grid_dependency_wait();
     const int N = a.N, t = threadIdx.x;
     int k = (int)floor((double)a.elite_frac * (double)N);
     k = max(1, min(k, N));
+    if (t == 0) {   // the elite count and the resampling offset, off the critical path
+        const uint32_t upd = a.win ? a.win->update_index : a.update_index;
+        const uint4 uw = rng_words(a.seed, 2, upd, 0, 0);
+        a.misc[M_K] = (double)k;
+        a.misc[M_U] = unit53(uw.x, uw.y);
+    }
     const int chunk = (N + kSel - 1) / kSel;
     const int lo = min(N, t * chunk), hi = min(N, lo + chunk);
     auto cost = [&](int i) -> double {
@@ -299,10 +327,6 @@ __global__ void __launch_bounds__(NT) select_kernel(const OptArgs a) {
     if (t == 0) {
         const double nf = s_val[1];
         const double c0 = cost(istar);
-        a.misc[M_K] = (double)k;
-        const uint32_t upd = a.win ? a.win->update_index : a.update_index;
-        const uint4 uw = rng_words(a.seed, 2, upd, 0, 0);
-        a.misc[M_U] = unit53(uw.x, uw.y);
         a.misc[M_ISTAR] = (double)istar;
         a.misc[M_CMIN] = nan_bits(c0) ? INFINITY : c0;
         a.misc[M_SD] = nf > 0 ? sqrt(ss / nf) : 0.0;
@@ -334,6 +358,7 @@ __global__ void __launch_bounds__(kOptBlock * kStatWarps) stats_kernel(const Opt
     __shared__ double s_w[kOptBlock];
     __shared__ double s_d[kOptBlock][9];   // (1, offsets): moment q = w e_{a(q)} e_{b(q)}
     __shared__ double tm[kOptBlock][kMoments + 1];
+    grid_dependency_wait();
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int j = blockIdx.x * kOptBlock + lane;
     const int k = (int)a.misc[M_K];
@@ -412,6 +437,7 @@ __global__ void __launch_bounds__(kFin) finalize_kernel(const OptArgs a, int nbl
     __shared__ double wtot[32];
     __shared__ double s_carry;
     __shared__ double nm[kMoments];
+    grid_dependency_wait();
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     // up to 32 blocks the first warp scans their weight sums alone (loaded
     // here, beside the moments)
@@ -533,6 +559,7 @@ constexpr int kApplyLanes = 4;
 
 __global__ void __launch_bounds__(kOptBlock * kApplyLanes) apply_kernel(const OptArgs a) {
     __shared__ double cdf[kCdfSmem];
+    grid_dependency_wait();
     const int sub = threadIdx.x & (kApplyLanes - 1);
     const int i = blockIdx.x * kOptBlock + (int)(threadIdx.x / kApplyLanes);
     const unsigned qmask = 0xfu << (threadIdx.x & 28u);   // this quad's lanes
@@ -963,12 +990,12 @@ cudaError_t launch_optimizer(const OptArgs &a, cudaStream_t s) {
     int k = (int)floor((double)a.elite_frac * (double)a.N);
     k = k < 1 ? 1 : (k > a.N ? a.N : k);
     const int kb = opt_blocks(k), nb = opt_blocks(a.N);
-    if (a.N <= kKeys * kSelSmall) select_kernel<kSelSmall><<<1, kSelSmall, 0, s>>>(a);
-    else select_kernel<kSel><<<1, kSel, 0, s>>>(a);
-    stats_kernel<<<kb, kOptBlock * kStatWarps, 0, s>>>(a);
-    finalize_kernel<<<1, kFin, 0, s>>>(a, kb);
-    apply_kernel<<<nb, kOptBlock * kApplyLanes, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = a.N <= kKeys * kSelSmall ? launch_dependent(select_kernel<kSelSmall>, 1, kSelSmall, s, a)
+                                             : launch_dependent(select_kernel<kSel>, 1, kSel, s, a);
+    if (e == cudaSuccess) e = launch_dependent(stats_kernel, kb, kOptBlock * kStatWarps, s, a);
+    if (e == cudaSuccess) e = launch_dependent(finalize_kernel, 1, kFin, s, a, kb);
+    if (e == cudaSuccess) e = launch_dependent(apply_kernel, nb, kOptBlock * kApplyLanes, s, a);
+    return e;
 }
 
 }  // namespace ih
