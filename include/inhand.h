@@ -254,8 +254,10 @@ ih_status sim_frames_argmin(ih_sim *sim, float *est_pose, int32_t *argmin);
 
 /* One tracking window of Algorithm 1: for k = 0..T-1, sim_step_track(frame0
  * + k, obs + k P 3, ...) writing est_pose[k] and argmin[k], then
- * optimizer_update(opt, update_index), launched as sim_step_frames,
- * sim_frames_argmin and the optimizer's kernels. obs is device float[T][P][3];
+ * optimizer_update(opt, update_index), launched as sim_step_frames, then
+ * sim_frames_argmin's kernel and the optimizer's kernels side by side (two
+ * branches of the graph: the argmin reads only the frames' buffers, the
+ * update sets i* and the window count itself). obs is device float[T][P][3];
  * est_pose (float[T][8]) and argmin (int32[T]) are device outputs (may be
  * NULL). The window's launches are captured once into a CUDA graph and
  * replayed on later calls with the same T, step shape and optimizer
